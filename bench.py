@@ -1,0 +1,341 @@
+"""Benchmark of the H-matrix hot path on GB300 (one JSON line on stdout).
+
+Workload (default): 65 536 Fibonacci points on the unit sphere, k_s = 16
+(rho = mu = 1, lambda = 2), U kernel, leaf 64, eta = 3, eps = 1e-4, FP32
+complex storage with FP64 Green's tensors, seeded N(0,1) complex RHS.
+
+One step = the whole hot path over the workload: H-matrix build (cluster
+tree, block partition, near-field Green's tensors, batched vector ACA,
+QR/SVD recompression, storage layout) followed by `--matvecs` H-matrix-vector
+products.  `value` is the H-matvec throughput in GB/s (algorithmic bytes of
+the stored H-matrix plus x and y per product / device time of the products);
+`build_s` is the device-synchronised build time per step.  The stored
+H-matrix (~8.5 GB) is far larger than L2, so no flush is needed between
+products.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (every S-th block of the same partition), on the host cores.
+Multi-GPU (torchrun): independent replicas, one per rank (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("H-matvec GB/s (% HBM peak) + build s, mixed vs plain GPU form at rel.err≤3ε")
+
+WORKLOADS = {
+    "sphere65536_ks16_U": dict(nc=65536, ks=16.0, kernel="U", leaf=64, eta=3.0, eps=1e-4),
+    "sphere1536_ks4_U": dict(nc=1536, ks=4.0, kernel="U", leaf=32, eta=3.0, eps=1e-4),
+}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel_file, kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, only if the kernel
+    source is unchanged since the capture (sha256 of the .cu file)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1706_09384_gb300", "csrc", kernel_file)
+    if not os.path.exists(p) or not os.path.exists(src):
+        return None
+    d = json.load(open(p)).get(kernel_name)
+    if not d:
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d.get("bytes_per_launch") if d.get("source_sha256") == h else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(num(r[2]) or 0 for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload: every
+    S-th block of the same partition is built (OpenMP over blocks), then the
+    oracle's serial H-matvec over those blocks is timed.  Returns GB/s counted
+    with the same algorithmic bytes as the GPU (complex64 entries + x, y)."""
+    import oracle as O
+    from paper_1706_09384_gb300 import inputs
+    pts = inputs.fibonacci_sphere(wl["nc"])
+    rho, lam, mu, om = inputs.material(wl["ks"])
+    pb = O.problem(rho, lam, mu, om, wl["kernel"])
+    stride = 97 if wl["nc"] > 10000 else 1
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    H = O.HMatrix(pb, pts, None, wl["eps"], wl["eta"], wl["leaf"], True, stride, threads)
+    build_s = time.perf_counter() - t0
+    blk, ra, r = H.blocks()
+    cl = H.clusters()
+    sz = cl["end"] - cl["begin"]
+    m, n = 3 * sz[blk["tau"]], 3 * sz[blk["sigma"]]
+    built = r >= 0
+    ent = np.where(blk["admissible"] == 1, r * (m + n), m * n)[built].sum()
+    nbytes = 8 * ent + 2 * 16 * 3 * wl["nc"]
+    x = inputs.random_rhs(3 * wl["nc"], seed=0)
+    H.matvec(x)
+    reps, t = 0, 0.0
+    while t < min(budget_s, 10.0) and reps < 20:
+        t1 = time.perf_counter()
+        H.matvec(x)
+        t += time.perf_counter() - t1
+        reps += 1
+    return {"value": nbytes * reps / t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": ("every %d-th block of the %d-point partition (%d of %d blocks) built by the "
+                       "oracle on %d threads in %.1f s; oracle H-matvec (serial, FP64) over those "
+                       "blocks timed %d times" % (stride, wl["nc"], int(built.sum()), len(blk),
+                                                  threads, build_s, reps)),
+            "build_threads": threads, "sample_build_s": build_s}
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(wl)
+    t0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        info = cpu_baseline(wl)
+        vals.append(info["value"])
+    wall = time.perf_counter() - t0
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload, **wl},
+           "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"],
+                            "value": v, "unit": "GB/s"},
+           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args, wl, world, rank, local):
+    import torch
+    from paper_1706_09384_gb300 import hm, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    pts = inputs.fibonacci_sphere(wl["nc"])
+    rho, lam, mu, om = inputs.material(wl["ks"])
+    x = torch.from_numpy(inputs.random_rhs(3 * wl["nc"], seed=rank)).to(dev)
+    y = torch.empty_like(x)
+
+    def build():
+        return hm.HMatrix.build(pts, None, rho, lam, mu, om, wl["kernel"], wl["eps"], wl["eta"],
+                                wl["leaf"])
+
+    H = None
+    for _ in range(args.warmup):
+        if H is not None:
+            H.free()
+        H = build()
+        for _ in range(args.matvecs):
+            H.matvec(x, y)
+    torch.cuda.synchronize()
+    stats = H.stats()
+    alg = stats["matvec_alg_bytes"]
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    build_ms, mv_ms = [], []
+    launches0 = hm.hm_kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start = ev()
+        t_start.record(st)
+        for _ in range(args.steps):
+            H.free()
+            b0, b1 = ev(), ev()
+            b0.record(st)
+            H = build()
+            b1.record(st)
+            m0, m1 = ev(), ev()
+            m0.record(st)
+            for _ in range(args.matvecs):
+                H.matvec(x, y)
+            m1.record(st)
+            torch.cuda.synchronize()
+            build_ms.append(b0.elapsed_time(b1))
+            mv_ms.append(m0.elapsed_time(m1))
+        t_end = ev()
+        t_end.record(st)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(world, t_start.elapsed_time(t_end))
+    mv_total = max_over_ranks(world, sum(mv_ms))
+    launches = hm.hm_kernel_launches() - launches0
+    value = world * alg * args.matvecs * args.steps / (mv_total * 1e-3) / 1e9
+    # per-kernel roofline of the dominant kernel (phase 2), events on the launching stream
+    prof = H.profile_matvec(reps=10)
+    peak, peak_kind = measured_peaks()
+    ph2 = prof["bytes"]["phase2"] / (prof["ms"]["phase2"] * 1e-3) / 1e9
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xh = torch.empty(3 * wl["nc"], dtype=torch.complex128).pin_memory()
+    xh.copy_(x.cpu())
+    yh = torch.empty_like(xh).pin_memory()
+    lib = hm.lib()
+    sp = hm._stream_ptr(None)
+    for _ in range(2):
+        lib.hm_matvec_host(H.h, 1, xh.data_ptr(), yh.data_ptr(), sp)
+    torch.cuda.synchronize()
+    reps = max(5, args.matvecs)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lib.hm_matvec_host(H.h, 1, xh.data_ptr(), yh.data_ptr(), sp)
+    e2e_s = (time.perf_counter() - t0) / reps
+    nb = 16 * 3 * wl["nc"]
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_c": wl["nc"], "kappa_s": wl["ks"],
+                   "kernel": wl["kernel"], "leaf": wl["leaf"], "eta": wl["eta"], "eps": wl["eps"],
+                   "storage": "fp32-complex", "green": "fp64",
+                   "matvecs_per_step": args.matvecs, "parallelism": "replicas" if world > 1 else "1gpu",
+                   "l2": "no flush: %.1f GB streamed per product >> 129 MB L2" % (alg / 1e9)},
+        "pct_hbm_peak": 100.0 * value / peak,
+        "build_s": statistics.mean(build_ms) / 1e3,
+        "matvec_ms": statistics.mean(mv_ms) / args.matvecs,
+        "hmatrix": {k: stats[k] for k in ("blocks", "dense_blocks", "lowrank_blocks", "C_sp",
+                                          "rank_aca_max", "rank_max", "tau_H", "stored_bytes",
+                                          "matvec_alg_bytes")},
+        "build_ms_phases": stats["ms"],
+        "roofline": {"bound": "hbm", "kernel": "mv_phase2", "achieved": ph2, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ph2 / peak,
+                     "traffic": kernel_traffic("matvec.cu", "mv_phase2"),
+                     "alg_bytes_per_launch": prof["bytes"]["phase2"],
+                     "ms_per_launch": prof["ms"]["phase2"], "kernels_ms": prof["ms"]},
+        "e2e": {"value": alg / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nb,
+                "d2h_bytes_per_step": nb, "api": "hm_matvec_host (pinned host buffers)"},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    H.free()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--matvecs", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="sphere65536_ks16_U", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, wl, world, rank)
+        return
+    world, rank, local = dist_setup(args.gpus)
+    run_gpu(args, wl, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

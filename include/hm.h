@@ -1,0 +1,199 @@
+/*
+ * hm.h — C ABI of the GB300 (sm_103a) H-matrix hot path for dense 3D
+ * time-harmonic elastodynamic systems, after Chaillat, Desiderio & Ciarlet,
+ * arXiv:1706.09384.
+ *
+ * The library builds, on one GPU, the H-matrix approximation A_H of the dense
+ * system A p = b of Eq. (syst_a) (Sec. 1), whose 3x3 block (i, j) is the
+ * Green's tensor U_w(x_i, x_j) of Eq. (elasto_U) or T_w(x_i, x_j) of
+ * Eq. (elasto_T), and applies it (Sec. 3.1) inside GMRES.  Steps:
+ *   cluster tree by box bisection (Sec. 2.1, "Clustering of the unknowns");
+ *   block partition with the box admissibility of Eq. (admissibility_cond_bis)
+ *     (Sec. 6.1) and eta (Sec. 6.2);
+ *   dense near-field blocks from the Green's tensors;
+ *   vector ACA with rank-3 updates and the sigma_3 pivot (Sec. 2.2 six steps
+ *     and stopping test Eq. (stop_part); Sec. 2.3 strategy 3);
+ *   QR + SVD recompression with eps_ACA (Sec. 3.2);
+ *   H-matrix-vector product (Sec. 3.1) and restarted GMRES.
+ *
+ * Conventions (all entry points)
+ *   - Point i owns the DOFs 3i, 3i+1, 3i+2 (point-major interleaving of the
+ *     3x3 block structure, Sec. 2.3).  Vectors are complex128 (interleaved
+ *     re/im doubles) of length 3*n_c in the caller's ORIGINAL point order;
+ *     with nrhs > 1 they are column-major 3*n_c x nrhs.
+ *   - k_s = omega sqrt(rho/mu), k_p = omega sqrt(rho/(lambda + 2 mu)) (Sec. 1).
+ *     Time convention e^{+i k r} (Eq. elasto_U).
+ *   - The diagonal 3x3 blocks (i = j) are opts->diag_value * I3 (the Green's
+ *     tensors are singular there; the paper's collocation quadrature of that
+ *     term, Sec. 4, is not part of this library).
+ *   - The library copies its inputs; the caller keeps ownership of every
+ *     pointer it passes.  Device pointers must be allocated on the current
+ *     device; "stream" is a cudaStream_t (NULL = legacy default stream).
+ *   - Every failure is reported as an hm_status; nothing aborts, no exception
+ *     crosses the ABI.  After an error a handle stays valid (or is NULL when
+ *     hm_build itself failed).  A handle must not be used from two host
+ *     threads at once.
+ *   - hm_last_error() returns a thread-local text describing the last error.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_matrix* hm_handle;
+
+typedef enum { HM_KERNEL_U = 0, HM_KERNEL_T = 1 } hm_kernel;
+typedef enum { HM_STORE_FP32 = 0, HM_STORE_BF16 = 1 } hm_storage;
+
+typedef enum {
+    HM_OK = 0,
+    HM_ERR_ARG = 1,       /* invalid argument (null pointer, size, NaN input ...) */
+    HM_ERR_CUDA = 2,      /* a CUDA call failed; see hm_last_error() */
+    HM_ERR_OOM = 3,       /* device memory exhausted */
+    HM_ERR_NOCONV = 4,    /* GMRES stopped at maxit above the tolerance */
+    HM_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    HM_ERR_NUMERIC = 6,   /* non-finite value produced (NaN/Inf) */
+    HM_ERR_UNSUPPORTED = 7
+} hm_status;
+
+/* Build options.  Always initialise with hm_opts_default(). */
+typedef struct {
+    int32_t storage;          /* hm_storage for dense blocks and factors (HM_STORE_FP32) */
+    int32_t aca_fp32;         /* 0: ACA residual rows/columns in FP64 (default), 1: FP32 */
+    double diag_value;        /* value of the i = j blocks: diag_value * I3 (1.0) */
+    double fp64_switch_ksr;   /* Green's tensors in FP64 where k_s r < this, FP32 beyond
+                                 (default +inf: always FP64) */
+    int32_t recompress;       /* 1: QR+SVD recompression of Sec. 3.2 (default), 0: keep ACA */
+    int32_t aca_max_rank;     /* initial ACA capacity in columns per block (0 = 144);
+                                 blocks that need more are re-run with twice the capacity */
+    int64_t workspace_bytes;  /* bound on the ACA workspace of one batch (0 = 24 GiB) */
+    int32_t verbose;          /* 1: phase timings on stderr */
+    int32_t reserved[7];
+} hm_opts;
+
+void hm_opts_default(hm_opts* opts);
+
+/* Builds A_H (Sec. 2-3.2) on the current device.
+ *   points   host, n_c x 3 row-major FP64 (x_i = y_i, one cloud: collocation, Sec. 4)
+ *   normals  host, n_c x 3 row-major FP64 unit normals n(y_j); required for
+ *            HM_KERNEL_T (Eq. elasto_T acts on y), ignored (may be NULL) for U
+ *   rho, lambda, mu, omega  material and circular frequency (Sec. 1), all > 0
+ *   kernel   HM_KERNEL_U or HM_KERNEL_T
+ *   eps      eps_ACA of Eq. (stop_part) and of the recompression (Sec. 3.2), in (0, 1)
+ *   eta      eta-hat of Eq. (admissibility_cond_bis) (the paper uses 3, Sec. 6.2), > 0
+ *   leaf_size  N_leaf: clusters with <= leaf_size points are not split (Sec. 2.1)
+ *   opts     NULL for defaults
+ *   stream   cudaStream_t for all work (the call returns after the build is complete)
+ *   out      receives the handle (NULL on error)
+ * Errors: HM_ERR_ARG (n_c < 1, non-finite or non-positive parameters, missing
+ * normals for T, non-finite coordinates), HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_build(const double* points, const double* normals, int64_t n_c, double rho,
+                   double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
+                   int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out);
+
+/* y = A_H x (Sec. 3.1: dense product on P^non-ad, U (V^H x) on P^ad).
+ *   x, y  DEVICE complex128, 3 n_c x nrhs column-major, original point order;
+ *         x is read, y is overwritten; they must not overlap.
+ *   nrhs  >= 1.  Work is enqueued on stream; the call does not synchronise.
+ * Errors: HM_ERR_ARG (null/overlapping pointers, nrhs < 1), HM_ERR_CUDA. */
+hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream);
+
+/* Same product with HOST buffers: x is copied to the device, y back to the
+ * host, inside the call (synchronises stream before returning).  Pinned host
+ * memory gives the fastest copies.  Errors as hm_matvec. */
+hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream);
+
+/* Solves A_H x = b by restarted GMRES(restart) with x_0 = 0 in FP64 vectors
+ * (Arnoldi by classical Gram-Schmidt with one re-orthogonalisation, complex
+ * Givens rotations), stopping when the true relative residual
+ * ||b - A_H x|| / ||b|| <= tol (checked at each restart) or after maxit
+ * matvecs.  b, x: DEVICE complex128, length 3 n_c, original order.
+ *   iters, relres: host outputs (may be NULL).
+ * Errors: HM_ERR_ARG, HM_ERR_NOCONV (maxit reached; x holds the last iterate),
+ * HM_ERR_CUDA. */
+hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double tol,
+                   int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/* Writes a JSON object (NUL-terminated) with the build statistics: n_c, tree
+ * depth, cluster and block counts, sparsity constant C_sp (Sec. 2.1), ACA
+ * and recompressed ranks (as in the rank tables of Sec. 7.2), stored bytes,
+ * compression tau(H) = N_s / N^2 (Sec. 7.2), phase times in ms.
+ * Errors: HM_ERR_ARG (cap too small: the required size is in *needed if non-NULL). */
+hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed);
+
+/* ---- inspection (host copies; used to check the GPU path piece by piece) ---- */
+
+/* One cluster of the tree T_I: points perm[begin..end) (tree order). */
+typedef struct {
+    int64_t begin, end;
+    int64_t child0, child1;   /* cluster indices, -1 for a leaf */
+    int32_t level, is_leaf;
+    double lo[3], hi[3];      /* tight bounding box (Sec. 6.1) */
+} hm_cluster;
+
+/* One block tau x sigma of the partition P. */
+typedef struct {
+    int64_t tau, sigma;       /* cluster indices */
+    int32_t admissible;       /* 1 = low rank (P^ad), 0 = dense (P^non-ad) */
+    int32_t rank_aca;         /* ACA rank (multiple of 3), 0 for dense blocks */
+    int32_t rank;             /* stored rank after recompression, 0 for dense blocks */
+    int32_t pad_;
+} hm_block;
+
+/* Sizes of the tree and partition. */
+hm_status hm_sizes(hm_handle h, int64_t* n_c, int64_t* n_clusters, int64_t* n_blocks);
+/* perm[p] = original index of the point at tree position p (n_c entries, host). */
+hm_status hm_get_tree(hm_handle h, int64_t* perm, hm_cluster* clusters);
+hm_status hm_get_blocks(hm_handle h, hm_block* blocks);
+/* Stored data of block b widened to complex128 on the host: dense block
+ * (3|tau| x 3|sigma| column-major) into a, or the factors U (3|tau| x rank) into
+ * a and V (3|sigma| x rank) into v, with block = U V^H; rows in tree order. */
+hm_status hm_get_block_data(hm_handle h, int64_t b, void* a, void* v);
+
+/* ---- direct kernel access ---- */
+
+/* Evaluates K(x_q, y_q) for q = 0..npairs-1 on the GPU in FP64 (Eq. elasto_U or
+ * Eq. elasto_T; for T the normal is taken at y).  x, y, ny: DEVICE npairs x 3 FP64;
+ * ny may be NULL for U.  out: DEVICE npairs x 9 complex128, each 3x3 row-major.
+ * Points with x_q == y_q give diag_value * I3. */
+hm_status hm_green_eval(int32_t kernel, double rho, double lambda, double mu, double omega,
+                        double diag_value, const double* x, const double* y, const double* ny,
+                        int64_t npairs, void* out, void* stream);
+
+/* Builds a handle from a given tree, partition and block data (host arrays, in
+ * the layouts of hm_get_tree / hm_get_blocks / hm_get_block_data, block data
+ * concatenated in block order: dense blocks 9|tau||sigma| entries, low-rank
+ * blocks U then V), converting them to the storage precision.  Used to apply
+ * an H-matrix computed elsewhere (e.g. restored from a file). */
+hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
+                    const hm_cluster* clusters, int64_t n_blocks, const hm_block* blocks,
+                    const void* data, const hm_opts* opts, void* stream, hm_handle* out);
+
+/* ---- measurement ---- */
+
+/* Runs `reps` products on internal vectors (x = 1 in tree order) and reports
+ * the average device time of each kernel of the product, measured with CUDA
+ * events on `stream`: ms[0] gather x, ms[1] phase 1 (t = V^H x), ms[2]
+ * phase 2 (dense blocks and U t), ms[3] scatter y.  bytes[0] / bytes[1] are
+ * the algorithmic bytes of phases 1 / 2 (stored entries actually used, plus
+ * the x, t and y entries each phase must read or write once); bytes[2] is the
+ * algorithmic byte count of one whole product (stored H-matrix + x + y).
+ * Errors: HM_ERR_ARG, HM_ERR_CUDA. */
+hm_status hm_profile_matvec(hm_handle h, int32_t reps, double* ms, int64_t* bytes, void* stream);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+int64_t hm_kernel_launches(void);
+
+void hm_free(hm_handle h);
+const char* hm_status_string(hm_status s);
+const char* hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -4,6 +4,7 @@
 differently, so the oracle rounds the same everywhere.
 """
 import os
+import platform
 import subprocess
 import sys
 
@@ -13,6 +14,9 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
+    stamp = LIB + ".host"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
                                              os.path.getmtime(os.path.join(HERE, "oracle.h")))):
@@ -21,6 +25,8 @@ def build(force: bool = False) -> str:
            "-ffp-contract=off", "-Wall", "-Wno-unused-variable", SRC, "-o", LIB + ".tmp", "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return LIB
 
 

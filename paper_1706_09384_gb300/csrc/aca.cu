@@ -1,0 +1,479 @@
+// aca.cu — batched vector ACA (Sec. 2.2, partially pivoted ACA in six steps,
+// with the rank-3 update and sigma_3 pivot of Sec. 2.3, strategy 3).
+//
+// One CTA compresses one admissible block at a time (persistent grid, dynamic
+// queue).  Per step:
+//   1. row block R(i^, :) = A(i^, :) - U(i^, :) V^H          (3 x 3n, FP64)
+//   2. j^ = argmax over unused j of sigma_3(R(i^, j)); gamma = R(i^, j^)^{-1}
+//      (a singular maximum, sigma_3 <= 1e-12 s_ref, retires row i^ and
+//      restarts on the lowest unused row; s_ref = largest sigma_1 seen)
+//   3. column block C = A(:, j^) - U V(j^, :)^H               (3m x 3)
+//   4. next i^ = argmax over unused i of sigma_3(C(i, :)), on C before the update
+//   5. U_{k+1} = C gamma, V_{k+1} = R(i^, :)^H
+//   6. ||B_{k+1}||_F^2 = ||B_k||^2 + 2 Re <B_k, dB> + ||dB||^2, FP64
+//   stop when ||dB||_F <= eps ||B_{k+1}||_F (Eq. stop_part read for rank 3),
+//   when no row is left, or at full rank.  Ties in an argmax go to the lowest
+//   index.  The factors live in a global FP64 workspace with a fixed column
+//   capacity; a block that needs more reports an overflow and is re-run with a
+//   larger capacity by the host.
+//
+// sigma_1 and sigma_3 of a 3x3 block M are computed from the invariants of
+// M^H M: e1 = ||M||_F^2, e2 = sum of |2x2 minors|^2, e3 = |det M|^2 (the
+// coefficients of its characteristic polynomial), whose roots follow from
+// the trigonometric solution of the cubic; when the smallest root is below
+// 1e-4 of the largest it is recomputed from the deflated quadratic
+// (sum = (e2 - e3/l1)/l1, product = e3/l1), which keeps sigma_3 accurate to
+// the precision of det M.
+#include <algorithm>
+
+#include "hm_internal.h"
+
+namespace {
+
+constexpr int AT = 256;
+constexpr int AW = AT / 32;
+constexpr double SING_REL = 1e-12;
+
+struct Cof {
+    double2 c[9];   // cofactor matrix, row-major
+    double2 det;
+};
+
+HM_D void cofactors(const double2 M[9], Cof& o) {
+    auto m = [&](int r, int c) { return M[3 * r + c]; };
+    auto minor2 = [&](int r0, int r1, int c0, int c1) {
+        return csub(cmul(m(r0, c0), m(r1, c1)), cmul(m(r0, c1), m(r1, c0)));
+    };
+    o.c[0] = minor2(1, 2, 1, 2);
+    o.c[1] = cscale(minor2(1, 2, 0, 2), -1.0);
+    o.c[2] = minor2(1, 2, 0, 1);
+    o.c[3] = cscale(minor2(0, 2, 1, 2), -1.0);
+    o.c[4] = minor2(0, 2, 0, 2);
+    o.c[5] = cscale(minor2(0, 2, 0, 1), -1.0);
+    o.c[6] = minor2(0, 1, 1, 2);
+    o.c[7] = cscale(minor2(0, 1, 0, 2), -1.0);
+    o.c[8] = minor2(0, 1, 0, 1);
+    o.det = cadd(cadd(cmul(M[0], o.c[0]), cmul(M[1], o.c[1])), cmul(M[2], o.c[2]));
+}
+
+HM_D double2 minor2(const double2 M[9], int r0, int r1, int c0, int c1) {
+    return csub(cmul(M[3 * r0 + c0], M[3 * r1 + c1]), cmul(M[3 * r0 + c1], M[3 * r1 + c0]));
+}
+
+// sigma_1 and sigma_3 of a 3x3 complex block (cofactors streamed one at a time).
+HM_D void sv13(const double2 M[9], double& s1, double& s3) {
+    double e1 = 0.0, e2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) e1 += cabs2(M[q]);
+    const double2 c0 = minor2(M, 1, 2, 1, 2);
+    const double2 c1 = minor2(M, 1, 2, 0, 2);   // cofactor is -c1
+    const double2 c2 = minor2(M, 1, 2, 0, 1);
+    const double2 det = cadd(csub(cmul(M[0], c0), cmul(M[1], c1)), cmul(M[2], c2));
+    e2 = cabs2(c0) + cabs2(c1) + cabs2(c2);
+    e2 += cabs2(minor2(M, 0, 2, 1, 2)) + cabs2(minor2(M, 0, 2, 0, 2)) + cabs2(minor2(M, 0, 2, 0, 1));
+    e2 += cabs2(minor2(M, 0, 1, 1, 2)) + cabs2(minor2(M, 0, 1, 0, 2)) + cabs2(minor2(M, 0, 1, 0, 1));
+    const double e3 = cabs2(det);
+    if (e1 == 0.0) {
+        s1 = 0.0;
+        s3 = 0.0;
+        return;
+    }
+    const double mm = e1 / 3.0;
+    const double p = fmax(mm * mm - e2 / 3.0, 0.0);
+    double l1, l3;
+    if (p <= 0.0) {
+        l1 = mm;
+        l3 = mm;
+    } else {
+        const double q = mm * mm * mm - 0.5 * mm * e2 + 0.5 * e3;
+        const double sp = sqrt(p);
+        const double cth = fmin(fmax(q / (p * sp), -1.0), 1.0);
+        const double th = acos(cth) / 3.0;
+        l1 = mm + 2.0 * sp * cos(th);
+        l3 = mm + 2.0 * sp * cos(th + 2.0943951023931954923);
+    }
+    if (l3 < 1e-4 * l1) {  // deflate: the two small roots from the quadratic
+        const double P = e3 / l1;
+        const double s = (e2 - P) / l1;
+        const double disc = fmax(s * s - 4.0 * P, 0.0);
+        const double l2 = 0.5 * (s + sqrt(disc));
+        l3 = l2 > 0.0 ? P / l2 : 0.0;
+    }
+    s1 = sqrt(fmax(l1, 0.0));
+    s3 = sqrt(fmax(l3, 0.0));
+}
+
+struct BlockRed {
+    double v[AW];
+    int64_t i[AW];
+    double w[AW];
+};
+
+// CTA argmax of (v, i) (ties -> lowest i) and max of w; result to all threads.
+HM_D void block_argmax(double& v, int64_t& i, double& w, BlockRed& sh) {
+    warp_argmax(v, i);
+    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh.v[wid] = v;
+        sh.i[wid] = i;
+        sh.w[wid] = w;
+    }
+    __syncthreads();
+    v = sh.v[0];
+    i = sh.i[0];
+    w = sh.w[0];
+    for (int q = 1; q < AW; ++q) {
+        argmax_merge(v, i, sh.v[q], sh.i[q]);
+        w = fmax(w, sh.w[q]);
+    }
+}
+
+template <int N>
+HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) x[q] = warp_sum(x[q]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < N; ++q) sh[q][wid] = x[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double s = 0.0;
+        for (int w = 0; w < AW; ++w) s += sh[q][w];
+        x[q] = s;
+    }
+}
+
+__global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* __restrict__ pts,
+                                                 const double* __restrict__ nrm,
+                                                 const AcaJob* __restrict__ jobs, int64_t njobs,
+                                                 int* counter, double2* work,
+                                                 unsigned char* flags, int64_t flag_stride,
+                                                 double2* rowbuf, double2* colbuf,
+                                                 int64_t rb_stride, int64_t cb_stride,
+                                                 int capmax, double eps, AcaResult* res) {
+    extern __shared__ double2 smem[];
+    double2* Urow = smem;             // 3 x capmax: U(3 i^ + a, p)
+    double2* Vrow = smem + 3 * capmax;  // 3 x capmax: V(3 j^ + c, p)
+    __shared__ BlockRed red;
+    __shared__ double sums[36][AW];
+    __shared__ int64_t s_job, s_ihat, s_jhat, s_inext;
+    __shared__ int s_k;
+    __shared__ double s_normB2, s_sref, s_best, s_dB2;
+    __shared__ double2 s_gam[9];
+    __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double2* R = rowbuf + blockIdx.x * rb_stride;   // [a][3n], row-major
+    double2* C = colbuf + blockIdx.x * cb_stride;   // [3m][3], row-major
+    unsigned char* used = flags + blockIdx.x * flag_stride;
+
+    for (;;) {
+        if (tid == 0) s_job = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t job = s_job;
+        if (job >= njobs) return;
+        const AcaJob J = jobs[job];
+        const int64_t m = J.m, n = J.n, m3 = 3 * m, n3 = 3 * n;
+        double2* U = work + J.u_off;
+        double2* V = work + J.v_off;
+        unsigned char* urow = used;
+        unsigned char* ucol = used + m;
+        for (int64_t q = tid; q < m + n; q += AT) used[q] = 0;
+        if (tid == 0) {
+            s_k = 0;
+            s_ihat = 0;
+            s_normB2 = 0.0;
+            s_sref = 0.0;
+            s_stop = 0;
+        }
+        const int64_t steps_max = m < n ? m : n;
+        const double* xr = pts + 3 * J.tau_begin;
+        const double* xc = pts + 3 * J.sig_begin;
+        const double* nc = nrm ? nrm + 3 * J.sig_begin : nullptr;
+        __syncthreads();
+
+        while (s_stop == 0) {
+            const int k = s_k;
+            const int64_t ihat = s_ihat;
+            for (int t = tid; t < 3 * k; t += AT) {
+                const int a = t / k, p = t - a * k;
+                Urow[a * capmax + p] = U[3 * ihat + a + (int64_t)p * m3];
+            }
+            __syncthreads();
+            // ---- step 1-2: row residual and sigma_3 pivot search ----
+            double best = -1.0, s1max = 0.0;
+            int64_t bj = -1;
+            for (int64_t j = tid; j < n; j += AT) {
+                double2 G[9];
+                if (J.tau_begin + ihat == J.sig_begin + j) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
+                } else {
+                    green_tensor(gp, xr + 3 * ihat, xc + 3 * j, nc ? nc + 3 * j : nullptr, G);
+                }
+                for (int p = 0; p < k; ++p) {
+                    const double2* vp = V + (int64_t)p * n3 + 3 * j;
+                    const double2 v0 = vp[0], v1 = vp[1], v2 = vp[2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const double2 u = Urow[a * capmax + p];
+                        cfms_conj(G[3 * a + 0], u, v0);
+                        cfms_conj(G[3 * a + 1], u, v1);
+                        cfms_conj(G[3 * a + 2], u, v2);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) R[a * n3 + 3 * j + c] = G[3 * a + c];
+                double s1, s3;
+                sv13(G, s1, s3);
+                s1max = fmax(s1max, s1);
+                if (!ucol[j]) argmax_merge(best, bj, s3, j);
+            }
+            block_argmax(best, bj, s1max, red);
+            if (tid == 0) {
+                s_sref = fmax(s_sref, s1max);
+                s_jhat = bj;
+                s_best = best;
+            }
+            __syncthreads();
+            if (s_jhat < 0) {  // no comparable candidate: columns remain, so values were NaN
+                if (tid == 0) s_stop = (k / 3 < steps_max) ? 3 : 1;
+                __syncthreads();
+                break;
+            }
+            if (!(s_best > SING_REL * s_sref)) {
+                // singular pivot: retire row i^, restart on the lowest unused row
+                if (tid == 0) urow[ihat] = 1;
+                __syncthreads();
+                double v = -1.0, dummy = 0.0;
+                int64_t li = -1;
+                for (int64_t i = tid; i < m; i += AT)
+                    if (!urow[i]) {
+                        argmax_merge(v, li, 0.0, i);
+                        break;
+                    }
+                block_argmax(v, li, dummy, red);
+                if (tid == 0) {
+                    if (li < 0 || !(s_best == s_best))
+                        s_stop = (s_best == s_best) ? 1 : 3;
+                    else
+                        s_ihat = li;
+                }
+                __syncthreads();
+                continue;
+            }
+            const int64_t jhat = s_jhat;
+            if (tid == 0) {
+                double2 P[9];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) P[3 * a + c] = R[a * n3 + 3 * jhat + c];
+                Cof cf;
+                cofactors(P, cf);
+                // inverse = adj / det, adj = cofactor^T
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) s_gam[3 * a + c] = cdiv(cf.c[3 * c + a], cf.det);
+                urow[ihat] = 1;
+                ucol[jhat] = 1;
+            }
+            for (int t = tid; t < 3 * k; t += AT) {
+                const int c = t / k, p = t - c * k;
+                Vrow[c * capmax + p] = V[3 * jhat + c + (int64_t)p * n3];
+            }
+            __syncthreads();
+            // ---- step 3-4: column residual and next row ----
+            double bestr = -1.0, unused = 0.0;
+            int64_t bi = -1;
+            for (int64_t i = tid; i < m; i += AT) {
+                double2 G[9];
+                if (J.tau_begin + i == J.sig_begin + jhat) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
+                } else {
+                    green_tensor(gp, xr + 3 * i, xc + 3 * jhat, nc ? nc + 3 * jhat : nullptr, G);
+                }
+                for (int p = 0; p < k; ++p) {
+                    const double2* up = U + (int64_t)p * m3 + 3 * i;
+                    const double2 u0 = up[0], u1 = up[1], u2 = up[2];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const double2 v = Vrow[c * capmax + p];
+                        cfms_conj(G[0 + c], u0, v);
+                        cfms_conj(G[3 + c], u1, v);
+                        cfms_conj(G[6 + c], u2, v);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) C[9 * i + q] = G[q];
+                if (!urow[i]) {
+                    double s1, s3;
+                    sv13(G, s1, s3);
+                    argmax_merge(bestr, bi, s3, i);
+                }
+            }
+            block_argmax(bestr, bi, unused, red);
+            if (tid == 0) s_inext = bi;
+            // ---- step 5: new factor columns and their Gram matrices ----
+            double g[36];
+#pragma unroll
+            for (int q = 0; q < 36; ++q) g[q] = 0.0;
+            if (k + 3 <= J.cap) {
+                for (int64_t r = tid; r < m3; r += AT) {
+                    double2 un[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) cfma(acc, C[3 * r + a], s_gam[3 * a + q]);
+                        un[q] = acc;
+                        U[r + (int64_t)(k + q) * m3] = acc;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int q2 = 0; q2 < 3; ++q2) {
+                            const double2 z = cconjmul(un[q], un[q2]);
+                            g[2 * (3 * q + q2)] += z.x;
+                            g[2 * (3 * q + q2) + 1] += z.y;
+                        }
+                }
+                for (int64_t c = tid; c < n3; c += AT) {
+                    double2 vn[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vn[a] = cconj(R[a * n3 + c]);
+                        V[c + (int64_t)(k + a) * n3] = vn[a];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int q2 = 0; q2 < 3; ++q2) {
+                            const double2 z = cconjmul(vn[q], vn[q2]);
+                            g[18 + 2 * (3 * q + q2)] += z.x;
+                            g[18 + 2 * (3 * q + q2) + 1] += z.y;
+                        }
+                }
+            }
+            block_sum<36>(g, sums);  // includes the barrier that publishes U, V
+            if (tid == 0) {
+                // ||dB||^2 = sum_{q,q'} (Un_q^H Un_q')(Vn_q'^H Vn_q)
+                double dB2 = 0.0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int q2 = 0; q2 < 3; ++q2) {
+                        const double2 gu = make_double2(g[2 * (3 * q + q2)], g[2 * (3 * q + q2) + 1]);
+                        const double2 gv =
+                            make_double2(g[18 + 2 * (3 * q2 + q)], g[18 + 2 * (3 * q2 + q) + 1]);
+                        dB2 += cmul(gu, gv).x;
+                    }
+                s_dB2 = dB2;
+            }
+            if (k + 3 > J.cap) {
+                if (tid == 0) s_stop = 2;
+                __syncthreads();
+                break;
+            }
+            // ---- step 6: cross term <B_k, dB> = sum_{p,q} (U_p^H Un_q)(Vn_q^H V_p) ----
+            double cre = 0.0, cim = 0.0;
+            for (int p = wid; p < k; p += AW) {
+                double x[6] = {0, 0, 0, 0, 0, 0}, y[6] = {0, 0, 0, 0, 0, 0};
+                const double2* Up = U + (int64_t)p * m3;
+                const double2* Vp = V + (int64_t)p * n3;
+                for (int64_t r = lane; r < m3; r += 32) {
+                    const double2 u = Up[r];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const double2 z = cconjmul(u, U[r + (int64_t)(k + q) * m3]);
+                        x[2 * q] += z.x;
+                        x[2 * q + 1] += z.y;
+                    }
+                }
+                for (int64_t c = lane; c < n3; c += 32) {
+                    const double2 v = Vp[c];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const double2 z = cconjmul(V[c + (int64_t)(k + q) * n3], v);
+                        y[2 * q] += z.x;
+                        y[2 * q + 1] += z.y;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    x[q] = warp_sum(x[q]);
+                    y[q] = warp_sum(y[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const double2 z = cmul(make_double2(x[2 * q], x[2 * q + 1]),
+                                           make_double2(y[2 * q], y[2 * q + 1]));
+                    cre += z.x;
+                    cim += z.y;
+                }
+            }
+            double cr[2] = {lane == 0 ? cre : 0.0, lane == 0 ? cim : 0.0};
+            block_sum<2>(cr, sums);
+            if (tid == 0) {
+                const double dB2 = s_dB2;
+                const double nb2 = s_normB2 + 2.0 * cr[0] + dB2;
+                s_normB2 = nb2;
+                const int k2 = k + 3;
+                s_k = k2;
+                if (!(nb2 == nb2) || !(dB2 == dB2))
+                    s_stop = 3;
+                else if (sqrt(dB2) <= eps * sqrt(fmax(nb2, 0.0)))
+                    s_stop = 1;
+                else if (s_inext < 0 || k2 / 3 >= steps_max)
+                    s_stop = 1;
+                else
+                    s_ihat = s_inext;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            res[job].k = s_k;
+            res[job].status = s_stop == 1 ? 0 : (s_stop == 2 ? 1 : 2);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
+                const AcaJob* d_jobs, int64_t njobs, double2* d_work, unsigned char* d_flags,
+                int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
+                int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
+                int* d_counter, cudaStream_t st) {
+    if (njobs == 0) return;
+    const size_t smem = (size_t)6 * capmax * sizeof(double2);
+    if (smem > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    HM_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
+    aca_kernel<<<nctas, AT, smem, st>>>(gp, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
+                                        d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
+                                        colbuf_stride, capmax, eps, d_res);
+                                        HM_LAUNCHED();
+    HM_CUDA(cudaGetLastError());
+}
+
+int aca_ctas_per_sm(int capmax) {
+    int nb = 0;
+    const size_t smem = (size_t)6 * capmax * sizeof(double2);
+    if (smem > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aca_kernel, AT, smem));
+    return nb > 0 ? nb : 1;
+}

@@ -1,0 +1,190 @@
+// hm_internal.h — internal declarations shared by the libhm CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+#include "green.cuh"
+
+// Thrown inside the library only; every entry point converts it to an hm_status.
+struct hm_error {
+    hm_status st;
+    std::string msg;
+};
+void hm_set_error(const std::string& msg);
+[[noreturn]] void hm_throw(hm_status st, const std::string& msg);
+void hm_check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define HM_CUDA(call) hm_check_cuda((call), #call, __FILE__, __LINE__)
+
+// Kernel launch counter (reported by hm_kernel_launches).
+extern std::atomic<long long> g_hm_launches;
+#define HM_LAUNCHED() g_hm_launches.fetch_add(1, std::memory_order_relaxed)
+
+// Device allocation owned by the handle (freed in hm_free).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+void* hm_dmalloc(std::vector<DevBuf>& owner, size_t bytes, cudaStream_t st, bool zero);
+
+// ---------------- tree + partition (tree.cu) ----------------
+struct TreeResult {
+    std::vector<hm_cluster> clusters;   // BFS order, root = 0
+    std::vector<int64_t> perm;          // perm[p] = original index at tree position p
+    int depth = 0;
+};
+// pts_p (device, n x 3) is permuted in place into tree order; d_perm receives perm.
+TreeResult build_cluster_tree(double* d_pts, int64_t* d_perm, int64_t nc, int64_t leaf,
+                              cudaStream_t st);
+// Level-synchronous block-cluster-tree traversal (Sec. 2.1) with the box
+// admissibility of Sec. 6.1.  Returns blocks (tau, sigma, admissible) in level order.
+std::vector<hm_block> build_partition(const std::vector<hm_cluster>& cl, double eta,
+                                      cudaStream_t st);
+
+// ---------------- matvec storage plan (matvec.cu) ----------------
+// One chunk = rows of one leaf cluster of a block's row set (dense block, U
+// factor) or column set (V factor); column-major with ld = padded rows.
+struct Chunk {
+    int64_t data;      // element offset (complex) into the arena
+    int32_t ld;        // padded row count (even)
+    int32_t rows;      // 3 |leaf|
+    int32_t ncols;     // dense: 3|sigma|; factors: rank
+    int32_t kind;      // 0 dense, 1 U, 2 V
+    int64_t vec;       // dense: x offset (tree order DOF); U/V: t offset
+    int64_t block;     // block index
+    int64_t leaf_dof;  // first tree-order DOF of the chunk's leaf
+};
+
+struct MatvecPlan {
+    // per leaf (row side): list of dense + U chunks; per leaf (col side): V chunks
+    std::vector<int64_t> row_leaf_begin;   // CSR over leaves
+    std::vector<int32_t> row_items;        // chunk ids
+    std::vector<int64_t> col_leaf_begin;
+    std::vector<int32_t> col_items;
+    std::vector<Chunk> chunks;
+    std::vector<int64_t> leaf_dof_begin;   // first DOF (tree order) of each leaf
+    std::vector<int32_t> leaf_rows;        // 3 |leaf|
+    int64_t arena_elems = 0;               // complex entries in the arena
+    int64_t t_elems = 0;                   // entries of the t = V^H x workspace
+};
+
+MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vector<hm_block>& blk,
+                             std::vector<int64_t>& t_off);
+struct MatvecDev;  // device side of the plan (matvec.cu)
+MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
+                             cudaStream_t st);
+void matvec_dev_destroy(MatvecDev* m);
+void* matvec_arena(MatvecDev* m);           // float2* (fp32) or bf16 pairs
+// y_p (tree order, float2) = A_H x_p (tree order, float2)
+void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);
+// Copies staged column-major blocks / factors (FP32, one pointer per block:
+// dense block or U in src_u, V in src_v, leading dimension 3|tau| / 3|sigma|)
+// into the chunks of the arena.
+void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<hm_block>& blk,
+                        const std::vector<hm_cluster>& cl, const std::vector<const float2*>& src_u,
+                        const std::vector<const float2*>& src_v, cudaStream_t st);
+// Gather/scatter between original order (complex128) and tree order (complex64).
+void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_t nc,
+                     cudaStream_t st);
+void launch_scatter_y(const int64_t* d_perm, const float2* yp, double2* y, int64_t nc,
+                      cudaStream_t st);
+// The three parts of the product, for per-kernel timing.
+void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st);
+void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);
+// algorithmic bytes: [0] phase 1, [1] phase 2, [2] whole product (given ndof)
+void matvec_alg_bytes(const MatvecDev* m, int64_t ndof, int64_t out[3]);
+int64_t matvec_stored_bytes(const MatvecDev* m);
+int64_t matvec_dense_bytes(const MatvecDev* m);
+
+// ---------------- near field (nearfield.cu) ----------------
+// Writes all dense chunks (kind 0) of the plan into the FP32 arena.
+void assemble_dense(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
+                    const MatvecPlan& plan, const std::vector<hm_block>& blocks,
+                    const std::vector<hm_cluster>& cl, MatvecDev* mv, std::vector<DevBuf>& owner,
+                    cudaStream_t st);
+void launch_green_eval(const GreenParams& gp, const double* x, const double* y,
+                       const double* ny, int64_t npairs, double2* out, cudaStream_t st);
+
+// ---------------- ACA + recompression (aca.cu, recompress.cu) ----------------
+struct AcaJob {              // one admissible block
+    int64_t tau_begin, m;    // tree-order point ranges
+    int64_t sig_begin, n;
+    int64_t u_off, v_off;    // complex128 offsets of U (3m x cap), V (3n x cap) in workspace
+    int32_t cap;             // column capacity (multiple of 3)
+    int32_t pad_;
+};
+struct AcaResult {
+    int32_t k;               // ACA rank (columns), multiple of 3
+    int32_t status;          // 0 converged, 1 capacity overflow, 2 non-finite
+};
+void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
+                const AcaJob* d_jobs, int64_t njobs, double2* d_work, unsigned char* d_flags,
+                int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
+                int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
+                int* d_counter, cudaStream_t st);
+int aca_ctas_per_sm(int capmax);
+// Core of the recompression for a batch: ranks r' and the k x r' transforms.
+void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64_t>& v_off,
+                      const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
+                      const std::vector<int32_t>& k, int recompress, double2* d_work, double eps,
+                      std::vector<int32_t>& ranks, std::vector<int64_t>& s_off, cudaStream_t st);
+// Writes U' = U T_U / V' = V T_V (FP32, column-major, ld = factor rows) for
+// row slices: job_of[i], which[i] (0 = U, 1 = V), first row row0[i], rows[i]
+// (<= 192), destination dst[i] (element offset of the slice's first row in
+// d_out), ld[i] (= factor rows).
+void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
+                      const std::vector<int32_t>& which, const std::vector<int64_t>& row0,
+                      const std::vector<int32_t>& rows, const std::vector<int64_t>& dst,
+                      const std::vector<int32_t>& ld, const std::vector<int32_t>& ranks,
+                      const double2* d_work, float2* d_out, cudaStream_t st);
+void recompress_release(void* batch, cudaStream_t st);
+
+// ---------------- GMRES (gmres.cu) ----------------
+struct GmresResult {
+    int iters;
+    double relres;
+    int converged;
+};
+struct hm_matrix;
+GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int restart, double tol,
+                        int maxit, cudaStream_t st);
+
+// ---------------- the handle ----------------
+struct hm_matrix {
+    int device = 0;
+    int64_t nc = 0;
+    int kernel = 0;
+    double rho = 1, lam = 2, mu = 1, omega = 1, eps = 1e-4, eta = 3;
+    int64_t leaf = 32;
+    hm_opts opts{};
+    GreenParams gp{};
+
+    std::vector<DevBuf> owner;       // every device allocation of the handle
+    double* d_pts_p = nullptr;       // tree-order points (n x 3)
+    double* d_nrm_p = nullptr;       // tree-order normals (n x 3) or null
+    int64_t* d_perm = nullptr;
+
+    std::vector<int64_t> perm;
+    std::vector<hm_cluster> clusters;
+    std::vector<hm_block> blocks;
+    int depth = 0;
+
+    MatvecPlan plan;
+    MatvecDev* mv = nullptr;
+    float2* d_xp = nullptr;          // tree-order work vectors (complex64)
+    float2* d_yp = nullptr;
+    double2* d_xh = nullptr;         // host-API staging (complex128)
+    double2* d_yh = nullptr;
+    int64_t staging_cols = 0;
+
+    // statistics
+    double t_tree_ms = 0, t_part_ms = 0, t_near_ms = 0, t_aca_ms = 0, t_recomp_ms = 0,
+           t_copy_ms = 0, t_total_ms = 0;
+    int64_t aca_overflow_reruns = 0;
+    int64_t aca_batches = 0;
+};

@@ -1,0 +1,505 @@
+// matvec.cu — H-matrix-vector product y = A_H x (Sec. 3.1): dense product on
+// the non-admissible leaves, U (V^H x) on the admissible ones.
+//
+// Storage layout ("chunk-major"): every block is cut along the leaf clusters
+// of its row set (dense blocks, U factors) or column set (V factors).  A
+// chunk is a column-major (ld x ncols) complex matrix, ld = 3|leaf| rounded up
+// to an even count so each column starts on a 16-byte boundary.  All chunks
+// that feed the rows of one leaf are stored back to back, so the product
+// streams the arena once, front to back.
+//
+// Phase 1:  t_b = V_b^H x_sigma     (per column leaf; partial sums by atomics)
+// Phase 2:  y_l = sum D x_sigma + sum U_b t_b   (per row leaf)
+// Both phases are HBM-bound (one complex FMA per stored complex entry).
+// Work items are slices of a leaf's chunk list of bounded byte size, so the
+// grid load-balances; each CTA keeps partial sums per warp in registers and
+// reduces them once.
+#include <algorithm>
+#include <cstring>
+
+#include "hm_internal.h"
+
+struct DevChunk {
+    int64_t data;   // arena element offset
+    int64_t vec;    // x (kind 0) or t (kind 1/2) element offset
+    int32_t ld;
+    int32_t ncols;
+    int32_t kind;
+    int32_t rows;
+};
+struct WorkItem {
+    int64_t dof;      // first tree-order DOF of the leaf
+    int32_t rows;     // 3 |leaf|
+    int32_t ld;
+    int32_t first;    // chunk ids [first, last)
+    int32_t last;
+};
+
+struct MatvecDev {
+    int storage = 0;
+    float2* arena = nullptr;
+    int64_t arena_elems = 0;
+    DevChunk* chunks = nullptr;
+    WorkItem* items1 = nullptr;   // phase 1 (V)
+    WorkItem* items2 = nullptr;   // phase 2 (dense + U)
+    int32_t* order1 = nullptr;    // chunk ids referenced by items, phase 1
+    int32_t* order2 = nullptr;
+    int64_t n1 = 0, n2 = 0;
+    float2* t = nullptr;
+    int64_t t_elems = 0;
+    int64_t dense_elems = 0;
+    int64_t lr_elems = 0;
+    int64_t alg_v = 0;      // stored entries (rows x cols, no padding) of V chunks
+    int64_t alg_du = 0;     // ... of dense and U chunks
+};
+
+namespace {
+
+constexpr int MV_THREADS = 256;
+constexpr int MV_WARPS = MV_THREADS / 32;
+constexpr int MAX_LD = 192;               // 3 * 64 rows: leaves up to 64 points
+constexpr int PAIRS_PER_LANE = MAX_LD / 64;  // row pairs per lane (3)
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p) { return __ldcs(p); }
+
+// Phase 1: for every V chunk of the item's column leaf, t[vec + c] += V[:, c]^H x_leaf.
+__global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
+                                                       const int32_t* order,
+                                                       const DevChunk* chunks,
+                                                       const float2* __restrict__ arena,
+                                                       const float2* __restrict__ xp,
+                                                       float2* t) {
+    const WorkItem it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this lane's x values (row pairs lane, lane+32, lane+64)
+    float4 xv[PAIRS_PER_LANE];
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+        const int r = 2 * (lane + 32 * q);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < it.rows) {
+            v.x = xp[it.dof + r].x;
+            v.y = xp[it.dof + r].y;
+            if (r + 1 < it.rows) {
+                v.z = xp[it.dof + r + 1].x;
+                v.w = xp[it.dof + r + 1].y;
+            }
+        }
+        xv[q] = v;
+    }
+    const int npair = (it.ld) >> 1;
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk ch = chunks[order[ci]];
+        const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const float4* col = base + (int64_t)c * (ch.ld >> 1);
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    const float4 v = ldg_stream(col + pr);
+                    // conj(v) * x
+                    re = fmaf(v.x, xv[q].x, fmaf(v.y, xv[q].y, re));
+                    im = fmaf(v.x, xv[q].y, fmaf(-v.y, xv[q].x, im));
+                    re = fmaf(v.z, xv[q].z, fmaf(v.w, xv[q].w, re));
+                    im = fmaf(v.z, xv[q].w, fmaf(-v.w, xv[q].z, im));
+                }
+            }
+            re = warp_sumf(re);
+            im = warp_sumf(im);
+            if (lane == 0) atomicAdd(t + ch.vec + c, make_float2(re, im));
+        }
+    }
+}
+
+// Phase 2: y_leaf += sum over chunks of chunk * v, v = x (dense) or t (U).
+__global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
+                                                       const int32_t* order,
+                                                       const DevChunk* chunks,
+                                                       const float2* __restrict__ arena,
+                                                       const float2* __restrict__ xp,
+                                                       const float2* __restrict__ t,
+                                                       float2* yp) {
+    __shared__ float4 part[MV_WARPS][MAX_LD / 2];
+    const WorkItem it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int npair = it.ld >> 1;
+    float4 acc[PAIRS_PER_LANE];
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk ch = chunks[order[ci]];
+        const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
+        const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
+        int c = warp;
+        // two columns per iteration for more loads in flight
+        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
+            const float2 v0 = __ldg(v + c), v1 = __ldg(v + c + MV_WARPS);
+            const float4* col0 = base + (int64_t)c * (ch.ld >> 1);
+            const float4* col1 = col0 + (int64_t)MV_WARPS * (ch.ld >> 1);
+            float4 a0[PAIRS_PER_LANE], a1[PAIRS_PER_LANE];
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    a0[q] = ldg_stream(col0 + pr);
+                    a1[q] = ldg_stream(col1 + pr);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    float4& s = acc[q];
+                    s.x = fmaf(a0[q].x, v0.x, fmaf(-a0[q].y, v0.y, s.x));
+                    s.y = fmaf(a0[q].x, v0.y, fmaf(a0[q].y, v0.x, s.y));
+                    s.z = fmaf(a0[q].z, v0.x, fmaf(-a0[q].w, v0.y, s.z));
+                    s.w = fmaf(a0[q].z, v0.y, fmaf(a0[q].w, v0.x, s.w));
+                    s.x = fmaf(a1[q].x, v1.x, fmaf(-a1[q].y, v1.y, s.x));
+                    s.y = fmaf(a1[q].x, v1.y, fmaf(a1[q].y, v1.x, s.y));
+                    s.z = fmaf(a1[q].z, v1.x, fmaf(-a1[q].w, v1.y, s.z));
+                    s.w = fmaf(a1[q].z, v1.y, fmaf(a1[q].w, v1.x, s.w));
+                }
+            }
+        }
+        for (; c < ch.ncols; c += MV_WARPS) {
+            const float2 v0 = __ldg(v + c);
+            const float4* col0 = base + (int64_t)c * (ch.ld >> 1);
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    const float4 a = ldg_stream(col0 + pr);
+                    float4& s = acc[q];
+                    s.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s.x));
+                    s.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s.y));
+                    s.z = fmaf(a.z, v0.x, fmaf(-a.w, v0.y, s.z));
+                    s.w = fmaf(a.z, v0.y, fmaf(a.w, v0.x, s.w));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+        const int pr = lane + 32 * q;
+        if (pr < MAX_LD / 2) part[warp][pr] = acc[q];
+    }
+    __syncthreads();
+    for (int pr = threadIdx.x; pr < npair; pr += MV_THREADS) {
+        float4 s = part[0][pr];
+        for (int w = 1; w < MV_WARPS; ++w) {
+            s.x += part[w][pr].x;
+            s.y += part[w][pr].y;
+            s.z += part[w][pr].z;
+            s.w += part[w][pr].w;
+        }
+        const int r = 2 * pr;
+        if (r < it.rows) atomicAdd(yp + it.dof + r, make_float2(s.x, s.y));
+        if (r + 1 < it.rows) atomicAdd(yp + it.dof + r + 1, make_float2(s.z, s.w));
+    }
+}
+
+__global__ void gather_x_kernel(const int64_t* perm, const double2* x, float2* xp, int64_t nc) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * nc) return;
+    const int64_t p = q / 3, a = q - 3 * p;
+    const double2 v = x[3 * perm[p] + a];
+    xp[q] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void scatter_y_kernel(const int64_t* perm, const float2* yp, double2* y, int64_t nc) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * nc) return;
+    const int64_t p = q / 3, a = q - 3 * p;
+    const float2 v = yp[q];
+    y[3 * perm[p] + a] = make_double2(v.x, v.y);
+}
+
+struct StagedCopy {
+    const float2* src;   // first row of the chunk's leaf in the staged block/factor
+    int64_t src_ld;
+    int64_t dst;
+    int32_t ld, rows, ncols, pad_;
+};
+
+__global__ void __launch_bounds__(192) staged_copy_kernel(const StagedCopy* jobs, float2* arena) {
+    const StagedCopy J = jobs[blockIdx.x];
+    const int row = threadIdx.x;
+    if (row >= J.ld) return;
+    for (int c = 0; c < J.ncols; ++c)
+        arena[J.dst + row + (int64_t)c * J.ld] =
+            row < J.rows ? J.src[row + (int64_t)c * J.src_ld] : make_float2(0.f, 0.f);
+}
+
+// Splits each leaf's chunk list into items of at most ~target bytes.
+void make_items(const std::vector<int64_t>& begin, const std::vector<int32_t>& list,
+                const std::vector<Chunk>& chunks, const MatvecPlan& plan, int64_t target,
+                std::vector<WorkItem>& items, std::vector<int32_t>& order) {
+    const int64_t nleaf = (int64_t)begin.size() - 1;
+    for (int64_t l = 0; l < nleaf; ++l) {
+        int64_t acc = 0;
+        int32_t first = (int32_t)order.size();
+        for (int64_t q = begin[l]; q < begin[l + 1]; ++q) {
+            const Chunk& c = chunks[list[q]];
+            if (c.ncols == 0) continue;
+            order.push_back(list[q]);
+            acc += (int64_t)c.ld * c.ncols * 8;
+            if (acc >= target) {
+                items.push_back({plan.leaf_dof_begin[l], plan.leaf_rows[l],
+                                 (int32_t)hm_round_up(plan.leaf_rows[l], 2), first,
+                                 (int32_t)order.size()});
+                first = (int32_t)order.size();
+                acc = 0;
+            }
+        }
+        if ((int32_t)order.size() > first)
+            items.push_back({plan.leaf_dof_begin[l], plan.leaf_rows[l],
+                             (int32_t)hm_round_up(plan.leaf_rows[l], 2), first,
+                             (int32_t)order.size()});
+    }
+}
+
+}  // namespace
+
+MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vector<hm_block>& blk,
+                             std::vector<int64_t>& t_off) {
+    MatvecPlan P;
+    // leaves in tree order
+    std::vector<int64_t> leaves;
+    for (int64_t c = 0; c < (int64_t)cl.size(); ++c)
+        if (cl[c].is_leaf) leaves.push_back(c);
+    std::sort(leaves.begin(), leaves.end(),
+              [&](int64_t a, int64_t b) { return cl[a].begin < cl[b].begin; });
+    const int64_t nleaf = (int64_t)leaves.size();
+    std::vector<int64_t> leaf_begin(nleaf);
+    for (int64_t l = 0; l < nleaf; ++l) {
+        leaf_begin[l] = cl[leaves[l]].begin;
+        P.leaf_dof_begin.push_back(3 * cl[leaves[l]].begin);
+        P.leaf_rows.push_back((int32_t)(3 * (cl[leaves[l]].end - cl[leaves[l]].begin)));
+    }
+    auto leaf_range = [&](int64_t c, int64_t& l0, int64_t& l1) {
+        l0 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].begin) - leaf_begin.begin();
+        l1 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].end) - leaf_begin.begin();
+    };
+    // t offsets
+    t_off.assign(blk.size(), 0);
+    int64_t toff = 0;
+    for (size_t b = 0; b < blk.size(); ++b)
+        if (blk[b].admissible) {
+            t_off[b] = toff;
+            toff += blk[b].rank;
+        }
+    P.t_elems = toff;
+    std::vector<std::vector<int32_t>> rows_of(nleaf), cols_of(nleaf);
+    for (size_t b = 0; b < blk.size(); ++b) {
+        const hm_cluster& t = cl[blk[b].tau];
+        const hm_cluster& s = cl[blk[b].sigma];
+        int64_t l0, l1;
+        leaf_range(blk[b].tau, l0, l1);
+        for (int64_t l = l0; l < l1; ++l) {
+            Chunk c;
+            c.rows = P.leaf_rows[l];
+            c.ld = (int32_t)hm_round_up(c.rows, 2);
+            c.block = (int64_t)b;
+            c.leaf_dof = P.leaf_dof_begin[l];
+            if (!blk[b].admissible) {
+                c.kind = 0;
+                c.ncols = (int32_t)(3 * (s.end - s.begin));
+                c.vec = 3 * s.begin;
+            } else {
+                c.kind = 1;
+                c.ncols = blk[b].rank;
+                c.vec = t_off[b];
+            }
+            c.data = -1;
+            rows_of[l].push_back((int32_t)P.chunks.size());
+            P.chunks.push_back(c);
+        }
+        (void)t;
+        if (blk[b].admissible) {
+            leaf_range(blk[b].sigma, l0, l1);
+            for (int64_t l = l0; l < l1; ++l) {
+                Chunk c;
+                c.rows = P.leaf_rows[l];
+                c.ld = (int32_t)hm_round_up(c.rows, 2);
+                c.block = (int64_t)b;
+                c.leaf_dof = P.leaf_dof_begin[l];
+                c.kind = 2;
+                c.ncols = blk[b].rank;
+                c.vec = t_off[b];
+                c.data = -1;
+                cols_of[l].push_back((int32_t)P.chunks.size());
+                P.chunks.push_back(c);
+            }
+        }
+    }
+    // arena offsets: row-leaf streams first (dense chunks, then U), then V by column leaf
+    int64_t off = 0;
+    P.row_leaf_begin.push_back(0);
+    for (int64_t l = 0; l < nleaf; ++l) {
+        std::stable_sort(rows_of[l].begin(), rows_of[l].end(), [&](int32_t a, int32_t b) {
+            return P.chunks[a].kind < P.chunks[b].kind;
+        });
+        for (int32_t id : rows_of[l]) {
+            P.chunks[id].data = off;
+            off += (int64_t)P.chunks[id].ld * P.chunks[id].ncols;
+            P.row_items.push_back(id);
+        }
+        P.row_leaf_begin.push_back((int64_t)P.row_items.size());
+    }
+    P.col_leaf_begin.push_back(0);
+    for (int64_t l = 0; l < nleaf; ++l) {
+        for (int32_t id : cols_of[l]) {
+            P.chunks[id].data = off;
+            off += (int64_t)P.chunks[id].ld * P.chunks[id].ncols;
+            P.col_items.push_back(id);
+        }
+        P.col_leaf_begin.push_back((int64_t)P.col_items.size());
+    }
+    P.arena_elems = off;
+    return P;
+}
+
+MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
+                             cudaStream_t st) {
+    MatvecDev* m = new MatvecDev();
+    m->storage = storage;
+    m->arena_elems = plan.arena_elems;
+    m->arena = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.arena_elems, 2) * sizeof(float2),
+                                   st, true);
+    std::vector<DevChunk> dc(plan.chunks.size());
+    for (size_t i = 0; i < plan.chunks.size(); ++i) {
+        const Chunk& c = plan.chunks[i];
+        dc[i] = {c.data, c.vec, c.ld, c.ncols, c.kind, c.rows};
+        if (c.kind == 0)
+            m->dense_elems += (int64_t)c.ld * c.ncols;
+        else
+            m->lr_elems += (int64_t)c.ld * c.ncols;
+        if (c.kind == 2)
+            m->alg_v += (int64_t)c.rows * c.ncols;
+        else
+            m->alg_du += (int64_t)c.rows * c.ncols;
+    }
+    m->chunks = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(dc.size(), 1) * sizeof(DevChunk), st,
+                                      false);
+    HM_CUDA(cudaMemcpyAsync(m->chunks, dc.data(), dc.size() * sizeof(DevChunk),
+                            cudaMemcpyHostToDevice, st));
+    const int64_t target = 256 * 1024;
+    std::vector<WorkItem> it1, it2;
+    std::vector<int32_t> o1, o2;
+    make_items(plan.col_leaf_begin, plan.col_items, plan.chunks, plan, target, it1, o1);
+    make_items(plan.row_leaf_begin, plan.row_items, plan.chunks, plan, target, it2, o2);
+    // largest items first
+    auto bytes_of = [&](const WorkItem& w, const std::vector<int32_t>& o) {
+        int64_t s = 0;
+        for (int32_t q = w.first; q < w.last; ++q)
+            s += (int64_t)plan.chunks[o[q]].ld * plan.chunks[o[q]].ncols;
+        return s;
+    };
+    std::stable_sort(it1.begin(), it1.end(), [&](const WorkItem& a, const WorkItem& b) {
+        return bytes_of(a, o1) > bytes_of(b, o1);
+    });
+    std::stable_sort(it2.begin(), it2.end(), [&](const WorkItem& a, const WorkItem& b) {
+        return bytes_of(a, o2) > bytes_of(b, o2);
+    });
+    m->n1 = (int64_t)it1.size();
+    m->n2 = (int64_t)it2.size();
+    m->items1 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it1.size(), 1) * sizeof(WorkItem), st, false);
+    m->items2 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it2.size(), 1) * sizeof(WorkItem), st, false);
+    m->order1 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o1.size(), 1) * 4, st, false);
+    m->order2 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o2.size(), 1) * 4, st, false);
+    HM_CUDA(cudaMemcpyAsync(m->items1, it1.data(), it1.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->items2, it2.data(), it2.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->order1, o1.data(), o1.size() * 4, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->order2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, st));
+    m->t_elems = plan.t_elems;
+    m->t = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(float2), st, true);
+    HM_CUDA(cudaStreamSynchronize(st));
+    return m;
+}
+
+void matvec_dev_destroy(MatvecDev* m) { delete m; }
+void* matvec_arena(MatvecDev* m) { return m->arena; }
+int64_t matvec_stored_bytes(const MatvecDev* m) { return m->arena_elems * 8; }
+int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
+
+void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
+    if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
+    if (m->n1) {
+        mv_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
+                                                         m->arena, xp, m->t);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+}
+
+void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
+    HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
+    if (m->n2) {
+        mv_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
+                                                         m->arena, xp, m->t, yp);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+}
+
+void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
+    matvec_phase1(m, xp, st);
+    matvec_phase2(m, xp, yp, ndof, st);
+}
+
+void matvec_alg_bytes(const MatvecDev* m, int64_t ndof, int64_t out[3]) {
+    const int64_t e = 8;  // complex64
+    out[0] = e * (m->alg_v + ndof + m->t_elems);
+    out[1] = e * (m->alg_du + ndof + m->t_elems + ndof);
+    out[2] = e * (m->alg_v + m->alg_du) + 2 * 16 * ndof;  // complex128 x in, y out
+}
+
+void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_t nc,
+                     cudaStream_t st) {
+    gather_x_kernel<<<(unsigned)hm_cdiv(3 * nc, 256), 256, 0, st>>>(d_perm, x, xp, nc);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+}
+
+void launch_scatter_y(const int64_t* d_perm, const float2* yp, double2* y, int64_t nc,
+                      cudaStream_t st) {
+    scatter_y_kernel<<<(unsigned)hm_cdiv(3 * nc, 256), 256, 0, st>>>(d_perm, yp, y, nc);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+}
+
+void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<hm_block>& blk,
+                        const std::vector<hm_cluster>& cl, const std::vector<const float2*>& src_u,
+                        const std::vector<const float2*>& src_v, cudaStream_t st) {
+    std::vector<StagedCopy> jobs;
+    for (const Chunk& c : plan.chunks) {
+        if (c.ncols == 0) continue;
+        const hm_block& b = blk[c.block];
+        const hm_cluster& t = cl[b.tau];
+        const hm_cluster& s = cl[b.sigma];
+        const float2* base = c.kind == 2 ? src_v[c.block] : src_u[c.block];
+        if (!base) continue;
+        const int64_t owner_begin = c.kind == 2 ? s.begin : t.begin;
+        const int64_t owner_rows = 3 * (c.kind == 2 ? s.end - s.begin : t.end - t.begin);
+        StagedCopy J;
+        J.src = base + (c.leaf_dof - 3 * owner_begin);
+        J.src_ld = owner_rows;
+        J.dst = c.data;
+        J.ld = c.ld;
+        J.rows = c.rows;
+        J.ncols = c.ncols;
+        J.pad_ = 0;
+        if (J.ld > 192) hm_throw(HM_ERR_UNSUPPORTED, "leaf clusters above 64 points");
+        jobs.push_back(J);
+    }
+    if (jobs.empty()) return;
+    StagedCopy* d = nullptr;
+    HM_CUDA(cudaMallocAsync((void**)&d, jobs.size() * sizeof(StagedCopy), st));
+    HM_CUDA(cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(StagedCopy), cudaMemcpyHostToDevice, st));
+    staged_copy_kernel<<<(unsigned)jobs.size(), 192, 0, st>>>(d, m->arena);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    HM_CUDA(cudaFreeAsync(d, st));
+}

@@ -1,0 +1,433 @@
+// recompress.cu — recompression of the ACA factors (Sec. 3.2).
+//
+// The paper writes B = U V^H = Q_U R_U R_V^H Q_V^H, takes the SVD
+// R_U R_V^H = P S L^H and keeps U' = Q_U P S^{1/2}, V' = Q_V L S^{1/2}
+// truncated with eps_ACA.  Here the triangular factors come from the Gram
+// matrices (U^H U = R_U^H R_U, a Cholesky factorisation of the equilibrated
+// Gram matrix, semi-definite: a non-positive pivot zeroes its row), and the
+// orthonormal factors are never formed: from R_U R_V^H L = P S and
+// (R_U R_V^H)^H P = L S,
+//     Q_U P_r S_r^{1/2} = U (R_V^H L_r S_r^{-1/2}) =: U T_U,
+//     Q_V L_r S_r^{1/2} = V (R_U^H P_r S_r^{-1/2}) =: V T_V,
+// which holds whether or not R_U, R_V are invertible.  The SVD of the k x k
+// core is a one-sided Jacobi (Hestenes) iteration in FP64 with round-robin
+// pair ordering.  Truncation: smallest r' with
+// (sum_{i >= r'} s_i^2)^{1/2} <= eps (sum s_i^2)^{1/2} (Frobenius, matching the
+// ACA stopping test).  The tall products U T_U, V T_V are applied by a second
+// kernel that writes straight into the matvec's chunk layout.
+#include <algorithm>
+
+#include "hm_internal.h"
+
+namespace {
+
+constexpr int RT = 256;
+constexpr int RW = RT / 32;
+constexpr int TILE_ROWS = 16;
+
+struct CoreJob {
+    int64_t u_off, v_off;   // workspace offsets of U (m3 x k), V (n3 x k)
+    int64_t m3, n3;
+    int64_t s_off;          // scratch offset: 6 k^2 complex
+    int32_t k;
+    int32_t recompress;
+};
+
+// G = A^H A for a col-major (rows x k) A, into G (k x k col-major).
+__device__ void gram(const double2* A, int64_t rows, int k, double2* G, double2* tile) {
+    const int tid = threadIdx.x;
+    const int64_t nent = (int64_t)k * k;
+    constexpr int EPT = 8;  // entries per thread per pass
+    for (int64_t e0 = 0; e0 < nent; e0 += (int64_t)RT * EPT) {
+        double2 acc[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (int64_t r0 = 0; r0 < rows; r0 += TILE_ROWS) {
+            __syncthreads();
+            const int tr = (int)(rows - r0 < TILE_ROWS ? rows - r0 : TILE_ROWS);
+            for (int t = tid; t < TILE_ROWS * k; t += RT) {
+                const int c = t / TILE_ROWS, r = t - c * TILE_ROWS;
+                tile[c * TILE_ROWS + r] = r < tr ? A[r0 + r + (int64_t)c * rows] : make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int64_t e = e0 + (int64_t)q * RT + tid;
+                if (e < nent) {
+                    const int p = (int)(e % k), c = (int)(e / k);
+                    if (p <= c) {
+                        const double2* tp = tile + p * TILE_ROWS;
+                        const double2* tc = tile + c * TILE_ROWS;
+#pragma unroll
+                        for (int r = 0; r < TILE_ROWS; ++r) cfma_conja(acc[q], tp[r], tc[r]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int64_t e = e0 + (int64_t)q * RT + tid;
+            if (e < nent) {
+                const int p = (int)(e % k), c = (int)(e / k);
+                if (p <= c) {
+                    G[p + (int64_t)c * k] = acc[q];
+                    if (p != c) G[c + (int64_t)p * k] = cconj(acc[q]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// In place: G (Hermitian PSD, k x k col-major) -> R upper with G = R^H R, after
+// equilibration G' = D^-1 G D^-1 (D = sqrt diag G); R = R' D.  Serial over
+// columns, parallel over the trailing entries.
+__device__ void chol_equil(double2* G, int k, double* dsc) {
+    const int tid = threadIdx.x;
+    for (int j = tid; j < k; j += RT) {
+        const double d = G[j + (int64_t)j * k].x;
+        dsc[j] = d > 0.0 ? sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
+        const int p = (int)(e % k), c = (int)(e / k);
+        const double s = (dsc[p] > 0.0 && dsc[c] > 0.0) ? 1.0 / (dsc[p] * dsc[c]) : 0.0;
+        G[e] = cscale(G[e], s);
+    }
+    __syncthreads();
+    // right-looking Cholesky on the upper triangle: G = R^H R
+    __shared__ double s_piv;
+    for (int j = 0; j < k; ++j) {
+        if (tid == 0) {
+            const double d = G[j + (int64_t)j * k].x;
+            s_piv = d > 1e-13 ? sqrt(d) : 0.0;
+        }
+        __syncthreads();
+        const double piv = s_piv;
+        // row j of R: R_jc = G_jc / piv for c > j
+        for (int c = j + 1 + tid; c < k; c += RT)
+            G[j + (int64_t)c * k] = piv > 0.0 ? cscale(G[j + (int64_t)c * k], 1.0 / piv) : make_double2(0.0, 0.0);
+        if (tid == 0) G[j + (int64_t)j * k] = make_double2(piv, 0.0);
+        __syncthreads();
+        // trailing update: G_ab -= conj(R_ja) R_jb for j < a <= b
+        const int64_t nt = (int64_t)(k - j - 1) * (k - j - 1);
+        for (int64_t e = tid; e < nt; e += RT) {
+            const int a = j + 1 + (int)(e % (k - j - 1)), b = j + 1 + (int)(e / (k - j - 1));
+            if (a <= b) {
+                const double2 ra = G[j + (int64_t)a * k], rb = G[j + (int64_t)b * k];
+                double2 g = G[a + (int64_t)b * k];
+                g = csub(g, cconjmul(ra, rb));
+                G[a + (int64_t)b * k] = g;
+            }
+        }
+        __syncthreads();
+    }
+    // zero the strict lower triangle, scale columns: R = R' D
+    for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
+        const int p = (int)(e % k), c = (int)(e / k);
+        G[e] = p > c ? make_double2(0.0, 0.0) : cscale(G[e], dsc[c]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, double2* work,
+                                                         double2* scratch, double eps,
+                                                         int32_t* rank_out, int tile_cap) {
+    extern __shared__ double2 tile[];       // TILE_ROWS x k
+    __shared__ double dsc[1024];
+    __shared__ int s_conv;
+    __shared__ int s_r;
+    const CoreJob J = jobs[blockIdx.x];
+    const int k = J.k;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (k == 0) {
+        if (tid == 0) rank_out[blockIdx.x] = 0;
+        return;
+    }
+    double2* RU = scratch + J.s_off;
+    double2* RV = RU + (int64_t)k * k;
+    double2* W = RV + (int64_t)k * k;
+    double2* L = W + (int64_t)k * k;
+    double2* TU = L + (int64_t)k * k;
+    double2* TV = TU + (int64_t)k * k;
+    double* sv = reinterpret_cast<double*>(L) ;  // reused only after T is built (see below)
+    (void)sv;
+    if (!J.recompress) {
+        for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
+            const int p = (int)(e % k), c = (int)(e / k);
+            TU[e] = make_double2(p == c ? 1.0 : 0.0, 0.0);
+            TV[e] = TU[e];
+        }
+        if (tid == 0) rank_out[blockIdx.x] = k;
+        return;
+    }
+    const double2* U = work + J.u_off;
+    const double2* V = work + J.v_off;
+    gram(U, J.m3, k, RU, tile);
+    gram(V, J.n3, k, RV, tile);
+    chol_equil(RU, k, dsc);
+    chol_equil(RV, k, dsc);
+    // W = R_U R_V^H, L = I
+    for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
+        const int p = (int)(e % k), c = (int)(e / k);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int t = max(p, c); t < k; ++t)  // R_U[p][t] nonzero for t >= p, R_V[c][t] for t >= c
+            acc = cadd(acc, cmulc(RU[p + (int64_t)t * k], RV[c + (int64_t)t * k]));
+        W[e] = acc;
+        L[e] = make_double2(p == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    // one-sided Jacobi on the columns of W, round-robin ordering
+    const int np = (k + 1) & ~1;  // players (a dummy when k is odd)
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_conv = 1;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pi = wid; pi < np / 2; pi += RW) {
+                int a, b;
+                if (pi == 0) {
+                    a = np - 1;
+                    b = round;
+                } else {
+                    a = (round + pi) % (np - 1);
+                    b = (round - pi + np - 1) % (np - 1);
+                }
+                if (a >= k || b >= k) continue;
+                if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+                for (int r = lane; r < k; r += 32) {
+                    const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
+                    al += cabs2(wa);
+                    be += cabs2(wb);
+                    const double2 z = cconjmul(wa, wb);
+                    gr += z.x;
+                    gi += z.y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                gr = warp_sum(gr);
+                gi = warp_sum(gi);
+                const double ag = sqrt(gr * gr + gi * gi);
+                if (ag == 0.0 || ag <= 1e-15 * sqrt(al * be)) continue;
+                if (lane == 0) s_conv = 0;
+                const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
+                const double zeta = (be - al) / (2.0 * ag);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                // [w_a, w_b] <- [w_a, w_b] [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+                for (int r = lane; r < k; r += 32) {
+                    const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
+                    const double2 pw = cmul(phc, wb);
+                    W[r + (int64_t)a * k] = csub(cscale(wa, c), cscale(pw, s));
+                    W[r + (int64_t)b * k] = cadd(cscale(wa, s), cscale(pw, c));
+                    const double2 la = L[r + (int64_t)a * k], lb = L[r + (int64_t)b * k];
+                    const double2 pl = cmul(phc, lb);
+                    L[r + (int64_t)a * k] = csub(cscale(la, c), cscale(pl, s));
+                    L[r + (int64_t)b * k] = cadd(cscale(la, s), cscale(pl, c));
+                }
+            }
+            __syncthreads();
+        }
+        if (s_conv) break;
+        __syncthreads();
+    }
+    // singular values (column norms) and descending order
+    __shared__ double s_sv[1024];
+    __shared__ int s_ord[1024];
+    for (int j = wid; j < k; j += RW) {
+        double a = 0.0;
+        for (int r = lane; r < k; r += 32) a += cabs2(W[r + (int64_t)j * k]);
+        a = warp_sum(a);
+        if (lane == 0) s_sv[j] = sqrt(a);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int j = 0; j < k; ++j) s_ord[j] = j;
+        for (int i = 0; i < k; ++i) {  // selection sort, ties keep index order
+            int best = i;
+            for (int j = i + 1; j < k; ++j)
+                if (s_sv[s_ord[j]] > s_sv[s_ord[best]]) best = j;
+            const int t = s_ord[i];
+            s_ord[i] = s_ord[best];
+            s_ord[best] = t;
+        }
+        double tot = 0.0;
+        for (int j = 0; j < k; ++j) tot += s_sv[j] * s_sv[j];
+        int r = k;
+        double tail = 0.0;
+        for (int i = k - 1; i >= 0; --i) {
+            const double sv = s_sv[s_ord[i]];
+            if (sqrt(tail + sv * sv) <= eps * sqrt(tot)) {
+                tail += sv * sv;
+                r = i;
+            } else {
+                break;
+            }
+        }
+        s_r = r;
+        rank_out[blockIdx.x] = r;
+    }
+    __syncthreads();
+    const int r = s_r;
+    // T_U[:, q] = R_V^H L_{o(q)} / sqrt(s), T_V[:, q] = R_U^H W_{o(q)} / s^{3/2}
+    for (int64_t e = tid; e < (int64_t)k * r; e += RT) {
+        const int p = (int)(e % k), q = (int)(e / k);
+        const int j = s_ord[q];
+        const double s = s_sv[j];
+        double2 au = make_double2(0.0, 0.0), av = make_double2(0.0, 0.0);
+        for (int t = 0; t <= p; ++t) {  // (R^H)_{p t} = conj(R_{t p}), nonzero for t <= p
+            cfma_conja(au, RV[t + (int64_t)p * k], L[t + (int64_t)j * k]);
+            cfma_conja(av, RU[t + (int64_t)p * k], W[t + (int64_t)j * k]);
+        }
+        TU[p + (int64_t)q * k] = cscale(au, 1.0 / sqrt(s));
+        TV[p + (int64_t)q * k] = cscale(av, 1.0 / (s * sqrt(s)));
+    }
+}
+
+// One item = the rows of one leaf of one factor.
+struct ApplyJob {
+    int64_t src;     // workspace offset of the leaf's first row in the factor (m3 x k)
+    int64_t src_ld;  // factor rows
+    int64_t t_off;   // scratch offset of T (k x r, ld k)
+    int64_t dst;     // arena offset of the chunk
+    int32_t k, r, rows, ld;
+};
+
+__global__ void __launch_bounds__(192) apply_factor_kernel(const ApplyJob* jobs,
+                                                           const double2* __restrict__ work,
+                                                           const double2* __restrict__ scratch,
+                                                           float2* out) {
+    const ApplyJob J = jobs[blockIdx.x];
+    const int row = threadIdx.x;
+    if (row >= J.rows) return;
+    const double2* T = scratch + J.t_off;
+    constexpr int QB = 8;
+    for (int q0 = 0; q0 < J.r; q0 += QB) {
+        double2 acc[QB];
+#pragma unroll
+        for (int q = 0; q < QB; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (int p = 0; p < J.k; ++p) {
+            const double2 u = work[J.src + row + (int64_t)p * J.src_ld];
+#pragma unroll
+            for (int q = 0; q < QB; ++q)
+                if (q0 + q < J.r) cfma(acc[q], u, T[p + (int64_t)(q0 + q) * J.k]);
+        }
+#pragma unroll
+        for (int q = 0; q < QB; ++q)
+            if (q0 + q < J.r)
+                out[J.dst + row + (int64_t)(q0 + q) * J.ld] = make_float2((float)acc[q].x, (float)acc[q].y);
+    }
+}
+
+}  // namespace
+
+// ---- host drivers ----
+struct RecompBatch {
+    std::vector<CoreJob> jobs;
+    CoreJob* d_jobs = nullptr;
+    double2* d_scratch = nullptr;
+    int32_t* d_rank = nullptr;
+};
+
+void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64_t>& v_off,
+                      const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
+                      const std::vector<int32_t>& k, int recompress, double2* d_work, double eps,
+                      std::vector<int32_t>& ranks, std::vector<int64_t>& s_off,
+                      cudaStream_t st) {
+    RecompBatch* B = new RecompBatch();
+    const size_t nj = k.size();
+    B->jobs.resize(nj);
+    s_off.resize(nj);
+    int64_t off = 0;
+    int kmax = 1;
+    for (size_t j = 0; j < nj; ++j) {
+        CoreJob& c = B->jobs[j];
+        c.u_off = u_off[j];
+        c.v_off = v_off[j];
+        c.m3 = m3[j];
+        c.n3 = n3[j];
+        c.k = k[j];
+        c.recompress = recompress;
+        c.s_off = off;
+        s_off[j] = off;
+        off += 6 * (int64_t)k[j] * k[j];
+        kmax = std::max(kmax, (int)k[j]);
+    }
+    if (kmax > 768) hm_throw(HM_ERR_UNSUPPORTED, "ACA rank above 768 columns");
+    HM_CUDA(cudaMallocAsync((void**)&B->d_jobs, std::max<size_t>(nj, 1) * sizeof(CoreJob), st));
+    HM_CUDA(cudaMallocAsync((void**)&B->d_scratch, std::max<int64_t>(off, 1) * sizeof(double2), st));
+    HM_CUDA(cudaMallocAsync((void**)&B->d_rank, std::max<size_t>(nj, 1) * sizeof(int32_t), st));
+    HM_CUDA(cudaMemcpyAsync(B->d_jobs, B->jobs.data(), nj * sizeof(CoreJob), cudaMemcpyHostToDevice, st));
+    const size_t smem = (size_t)TILE_ROWS * kmax * sizeof(double2);
+    if (smem > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(recomp_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    if (nj) {
+        recomp_core_kernel<<<(unsigned)nj, RT, smem, st>>>(B->d_jobs, d_work, B->d_scratch, eps,
+                                                          B->d_rank, kmax);
+                                                          HM_LAUNCHED();
+        HM_CUDA(cudaGetLastError());
+    }
+    ranks.resize(nj);
+    HM_CUDA(cudaMemcpyAsync(ranks.data(), B->d_rank, nj * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    return B;
+}
+
+// Applies T_U / T_V to the factors and writes the chunks.  items: for every
+// (job, leaf) pair: (job, which: 0 = U / 1 = V, first row in the factor, rows,
+// arena offset, ld).
+void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
+                      const std::vector<int32_t>& which, const std::vector<int64_t>& row0,
+                      const std::vector<int32_t>& rows, const std::vector<int64_t>& dst,
+                      const std::vector<int32_t>& ld, const std::vector<int32_t>& ranks,
+                      const double2* d_work, float2* d_out, cudaStream_t st) {
+    RecompBatch* B = (RecompBatch*)batch;
+    std::vector<ApplyJob> aj;
+    aj.reserve(job_of.size());
+    for (size_t i = 0; i < job_of.size(); ++i) {
+        const CoreJob& c = B->jobs[job_of[i]];
+        const int32_t r = ranks[job_of[i]];
+        if (r == 0) continue;
+        ApplyJob a;
+        const int64_t k2 = (int64_t)c.k * c.k;
+        if (which[i] == 0) {
+            a.src = c.u_off + row0[i];
+            a.src_ld = c.m3;
+            a.t_off = c.s_off + 4 * k2;
+        } else {
+            a.src = c.v_off + row0[i];
+            a.src_ld = c.n3;
+            a.t_off = c.s_off + 5 * k2;
+        }
+        a.dst = dst[i];
+        a.k = c.k;
+        a.r = r;
+        a.rows = rows[i];
+        a.ld = ld[i];
+        if (a.rows > 192) hm_throw(HM_ERR_ARG, "factor slice longer than 192 rows");
+        aj.push_back(a);
+    }
+    if (!aj.empty()) {
+        ApplyJob* d = nullptr;
+        HM_CUDA(cudaMallocAsync((void**)&d, aj.size() * sizeof(ApplyJob), st));
+        HM_CUDA(cudaMemcpyAsync(d, aj.data(), aj.size() * sizeof(ApplyJob), cudaMemcpyHostToDevice, st));
+        apply_factor_kernel<<<(unsigned)aj.size(), 192, 0, st>>>(d, d_work, B->d_scratch, d_out);
+        HM_LAUNCHED();
+        HM_CUDA(cudaGetLastError());
+        HM_CUDA(cudaFreeAsync(d, st));
+    }
+}
+
+void recompress_release(void* batch, cudaStream_t st) {
+    RecompBatch* B = (RecompBatch*)batch;
+    if (!B) return;
+    if (B->d_jobs) HM_CUDA(cudaFreeAsync(B->d_jobs, st));
+    if (B->d_scratch) HM_CUDA(cudaFreeAsync(B->d_scratch, st));
+    if (B->d_rank) HM_CUDA(cudaFreeAsync(B->d_rank, st));
+    delete B;
+}

@@ -1,0 +1,275 @@
+"""Thin ctypes binding of ``libhm.so`` (the C ABI in ``include/hm.h``).
+
+Names follow the C entry points.  Only argument marshalling happens here:
+every step of the build, the product and the solver runs in the library's
+CUDA kernels.  Device buffers are torch tensors (PyTorch supplies device
+memory and streams).  If ``libhm.so`` cannot be loaded this module raises:
+there is no fallback path.
+"""
+import ctypes as C
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhm.so")
+
+HM_OK, HM_ERR_ARG, HM_ERR_CUDA, HM_ERR_OOM, HM_ERR_NOCONV, HM_ERR_TIMEOUT, HM_ERR_NUMERIC, \
+    HM_ERR_UNSUPPORTED = range(8)
+HM_KERNEL_U, HM_KERNEL_T = 0, 1
+HM_STORE_FP32, HM_STORE_BF16 = 0, 1
+
+
+class HmError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s failed: %s (%s)" % (where, msg, _status_name(status)))
+        self.status = status
+
+
+class hm_opts(C.Structure):
+    _fields_ = [("storage", C.c_int32), ("aca_fp32", C.c_int32), ("diag_value", C.c_double),
+                ("fp64_switch_ksr", C.c_double), ("recompress", C.c_int32),
+                ("aca_max_rank", C.c_int32), ("workspace_bytes", C.c_int64),
+                ("verbose", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class hm_cluster(C.Structure):
+    _fields_ = [("begin", C.c_int64), ("end", C.c_int64), ("child0", C.c_int64),
+                ("child1", C.c_int64), ("level", C.c_int32), ("is_leaf", C.c_int32),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class hm_block(C.Structure):
+    _fields_ = [("tau", C.c_int64), ("sigma", C.c_int64), ("admissible", C.c_int32),
+                ("rank_aca", C.c_int32), ("rank", C.c_int32), ("pad_", C.c_int32)]
+
+
+CLUSTER_DTYPE = np.dtype([("begin", "<i8"), ("end", "<i8"), ("child0", "<i8"), ("child1", "<i8"),
+                          ("level", "<i4"), ("is_leaf", "<i4"), ("lo", "<f8", (3,)),
+                          ("hi", "<f8", (3,))])
+BLOCK_DTYPE = np.dtype([("tau", "<i8"), ("sigma", "<i8"), ("admissible", "<i4"),
+                        ("rank_aca", "<i4"), ("rank", "<i4"), ("pad_", "<i4")])
+assert CLUSTER_DTYPE.itemsize == C.sizeof(hm_cluster)
+assert BLOCK_DTYPE.itemsize == C.sizeof(hm_block)
+
+_P, _I64, _I32, _D, _SZ = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_size_t
+SIGNATURES = {
+    "hm_opts_default": (None, [_P]),
+    "hm_build": (_I32, [_P, _P, _I64, _D, _D, _D, _D, _I32, _D, _D, _I64, _P, _P, _P]),
+    "hm_matvec": (_I32, [_P, _I32, _P, _P, _P]),
+    "hm_matvec_host": (_I32, [_P, _I32, _P, _P, _P]),
+    "hm_gmres": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
+    "hm_stats": (_I32, [_P, C.c_char_p, _SZ, _P]),
+    "hm_sizes": (_I32, [_P, _P, _P, _P]),
+    "hm_get_tree": (_I32, [_P, _P, _P]),
+    "hm_get_blocks": (_I32, [_P, _P]),
+    "hm_get_block_data": (_I32, [_P, _I64, _P, _P]),
+    "hm_green_eval": (_I32, [_I32, _D, _D, _D, _D, _D, _P, _P, _P, _I64, _P, _P]),
+    "hm_import": (_I32, [_I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P]),
+    "hm_profile_matvec": (_I32, [_P, _I32, _P, _P, _P]),
+    "hm_kernel_launches": (_I64, []),
+    "hm_free": (None, [_P]),
+    "hm_status_string": (C.c_char_p, [_I32]),
+    "hm_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhm.so (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhm.so not built (run __graft_entry__.build()): " + LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_name(s):
+    try:
+        return lib().hm_status_string(s).decode()
+    except Exception:  # noqa: BLE001
+        return str(s)
+
+
+def _check(st, where):
+    if st != HM_OK:
+        raise HmError(st, where, lib().hm_last_error().decode())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def hm_kernel_launches():
+    return lib().hm_kernel_launches()
+
+
+def hm_opts_default(**kw):
+    o = hm_opts()
+    lib().hm_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def hm_green_eval(kernel, rho, lam, mu, omega, x, y, ny=None, diag_value=1.0, stream=None):
+    """Green's tensors K(x_q, y_q) on the GPU.  x, y, ny: cuda float64 (n, 3).
+    Returns a cuda complex128 tensor (n, 3, 3)."""
+    import torch
+    n = x.shape[0]
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=x.device)
+    _check(lib().hm_green_eval(kernel, rho, lam, mu, omega, diag_value, x.data_ptr(),
+                               y.data_ptr(), ny.data_ptr() if ny is not None else None, n,
+                               out.data_ptr(), _stream_ptr(stream)), "hm_green_eval")
+    return out
+
+
+class HMatrix:
+    """An H-matrix built (or imported) on the current CUDA device."""
+
+    def __init__(self, handle, n_c):
+        self.h = handle
+        self.n_c = n_c
+
+    @classmethod
+    def build(cls, points, normals=None, rho=1.0, lam=2.0, mu=1.0, omega=4.0, kernel="U",
+              eps=1e-4, eta=3.0, leaf_size=32, opts=None, stream=None):
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        nrm = np.ascontiguousarray(normals, dtype=np.float64) if normals is not None else None
+        k = {"U": HM_KERNEL_U, "T": HM_KERNEL_T}[kernel] if isinstance(kernel, str) else kernel
+        h = C.c_void_p()
+        st = lib().hm_build(_np_ptr(pts), _np_ptr(nrm) if nrm is not None else None,
+                            pts.shape[0], rho, lam, mu, omega, k, eps, eta, leaf_size,
+                            C.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                            C.byref(h))
+        _check(st, "hm_build")
+        return cls(h, pts.shape[0])
+
+    @classmethod
+    def import_(cls, n_c, perm, clusters, blocks, data, opts=None, stream=None):
+        perm = np.ascontiguousarray(perm, np.int64)
+        clusters = np.ascontiguousarray(clusters, CLUSTER_DTYPE)
+        blocks = np.ascontiguousarray(blocks, BLOCK_DTYPE)
+        data = np.ascontiguousarray(data, np.complex128)
+        h = C.c_void_p()
+        st = lib().hm_import(n_c, _np_ptr(perm), len(clusters), _np_ptr(clusters), len(blocks),
+                             _np_ptr(blocks), _np_ptr(data),
+                             C.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                             C.byref(h))
+        _check(st, "hm_import")
+        return cls(h, n_c)
+
+    def free(self):
+        if self.h:
+            lib().hm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def matvec(self, x, y=None, stream=None):
+        """y = A_H x for cuda complex128 x of shape (3 n_c,) or (3 n_c, nrhs) (column-major)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        xc = x if x.dim() == 1 else x.t().contiguous()
+        yc = y if y.dim() == 1 else torch.empty_like(xc)
+        _check(lib().hm_matvec(self.h, nrhs, xc.data_ptr(), yc.data_ptr(), _stream_ptr(stream)),
+               "hm_matvec")
+        if y.dim() != 1:
+            y.copy_(yc.t())
+        return y
+
+    def matvec_host(self, x, y=None, stream=None):
+        """Same product from host numpy complex128 arrays (copies inside the call)."""
+        x = np.asarray(x)
+        assert x.dtype == np.complex128 and x.flags.f_contiguous
+        if y is None:
+            y = np.empty_like(x, order="F")
+        nrhs = 1 if x.ndim == 1 else x.shape[1]
+        _check(lib().hm_matvec_host(self.h, nrhs, _np_ptr(x), _np_ptr(y), _stream_ptr(stream)),
+               "hm_matvec_host")
+        return y
+
+    def gmres(self, b, x=None, restart=50, tol=1e-6, maxit=1000, stream=None, check=True):
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        it = C.c_int32(0)
+        rr = C.c_double(0.0)
+        st = lib().hm_gmres(self.h, b.data_ptr(), x.data_ptr(), restart, tol, maxit,
+                            C.byref(it), C.byref(rr), _stream_ptr(stream))
+        if check and st != HM_ERR_NOCONV:
+            _check(st, "hm_gmres")
+        return x, it.value, rr.value, st
+
+    def profile_matvec(self, reps=10, stream=None):
+        """Average per-kernel device times (ms) of the product and its algorithmic bytes."""
+        ms = (C.c_double * 4)()
+        by = (C.c_int64 * 3)()
+        _check(lib().hm_profile_matvec(self.h, reps, ms, by, _stream_ptr(stream)),
+               "hm_profile_matvec")
+        return {"ms": {"gather": ms[0], "phase1": ms[1], "phase2": ms[2], "scatter": ms[3]},
+                "bytes": {"phase1": by[0], "phase2": by[1], "matvec": by[2]}}
+
+    def stats(self):
+        need = C.c_size_t(0)
+        lib().hm_stats(self.h, None, 0, C.byref(need))
+        buf = C.create_string_buffer(need.value)
+        _check(lib().hm_stats(self.h, buf, need.value, None), "hm_stats")
+        return json.loads(buf.value.decode())
+
+    def sizes(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().hm_sizes(self.h, C.byref(a), C.byref(b), C.byref(c)), "hm_sizes")
+        return a.value, b.value, c.value
+
+    def tree(self):
+        nc, ncl, _ = self.sizes()
+        perm = np.zeros(nc, np.int64)
+        cl = np.zeros(ncl, CLUSTER_DTYPE)
+        _check(lib().hm_get_tree(self.h, _np_ptr(perm), _np_ptr(cl)), "hm_get_tree")
+        return perm, cl
+
+    def blocks(self):
+        _, _, nb = self.sizes()
+        b = np.zeros(nb, BLOCK_DTYPE)
+        _check(lib().hm_get_blocks(self.h, _np_ptr(b)), "hm_get_blocks")
+        return b
+
+    def block_data(self, b, blocks=None, clusters=None):
+        if blocks is None:
+            blocks = self.blocks()
+        if clusters is None:
+            clusters = self.tree()[1]
+        B = blocks[b]
+        t, s = clusters[B["tau"]], clusters[B["sigma"]]
+        m3, n3 = 3 * (t["end"] - t["begin"]), 3 * (s["end"] - s["begin"])
+        if not B["admissible"]:
+            a = np.zeros((n3, m3), np.complex128)
+            _check(lib().hm_get_block_data(self.h, b, _np_ptr(a), None), "hm_get_block_data")
+            return a.T.copy()
+        r = int(B["rank"])
+        u = np.zeros((max(r, 1), m3), np.complex128)
+        v = np.zeros((max(r, 1), n3), np.complex128)
+        _check(lib().hm_get_block_data(self.h, b, _np_ptr(u), _np_ptr(v)), "hm_get_block_data")
+        return u[:r].T.copy(), v[:r].T.copy()

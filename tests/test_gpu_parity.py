@@ -1,0 +1,325 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Ladder: (1) Green's tensors, (2) tree and partition identical, (3) GPU
+product on oracle-exported factors, (4) full GPU build vs oracle H-matvec
+(<= 1e-5) and vs the dense product (<= 3 eps), (5) GMRES, plus edge cases
+and a full-size (65 536-point) check on sampled rows.
+"""
+import numpy as np
+import pytest
+
+from paper_1706_09384_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def hm():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1706_09384_gb300 import build, hm as H
+    build.build()
+    H.lib()
+    return H
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------- (1) Green's tensors
+@pytest.mark.parametrize("kern", ["U", "T"])
+def test_green_eval_matches_oracle(hm, oracle, kern):
+    rng = np.random.default_rng(0)
+    n = 4000
+    x = rng.standard_normal((n, 3))
+    r = 10 ** rng.uniform(-2.5, 1.0, n)
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    y = x - d * r[:, None]
+    ny = rng.standard_normal((n, 3))
+    ny /= np.linalg.norm(ny, axis=1, keepdims=True)
+    y[7] = x[7]  # coincident pair -> diag_value * I3
+    for rho, lam, mu, om in [(1, 2, 1, 4.0), (1, 2, 1, 16.0), (2.5, 0.7, 1.3, 3.0)]:
+        k = 0 if kern == "U" else 1
+        G = hm.hm_green_eval(k, rho, lam, mu, om, cuda(x), cuda(y), cuda(ny)).cpu().numpy()
+        pb = oracle.problem(rho, lam, mu, om, kern, diag_value=1.0)
+        for q in range(0, n, 37):
+            ref = oracle.green(pb, x[q], y[q], ny[q]) if q != 7 else np.eye(3)
+            assert np.abs(G[q] - ref).max() <= 1e-12 * np.abs(ref).max(), q
+
+
+# ---------------------------------------------------------------- (2) tree + partition
+def block_set(blk, cl, adm_key="admissible"):
+    return {(int(cl[b["tau"]]["begin"]), int(cl[b["tau"]]["end"]), int(cl[b["sigma"]]["begin"]),
+             int(cl[b["sigma"]]["end"]), int(b[adm_key])) for b in blk}
+
+
+@pytest.mark.parametrize("cloud,leaf,eta", [("sphere1536", 32, 3.0), ("sphere5000", 64, 3.0),
+                                            ("plate", 20, 2.0), ("cube", 17, 3.0)])
+def test_tree_and_partition_identical(hm, oracle, cloud, leaf, eta):
+    pts = {"sphere1536": lambda: inputs.fibonacci_sphere(1536),
+           "sphere5000": lambda: inputs.fibonacci_sphere(5000),
+           "plate": lambda: inputs.plate(40),
+           "cube": lambda: inputs.cube_surface(3001, seed=2)[0]}[cloud]()
+    H = hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", EPS, eta, leaf)
+    perm_g, cl_g = H.tree()
+    perm_o, cl_o = oracle.tree_build(pts, leaf)
+    assert np.array_equal(perm_g, perm_o)
+    key = lambda c: (int(c["level"]), int(c["begin"]))  # noqa: E731
+    A = sorted(cl_g, key=key)
+    B = sorted(cl_o, key=key)
+    assert len(A) == len(B)
+    for a, b in zip(A, B):
+        assert (a["begin"], a["end"], a["level"], a["is_leaf"]) == (b["begin"], b["end"], b["level"], b["is_leaf"])
+        assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"])
+    blk_o = oracle.partition(cl_o, eta)
+    assert block_set(H.blocks(), cl_g) == block_set(blk_o, cl_o)
+
+
+# ---------------------------------------------------------------- (3) product on oracle factors
+def oracle_export(ref):
+    perm = ref.perm()
+    cl_o = ref.clusters()
+    blk_o, ra, r = ref.blocks()
+    cl = np.zeros(len(cl_o), hm_cluster_dtype())
+    for f in ("begin", "end", "child0", "child1", "level", "is_leaf", "lo", "hi"):
+        cl[f] = cl_o[f]
+    blk = np.zeros(len(blk_o), hm_block_dtype())
+    blk["tau"], blk["sigma"], blk["admissible"] = blk_o["tau"], blk_o["sigma"], blk_o["admissible"]
+    blk["rank"] = np.where(blk_o["admissible"] == 1, r, 0)
+    blk["rank_aca"] = np.where(blk_o["admissible"] == 1, ra, 0)
+    parts = []
+    for b in range(len(blk_o)):
+        d = ref.block_data(b, blk_o, cl_o, r)
+        if blk_o[b]["admissible"]:
+            parts += [d[0].ravel(order="F"), d[1].ravel(order="F")]
+        else:
+            parts.append(d.ravel(order="F"))
+    return perm, cl, blk, np.concatenate(parts)
+
+
+def hm_cluster_dtype():
+    from paper_1706_09384_gb300 import hm as H
+    return H.CLUSTER_DTYPE
+
+
+def hm_block_dtype():
+    from paper_1706_09384_gb300 import hm as H
+    return H.BLOCK_DTYPE
+
+
+@pytest.mark.parametrize("kern", ["U", "T"])
+def test_matvec_on_oracle_factors(hm, oracle, kern):
+    nc = 1536
+    pts = inputs.fibonacci_sphere(nc)
+    nrm = inputs.sphere_normals(pts)
+    ref = oracle.HMatrix(oracle.problem(1, 2, 1, 4.0, kern), pts, nrm, eps=EPS, eta=3.0, leaf=32)
+    perm, cl, blk, data = oracle_export(ref)
+    H = hm.HMatrix.import_(nc, perm, cl, blk, data)
+    for seed in range(3):
+        x = inputs.random_rhs(3 * nc, seed=seed)
+        y = H.matvec(cuda(x)).cpu().numpy()
+        yo = ref.matvec(x)
+        assert np.linalg.norm(y - yo) <= 1e-6 * np.linalg.norm(yo)
+    # host-buffer entry point gives the same product
+    x = inputs.random_rhs(3 * nc, seed=9)
+    yh = H.matvec_host(np.asfortranarray(x))
+    assert np.linalg.norm(yh - ref.matvec(x)) <= 1e-6 * np.linalg.norm(yh)
+
+
+# ---------------------------------------------------------------- (4) full GPU build
+@pytest.fixture(scope="module")
+def cfg1(hm, oracle):
+    nc = 1536
+    pts = inputs.fibonacci_sphere(nc)
+    nrm = inputs.sphere_normals(pts)
+    rho, lam, mu, om = inputs.material(4.0)
+    out = {}
+    for kern in ("U", "T"):
+        pb = oracle.problem(rho, lam, mu, om, kern)
+        ref = oracle.HMatrix(pb, pts, nrm, eps=EPS, eta=3.0, leaf=32)
+        H = hm.HMatrix.build(pts, nrm if kern == "T" else None, rho, lam, mu, om, kern, EPS, 3.0, 32)
+        out[kern] = (pb, ref, H, oracle.dense_matrix(pb, pts, nrm))
+    return pts, nrm, out
+
+
+@pytest.mark.parametrize("kern", ["U", "T"])
+def test_build_matvec_vs_dense_and_oracle(hm, cfg1, kern):
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d[kern]
+    for seed in (0, 1):
+        x = inputs.random_rhs(3 * len(pts), seed=seed)
+        y = H.matvec(cuda(x)).cpu().numpy()
+        yd = A @ x
+        yo = ref.matvec(x)
+        assert np.linalg.norm(y - yd) <= 3 * EPS * np.linalg.norm(yd)
+        assert np.linalg.norm(y - yo) <= 1e-5 * np.linalg.norm(yo)
+
+
+@pytest.mark.parametrize("kern", ["U", "T"])
+def test_build_ranks_match_oracle(hm, oracle, cfg1, kern):
+    """Same tree and partition; ACA ranks equal the oracle's except where a
+    near-tie flips a pivot; recompressed ranks within one of the oracle's."""
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d[kern]
+    blk_g = H.blocks()
+    perm_g, cl_g = H.tree()
+    blk_o, ra_o, r_o = ref.blocks()
+    cl_o = ref.clusters()
+    key_o = {(int(cl_o[b["tau"]]["begin"]), int(cl_o[b["sigma"]]["begin"]), int(b["admissible"])): i
+             for i, b in enumerate(blk_o)}
+    same_k, close_r, n = 0, 0, 0
+    for b in blk_g:
+        if not b["admissible"]:
+            continue
+        i = key_o[(int(cl_g[b["tau"]]["begin"]), int(cl_g[b["sigma"]]["begin"]), 1)]
+        n += 1
+        same_k += int(b["rank_aca"] == ra_o[i])
+        close_r += int(abs(int(b["rank"]) - int(r_o[i])) <= 1)
+        assert b["rank_aca"] % 3 == 0
+    assert same_k >= 0.98 * n, (same_k, n)
+    assert close_r >= 0.98 * n, (close_r, n)
+
+
+def test_block_factors_vs_dense(hm, cfg1):
+    """Per admissible block: ||A_b - U V^H||_F <= 3 eps ||A_b||_F (95th pct), <= 10 eps max."""
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d["U"]
+    perm, cl = H.tree()
+    blk = H.blocks()
+    errs = []
+    for b in np.nonzero(blk["admissible"])[0][::5]:
+        t, s = cl[blk[b]["tau"]], cl[blk[b]["sigma"]]
+        ri = (3 * perm[t["begin"]:t["end"]][:, None] + np.arange(3)).ravel()
+        ci = (3 * perm[s["begin"]:s["end"]][:, None] + np.arange(3)).ravel()
+        Ab = A[np.ix_(ri, ci)]
+        U, V = H.block_data(b, blk, cl)
+        errs.append(np.linalg.norm(Ab - U @ V.conj().T) / np.linalg.norm(Ab))
+    errs = np.array(errs)
+    assert np.percentile(errs, 95) <= 3 * EPS and errs.max() <= 10 * EPS
+
+
+def test_dense_blocks_exact(hm, cfg1):
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d["T"]
+    perm, cl = H.tree()
+    blk = H.blocks()
+    for b in np.nonzero(blk["admissible"] == 0)[0][::7]:
+        t, s = cl[blk[b]["tau"]], cl[blk[b]["sigma"]]
+        ri = (3 * perm[t["begin"]:t["end"]][:, None] + np.arange(3)).ravel()
+        ci = (3 * perm[s["begin"]:s["end"]][:, None] + np.arange(3)).ravel()
+        D = H.block_data(b, blk, cl)
+        Ab = A[np.ix_(ri, ci)]
+        assert np.abs(D - Ab).max() <= 1e-6 * np.abs(Ab).max()
+
+
+def test_multi_rhs_matvec(hm, cfg1):
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d["U"]
+    X = inputs.random_rhs(3 * len(pts), nrhs=4, seed=5)
+    Y = H.matvec(cuda(X)).cpu().numpy()
+    for c in range(4):
+        yo = ref.matvec(np.ascontiguousarray(X[:, c]))
+        assert np.linalg.norm(Y[:, c] - yo) <= 1e-5 * np.linalg.norm(yo)
+
+
+# ---------------------------------------------------------------- (5) GMRES
+def test_gmres_converges_and_estimator(hm, cfg1):
+    """GMRES(50) reaches 1e-6 on A_H; the a-posteriori bound of Eq. est_direct
+    holds for the dense system: ||b - A x||/||b|| <= (delta + ||A_H - A||_F ||x||)/||b||."""
+    pts, nrm, d = cfg1
+    pb, ref, H, A = d["U"]
+    b = inputs.random_rhs(3 * len(pts), seed=0)
+    x, it, rr, st = H.gmres(cuda(b), restart=50, tol=1e-6, maxit=3000)
+    assert st == 0 and rr <= 1e-6
+    x = x.cpu().numpy()
+    bn = np.linalg.norm(b)
+    delta = np.linalg.norm(b - H.matvec(cuda(x)).cpu().numpy())
+    assert delta <= 2e-6 * bn
+    # ||A_H - A||_F from the exported blocks
+    perm, cl = H.tree()
+    blk = H.blocks()
+    diff2 = 0.0
+    for q in range(len(blk)):
+        t, s = cl[blk[q]["tau"]], cl[blk[q]["sigma"]]
+        ri = (3 * perm[t["begin"]:t["end"]][:, None] + np.arange(3)).ravel()
+        ci = (3 * perm[s["begin"]:s["end"]][:, None] + np.arange(3)).ravel()
+        dat = H.block_data(q, blk, cl)
+        M = dat if not blk[q]["admissible"] else dat[0] @ dat[1].conj().T
+        diff2 += np.linalg.norm(A[np.ix_(ri, ci)] - M) ** 2
+    true = np.linalg.norm(b - A @ x) / bn
+    assert true <= (delta + np.sqrt(diff2) * np.linalg.norm(x)) / bn
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("nc,leaf", [(1, 8), (5, 8), (31, 32), (1000, 17)])
+def test_small_and_ragged(hm, oracle, nc, leaf):
+    pts = inputs.fibonacci_sphere(nc) if nc > 1 else np.array([[0.1, 0.2, 0.3]])
+    rho, lam, mu, om = inputs.material(4.0)
+    H = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, leaf)
+    pb = oracle.problem(rho, lam, mu, om, "U")
+    ref = oracle.HMatrix(pb, pts, eps=EPS, eta=3.0, leaf=leaf)
+    x = inputs.random_rhs(3 * nc, seed=1)
+    y = H.matvec(cuda(x)).cpu().numpy()
+    yd = oracle.dense_matrix(pb, pts) @ x
+    assert np.linalg.norm(y - ref.matvec(x)) <= 1e-5 * np.linalg.norm(yd)
+    assert np.linalg.norm(y - yd) <= 3 * EPS * np.linalg.norm(yd)
+
+
+def test_all_dense_limit(hm, oracle):
+    nc = 800
+    pts = inputs.fibonacci_sphere(nc)
+    H = hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", EPS, 1e-12, 32)
+    assert H.blocks()["admissible"].sum() == 0
+    x = inputs.random_rhs(3 * nc, seed=2)
+    yd = oracle.dense_matrix(oracle.problem(1, 2, 1, 4.0, "U"), pts) @ x
+    y = H.matvec(cuda(x)).cpu().numpy()
+    assert np.linalg.norm(y - yd) <= 1e-6 * np.linalg.norm(yd)
+
+
+def test_coplanar_plate(hm, oracle):
+    """Coplanar cloud (reducible 3x3 structure, Eq. FSplane): the sigma_3 pivot
+    keeps the vector ACA accurate."""
+    pts = inputs.plate(40)
+    rho, lam, mu, om = inputs.material(5 * np.pi)
+    pb = oracle.problem(rho, lam, mu, om, "U")
+    H = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 32)
+    x = inputs.random_rhs(3 * len(pts), seed=3)
+    yd = oracle.dense_matrix(pb, pts) @ x
+    y = H.matvec(cuda(x)).cpu().numpy()
+    assert np.linalg.norm(y - yd) <= 3 * EPS * np.linalg.norm(yd)
+
+
+def test_small_capacity_overflow_reruns(hm, oracle):
+    """A tiny initial ACA capacity forces overflow re-runs; the result is unchanged."""
+    nc = 1536
+    pts = inputs.fibonacci_sphere(nc)
+    rho, lam, mu, om = inputs.material(4.0)
+    o = hm.hm_opts_default(aca_max_rank=6)
+    H = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 32, opts=o)
+    assert H.stats()["aca_overflow_reruns"] > 0
+    ref = oracle.HMatrix(oracle.problem(rho, lam, mu, om, "U"), pts, eps=EPS, eta=3.0, leaf=32)
+    x = inputs.random_rhs(3 * nc, seed=4)
+    y = H.matvec(cuda(x)).cpu().numpy()
+    assert np.linalg.norm(y - ref.matvec(x)) <= 1e-5 * np.linalg.norm(y)
+
+
+# ---------------------------------------------------------------- full size, sampled rows
+def test_full_size_sampled_rows(hm, oracle):
+    """65 536 Fibonacci points, k_s = 16, leaf 64 (the plain-form workload):
+    sampled rows of A_H x against rows of the dense product evaluated one by
+    one in FP64 by the oracle."""
+    nc = 65536
+    pts = inputs.fibonacci_sphere(nc)
+    rho, lam, mu, om = inputs.material(16.0)
+    H = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 64)
+    x = inputs.random_rhs(3 * nc, seed=0)
+    y = H.matvec(cuda(x)).cpu().numpy()
+    rows = np.sort(np.random.default_rng(0).choice(3 * nc, 192, replace=False))
+    yd = oracle.dense_rows_matvec(oracle.problem(rho, lam, mu, om, "U"), pts, None, rows, x)
+    assert np.linalg.norm(y[rows] - yd) <= 3 * EPS * np.linalg.norm(yd)
+    st = H.stats()
+    assert st["rank_aca_max"] % 3 == 0 and st["tau_H"] < 0.2
