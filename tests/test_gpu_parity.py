@@ -46,9 +46,13 @@ def test_green_eval_matches_oracle(hm, oracle, kern):
         k = 0 if kern == "U" else 1
         G = hm.hm_green_eval(k, rho, lam, mu, om, cuda(x), cuda(y), cuda(ny)).cpu().numpy()
         pb = oracle.problem(rho, lam, mu, om, kern, diag_value=1.0)
+        ks = om * np.sqrt(rho / mu)
         for q in range(0, n, 37):
             ref = oracle.green(pb, x[q], y[q], ny[q]) if q != 7 else np.eye(3)
-            assert np.abs(G[q] - ref).max() <= 1e-12 * np.abs(ref).max(), q
+            # both FP64 evaluations lose digits to the cancellation of the
+            # curl-curl and grad-div terms of Eq. elasto_U, ~ u / (k_s r)^2
+            tol = 1e-12 + 4e-15 / min(1.0, (ks * r[q]) ** 2)
+            assert np.abs(G[q] - ref).max() <= tol * np.abs(ref).max(), q
 
 
 # ---------------------------------------------------------------- (2) tree + partition
