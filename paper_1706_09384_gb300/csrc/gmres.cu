@@ -1,6 +1,10 @@
 // gmres.cu — restarted GMRES(m) on the H-matrix (Sec. 3.1: the H-matvec is
 // the only operation the iterative solver needs).  FP64 vectors on the
-// device; Arnoldi by classical Gram-Schmidt with one re-orthogonalisation
+// device.  The Arnoldi products use the fast product (FP32 sums); the true
+// residual at each restart uses the accurate product (FP64 sums over the same
+// stored entries), so each restart cycle is one step of iterative refinement
+// and the solve reaches tolerances below the FP32 summation noise.
+// Arnoldi by classical Gram-Schmidt with one re-orthogonalisation
 // (two passes of h = V^H w, w -= V h); complex Givens rotations and the least
 // squares update run in a one-thread kernel, so the only host traffic per
 // iteration is the 8-byte residual estimate.  x_0 = 0; convergence is
@@ -169,6 +173,8 @@ GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int m, doubl
     S.h2 = (double*)dm((size_t)2 * (m + 1) * sizeof(double));
     S.nrm2 = (double*)dm(sizeof(double));
     S.est = (double*)dm(sizeof(double));
+    double2* xp64 = (double2*)dm((size_t)n * sizeof(double2));
+    double2* yp64 = (double2*)dm((size_t)n * sizeof(double2));
     auto cleanup = [&]() {
         cudaStreamSynchronize(st);
         for (DevBuf& d : tmp) cudaFree(d.p);
@@ -198,8 +204,9 @@ GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int m, doubl
         }
         int iters = 0;
         for (;;) {
-            // r = b - A x, into V_0
-            apply_fp64(h, x, w, st);
+            // r = b - A x with the accurate product (iterative refinement of the
+            // fast FP32 inner iterations), into V_0
+            matvec_accurate(h->mv, h->d_perm, x, xp64, yp64, w, h->nc, st);
             axpby_kernel<<<nb, GT, 0, st>>>(w, b, 1.0, w, -1.0, n);
             HM_LAUNCHED();
             HM_CUDA(cudaGetLastError());

@@ -93,6 +93,10 @@ void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_
                      cudaStream_t st);
 void launch_scatter_y(const int64_t* d_perm, const float2* yp, double2* y, int64_t nc,
                       cudaStream_t st);
+// Accurate product (FP32-stored entries, FP64 x / t / y and FP64 sums), used for
+// the true residual of GMRES restarts.  xp64, yp64: tree-order scratch (3 nc).
+void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* xp64,
+                     double2* yp64, double2* y, int64_t nc, cudaStream_t st);
 // The three parts of the product, for per-kernel timing.
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st);
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);

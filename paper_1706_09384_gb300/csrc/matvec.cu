@@ -46,6 +46,7 @@ struct MatvecDev {
     int32_t* order2 = nullptr;
     int64_t n1 = 0, n2 = 0;
     float2* t = nullptr;
+    double2* t64 = nullptr;       // accurate product: t in FP64
     int64_t t_elems = 0;
     int64_t dense_elems = 0;
     int64_t lr_elems = 0;
@@ -62,21 +63,49 @@ constexpr int PAIRS_PER_LANE = MAX_LD / 64;  // row pairs per lane (3)
 
 __device__ __forceinline__ float4 ldg_stream(const float4* p) { return __ldcs(p); }
 
+// Accumulation precision: the fast product keeps x, t, y and the sums in
+// FP32; the accurate product (used for GMRES restart residuals) widens the
+// FP32-stored entries to FP64 and keeps x, t, y and the sums in FP64.
+template <bool ACC> struct MvT;
+template <> struct MvT<false> {
+    using R = float;
+    using C2 = float2;
+    struct C4 { float x, y, z, w; };
+};
+template <> struct MvT<true> {
+    using R = double;
+    using C2 = double2;
+    struct C4 { double x, y, z, w; };
+};
+
+__device__ __forceinline__ float red_sum(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double red_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ void atomic_add_c(float2* p, float re, float im) {
+    atomicAdd(p, make_float2(re, im));
+}
+__device__ __forceinline__ void atomic_add_c(double2* p, double re, double im) {
+    atomicAdd(&p->x, re);
+    atomicAdd(&p->y, im);
+}
+
 // Phase 1: for every V chunk of the item's column leaf, t[vec + c] += V[:, c]^H x_leaf.
+template <bool ACC>
 __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
                                                        const int32_t* order,
                                                        const DevChunk* chunks,
                                                        const float2* __restrict__ arena,
-                                                       const float2* __restrict__ xp,
-                                                       float2* t) {
+                                                       const typename MvT<ACC>::C2* __restrict__ xp,
+                                                       typename MvT<ACC>::C2* t) {
+    using R = typename MvT<ACC>::R;
+    using C4 = typename MvT<ACC>::C4;
     const WorkItem it = items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this lane's x values (row pairs lane, lane+32, lane+64)
-    float4 xv[PAIRS_PER_LANE];
+    C4 xv[PAIRS_PER_LANE];
 #pragma unroll
     for (int q = 0; q < PAIRS_PER_LANE; ++q) {
         const int r = 2 * (lane + 32 * q);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        C4 v = {0, 0, 0, 0};
         if (r < it.rows) {
             v.x = xp[it.dof + r].x;
             v.y = xp[it.dof + r].y;
@@ -93,49 +122,61 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
         for (int c = warp; c < ch.ncols; c += MV_WARPS) {
             const float4* col = base + (int64_t)c * (ch.ld >> 1);
-            float re = 0.f, im = 0.f;
+            R re = 0, im = 0;
 #pragma unroll
             for (int q = 0; q < PAIRS_PER_LANE; ++q) {
                 const int pr = lane + 32 * q;
                 if (pr < npair) {
-                    const float4 v = ldg_stream(col + pr);
+                    const float4 v4 = ldg_stream(col + pr);
+                    const R vx = v4.x, vy = v4.y, vz = v4.z, vw = v4.w;
                     // conj(v) * x
-                    re = fmaf(v.x, xv[q].x, fmaf(v.y, xv[q].y, re));
-                    im = fmaf(v.x, xv[q].y, fmaf(-v.y, xv[q].x, im));
-                    re = fmaf(v.z, xv[q].z, fmaf(v.w, xv[q].w, re));
-                    im = fmaf(v.z, xv[q].w, fmaf(-v.w, xv[q].z, im));
+                    re = fma(vx, xv[q].x, fma(vy, xv[q].y, re));
+                    im = fma(vx, xv[q].y, fma(-vy, xv[q].x, im));
+                    re = fma(vz, xv[q].z, fma(vw, xv[q].w, re));
+                    im = fma(vz, xv[q].w, fma(-vw, xv[q].z, im));
                 }
             }
-            re = warp_sumf(re);
-            im = warp_sumf(im);
-            if (lane == 0) atomicAdd(t + ch.vec + c, make_float2(re, im));
+            re = red_sum(re);
+            im = red_sum(im);
+            if (lane == 0) atomic_add_c(t + ch.vec + c, re, im);
         }
     }
 }
 
 // Phase 2: y_leaf += sum over chunks of chunk * v, v = x (dense) or t (U).
+template <bool ACC>
 __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
                                                        const int32_t* order,
                                                        const DevChunk* chunks,
                                                        const float2* __restrict__ arena,
-                                                       const float2* __restrict__ xp,
-                                                       const float2* __restrict__ t,
-                                                       float2* yp) {
-    __shared__ float4 part[MV_WARPS][MAX_LD / 2];
+                                                       const typename MvT<ACC>::C2* __restrict__ xp,
+                                                       const typename MvT<ACC>::C2* __restrict__ t,
+                                                       typename MvT<ACC>::C2* yp) {
+    using R = typename MvT<ACC>::R;
+    using C2 = typename MvT<ACC>::C2;
+    using C4 = typename MvT<ACC>::C4;
+    __shared__ C4 part[MV_WARPS][MAX_LD / 2];
     const WorkItem it = items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npair = it.ld >> 1;
-    float4 acc[PAIRS_PER_LANE];
+    C4 acc[PAIRS_PER_LANE];
 #pragma unroll
-    for (int q = 0; q < PAIRS_PER_LANE; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) acc[q] = C4{0, 0, 0, 0};
+    auto fma_col = [&](C4& s, const float4& a, const C2& v) {
+        const R ax = a.x, ay = a.y, az = a.z, aw = a.w;
+        s.x = fma(ax, v.x, fma(-ay, v.y, s.x));
+        s.y = fma(ax, v.y, fma(ay, v.x, s.y));
+        s.z = fma(az, v.x, fma(-aw, v.y, s.z));
+        s.w = fma(az, v.y, fma(aw, v.x, s.w));
+    };
     for (int ci = it.first; ci < it.last; ++ci) {
         const DevChunk ch = chunks[order[ci]];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
-        const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
+        const C2* v = (ch.kind == 0 ? xp : t) + ch.vec;
         int c = warp;
         // two columns per iteration for more loads in flight
         for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
-            const float2 v0 = __ldg(v + c), v1 = __ldg(v + c + MV_WARPS);
+            const C2 v0 = v[c], v1 = v[c + MV_WARPS];
             const float4* col0 = base + (int64_t)c * (ch.ld >> 1);
             const float4* col1 = col0 + (int64_t)MV_WARPS * (ch.ld >> 1);
             float4 a0[PAIRS_PER_LANE], a1[PAIRS_PER_LANE];
@@ -151,32 +192,18 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
             for (int q = 0; q < PAIRS_PER_LANE; ++q) {
                 const int pr = lane + 32 * q;
                 if (pr < npair) {
-                    float4& s = acc[q];
-                    s.x = fmaf(a0[q].x, v0.x, fmaf(-a0[q].y, v0.y, s.x));
-                    s.y = fmaf(a0[q].x, v0.y, fmaf(a0[q].y, v0.x, s.y));
-                    s.z = fmaf(a0[q].z, v0.x, fmaf(-a0[q].w, v0.y, s.z));
-                    s.w = fmaf(a0[q].z, v0.y, fmaf(a0[q].w, v0.x, s.w));
-                    s.x = fmaf(a1[q].x, v1.x, fmaf(-a1[q].y, v1.y, s.x));
-                    s.y = fmaf(a1[q].x, v1.y, fmaf(a1[q].y, v1.x, s.y));
-                    s.z = fmaf(a1[q].z, v1.x, fmaf(-a1[q].w, v1.y, s.z));
-                    s.w = fmaf(a1[q].z, v1.y, fmaf(a1[q].w, v1.x, s.w));
+                    fma_col(acc[q], a0[q], v0);
+                    fma_col(acc[q], a1[q], v1);
                 }
             }
         }
         for (; c < ch.ncols; c += MV_WARPS) {
-            const float2 v0 = __ldg(v + c);
+            const C2 v0 = v[c];
             const float4* col0 = base + (int64_t)c * (ch.ld >> 1);
 #pragma unroll
             for (int q = 0; q < PAIRS_PER_LANE; ++q) {
                 const int pr = lane + 32 * q;
-                if (pr < npair) {
-                    const float4 a = ldg_stream(col0 + pr);
-                    float4& s = acc[q];
-                    s.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s.x));
-                    s.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s.y));
-                    s.z = fmaf(a.z, v0.x, fmaf(-a.w, v0.y, s.z));
-                    s.w = fmaf(a.z, v0.y, fmaf(a.w, v0.x, s.w));
-                }
+                if (pr < npair) fma_col(acc[q], ldg_stream(col0 + pr), v0);
             }
         }
     }
@@ -187,7 +214,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
     }
     __syncthreads();
     for (int pr = threadIdx.x; pr < npair; pr += MV_THREADS) {
-        float4 s = part[0][pr];
+        C4 s = part[0][pr];
         for (int w = 1; w < MV_WARPS; ++w) {
             s.x += part[w][pr].x;
             s.y += part[w][pr].y;
@@ -195,9 +222,23 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
             s.w += part[w][pr].w;
         }
         const int r = 2 * pr;
-        if (r < it.rows) atomicAdd(yp + it.dof + r, make_float2(s.x, s.y));
-        if (r + 1 < it.rows) atomicAdd(yp + it.dof + r + 1, make_float2(s.z, s.w));
+        if (r < it.rows) atomic_add_c(yp + it.dof + r, s.x, s.y);
+        if (r + 1 < it.rows) atomic_add_c(yp + it.dof + r + 1, s.z, s.w);
     }
+}
+
+__global__ void gather_x64_kernel(const int64_t* perm, const double2* x, double2* xp, int64_t nc) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * nc) return;
+    const int64_t p = q / 3, a = q - 3 * p;
+    xp[q] = x[3 * perm[p] + a];
+}
+
+__global__ void scatter_y64_kernel(const int64_t* perm, const double2* yp, double2* y, int64_t nc) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * nc) return;
+    const int64_t p = q / 3, a = q - 3 * p;
+    y[3 * perm[p] + a] = yp[q];
 }
 
 __global__ void gather_x_kernel(const int64_t* perm, const double2* x, float2* xp, int64_t nc) {
@@ -415,6 +456,7 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
     HM_CUDA(cudaMemcpyAsync(m->order2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, st));
     m->t_elems = plan.t_elems;
     m->t = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(float2), st, true);
+    m->t64 = (double2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(double2), st, true);
     HM_CUDA(cudaStreamSynchronize(st));
     return m;
 }
@@ -427,8 +469,8 @@ int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
     if (m->n1) {
-        mv_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
-                                                         m->arena, xp, m->t);
+        mv_phase1<false><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
+                                                                m->arena, xp, m->t);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
@@ -437,8 +479,8 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
     if (m->n2) {
-        mv_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
-                                                         m->arena, xp, m->t, yp);
+        mv_phase2<false><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
+                                                                m->arena, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
@@ -447,6 +489,32 @@ void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cud
 void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     matvec_phase1(m, xp, st);
     matvec_phase2(m, xp, yp, ndof, st);
+}
+
+void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* xp64,
+                     double2* yp64, double2* y, int64_t nc, cudaStream_t st) {
+    const int64_t n = 3 * nc;
+    const unsigned nb = (unsigned)hm_cdiv(n, 256);
+    gather_x64_kernel<<<nb, 256, 0, st>>>(d_perm, x, xp64, nc);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t64, 0, m->t_elems * sizeof(double2), st));
+    HM_CUDA(cudaMemsetAsync(yp64, 0, n * sizeof(double2), st));
+    if (m->n1) {
+        mv_phase1<true><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
+                                                               m->arena, xp64, m->t64);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    if (m->n2) {
+        mv_phase2<true><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
+                                                               m->arena, xp64, m->t64, yp64);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    scatter_y64_kernel<<<nb, 256, 0, st>>>(d_perm, yp64, y, nc);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
 }
 
 void matvec_alg_bytes(const MatvecDev* m, int64_t ndof, int64_t out[3]) {
