@@ -457,9 +457,8 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                 int* d_counter, cudaStream_t st) {
     if (njobs == 0) return;
     const size_t smem = (size_t)6 * capmax * sizeof(double2);
-    if (smem > 48 * 1024)
-        HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     HM_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
     aca_kernel<<<nctas, AT, smem, st>>>(gp, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
                                         d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
@@ -471,9 +470,8 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
 int aca_ctas_per_sm(int capmax) {
     int nb = 0;
     const size_t smem = (size_t)6 * capmax * sizeof(double2);
-    if (smem > 48 * 1024)
-        HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aca_kernel, AT, smem));
     return nb > 0 ? nb : 1;
 }

@@ -363,9 +363,9 @@ void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64
     HM_CUDA(cudaMallocAsync((void**)&B->d_rank, std::max<size_t>(nj, 1) * sizeof(int32_t), st));
     HM_CUDA(cudaMemcpyAsync(B->d_jobs, B->jobs.data(), nj * sizeof(CoreJob), cudaMemcpyHostToDevice, st));
     const size_t smem = (size_t)TILE_ROWS * kmax * sizeof(double2);
-    if (smem > 48 * 1024)
-        HM_CUDA(cudaFuncSetAttribute(recomp_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    // static (about 20 KB) + dynamic shared memory may exceed the 48 KB default
+    HM_CUDA(cudaFuncSetAttribute(recomp_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     if (nj) {
         recomp_core_kernel<<<(unsigned)nj, RT, smem, st>>>(B->d_jobs, d_work, B->d_scratch, eps,
                                                           B->d_rank, kmax);
