@@ -37,6 +37,7 @@ METRIC = ("H-matvec GB/s (% HBM peak) + build s, mixed vs plain GPU form at rel.
 
 WORKLOADS = {
     "sphere65536_ks16_U": dict(nc=65536, ks=16.0, kernel="U", leaf=64, eta=3.0, eps=1e-4),
+    "sphere16384_ks16_U": dict(nc=16384, ks=16.0, kernel="U", leaf=64, eta=3.0, eps=1e-4),
     "sphere1536_ks4_U": dict(nc=1536, ks=4.0, kernel="U", leaf=32, eta=3.0, eps=1e-4),
 }
 
