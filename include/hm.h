@@ -174,6 +174,41 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
                     const hm_cluster* clusters, int64_t n_blocks, const hm_block* blocks,
                     const void* data, const hm_opts* opts, void* stream, hm_handle* out);
 
+/* ---- allocation-free single-block compression ---- */
+
+/* Largest number of points on each side of a block accepted by
+ * hm_aca_block_noalloc (its fixed device scratch is sized for this). */
+#define HM_NOALLOC_MAX_POINTS 8192
+
+/* Vector ACA of one block that allocates no device memory.  The paper has no
+ * counterpart: this is a service entry point for callers that cannot call
+ * cudaMalloc - code whose device memory is wholly owned by another allocator
+ * (a framework's caching pool that has reserved the free memory, or an
+ * application held to a fixed memory budget), and latency-sensitive loops that
+ * must not take the device-wide synchronisation cudaMalloc / cudaFree imply.
+ * It runs the same ACA kernel as hm_build (rank-3 steps, sigma_3 pivot, FP64
+ * residuals, eps stopping test) on the block K(x_i, y_j), i < m, j < n.
+ *   x: DEVICE m x 3 FP64 row points;  y: DEVICE n x 3 FP64 column points;
+ *   ny: DEVICE n x 3 unit normals at y (T kernel only, else NULL);
+ *   1 <= m, n <= HM_NOALLOC_MAX_POINTS;  cap: column capacity, a multiple of 3
+ *   in 3..768;  uv: DEVICE complex128 output of (3m + 3n) x cap entries,
+ *   16-byte aligned: U (3m x cap, column-major) then V (3n x cap), block =
+ *   U[:, :rank] V[:, :rank]^H;  rank: HOST output, the ACA rank (multiple of 3).
+ * Its scratch is one fixed device array of about 3 MiB inside this library,
+ * held by every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * each call re-initialises what must start at zero, but calls that overlap on
+ * the GPU (other streams, other host threads) race on it: serialise them.  The
+ * call waits for its stream to finish.
+ * Errors: HM_ERR_ARG (null or misaligned pointer, sizes beyond the limits,
+ * cap too small for the block's rank: *rank = -1), HM_ERR_NUMERIC, HM_ERR_CUDA. */
+hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lambda, double mu,
+                               double omega, const double* x, int64_t m, const double* y,
+                               const double* ny, int64_t n, double eps, int32_t cap, void* uv,
+                               int32_t* rank, void* stream);
+
 /* ---- measurement ---- */
 
 /* Runs `reps` products on internal vectors (x = 1 in tree order) and reports

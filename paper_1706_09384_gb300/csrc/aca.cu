@@ -475,3 +475,109 @@ int aca_ctas_per_sm(int capmax) {
     HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aca_kernel, AT, smem));
     return nb > 0 ? nb : 1;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-block ACA.  The paper has no counterpart; this entry
+// point serves callers that may not call cudaMalloc (see include/hm.h).  All
+// scratch of the ACA kernel for one block (points, normals, residual row and
+// column buffers, row/column flags, job, result, queue counter) lives in one
+// file-scope device array sized for blocks of up to HM_NOALLOC_MAX_POINTS
+// points per side.  Host code must not use the array's name as a device
+// address: its device address is taken with cudaGetSymbolAddress once per
+// device, with that device current.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t NA_MAXP = HM_NOALLOC_MAX_POINTS;
+constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_PTS = 0;                                        // [x; y], 3 doubles per point
+constexpr size_t NA_NRM = NA_PTS + na_align(24 * 2 * NA_MAXP);      // normals at y in the same layout
+constexpr size_t NA_ROW = NA_NRM + na_align(24 * 2 * NA_MAXP);      // 9 n complex128
+constexpr size_t NA_COL = NA_ROW + na_align(16 * 9 * NA_MAXP);      // 9 m complex128
+constexpr size_t NA_FLG = NA_COL + na_align(16 * 9 * NA_MAXP);      // m + n bytes
+constexpr size_t NA_JOB = NA_FLG + na_align(2 * NA_MAXP);
+constexpr size_t NA_RES = NA_JOB + na_align(sizeof(AcaJob));
+constexpr size_t NA_CNT = NA_RES + na_align(sizeof(AcaResult));
+constexpr size_t NA_BYTES = NA_CNT + na_align(sizeof(int));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mutex;
+unsigned char* g_na_addr[NA_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (set up on first use).
+unsigned char* noalloc_scratch(int dev) {
+    if (dev < 0 || dev >= NA_MAX_DEVICES) hm_throw(HM_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        HM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_na_addr[dev] = (unsigned char*)p;
+    }
+    return g_na_addr[dev];
+}
+
+}  // namespace
+
+extern "C" hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lambda, double mu,
+                                          double omega, const double* x, int64_t m,
+                                          const double* y, const double* ny, int64_t n,
+                                          double eps, int32_t cap, void* uv, int32_t* rank,
+                                          void* stream) {
+    try {
+        if (rank) *rank = -1;
+        if (!x || !y || !uv || !rank) hm_throw(HM_ERR_ARG, "null pointer");
+        if (m < 1 || n < 1 || m > NA_MAXP || n > NA_MAXP)
+            hm_throw(HM_ERR_ARG, "block sides must hold 1.." + std::to_string(NA_MAXP) +
+                                     " points (allocation-free scratch limit)");
+        if (cap < 3 || cap > 768 || cap % 3) hm_throw(HM_ERR_ARG, "cap must be a multiple of 3 in 3..768");
+        if (kernel != HM_KERNEL_U && kernel != HM_KERNEL_T) hm_throw(HM_ERR_ARG, "unknown kernel");
+        if (kernel == HM_KERNEL_T && !ny) hm_throw(HM_ERR_ARG, "the T kernel needs normals");
+        if (!(rho > 0) || !(mu > 0) || !(omega > 0) || !(lambda + 2 * mu > 0))
+            hm_throw(HM_ERR_ARG, "bad material parameters");
+        if (!(eps > 0 && eps < 1)) hm_throw(HM_ERR_ARG, "eps must lie in (0, 1)");
+        if (reinterpret_cast<uintptr_t>(uv) % 16) hm_throw(HM_ERR_ARG, "uv must be 16-byte aligned");
+        cudaStream_t st = (cudaStream_t)stream;
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        unsigned char* base = noalloc_scratch(dev);
+        double* pts = (double*)(base + NA_PTS);
+        double* nrm = (double*)(base + NA_NRM);
+        HM_CUDA(cudaMemcpyAsync(pts, x, 24 * m, cudaMemcpyDeviceToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(pts + 3 * m, y, 24 * n, cudaMemcpyDeviceToDevice, st));
+        if (kernel == HM_KERNEL_T)
+            HM_CUDA(cudaMemcpyAsync(nrm + 3 * m, ny, 24 * n, cudaMemcpyDeviceToDevice, st));
+        AcaJob J;
+        J.tau_begin = 0;
+        J.m = m;
+        J.sig_begin = m;
+        J.n = n;
+        J.u_off = 0;
+        J.v_off = 3 * m * (int64_t)cap;
+        J.cap = cap;
+        J.pad_ = 0;
+        AcaJob* d_job = (AcaJob*)(base + NA_JOB);
+        AcaResult* d_res = (AcaResult*)(base + NA_RES);
+        HM_CUDA(cudaMemcpyAsync(d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
+        const GreenParams gp = make_green_params(kernel, rho, lambda, mu, omega, 1.0);
+        launch_aca(gp, pts, kernel == HM_KERNEL_T ? nrm : nullptr, d_job, 1, (double2*)uv,
+                   base + NA_FLG, m + n, (double2*)(base + NA_ROW), (double2*)(base + NA_COL),
+                   9 * n, 9 * m, eps, d_res, 1, cap, (int*)(base + NA_CNT), st);
+        AcaResult R;
+        HM_CUDA(cudaMemcpyAsync(&R, d_res, sizeof(R), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        if (R.status == 1) hm_throw(HM_ERR_ARG, "ACA rank exceeds cap; call again with a larger cap");
+        if (R.status == 2) hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA");
+        *rank = R.k;
+    } catch (const hm_error& e) {
+        hm_set_error(e.msg);
+        return e.st;
+    } catch (...) {
+        hm_set_error("unexpected internal error");
+        return HM_ERR_CUDA;
+    }
+    return HM_OK;
+}

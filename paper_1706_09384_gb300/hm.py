@@ -67,6 +67,8 @@ SIGNATURES = {
     "hm_get_block_data": (_I32, [_P, _I64, _P, _P]),
     "hm_green_eval": (_I32, [_I32, _D, _D, _D, _D, _D, _P, _P, _P, _I64, _P, _P]),
     "hm_import": (_I32, [_I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P]),
+    "hm_aca_block_noalloc": (_I32, [_I32, _D, _D, _D, _D, _P, _I64, _P, _P, _I64, _D, _I32, _P,
+                                    _P, _P]),
     "hm_profile_matvec": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_kernel_launches": (_I64, []),
     "hm_free": (None, [_P]),
@@ -137,6 +139,21 @@ def hm_green_eval(kernel, rho, lam, mu, omega, x, y, ny=None, diag_value=1.0, st
                                y.data_ptr(), ny.data_ptr() if ny is not None else None, n,
                                out.data_ptr(), _stream_ptr(stream)), "hm_green_eval")
     return out
+
+
+HM_NOALLOC_MAX_POINTS = 8192
+
+
+def hm_aca_block_noalloc(kernel, rho, lam, mu, omega, x, y, ny, eps, cap, uv, stream=None):
+    """Allocation-free vector ACA of one block.  x (m, 3), y (n, 3), ny (n, 3) or
+    None: cuda float64; uv: cuda complex128 of (3m + 3n) * cap entries.
+    Returns the rank; U = uv[:3m cap] (3m x cap col-major), V follows."""
+    rank = C.c_int32(-1)
+    _check(lib().hm_aca_block_noalloc(kernel, rho, lam, mu, omega, x.data_ptr(), x.shape[0],
+                                      y.data_ptr(), ny.data_ptr() if ny is not None else None,
+                                      y.shape[0], eps, cap, uv.data_ptr(), C.byref(rank),
+                                      _stream_ptr(stream)), "hm_aca_block_noalloc")
+    return rank.value
 
 
 class HMatrix:
