@@ -120,8 +120,9 @@ void or_green(const or_problem* pb, const double* x, const double* y, const doub
         for (int b = 0; b < 3; ++b) st(G18 + 2 * (3 * a + b), G[a][b]);
 }
 
-/* Block (i, j) of A: K(x_i, x_j) off the diagonal, diag_value * I3 on it.
- * The same cloud serves as x and y (collocation, Sec. 4). */
+/* Block (i, j) of A: K(x_i, x_j) w_j off the diagonal (w_j = 1 without
+ * weights; the column scaling W_y of the collocation matrix, Sec. 4),
+ * diag_value * I3 on it.  The same cloud serves as x and y (Sec. 4). */
 static void entry_block(const or_problem* pb, const double* pts, const double* nrm, int64_t i,
                         int64_t j, cplx G[3][3])
 {
@@ -131,6 +132,9 @@ static void entry_block(const or_problem* pb, const double* pts, const double* n
         return;
     }
     green(pb, pts + 3 * i, pts + 3 * j, nrm ? nrm + 3 * j : NULL, G);
+    if (pb->weights)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[a][b] *= pb->weights[j];
 }
 
 void or_dense_matrix(const or_problem* pb, const double* pts, const double* nrm, int64_t nc,

@@ -29,13 +29,15 @@ extern "C" {
 #endif
 
 /* Problem definition: material (rho, lambda, mu), frequency omega, kernel
- * (0 = U_omega, Eq. elasto_U; 1 = T_omega, Eq. elasto_T) and the value put on
- * the i = j diagonal 3x3 block (diag_value * I3). */
+ * (0 = U_omega, Eq. elasto_U; 1 = T_omega, Eq. elasto_T), the value put on
+ * the i = j diagonal 3x3 block (diag_value * I3) and optional column weights:
+ * block (i, j), i != j, is K(x_i, x_j) w_j (A = K W_y, Sec. 4). */
 typedef struct {
     double rho, lam, mu, omega;
     int32_t kernel;
     int32_t pad_;
     double diag_value;
+    const double* weights;   /* column weights w_j (the diagonal W_y of Sec. 4), NULL = 1 */
 } or_problem;
 
 /* One node of the binary cluster tree T_I (Sec. 2.1, "Clustering"). Points

@@ -15,7 +15,7 @@ _lib = None
 class Problem(C.Structure):
     _fields_ = [("rho", C.c_double), ("lam", C.c_double), ("mu", C.c_double),
                 ("omega", C.c_double), ("kernel", C.c_int32), ("pad_", C.c_int32),
-                ("diag_value", C.c_double)]
+                ("diag_value", C.c_double), ("weights", C.c_void_p)]
 
 
 class Cluster(C.Structure):
@@ -95,9 +95,16 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def problem(rho=1.0, lam=2.0, mu=1.0, omega=4.0, kernel="U", diag_value=1.0):
+def problem(rho=1.0, lam=2.0, mu=1.0, omega=4.0, kernel="U", diag_value=1.0, weights=None):
+    """Problem definition; `weights` (n_c column weights w_j) are kept alive on
+    the returned object."""
     k = {"U": 0, "T": 1}[kernel] if isinstance(kernel, str) else int(kernel)
-    return Problem(rho, lam, mu, omega, k, 0, diag_value)
+    pb = Problem(rho, lam, mu, omega, k, 0, diag_value, None)
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        pb._w = w
+        pb.weights = w.ctypes.data
+    return pb
 
 
 def radial(r, rho, lam, mu, omega):

@@ -105,3 +105,29 @@ def test_gmres_hmatrix_and_estimator(oracle):
     true = np.linalg.norm(b - A @ x0) / bn
     assert true <= (delta + dHF * np.linalg.norm(x0)) / bn
     assert np.linalg.norm(AH @ np.ones(3 * nc) - H.matvec(np.ones(3 * nc))) < 1e-12 * np.linalg.norm(AH @ np.ones(3 * nc))
+
+
+def test_uniform_weights_scale_the_offdiagonal(oracle):
+    """A = K W_y (Sec. 4) with uniform w_j = c equals c times the unweighted
+    matrix whose diagonal is diag/c: the tree, the partition, every ACA pivot
+    and the truncation are scale invariant, so the H-matvecs agree to rounding."""
+    nc, c = 900, 4 * np.pi / 900
+    pts = inputs.fibonacci_sphere(nc)
+    x = inputs.random_rhs(3 * nc, seed=6)
+    Hw = oracle.HMatrix(oracle.problem(1, 2, 1, 4.0, "U", 1.0, np.full(nc, c)), pts, leaf=32)
+    H1 = oracle.HMatrix(oracle.problem(1, 2, 1, 4.0, "U", 1.0 / c), pts, leaf=32)
+    y1 = c * H1.matvec(x)
+    assert np.linalg.norm(Hw.matvec(x) - y1) <= 1e-13 * np.linalg.norm(y1)
+    assert np.array_equal(Hw.blocks()[1], H1.blocks()[1])
+
+
+def test_weighted_hmatvec_vs_dense(oracle):
+    nc = 1200
+    pts, nrm = inputs.ellipsoid(nc)
+    w = np.random.default_rng(8).uniform(0.5, 1.5, nc) * 4 * np.pi / nc
+    for kern in ("U", "T"):
+        pb = oracle.problem(1, 2, 1, 6.0, kern, 1.0, w)
+        H = oracle.HMatrix(pb, pts, nrm, eps=1e-4, eta=3.0, leaf=32)
+        x = inputs.random_rhs(3 * nc, seed=7)
+        yd = oracle.dense_matrix(pb, pts, nrm) @ x
+        assert np.linalg.norm(H.matvec(x) - yd) <= 3e-4 * np.linalg.norm(yd)
