@@ -73,7 +73,11 @@ typedef struct {
                                  blocks that need more are re-run with twice the capacity */
     int64_t workspace_bytes;  /* bound on the ACA workspace of one batch (0 = 24 GiB) */
     int32_t verbose;          /* 1: phase timings on stderr */
-    int32_t reserved[7];
+    int32_t pad_;
+    const double* weights;    /* HOST, n_c column weights w_j (NULL = 1): block (i, j), i != j,
+                                 becomes K(x_i, x_j) w_j - the quadrature weights W_y of the
+                                 collocation matrix A = U W_y V_y (Sec. 4) */
+    int32_t reserved[4];
 } hm_opts;
 
 void hm_opts_default(hm_opts* opts);

@@ -151,7 +151,7 @@ HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
 __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* __restrict__ pts,
                                                  const double* __restrict__ nrm,
                                                  const AcaJob* __restrict__ jobs, int64_t njobs,
-                                                 int* counter, double2* work,
+                                                 int* counter, double2* work, double2* gram,
                                                  unsigned char* flags, int64_t flag_stride,
                                                  double2* rowbuf, double2* colbuf,
                                                  int64_t rb_stride, int64_t cb_stride,
@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
         const int64_t m = J.m, n = J.n, m3 = 3 * m, n3 = 3 * n;
         double2* U = work + J.u_off;
         double2* V = work + J.v_off;
+        double2* GU = (gram && J.g_off >= 0) ? gram + J.g_off : nullptr;  // U^H U, ld cap
+        double2* GV = GU ? GU + (int64_t)J.cap * J.cap : nullptr;          // V^H V, ld cap
         unsigned char* urow = used;
         unsigned char* ucol = used + m;
         for (int64_t q = tid; q < m + n; q += AT) used[q] = 0;
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                     for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
                 } else {
                     green_tensor(gp, xr + 3 * ihat, xc + 3 * j, nc ? nc + 3 * j : nullptr, G);
+                    apply_weight(gp, J.sig_begin + j, G);
                 }
                 for (int p = 0; p < k; ++p) {
                     const double2* vp = V + (int64_t)p * n3 + 3 * j;
@@ -301,6 +304,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                     for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
                 } else {
                     green_tensor(gp, xr + 3 * i, xc + 3 * jhat, nc ? nc + 3 * jhat : nullptr, G);
+                    apply_weight(gp, J.sig_begin + jhat, G);
                 }
                 for (int p = 0; p < k; ++p) {
                     const double2* up = U + (int64_t)p * m3 + 3 * i;
@@ -378,6 +382,17 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                         dB2 += cmul(gu, gv).x;
                     }
                 s_dB2 = dB2;
+                if (GU && k + 3 <= J.cap) {
+                    // new diagonal blocks of the Gram matrices: Un^H Un and Vn^H Vn
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int q2 = 0; q2 < 3; ++q2) {
+                            const int64_t at = (k + q) + (int64_t)(k + q2) * J.cap;
+                            GU[at] = make_double2(g[2 * (3 * q + q2)], g[2 * (3 * q + q2) + 1]);
+                            GV[at] = make_double2(g[18 + 2 * (3 * q + q2)], g[18 + 2 * (3 * q + q2) + 1]);
+                        }
+                }
             }
             if (k + 3 > J.cap) {
                 if (tid == 0) s_stop = 2;
@@ -415,10 +430,17 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                 }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const double2 z = cmul(make_double2(x[2 * q], x[2 * q + 1]),
-                                           make_double2(y[2 * q], y[2 * q + 1]));
+                    const double2 xq = make_double2(x[2 * q], x[2 * q + 1]);  // U_p^H Un_q
+                    const double2 yq = make_double2(y[2 * q], y[2 * q + 1]);  // Vn_q^H V_p
+                    const double2 z = cmul(xq, yq);
                     cre += z.x;
                     cim += z.y;
+                    if (GU && lane == 0) {  // the new Gram columns, by Hermitian symmetry
+                        GU[p + (int64_t)(k + q) * J.cap] = xq;
+                        GU[(k + q) + (int64_t)p * J.cap] = cconj(xq);
+                        GV[(k + q) + (int64_t)p * J.cap] = yq;
+                        GV[p + (int64_t)(k + q) * J.cap] = cconj(yq);
+                    }
                 }
             }
             double cr[2] = {lane == 0 ? cre : 0.0, lane == 0 ? cim : 0.0};
@@ -451,7 +473,8 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
 }  // namespace
 
 void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
-                const AcaJob* d_jobs, int64_t njobs, double2* d_work, unsigned char* d_flags,
+                const AcaJob* d_jobs, int64_t njobs, double2* d_work, double2* d_gram,
+                unsigned char* d_flags,
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
                 int* d_counter, cudaStream_t st) {
@@ -461,7 +484,7 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                                  (int)smem));
     HM_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
     aca_kernel<<<nctas, AT, smem, st>>>(gp, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
-                                        d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
+                                        d_gram, d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
                                         colbuf_stride, capmax, eps, d_res);
                                         HM_LAUNCHED();
     HM_CUDA(cudaGetLastError());
@@ -557,13 +580,14 @@ extern "C" hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lam
         J.n = n;
         J.u_off = 0;
         J.v_off = 3 * m * (int64_t)cap;
+        J.g_off = -1;
         J.cap = cap;
         J.pad_ = 0;
         AcaJob* d_job = (AcaJob*)(base + NA_JOB);
         AcaResult* d_res = (AcaResult*)(base + NA_RES);
         HM_CUDA(cudaMemcpyAsync(d_job, &J, sizeof(J), cudaMemcpyHostToDevice, st));
         const GreenParams gp = make_green_params(kernel, rho, lambda, mu, omega, 1.0);
-        launch_aca(gp, pts, kernel == HM_KERNEL_T ? nrm : nullptr, d_job, 1, (double2*)uv,
+        launch_aca(gp, pts, kernel == HM_KERNEL_T ? nrm : nullptr, d_job, 1, (double2*)uv, nullptr,
                    base + NA_FLG, m + n, (double2*)(base + NA_ROW), (double2*)(base + NA_COL),
                    9 * n, 9 * m, eps, d_res, 1, cap, (int*)(base + NA_CNT), st);
         AcaResult R;

@@ -105,13 +105,13 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             // ---- form a batch ----
             std::vector<AcaJob> jobs;
             std::vector<int64_t> ids;
-            int64_t woff = 0, maxm = 1, maxn = 1;
+            int64_t woff = 0, goff = 0, maxm = 1, maxn = 1;
             int capmax = 3;
             while (pos < todo.size()) {
                 const int64_t b = todo[pos];
                 const int64_t m = pts_of(blk[b].tau), n = pts_of(blk[b].sigma);
-                const int64_t need = 3 * (m + n) * (int64_t)cap[b] * 16;
-                if (!jobs.empty() && (woff * 16 + need) > budget) break;
+                const int64_t need = (3 * (m + n) * (int64_t)cap[b] + 2 * (int64_t)cap[b] * cap[b]) * 16;
+                if (!jobs.empty() && (woff + goff) * 16 + need > budget) break;
                 AcaJob J;
                 J.tau_begin = cl[blk[b].tau].begin;
                 J.m = m;
@@ -119,9 +119,11 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                 J.n = n;
                 J.u_off = woff;
                 J.v_off = woff + 3 * m * cap[b];
+                J.g_off = goff;
                 J.cap = cap[b];
                 J.pad_ = 0;
                 woff += 3 * (m + n) * cap[b];
+                goff += 2 * (int64_t)cap[b] * cap[b];
                 maxm = std::max(maxm, m);
                 maxn = std::max(maxn, n);
                 capmax = std::max(capmax, cap[b]);
@@ -134,6 +136,7 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
             double2* d_work = (double2*)hm_dmalloc(tmp, (size_t)woff * 16, st, false);
+            double2* d_gram = (double2*)hm_dmalloc(tmp, (size_t)goff * 16, st, false);
             AcaJob* d_jobs = (AcaJob*)hm_dmalloc(tmp, nj * sizeof(AcaJob), st, false);
             AcaResult* d_res = (AcaResult*)hm_dmalloc(tmp, nj * sizeof(AcaResult), st, false);
             const int64_t fstride = hm_round_up(maxm + maxn, 16);
@@ -142,7 +145,7 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             double2* d_rb = (double2*)hm_dmalloc(tmp, (size_t)nctas * rbs * 16, st, false);
             double2* d_cb = (double2*)hm_dmalloc(tmp, (size_t)nctas * cbs * 16, st, false);
             HM_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nj * sizeof(AcaJob), cudaMemcpyHostToDevice, st));
-            launch_aca(h->gp, h->d_pts_p, h->d_nrm_p, d_jobs, nj, d_work, d_flags, fstride, d_rb,
+            launch_aca(h->gp, h->d_pts_p, h->d_nrm_p, d_jobs, nj, d_work, d_gram, d_flags, fstride, d_rb,
                        d_cb, rbs, cbs, h->eps, d_res, nctas, capmax, d_counter, st);
             std::vector<AcaResult> res(nj);
             HM_CUDA(cudaMemcpyAsync(res.data(), d_res, nj * sizeof(AcaResult), cudaMemcpyDeviceToHost, st));
@@ -151,8 +154,8 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             h->aca_batches++;
             // ---- recompression of the converged jobs ----
             t0 = clk::now();
-            std::vector<int64_t> uo, vo, m3, n3, keep;
-            std::vector<int32_t> kk;
+            std::vector<int64_t> uo, vo, m3, n3, keep, go;
+            std::vector<int32_t> kk, gl;
             for (int64_t j = 0; j < nj; ++j) {
                 if (res[j].status == 2)
                     hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA of a block");
@@ -171,11 +174,13 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                 m3.push_back(3 * jobs[j].m);
                 n3.push_back(3 * jobs[j].n);
                 kk.push_back(res[j].k);
+                go.push_back(jobs[j].g_off);
+                gl.push_back(jobs[j].cap);
             }
             std::vector<int32_t> ranks;
             std::vector<int64_t> soff;
-            void* rb = recompress_core(uo, vo, m3, n3, kk, h->opts.recompress, d_work, h->eps,
-                                       ranks, soff, st);
+            void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h->opts.recompress,
+                                       d_work, h->eps, ranks, soff, st);
             try {
                 // staging for this batch: FP32 U' (3m x r'), V' (3n x r')
                 int64_t tot = 0;
@@ -248,6 +253,7 @@ void hm_opts_default(hm_opts* o) {
     o->aca_max_rank = 0;
     o->workspace_bytes = 0;
     o->verbose = 0;
+    o->weights = nullptr;
 }
 
 const char* hm_status_string(hm_status s) {
@@ -318,6 +324,16 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
         h->clusters = std::move(tr.clusters);
         h->perm = std::move(tr.perm);
         h->depth = tr.depth;
+    }
+    if (o.weights) {
+        std::vector<double> wp(n_c);
+        for (int64_t p = 0; p < n_c; ++p) wp[p] = o.weights[h->perm[p]];
+        if (!finite_all(wp.data(), n_c)) hm_throw(HM_ERR_ARG, "non-finite weights");
+        double* d_w = (double*)hm_dmalloc(h->owner, 8 * n_c, st, false);
+        HM_CUDA(cudaMemcpyAsync(d_w, wp.data(), 8 * n_c, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        h->gp.w = d_w;
+        h->opts.weights = nullptr;  // the caller's array is not kept
     }
     if (kernel == HM_KERNEL_T) {
         std::vector<double> np(3 * n_c);

@@ -19,6 +19,7 @@ struct GreenParams {
     double inv_ks2;       // 1/k_s^2
     double diag;          // value of the i = j block (diag * I3)
     int kernel;           // 0 = U, 1 = T
+    const double* w;      // device column weights in tree order (A = K W_y, Sec. 4), or null
 };
 
 static inline GreenParams make_green_params(int kernel, double rho, double lam, double mu,
@@ -31,6 +32,7 @@ static inline GreenParams make_green_params(int kernel, double rho, double lam, 
     p.inv_ks2 = 1.0 / (p.ks * p.ks);
     p.diag = diag;
     p.kernel = kernel;
+    p.w = nullptr;
     return p;
 }
 
@@ -97,7 +99,16 @@ HM_D void green_tensor(const GreenParams& p, const double* x, const double* y, c
         }
 }
 
-// Block (i, j) of A: diag * I3 when the two points are the same index.
+// Column weight w_j (tree-order index j) applied to an off-diagonal block.
+HM_D void apply_weight(const GreenParams& p, int64_t j, double2 G[9]) {
+    if (!p.w) return;
+    const double wj = p.w[j];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) G[q] = cscale(G[q], wj);
+}
+
+// Block (i, j) of A: diag * I3 when the two points are the same index, else
+// K(x_i, x_j) w_j.
 HM_D void entry_block(const GreenParams& p, const double* pts, const double* nrm, int64_t i,
                       int64_t j, double2 G[9]) {
     if (i == j) {
@@ -106,4 +117,5 @@ HM_D void entry_block(const GreenParams& p, const double* pts, const double* nrm
         return;
     }
     green_tensor(p, pts + 3 * i, pts + 3 * j, nrm ? nrm + 3 * j : nullptr, G);
+    apply_weight(p, j, G);
 }

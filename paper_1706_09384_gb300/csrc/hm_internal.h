@@ -119,6 +119,8 @@ struct AcaJob {              // one admissible block
     int64_t tau_begin, m;    // tree-order point ranges
     int64_t sig_begin, n;
     int64_t u_off, v_off;    // complex128 offsets of U (3m x cap), V (3n x cap) in workspace
+    int64_t g_off;           // offset of G_U = U^H U then G_V = V^H V (cap x cap each) in the
+                             // Gram buffer, or -1 when the caller does not want them
     int32_t cap;             // column capacity (multiple of 3)
     int32_t pad_;
 };
@@ -127,16 +129,21 @@ struct AcaResult {
     int32_t status;          // 0 converged, 1 capacity overflow, 2 non-finite
 };
 void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
-                const AcaJob* d_jobs, int64_t njobs, double2* d_work, unsigned char* d_flags,
+                const AcaJob* d_jobs, int64_t njobs, double2* d_work, double2* d_gram,
+                unsigned char* d_flags,
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
                 int* d_counter, cudaStream_t st);
 int aca_ctas_per_sm(int capmax);
 // Core of the recompression for a batch: ranks r' and the k x r' transforms.
+// g_off[j] >= 0: the job's Gram matrices (ld g_ld[j]) are read from d_gram instead of
+// being recomputed from the factors.
 void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64_t>& v_off,
                       const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
-                      const std::vector<int32_t>& k, int recompress, double2* d_work, double eps,
-                      std::vector<int32_t>& ranks, std::vector<int64_t>& s_off, cudaStream_t st);
+                      const std::vector<int32_t>& k, const std::vector<int64_t>& g_off,
+                      const std::vector<int32_t>& g_ld, const double2* d_gram, int recompress,
+                      double2* d_work, double eps, std::vector<int32_t>& ranks,
+                      std::vector<int64_t>& s_off, cudaStream_t st);
 // Writes U' = U T_U / V' = V T_V (FP32, column-major, ld = factor rows) for
 // row slices: job_of[i], which[i] (0 = U, 1 = V), first row row0[i], rows[i]
 // (<= 192), destination dst[i] (element offset of the slice's first row in

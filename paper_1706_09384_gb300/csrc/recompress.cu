@@ -29,8 +29,11 @@ struct CoreJob {
     int64_t u_off, v_off;   // workspace offsets of U (m3 x k), V (n3 x k)
     int64_t m3, n3;
     int64_t s_off;          // scratch offset: 6 k^2 complex
+    int64_t g_off;          // Gram matrices from the ACA (G_U then G_V, ld g_ld), or -1
+    int32_t g_ld;
     int32_t k;
     int32_t recompress;
+    int32_t pad_;
 };
 
 // G = A^H A for a col-major (rows x k) A, into G (k x k col-major).
@@ -131,8 +134,9 @@ __device__ void chol_equil(double2* G, int k, double* dsc) {
 }
 
 __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, double2* work,
-                                                         double2* scratch, double eps,
-                                                         int32_t* rank_out, int tile_cap) {
+                                                         const double2* gram_in, double2* scratch,
+                                                         double eps, int32_t* rank_out,
+                                                         int tile_cap) {
     extern __shared__ double2 tile[];       // TILE_ROWS x k
     __shared__ double dsc[1024];
     __shared__ int s_conv;
@@ -161,10 +165,19 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
         if (tid == 0) rank_out[blockIdx.x] = k;
         return;
     }
-    const double2* U = work + J.u_off;
-    const double2* V = work + J.v_off;
-    gram(U, J.m3, k, RU, tile);
-    gram(V, J.n3, k, RV, tile);
+    if (gram_in && J.g_off >= 0) {  // G_U, G_V accumulated by the ACA
+        const double2* GU = gram_in + J.g_off;
+        const double2* GV = GU + (int64_t)J.g_ld * J.g_ld;
+        for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
+            const int p = (int)(e % k), c = (int)(e / k);
+            RU[e] = GU[p + (int64_t)c * J.g_ld];
+            RV[e] = GV[p + (int64_t)c * J.g_ld];
+        }
+        __syncthreads();
+    } else {
+        gram(work + J.u_off, J.m3, k, RU, tile);
+        gram(work + J.v_off, J.n3, k, RV, tile);
+    }
     chol_equil(RU, k, dsc);
     chol_equil(RV, k, dsc);
     // W = R_U R_V^H, L = I
@@ -335,9 +348,10 @@ struct RecompBatch {
 
 void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64_t>& v_off,
                       const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
-                      const std::vector<int32_t>& k, int recompress, double2* d_work, double eps,
-                      std::vector<int32_t>& ranks, std::vector<int64_t>& s_off,
-                      cudaStream_t st) {
+                      const std::vector<int32_t>& k, const std::vector<int64_t>& g_off,
+                      const std::vector<int32_t>& g_ld, const double2* d_gram, int recompress,
+                      double2* d_work, double eps, std::vector<int32_t>& ranks,
+                      std::vector<int64_t>& s_off, cudaStream_t st) {
     RecompBatch* B = new RecompBatch();
     const size_t nj = k.size();
     B->jobs.resize(nj);
@@ -351,6 +365,9 @@ void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64
         c.m3 = m3[j];
         c.n3 = n3[j];
         c.k = k[j];
+        c.g_off = g_off[j];
+        c.g_ld = g_ld[j];
+        c.pad_ = 0;
         c.recompress = recompress;
         c.s_off = off;
         s_off[j] = off;
@@ -362,13 +379,15 @@ void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64
     HM_CUDA(cudaMallocAsync((void**)&B->d_scratch, std::max<int64_t>(off, 1) * sizeof(double2), st));
     HM_CUDA(cudaMallocAsync((void**)&B->d_rank, std::max<size_t>(nj, 1) * sizeof(int32_t), st));
     HM_CUDA(cudaMemcpyAsync(B->d_jobs, B->jobs.data(), nj * sizeof(CoreJob), cudaMemcpyHostToDevice, st));
-    const size_t smem = (size_t)TILE_ROWS * kmax * sizeof(double2);
+    bool need_tile = false;
+    for (size_t j = 0; j < nj; ++j) need_tile |= g_off[j] < 0;
+    const size_t smem = need_tile ? (size_t)TILE_ROWS * kmax * sizeof(double2) : 0;
     // static (about 20 KB) + dynamic shared memory may exceed the 48 KB default
     HM_CUDA(cudaFuncSetAttribute(recomp_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     if (nj) {
-        recomp_core_kernel<<<(unsigned)nj, RT, smem, st>>>(B->d_jobs, d_work, B->d_scratch, eps,
-                                                          B->d_rank, kmax);
+        recomp_core_kernel<<<(unsigned)nj, RT, smem, st>>>(B->d_jobs, d_work, d_gram,
+                                                          B->d_scratch, eps, B->d_rank, kmax);
                                                           HM_LAUNCHED();
         HM_CUDA(cudaGetLastError());
     }

@@ -31,7 +31,8 @@ class hm_opts(C.Structure):
     _fields_ = [("storage", C.c_int32), ("aca_fp32", C.c_int32), ("diag_value", C.c_double),
                 ("fp64_switch_ksr", C.c_double), ("recompress", C.c_int32),
                 ("aca_max_rank", C.c_int32), ("workspace_bytes", C.c_int64),
-                ("verbose", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("verbose", C.c_int32), ("pad_", C.c_int32), ("weights", C.c_void_p),
+                ("reserved", C.c_int32 * 4)]
 
 
 class hm_cluster(C.Structure):
@@ -122,10 +123,16 @@ def hm_kernel_launches():
 
 
 def hm_opts_default(**kw):
+    """Default options; weights=<array of n_c floats> is kept alive on the object."""
     o = hm_opts()
     lib().hm_opts_default(C.byref(o))
     for k, v in kw.items():
-        setattr(o, k, v)
+        if k == "weights" and v is not None:
+            w = np.ascontiguousarray(v, dtype=np.float64)
+            o._w = w
+            o.weights = w.ctypes.data
+        else:
+            setattr(o, k, v)
     return o
 
 
