@@ -103,6 +103,60 @@ HM_D void sv13(const double2 M[9], double& s1, double& s3) {
     s3 = sqrt(fmax(l3, 0.0));
 }
 
+// FP32 estimate of (sigma_1, sigma_3) used to shortlist pivot candidates.
+HM_D void sv13f(const double2 Md[9], float& s1, float& s3) {
+    float2 M[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) M[q] = make_float2((float)Md[q].x, (float)Md[q].y);
+    auto mn = [&](int r0, int r1, int c0, int c1) {
+        const float2 a = M[3 * r0 + c0], b = M[3 * r1 + c1], c = M[3 * r0 + c1], d = M[3 * r1 + c0];
+        return make_float2(a.x * b.x - a.y * b.y - (c.x * d.x - c.y * d.y),
+                           a.x * b.y + a.y * b.x - (c.x * d.y + c.y * d.x));
+    };
+    auto ab2 = [](float2 z) { return z.x * z.x + z.y * z.y; };
+    float e1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) e1 += ab2(M[q]);
+    const float2 c0 = mn(1, 2, 1, 2), c1 = mn(1, 2, 0, 2), c2 = mn(1, 2, 0, 1);
+    const float2 det = make_float2(M[0].x * c0.x - M[0].y * c0.y - (M[1].x * c1.x - M[1].y * c1.y) +
+                                       M[2].x * c2.x - M[2].y * c2.y,
+                                   M[0].x * c0.y + M[0].y * c0.x - (M[1].x * c1.y + M[1].y * c1.x) +
+                                       M[2].x * c2.y + M[2].y * c2.x);
+    float e2 = ab2(c0) + ab2(c1) + ab2(c2) + ab2(mn(0, 2, 1, 2)) + ab2(mn(0, 2, 0, 2)) +
+               ab2(mn(0, 2, 0, 1)) + ab2(mn(0, 1, 1, 2)) + ab2(mn(0, 1, 0, 2)) + ab2(mn(0, 1, 0, 1));
+    const float e3 = ab2(det);
+    if (!(e1 > 0.f)) {
+        s1 = e1 == 0.f ? 0.f : e1;  // NaN propagates
+        s3 = s1;
+        return;
+    }
+    const float mm = e1 / 3.f;
+    const float pp = fmaxf(mm * mm - e2 / 3.f, 0.f);
+    float l1, l3;
+    if (pp <= 0.f) {
+        l1 = l3 = mm;
+    } else {
+        const float q = mm * mm * mm - 0.5f * mm * e2 + 0.5f * e3;
+        const float sp = sqrtf(pp);
+        const float th = acosf(fminf(fmaxf(q / (pp * sp), -1.f), 1.f)) / 3.f;
+        l1 = mm + 2.f * sp * cosf(th);
+        l3 = mm + 2.f * sp * cosf(th + 2.0943951f);
+    }
+    if (l3 < 1e-3f * l1) {
+        const float P = e3 / l1;
+        const float sm = (e2 - P) / l1;
+        const float l2 = 0.5f * (sm + sqrtf(fmaxf(sm * sm - 4.f * P, 0.f)));
+        l3 = l2 > 0.f ? P / l2 : 0.f;
+    }
+    s1 = sqrtf(fmaxf(l1, 0.f));
+    s3 = sqrtf(fmaxf(l3, 0.f));
+}
+
+// A candidate whose FP32 sigma_3 is within this fraction of its sigma_1 of the
+// best lower bound is re-evaluated in FP64 (bounds the FP32 error, including
+// the double-root sensitivity of the trigonometric formula).
+constexpr float SHORTLIST_REL = 1e-3f;
+
 struct BlockRed {
     double v[AW];
     int64_t i[AW];
@@ -168,8 +222,8 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
     __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double2* R = rowbuf + blockIdx.x * rb_stride;   // [a][3n], row-major
-    double2* C = colbuf + blockIdx.x * cb_stride;   // [3m][3], row-major
+    double2* R = rowbuf + blockIdx.x * rb_stride;   // [a][3n], row-major, then n float2
+    double2* C = colbuf + blockIdx.x * cb_stride;   // [3m][3], row-major, then m float2
     unsigned char* used = flags + blockIdx.x * flag_stride;
 
     for (;;) {
@@ -194,6 +248,8 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
             s_stop = 0;
         }
         const int64_t steps_max = m < n ? m : n;
+        float2* Rs = reinterpret_cast<float2*>(R + 9 * n);  // FP32 (sigma_1, sigma_3) of row candidates
+        float2* Cs = reinterpret_cast<float2*>(C + 9 * m);  // ... of column candidates
         const double* xr = pts + 3 * J.tau_begin;
         const double* xc = pts + 3 * J.sig_begin;
         const double* nc = nrm ? nrm + 3 * J.sig_begin : nullptr;
@@ -234,12 +290,41 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) R[a * n3 + 3 * j + c] = G[3 * a + c];
-                double s1, s3;
-                sv13(G, s1, s3);
-                s1max = fmax(s1max, s1);
-                if (!ucol[j]) argmax_merge(best, bj, s3, j);
+                float s1f, s3f;
+                sv13f(G, s1f, s3f);
+                Rs[j] = make_float2(s1f, s3f);
+                s1max = fmax(s1max, (double)s1f);
+                if (!ucol[j]) {
+                    const double lo = (double)s3f - SHORTLIST_REL * (double)s1f;
+                    if (lo > best || (bj < 0 && lo == lo)) {
+                        best = lo;
+                        bj = j;
+                    }
+                }
             }
-            block_argmax(best, bj, s1max, red);
+            block_argmax(best, bj, s1max, red);  // best = largest lower bound
+            {
+                // FP64 sigma_3 on the shortlist; exact argmax with ties to the lowest j
+                const double lstar = best;
+                double b64 = -1.0, dummy = 0.0;
+                int64_t j64 = -1;
+                for (int64_t j = tid; j < n; j += AT) {
+                    if (ucol[j]) continue;
+                    const float2 sf = Rs[j];
+                    if (!((double)sf.y + SHORTLIST_REL * (double)sf.x >= lstar)) continue;
+                    double2 G[9];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) G[3 * a + c] = R[a * n3 + 3 * j + c];
+                    double s1, s3;
+                    sv13(G, s1, s3);
+                    argmax_merge(b64, j64, s3, j);
+                }
+                block_argmax(b64, j64, dummy, red);
+                best = b64;
+                bj = j64;
+            }
             if (tid == 0) {
                 s_sref = fmax(s_sref, s1max);
                 s_jhat = bj;
@@ -320,12 +405,36 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
 #pragma unroll
                 for (int q = 0; q < 9; ++q) C[9 * i + q] = G[q];
                 if (!urow[i]) {
-                    double s1, s3;
-                    sv13(G, s1, s3);
-                    argmax_merge(bestr, bi, s3, i);
+                    float s1f, s3f;
+                    sv13f(G, s1f, s3f);
+                    Cs[i] = make_float2(s1f, s3f);
+                    const double lo = (double)s3f - SHORTLIST_REL * (double)s1f;
+                    if (lo > bestr || (bi < 0 && lo == lo)) {
+                        bestr = lo;
+                        bi = i;
+                    }
                 }
             }
             block_argmax(bestr, bi, unused, red);
+            {
+                const double lstar = bestr;
+                double b64 = -1.0;
+                int64_t i64 = -1;
+                for (int64_t i = tid; i < m; i += AT) {
+                    if (urow[i]) continue;
+                    const float2 sf = Cs[i];
+                    if (!((double)sf.y + SHORTLIST_REL * (double)sf.x >= lstar)) continue;
+                    double2 G[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) G[q] = C[9 * i + q];
+                    double s1, s3;
+                    sv13(G, s1, s3);
+                    argmax_merge(b64, i64, s3, i);
+                }
+                block_argmax(b64, i64, unused, red);
+                bestr = b64;
+                bi = i64;
+            }
             if (tid == 0) s_inext = bi;
             // ---- step 5: new factor columns and their Gram matrices ----
             double g[36];
@@ -518,8 +627,8 @@ constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t NA_PTS = 0;                                        // [x; y], 3 doubles per point
 constexpr size_t NA_NRM = NA_PTS + na_align(24 * 2 * NA_MAXP);      // normals at y in the same layout
 constexpr size_t NA_ROW = NA_NRM + na_align(24 * 2 * NA_MAXP);      // 9 n complex128
-constexpr size_t NA_COL = NA_ROW + na_align(16 * 9 * NA_MAXP);      // 9 m complex128
-constexpr size_t NA_FLG = NA_COL + na_align(16 * 9 * NA_MAXP);      // m + n bytes
+constexpr size_t NA_COL = NA_ROW + na_align(16 * (9 * NA_MAXP + NA_MAXP / 2 + 1));  // 9 m complex128 + m float2
+constexpr size_t NA_FLG = NA_COL + na_align(16 * (9 * NA_MAXP + NA_MAXP / 2 + 1));  // m + n bytes
 constexpr size_t NA_JOB = NA_FLG + na_align(2 * NA_MAXP);
 constexpr size_t NA_RES = NA_JOB + na_align(sizeof(AcaJob));
 constexpr size_t NA_CNT = NA_RES + na_align(sizeof(AcaResult));
@@ -589,7 +698,7 @@ extern "C" hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lam
         const GreenParams gp = make_green_params(kernel, rho, lambda, mu, omega, 1.0);
         launch_aca(gp, pts, kernel == HM_KERNEL_T ? nrm : nullptr, d_job, 1, (double2*)uv, nullptr,
                    base + NA_FLG, m + n, (double2*)(base + NA_ROW), (double2*)(base + NA_COL),
-                   9 * n, 9 * m, eps, d_res, 1, cap, (int*)(base + NA_CNT), st);
+                   9 * n + n / 2 + 1, 9 * m + m / 2 + 1, eps, d_res, 1, cap, (int*)(base + NA_CNT), st);
         AcaResult R;
         HM_CUDA(cudaMemcpyAsync(&R, d_res, sizeof(R), cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaStreamSynchronize(st));

@@ -141,7 +141,7 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             AcaResult* d_res = (AcaResult*)hm_dmalloc(tmp, nj * sizeof(AcaResult), st, false);
             const int64_t fstride = hm_round_up(maxm + maxn, 16);
             unsigned char* d_flags = (unsigned char*)hm_dmalloc(tmp, (size_t)nctas * fstride, st, false);
-            const int64_t rbs = 9 * maxn, cbs = 9 * maxm;
+            const int64_t rbs = 9 * maxn + maxn / 2 + 1, cbs = 9 * maxm + maxm / 2 + 1;
             double2* d_rb = (double2*)hm_dmalloc(tmp, (size_t)nctas * rbs * 16, st, false);
             double2* d_cb = (double2*)hm_dmalloc(tmp, (size_t)nctas * cbs * 16, st, false);
             HM_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nj * sizeof(AcaJob), cudaMemcpyHostToDevice, st));

@@ -154,8 +154,6 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
     double2* L = W + (int64_t)k * k;
     double2* TU = L + (int64_t)k * k;
     double2* TV = TU + (int64_t)k * k;
-    double* sv = reinterpret_cast<double*>(L) ;  // reused only after T is built (see below)
-    (void)sv;
     if (!J.recompress) {
         for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
             const int p = (int)(e % k), c = (int)(e / k);
@@ -178,25 +176,36 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
         gram(work + J.u_off, J.m3, k, RU, tile);
         gram(work + J.v_off, J.n3, k, RV, tile);
     }
+    double2* GVc = L;  // keep G_V = V^H V: T_U is formed from it after the SVD
+    for (int64_t e = tid; e < (int64_t)k * k; e += RT) GVc[e] = RV[e];
+    __syncthreads();
     chol_equil(RU, k, dsc);
     chol_equil(RV, k, dsc);
-    // W = R_U R_V^H, L = I
+    // W = R_U R_V^H (the k x k core)
     for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
         const int p = (int)(e % k), c = (int)(e / k);
         double2 acc = make_double2(0.0, 0.0);
         for (int t = max(p, c); t < k; ++t)  // R_U[p][t] nonzero for t >= p, R_V[c][t] for t >= c
             acc = cadd(acc, cmulc(RU[p + (int64_t)t * k], RV[c + (int64_t)t * k]));
         W[e] = acc;
-        L[e] = make_double2(p == c ? 1.0 : 0.0, 0.0);
     }
     __syncthreads();
-    // one-sided Jacobi on the columns of W, round-robin ordering
+    // One-sided Jacobi on the columns of W (round-robin ordering).  Each pair is
+    // handled by a group of G lanes (G grows with k); the group leader computes
+    // the rotation and broadcasts it, so the scarce FP64 pipe is not spent on
+    // redundant square roots and divisions.  Only W's final columns P_j s_j are
+    // needed (see T below), so the rotations are not accumulated.
+    const int G = k <= 32 ? 8 : (k <= 96 ? 16 : 32);
+    const int gl = lane % G;                // lane within the group
+    const int gid = tid / G;                // group index in the CTA
+    const int ngroups = RT / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
     const int np = (k + 1) & ~1;  // players (a dummy when k is odd)
     for (int sweep = 0; sweep < 40; ++sweep) {
         if (tid == 0) s_conv = 1;
         __syncthreads();
         for (int round = 0; round < np - 1; ++round) {
-            for (int pi = wid; pi < np / 2; pi += RW) {
+            for (int pi = gid; pi < np / 2; pi += ngroups) {
                 int a, b;
                 if (pi == 0) {
                     a = np - 1;
@@ -205,14 +214,9 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
                     a = (round + pi) % (np - 1);
                     b = (round - pi + np - 1) % (np - 1);
                 }
-                if (a >= k || b >= k) continue;
-                if (a > b) {
-                    const int t = a;
-                    a = b;
-                    b = t;
-                }
+                if (a >= k || b >= k) continue;  // uniform within the group
                 double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-                for (int r = lane; r < k; r += 32) {
+                for (int r = gl; r < k; r += G) {
                     const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
                     al += cabs2(wa);
                     be += cabs2(wb);
@@ -220,27 +224,42 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
                     gr += z.x;
                     gi += z.y;
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                gr = warp_sum(gr);
-                gi = warp_sum(gi);
-                const double ag = sqrt(gr * gr + gi * gi);
-                if (ag == 0.0 || ag <= 1e-15 * sqrt(al * be)) continue;
-                if (lane == 0) s_conv = 0;
-                const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
-                const double zeta = (be - al) / (2.0 * ag);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(gmask, al, o);
+                    be += __shfl_xor_sync(gmask, be, o);
+                    gr += __shfl_xor_sync(gmask, gr, o);
+                    gi += __shfl_xor_sync(gmask, gi, o);
+                }
+                // rotation parameters on the group leader only
+                double c = 1.0, sn = 0.0, pr = 0.0, pim = 0.0;
+                int rot = 0;
+                if (gl == 0) {
+                    const double ag = sqrt(gr * gr + gi * gi);
+                    if (ag != 0.0 && ag > 1e-15 * sqrt(al * be)) {
+                        rot = 1;
+                        pr = gr / ag;
+                        pim = -gi / ag;  // e^{-i phi}
+                        const double zeta = (be - al) / (2.0 * ag);
+                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = c * t;
+                    }
+                }
+                const int src = lane - gl;
+                rot = __shfl_sync(gmask, rot, src);
+                if (!rot) continue;
+                c = __shfl_sync(gmask, c, src);
+                sn = __shfl_sync(gmask, sn, src);
+                pr = __shfl_sync(gmask, pr, src);
+                pim = __shfl_sync(gmask, pim, src);
+                if (gl == 0) s_conv = 0;
+                const double2 phc = make_double2(pr, pim);
                 // [w_a, w_b] <- [w_a, w_b] [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
-                for (int r = lane; r < k; r += 32) {
+                for (int r = gl; r < k; r += G) {
                     const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
                     const double2 pw = cmul(phc, wb);
-                    W[r + (int64_t)a * k] = csub(cscale(wa, c), cscale(pw, s));
-                    W[r + (int64_t)b * k] = cadd(cscale(wa, s), cscale(pw, c));
-                    const double2 la = L[r + (int64_t)a * k], lb = L[r + (int64_t)b * k];
-                    const double2 pl = cmul(phc, lb);
-                    L[r + (int64_t)a * k] = csub(cscale(la, c), cscale(pl, s));
-                    L[r + (int64_t)b * k] = cadd(cscale(la, s), cscale(pl, c));
+                    W[r + (int64_t)a * k] = csub(cscale(wa, c), cscale(pw, sn));
+                    W[r + (int64_t)b * k] = cadd(cscale(wa, sn), cscale(pw, c));
                 }
             }
             __syncthreads();
@@ -286,18 +305,26 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
     }
     __syncthreads();
     const int r = s_r;
-    // T_U[:, q] = R_V^H L_{o(q)} / sqrt(s), T_V[:, q] = R_U^H W_{o(q)} / s^{3/2}
+    // With M = R_U R_V^H = P S L^H:  M M^H P = P S^2  and  M^H P = L S, so
+    //   T_V = R_U^H P_r S_r^{-1/2}                  (V' = V T_V = Q_V L_r S_r^{1/2})
+    //   T_U = G_V T_V S_r^{-1} = R_V^H L_r S_r^{-1/2} (U' = U T_U = Q_U P_r S_r^{1/2}),
+    // with P_j = W_j / s_j and G_V = V^H V = R_V^H R_V.
     for (int64_t e = tid; e < (int64_t)k * r; e += RT) {
         const int p = (int)(e % k), q = (int)(e / k);
         const int j = s_ord[q];
         const double s = s_sv[j];
-        double2 au = make_double2(0.0, 0.0), av = make_double2(0.0, 0.0);
-        for (int t = 0; t <= p; ++t) {  // (R^H)_{p t} = conj(R_{t p}), nonzero for t <= p
-            cfma_conja(au, RV[t + (int64_t)p * k], L[t + (int64_t)j * k]);
+        double2 av = make_double2(0.0, 0.0);
+        for (int t = 0; t <= p; ++t)  // (R_U^H)_{p t} = conj(R_U[t][p]), nonzero for t <= p
             cfma_conja(av, RU[t + (int64_t)p * k], W[t + (int64_t)j * k]);
-        }
-        TU[p + (int64_t)q * k] = cscale(au, 1.0 / sqrt(s));
         TV[p + (int64_t)q * k] = cscale(av, 1.0 / (s * sqrt(s)));
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)k * r; e += RT) {
+        const int p = (int)(e % k), q = (int)(e / k);
+        const double s = s_sv[s_ord[q]];
+        double2 au = make_double2(0.0, 0.0);
+        for (int t = 0; t < k; ++t) cfma(au, GVc[p + (int64_t)t * k], TV[t + (int64_t)q * k]);
+        TU[p + (int64_t)q * k] = cscale(au, 1.0 / s);
     }
 }
 
