@@ -366,3 +366,21 @@ def test_weighted_gmres_full_size(hm, oracle):
     Ax = oracle.dense_rows_matvec(oracle.problem(rho, lam, mu, om, "U", 1.0, w), pts, None, rows, x)
     # A_H x = b to 1e-6 and A_H is within 3 eps of A in the product
     assert np.linalg.norm(Ax - b[rows]) <= 3 * EPS * np.linalg.norm(b[rows]) + 1e-6 * np.linalg.norm(b)
+
+
+def test_uniform_weights_keep_every_pivot(hm):
+    """Uniform weights c scale every block by c: the tree, partition and every
+    ACA pivot are scale invariant, so the ACA ranks must equal those of the
+    unweighted build block by block (guards the FP32 pivot shortlist against
+    under/overflow of small residuals)."""
+    nc = 16384
+    pts = inputs.fibonacci_sphere(nc)
+    rho, lam, mu, om = inputs.material(16.0)
+    c = 4 * np.pi / nc
+    H1 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 64)
+    Hc = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 64,
+                          opts=hm.hm_opts_default(weights=np.full(nc, c), diag_value=1.0))
+    b1, bc = H1.blocks(), Hc.blocks()
+    assert np.array_equal(b1["tau"], bc["tau"]) and np.array_equal(b1["sigma"], bc["sigma"])
+    same = np.mean(b1["rank_aca"] == bc["rank_aca"])
+    assert same >= 0.995, same
