@@ -6,8 +6,10 @@ complex storage with FP64 Green's tensors, seeded N(0,1) complex RHS.
 
 One step = the whole hot path over the workload: H-matrix build (cluster
 tree, block partition, near-field Green's tensors, batched vector ACA,
-QR/SVD recompression, storage layout) followed by `--matvecs` H-matrix-vector
-products.  `value` is the H-matvec throughput in GB/s (algorithmic bytes of
+QR/SVD recompression, storage layout), `--matvecs` H-matrix-vector products
+and a GMRES(100) solve to 1e-6.  The matrix carries the quadrature weights
+w_j = 4 pi / n_c of the collocation matrix (Sec. 4), which keeps the system
+well conditioned (without them GMRES stalls at this size).  `value` is the H-matvec throughput in GB/s (algorithmic bytes of
 the stored H-matrix plus x and y per product / device time of the products);
 `build_s` is the device-synchronised build time per step.  The stored
 H-matrix (~8.5 GB) is far larger than L2, so no flush is needed between
@@ -207,6 +209,9 @@ def run_reference(args, wl, world, rank):
     print(json.dumps(out), flush=True)
 
 
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate (no measured FP64 peak is available)
+
+
 def run_gpu(args, wl, world, rank, local):
     import torch
     from paper_1706_09384_gb300 import hm, inputs
@@ -215,12 +220,15 @@ def run_gpu(args, wl, world, rank, local):
     st = torch.cuda.current_stream()
     pts = inputs.fibonacci_sphere(wl["nc"])
     rho, lam, mu, om = inputs.material(wl["ks"])
+    # quadrature weights W_y (Sec. 4): area per point of the unit sphere
+    weights = np.full(wl["nc"], 4 * math.pi / wl["nc"])
+    opts = hm.hm_opts_default(weights=weights)
     x = torch.from_numpy(inputs.random_rhs(3 * wl["nc"], seed=rank)).to(dev)
     y = torch.empty_like(x)
 
     def build():
         return hm.HMatrix.build(pts, None, rho, lam, mu, om, wl["kernel"], wl["eps"], wl["eta"],
-                                wl["leaf"])
+                                wl["leaf"], opts=opts)
 
     H = None
     for _ in range(args.warmup):
@@ -229,11 +237,12 @@ def run_gpu(args, wl, world, rank, local):
         H = build()
         for _ in range(args.matvecs):
             H.matvec(x, y)
+        H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
     torch.cuda.synchronize()
     stats = H.stats()
     alg = stats["matvec_alg_bytes"]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    build_ms, mv_ms = [], []
+    build_ms, mv_ms, gm_ms, gm_it, gm_rr, aca_ms, rec_ms, aca_fl = [], [], [], [], [], [], [], []
     launches0 = hm.hm_kernel_launches()
     barrier(world)
     torch.cuda.synchronize()
@@ -251,9 +260,20 @@ def run_gpu(args, wl, world, rank, local):
             for _ in range(args.matvecs):
                 H.matvec(x, y)
             m1.record(st)
+            g0, g1 = ev(), ev()
+            g0.record(st)
+            _, it, rr, gst = H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
+            g1.record(st)
             torch.cuda.synchronize()
             build_ms.append(b0.elapsed_time(b1))
             mv_ms.append(m0.elapsed_time(m1))
+            gm_ms.append(g0.elapsed_time(g1))
+            gm_it.append(it)
+            gm_rr.append(rr)
+            sd = H.stats()
+            aca_ms.append(sd["device_ms"]["aca"])
+            rec_ms.append(sd["device_ms"]["recompress"])
+            aca_fl.append(sd["aca_flops"])
         t_end = ev()
         t_end.record(st)
         torch.cuda.synchronize()
@@ -262,10 +282,26 @@ def run_gpu(args, wl, world, rank, local):
     mv_total = max_over_ranks(world, sum(mv_ms))
     launches = hm.hm_kernel_launches() - launches0
     value = world * alg * args.matvecs * args.steps / (mv_total * 1e-3) / 1e9
-    # per-kernel roofline of the dominant kernel (phase 2), events on the launching stream
+    # per-kernel roofline of the product (phase 2), events on the launching stream
     prof = H.profile_matvec(reps=10)
     peak, peak_kind = measured_peaks()
     ph2 = prof["bytes"]["phase2"] / (prof["ms"]["phase2"] * 1e-3) / 1e9
+    roof_mv = {"bound": "hbm", "kernel": "mv_phase2", "achieved": ph2, "peak": peak,
+               "peak_kind": peak_kind, "unit": "GB/s", "frac": ph2 / peak,
+               "traffic": kernel_traffic("matvec.cu", "mv_phase2"),
+               "alg_bytes_per_launch": prof["bytes"]["phase2"],
+               "ms_per_launch": prof["ms"]["phase2"], "kernels_ms": prof["ms"]}
+    # the dominant kernel of a step: the FP64 vector ACA of the build
+    aca_t = statistics.mean(aca_ms)
+    per_step = {"aca_kernel": aca_t, "recompression": statistics.mean(rec_ms),
+                "h_matvec": statistics.mean(mv_ms), "gmres": statistics.mean(gm_ms)}
+    aca_tf = statistics.mean(aca_fl) / (aca_t * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "aca_kernel", "achieved": aca_tf,
+                "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (no measured FP64 peak)",
+                "unit": "TFLOP/s", "frac": aca_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "alg_flops_per_launch": statistics.mean(aca_fl), "ms_per_step": aca_t,
+                "note": "ACA device time per build (all batches), FP64 flops of the residual "
+                        "rows/columns and Gram updates"}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.empty(3 * wl["nc"], dtype=torch.complex128).pin_memory()
     xh.copy_(x.cpu())
@@ -288,21 +324,22 @@ def run_gpu(args, wl, world, rank, local):
         "data": "synthetic",
         "config": {"workload": args.workload, "n_c": wl["nc"], "kappa_s": wl["ks"],
                    "kernel": wl["kernel"], "leaf": wl["leaf"], "eta": wl["eta"], "eps": wl["eps"],
-                   "storage": "fp32-complex", "green": "fp64",
-                   "matvecs_per_step": args.matvecs, "parallelism": "replicas" if world > 1 else "1gpu",
+                   "weights": "4 pi / n_c (W_y of Sec. 4)", "storage": "fp32-complex",
+                   "green": "fp64", "matvecs_per_step": args.matvecs,
+                   "gmres": "GMRES(100) to 1e-6, FP64 vectors",
+                   "parallelism": "replicas" if world > 1 else "1gpu",
                    "l2": "no flush: %.1f GB streamed per product >> 129 MB L2" % (alg / 1e9)},
         "pct_hbm_peak": 100.0 * value / peak,
         "build_s": statistics.mean(build_ms) / 1e3,
         "matvec_ms": statistics.mean(mv_ms) / args.matvecs,
+        "gmres": {"iters": gm_it[-1], "relres": gm_rr[-1], "ms": statistics.mean(gm_ms)},
+        "step_device_ms": per_step,
         "hmatrix": {k: stats[k] for k in ("blocks", "dense_blocks", "lowrank_blocks", "C_sp",
                                           "rank_aca_max", "rank_max", "tau_H", "stored_bytes",
                                           "matvec_alg_bytes")},
         "build_ms_phases": stats["ms"],
-        "roofline": {"bound": "hbm", "kernel": "mv_phase2", "achieved": ph2, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ph2 / peak,
-                     "traffic": kernel_traffic("matvec.cu", "mv_phase2"),
-                     "alg_bytes_per_launch": prof["bytes"]["phase2"],
-                     "ms_per_launch": prof["ms"]["phase2"], "kernels_ms": prof["ms"]},
+        "roofline": roofline,
+        "roofline_matvec": roof_mv,
         "e2e": {"value": alg / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nb,
                 "d2h_bytes_per_step": nb, "api": "hm_matvec_host (pinned host buffers)"},
         "gpu_launches": launches,

@@ -65,6 +65,27 @@ void free_all(std::vector<DevBuf>& owner) {
     owner.clear();
 }
 
+// A pair of CUDA events bracketing work on one stream.
+struct EvPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    explicit EvPair(cudaStream_t st) {
+        HM_CUDA(cudaEventCreate(&a));
+        HM_CUDA(cudaEventCreate(&b));
+        HM_CUDA(cudaEventRecord(a, st));
+    }
+    double stop(cudaStream_t st) {
+        HM_CUDA(cudaEventRecord(b, st));
+        HM_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        HM_CUDA(cudaEventElapsedTime(&ms, a, b));
+        return ms;
+    }
+    ~EvPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 bool finite_all(const double* p, int64_t n) {
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(p[i])) return false;
@@ -145,8 +166,10 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             double2* d_rb = (double2*)hm_dmalloc(tmp, (size_t)nctas * rbs * 16, st, false);
             double2* d_cb = (double2*)hm_dmalloc(tmp, (size_t)nctas * cbs * 16, st, false);
             HM_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nj * sizeof(AcaJob), cudaMemcpyHostToDevice, st));
+            EvPair ea(st);
             launch_aca(h->gp, h->d_pts_p, h->d_nrm_p, d_jobs, nj, d_work, d_gram, d_flags, fstride, d_rb,
                        d_cb, rbs, cbs, h->eps, d_res, nctas, capmax, d_counter, st);
+            h->ev_aca_ms += ea.stop(st);
             std::vector<AcaResult> res(nj);
             HM_CUDA(cudaMemcpyAsync(res.data(), d_res, nj * sizeof(AcaResult), cudaMemcpyDeviceToHost, st));
             HM_CUDA(cudaStreamSynchronize(st));
@@ -168,6 +191,10 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                     overflow.push_back(b);
                     continue;
                 }
+                {
+                    const double K = res[j].k / 3, mn = (double)(jobs[j].m + jobs[j].n);
+                    h->aca_flops += 8.0 * 18.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
+                }
                 keep.push_back(j);
                 uo.push_back(jobs[j].u_off);
                 vo.push_back(jobs[j].v_off);
@@ -179,6 +206,7 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             }
             std::vector<int32_t> ranks;
             std::vector<int64_t> soff;
+            EvPair er(st);
             void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h->opts.recompress,
                                        d_work, h->eps, ranks, soff, st);
             try {
@@ -208,6 +236,7 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                     }
                 }
                 recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_stage, st);
+                h->ev_recomp_ms += er.stop(st);
                 for (size_t q = 0; q < keep.size(); ++q) {
                     const int64_t b = ids[keep[q]];
                     blk[b].rank_aca = kk[q];
@@ -511,7 +540,9 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"ms\": {\"tree\": " << h->t_tree_ms << ", \"partition\": " << h->t_part_ms
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms
-       << ", \"total\": " << h->t_total_ms << "}}";
+       << ", \"total\": " << h->t_total_ms << "}"
+       << ", \"device_ms\": {\"aca\": " << h->ev_aca_ms << ", \"recompress\": " << h->ev_recomp_ms
+       << "}, \"aca_flops\": " << h->aca_flops << "}";
     const std::string s = os.str();
     if (needed) *needed = s.size() + 1;
     if (!json || cap < s.size() + 1) hm_throw(HM_ERR_ARG, "stats buffer too small");

@@ -198,4 +198,10 @@ struct hm_matrix {
            t_copy_ms = 0, t_total_ms = 0;
     int64_t aca_overflow_reruns = 0;
     int64_t aca_batches = 0;
+    // device time of the ACA and recompression kernels (CUDA events on the build stream)
+    double ev_aca_ms = 0, ev_recomp_ms = 0;
+    // algorithmic FP64 flops of the ACA: per rank-3 step with k columns already
+    // built, 18 k (m + n) complex multiply-adds (residual row and column, and the
+    // Gram / cross terms of the norm update), 8 flops each
+    double aca_flops = 0;
 };
