@@ -198,10 +198,50 @@ HM_D void block_argmax(double& v, int64_t& i, double& w, BlockRed& sh) {
     }
 }
 
+// Warp sum of N values with a halving exchange: at each level a lane keeps the
+// half of its values that its partner does not, so each level costs half the
+// shuffles and adds of the previous one (about 2N instead of 5N for N >= 32).
+// On return every lane holds all N totals.
+template <int N>
+HM_D void warp_sum_many(double (&x)[N]) {
+    const int lane = threadIdx.x & 31;
+    if (N >= 4) {
+        constexpr int H = N / 2;
+        const bool up = (lane & 16) != 0;
+        // level 1: lanes < 16 keep values [0, H), lanes >= 16 keep [H, N)
+        double y[N - H > H ? N - H : H];
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q) {
+            const int mine = up ? H + q : q, theirs = up ? q : H + q;
+            const double send = (theirs < N && (up ? q < H : H + q < N)) ? x[theirs] : 0.0;
+            const double got = __shfl_xor_sync(0xffffffffu, send, 16);
+            y[q] = (mine < N ? x[mine] : 0.0) + got;
+        }
+        // levels 2..5 on the kept half (plain butterflies)
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q)
+            for (int o = 8; o > 0; o >>= 1) y[q] += __shfl_xor_sync(0xffffffffu, y[q], o);
+        // gather the two halves back to every lane
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q) {
+            const double other = __shfl_xor_sync(0xffffffffu, y[q], 16);
+            if (up) {
+                if (q < H) x[q] = other;
+                if (H + q < N) x[H + q] = y[q];
+            } else {
+                if (q < H) x[q] = y[q];
+                if (H + q < N) x[H + q] = other;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) x[q] = warp_sum(x[q]);
+    }
+}
+
 template <int N>
 HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
-#pragma unroll
-    for (int q = 0; q < N; ++q) x[q] = warp_sum(x[q]);
+    warp_sum_many<N>(x);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0)
@@ -469,9 +509,10 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                     for (int q = 0; q < 3; ++q)
 #pragma unroll
                         for (int q2 = 0; q2 < 3; ++q2) {
-                            const double2 z = cconjmul(un[q], un[q2]);
-                            g[2 * (3 * q + q2)] += z.x;
-                            g[2 * (3 * q + q2) + 1] += z.y;
+                            double2 z = make_double2(g[2 * (3 * q + q2)], g[2 * (3 * q + q2) + 1]);
+                            cfma_conja(z, un[q], un[q2]);
+                            g[2 * (3 * q + q2)] = z.x;
+                            g[2 * (3 * q + q2) + 1] = z.y;
                         }
                 }
                 for (int64_t c = tid; c < n3; c += AT) {
@@ -485,9 +526,10 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
                     for (int q = 0; q < 3; ++q)
 #pragma unroll
                         for (int q2 = 0; q2 < 3; ++q2) {
-                            const double2 z = cconjmul(vn[q], vn[q2]);
-                            g[18 + 2 * (3 * q + q2)] += z.x;
-                            g[18 + 2 * (3 * q + q2) + 1] += z.y;
+                            double2 z = make_double2(g[18 + 2 * (3 * q + q2)], g[18 + 2 * (3 * q + q2) + 1]);
+                            cfma_conja(z, vn[q], vn[q2]);
+                            g[18 + 2 * (3 * q + q2)] = z.x;
+                            g[18 + 2 * (3 * q + q2) + 1] = z.y;
                         }
                 }
             }
@@ -525,31 +567,33 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
             // ---- step 6: cross term <B_k, dB> = sum_{p,q} (U_p^H Un_q)(Vn_q^H V_p) ----
             double cre = 0.0, cim = 0.0;
             for (int p = wid; p < k; p += AW) {
-                double x[6] = {0, 0, 0, 0, 0, 0}, y[6] = {0, 0, 0, 0, 0, 0};
+                double2 ax[3] = {}, ay[3] = {};
                 const double2* Up = U + (int64_t)p * m3;
                 const double2* Vp = V + (int64_t)p * n3;
                 for (int64_t r = lane; r < m3; r += 32) {
                     const double2 u = Up[r];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const double2 z = cconjmul(u, U[r + (int64_t)(k + q) * m3]);
-                        x[2 * q] += z.x;
-                        x[2 * q + 1] += z.y;
-                    }
+                    for (int q = 0; q < 3; ++q) cfma_conja(ax[q], u, U[r + (int64_t)(k + q) * m3]);
                 }
                 for (int64_t c = lane; c < n3; c += 32) {
                     const double2 v = Vp[c];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const double2 z = cconjmul(V[c + (int64_t)(k + q) * n3], v);
-                        y[2 * q] += z.x;
-                        y[2 * q + 1] += z.y;
-                    }
+                    for (int q = 0; q < 3; ++q) cfma_conja(ay[q], V[c + (int64_t)(k + q) * n3], v);
                 }
+                double xy[12];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    xy[2 * q] = ax[q].x;
+                    xy[2 * q + 1] = ax[q].y;
+                    xy[6 + 2 * q] = ay[q].x;
+                    xy[6 + 2 * q + 1] = ay[q].y;
+                }
+                warp_sum_many<12>(xy);
+                double x[6], y[6];
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    x[q] = warp_sum(x[q]);
-                    y[q] = warp_sum(y[q]);
+                    x[q] = xy[q];
+                    y[q] = xy[6 + q];
                 }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
