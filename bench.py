@@ -222,7 +222,9 @@ def run_gpu(args, wl, world, rank, local):
     rho, lam, mu, om = inputs.material(wl["ks"])
     # quadrature weights W_y (Sec. 4): area per point of the unit sphere
     weights = np.full(wl["nc"], 4 * math.pi / wl["nc"])
-    opts = hm.hm_opts_default(weights=weights)
+    form = args.form
+    opts = hm.hm_opts_default(weights=weights,
+                              storage=hm.HM_STORE_BF16 if form == "mixed" else hm.HM_STORE_FP32)
     x = torch.from_numpy(inputs.random_rhs(3 * wl["nc"], seed=rank)).to(dev)
     y = torch.empty_like(x)
 
@@ -320,11 +322,14 @@ def run_gpu(args, wl, world, rank, local):
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16c" if form == "mixed" else "c64", "data": "synthetic",
         "config": {"workload": args.workload, "n_c": wl["nc"], "kappa_s": wl["ks"],
                    "kernel": wl["kernel"], "leaf": wl["leaf"], "eta": wl["eta"], "eps": wl["eps"],
-                   "weights": "4 pi / n_c (W_y of Sec. 4)", "storage": "fp32-complex",
+                   "weights": "4 pi / n_c (W_y of Sec. 4)",
+                   "storage": ("bf16-complex + fp32 scale per chunk (products); fp32 for "
+                               "refinement residuals") if form == "mixed" else "fp32-complex",
+                   "form": form,
                    "green": "fp64", "matvecs_per_step": args.matvecs,
                    "gmres": "GMRES(100) to 1e-6, FP64 vectors",
                    "parallelism": "replicas" if world > 1 else "1gpu",
@@ -345,9 +350,42 @@ def run_gpu(args, wl, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if form == "mixed" and not args.no_compare:
+        # the plain form on the same workload, once, outside the timed steps
+        H.free()
+        H = None
+        popts = hm.hm_opts_default(weights=weights)
+        b0, b1 = ev(), ev()
+        b0.record(st)
+        Hp = hm.HMatrix.build(pts, None, rho, lam, mu, om, wl["kernel"], wl["eps"], wl["eta"],
+                              wl["leaf"], opts=popts)
+        b1.record(st)
+        for _ in range(3):
+            Hp.matvec(x, y)
+        m0, m1 = ev(), ev()
+        m0.record(st)
+        for _ in range(args.matvecs):
+            Hp.matvec(x, y)
+        m1.record(st)
+        g0, g1 = ev(), ev()
+        g0.record(st)
+        _, pit, prr, _ = Hp.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
+        g1.record(st)
+        torch.cuda.synchronize()
+        palg = Hp.stats()["matvec_alg_bytes"]
+        pmv = m0.elapsed_time(m1) / args.matvecs
+        out["plain"] = {"value": palg / (pmv * 1e-3) / 1e9, "unit": "GB/s",
+                        "pct_hbm_peak": 100.0 * palg / (pmv * 1e-3) / 1e9 / peak,
+                        "matvec_ms": pmv, "build_s": b0.elapsed_time(b1) / 1e3,
+                        "gmres": {"iters": pit, "relres": prr, "ms": g0.elapsed_time(g1)},
+                        "stored_bytes": Hp.stats()["stored_bytes"]}
+        out["mixed_vs_plain"] = {"matvec_speedup": pmv / out["matvec_ms"],
+                                 "gmres_speedup_at_1e-6": g0.elapsed_time(g1) / out["gmres"]["ms"]}
+        Hp.free()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
-    H.free()
+    if H is not None:
+        H.free()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -361,6 +399,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="sphere65536_ks16_U", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="mixed", choices=["mixed", "plain"],
+                    help="mixed: BF16 storage (per-chunk scale) for the products, FP32-stored "
+                         "operator for the refinement residuals; plain: FP32 storage")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the untimed plain-form comparison run")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -323,7 +323,8 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
     hm_opts o;
     hm_opts_default(&o);
     if (opts) o = *opts;
-    if (o.storage != HM_STORE_FP32) hm_throw(HM_ERR_UNSUPPORTED, "only FP32 storage is built");
+    if (o.storage != HM_STORE_FP32 && o.storage != HM_STORE_BF16)
+        hm_throw(HM_ERR_ARG, "unknown storage type");
     if (!std::isfinite(o.diag_value)) hm_throw(HM_ERR_ARG, "non-finite diag_value");
     cudaStream_t st = (cudaStream_t)stream;
     const auto t_all = clk::now();
@@ -394,6 +395,7 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
         h->t_near_ms = ms_since(tn);
         copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
         HM_CUDA(cudaStreamSynchronize(st));
+        if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
         h->t_copy_ms = ms_since(t0) - h->t_near_ms;
     } catch (...) {
         cudaStreamSynchronize(st);
@@ -683,6 +685,7 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
         h->mv = matvec_dev_create(h->plan, o.storage, h->owner, st);
         copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
         HM_CUDA(cudaStreamSynchronize(st));
+        if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(staging);

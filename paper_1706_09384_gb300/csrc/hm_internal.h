@@ -79,6 +79,10 @@ struct MatvecDev;  // device side of the plan (matvec.cu)
 MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
                              cudaStream_t st);
 void matvec_dev_destroy(MatvecDev* m);
+// Adds the BF16 copy of the arena (per-chunk FP32 scale); the fast product then
+// reads it, the accurate product keeps reading the FP32 arena.
+void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
+                      cudaStream_t st);
 void* matvec_arena(MatvecDev* m);           // float2* (fp32) or bf16 pairs
 // y_p (tree order, float2) = A_H x_p (tree order, float2)
 void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);

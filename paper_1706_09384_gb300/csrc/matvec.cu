@@ -14,6 +14,8 @@
 // Work items are slices of a leaf's chunk list of bounded byte size, so the
 // grid load-balances; each CTA keeps partial sums per warp in registers and
 // reduces them once.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 
@@ -26,6 +28,18 @@ struct DevChunk {
     int32_t ncols;
     int32_t kind;
     int32_t rows;
+};
+// Chunk of the BF16 arena: complex entries as two bf16 (4 bytes), scaled by a
+// per-chunk FP32 factor; rows padded to a multiple of 4 (16-byte columns).
+struct DevChunk16 {
+    int64_t data;   // element offset in arena16
+    int64_t vec;
+    int32_t ld;
+    int32_t ncols;
+    int32_t kind;
+    int32_t rows;
+    float scale;
+    int32_t pad_;
 };
 struct WorkItem {
     int64_t dof;      // first tree-order DOF of the leaf
@@ -52,6 +66,13 @@ struct MatvecDev {
     int64_t lr_elems = 0;
     int64_t alg_v = 0;      // stored entries (rows x cols, no padding) of V chunks
     int64_t alg_du = 0;     // ... of dense and U chunks
+    // BF16 copy of the arena (HM_STORE_BF16): the fast product reads it; the
+    // FP32 arena stays for the accurate product
+    uint32_t* arena16 = nullptr;
+    int64_t arena16_elems = 0;
+    DevChunk16* chunks16 = nullptr;
+    int64_t nchunks = 0;
+    int64_t nchunks_v = 0, nchunks_du = 0;  // scale counts for the byte model
 };
 
 namespace {
@@ -225,6 +246,187 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
         if (r < it.rows) atomic_add_c(yp + it.dof + r, s.x, s.y);
         if (r + 1 < it.rows) atomic_add_c(yp + it.dof + r + 1, s.z, s.w);
     }
+}
+
+// ---- BF16 storage ----
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (192 rows -> 48 quads -> 2)
+
+__global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
+                                                         const int32_t* order,
+                                                         const DevChunk16* chunks,
+                                                         const uint32_t* __restrict__ arena,
+                                                         const float2* __restrict__ xp, float2* t) {
+    const WorkItem it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 xv[QUADS_PER_LANE][4];
+#pragma unroll
+    for (int q = 0; q < QUADS_PER_LANE; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * (lane + 32 * q) + e;
+            xv[q][e] = r < it.rows ? xp[it.dof + r] : make_float2(0.f, 0.f);
+        }
+    const int nquad = (it.rows + 3) >> 2;
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk16 ch = chunks[order[ci]];
+        const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const uint4* col = base + (int64_t)c * (ch.ld >> 2);
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint4 w = __ldcs(col + qq);
+                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 a = bf2_to_f2(ww[e]);
+                        re = fmaf(a.x, xv[q][e].x, fmaf(a.y, xv[q][e].y, re));   // conj(a) x
+                        im = fmaf(a.x, xv[q][e].y, fmaf(-a.y, xv[q][e].x, im));
+                    }
+                }
+            }
+            re = warp_sumf(re);
+            im = warp_sumf(im);
+            if (lane == 0) atomicAdd(t + ch.vec + c, make_float2(re * ch.scale, im * ch.scale));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
+                                                         const int32_t* order,
+                                                         const DevChunk16* chunks,
+                                                         const uint32_t* __restrict__ arena,
+                                                         const float2* __restrict__ xp,
+                                                         const float2* __restrict__ t,
+                                                         float2* yp) {
+    __shared__ float2 part[MV_WARPS][MAX_LD];
+    const WorkItem it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nquad = (it.rows + 3) >> 2;
+    float2 acc[QUADS_PER_LANE][4];
+#pragma unroll
+    for (int q = 0; q < QUADS_PER_LANE; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[q][e] = make_float2(0.f, 0.f);
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk16 ch = chunks[order[ci]];
+        const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
+        const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
+        const int ldq = ch.ld >> 2;
+        int c = warp;
+        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
+            float2 v0 = __ldg(v + c), v1 = __ldg(v + c + MV_WARPS);
+            v0.x *= ch.scale; v0.y *= ch.scale;
+            v1.x *= ch.scale; v1.y *= ch.scale;
+            uint4 w0[QUADS_PER_LANE], w1[QUADS_PER_LANE];
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    w0[q] = __ldcs(base + (int64_t)c * ldq + qq);
+                    w1[q] = __ldcs(base + (int64_t)(c + MV_WARPS) * ldq + qq);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint32_t a0[4] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w};
+                    const uint32_t a1[4] = {w1[q].x, w1[q].y, w1[q].z, w1[q].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 a = bf2_to_f2(a0[e]), b = bf2_to_f2(a1[e]);
+                        float2& s2 = acc[q][e];
+                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
+                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
+                        s2.x = fmaf(b.x, v1.x, fmaf(-b.y, v1.y, s2.x));
+                        s2.y = fmaf(b.x, v1.y, fmaf(b.y, v1.x, s2.y));
+                    }
+                }
+            }
+        }
+        for (; c < ch.ncols; c += MV_WARPS) {
+            float2 v0 = __ldg(v + c);
+            v0.x *= ch.scale; v0.y *= ch.scale;
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint4 w = __ldcs(base + (int64_t)c * ldq + qq);
+                    const uint32_t a0[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 a = bf2_to_f2(a0[e]);
+                        float2& s2 = acc[q][e];
+                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
+                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QUADS_PER_LANE; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * (lane + 32 * q) + e;
+            if (r < MAX_LD) part[warp][r] = acc[q][e];
+        }
+    __syncthreads();
+    for (int r = threadIdx.x; r < it.rows; r += MV_THREADS) {
+        float2 s2 = part[0][r];
+        for (int w = 1; w < MV_WARPS; ++w) {
+            s2.x += part[w][r].x;
+            s2.y += part[w][r].y;
+        }
+        atomicAdd(yp + it.dof + r, s2);
+    }
+}
+
+// FP32 chunk -> BF16 chunk with a per-chunk scale (largest component magnitude).
+struct ConvJob {
+    int64_t src;   // FP32 arena offset
+    int32_t ld32;
+    int32_t chunk;  // index into chunks16
+};
+__global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const float2* arena32,
+                                                      uint32_t* arena16, DevChunk16* chunks16) {
+    __shared__ float red[8];
+    const ConvJob J = jobs[blockIdx.x];
+    DevChunk16* ch = chunks16 + J.chunk;
+    const int rows = ch->rows, ncols = ch->ncols, ld16 = ch->ld;
+    const int64_t n = (int64_t)rows * ncols;
+    float mx = 0.f;
+    for (int64_t e = threadIdx.x; e < n; e += 256) {
+        const int r = (int)(e % rows), c = (int)(e / rows);
+        const float2 v = arena32[J.src + r + (int64_t)c * J.ld32];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+    const float scale = mx > 0.f ? mx : 1.f;
+    const float inv = 1.f / scale;
+    const int64_t n16 = (int64_t)ld16 * ncols;
+    for (int64_t e = threadIdx.x; e < n16; e += 256) {
+        const int r = (int)(e % ld16), c = (int)(e / ld16);
+        uint32_t w = 0;
+        if (r < rows) {
+            const float2 v = arena32[J.src + r + (int64_t)c * J.ld32];
+            const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v.x * inv));
+            const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v.y * inv));
+            w = lo | (hi << 16);
+        }
+        arena16[ch->data + e] = w;
+    }
+    if (threadIdx.x == 0) ch->scale = scale;
 }
 
 __global__ void gather_x64_kernel(const int64_t* perm, const double2* x, double2* xp, int64_t nc) {
@@ -461,14 +663,64 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
     return m;
 }
 
+void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
+                      cudaStream_t st) {
+    std::vector<DevChunk16> c16(plan.chunks.size());
+    std::vector<ConvJob> jobs;
+    int64_t off = 0;
+    // same order as the FP32 arena: row streams first, then V by column leaf
+    std::vector<int32_t> seq(plan.row_items);
+    seq.insert(seq.end(), plan.col_items.begin(), plan.col_items.end());
+    for (int32_t id : seq) {
+        const Chunk& c = plan.chunks[id];
+        DevChunk16& d = c16[id];
+        d.data = off;
+        d.vec = c.vec;
+        d.ld = (int32_t)hm_round_up(c.rows, 4);
+        d.ncols = c.ncols;
+        d.kind = c.kind;
+        d.rows = c.rows;
+        d.scale = 1.f;
+        d.pad_ = 0;
+        off += (int64_t)d.ld * c.ncols;
+        if (c.ncols > 0) jobs.push_back({c.data, c.ld, id});
+        if (c.ncols > 0) (c.kind == 2 ? m->nchunks_v : m->nchunks_du)++;
+    }
+    m->arena16_elems = off;
+    m->nchunks = (int64_t)c16.size();
+    m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4, st, true);
+    m->chunks16 = (DevChunk16*)hm_dmalloc(owner, std::max<size_t>(c16.size(), 1) * sizeof(DevChunk16),
+                                          st, false);
+    HM_CUDA(cudaMemcpyAsync(m->chunks16, c16.data(), c16.size() * sizeof(DevChunk16),
+                            cudaMemcpyHostToDevice, st));
+    if (!jobs.empty()) {
+        ConvJob* d = nullptr;
+        HM_CUDA(cudaMallocAsync((void**)&d, jobs.size() * sizeof(ConvJob), st));
+        HM_CUDA(cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(ConvJob), cudaMemcpyHostToDevice, st));
+        to_bf16_kernel<<<(unsigned)jobs.size(), 256, 0, st>>>(d, m->arena, m->arena16, m->chunks16);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+        HM_CUDA(cudaFreeAsync(d, st));
+    }
+    HM_CUDA(cudaStreamSynchronize(st));
+    m->storage = HM_STORE_BF16;
+}
+
 void matvec_dev_destroy(MatvecDev* m) { delete m; }
 void* matvec_arena(MatvecDev* m) { return m->arena; }
-int64_t matvec_stored_bytes(const MatvecDev* m) { return m->arena_elems * 8; }
+int64_t matvec_stored_bytes(const MatvecDev* m) {
+    return m->arena16 ? m->arena16_elems * 4 : m->arena_elems * 8;
+}
 int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
-    if (m->n1) {
+    if (m->n1 && m->arena16) {
+        mv16_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks16,
+                                                           m->arena16, xp, m->t);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    } else if (m->n1) {
         mv_phase1<false><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
                                                                 m->arena, xp, m->t);
         HM_CUDA(cudaGetLastError());
@@ -478,7 +730,12 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
-    if (m->n2) {
+    if (m->n2 && m->arena16) {
+        mv16_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks16,
+                                                           m->arena16, xp, m->t, yp);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    } else if (m->n2) {
         mv_phase2<false><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
                                                                 m->arena, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
@@ -518,10 +775,16 @@ void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, doub
 }
 
 void matvec_alg_bytes(const MatvecDev* m, int64_t ndof, int64_t out[3]) {
-    const int64_t e = 8;  // complex64
-    out[0] = e * (m->alg_v + ndof + m->t_elems);
-    out[1] = e * (m->alg_du + ndof + m->t_elems + ndof);
-    out[2] = e * (m->alg_v + m->alg_du) + 2 * 16 * ndof;  // complex128 x in, y out
+    const int64_t v = 8;  // complex64 vectors (x, t, y in tree order)
+    if (m->arena16) {     // 4 bytes per stored entry + one FP32 scale per chunk
+        out[0] = 4 * m->alg_v + 4 * m->nchunks_v + v * (ndof + m->t_elems);
+        out[1] = 4 * m->alg_du + 4 * m->nchunks_du + v * (ndof + m->t_elems + ndof);
+        out[2] = 4 * (m->alg_v + m->alg_du) + 4 * (m->nchunks_v + m->nchunks_du) + 2 * 16 * ndof;
+        return;
+    }
+    out[0] = v * (m->alg_v + ndof + m->t_elems);
+    out[1] = v * (m->alg_du + ndof + m->t_elems + ndof);
+    out[2] = v * (m->alg_v + m->alg_du) + 2 * 16 * ndof;  // complex128 x in, y out
 }
 
 void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_t nc,

@@ -384,3 +384,34 @@ def test_uniform_weights_keep_every_pivot(hm):
     assert np.array_equal(b1["tau"], bc["tau"]) and np.array_equal(b1["sigma"], bc["sigma"])
     same = np.mean(b1["rank_aca"] == bc["rank_aca"])
     assert same >= 0.995, same
+
+
+def test_bf16_storage_product_and_refinement(hm, oracle):
+    """Mixed form: dense blocks and factors stored as BF16 with one FP32 scale
+    per chunk.  The fast product then carries the BF16 rounding (unit roundoff
+    2^-9 of each chunk's largest entry, so a few 1e-3 relative), and GMRES with
+    BF16 inner products and accurate restart residuals (iterative refinement)
+    still reaches 1e-6 and the plain form's solution."""
+    nc = 4000
+    pts = inputs.fibonacci_sphere(nc)
+    rho, lam, mu, om = inputs.material(8.0)
+    w = np.full(nc, 4 * np.pi / nc)
+    H32 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 32,
+                           opts=hm.hm_opts_default(weights=w))
+    H16 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 32,
+                           opts=hm.hm_opts_default(weights=w, storage=hm.HM_STORE_BF16))
+    x = inputs.random_rhs(3 * nc, seed=2)
+    y32 = H32.matvec(cuda(x)).cpu().numpy()
+    y16 = H16.matvec(cuda(x)).cpu().numpy()
+    err = np.linalg.norm(y16 - y32) / np.linalg.norm(y32)
+    assert err <= 2.0 ** -8, err
+    assert H16.stats()["stored_bytes"] < 0.55 * H32.stats()["stored_bytes"]
+    b = cuda(inputs.random_rhs(3 * nc, seed=3))
+    x32, it32, rr32, st32 = H32.gmres(b, restart=50, tol=1e-6, maxit=500)
+    x16, it16, rr16, st16 = H16.gmres(b, restart=50, tol=1e-6, maxit=500)
+    assert st16 == 0 and rr16 <= 1e-6
+    x32, x16 = x32.cpu().numpy(), x16.cpu().numpy()
+    assert np.linalg.norm(x16 - x32) <= 1e-5 * np.linalg.norm(x32)
+    # the residual of the mixed solution, with the plain operator
+    r = b.cpu().numpy() - H32.matvec(cuda(x16)).cpu().numpy()
+    assert np.linalg.norm(r) <= 2e-6 * np.linalg.norm(b.cpu().numpy())
