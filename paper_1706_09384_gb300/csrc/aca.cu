@@ -198,6 +198,47 @@ HM_D void block_argmax(double& v, int64_t& i, double& w, BlockRed& sh) {
     }
 }
 
+// Warp sum of N values with a halving exchange: at each level a lane keeps the
+// half of its values that its partner does not, so each level costs half the
+// shuffles and adds of the previous one (about 2N instead of 5N for N >= 32).
+// On return every lane holds all N totals.
+template <int N>
+HM_D void warp_sum_many(double (&x)[N]) {
+    const int lane = threadIdx.x & 31;
+    if (N >= 4) {
+        constexpr int H = N / 2;
+        const bool up = (lane & 16) != 0;
+        // level 1: lanes < 16 keep values [0, H), lanes >= 16 keep [H, N)
+        double y[N - H > H ? N - H : H];
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q) {
+            const int mine = up ? H + q : q, theirs = up ? q : H + q;
+            const double send = (theirs < N && (up ? q < H : H + q < N)) ? x[theirs] : 0.0;
+            const double got = __shfl_xor_sync(0xffffffffu, send, 16);
+            y[q] = (mine < N ? x[mine] : 0.0) + got;
+        }
+        // levels 2..5 on the kept half (plain butterflies)
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q)
+            for (int o = 8; o > 0; o >>= 1) y[q] += __shfl_xor_sync(0xffffffffu, y[q], o);
+        // gather the two halves back to every lane
+#pragma unroll
+        for (int q = 0; q < (N - H > H ? N - H : H); ++q) {
+            const double other = __shfl_xor_sync(0xffffffffu, y[q], 16);
+            if (up) {
+                if (q < H) x[q] = other;
+                if (H + q < N) x[H + q] = y[q];
+            } else {
+                if (q < H) x[q] = y[q];
+                if (H + q < N) x[H + q] = other;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) x[q] = warp_sum(x[q]);
+    }
+}
+
 template <int N>
 HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
     warp_sum_many<N>(x);

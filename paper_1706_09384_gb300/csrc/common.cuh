@@ -70,40 +70,6 @@ HM_D float warp_sumf(float v) {
     return v;
 }
 
-// Warp sum of N values with a halving first exchange: lanes 0-15 keep the
-// first half of the values and lanes 16-31 the second, so the remaining four
-// butterfly levels run on N/2 values; every lane returns all N totals.
-template <int N, typename T>
-HM_D void warp_sum_many(T (&x)[N]) {
-    if constexpr (N >= 4 && N % 2 == 0) {
-        constexpr int H = N / 2;
-        const int lane = threadIdx.x & 31;
-        const bool up = (lane & 16) != 0;
-        T y[H];
-#pragma unroll
-        for (int q = 0; q < H; ++q) {
-            const T send = up ? x[q] : x[H + q];
-            const T got = __shfl_xor_sync(0xffffffffu, send, 16);
-            y[q] = (up ? x[H + q] : x[q]) + got;
-        }
-#pragma unroll
-        for (int q = 0; q < H; ++q)
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) y[q] += __shfl_xor_sync(0xffffffffu, y[q], o);
-#pragma unroll
-        for (int q = 0; q < H; ++q) {
-            const T other = __shfl_xor_sync(0xffffffffu, y[q], 16);
-            x[q] = up ? other : y[q];
-            x[H + q] = up ? y[q] : other;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < N; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
-    }
-}
-
 // argmax over (value, index): larger value wins, ties go to the lower index.
 HM_D void argmax_merge(double& v, int64_t& i, double v2, int64_t i2) {
     if (v2 > v || (v2 == v && i2 >= 0 && (i < 0 || i2 < i))) {

@@ -138,51 +138,28 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
         xv[q] = v;
     }
     const int npair = (it.ld) >> 1;
-    constexpr int CB = 4;  // columns in flight per warp
     for (int ci = it.first; ci < it.last; ++ci) {
         const DevChunk ch = chunks[order[ci]];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
-        for (int c0 = warp; c0 < ch.ncols; c0 += CB * MV_WARPS) {
-            R acc[2 * CB];
-            float4 v4[CB][PAIRS_PER_LANE];
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const float4* col = base + (int64_t)c * (ch.ld >> 1);
+            R re = 0, im = 0;
 #pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                const int c = c0 + b * MV_WARPS;
-                const float4* col = base + (int64_t)c * (ch.ld >> 1);
-#pragma unroll
-                for (int q = 0; q < PAIRS_PER_LANE; ++q) {
-                    const int pr = lane + 32 * q;
-                    v4[b][q] = (c < ch.ncols && pr < npair) ? ldg_stream(col + pr)
-                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                R re = 0, im = 0;
-#pragma unroll
-                for (int q = 0; q < PAIRS_PER_LANE; ++q) {
-                    const R vx = v4[b][q].x, vy = v4[b][q].y, vz = v4[b][q].z, vw = v4[b][q].w;
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    const float4 v4 = ldg_stream(col + pr);
+                    const R vx = v4.x, vy = v4.y, vz = v4.z, vw = v4.w;
                     // conj(v) * x
                     re = fma(vx, xv[q].x, fma(vy, xv[q].y, re));
                     im = fma(vx, xv[q].y, fma(-vy, xv[q].x, im));
                     re = fma(vz, xv[q].z, fma(vw, xv[q].w, re));
                     im = fma(vz, xv[q].w, fma(-vw, xv[q].z, im));
                 }
-                acc[2 * b] = re;
-                acc[2 * b + 1] = im;
             }
-            warp_sum_many<2 * CB>(acc);
-            if (lane < CB) {
-                const int c = c0 + lane * MV_WARPS;
-                R re = acc[0], im = acc[1];
-#pragma unroll
-                for (int b = 1; b < CB; ++b)
-                    if (lane == b) {
-                        re = acc[2 * b];
-                        im = acc[2 * b + 1];
-                    }
-                if (c < ch.ncols) atomic_add_c(t + ch.vec + c, re, im);
-            }
+            re = red_sum(re);
+            im = red_sum(im);
+            if (lane == 0) atomic_add_c(t + ch.vec + c, re, im);
         }
     }
 }
@@ -293,29 +270,18 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
             xv[q][e] = r < it.rows ? xp[it.dof + r] : make_float2(0.f, 0.f);
         }
     const int nquad = (it.rows + 3) >> 2;
-    constexpr int CB = 4;  // columns in flight per warp
     for (int ci = it.first; ci < it.last; ++ci) {
         const DevChunk16 ch = chunks[order[ci]];
         const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
-        for (int c0 = warp; c0 < ch.ncols; c0 += CB * MV_WARPS) {
-            uint4 w4[CB][QUADS_PER_LANE];
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const uint4* col = base + (int64_t)c * (ch.ld >> 2);
+            float re = 0.f, im = 0.f;
 #pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                const int c = c0 + b * MV_WARPS;
-                const uint4* col = base + (int64_t)c * (ch.ld >> 2);
-#pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const int qq = lane + 32 * q;
-                    w4[b][q] = (c < ch.ncols && qq < nquad) ? __ldcs(col + qq) : make_uint4(0, 0, 0, 0);
-                }
-            }
-            float acc[2 * CB];
-#pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                float re = 0.f, im = 0.f;
-#pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const uint32_t ww[4] = {w4[b][q].x, w4[b][q].y, w4[b][q].z, w4[b][q].w};
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint4 w = __ldcs(col + qq);
+                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const float2 a = bf2_to_f2(ww[e]);
@@ -323,21 +289,10 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
                         im = fmaf(a.x, xv[q][e].y, fmaf(-a.y, xv[q][e].x, im));
                     }
                 }
-                acc[2 * b] = re;
-                acc[2 * b + 1] = im;
             }
-            warp_sum_many<2 * CB>(acc);
-            if (lane < CB) {
-                const int c = c0 + lane * MV_WARPS;
-                float re = acc[0], im = acc[1];
-#pragma unroll
-                for (int b = 1; b < CB; ++b)
-                    if (lane == b) {
-                        re = acc[2 * b];
-                        im = acc[2 * b + 1];
-                    }
-                if (c < ch.ncols) atomicAdd(t + ch.vec + c, make_float2(re * ch.scale, im * ch.scale));
-            }
+            re = warp_sumf(re);
+            im = warp_sumf(im);
+            if (lane == 0) atomicAdd(t + ch.vec + c, make_float2(re * ch.scale, im * ch.scale));
         }
     }
 }
@@ -363,36 +318,56 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
         const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
         const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
         const int ldq = ch.ld >> 2;
-        constexpr int CB = 4;
-        for (int c0 = warp; c0 < ch.ncols; c0 += CB * MV_WARPS) {
-            float2 vb[CB];
-            uint4 w4[CB][QUADS_PER_LANE];
+        int c = warp;
+        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
+            float2 v0 = __ldg(v + c), v1 = __ldg(v + c + MV_WARPS);
+            v0.x *= ch.scale; v0.y *= ch.scale;
+            v1.x *= ch.scale; v1.y *= ch.scale;
+            uint4 w0[QUADS_PER_LANE], w1[QUADS_PER_LANE];
 #pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                const int c = c0 + b * MV_WARPS;
-                const bool ok = c < ch.ncols;
-                float2 vv = ok ? __ldg(v + c) : make_float2(0.f, 0.f);
-                vb[b] = make_float2(vv.x * ch.scale, vv.y * ch.scale);
-#pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const int qq = lane + 32 * q;
-                    w4[b][q] = (ok && qq < nquad) ? __ldcs(base + (int64_t)c * ldq + qq)
-                                                  : make_uint4(0, 0, 0, 0);
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    w0[q] = __ldcs(base + (int64_t)c * ldq + qq);
+                    w1[q] = __ldcs(base + (int64_t)(c + MV_WARPS) * ldq + qq);
                 }
             }
 #pragma unroll
-            for (int b = 0; b < CB; ++b)
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint32_t a0[4] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w};
+                    const uint32_t a1[4] = {w1[q].x, w1[q].y, w1[q].z, w1[q].w};
 #pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const uint32_t a0[4] = {w4[b][q].x, w4[b][q].y, w4[b][q].z, w4[b][q].w};
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 a = bf2_to_f2(a0[e]), b = bf2_to_f2(a1[e]);
+                        float2& s2 = acc[q][e];
+                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
+                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
+                        s2.x = fmaf(b.x, v1.x, fmaf(-b.y, v1.y, s2.x));
+                        s2.y = fmaf(b.x, v1.y, fmaf(b.y, v1.x, s2.y));
+                    }
+                }
+            }
+        }
+        for (; c < ch.ncols; c += MV_WARPS) {
+            float2 v0 = __ldg(v + c);
+            v0.x *= ch.scale; v0.y *= ch.scale;
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                if (qq < nquad) {
+                    const uint4 w = __ldcs(base + (int64_t)c * ldq + qq);
+                    const uint32_t a0[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const float2 a = bf2_to_f2(a0[e]);
                         float2& s2 = acc[q][e];
-                        s2.x = fmaf(a.x, vb[b].x, fmaf(-a.y, vb[b].y, s2.x));
-                        s2.y = fmaf(a.x, vb[b].y, fmaf(a.y, vb[b].x, s2.y));
+                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
+                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
                     }
                 }
+            }
         }
     }
 #pragma unroll
