@@ -58,6 +58,11 @@ struct MatvecDev {
     WorkItem* items2 = nullptr;   // phase 2 (dense + U)
     int32_t* order1 = nullptr;    // chunk ids referenced by items, phase 1
     int32_t* order2 = nullptr;
+    DevChunk* hdr1 = nullptr;     // chunk headers in item order (phase 1, phase 2)
+    DevChunk* hdr2 = nullptr;
+    DevChunk16* hdr16_1 = nullptr;
+    DevChunk16* hdr16_2 = nullptr;
+    int64_t n_o1 = 0, n_o2 = 0;
     int64_t n1 = 0, n2 = 0;
     float2* t = nullptr;
     double2* t64 = nullptr;       // accurate product: t in FP64
@@ -81,6 +86,7 @@ constexpr int MV_THREADS = 256;
 constexpr int MV_WARPS = MV_THREADS / 32;
 constexpr int MAX_LD = 192;               // 3 * 64 rows: leaves up to 64 points
 constexpr int PAIRS_PER_LANE = MAX_LD / 64;  // row pairs per lane (3)
+constexpr int MAX_ITEM_CHUNKS = 64;          // chunk headers staged in shared memory per item
 
 __device__ __forceinline__ float4 ldg_stream(const float4* p) { return __ldcs(p); }
 
@@ -112,14 +118,16 @@ __device__ __forceinline__ void atomic_add_c(double2* p, double re, double im) {
 // Phase 1: for every V chunk of the item's column leaf, t[vec + c] += V[:, c]^H x_leaf.
 template <bool ACC>
 __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
-                                                       const int32_t* order,
-                                                       const DevChunk* chunks,
+                                                       const DevChunk* hdr,
                                                        const float2* __restrict__ arena,
                                                        const typename MvT<ACC>::C2* __restrict__ xp,
                                                        typename MvT<ACC>::C2* t) {
     using R = typename MvT<ACC>::R;
     using C4 = typename MvT<ACC>::C4;
     const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this lane's x values (row pairs lane, lane+32, lane+64)
     C4 xv[PAIRS_PER_LANE];
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
     }
     const int npair = (it.ld) >> 1;
     for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk ch = chunks[order[ci]];
+        const DevChunk ch = sh_hdr[ci - it.first];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
         for (int c = warp; c < ch.ncols; c += MV_WARPS) {
             const float4* col = base + (int64_t)c * (ch.ld >> 1);
@@ -167,8 +175,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase1(const WorkItem* items,
 // Phase 2: y_leaf += sum over chunks of chunk * v, v = x (dense) or t (U).
 template <bool ACC>
 __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
-                                                       const int32_t* order,
-                                                       const DevChunk* chunks,
+                                                       const DevChunk* hdr,
                                                        const float2* __restrict__ arena,
                                                        const typename MvT<ACC>::C2* __restrict__ xp,
                                                        const typename MvT<ACC>::C2* __restrict__ t,
@@ -178,6 +185,9 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
     using C4 = typename MvT<ACC>::C4;
     __shared__ C4 part[MV_WARPS][MAX_LD / 2];
     const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int npair = it.ld >> 1;
     C4 acc[PAIRS_PER_LANE];
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
         s.w = fma(az, v.y, fma(aw, v.x, s.w));
     };
     for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk ch = chunks[order[ci]];
+        const DevChunk ch = sh_hdr[ci - it.first];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
         const C2* v = (ch.kind == 0 ? xp : t) + ch.vec;
         int c = warp;
@@ -255,11 +265,13 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
 constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (192 rows -> 48 quads -> 2)
 
 __global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
-                                                         const int32_t* order,
-                                                         const DevChunk16* chunks,
+                                                         const DevChunk16* hdr,
                                                          const uint32_t* __restrict__ arena,
                                                          const float2* __restrict__ xp, float2* t) {
     const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk16 sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float2 xv[QUADS_PER_LANE][4];
 #pragma unroll
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
         }
     const int nquad = (it.rows + 3) >> 2;
     for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk16 ch = chunks[order[ci]];
+        const DevChunk16 ch = sh_hdr[ci - it.first];
         const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
         for (int c = warp; c < ch.ncols; c += MV_WARPS) {
             const uint4* col = base + (int64_t)c * (ch.ld >> 2);
@@ -298,14 +310,16 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
 }
 
 __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
-                                                         const int32_t* order,
-                                                         const DevChunk16* chunks,
+                                                         const DevChunk16* hdr,
                                                          const uint32_t* __restrict__ arena,
                                                          const float2* __restrict__ xp,
                                                          const float2* __restrict__ t,
                                                          float2* yp) {
     __shared__ float2 part[MV_WARPS][MAX_LD];
     const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk16 sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nquad = (it.rows + 3) >> 2;
     float2 acc[QUADS_PER_LANE][4];
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[q][e] = make_float2(0.f, 0.f);
     for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk16 ch = chunks[order[ci]];
+        const DevChunk16 ch = sh_hdr[ci - it.first];
         const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
         const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
         const int ldq = ch.ld >> 2;
@@ -386,6 +400,12 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
         }
         atomicAdd(yp + it.dof + r, s2);
     }
+}
+
+__global__ void gather_hdr16_kernel(const DevChunk16* src, const int32_t* order, int64_t n,
+                                    DevChunk16* dst) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) dst[q] = src[order[q]];
 }
 
 // FP32 chunk -> BF16 chunk with a per-chunk scale (largest component magnitude).
@@ -488,7 +508,7 @@ void make_items(const std::vector<int64_t>& begin, const std::vector<int32_t>& l
             if (c.ncols == 0) continue;
             order.push_back(list[q]);
             acc += (int64_t)c.ld * c.ncols * 8;
-            if (acc >= target) {
+            if (acc >= target || (int32_t)order.size() - first >= MAX_ITEM_CHUNKS) {
                 items.push_back({plan.leaf_dof_begin[l], plan.leaf_rows[l],
                                  (int32_t)hm_round_up(plan.leaf_rows[l], 2), first,
                                  (int32_t)order.size()});
@@ -656,6 +676,17 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
     HM_CUDA(cudaMemcpyAsync(m->items2, it2.data(), it2.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(m->order1, o1.data(), o1.size() * 4, cudaMemcpyHostToDevice, st));
     HM_CUDA(cudaMemcpyAsync(m->order2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<DevChunk> h1(o1.size()), h2(o2.size());
+        for (size_t q = 0; q < o1.size(); ++q) h1[q] = dc[o1[q]];
+        for (size_t q = 0; q < o2.size(); ++q) h2[q] = dc[o2[q]];
+        m->hdr1 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h1.size(), 1) * sizeof(DevChunk), st, false);
+        m->hdr2 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h2.size(), 1) * sizeof(DevChunk), st, false);
+        HM_CUDA(cudaMemcpyAsync(m->hdr1, h1.data(), h1.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(m->hdr2, h2.data(), h2.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
+        m->n_o1 = (int64_t)o1.size();
+        m->n_o2 = (int64_t)o2.size();
+    }
     m->t_elems = plan.t_elems;
     m->t = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(float2), st, true);
     m->t64 = (double2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(double2), st, true);
@@ -702,6 +733,18 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
         HM_LAUNCHED();
         HM_CUDA(cudaFreeAsync(d, st));
     }
+    m->hdr16_1 = (DevChunk16*)hm_dmalloc(owner, std::max<int64_t>(m->n_o1, 1) * sizeof(DevChunk16), st, false);
+    m->hdr16_2 = (DevChunk16*)hm_dmalloc(owner, std::max<int64_t>(m->n_o2, 1) * sizeof(DevChunk16), st, false);
+    if (m->n_o1) {
+        gather_hdr16_kernel<<<(unsigned)hm_cdiv(m->n_o1, 256), 256, 0, st>>>(m->chunks16, m->order1, m->n_o1, m->hdr16_1);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    if (m->n_o2) {
+        gather_hdr16_kernel<<<(unsigned)hm_cdiv(m->n_o2, 256), 256, 0, st>>>(m->chunks16, m->order2, m->n_o2, m->hdr16_2);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
     HM_CUDA(cudaStreamSynchronize(st));
     m->storage = HM_STORE_BF16;
 }
@@ -716,12 +759,12 @@ int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
     if (m->n1 && m->arena16) {
-        mv16_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks16,
+        mv16_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr16_1,
                                                            m->arena16, xp, m->t);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     } else if (m->n1) {
-        mv_phase1<false><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
+        mv_phase1<false><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr1,
                                                                 m->arena, xp, m->t);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
@@ -731,12 +774,12 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
     if (m->n2 && m->arena16) {
-        mv16_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks16,
+        mv16_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr16_2,
                                                            m->arena16, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     } else if (m->n2) {
-        mv_phase2<false><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
+        mv_phase2<false><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr2,
                                                                 m->arena, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
@@ -758,13 +801,13 @@ void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, doub
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t64, 0, m->t_elems * sizeof(double2), st));
     HM_CUDA(cudaMemsetAsync(yp64, 0, n * sizeof(double2), st));
     if (m->n1) {
-        mv_phase1<true><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->order1, m->chunks,
+        mv_phase1<true><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr1,
                                                                m->arena, xp64, m->t64);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
     if (m->n2) {
-        mv_phase2<true><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->order2, m->chunks,
+        mv_phase2<true><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr2,
                                                                m->arena, xp64, m->t64, yp64);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
