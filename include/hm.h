@@ -77,7 +77,13 @@ typedef struct {
     const double* weights;    /* HOST, n_c column weights w_j (NULL = 1): block (i, j), i != j,
                                  becomes K(x_i, x_j) w_j - the quadrature weights W_y of the
                                  collocation matrix A = U W_y V_y (Sec. 4) */
-    int32_t reserved[4];
+    const float* rank_model;  /* HOST, HM_RANK_MODEL_PARAMS floats of a trained rank predictor
+                                 (see hm_rank_model_train), or NULL: when given, each admissible
+                                 block's ACA workspace is sized from the predicted rank and
+                                 blocks of similar predicted rank are batched together; blocks
+                                 whose rank exceeds the prediction are re-run, so the H-matrix
+                                 is the same either way */
+    int32_t reserved[2];
 } hm_opts;
 
 void hm_opts_default(hm_opts* opts);
@@ -212,6 +218,41 @@ hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lambda, double
                                double omega, const double* x, int64_t m, const double* y,
                                const double* ny, int64_t n, double eps, int32_t cap, void* uv,
                                int32_t* rank, void* stream);
+
+/* ---- learned rank predictor (no counterpart in the paper) ----
+ * An MLP 6 -> 64 -> 64 -> 1 (exact GELU, FP32) predicts log(1 + rank/3) of an
+ * admissible block from f = (k_s D, k_p D, dist/D, log2|tau|, log2|sigma|,
+ * log10 eps), D = max of the two box diameters, dist = dist_box (Sec. 6.1); the
+ * rank grows with k_s D (Sec. 5.3, Sec. 8).  Parameter block layout (floats):
+ * [0,6) feature mean, [6,12) feature deviation, [12] target mean, [13] target
+ * deviation, W1 (64x6 row-major), b1 (64), W2 (64x64), b2 (64), w3 (64), b3. */
+#define HM_RANK_MODEL_PARAMS 4687
+
+/* Training samples of a built handle: for each admissible block (block order)
+ * the 6 features into feats (HOST, n x 6) and log(1 + rank_aca/3) into targets
+ * (HOST, n).  *n receives the count; pass feats = targets = NULL to query it. */
+hm_status hm_rank_samples(hm_handle h, float* feats, float* targets, int64_t* n);
+
+/* Trains the model on the GPU by mini-batch Adam on the mean squared error of
+ * the standardised target.  feats (n x 6), targets (n): DEVICE.  params: DEVICE,
+ * HM_RANK_MODEL_PARAMS floats holding the initial weights; the standardisation
+ * constants are computed from the data and the weights updated in place.
+ * Mini-batches of `batch` samples are drawn by a counter-based hash of (seed,
+ * step, position).  loss: HOST array of `steps` batch losses, or NULL.
+ * Errors: HM_ERR_ARG (n < 2, steps < 0, batch < 1, lr <= 0), HM_ERR_CUDA. */
+hm_status hm_rank_model_train(const float* feats, const float* targets, int64_t n,
+                              int32_t steps, int32_t batch, float lr, uint64_t seed,
+                              float* params, float* loss, void* stream);
+
+/* Predictions (standardised target units) for n raw feature rows; all DEVICE. */
+hm_status hm_rank_model_predict(const float* params, const float* feats, int64_t n, float* out,
+                                void* stream);
+
+/* Full-batch loss and gradient of the trainable parameters (the
+ * HM_RANK_MODEL_PARAMS - 14 floats after the standardisation constants);
+ * params, feats, targets, grad: DEVICE; loss: HOST or NULL. */
+hm_status hm_rank_model_grad(const float* params, const float* feats, const float* targets,
+                             int64_t n, float* grad, float* loss, void* stream);
 
 /* ---- measurement ---- */
 

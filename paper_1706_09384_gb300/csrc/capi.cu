@@ -117,6 +117,40 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
         const int64_t full = 3 * std::min(pts_of(blk[b].tau), pts_of(blk[b].sigma));
         cap[b] = (int)std::min<int64_t>(full, cap0);
     }
+    if (h->opts.rank_model && !adm.empty()) {
+        // learned capacities: predicted rank-3 steps with a safety margin; the
+        // ACA still decides the rank and overflowing blocks are re-run
+        const int64_t na = (int64_t)adm.size();
+        std::vector<float> feats(6 * na), pred(na);
+        for (int64_t q = 0; q < na; ++q)
+            rank_features(cl[blk[adm[q]].tau], cl[blk[adm[q]].sigma], h->gp.ks, h->gp.kp, h->eps,
+                          &feats[6 * q]);
+        std::vector<DevBuf> tmp;
+        float* dP = (float*)hm_dmalloc(tmp, HM_RANK_MODEL_PARAMS * 4, st, false);
+        float* dF = (float*)hm_dmalloc(tmp, feats.size() * 4, st, false);
+        float* dO = (float*)hm_dmalloc(tmp, na * 4, st, false);
+        HM_CUDA(cudaMemcpyAsync(dP, h->opts.rank_model, HM_RANK_MODEL_PARAMS * 4, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(dF, feats.data(), feats.size() * 4, cudaMemcpyHostToDevice, st));
+        rank_model_predict_dev(dP, dF, na, dO, st);
+        HM_CUDA(cudaMemcpyAsync(pred.data(), dO, na * 4, cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        free_all(tmp);
+        const float tm = h->opts.rank_model[12], ts = h->opts.rank_model[13];
+        for (int64_t q = 0; q < na; ++q) {
+            const int64_t b = adm[q];
+            const double steps = std::exp((double)pred[q] * ts + tm) - 1.0;
+            const int64_t full = 3 * std::min(pts_of(blk[b].tau), pts_of(blk[b].sigma));
+            int64_t c = 3 * (int64_t)std::ceil(1.25 * std::max(steps, 0.0) + 2.0);
+            if (!std::isfinite(steps)) c = cap0;
+            cap[b] = (int)std::max<int64_t>(3, std::min<int64_t>({c, full, 768}));
+        }
+        // bin blocks of similar predicted rank into the same batches
+        std::stable_sort(adm.begin(), adm.end(), [&](int64_t a, int64_t b) {
+            if (cap[a] != cap[b]) return cap[a] > cap[b];
+            return pts_of(blk[a].tau) + pts_of(blk[a].sigma) > pts_of(blk[b].tau) + pts_of(blk[b].sigma);
+        });
+        h->used_rank_model = 1;
+    }
     int* d_counter = (int*)hm_dmalloc(staging, sizeof(int), st, true);
     std::vector<int64_t> todo = adm;
     while (!todo.empty()) {
@@ -153,6 +187,8 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                 ++pos;
             }
             const int64_t nj = (int64_t)jobs.size();
+            h->aca_workspace_peak = std::max<int64_t>(h->aca_workspace_peak, (woff + goff) * 16);
+            h->aca_workspace_total += (woff + goff) * 16;
             const int nctas = (int)std::min<int64_t>(nj, (int64_t)nsm * aca_ctas_per_sm(capmax));
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
@@ -259,6 +295,20 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
     }
 }
 
+double box_diam(const hm_cluster& c) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) s += (c.hi[a] - c.lo[a]) * (c.hi[a] - c.lo[a]);
+    return std::sqrt(s);
+}
+double box_dist(const hm_cluster& x, const hm_cluster& y) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double g = std::max({0.0, x.lo[a] - y.hi[a], y.lo[a] - x.hi[a]});
+        s += g * g;
+    }
+    return std::sqrt(s);
+}
+
 hm_status validate_common(const hm_matrix* h) {
     if (!h) {
         hm_set_error("null handle");
@@ -268,6 +318,17 @@ hm_status validate_common(const hm_matrix* h) {
 }
 
 }  // namespace
+
+void rank_features(const hm_cluster& t, const hm_cluster& s, double ks, double kp, double eps,
+                   float f[6]) {
+    const double D = std::max({box_diam(t), box_diam(s), 1e-30});
+    f[0] = (float)(ks * D);
+    f[1] = (float)(kp * D);
+    f[2] = (float)(box_dist(t, s) / D);
+    f[3] = (float)std::log2((double)(t.end - t.begin));
+    f[4] = (float)std::log2((double)(s.end - s.begin));
+    f[5] = (float)std::log10(eps);
+}
 
 extern "C" {
 
@@ -283,6 +344,7 @@ void hm_opts_default(hm_opts* o) {
     o->workspace_bytes = 0;
     o->verbose = 0;
     o->weights = nullptr;
+    o->rank_model = nullptr;
 }
 
 const char* hm_status_string(hm_status s) {
@@ -445,9 +507,8 @@ hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* str
     if (xb < yb + bytes && yb < xb + bytes) hm_throw(HM_ERR_ARG, "x and y overlap");
     cudaStream_t st = (cudaStream_t)stream;
     for (int32_t c = 0; c < nrhs; ++c) {
-        launch_gather_x(h->d_perm, (const double2*)x + c * n, h->d_xp, h->nc, st);
-        matvec_tree_order(h->mv, h->d_xp, h->d_yp, n, st);
-        launch_scatter_y(h->d_perm, h->d_yp, (double2*)y + c * n, h->nc, st);
+        matvec_graph(h->mv, h->d_perm, (const double2*)x + c * n, h->d_xp, h->d_yp,
+                     (double2*)y + c * n, h->nc, st);
     }
     HM_API_END
 }
@@ -539,6 +600,9 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"dense_bytes\": " << matvec_dense_bytes(h->mv)
        << ", \"aca_batches\": " << h->aca_batches
        << ", \"aca_overflow_reruns\": " << h->aca_overflow_reruns
+       << ", \"aca_workspace_peak_bytes\": " << h->aca_workspace_peak
+       << ", \"aca_workspace_total_bytes\": " << h->aca_workspace_total
+       << ", \"rank_model\": " << h->used_rank_model
        << ", \"ms\": {\"tree\": " << h->t_tree_ms << ", \"partition\": " << h->t_part_ms
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms
@@ -549,6 +613,21 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
     if (needed) *needed = s.size() + 1;
     if (!json || cap < s.size() + 1) hm_throw(HM_ERR_ARG, "stats buffer too small");
     std::memcpy(json, s.c_str(), s.size() + 1);
+    HM_API_END
+}
+
+hm_status hm_rank_samples(hm_handle h, float* feats, float* targets, int64_t* n) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    int64_t q = 0;
+    for (const hm_block& b : h->blocks) {
+        if (!b.admissible) continue;
+        if (feats) rank_features(h->clusters[b.tau], h->clusters[b.sigma], h->gp.ks, h->gp.kp, h->eps,
+                                 feats + 6 * q);
+        if (targets) targets[q] = (float)std::log1p(b.rank_aca / 3.0);
+        ++q;
+    }
+    if (n) *n = q;
     HM_API_END
 }
 

@@ -150,9 +150,7 @@ __global__ void init_g_kernel(double* g, const double* nrm2, int m) {
 
 // y = A_H x for FP64 vectors (tree-order work vectors of the handle).
 static void apply_fp64(hm_matrix* h, const double2* x, double2* y, cudaStream_t st) {
-    launch_gather_x(h->d_perm, x, h->d_xp, h->nc, st);
-    matvec_tree_order(h->mv, h->d_xp, h->d_yp, 3 * h->nc, st);
-    launch_scatter_y(h->d_perm, h->d_yp, y, h->nc, st);
+    matvec_graph(h->mv, h->d_perm, x, h->d_xp, h->d_yp, y, h->nc, st);
 }
 
 GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int m, double tol, int maxit,

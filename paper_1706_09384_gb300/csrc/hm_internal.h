@@ -84,6 +84,13 @@ void matvec_dev_destroy(MatvecDev* m);
 void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
                       cudaStream_t st);
 void* matvec_arena(MatvecDev* m);           // float2* (fp32) or bf16 pairs
+// y (original order, complex128) = A_H x through the product's CUDA graph;
+// xp, yp: tree-order complex64 scratch owned by the caller, fixed per handle.
+void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp, float2* yp,
+                  double2* y, int64_t nc, cudaStream_t st);
+// Error code left by the streamed product kernels (0 = none; 1 = a wait on a
+// copy gave up); reading it synchronises st and clears it.
+int matvec_take_error(MatvecDev* m, cudaStream_t st);
 // y_p (tree order, float2) = A_H x_p (tree order, float2)
 void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);
 // Copies staged column-major blocks / factors (FP32, one pointer per block:
@@ -159,6 +166,13 @@ void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
                       const double2* d_work, float2* d_out, cudaStream_t st);
 void recompress_release(void* batch, cudaStream_t st);
 
+// ---------------- rank predictor (rankmlp.cu) ----------------
+void rank_model_predict_dev(const float* dP, const float* dF, int64_t n, float* dOut,
+                            cudaStream_t st);
+// features of an admissible block (f of the rank predictor)
+void rank_features(const hm_cluster& t, const hm_cluster& s, double ks, double kp, double eps,
+                   float f[6]);
+
 // ---------------- GMRES (gmres.cu) ----------------
 struct GmresResult {
     int iters;
@@ -208,4 +222,7 @@ struct hm_matrix {
     // built, 18 k (m + n) complex multiply-adds (residual row and column, and the
     // Gram / cross terms of the norm update), 8 flops each
     double aca_flops = 0;
+    int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
+    int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
+    int used_rank_model = 0;
 };

@@ -32,7 +32,7 @@ class hm_opts(C.Structure):
                 ("fp64_switch_ksr", C.c_double), ("recompress", C.c_int32),
                 ("aca_max_rank", C.c_int32), ("workspace_bytes", C.c_int64),
                 ("verbose", C.c_int32), ("pad_", C.c_int32), ("weights", C.c_void_p),
-                ("reserved", C.c_int32 * 4)]
+                ("rank_model", C.c_void_p), ("reserved", C.c_int32 * 2)]
 
 
 class hm_cluster(C.Structure):
@@ -70,6 +70,10 @@ SIGNATURES = {
     "hm_import": (_I32, [_I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P]),
     "hm_aca_block_noalloc": (_I32, [_I32, _D, _D, _D, _D, _P, _I64, _P, _P, _I64, _D, _I32, _P,
                                     _P, _P]),
+    "hm_rank_samples": (_I32, [_P, _P, _P, _P]),
+    "hm_rank_model_train": (_I32, [_P, _P, _I64, _I32, _I32, C.c_float, C.c_uint64, _P, _P, _P]),
+    "hm_rank_model_predict": (_I32, [_P, _P, _I64, _P, _P]),
+    "hm_rank_model_grad": (_I32, [_P, _P, _P, _I64, _P, _P, _P]),
     "hm_profile_matvec": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_kernel_launches": (_I64, []),
     "hm_free": (None, [_P]),
@@ -131,6 +135,11 @@ def hm_opts_default(**kw):
             w = np.ascontiguousarray(v, dtype=np.float64)
             o._w = w
             o.weights = w.ctypes.data
+        elif k == "rank_model" and v is not None:
+            m = np.ascontiguousarray(v, dtype=np.float32)
+            assert m.size == HM_RANK_MODEL_PARAMS
+            o._m = m
+            o.rank_model = m.ctypes.data
         else:
             setattr(o, k, v)
     return o
@@ -149,6 +158,7 @@ def hm_green_eval(kernel, rho, lam, mu, omega, x, y, ny=None, diag_value=1.0, st
 
 
 HM_NOALLOC_MAX_POINTS = 8192
+HM_RANK_MODEL_PARAMS = 4687
 
 
 def hm_aca_block_noalloc(kernel, rho, lam, mu, omega, x, y, ny, eps, cap, uv, stream=None):
@@ -261,6 +271,15 @@ class HMatrix:
         buf = C.create_string_buffer(need.value)
         _check(lib().hm_stats(self.h, buf, need.value, None), "hm_stats")
         return json.loads(buf.value.decode())
+
+    def rank_samples(self):
+        """(features n x 6, targets n) of the admissible blocks (float32, host)."""
+        n = C.c_int64(0)
+        _check(lib().hm_rank_samples(self.h, None, None, C.byref(n)), "hm_rank_samples")
+        f = np.zeros((n.value, 6), np.float32)
+        t = np.zeros(n.value, np.float32)
+        _check(lib().hm_rank_samples(self.h, _np_ptr(f), _np_ptr(t), C.byref(n)), "hm_rank_samples")
+        return f, t
 
     def sizes(self):
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
