@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "hm_internal.h"
@@ -78,6 +79,18 @@ struct MatvecDev {
     DevChunk16* chunks16 = nullptr;
     int64_t nchunks = 0;
     int64_t nchunks_v = 0, nchunks_du = 0;  // scale counts for the byte model
+    // CUDA graph of one whole product (gather, both phases, scatter), captured
+    // on first use; x and y are re-pointed in the instantiated graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t g_gather = nullptr, g_scatter = nullptr;
+    const double2* g_x = nullptr;
+    double2* g_y = nullptr;
+    long long g_kernels = 0;
+    int* d_err = nullptr;             // error code written by the streamed kernels
+    std::vector<WorkItem> h_items1, h_items2;
+    std::vector<int32_t> h_order1, h_order2;
+    bool legacy16 = false;
 };
 
 namespace {
@@ -402,6 +415,250 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
     }
 }
 
+// ---- BF16 storage, streamed through shared memory ----
+// Every work item is one contiguous byte range of the BF16 arena: the chunks of
+// one leaf, all with the same leading dimension ld16, stored back to back, so
+// the item is a column-major (ld16 x ncol) matrix.  One producer warp moves it
+// into a ring of shared-memory stages with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier per stage); eight consumer
+// warps compute from the stages and release them through a second mbarrier
+// per stage.  The bytes in flight per SM are set by the ring, not by the
+// registers of the consumers.  Each wait gives up after S16_WAIT_NS, records
+// an error code and lets the CTA finish; the producer always waits for its own
+// copies before it exits.
+constexpr int S16_CONSUMERS = 8;
+constexpr int S16_THREADS = 32 * (S16_CONSUMERS + 1);
+constexpr int S16_NSTAGE = 4;
+constexpr int S16_STAGE_BYTES = 16384;
+constexpr int MAX_ITEM_COLS = 2048;                   // columns of one item (per-column table in smem)
+constexpr unsigned long long S16_WAIT_NS = 1000000000ull;
+constexpr int MV_ERR_TIMEOUT = 1;
+
+struct S16Smem {
+    alignas(128) unsigned char stage[S16_NSTAGE][S16_STAGE_BYTES];
+    float2 w[MAX_ITEM_COLS];                   // phase 2: scale * v_j; phase 1: (t index bits, scale)
+    float2 part[S16_CONSUMERS][MAX_LD];        // phase 2: per-warp row sums
+    DevChunk16 hdr[MAX_ITEM_CHUNKS];
+    int32_t colstart[MAX_ITEM_CHUNKS + 1];
+    int32_t ncol;
+    alignas(8) uint64_t full[S16_NSTAGE];
+    uint64_t empty[S16_NSTAGE];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for the completion of the phase with the given parity
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    if (mbar_try_wait(b, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(b, parity))
+        if (global_ns() - t0 > S16_WAIT_NS) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * S16_CONSUMERS) : "memory");
+}
+
+// PHASE 1: t[vec_j] += scale_j * V_j^H x_leaf;  PHASE 2: y_leaf += sum_j M_j scale_j v_j.
+template <int PHASE>
+__global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* items,
+                                                           const DevChunk16* hdr,
+                                                           const uint32_t* __restrict__ arena,
+                                                           const float2* __restrict__ xp,
+                                                           float2* t, float2* yp, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S16Smem& S = *reinterpret_cast<S16Smem*>(smem_raw);
+    const WorkItem it = items[blockIdx.x];
+    const int nch = it.last - it.first;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < nch; i += S16_THREADS) S.hdr[i] = hdr[it.first + i];
+    if (tid == 0) {
+        for (int s = 0; s < S16_NSTAGE; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], S16_CONSUMERS);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == 0) {  // column offsets of the chunks (exclusive scan, two chunks per lane)
+        const int a0 = 2 * lane < nch ? S.hdr[2 * lane].ncols : 0;
+        const int a1 = 2 * lane + 1 < nch ? S.hdr[2 * lane + 1].ncols : 0;
+        int inc = a0 + a1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int exc = inc - a0 - a1;
+        S.colstart[2 * lane] = exc;
+        S.colstart[2 * lane + 1] = exc + a0;
+        if (lane == 31) {
+            S.colstart[MAX_ITEM_CHUNKS] = inc;
+            S.ncol = inc;
+        }
+    }
+    __syncthreads();
+    const int ncol = S.ncol;
+    const int ld16 = S.hdr[0].ld;
+    const int colb = ld16 * 4;
+    const int sc = S16_STAGE_BYTES / colb;  // columns per stage
+    const int nst = (ncol + sc - 1) / sc;
+    if (warp == S16_CONSUMERS) {  // ---- producer ----
+        if (lane == 0) {
+            const unsigned char* src0 = reinterpret_cast<const unsigned char*>(arena + S.hdr[0].data);
+            int issued = 0;
+            for (int k = 0; k < nst; ++k) {
+                const int s = k % S16_NSTAGE;
+                if (k >= S16_NSTAGE && !mbar_wait(&S.empty[s], ((k / S16_NSTAGE) - 1) & 1)) {
+                    atomicExch(err, MV_ERR_TIMEOUT);
+                    break;
+                }
+                const int g = min(sc, ncol - k * sc);
+                const uint32_t bytes = (uint32_t)(g * colb);
+                mbar_arrive_expect_tx(&S.full[s], bytes);
+                bulk_g2s(S.stage[s], src0 + (size_t)k * sc * colb, bytes, &S.full[s]);
+                ++issued;
+            }
+            for (int k = max(0, issued - S16_NSTAGE); k < issued; ++k)  // own copies landed
+                if (!mbar_wait(&S.full[k % S16_NSTAGE], (k / S16_NSTAGE) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+        }
+        return;
+    }
+    // ---- consumers: per-column table ----
+    for (int ci = warp; ci < nch; ci += S16_CONSUMERS) {
+        const DevChunk16 ch = S.hdr[ci];
+        const int j0 = S.colstart[ci];
+        for (int c = lane; c < ch.ncols; c += 32) {
+            if (PHASE == 2) {
+                const float2 v = __ldg((ch.kind == 0 ? xp : t) + ch.vec + c);
+                S.w[j0 + c] = make_float2(v.x * ch.scale, v.y * ch.scale);
+            } else {
+                S.w[j0 + c] = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale);
+            }
+        }
+    }
+    consumers_sync();
+    const int nquad = (it.rows + 3) >> 2;
+    const int ldq = ld16 >> 2;
+    float2 xa[QUADS_PER_LANE][4];  // phase 1: x of this lane's rows; phase 2: row sums
+#pragma unroll
+    for (int q = 0; q < QUADS_PER_LANE; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int r = 4 * (lane + 32 * q) + e;
+            xa[q][e] = (PHASE == 1 && r < it.rows) ? xp[it.dof + r] : make_float2(0.f, 0.f);
+        }
+    for (int k = 0; k < nst; ++k) {
+        const int s = k % S16_NSTAGE;
+        if (!mbar_wait(&S.full[s], (k / S16_NSTAGE) & 1)) {
+            atomicExch(err, MV_ERR_TIMEOUT);
+            break;
+        }
+        const int jb = k * sc;
+        const int g = min(sc, ncol - jb);
+        const uint4* sb = reinterpret_cast<const uint4*>(S.stage[s]);
+        for (int c = warp; c < g; c += S16_CONSUMERS) {
+            const uint4* col = sb + c * ldq;
+            const float2 wj = S.w[jb + c];
+            if (PHASE == 2) {
+#pragma unroll
+                for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                    const int qq = lane + 32 * q;
+                    if (qq < nquad) {
+                        const uint4 u = col[qq];
+                        const uint32_t a4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 a = bf2_to_f2(a4[e]);
+                            float2& s2 = xa[q][e];
+                            s2.x = fmaf(a.x, wj.x, fmaf(-a.y, wj.y, s2.x));
+                            s2.y = fmaf(a.x, wj.y, fmaf(a.y, wj.x, s2.y));
+                        }
+                    }
+                }
+            } else {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                    const int qq = lane + 32 * q;
+                    if (qq < nquad) {
+                        const uint4 u = col[qq];
+                        const uint32_t a4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 a = bf2_to_f2(a4[e]);  // conj(a) x
+                            re = fmaf(a.x, xa[q][e].x, fmaf(a.y, xa[q][e].y, re));
+                            im = fmaf(a.x, xa[q][e].y, fmaf(-a.y, xa[q][e].x, im));
+                        }
+                    }
+                }
+                re = warp_sumf(re);
+                im = warp_sumf(im);
+                if (lane == 0)
+                    atomicAdd(t + __float_as_int(wj.x), make_float2(re * wj.y, im * wj.y));
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[s]);
+    }
+    if (PHASE == 2) {
+#pragma unroll
+        for (int q = 0; q < QUADS_PER_LANE; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = 4 * (lane + 32 * q) + e;
+                if (r < MAX_LD) S.part[warp][r] = xa[q][e];
+            }
+        consumers_sync();
+        for (int r = tid; r < it.rows; r += 32 * S16_CONSUMERS) {
+            float2 s2 = S.part[0][r];
+            for (int w = 1; w < S16_CONSUMERS; ++w) {
+                s2.x += S.part[w][r].x;
+                s2.y += S.part[w][r].y;
+            }
+            atomicAdd(yp + it.dof + r, s2);
+        }
+    }
+}
+
 __global__ void gather_hdr16_kernel(const DevChunk16* src, const int32_t* order, int64_t n,
                                     DevChunk16* dst) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -503,17 +760,29 @@ void make_items(const std::vector<int64_t>& begin, const std::vector<int32_t>& l
     for (int64_t l = 0; l < nleaf; ++l) {
         int64_t acc = 0;
         int32_t first = (int32_t)order.size();
+        int64_t cols = 0;
         for (int64_t q = begin[l]; q < begin[l + 1]; ++q) {
             const Chunk& c = chunks[list[q]];
             if (c.ncols == 0) continue;
+            if (c.ncols > MAX_ITEM_COLS) hm_throw(HM_ERR_UNSUPPORTED, "chunk wider than an item");
+            if (cols + c.ncols > MAX_ITEM_COLS) {
+                items.push_back({plan.leaf_dof_begin[l], plan.leaf_rows[l],
+                                 (int32_t)hm_round_up(plan.leaf_rows[l], 2), first,
+                                 (int32_t)order.size()});
+                first = (int32_t)order.size();
+                acc = 0;
+                cols = 0;
+            }
             order.push_back(list[q]);
             acc += (int64_t)c.ld * c.ncols * 8;
+            cols += c.ncols;
             if (acc >= target || (int32_t)order.size() - first >= MAX_ITEM_CHUNKS) {
                 items.push_back({plan.leaf_dof_begin[l], plan.leaf_rows[l],
                                  (int32_t)hm_round_up(plan.leaf_rows[l], 2), first,
                                  (int32_t)order.size()});
                 first = (int32_t)order.size();
                 acc = 0;
+                cols = 0;
             }
         }
         if ((int32_t)order.size() > first)
@@ -687,6 +956,11 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
         m->n_o1 = (int64_t)o1.size();
         m->n_o2 = (int64_t)o2.size();
     }
+    m->h_items1 = it1;
+    m->h_items2 = it2;
+    m->h_order1 = o1;
+    m->h_order2 = o2;
+    m->d_err = (int*)hm_dmalloc(owner, sizeof(int), st, true);
     m->t_elems = plan.t_elems;
     m->t = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(float2), st, true);
     m->t64 = (double2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(double2), st, true);
@@ -694,8 +968,17 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
     return m;
 }
 
+static void matvec_graph_reset(MatvecDev* m) {
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    m->gexec = nullptr;
+    m->graph = nullptr;
+    m->g_gather = m->g_scatter = nullptr;
+}
+
 void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
                       cudaStream_t st) {
+    matvec_graph_reset(m);
     std::vector<DevChunk16> c16(plan.chunks.size());
     std::vector<ConvJob> jobs;
     int64_t off = 0;
@@ -716,6 +999,32 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
         off += (int64_t)d.ld * c.ncols;
         if (c.ncols > 0) jobs.push_back({c.data, c.ld, id});
         if (c.ncols > 0) (c.kind == 2 ? m->nchunks_v : m->nchunks_du)++;
+    }
+    // the streamed kernels read every item as one contiguous column-major matrix
+    auto check_items = [&](const std::vector<WorkItem>& items, const std::vector<int32_t>& order) {
+        for (const WorkItem& w : items) {
+            int64_t cols = 0;
+            for (int32_t q = w.first; q < w.last; ++q) {
+                const DevChunk16& a = c16[order[q]];
+                cols += a.ncols;
+                if (a.ld != c16[order[w.first]].ld || a.ld > MAX_LD || (a.data & 3))
+                    hm_throw(HM_ERR_UNSUPPORTED, "BF16 item layout");
+                if (q + 1 < w.last && c16[order[q + 1]].data != a.data + (int64_t)a.ld * a.ncols)
+                    hm_throw(HM_ERR_UNSUPPORTED, "BF16 item not contiguous");
+            }
+            if (cols > MAX_ITEM_COLS || w.last - w.first > MAX_ITEM_CHUNKS)
+                hm_throw(HM_ERR_UNSUPPORTED, "BF16 item too large");
+        }
+    };
+    check_items(m->h_items1, m->h_order1);
+    check_items(m->h_items2, m->h_order2);
+    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(S16Smem)));
+    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(S16Smem)));
+    {
+        const char* e = getenv("HM_MV16_LEGACY");
+        m->legacy16 = e && e[0] == '1';
     }
     m->arena16_elems = off;
     m->nchunks = (int64_t)c16.size();
@@ -749,7 +1058,11 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
     m->storage = HM_STORE_BF16;
 }
 
-void matvec_dev_destroy(MatvecDev* m) { delete m; }
+void matvec_dev_destroy(MatvecDev* m) {
+    if (!m) return;
+    matvec_graph_reset(m);
+    delete m;
+}
 void* matvec_arena(MatvecDev* m) { return m->arena; }
 int64_t matvec_stored_bytes(const MatvecDev* m) {
     return m->arena16 ? m->arena16_elems * 4 : m->arena_elems * 8;
@@ -758,7 +1071,12 @@ int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
-    if (m->n1 && m->arena16) {
+    if (m->n1 && m->arena16 && !m->legacy16) {
+        mv16s_kernel<1><<<(unsigned)m->n1, S16_THREADS, sizeof(S16Smem), st>>>(
+            m->items1, m->hdr16_1, m->arena16, xp, m->t, nullptr, m->d_err);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    } else if (m->n1 && m->arena16) {
         mv16_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr16_1,
                                                            m->arena16, xp, m->t);
         HM_CUDA(cudaGetLastError());
@@ -773,7 +1091,12 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
-    if (m->n2 && m->arena16) {
+    if (m->n2 && m->arena16 && !m->legacy16) {
+        mv16s_kernel<2><<<(unsigned)m->n2, S16_THREADS, sizeof(S16Smem), st>>>(
+            m->items2, m->hdr16_2, m->arena16, xp, m->t, yp, m->d_err);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    } else if (m->n2 && m->arena16) {
         mv16_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr16_2,
                                                            m->arena16, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
@@ -876,4 +1199,109 @@ void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
     HM_CUDA(cudaFreeAsync(d, st));
+}
+
+// The product through its CUDA graph.  The graph is captured on a private
+// stream (capture is not allowed on the legacy default stream) and launched on
+// st; a call with other x / y pointers rewrites only the gather and scatter
+// kernel nodes.
+void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp, float2* yp,
+                  double2* y, int64_t nc, cudaStream_t st) {
+    const unsigned nb = (unsigned)hm_cdiv(3 * nc, 256);
+    if (!m->gexec) {
+        cudaStream_t cs = nullptr;
+        HM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const long long before = g_hm_launches.load();
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            HM_CUDA(e);
+        }
+        try {
+            launch_gather_x(d_perm, x, xp, nc, cs);
+            matvec_tree_order(m, xp, yp, 3 * nc, cs);
+            launch_scatter_y(d_perm, yp, y, nc, cs);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            g_hm_launches.store(before);
+            throw;
+        }
+        e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        HM_CUDA(e);
+        m->g_kernels = g_hm_launches.load() - before;
+        g_hm_launches.store(before);
+        m->graph = g;
+        size_t nn = 0;
+        HM_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        HM_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            HM_CUDA(cudaGraphNodeGetType(nd, &ty));
+            if (ty != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams p;
+            HM_CUDA(cudaGraphKernelNodeGetParams(nd, &p));
+            if (p.func == (void*)gather_x_kernel) m->g_gather = nd;
+            if (p.func == (void*)scatter_y_kernel) m->g_scatter = nd;
+        }
+        if (!m->g_gather || !m->g_scatter) {
+            matvec_graph_reset(m);
+            hm_throw(HM_ERR_CUDA, "matvec graph: gather/scatter nodes not found");
+        }
+        e = cudaGraphInstantiate(&m->gexec, g, 0);
+        if (e != cudaSuccess) {
+            matvec_graph_reset(m);
+            HM_CUDA(e);
+        }
+        m->g_x = x;
+        m->g_y = y;
+    } else {
+        if (x != m->g_x) {
+            const int64_t* a0 = d_perm;
+            const double2* a1 = x;
+            float2* a2 = xp;
+            int64_t a3 = nc;
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+            cudaKernelNodeParams p = {};
+            p.func = (void*)gather_x_kernel;
+            p.gridDim = dim3(nb);
+            p.blockDim = dim3(256);
+            p.sharedMemBytes = 0;
+            p.kernelParams = args;
+            p.extra = nullptr;
+            HM_CUDA(cudaGraphExecKernelNodeSetParams(m->gexec, m->g_gather, &p));
+            m->g_x = x;
+        }
+        if (y != m->g_y) {
+            const int64_t* a0 = d_perm;
+            const float2* a1 = yp;
+            double2* a2 = y;
+            int64_t a3 = nc;
+            void* args[] = {(void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3};
+            cudaKernelNodeParams p = {};
+            p.func = (void*)scatter_y_kernel;
+            p.gridDim = dim3(nb);
+            p.blockDim = dim3(256);
+            p.sharedMemBytes = 0;
+            p.kernelParams = args;
+            p.extra = nullptr;
+            HM_CUDA(cudaGraphExecKernelNodeSetParams(m->gexec, m->g_scatter, &p));
+            m->g_y = y;
+        }
+    }
+    HM_CUDA(cudaGraphLaunch(m->gexec, st));
+    g_hm_launches.fetch_add(m->g_kernels, std::memory_order_relaxed);
+}
+
+// Error code of the streamed kernels since the last call (0 = none); resets it.
+int matvec_take_error(MatvecDev* m, cudaStream_t st) {
+    int e = 0;
+    HM_CUDA(cudaMemcpyAsync(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (e) HM_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
+    return e;
 }
