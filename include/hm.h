@@ -110,7 +110,10 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
  *   x, y  DEVICE complex128, 3 n_c x nrhs column-major, original point order;
  *         x is read, y is overwritten; they must not overlap.
  *   nrhs  >= 1.  Work is enqueued on stream; the call does not synchronise.
- * Errors: HM_ERR_ARG (null/overlapping pointers, nrhs < 1), HM_ERR_CUDA. */
+ * Errors: HM_ERR_ARG (null/overlapping pointers, nrhs < 1), HM_ERR_CUDA.  With
+ * BF16 storage the product kernels wait on their own shared-memory copies with
+ * a time limit; a wait that gives up is reported as HM_ERR_TIMEOUT by the next
+ * hm_matvec_host or hm_gmres on the handle. */
 hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream);
 
 /* Same product with HOST buffers: x is copied to the device, y back to the
@@ -125,7 +128,7 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
  * matvecs.  b, x: DEVICE complex128, length 3 n_c, original order.
  *   iters, relres: host outputs (may be NULL).
  * Errors: HM_ERR_ARG, HM_ERR_NOCONV (maxit reached; x holds the last iterate),
- * HM_ERR_CUDA. */
+ * HM_ERR_TIMEOUT (see hm_matvec), HM_ERR_CUDA. */
 hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double tol,
                    int32_t maxit, int32_t* iters, double* relres, void* stream);
 

@@ -536,6 +536,8 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
     if (s != HM_OK) return s;
     HM_CUDA(cudaMemcpyAsync(y, h->d_yh, (size_t)n * nrhs * 16, cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
+    if (matvec_take_error(h->mv, st))
+        hm_throw(HM_ERR_TIMEOUT, "a product kernel gave up waiting for its copies");
     HM_API_END
 }
 
@@ -549,6 +551,8 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
                                       (cudaStream_t)stream);
     if (iters) *iters = R.iters;
     if (relres) *relres = R.relres;
+    if (matvec_take_error(h->mv, (cudaStream_t)stream))
+        hm_throw(HM_ERR_TIMEOUT, "a product kernel gave up waiting for its copies");
     if (!R.converged) {
         hm_set_error("GMRES reached maxit above the tolerance");
         return HM_ERR_NOCONV;

@@ -17,7 +17,6 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <cstdlib>
 #include <cstring>
 
 #include "hm_internal.h"
@@ -90,7 +89,6 @@ struct MatvecDev {
     int* d_err = nullptr;             // error code written by the streamed kernels
     std::vector<WorkItem> h_items1, h_items2;
     std::vector<int32_t> h_order1, h_order2;
-    bool legacy16 = false;
 };
 
 namespace {
@@ -277,144 +275,6 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
 }
 constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (192 rows -> 48 quads -> 2)
 
-__global__ void __launch_bounds__(MV_THREADS) mv16_phase1(const WorkItem* items,
-                                                         const DevChunk16* hdr,
-                                                         const uint32_t* __restrict__ arena,
-                                                         const float2* __restrict__ xp, float2* t) {
-    const WorkItem it = items[blockIdx.x];
-    __shared__ DevChunk16 sh_hdr[MAX_ITEM_CHUNKS];
-    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 xv[QUADS_PER_LANE][4];
-#pragma unroll
-    for (int q = 0; q < QUADS_PER_LANE; ++q)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int r = 4 * (lane + 32 * q) + e;
-            xv[q][e] = r < it.rows ? xp[it.dof + r] : make_float2(0.f, 0.f);
-        }
-    const int nquad = (it.rows + 3) >> 2;
-    for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk16 ch = sh_hdr[ci - it.first];
-        const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
-        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
-            const uint4* col = base + (int64_t)c * (ch.ld >> 2);
-            float re = 0.f, im = 0.f;
-#pragma unroll
-            for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                const int qq = lane + 32 * q;
-                if (qq < nquad) {
-                    const uint4 w = __ldcs(col + qq);
-                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 a = bf2_to_f2(ww[e]);
-                        re = fmaf(a.x, xv[q][e].x, fmaf(a.y, xv[q][e].y, re));   // conj(a) x
-                        im = fmaf(a.x, xv[q][e].y, fmaf(-a.y, xv[q][e].x, im));
-                    }
-                }
-            }
-            re = warp_sumf(re);
-            im = warp_sumf(im);
-            if (lane == 0) atomicAdd(t + ch.vec + c, make_float2(re * ch.scale, im * ch.scale));
-        }
-    }
-}
-
-__global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
-                                                         const DevChunk16* hdr,
-                                                         const uint32_t* __restrict__ arena,
-                                                         const float2* __restrict__ xp,
-                                                         const float2* __restrict__ t,
-                                                         float2* yp) {
-    __shared__ float2 part[MV_WARPS][MAX_LD];
-    const WorkItem it = items[blockIdx.x];
-    __shared__ DevChunk16 sh_hdr[MAX_ITEM_CHUNKS];
-    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nquad = (it.rows + 3) >> 2;
-    float2 acc[QUADS_PER_LANE][4];
-#pragma unroll
-    for (int q = 0; q < QUADS_PER_LANE; ++q)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[q][e] = make_float2(0.f, 0.f);
-    for (int ci = it.first; ci < it.last; ++ci) {
-        const DevChunk16 ch = sh_hdr[ci - it.first];
-        const uint4* base = reinterpret_cast<const uint4*>(arena + ch.data);
-        const float2* v = (ch.kind == 0 ? xp : t) + ch.vec;
-        const int ldq = ch.ld >> 2;
-        int c = warp;
-        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
-            float2 v0 = __ldg(v + c), v1 = __ldg(v + c + MV_WARPS);
-            v0.x *= ch.scale; v0.y *= ch.scale;
-            v1.x *= ch.scale; v1.y *= ch.scale;
-            uint4 w0[QUADS_PER_LANE], w1[QUADS_PER_LANE];
-#pragma unroll
-            for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                const int qq = lane + 32 * q;
-                if (qq < nquad) {
-                    w0[q] = __ldcs(base + (int64_t)c * ldq + qq);
-                    w1[q] = __ldcs(base + (int64_t)(c + MV_WARPS) * ldq + qq);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                const int qq = lane + 32 * q;
-                if (qq < nquad) {
-                    const uint32_t a0[4] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w};
-                    const uint32_t a1[4] = {w1[q].x, w1[q].y, w1[q].z, w1[q].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 a = bf2_to_f2(a0[e]), b = bf2_to_f2(a1[e]);
-                        float2& s2 = acc[q][e];
-                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
-                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
-                        s2.x = fmaf(b.x, v1.x, fmaf(-b.y, v1.y, s2.x));
-                        s2.y = fmaf(b.x, v1.y, fmaf(b.y, v1.x, s2.y));
-                    }
-                }
-            }
-        }
-        for (; c < ch.ncols; c += MV_WARPS) {
-            float2 v0 = __ldg(v + c);
-            v0.x *= ch.scale; v0.y *= ch.scale;
-#pragma unroll
-            for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                const int qq = lane + 32 * q;
-                if (qq < nquad) {
-                    const uint4 w = __ldcs(base + (int64_t)c * ldq + qq);
-                    const uint32_t a0[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 a = bf2_to_f2(a0[e]);
-                        float2& s2 = acc[q][e];
-                        s2.x = fmaf(a.x, v0.x, fmaf(-a.y, v0.y, s2.x));
-                        s2.y = fmaf(a.x, v0.y, fmaf(a.y, v0.x, s2.y));
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < QUADS_PER_LANE; ++q)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int r = 4 * (lane + 32 * q) + e;
-            if (r < MAX_LD) part[warp][r] = acc[q][e];
-        }
-    __syncthreads();
-    for (int r = threadIdx.x; r < it.rows; r += MV_THREADS) {
-        float2 s2 = part[0][r];
-        for (int w = 1; w < MV_WARPS; ++w) {
-            s2.x += part[w][r].x;
-            s2.y += part[w][r].y;
-        }
-        atomicAdd(yp + it.dof + r, s2);
-    }
-}
-
 // ---- BF16 storage, streamed through shared memory ----
 // Every work item is one contiguous byte range of the BF16 arena: the chunks of
 // one leaf, all with the same leading dimension ld16, stored back to back, so
@@ -428,16 +288,19 @@ __global__ void __launch_bounds__(MV_THREADS) mv16_phase2(const WorkItem* items,
 // copies before it exits.
 constexpr int S16_CONSUMERS = 8;
 constexpr int S16_THREADS = 32 * (S16_CONSUMERS + 1);
-constexpr int S16_NSTAGE = 4;
-constexpr int S16_STAGE_BYTES = 16384;
-constexpr int MAX_ITEM_COLS = 2048;                   // columns of one item (per-column table in smem)
+constexpr int S16_NSTAGE = 3;
+constexpr int S16_STAGE_BYTES = 12288;
+constexpr int MAX_ITEM_COLS = 1024;                   // columns of one item (per-column table in smem)
 constexpr unsigned long long S16_WAIT_NS = 1000000000ull;
 constexpr int MV_ERR_TIMEOUT = 1;
 
+static_assert(S16_CONSUMERS * MAX_LD * sizeof(float2) <= S16_NSTAGE * S16_STAGE_BYTES,
+              "row sums fit in the stages");
 struct S16Smem {
+    // the stages; once every stage is consumed, phase 2 reuses them for the
+    // per-warp row sums (S16_CONSUMERS x MAX_LD float2)
     alignas(128) unsigned char stage[S16_NSTAGE][S16_STAGE_BYTES];
     float2 w[MAX_ITEM_COLS];                   // phase 2: scale * v_j; phase 1: (t index bits, scale)
-    float2 part[S16_CONSUMERS][MAX_LD];        // phase 2: per-warp row sums
     DevChunk16 hdr[MAX_ITEM_CHUNKS];
     int32_t colstart[MAX_ITEM_CHUNKS + 1];
     int32_t ncol;
@@ -480,12 +343,14 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // bounded wait for the completion of the phase with the given parity
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    if (mbar_try_wait(b, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity) {
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(b, parity))
         if (global_ns() - t0 > S16_WAIT_NS) return false;
     return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    return mbar_try_wait(b, parity) || mbar_wait_slow(b, parity);
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
@@ -595,64 +460,85 @@ __global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* item
         const int jb = k * sc;
         const int g = min(sc, ncol - jb);
         const uint4* sb = reinterpret_cast<const uint4*>(S.stage[s]);
-        for (int c = warp; c < g; c += S16_CONSUMERS) {
-            const uint4* col = sb + c * ldq;
-            const float2 wj = S.w[jb + c];
+        // two columns (c, c + S16_CONSUMERS) per pass: loads first, then arithmetic
+        for (int c = warp; c < g; c += 2 * S16_CONSUMERS) {
+            const int c1 = c + S16_CONSUMERS;
+            const bool two = c1 < g;
+            const float2 w0 = S.w[jb + c];
+            const float2 w1 = two ? S.w[jb + c1] : make_float2(0.f, 0.f);
+            uint4 u0[QUADS_PER_LANE], u1[QUADS_PER_LANE];
+#pragma unroll
+            for (int q = 0; q < QUADS_PER_LANE; ++q) {
+                const int qq = lane + 32 * q;
+                u0[q] = qq < nquad ? sb[c * ldq + qq] : make_uint4(0, 0, 0, 0);
+                u1[q] = (two && qq < nquad) ? sb[c1 * ldq + qq] : make_uint4(0, 0, 0, 0);
+            }
             if (PHASE == 2) {
 #pragma unroll
                 for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const int qq = lane + 32 * q;
-                    if (qq < nquad) {
-                        const uint4 u = col[qq];
-                        const uint32_t a4[4] = {u.x, u.y, u.z, u.w};
+                    const uint32_t a4[4] = {u0[q].x, u0[q].y, u0[q].z, u0[q].w};
+                    const uint32_t b4[4] = {u1[q].x, u1[q].y, u1[q].z, u1[q].w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float2 a = bf2_to_f2(a4[e]);
-                            float2& s2 = xa[q][e];
-                            s2.x = fmaf(a.x, wj.x, fmaf(-a.y, wj.y, s2.x));
-                            s2.y = fmaf(a.x, wj.y, fmaf(a.y, wj.x, s2.y));
-                        }
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 a = bf2_to_f2(a4[e]), b = bf2_to_f2(b4[e]);
+                        float2& s2 = xa[q][e];
+                        s2.x = fmaf(a.x, w0.x, fmaf(-a.y, w0.y, s2.x));
+                        s2.y = fmaf(a.x, w0.y, fmaf(a.y, w0.x, s2.y));
+                        s2.x = fmaf(b.x, w1.x, fmaf(-b.y, w1.y, s2.x));
+                        s2.y = fmaf(b.x, w1.y, fmaf(b.y, w1.x, s2.y));
                     }
                 }
             } else {
-                float re = 0.f, im = 0.f;
+                float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const int qq = lane + 32 * q;
-                    if (qq < nquad) {
-                        const uint4 u = col[qq];
-                        const uint32_t a4[4] = {u.x, u.y, u.z, u.w};
+                    const uint32_t a4[4] = {u0[q].x, u0[q].y, u0[q].z, u0[q].w};
+                    const uint32_t b4[4] = {u1[q].x, u1[q].y, u1[q].z, u1[q].w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float2 a = bf2_to_f2(a4[e]);  // conj(a) x
-                            re = fmaf(a.x, xa[q][e].x, fmaf(a.y, xa[q][e].y, re));
-                            im = fmaf(a.x, xa[q][e].y, fmaf(-a.y, xa[q][e].x, im));
-                        }
+                    for (int e = 0; e < 4; ++e) {  // conj(a) x
+                        const float2 a = bf2_to_f2(a4[e]), b = bf2_to_f2(b4[e]);
+                        const float2 xv = xa[q][e];
+                        re0 = fmaf(a.x, xv.x, fmaf(a.y, xv.y, re0));
+                        im0 = fmaf(a.x, xv.y, fmaf(-a.y, xv.x, im0));
+                        re1 = fmaf(b.x, xv.x, fmaf(b.y, xv.y, re1));
+                        im1 = fmaf(b.x, xv.y, fmaf(-b.y, xv.x, im1));
                     }
                 }
-                re = warp_sumf(re);
-                im = warp_sumf(im);
-                if (lane == 0)
-                    atomicAdd(t + __float_as_int(wj.x), make_float2(re * wj.y, im * wj.y));
+                // halving reduction: lanes < 16 finish column c, lanes >= 16 column c1
+                const bool up = (lane & 16) != 0;
+                float k0 = up ? re1 : re0, k1 = up ? im1 : im0;
+                k0 += __shfl_xor_sync(0xffffffffu, up ? re0 : re1, 16);
+                k1 += __shfl_xor_sync(0xffffffffu, up ? im0 : im1, 16);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    k0 += __shfl_xor_sync(0xffffffffu, k0, o);
+                    k1 += __shfl_xor_sync(0xffffffffu, k1, o);
+                }
+                if ((lane & 15) == 0 && (!up || two)) {
+                    const float2 wj = up ? w1 : w0;
+                    atomicAdd(t + __float_as_int(wj.x), make_float2(k0 * wj.y, k1 * wj.y));
+                }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);
     }
     if (PHASE == 2) {
+        consumers_sync();  // every stage consumed: reuse them for the row sums
+        float2(*part)[MAX_LD] = reinterpret_cast<float2(*)[MAX_LD]>(S.stage[0]);
 #pragma unroll
         for (int q = 0; q < QUADS_PER_LANE; ++q)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int r = 4 * (lane + 32 * q) + e;
-                if (r < MAX_LD) S.part[warp][r] = xa[q][e];
+                if (r < MAX_LD) part[warp][r] = xa[q][e];
             }
         consumers_sync();
         for (int r = tid; r < it.rows; r += 32 * S16_CONSUMERS) {
-            float2 s2 = S.part[0][r];
+            float2 s2 = part[0][r];
             for (int w = 1; w < S16_CONSUMERS; ++w) {
-                s2.x += S.part[w][r].x;
-                s2.y += S.part[w][r].y;
+                s2.x += part[w][r].x;
+                s2.y += part[w][r].y;
             }
             atomicAdd(yp + it.dof + r, s2);
         }
@@ -1022,10 +908,6 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
                                  (int)sizeof(S16Smem)));
     HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(S16Smem)));
-    {
-        const char* e = getenv("HM_MV16_LEGACY");
-        m->legacy16 = e && e[0] == '1';
-    }
     m->arena16_elems = off;
     m->nchunks = (int64_t)c16.size();
     m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4, st, true);
@@ -1071,14 +953,9 @@ int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
-    if (m->n1 && m->arena16 && !m->legacy16) {
+    if (m->n1 && m->arena16) {
         mv16s_kernel<1><<<(unsigned)m->n1, S16_THREADS, sizeof(S16Smem), st>>>(
             m->items1, m->hdr16_1, m->arena16, xp, m->t, nullptr, m->d_err);
-        HM_CUDA(cudaGetLastError());
-        HM_LAUNCHED();
-    } else if (m->n1 && m->arena16) {
-        mv16_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr16_1,
-                                                           m->arena16, xp, m->t);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     } else if (m->n1) {
@@ -1091,14 +968,9 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
-    if (m->n2 && m->arena16 && !m->legacy16) {
+    if (m->n2 && m->arena16) {
         mv16s_kernel<2><<<(unsigned)m->n2, S16_THREADS, sizeof(S16Smem), st>>>(
             m->items2, m->hdr16_2, m->arena16, xp, m->t, yp, m->d_err);
-        HM_CUDA(cudaGetLastError());
-        HM_LAUNCHED();
-    } else if (m->n2 && m->arena16) {
-        mv16_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr16_2,
-                                                           m->arena16, xp, m->t, yp);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     } else if (m->n2) {
