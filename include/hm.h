@@ -106,10 +106,18 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
                    double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
                    int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out);
 
+/* Right-hand sides per block of the tensor-core product (see hm_matvec). */
+#define HM_NRHS_BLOCK 32
+
 /* y = A_H x (Sec. 3.1: dense product on P^non-ad, U (V^H x) on P^ad).
  *   x, y  DEVICE complex128, 3 n_c x nrhs column-major, original point order;
  *         x is read, y is overwritten; they must not overlap.
  *   nrhs  >= 1.  Work is enqueued on stream; the call does not synchronise.
+ * With BF16 storage and nrhs > 1 the right-hand sides are taken in blocks of
+ * HM_NRHS_BLOCK (the last one padded with zeros) and each block runs as one
+ * dense contraction on the tensor cores: X, T = V^H X and the products in
+ * BF16, sums in FP32 (relative error a few 2^-9).  Otherwise each right-hand
+ * side is one product with FP32 (or BF16 x FP32) arithmetic.
  * Errors: HM_ERR_ARG (null/overlapping pointers, nrhs < 1), HM_ERR_CUDA.  With
  * BF16 storage the product kernels wait on their own shared-memory copies with
  * a time limit; a wait that gives up is reported as HM_ERR_TIMEOUT by the next
@@ -268,6 +276,16 @@ hm_status hm_rank_model_grad(const float* params, const float* feats, const floa
  * algorithmic byte count of one whole product (stored H-matrix + x + y).
  * Errors: HM_ERR_ARG, HM_ERR_CUDA. */
 hm_status hm_profile_matvec(hm_handle h, int32_t reps, double* ms, int64_t* bytes, void* stream);
+
+/* Same report for the tensor-core product of one block of HM_NRHS_BLOCK
+ * right-hand sides (BF16 storage only): ms[0] gather X, ms[1] phase 1
+ * (T = V^H X), ms[2] phase 2 (Y = D X + U T), ms[3] scatter Y; bytes[0] is its
+ * algorithmic byte count (stored BF16 entries and scales, plus X, T and Y,
+ * complex64, read or written once each).
+ * Errors: HM_ERR_ARG, HM_ERR_UNSUPPORTED (FP32 storage), HM_ERR_TIMEOUT,
+ * HM_ERR_CUDA. */
+hm_status hm_profile_matvec_multi(hm_handle h, int32_t reps, double* ms, int64_t* bytes,
+                                  void* stream);
 
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t hm_kernel_launches(void);

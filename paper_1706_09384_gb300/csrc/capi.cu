@@ -506,6 +506,10 @@ hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* str
     const int64_t bytes = n * nrhs * 16;
     if (xb < yb + bytes && yb < xb + bytes) hm_throw(HM_ERR_ARG, "x and y overlap");
     cudaStream_t st = (cudaStream_t)stream;
+    if (nrhs > 1 && h->opts.storage == HM_STORE_BF16) {
+        matvec_multi(h->mv, h->d_perm, (const double2*)x, (double2*)y, h->nc, nrhs, st);
+        return HM_OK;
+    }
     for (int32_t c = 0; c < nrhs; ++c) {
         matvec_graph(h->mv, h->d_perm, (const double2*)x + c * n, h->d_xp, h->d_yp,
                      (double2*)y + c * n, h->nc, st);
@@ -842,6 +846,34 @@ hm_status hm_profile_matvec(hm_handle h, int32_t reps, double* ms, int64_t* byte
     bytes[0] = b3[0];
     bytes[1] = b3[1];
     bytes[2] = b3[2];
+    HM_API_END
+}
+
+hm_status hm_profile_matvec_multi(hm_handle h, int32_t reps, double* ms, int64_t* bytes,
+                                  void* stream) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (reps < 1 || !ms || !bytes) hm_throw(HM_ERR_ARG, "reps < 1 or null output");
+    if (h->opts.storage != HM_STORE_BF16) hm_throw(HM_ERR_UNSUPPORTED, "block product needs BF16 storage");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = 3 * h->nc;
+    std::vector<DevBuf> tmp;
+    double2* x = (double2*)hm_dmalloc(tmp, (size_t)n * HM_NRHS_BLOCK * 16, st, false);
+    double2* y = (double2*)hm_dmalloc(tmp, (size_t)n * HM_NRHS_BLOCK * 16, st, false);
+    try {
+        std::vector<double2> ones((size_t)n * HM_NRHS_BLOCK);
+        for (size_t q = 0; q < ones.size(); ++q) ones[q] = make_double2(1.0 + (q / n) * 1e-3, 0.5);
+        HM_CUDA(cudaMemcpyAsync(x, ones.data(), ones.size() * 16, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        matvec_multi_profile(h->mv, h->d_perm, x, y, h->nc, reps, ms, st);
+    } catch (...) {
+        free_all(tmp);
+        throw;
+    }
+    free_all(tmp);
+    bytes[0] = matvec_multi_alg_bytes(h->mv, n);
+    if (matvec_take_error(h->mv, st))
+        hm_throw(HM_ERR_TIMEOUT, "a product kernel gave up waiting for its copies");
     HM_API_END
 }
 

@@ -91,6 +91,15 @@ void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2*
 // Error code left by the streamed product kernels (0 = none; 1 = a wait on a
 // copy gave up); reading it synchronises st and clears it.
 int matvec_take_error(MatvecDev* m, cudaStream_t st);
+// Y = A_H X for nrhs right-hand sides (complex128, 3 nc x nrhs column-major,
+// original order) on the tensor cores, in blocks of 32; BF16 storage only.
+void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* y, int64_t nc,
+                  int32_t nrhs, cudaStream_t st);
+// algorithmic bytes of one 32-right-hand-side block product (stored entries + vectors)
+int64_t matvec_multi_alg_bytes(const MatvecDev* m, int64_t ndof);
+// mean device ms of gather, phase 1, phase 2, scatter of one 32-column block product
+void matvec_multi_profile(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* y,
+                          int64_t nc, int32_t reps, double ms[4], cudaStream_t st);
 // y_p (tree order, float2) = A_H x_p (tree order, float2)
 void matvec_tree_order(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st);
 // Copies staged column-major blocks / factors (FP32, one pointer per block:

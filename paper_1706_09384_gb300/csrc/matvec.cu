@@ -19,85 +19,14 @@
 #include <algorithm>
 #include <cstring>
 
-#include "hm_internal.h"
-
-struct DevChunk {
-    int64_t data;   // arena element offset
-    int64_t vec;    // x (kind 0) or t (kind 1/2) element offset
-    int32_t ld;
-    int32_t ncols;
-    int32_t kind;
-    int32_t rows;
-};
-// Chunk of the BF16 arena: complex entries as two bf16 (4 bytes), scaled by a
-// per-chunk FP32 factor; rows padded to a multiple of 4 (16-byte columns).
-struct DevChunk16 {
-    int64_t data;   // element offset in arena16
-    int64_t vec;
-    int32_t ld;
-    int32_t ncols;
-    int32_t kind;
-    int32_t rows;
-    float scale;
-    int32_t pad_;
-};
-struct WorkItem {
-    int64_t dof;      // first tree-order DOF of the leaf
-    int32_t rows;     // 3 |leaf|
-    int32_t ld;
-    int32_t first;    // chunk ids [first, last)
-    int32_t last;
-};
-
-struct MatvecDev {
-    int storage = 0;
-    float2* arena = nullptr;
-    int64_t arena_elems = 0;
-    DevChunk* chunks = nullptr;
-    WorkItem* items1 = nullptr;   // phase 1 (V)
-    WorkItem* items2 = nullptr;   // phase 2 (dense + U)
-    int32_t* order1 = nullptr;    // chunk ids referenced by items, phase 1
-    int32_t* order2 = nullptr;
-    DevChunk* hdr1 = nullptr;     // chunk headers in item order (phase 1, phase 2)
-    DevChunk* hdr2 = nullptr;
-    DevChunk16* hdr16_1 = nullptr;
-    DevChunk16* hdr16_2 = nullptr;
-    int64_t n_o1 = 0, n_o2 = 0;
-    int64_t n1 = 0, n2 = 0;
-    float2* t = nullptr;
-    double2* t64 = nullptr;       // accurate product: t in FP64
-    int64_t t_elems = 0;
-    int64_t dense_elems = 0;
-    int64_t lr_elems = 0;
-    int64_t alg_v = 0;      // stored entries (rows x cols, no padding) of V chunks
-    int64_t alg_du = 0;     // ... of dense and U chunks
-    // BF16 copy of the arena (HM_STORE_BF16): the fast product reads it; the
-    // FP32 arena stays for the accurate product
-    uint32_t* arena16 = nullptr;
-    int64_t arena16_elems = 0;
-    DevChunk16* chunks16 = nullptr;
-    int64_t nchunks = 0;
-    int64_t nchunks_v = 0, nchunks_du = 0;  // scale counts for the byte model
-    // CUDA graph of one whole product (gather, both phases, scatter), captured
-    // on first use; x and y are re-pointed in the instantiated graph
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t g_gather = nullptr, g_scatter = nullptr;
-    const double2* g_x = nullptr;
-    double2* g_y = nullptr;
-    long long g_kernels = 0;
-    int* d_err = nullptr;             // error code written by the streamed kernels
-    std::vector<WorkItem> h_items1, h_items2;
-    std::vector<int32_t> h_order1, h_order2;
-};
+#include "matvec_dev.cuh"
+#include "pipeline.cuh"
 
 namespace {
 
 constexpr int MV_THREADS = 256;
 constexpr int MV_WARPS = MV_THREADS / 32;
-constexpr int MAX_LD = 192;               // 3 * 64 rows: leaves up to 64 points
 constexpr int PAIRS_PER_LANE = MAX_LD / 64;  // row pairs per lane (3)
-constexpr int MAX_ITEM_CHUNKS = 64;          // chunk headers staged in shared memory per item
 
 __device__ __forceinline__ float4 ldg_stream(const float4* p) { return __ldcs(p); }
 
@@ -283,15 +212,13 @@ constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (1
 // (cp.async.bulk, completion counted on an mbarrier per stage); eight consumer
 // warps compute from the stages and release them through a second mbarrier
 // per stage.  The bytes in flight per SM are set by the ring, not by the
-// registers of the consumers.  Each wait gives up after S16_WAIT_NS, records
+// registers of the consumers.  Each wait gives up after PIPE_WAIT_NS, records
 // an error code and lets the CTA finish; the producer always waits for its own
 // copies before it exits.
 constexpr int S16_CONSUMERS = 8;
 constexpr int S16_THREADS = 32 * (S16_CONSUMERS + 1);
 constexpr int S16_NSTAGE = 3;
 constexpr int S16_STAGE_BYTES = 12288;
-constexpr int MAX_ITEM_COLS = 1024;                   // columns of one item (per-column table in smem)
-constexpr unsigned long long S16_WAIT_NS = 1000000000ull;
 constexpr int MV_ERR_TIMEOUT = 1;
 
 static_assert(S16_CONSUMERS * MAX_LD * sizeof(float2) <= S16_NSTAGE * S16_STAGE_BYTES,
@@ -308,60 +235,7 @@ struct S16Smem {
     uint64_t empty[S16_NSTAGE];
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// bounded wait for the completion of the phase with the given parity
-__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity) {
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(b, parity))
-        if (global_ns() - t0 > S16_WAIT_NS) return false;
-    return true;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    return mbar_try_wait(b, parity) || mbar_wait_slow(b, parity);
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void consumers_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * S16_CONSUMERS) : "memory");
-}
+__device__ __forceinline__ void consumers_sync() { named_sync<1, 32 * S16_CONSUMERS>(); }
 
 // PHASE 1: t[vec_j] += scale_j * V_j^H x_leaf;  PHASE 2: y_leaf += sum_j M_j scale_j v_j.
 template <int PHASE>
@@ -943,6 +817,9 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
 void matvec_dev_destroy(MatvecDev* m) {
     if (!m) return;
     matvec_graph_reset(m);
+    if (m->xm) cudaFree(m->xm);
+    if (m->ym) cudaFree(m->ym);
+    if (m->tm) cudaFree(m->tm);
     delete m;
 }
 void* matvec_arena(MatvecDev* m) { return m->arena; }

@@ -1,0 +1,89 @@
+// matvec_dev.cuh — device-side layout of the stored H-matrix shared by the
+// product kernels (matvec.cu: one right-hand side; matvec_multi.cu: blocks of
+// right-hand sides on the tensor cores).
+#pragma once
+#include <vector>
+
+#include "hm_internal.h"
+
+constexpr int MAX_LD = 192;               // 3 * 64 rows: leaves up to 64 points
+constexpr int MAX_ITEM_CHUNKS = 64;       // chunk headers staged in shared memory per item
+constexpr int MAX_ITEM_COLS = 1024;       // columns of one item (per-column table in smem)
+
+struct DevChunk {
+    int64_t data;   // arena element offset
+    int64_t vec;    // x (kind 0) or t (kind 1/2) element offset
+    int32_t ld;
+    int32_t ncols;
+    int32_t kind;
+    int32_t rows;
+};
+// Chunk of the BF16 arena: complex entries as two bf16 (4 bytes), scaled by a
+// per-chunk FP32 factor; rows padded to a multiple of 4 (16-byte columns).
+struct DevChunk16 {
+    int64_t data;   // element offset in arena16
+    int64_t vec;
+    int32_t ld;
+    int32_t ncols;
+    int32_t kind;
+    int32_t rows;
+    float scale;
+    int32_t pad_;
+};
+struct WorkItem {
+    int64_t dof;      // first tree-order DOF of the leaf
+    int32_t rows;     // 3 |leaf|
+    int32_t ld;
+    int32_t first;    // chunk ids [first, last)
+    int32_t last;
+};
+
+struct MatvecDev {
+    int storage = 0;
+    float2* arena = nullptr;
+    int64_t arena_elems = 0;
+    DevChunk* chunks = nullptr;
+    WorkItem* items1 = nullptr;   // phase 1 (V)
+    WorkItem* items2 = nullptr;   // phase 2 (dense + U)
+    int32_t* order1 = nullptr;    // chunk ids referenced by items, phase 1
+    int32_t* order2 = nullptr;
+    DevChunk* hdr1 = nullptr;     // chunk headers in item order (phase 1, phase 2)
+    DevChunk* hdr2 = nullptr;
+    DevChunk16* hdr16_1 = nullptr;
+    DevChunk16* hdr16_2 = nullptr;
+    int64_t n_o1 = 0, n_o2 = 0;
+    int64_t n1 = 0, n2 = 0;
+    float2* t = nullptr;
+    double2* t64 = nullptr;       // accurate product: t in FP64
+    int64_t t_elems = 0;
+    int64_t dense_elems = 0;
+    int64_t lr_elems = 0;
+    int64_t alg_v = 0;      // stored entries (rows x cols, no padding) of V chunks
+    int64_t alg_du = 0;     // ... of dense and U chunks
+    // BF16 copy of the arena (HM_STORE_BF16): the fast product reads it; the
+    // FP32 arena stays for the accurate product
+    uint32_t* arena16 = nullptr;
+    int64_t arena16_elems = 0;
+    DevChunk16* chunks16 = nullptr;
+    int64_t nchunks = 0;
+    int64_t nchunks_v = 0, nchunks_du = 0;  // scale counts for the byte model
+    // CUDA graph of one whole product (gather, both phases, scatter), captured
+    // on first use; x and y are re-pointed in the instantiated graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t g_gather = nullptr, g_scatter = nullptr;
+    const double2* g_x = nullptr;
+    double2* g_y = nullptr;
+    long long g_kernels = 0;
+    int* d_err = nullptr;             // error code written by the streamed kernels
+    std::vector<WorkItem> h_items1, h_items2;
+    std::vector<int32_t> h_order1, h_order2;
+    // block of NRHS_BLOCK right-hand sides (tensor-core product), allocated on first use
+    float2* xm = nullptr;
+    float2* ym = nullptr;
+    float2* tm = nullptr;
+};
+
+// Block of NRHS_BLOCK right-hand sides for the tensor-core product (created on
+// first use; tree-order vectors, right-hand side fastest: v[dof * NRHS_BLOCK + s]).
+constexpr int NRHS_BLOCK = 32;

@@ -75,6 +75,7 @@ SIGNATURES = {
     "hm_rank_model_predict": (_I32, [_P, _P, _I64, _P, _P]),
     "hm_rank_model_grad": (_I32, [_P, _P, _P, _I64, _P, _P, _P]),
     "hm_profile_matvec": (_I32, [_P, _I32, _P, _P, _P]),
+    "hm_profile_matvec_multi": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_kernel_launches": (_I64, []),
     "hm_free": (None, [_P]),
     "hm_status_string": (C.c_char_p, [_I32]),
@@ -264,6 +265,16 @@ class HMatrix:
                "hm_profile_matvec")
         return {"ms": {"gather": ms[0], "phase1": ms[1], "phase2": ms[2], "scatter": ms[3]},
                 "bytes": {"phase1": by[0], "phase2": by[1], "matvec": by[2]}}
+
+    def profile_matvec_multi(self, reps=10, stream=None):
+        """Per-kernel device times (ms) of one tensor-core block product of
+        HM_NRHS_BLOCK right-hand sides (BF16 storage) and its algorithmic bytes."""
+        ms = (C.c_double * 4)()
+        by = (C.c_int64 * 1)()
+        _check(lib().hm_profile_matvec_multi(self.h, reps, ms, by, _stream_ptr(stream)),
+               "hm_profile_matvec_multi")
+        return {"ms": {"gather": ms[0], "phase1": ms[1], "phase2": ms[2], "scatter": ms[3]},
+                "bytes": by[0]}
 
     def stats(self):
         need = C.c_size_t(0)

@@ -89,3 +89,18 @@ def plane_wave_directions(nrhs: int, seed: int = 0):
 def material(kappa_s: float, rho: float = 1.0, mu: float = 1.0, lam: float = 2.0):
     """(rho, lam, mu, omega) with omega chosen so that k_s = omega sqrt(rho/mu) = kappa_s."""
     return rho, lam, mu, kappa_s / math.sqrt(rho / mu)
+
+
+def plane_wave_rhs(points: np.ndarray, kappa_p: float, kappa_s: float, nrhs: int, seed: int = 0):
+    """Incident plane waves sampled at the points, DOF order, shape (3 n_c, nrhs)
+    column-major: even s a P wave d_s exp(i k_p d_s.x), odd s an S wave
+    p_s exp(i k_s d_s.x), with d_s, p_s from plane_wave_directions."""
+    d, p = plane_wave_directions(nrhs, seed)
+    out = np.empty((3 * len(points), nrhs), dtype=np.complex128, order="F")
+    for s in range(nrhs):
+        if s % 2 == 0:
+            u = d[s][None, :] * np.exp(1j * kappa_p * (points @ d[s]))[:, None]
+        else:
+            u = p[s][None, :] * np.exp(1j * kappa_s * (points @ d[s]))[:, None]
+        out[:, s] = u.reshape(-1)
+    return out
