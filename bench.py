@@ -288,11 +288,25 @@ def run_gpu(args, wl, world, rank, local):
     prof = H.profile_matvec(reps=10)
     peak, peak_kind = measured_peaks()
     ph2 = prof["bytes"]["phase2"] / (prof["ms"]["phase2"] * 1e-3) / 1e9
-    roof_mv = {"bound": "hbm", "kernel": "mv_phase2", "achieved": ph2, "peak": peak,
+    kname = "mv16s_kernel<2>" if form == "mixed" else "mv_phase2"
+    roof_mv = {"bound": "hbm", "kernel": kname, "achieved": ph2, "peak": peak,
                "peak_kind": peak_kind, "unit": "GB/s", "frac": ph2 / peak,
-               "traffic": kernel_traffic("matvec.cu", "mv_phase2"),
+               "traffic": kernel_traffic("matvec.cu", kname),
                "alg_bytes_per_launch": prof["bytes"]["phase2"],
                "ms_per_launch": prof["ms"]["phase2"], "kernels_ms": prof["ms"]}
+    # the product for a block of 32 right-hand sides on the tensor cores (mixed form)
+    block = None
+    if form == "mixed":
+        pm = H.profile_matvec_multi(reps=10)
+        tb = sum(pm["ms"].values())
+        tk = pm["ms"]["phase1"] + pm["ms"]["phase2"]
+        block = {"nrhs": hm.HM_NRHS_BLOCK, "kernels": "mvm_phase1 / mvm_phase2 (BF16 mma.sync "
+                 "m16n8k16, FP32 accumulation)", "ms": pm["ms"], "alg_bytes": pm["bytes"],
+                 "achieved_GBps": pm["bytes"] / (tk * 1e-3) / 1e9,
+                 "frac": pm["bytes"] / (tk * 1e-3) / 1e9 / peak, "peak": peak,
+                 "per_rhs_ms": tb / hm.HM_NRHS_BLOCK,
+                 "speedup_vs_one_vector_products": statistics.mean(mv_ms) / args.matvecs
+                 * hm.HM_NRHS_BLOCK / tb}
     # the dominant kernel of a step: the FP64 vector ACA of the build
     aca_t = statistics.mean(aca_ms)
     per_step = {"aca_kernel": aca_t, "recompression": statistics.mean(rec_ms),
@@ -350,6 +364,8 @@ def run_gpu(args, wl, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }
+    if block:
+        out["block_product_32rhs"] = block
     if form == "mixed" and not args.no_compare:
         # the plain form on the same workload, once, outside the timed steps
         H.free()

@@ -109,6 +109,34 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
 /* Right-hand sides per block of the tensor-core product (see hm_matvec). */
 #define HM_NRHS_BLOCK 32
 
+/* One problem of a batch build (arguments of hm_build, plus its own column
+ * weights; the batch shares eps and the options). */
+typedef struct {
+    const double* points;   /* HOST n_c x 3 row-major */
+    const double* normals;  /* HOST n_c x 3, required for the T kernel, else NULL */
+    int64_t n_c;
+    double rho, lambda, mu, omega;
+    int32_t kernel;         /* HM_KERNEL_U or HM_KERNEL_T */
+    int32_t pad_;
+    double eta;
+    int64_t leaf_size;
+    const double* weights;  /* HOST n_c column weights w_j (W_y of Sec. 4) or NULL */
+} hm_problem;
+
+/* Builds nprob independent H-matrices at once: trees, partitions, near
+ * fields and storage per problem, while the vector ACA and the recompression
+ * of the admissible blocks of all problems run in shared launches (one
+ * persistent ACA launch serves blocks of every problem; no paper counterpart:
+ * batching of independent problems).  Each handle is the same H-matrix that
+ * hm_build would give for its problem with opts.weights = probs[q].weights;
+ * its statistics report the shared launches (batch_problems = nprob).
+ *   probs    HOST array of nprob problems; eps and opts (NULL = defaults; its
+ *            weights field is ignored) are common to the batch
+ *   out      HOST array of nprob handles (all NULL on error)
+ * Errors: as hm_build, for the first problem that fails. */
+hm_status hm_build_batch(int32_t nprob, const hm_problem* probs, double eps, const hm_opts* opts,
+                         void* stream, hm_handle* out);
+
 /* y = A_H x (Sec. 3.1: dense product on P^non-ad, U (V^H x) on P^ad).
  *   x, y  DEVICE complex128, 3 n_c x nrhs column-major, original point order;
  *         x is read, y is overwritten; they must not overlap.
@@ -139,6 +167,20 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
  * HM_ERR_TIMEOUT (see hm_matvec), HM_ERR_CUDA. */
 hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double tol,
                    int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/* hm_gmres for nrhs right-hand sides at once: one restarted GMRES per column,
+ * run in lockstep so that each Arnoldi step makes one product of all columns
+ * (the tensor-core block product when the storage is BF16).  A column whose
+ * residual estimate reaches tol stops for the rest of its cycle; restarts use
+ * the accurate product per column (iterative refinement).
+ *   b, x    DEVICE complex128, 3 n_c x nrhs column-major, original order; no overlap
+ *   iters   HOST int32[nrhs] or NULL: products made until each column converged
+ *   relres  HOST double[nrhs] or NULL: final true relative residual per column
+ * Memory: (restart + 2) * nrhs vectors of 3 n_c complex128 on the device.
+ * Errors: HM_ERR_ARG, HM_ERR_NOCONV (some column reached maxit; x holds the
+ * last iterates), HM_ERR_TIMEOUT, HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int32_t restart,
+                         double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
 
 /* Writes a JSON object (NUL-terminated) with the build statistics: n_c, tree
  * depth, cluster and block counts, sparsity constant C_sp (Sec. 2.1), ACA

@@ -256,7 +256,9 @@ HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
     }
 }
 
-__global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* __restrict__ pts,
+__global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
+                                                 const GreenParams* __restrict__ gps,
+                                                 const double* __restrict__ pts,
                                                  const double* __restrict__ nrm,
                                                  const AcaJob* __restrict__ jobs, int64_t njobs,
                                                  int* counter, double2* work, double2* gram,
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
     __shared__ double s_normB2, s_sref, s_best, s_dB2;
     __shared__ double2 s_gam[9];
     __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
+    __shared__ GreenParams s_gp;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double2* R = rowbuf + blockIdx.x * rb_stride;   // [a][3n], row-major, then n float2
@@ -286,6 +289,10 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp, const double* _
         const int64_t job = s_job;
         if (job >= njobs) return;
         const AcaJob J = jobs[job];
+        // one problem (kernel parameters), or a batch of problems (J.pad_ =
+        // problem index; its parameters are read from shared memory)
+        if (gps && tid == 0) s_gp = gps[J.pad_];
+        const GreenParams& gp = gps ? s_gp : gp0;
         const int64_t m = J.m, n = J.n, m3 = 3 * m, n3 = 3 * n;
         double2* U = work + J.u_off;
         double2* V = work + J.v_off;
@@ -644,13 +651,13 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                 unsigned char* d_flags,
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
-                int* d_counter, cudaStream_t st) {
+                int* d_counter, cudaStream_t st, const GreenParams* d_gps) {
     if (njobs == 0) return;
     const size_t smem = (size_t)6 * capmax * sizeof(double2);
     HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     HM_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
-    aca_kernel<<<nctas, AT, smem, st>>>(gp, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
+    aca_kernel<<<nctas, AT, smem, st>>>(gp, d_gps, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
                                         d_gram, d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
                                         colbuf_stride, capmax, eps, d_res);
                                         HM_LAUNCHED();

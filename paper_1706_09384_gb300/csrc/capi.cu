@@ -92,67 +92,122 @@ bool finite_all(const double* p, int64_t n) {
     return true;
 }
 
-// ACA + recompression of every admissible block, in batches bounded by the
+// ACA + recompression of every admissible block of one or several problems
+// (one launch serves blocks of every problem), in batches bounded by the
 // workspace budget.  Writes the FP32 factors (U' column-major 3m x r', V'
 // 3n x r') into staging buffers owned by `staging` and records per block the
-// pointers and ranks.
-void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<const float2*>& su,
-                    std::vector<const float2*>& sv, cudaStream_t st) {
-    const std::vector<hm_cluster>& cl = h->clusters;
-    std::vector<hm_block>& blk = h->blocks;
-    std::vector<int64_t> adm;
-    for (int64_t b = 0; b < (int64_t)blk.size(); ++b)
-        if (blk[b].admissible) adm.push_back(b);
-    auto pts_of = [&](int64_t c) { return cl[c].end - cl[c].begin; };
-    std::stable_sort(adm.begin(), adm.end(), [&](int64_t a, int64_t b) {
-        return pts_of(blk[a].tau) + pts_of(blk[a].sigma) > pts_of(blk[b].tau) + pts_of(blk[b].sigma);
-    });
-    int cap0 = h->opts.aca_max_rank > 0 ? h->opts.aca_max_rank : 144;
+// pointers and ranks.  Options, eps and the recompression switch are those of
+// the first problem (a batch shares them).
+void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
+                    std::vector<std::vector<const float2*>>& su,
+                    std::vector<std::vector<const float2*>>& sv, cudaStream_t st) {
+    hm_matrix* h0 = hs[0];
+    const int nprob = (int)hs.size();
+    // admissible blocks of all problems: (problem, block)
+    std::vector<int32_t> aq;
+    std::vector<int64_t> ab;
+    for (int q = 0; q < nprob; ++q)
+        for (int64_t b = 0; b < (int64_t)hs[q]->blocks.size(); ++b)
+            if (hs[q]->blocks[b].admissible) {
+                aq.push_back(q);
+                ab.push_back(b);
+            }
+    const int64_t na = (int64_t)aq.size();
+    auto blk_of = [&](int64_t a) -> hm_block& { return hs[aq[a]]->blocks[ab[a]]; };
+    auto cl_of = [&](int64_t a, int64_t c) -> const hm_cluster& { return hs[aq[a]]->clusters[c]; };
+    auto pts_of = [&](int64_t a, int64_t c) { return cl_of(a, c).end - cl_of(a, c).begin; };
+    auto size_of = [&](int64_t a) { return pts_of(a, blk_of(a).tau) + pts_of(a, blk_of(a).sigma); };
+    std::vector<int64_t> adm(na);
+    std::iota(adm.begin(), adm.end(), 0);
+    std::stable_sort(adm.begin(), adm.end(), [&](int64_t a, int64_t b) { return size_of(a) > size_of(b); });
+    int cap0 = h0->opts.aca_max_rank > 0 ? h0->opts.aca_max_rank : 144;
     cap0 = std::max(3, cap0 - cap0 % 3);
-    const int64_t budget = h->opts.workspace_bytes > 0 ? h->opts.workspace_bytes : (24ll << 30);
+    const int64_t budget = h0->opts.workspace_bytes > 0 ? h0->opts.workspace_bytes : (24ll << 30);
     int nsm = 0;
-    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    std::vector<int> cap(blk.size(), 0);
-    for (int64_t b : adm) {
-        const int64_t full = 3 * std::min(pts_of(blk[b].tau), pts_of(blk[b].sigma));
-        cap[b] = (int)std::min<int64_t>(full, cap0);
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device));
+    std::vector<int> cap(na, 0);
+    for (int64_t a = 0; a < na; ++a) {
+        const int64_t full = 3 * std::min(pts_of(a, blk_of(a).tau), pts_of(a, blk_of(a).sigma));
+        cap[a] = (int)std::min<int64_t>(full, cap0);
     }
-    if (h->opts.rank_model && !adm.empty()) {
+    int used_model = 0;
+    if (h0->opts.rank_model && na > 0) {
         // learned capacities: predicted rank-3 steps with a safety margin; the
         // ACA still decides the rank and overflowing blocks are re-run
-        const int64_t na = (int64_t)adm.size();
         std::vector<float> feats(6 * na), pred(na);
-        for (int64_t q = 0; q < na; ++q)
-            rank_features(cl[blk[adm[q]].tau], cl[blk[adm[q]].sigma], h->gp.ks, h->gp.kp, h->eps,
-                          &feats[6 * q]);
+        for (int64_t a = 0; a < na; ++a) {
+            const hm_matrix* hq = hs[aq[a]];
+            rank_features(cl_of(a, blk_of(a).tau), cl_of(a, blk_of(a).sigma), hq->gp.ks, hq->gp.kp,
+                          hq->eps, &feats[6 * a]);
+        }
         std::vector<DevBuf> tmp;
         float* dP = (float*)hm_dmalloc(tmp, HM_RANK_MODEL_PARAMS * 4, st, false);
         float* dF = (float*)hm_dmalloc(tmp, feats.size() * 4, st, false);
         float* dO = (float*)hm_dmalloc(tmp, na * 4, st, false);
-        HM_CUDA(cudaMemcpyAsync(dP, h->opts.rank_model, HM_RANK_MODEL_PARAMS * 4, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(dP, h0->opts.rank_model, HM_RANK_MODEL_PARAMS * 4, cudaMemcpyHostToDevice, st));
         HM_CUDA(cudaMemcpyAsync(dF, feats.data(), feats.size() * 4, cudaMemcpyHostToDevice, st));
         rank_model_predict_dev(dP, dF, na, dO, st);
         HM_CUDA(cudaMemcpyAsync(pred.data(), dO, na * 4, cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaStreamSynchronize(st));
         free_all(tmp);
-        const float tm = h->opts.rank_model[12], ts = h->opts.rank_model[13];
-        for (int64_t q = 0; q < na; ++q) {
-            const int64_t b = adm[q];
-            const double steps = std::exp((double)pred[q] * ts + tm) - 1.0;
-            const int64_t full = 3 * std::min(pts_of(blk[b].tau), pts_of(blk[b].sigma));
+        const float tm = h0->opts.rank_model[12], ts = h0->opts.rank_model[13];
+        for (int64_t a = 0; a < na; ++a) {
+            const double steps = std::exp((double)pred[a] * ts + tm) - 1.0;
+            const int64_t full = 3 * std::min(pts_of(a, blk_of(a).tau), pts_of(a, blk_of(a).sigma));
             int64_t c = 3 * (int64_t)std::ceil(1.25 * std::max(steps, 0.0) + 2.0);
             if (!std::isfinite(steps)) c = cap0;
-            cap[b] = (int)std::max<int64_t>(3, std::min<int64_t>({c, full, 768}));
+            cap[a] = (int)std::max<int64_t>(3, std::min<int64_t>({c, full, 768}));
         }
         // bin blocks of similar predicted rank into the same batches
         std::stable_sort(adm.begin(), adm.end(), [&](int64_t a, int64_t b) {
             if (cap[a] != cap[b]) return cap[a] > cap[b];
-            return pts_of(blk[a].tau) + pts_of(blk[a].sigma) > pts_of(blk[b].tau) + pts_of(blk[b].sigma);
+            return size_of(a) > size_of(b);
         });
-        h->used_rank_model = 1;
+        used_model = 1;
     }
+    // points, normals and Green parameters: the problem's own, or all problems
+    // concatenated (job point offsets become global, J.pad_ names the problem)
+    std::vector<int64_t> poff(nprob, 0);
+    const double* d_pts = h0->d_pts_p;
+    const double* d_nrm = h0->d_nrm_p;
+    const GreenParams* d_gps = nullptr;
+    std::vector<DevBuf> batchbuf;
+    if (nprob > 1) {
+        int64_t tot = 0;
+        bool any_nrm = false, any_w = false;
+        for (int q = 0; q < nprob; ++q) {
+            poff[q] = tot;
+            tot += hs[q]->nc;
+            any_nrm = any_nrm || hs[q]->d_nrm_p;
+            any_w = any_w || hs[q]->gp.w;
+        }
+        double* pa = (double*)hm_dmalloc(batchbuf, 24 * tot, st, false);
+        double* na3 = any_nrm ? (double*)hm_dmalloc(batchbuf, 24 * tot, st, true) : nullptr;
+        double* wa = any_w ? (double*)hm_dmalloc(batchbuf, 8 * tot, st, false) : nullptr;
+        std::vector<GreenParams> gps(nprob);
+        for (int q = 0; q < nprob; ++q) {
+            HM_CUDA(cudaMemcpyAsync(pa + 3 * poff[q], hs[q]->d_pts_p, 24 * hs[q]->nc, cudaMemcpyDeviceToDevice, st));
+            if (hs[q]->d_nrm_p)
+                HM_CUDA(cudaMemcpyAsync(na3 + 3 * poff[q], hs[q]->d_nrm_p, 24 * hs[q]->nc,
+                                        cudaMemcpyDeviceToDevice, st));
+            gps[q] = hs[q]->gp;
+            if (hs[q]->gp.w) {
+                HM_CUDA(cudaMemcpyAsync(wa + poff[q], hs[q]->gp.w, 8 * hs[q]->nc, cudaMemcpyDeviceToDevice, st));
+                gps[q].w = wa;  // indexed by the global point index
+            }
+        }
+        GreenParams* dg = (GreenParams*)hm_dmalloc(batchbuf, nprob * sizeof(GreenParams), st, false);
+        HM_CUDA(cudaMemcpyAsync(dg, gps.data(), nprob * sizeof(GreenParams), cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        d_pts = pa;
+        d_nrm = na3;
+        d_gps = dg;
+    }
+    double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0;
+    int64_t batches = 0, reruns = 0, ws_peak = 0, ws_tot = 0;
     int* d_counter = (int*)hm_dmalloc(staging, sizeof(int), st, true);
     std::vector<int64_t> todo = adm;
+    try {
     while (!todo.empty()) {
         std::vector<int64_t> overflow;
         size_t pos = 0;
@@ -163,32 +218,33 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             int64_t woff = 0, goff = 0, maxm = 1, maxn = 1;
             int capmax = 3;
             while (pos < todo.size()) {
-                const int64_t b = todo[pos];
-                const int64_t m = pts_of(blk[b].tau), n = pts_of(blk[b].sigma);
-                const int64_t need = (3 * (m + n) * (int64_t)cap[b] + 2 * (int64_t)cap[b] * cap[b]) * 16;
+                const int64_t a = todo[pos];
+                const hm_block& bk = blk_of(a);
+                const int64_t m = pts_of(a, bk.tau), n = pts_of(a, bk.sigma);
+                const int64_t need = (3 * (m + n) * (int64_t)cap[a] + 2 * (int64_t)cap[a] * cap[a]) * 16;
                 if (!jobs.empty() && (woff + goff) * 16 + need > budget) break;
                 AcaJob J;
-                J.tau_begin = cl[blk[b].tau].begin;
+                J.tau_begin = poff[aq[a]] + cl_of(a, bk.tau).begin;
                 J.m = m;
-                J.sig_begin = cl[blk[b].sigma].begin;
+                J.sig_begin = poff[aq[a]] + cl_of(a, bk.sigma).begin;
                 J.n = n;
                 J.u_off = woff;
-                J.v_off = woff + 3 * m * cap[b];
+                J.v_off = woff + 3 * m * cap[a];
                 J.g_off = goff;
-                J.cap = cap[b];
-                J.pad_ = 0;
-                woff += 3 * (m + n) * cap[b];
-                goff += 2 * (int64_t)cap[b] * cap[b];
+                J.cap = cap[a];
+                J.pad_ = aq[a];
+                woff += 3 * (m + n) * cap[a];
+                goff += 2 * (int64_t)cap[a] * cap[a];
                 maxm = std::max(maxm, m);
                 maxn = std::max(maxn, n);
-                capmax = std::max(capmax, cap[b]);
+                capmax = std::max(capmax, cap[a]);
                 jobs.push_back(J);
-                ids.push_back(b);
+                ids.push_back(a);
                 ++pos;
             }
             const int64_t nj = (int64_t)jobs.size();
-            h->aca_workspace_peak = std::max<int64_t>(h->aca_workspace_peak, (woff + goff) * 16);
-            h->aca_workspace_total += (woff + goff) * 16;
+            ws_peak = std::max<int64_t>(ws_peak, (woff + goff) * 16);
+            ws_tot += (woff + goff) * 16;
             const int nctas = (int)std::min<int64_t>(nj, (int64_t)nsm * aca_ctas_per_sm(capmax));
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
@@ -203,14 +259,14 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             double2* d_cb = (double2*)hm_dmalloc(tmp, (size_t)nctas * cbs * 16, st, false);
             HM_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nj * sizeof(AcaJob), cudaMemcpyHostToDevice, st));
             EvPair ea(st);
-            launch_aca(h->gp, h->d_pts_p, h->d_nrm_p, d_jobs, nj, d_work, d_gram, d_flags, fstride, d_rb,
-                       d_cb, rbs, cbs, h->eps, d_res, nctas, capmax, d_counter, st);
-            h->ev_aca_ms += ea.stop(st);
+            launch_aca(h0->gp, d_pts, d_nrm, d_jobs, nj, d_work, d_gram, d_flags, fstride, d_rb,
+                       d_cb, rbs, cbs, h0->eps, d_res, nctas, capmax, d_counter, st, d_gps);
+            ev_aca += ea.stop(st);
             std::vector<AcaResult> res(nj);
             HM_CUDA(cudaMemcpyAsync(res.data(), d_res, nj * sizeof(AcaResult), cudaMemcpyDeviceToHost, st));
             HM_CUDA(cudaStreamSynchronize(st));
-            h->t_aca_ms += ms_since(t0);
-            h->aca_batches++;
+            t_aca += ms_since(t0);
+            batches++;
             // ---- recompression of the converged jobs ----
             t0 = clk::now();
             std::vector<int64_t> uo, vo, m3, n3, keep, go;
@@ -219,17 +275,17 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                 if (res[j].status == 2)
                     hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA of a block");
                 if (res[j].status == 1) {
-                    const int64_t b = ids[j];
+                    const int64_t a = ids[j];
                     const int64_t full = 3 * std::min(jobs[j].m, jobs[j].n);
-                    const int nc2 = (int)std::min<int64_t>({full, 2 * (int64_t)cap[b], 768});
-                    if (nc2 <= cap[b]) hm_throw(HM_ERR_UNSUPPORTED, "ACA rank above 768 columns");
-                    cap[b] = nc2;
-                    overflow.push_back(b);
+                    const int nc2 = (int)std::min<int64_t>({full, 2 * (int64_t)cap[a], 768});
+                    if (nc2 <= cap[a]) hm_throw(HM_ERR_UNSUPPORTED, "ACA rank above 768 columns");
+                    cap[a] = nc2;
+                    overflow.push_back(a);
                     continue;
                 }
                 {
                     const double K = res[j].k / 3, mn = (double)(jobs[j].m + jobs[j].n);
-                    h->aca_flops += 8.0 * 18.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
+                    flops += 8.0 * 18.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
                 }
                 keep.push_back(j);
                 uo.push_back(jobs[j].u_off);
@@ -243,8 +299,8 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             std::vector<int32_t> ranks;
             std::vector<int64_t> soff;
             EvPair er(st);
-            void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h->opts.recompress,
-                                       d_work, h->eps, ranks, soff, st);
+            void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h0->opts.recompress,
+                                       d_work, h0->eps, ranks, soff, st);
             try {
                 // staging for this batch: FP32 U' (3m x r'), V' (3n x r')
                 int64_t tot = 0;
@@ -272,13 +328,14 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
                     }
                 }
                 recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_stage, st);
-                h->ev_recomp_ms += er.stop(st);
+                ev_rec += er.stop(st);
                 for (size_t q = 0; q < keep.size(); ++q) {
-                    const int64_t b = ids[keep[q]];
-                    blk[b].rank_aca = kk[q];
-                    blk[b].rank = ranks[q];
-                    su[b] = d_stage + so[q];
-                    sv[b] = d_stage + so[q] + m3[q] * ranks[q];
+                    const int64_t a = ids[keep[q]];
+                    hm_block& bk = blk_of(a);
+                    bk.rank_aca = kk[q];
+                    bk.rank = ranks[q];
+                    su[aq[a]][ab[a]] = d_stage + so[q];
+                    sv[aq[a]][ab[a]] = d_stage + so[q] + m3[q] * ranks[q];
                 }
                 HM_CUDA(cudaStreamSynchronize(st));
             } catch (...) {
@@ -288,10 +345,29 @@ void build_low_rank(hm_matrix* h, std::vector<DevBuf>& staging, std::vector<cons
             recompress_release(rb, st);
             HM_CUDA(cudaStreamSynchronize(st));
             free_all(tmp);
-            h->t_recomp_ms += ms_since(t0);
+            t_rec += ms_since(t0);
         }
-        h->aca_overflow_reruns += (int64_t)overflow.size();
+        reruns += (int64_t)overflow.size();
         todo.swap(overflow);
+    }
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        free_all(batchbuf);
+        throw;
+    }
+    free_all(batchbuf);
+    for (hm_matrix* h : hs) {  // a batch reports the shared launches in every handle
+        h->ev_aca_ms += ev_aca;
+        h->t_aca_ms += t_aca;
+        h->ev_recomp_ms += ev_rec;
+        h->t_recomp_ms += t_rec;
+        h->aca_flops += flops;
+        h->aca_batches += batches;
+        h->aca_overflow_reruns += reruns;
+        h->aca_workspace_peak = std::max(h->aca_workspace_peak, ws_peak);
+        h->aca_workspace_total += ws_tot;
+        h->used_rank_model = used_model;
+        h->batch_problems = nprob;
     }
 }
 
@@ -330,46 +406,27 @@ void rank_features(const hm_cluster& t, const hm_cluster& s, double ks, double k
     f[5] = (float)std::log10(eps);
 }
 
-extern "C" {
-
-void hm_opts_default(hm_opts* o) {
-    if (!o) return;
-    std::memset(o, 0, sizeof(*o));
-    o->storage = HM_STORE_FP32;
-    o->aca_fp32 = 0;
-    o->diag_value = 1.0;
-    o->fp64_switch_ksr = INFINITY;
-    o->recompress = 1;
-    o->aca_max_rank = 0;
-    o->workspace_bytes = 0;
-    o->verbose = 0;
-    o->weights = nullptr;
-    o->rank_model = nullptr;
-}
-
-const char* hm_status_string(hm_status s) {
-    switch (s) {
-        case HM_OK: return "ok";
-        case HM_ERR_ARG: return "invalid argument";
-        case HM_ERR_CUDA: return "CUDA error";
-        case HM_ERR_OOM: return "out of device memory";
-        case HM_ERR_NOCONV: return "GMRES did not converge";
-        case HM_ERR_TIMEOUT: return "device wait timed out";
-        case HM_ERR_NUMERIC: return "non-finite value";
-        case HM_ERR_UNSUPPORTED: return "unsupported configuration";
+// Validation, handle, points, tree, weights, normals and partition of one
+// problem (everything before the low-rank blocks).  The handle is owned by
+// `hold` until the caller releases it.
+struct HandleHold {
+    hm_matrix* p = nullptr;
+    void reset(hm_matrix* h) { p = h; }
+    hm_matrix* release() {
+        hm_matrix* h = p;
+        p = nullptr;
+        return h;
     }
-    return "unknown status";
-}
+    ~HandleHold() {
+        if (p) hm_free(p);
+    }
+};
 
-const char* hm_last_error(void) { return g_last_error.c_str(); }
-
-hm_status hm_build(const double* points, const double* normals, int64_t n_c, double rho,
-                   double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
-                   int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out) {
-    if (out) *out = nullptr;
-    hm_matrix* h = nullptr;
-    HM_API_BEGIN
-    if (!out || !points || n_c < 1) hm_throw(HM_ERR_ARG, "null pointer or n_c < 1");
+hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c, double rho,
+                       double lambda, double mu, double omega, int32_t kernel, double eps,
+                       double eta, int64_t leaf_size, const hm_opts* opts, cudaStream_t st,
+                       HandleHold& hold) {
+    if (!points || n_c < 1) hm_throw(HM_ERR_ARG, "null pointer or n_c < 1");
     if (!(rho > 0) || !(mu > 0) || !(omega > 0) || !std::isfinite(rho) || !std::isfinite(mu) ||
         !std::isfinite(omega) || !std::isfinite(lambda) || !(lambda + 2 * mu > 0))
         hm_throw(HM_ERR_ARG, "material parameters must be finite with rho, mu, omega > 0");
@@ -388,9 +445,8 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
     if (o.storage != HM_STORE_FP32 && o.storage != HM_STORE_BF16)
         hm_throw(HM_ERR_ARG, "unknown storage type");
     if (!std::isfinite(o.diag_value)) hm_throw(HM_ERR_ARG, "non-finite diag_value");
-    cudaStream_t st = (cudaStream_t)stream;
-    const auto t_all = clk::now();
-    h = new hm_matrix();
+    hm_matrix* h = new hm_matrix();
+    hold.reset(h);
     h->nc = n_c;
     h->kernel = kernel;
     h->rho = rho;
@@ -440,60 +496,146 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
     t0 = clk::now();
     h->blocks = build_partition(h->clusters, eta, st);
     h->t_part_ms = ms_since(t0);
-    // ---- low-rank blocks ----
+    return h;
+}
+
+// Storage plan, arena, near field, factor chunks (BF16 copy) and work vectors
+// once the low-rank factors of the problem are staged.
+void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<const float2*>& sv,
+                  cudaStream_t st) {
+    const hm_opts& o = h->opts;
+    auto t0 = clk::now();
+    std::vector<int64_t> t_off;
+    h->plan = build_matvec_plan(h->clusters, h->blocks, t_off);
+    h->mv = matvec_dev_create(h->plan, o.storage, h->owner, st);
+    auto tn = clk::now();
+    assemble_dense(h->gp, h->d_pts_p, h->d_nrm_p, h->plan, h->blocks, h->clusters, h->mv, h->owner,
+                   st);
+    HM_CUDA(cudaStreamSynchronize(st));
+    h->t_near_ms = ms_since(tn);
+    copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
+    h->t_copy_ms = ms_since(t0) - h->t_near_ms;
+    h->d_xp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
+    h->d_yp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
+    HM_CUDA(cudaStreamSynchronize(st));
+}
+
+void report_build(const hm_matrix* h) {
+    if (h->opts.verbose)
+        std::fprintf(stderr,
+                     "[hm] n_c=%lld blocks=%zu tree=%.1fms part=%.1fms aca=%.1fms recomp=%.1fms "
+                     "near=%.1fms copy=%.1fms total=%.1fms\n",
+                     (long long)h->nc, h->blocks.size(), h->t_tree_ms, h->t_part_ms, h->t_aca_ms,
+                     h->t_recomp_ms, h->t_near_ms, h->t_copy_ms, h->t_total_ms);
+}
+
+extern "C" {
+
+void hm_opts_default(hm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->storage = HM_STORE_FP32;
+    o->aca_fp32 = 0;
+    o->diag_value = 1.0;
+    o->fp64_switch_ksr = INFINITY;
+    o->recompress = 1;
+    o->aca_max_rank = 0;
+    o->workspace_bytes = 0;
+    o->verbose = 0;
+    o->weights = nullptr;
+    o->rank_model = nullptr;
+}
+
+const char* hm_status_string(hm_status s) {
+    switch (s) {
+        case HM_OK: return "ok";
+        case HM_ERR_ARG: return "invalid argument";
+        case HM_ERR_CUDA: return "CUDA error";
+        case HM_ERR_OOM: return "out of device memory";
+        case HM_ERR_NOCONV: return "GMRES did not converge";
+        case HM_ERR_TIMEOUT: return "device wait timed out";
+        case HM_ERR_NUMERIC: return "non-finite value";
+        case HM_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* hm_last_error(void) { return g_last_error.c_str(); }
+
+hm_status hm_build(const double* points, const double* normals, int64_t n_c, double rho,
+                   double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
+                   int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out) {
+    if (out) *out = nullptr;
+    HM_API_BEGIN
+    if (!out) hm_throw(HM_ERR_ARG, "null output handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t_all = clk::now();
+    HandleHold hold;
+    hm_matrix* h = build_setup(points, normals, n_c, rho, lambda, mu, omega, kernel, eps, eta,
+                               leaf_size, opts, st, hold);
+    std::vector<hm_matrix*> hs{h};
     std::vector<DevBuf> staging;
-    std::vector<const float2*> su(h->blocks.size(), nullptr), sv(h->blocks.size(), nullptr);
+    std::vector<std::vector<const float2*>> su(1), sv(1);
+    su[0].assign(h->blocks.size(), nullptr);
+    sv[0].assign(h->blocks.size(), nullptr);
     try {
-        build_low_rank(h, staging, su, sv, st);
-        // ---- storage plan, arena, near field, factor chunks ----
-        t0 = clk::now();
-        std::vector<int64_t> t_off;
-        h->plan = build_matvec_plan(h->clusters, h->blocks, t_off);
-        h->mv = matvec_dev_create(h->plan, o.storage, h->owner, st);
-        auto tn = clk::now();
-        assemble_dense(h->gp, h->d_pts_p, h->d_nrm_p, h->plan, h->blocks, h->clusters, h->mv,
-                       h->owner, st);
-        HM_CUDA(cudaStreamSynchronize(st));
-        h->t_near_ms = ms_since(tn);
-        copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
-        HM_CUDA(cudaStreamSynchronize(st));
-        if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
-        h->t_copy_ms = ms_since(t0) - h->t_near_ms;
+        build_low_rank(hs, staging, su, sv, st);
+        build_finish(h, su[0], sv[0], st);
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(staging);
         throw;
     }
     free_all(staging);
-    h->d_xp = (float2*)hm_dmalloc(h->owner, 8 * 3 * n_c, st, true);
-    h->d_yp = (float2*)hm_dmalloc(h->owner, 8 * 3 * n_c, st, true);
-    HM_CUDA(cudaStreamSynchronize(st));
     h->t_total_ms = ms_since(t_all);
-    if (o.verbose)
-        std::fprintf(stderr,
-                     "[hm] n_c=%lld blocks=%zu tree=%.1fms part=%.1fms aca=%.1fms recomp=%.1fms "
-                     "near=%.1fms copy=%.1fms total=%.1fms\n",
-                     (long long)n_c, h->blocks.size(), h->t_tree_ms, h->t_part_ms, h->t_aca_ms,
-                     h->t_recomp_ms, h->t_near_ms, h->t_copy_ms, h->t_total_ms);
-    *out = h;
-    h = nullptr;
+    report_build(h);
+    *out = hold.release();
+    HM_API_END
+}
+
+hm_status hm_build_batch(int32_t nprob, const hm_problem* probs, double eps, const hm_opts* opts,
+                         void* stream, hm_handle* out) {
+    if (out && nprob > 0)
+        for (int32_t q = 0; q < nprob; ++q) out[q] = nullptr;
+    HM_API_BEGIN
+    if (!out || !probs || nprob < 1) hm_throw(HM_ERR_ARG, "null pointer or nprob < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t_all = clk::now();
+    std::vector<HandleHold> hold(nprob);
+    std::vector<hm_matrix*> hs(nprob);
+    hm_opts o;
+    hm_opts_default(&o);
+    if (opts) o = *opts;
+    for (int32_t q = 0; q < nprob; ++q) {
+        const hm_problem& P = probs[q];
+        o.weights = P.weights;
+        hs[q] = build_setup(P.points, P.normals, P.n_c, P.rho, P.lambda, P.mu, P.omega, P.kernel,
+                            eps, P.eta, P.leaf_size, &o, st, hold[q]);
     }
-    catch (const hm_error& e) {
-        hm_set_error(e.msg);
-        if (h) hm_free(h);
-        return e.st;
+    std::vector<DevBuf> staging;
+    std::vector<std::vector<const float2*>> su(nprob), sv(nprob);
+    for (int32_t q = 0; q < nprob; ++q) {
+        su[q].assign(hs[q]->blocks.size(), nullptr);
+        sv[q].assign(hs[q]->blocks.size(), nullptr);
     }
-    catch (const std::bad_alloc&) {
-        hm_set_error("host allocation failed");
-        if (h) hm_free(h);
-        return HM_ERR_OOM;
+    try {
+        build_low_rank(hs, staging, su, sv, st);
+        for (int32_t q = 0; q < nprob; ++q) build_finish(hs[q], su[q], sv[q], st);
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        free_all(staging);
+        throw;
     }
-    catch (...) {
-        hm_set_error("unexpected internal error");
-        if (h) hm_free(h);
-        return HM_ERR_CUDA;
+    free_all(staging);
+    const double tot = ms_since(t_all);
+    for (int32_t q = 0; q < nprob; ++q) {
+        hs[q]->t_total_ms = tot;
+        report_build(hs[q]);
     }
-    return HM_OK;
+    for (int32_t q = 0; q < nprob; ++q) out[q] = hold[q].release();
+    HM_API_END
 }
 
 hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream) {
@@ -564,6 +706,34 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
     HM_API_END
 }
 
+hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int32_t restart,
+                         double tol, int32_t maxit, int32_t* iters, double* relres, void* stream) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (!b || !x || nrhs < 1 || restart < 1 || restart > 500 || !(tol > 0) || maxit < 1)
+        hm_throw(HM_ERR_ARG, "invalid GMRES arguments (restart must be in 1..500)");
+    const int64_t bytes = 3 * h->nc * (int64_t)nrhs * 16;
+    const char* bb = (const char*)b;
+    const char* xb = (const char*)x;
+    if (bb < xb + bytes && xb < bb + bytes) hm_throw(HM_ERR_ARG, "b and x overlap");
+    std::vector<GmresResult> R;
+    gmres_solve_multi(h, nrhs, (const double2*)b, (double2*)x, restart, tol, maxit, R,
+                      (cudaStream_t)stream);
+    bool all = true;
+    for (int32_t s = 0; s < nrhs; ++s) {
+        if (iters) iters[s] = R[s].iters;
+        if (relres) relres[s] = R[s].relres;
+        all = all && R[s].converged;
+    }
+    if (matvec_take_error(h->mv, (cudaStream_t)stream))
+        hm_throw(HM_ERR_TIMEOUT, "a product kernel gave up waiting for its copies");
+    if (!all) {
+        hm_set_error("GMRES reached maxit above the tolerance for some right-hand side");
+        return HM_ERR_NOCONV;
+    }
+    HM_API_END
+}
+
 hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
@@ -611,6 +781,7 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"aca_workspace_peak_bytes\": " << h->aca_workspace_peak
        << ", \"aca_workspace_total_bytes\": " << h->aca_workspace_total
        << ", \"rank_model\": " << h->used_rank_model
+       << ", \"batch_problems\": " << h->batch_problems
        << ", \"ms\": {\"tree\": " << h->t_tree_ms << ", \"partition\": " << h->t_part_ms
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms

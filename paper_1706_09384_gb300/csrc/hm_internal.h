@@ -153,7 +153,7 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                 unsigned char* d_flags,
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
-                int* d_counter, cudaStream_t st);
+                int* d_counter, cudaStream_t st, const GreenParams* d_gps = nullptr);
 int aca_ctas_per_sm(int capmax);
 // Core of the recompression for a batch: ranks r' and the k x r' transforms.
 // g_off[j] >= 0: the job's Gram matrices (ld g_ld[j]) are read from d_gram instead of
@@ -191,6 +191,9 @@ struct GmresResult {
 struct hm_matrix;
 GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int restart, double tol,
                         int maxit, cudaStream_t st);
+// nrhs right-hand sides in lockstep (b, x: 3 nc x nrhs column-major, device)
+void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* b, double2* x, int restart, double tol,
+                       int maxit, std::vector<GmresResult>& out, cudaStream_t st);
 
 // ---------------- the handle ----------------
 struct hm_matrix {
@@ -233,5 +236,6 @@ struct hm_matrix {
     double aca_flops = 0;
     int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
     int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
+    int batch_problems = 1;          // problems that shared the ACA / recompression launches
     int used_rank_model = 0;
 };

@@ -286,30 +286,52 @@ __global__ void __launch_bounds__(P2_THREADS, 2) mvm_phase2(const WorkItem* item
             for (int e = 0; e < 4; ++e) acc[i][q][e] = 0.f;
     const int ncol = S.ncol;
     const int nst = (ncol + P2_G - 1) / P2_G;
+    // weights of stage k: loaded into registers one stage ahead (the L2
+    // latency hides behind the MMAs of the stage before), converted and stored
+    // into the double-buffered table after those MMAs
+    constexpr int WPW = P2_G / P2_CONS;  // columns per warp per stage
+    float2 wv[WPW];
+    float wsc[WPW];
+    auto load_w = [&](int k) {
+#pragma unroll
+        for (int c = 0; c < WPW; ++c) {
+            const int jj = warp + c * P2_CONS;
+            const int j = k * P2_G + jj;
+            wv[c] = make_float2(0.f, 0.f);
+            wsc[c] = 0.f;
+            if (k < nst && j < ncol) {
+                const float2 ci = S.cinfo[j];
+                const uint32_t code = __float_as_uint(ci.x);
+                const float2* src = (code & 0x80000000u) ? T : X;
+                wv[c] = __ldg(src + (int64_t)(code & 0x7fffffffu) * NR + lane);
+                wsc[c] = ci.y;
+            }
+        }
+    };
+    auto store_w = [&](int k) {
+        uint32_t* wt = S.wt[k & 1];
+#pragma unroll
+        for (int c = 0; c < WPW; ++c) {
+            const int jj = warp + c * P2_CONS;
+            const float wr = wv[c].x * wsc[c], wi = wv[c].y * wsc[c];
+            *reinterpret_cast<uint2*>(wt + jj * P2_WLD + 2 * lane) =
+                make_uint2(pack_bf16(wr, -wi), pack_bf16(wi, wr));
+        }
+    };
+    load_w(0);
+    store_w(0);
     for (int k = 0; k < nst; ++k) {
         const int s = k % P2_NSTAGE;
         const int jb = k * P2_G;
         const int gk = min(P2_G, ncol - jb);
-        uint32_t* wt = S.wt[k & 1];
-        // weights of this stage's columns (zero beyond the last column)
-        for (int jj = warp; jj < P2_G; jj += P2_CONS) {
-            uint2 pq = make_uint2(0u, 0u);
-            if (jj < gk) {
-                const float2 ci = S.cinfo[jb + jj];
-                const uint32_t code = __float_as_uint(ci.x);
-                const float2* src = (code & 0x80000000u) ? T : X;
-                const float2 v = __ldg(src + (int64_t)(code & 0x7fffffffu) * NR + lane);
-                const float wr = v.x * ci.y, wi = v.y * ci.y;
-                pq = make_uint2(pack_bf16(wr, -wi), pack_bf16(wi, wr));
-            }
-            *reinterpret_cast<uint2*>(wt + jj * P2_WLD + 2 * lane) = pq;
-        }
         if (!mbar_wait(&S.full[s], (k / P2_NSTAGE) & 1)) {
             atomicExch(err, MV_ERR_TIMEOUT);
             *(volatile int32_t*)&S.abort = 1;
         }
-        named_sync<1, 32 * P2_CONS>();  // weights of stage k visible to every warp
+        named_sync<1, 32 * P2_CONS>();  // weights of stage k visible; stage k-1 done everywhere
         if (*(volatile int32_t*)&S.abort) break;  // same decision in every consumer warp
+        load_w(k + 1);
+        const uint32_t* wt = S.wt[k & 1];
         const uint32_t* sb = S.stage[s];
 #pragma unroll
         for (int ks = 0; ks < P2_G / 8; ++ks) {
@@ -339,6 +361,7 @@ __global__ void __launch_bounds__(P2_THREADS, 2) mvm_phase2(const WorkItem* item
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);
+        if (k + 1 < nst) store_w(k + 1);
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {

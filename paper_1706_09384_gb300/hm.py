@@ -35,6 +35,13 @@ class hm_opts(C.Structure):
                 ("rank_model", C.c_void_p), ("reserved", C.c_int32 * 2)]
 
 
+class hm_problem(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("normals", C.c_void_p), ("n_c", C.c_int64),
+                ("rho", C.c_double), ("lambda_", C.c_double), ("mu", C.c_double),
+                ("omega", C.c_double), ("kernel", C.c_int32), ("pad_", C.c_int32),
+                ("eta", C.c_double), ("leaf_size", C.c_int64), ("weights", C.c_void_p)]
+
+
 class hm_cluster(C.Structure):
     _fields_ = [("begin", C.c_int64), ("end", C.c_int64), ("child0", C.c_int64),
                 ("child1", C.c_int64), ("level", C.c_int32), ("is_leaf", C.c_int32),
@@ -58,9 +65,11 @@ _P, _I64, _I32, _D, _SZ = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_size
 SIGNATURES = {
     "hm_opts_default": (None, [_P]),
     "hm_build": (_I32, [_P, _P, _I64, _D, _D, _D, _D, _I32, _D, _D, _I64, _P, _P, _P]),
+    "hm_build_batch": (_I32, [_I32, _P, _D, _P, _P, _P]),
     "hm_matvec": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_matvec_host": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_gmres": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
+    "hm_gmres_multi": (_I32, [_P, _I32, _P, _P, _I32, C.c_double, _I32, _P, _P, _P]),
     "hm_stats": (_I32, [_P, C.c_char_p, _SZ, _P]),
     "hm_sizes": (_I32, [_P, _P, _P, _P]),
     "hm_get_tree": (_I32, [_P, _P, _P]),
@@ -196,6 +205,38 @@ class HMatrix:
         return cls(h, pts.shape[0])
 
     @classmethod
+    def build_batch(cls, problems, eps=1e-4, opts=None, stream=None):
+        """Several problems in one batch build.  problems: list of dicts with
+        keys points, normals (or None), rho, lam, mu, omega, kernel ("U"/"T"),
+        eta, leaf_size, weights (or None).  Returns a list of HMatrix."""
+        keep = []
+        arr = (hm_problem * len(problems))()
+        for q, P in enumerate(problems):
+            pts = np.ascontiguousarray(P["points"], dtype=np.float64)
+            nrm = P.get("normals")
+            nrm = np.ascontiguousarray(nrm, dtype=np.float64) if nrm is not None else None
+            w = P.get("weights")
+            w = np.ascontiguousarray(w, dtype=np.float64) if w is not None else None
+            keep += [pts, nrm, w]
+            k = P.get("kernel", "U")
+            a = arr[q]
+            a.points = pts.ctypes.data
+            a.normals = nrm.ctypes.data if nrm is not None else None
+            a.n_c = pts.shape[0]
+            a.rho, a.lambda_, a.mu, a.omega = P["rho"], P["lam"], P["mu"], P["omega"]
+            a.kernel = {"U": HM_KERNEL_U, "T": HM_KERNEL_T}[k] if isinstance(k, str) else k
+            a.pad_ = 0
+            a.eta = P.get("eta", 3.0)
+            a.leaf_size = P.get("leaf_size", 32)
+            a.weights = w.ctypes.data if w is not None else None
+        hs = (C.c_void_p * len(problems))()
+        st = lib().hm_build_batch(len(problems), arr, eps,
+                                  C.byref(opts) if opts is not None else None,
+                                  _stream_ptr(stream), hs)
+        _check(st, "hm_build_batch")
+        return [cls(C.c_void_p(hs[q]), arr[q].n_c) for q in range(len(problems))]
+
+    @classmethod
     def import_(cls, n_c, perm, clusters, blocks, data, opts=None, stream=None):
         perm = np.ascontiguousarray(perm, np.int64)
         clusters = np.ascontiguousarray(clusters, CLUSTER_DTYPE)
@@ -256,6 +297,24 @@ class HMatrix:
         if check and st != HM_ERR_NOCONV:
             _check(st, "hm_gmres")
         return x, it.value, rr.value, st
+
+    def gmres_multi(self, B, X=None, restart=50, tol=1e-6, maxit=1000, stream=None, check=True):
+        """Lockstep GMRES for the columns of cuda complex128 B (3 n_c, nrhs).
+        Returns (X, iters[nrhs], relres[nrhs], status)."""
+        import torch
+        nrhs = B.shape[1]
+        Bc = B.t().contiguous()
+        Xc = torch.zeros_like(Bc)
+        it = np.zeros(nrhs, np.int32)
+        rr = np.zeros(nrhs, np.float64)
+        st = lib().hm_gmres_multi(self.h, nrhs, Bc.data_ptr(), Xc.data_ptr(), restart, tol, maxit,
+                                  _np_ptr(it), _np_ptr(rr), _stream_ptr(stream))
+        if check and st != HM_ERR_NOCONV:
+            _check(st, "hm_gmres_multi")
+        if X is None:
+            X = torch.empty_like(B)
+        X.copy_(Xc.t())
+        return X, it, rr, st
 
     def profile_matvec(self, reps=10, stream=None):
         """Average per-kernel device times (ms) of the product and its algorithmic bytes."""

@@ -116,3 +116,50 @@ def test_block_profile_reports_kernels(hm):
     assert hm.hm_kernel_launches() - before >= 4 * 4
     assert p["bytes"] > H16.stats()["stored_bytes"]
     assert all(v > 0 for v in p["ms"].values())
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp32"])
+def test_gmres_multi_matches_single(hm, storage):
+    """Lockstep GMRES for 33 columns (two blocks of the tensor-core product with
+    BF16 storage; one product per column with FP32 storage): every column
+    converges and agrees with the one-column solver on FP32 storage."""
+    nc = 4000
+    pts = inputs.fibonacci_sphere(nc)
+    H32, H16 = build_pair(hm, pts, None, 8.0, "U", 32)
+    H = H16 if storage == "bf16" else H32
+    nrhs = 33 if storage == "bf16" else 3
+    B = inputs.random_rhs(3 * nc, nrhs, seed=11)
+    X, it, rr, st = H.gmres_multi(cuda(B), restart=50, tol=1e-6, maxit=500)
+    assert st == 0 and (rr <= 1e-6).all() and (it > 0).all()
+    X = X.cpu().numpy()
+    for s in sorted({0, min(5, nrhs - 1), nrhs - 1}):
+        xs, its, rrs, sts = H32.gmres(cuda(B[:, s]), restart=50, tol=1e-6, maxit=500)
+        xs = xs.cpu().numpy()
+        assert sts == 0
+        assert np.linalg.norm(X[:, s] - xs) <= 1e-5 * np.linalg.norm(xs), s
+        r = B[:, s] - H32.matvec(cuda(X[:, s])).cpu().numpy()
+        assert np.linalg.norm(r) <= 2e-6 * np.linalg.norm(B[:, s])
+
+
+def test_gmres_multi_plane_waves_T_vs_oracle(hm, oracle):
+    """Scaled-down precision + multi-RHS workload: T kernel with outward
+    normals, 32 plane-wave right-hand sides, BF16 tensor-core products inside
+    GMRES with FP64 refinement; solutions against the FP64 oracle's GMRES on its
+    own H-matrix, per right-hand side."""
+    nc = 2500
+    pts = inputs.fibonacci_sphere(nc)
+    nrm = inputs.sphere_normals(pts)
+    ks = 8.0
+    _, H16 = build_pair(hm, pts, nrm, ks, "T", 32)
+    B = inputs.plane_wave_rhs(pts, ks / 2, ks, 32, seed=0)
+    X, it, rr, st = H16.gmres_multi(cuda(B), restart=50, tol=1e-8, maxit=1000)
+    assert st == 0 and (rr <= 1e-8).all()
+    X = X.cpu().numpy()
+    rho, lam, mu, om = inputs.material(ks)
+    pb = oracle.problem(rho, lam, mu, om, "T", 1.0, np.full(nc, 4 * np.pi / nc))
+    Ho = oracle.HMatrix(pb, pts, nrm, eps=EPS, eta=3.0, leaf=32)
+    for s in (0, 1, 30, 31):
+        xo, ito, rro, sto = Ho.gmres(B[:, s], restart=50, tol=1e-10, maxit=2000)
+        assert sto == 0
+        # the GPU operator carries FP32-stored entries: relative distance ~1e-7 x condition
+        assert np.linalg.norm(X[:, s] - xo) <= 1e-5 * np.linalg.norm(xo), s
