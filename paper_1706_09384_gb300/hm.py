@@ -168,6 +168,7 @@ def hm_green_eval(kernel, rho, lam, mu, omega, x, y, ny=None, diag_value=1.0, st
 
 
 HM_NOALLOC_MAX_POINTS = 8192
+HM_NRHS_BLOCK = 32  # right-hand sides per tensor-core block product (include/hm.h)
 HM_RANK_MODEL_PARAMS = 4687
 
 

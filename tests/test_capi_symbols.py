@@ -66,3 +66,26 @@ def test_argument_errors_without_gpu():
     assert st == hm.HM_ERR_ARG
     assert b"non-finite" in L.hm_last_error()
     assert L.hm_matvec(None, 1, None, None, None) == hm.HM_ERR_ARG
+
+
+def test_binding_constants_match_header():
+    """Every #define of include/hm.h that the binding mirrors has the same value,
+    and the binding's structures have the header's sizes (checked field by field
+    through the offsets the C compiler would give: all fields are 8-byte or
+    4-byte scalars in declaration order)."""
+    from paper_1706_09384_gb300 import hm
+    text = open(os.path.join(ROOT, "include", "hm.h")).read()
+    defines = dict(re.findall(r"#define\s+(HM_[A-Z0-9_]+)\s+(\d+)", text))
+    for name in ("HM_NOALLOC_MAX_POINTS", "HM_RANK_MODEL_PARAMS", "HM_NRHS_BLOCK"):
+        assert name in defines, name
+        assert getattr(hm, name) == int(defines[name]), name
+    # points, normals, n_c | rho, lambda, mu, omega | kernel, pad_ | eta, leaf_size, weights
+    assert ctypes.sizeof(hm.hm_problem) == 3 * 8 + 4 * 8 + 2 * 4 + 3 * 8
+
+
+def test_batch_argument_errors_without_gpu():
+    from paper_1706_09384_gb300 import hm
+    L = hm.lib()
+    outs = (ctypes.c_void_p * 2)()
+    assert L.hm_build_batch(0, None, 1e-4, None, None, outs) == hm.HM_ERR_ARG
+    assert L.hm_gmres_multi(None, 2, None, None, 50, 1e-6, 100, None, None, None) == hm.HM_ERR_ARG
