@@ -139,13 +139,20 @@ def barrier(world):
 
 
 def max_over_ranks(world, v):
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(world, bytes_per_product, products_per_rank, max_ms):
+    """GB/s of the whole job: the products of all ranks over the slowest rank's time."""
+    return world * bytes_per_product * products_per_rank / (max_ms * 1e-3) / 1e9
 
 
 def cpu_baseline(wl, budget_s=20.0):
@@ -283,7 +290,7 @@ def run_gpu(args, wl, world, rank, local):
     total_ms = max_over_ranks(world, t_start.elapsed_time(t_end))
     mv_total = max_over_ranks(world, sum(mv_ms))
     launches = hm.hm_kernel_launches() - launches0
-    value = world * alg * args.matvecs * args.steps / (mv_total * 1e-3) / 1e9
+    value = whole_job_value(world, alg, args.matvecs * args.steps, mv_total)
     # per-kernel roofline of the product (phase 2), events on the launching stream
     prof = H.profile_matvec(reps=10)
     peak, peak_kind = measured_peaks()

@@ -1,9 +1,10 @@
 // gmres.cu — restarted GMRES(m) on the H-matrix (Sec. 3.1: the H-matvec is
 // the only operation the iterative solver needs).  FP64 vectors on the
 // device.  The Arnoldi products use the fast product (FP32 sums); the true
-// residual at each restart uses the accurate product (FP64 sums over the same
-// stored entries), so each restart cycle is one step of iterative refinement
-// and the solve reaches tolerances below the FP32 summation noise.
+// residual at each restart uses the accurate product (double-float sums of
+// about 44 significant bits over the same stored entries), so each restart
+// cycle is one step of iterative refinement and the solve reaches tolerances
+// below the FP32 summation noise.
 // Arnoldi by classical Gram-Schmidt with one re-orthogonalisation
 // (two passes of h = V^H w, w -= V h); complex Givens rotations and the least
 // squares update run in a one-thread kernel, so the only host traffic per
@@ -338,13 +339,17 @@ GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int m, doubl
             return R;
         }
         int iters = 0;
-        for (;;) {
+        for (bool first = true;; first = false) {
             // r = b - A x with the accurate product (iterative refinement of the
-            // fast FP32 inner iterations), into V_0
-            matvec_accurate(h->mv, h->d_perm, x, xp64, yp64, w, h->nc, st);
-            axpby_kernel<<<nb, GT, 0, st>>>(w, b, 1.0, w, -1.0, n);
-            HM_LAUNCHED();
-            HM_CUDA(cudaGetLastError());
+            // fast FP32 inner iterations), into V_0; r = b for x_0 = 0
+            if (first) {
+                HM_CUDA(cudaMemcpyAsync(w, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            } else {
+                matvec_accurate(h->mv, h->d_perm, x, xp64, yp64, w, h->nc, st);
+                axpby_kernel<<<nb, GT, 0, st>>>(w, b, 1.0, w, -1.0, n);
+                HM_LAUNCHED();
+                HM_CUDA(cudaGetLastError());
+            }
             const double beta2 = nrm2_of(w);
             R.relres = std::sqrt(beta2) / bn;
             if (R.relres <= tol) {
@@ -462,14 +467,19 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
             }
         }
         int iters = 0;
-        for (;;) {
-            // true residuals of the unconverged right-hand sides (accurate products)
+        for (bool first = true;; first = false) {
+            // true residuals of the unconverged right-hand sides (accurate
+            // products; W = A X = 0 for X_0 = 0)
             for (int s = 0; s < nrhs; ++s) act[s] = !out[s].converged;
             upload_act();
-            for (int s = 0; s < nrhs; ++s)
-                if (act[s])
-                    matvec_accurate(h->mv, h->d_perm, X + (int64_t)s * n, xp64, yp64,
-                                    W + (int64_t)s * n, h->nc, st);
+            if (first) {
+                HM_CUDA(cudaMemsetAsync(W, 0, (size_t)n * nrhs * sizeof(double2), st));
+            } else {
+                for (int s = 0; s < nrhs; ++s)
+                    if (act[s])
+                        matvec_accurate(h->mv, h->d_perm, X + (int64_t)s * n, xp64, yp64,
+                                        W + (int64_t)s * n, h->nc, st);
+            }
             residual_b_kernel<<<gv, GT, 0, st>>>(W, B, n, d_act);
             HM_LAUNCHED();
             HM_CUDA(cudaGetLastError());

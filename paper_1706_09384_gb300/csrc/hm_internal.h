@@ -113,7 +113,8 @@ void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_
                      cudaStream_t st);
 void launch_scatter_y(const int64_t* d_perm, const float2* yp, double2* y, int64_t nc,
                       cudaStream_t st);
-// Accurate product (FP32-stored entries, FP64 x / t / y and FP64 sums), used for
+// Accurate product (FP32-stored entries, x / t and the sums as double-float
+// pairs of FP32 numbers, results in complex128), used for
 // the true residual of GMRES restarts.  xp64, yp64: tree-order scratch (3 nc).
 void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* xp64,
                      double2* yp64, double2* y, int64_t nc, cudaStream_t st);

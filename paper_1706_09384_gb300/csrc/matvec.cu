@@ -30,29 +30,18 @@ constexpr int PAIRS_PER_LANE = MAX_LD / 64;  // row pairs per lane (3)
 
 __device__ __forceinline__ float4 ldg_stream(const float4* p) { return __ldcs(p); }
 
-// Accumulation precision: the fast product keeps x, t, y and the sums in
-// FP32; the accurate product (used for GMRES restart residuals) widens the
-// FP32-stored entries to FP64 and keeps x, t, y and the sums in FP64.
+// Types of the fast product (x, t, y and the sums in FP32); the accurate
+// product of the GMRES restarts has its own double-float kernels below.
 template <bool ACC> struct MvT;
 template <> struct MvT<false> {
     using R = float;
     using C2 = float2;
     struct C4 { float x, y, z, w; };
 };
-template <> struct MvT<true> {
-    using R = double;
-    using C2 = double2;
-    struct C4 { double x, y, z, w; };
-};
 
 __device__ __forceinline__ float red_sum(float v) { return warp_sumf(v); }
-__device__ __forceinline__ double red_sum(double v) { return warp_sum(v); }
 __device__ __forceinline__ void atomic_add_c(float2* p, float re, float im) {
     atomicAdd(p, make_float2(re, im));
-}
-__device__ __forceinline__ void atomic_add_c(double2* p, double re, double im) {
-    atomicAdd(&p->x, re);
-    atomicAdd(&p->y, im);
 }
 
 // Phase 1: for every V chunk of the item's column leaf, t[vec + c] += V[:, c]^H x_leaf.
@@ -196,6 +185,175 @@ __global__ void __launch_bounds__(MV_THREADS) mv_phase2(const WorkItem* items,
         if (r < it.rows) atomic_add_c(yp + it.dof + r, s.x, s.y);
         if (r + 1 < it.rows) atomic_add_c(yp + it.dof + r + 1, s.z, s.w);
     }
+}
+
+// ---- accurate product: FP32-stored entries, double-float sums ----
+// x, t and the partial sums are carried as unevaluated pairs (hi, lo) of FP32
+// numbers.  Each product a x_hi is split exactly into p + e with an FMA
+// (e = a x_hi - p), p is added to the running hi part by an exact two-sum, and
+// the rounding errors, e and a x_lo are gathered in the lo part (Dekker's
+// product, Knuth's two-sum).  The sums carry about 44 significant bits,
+// FP64-grade for the GMRES restart residuals, while the loops run on the FP32
+// pipes (GB300's FP64 rate is 1/64 of its FP32 rate).  Every operation is an
+// explicitly rounded intrinsic so the compiler cannot fuse the two-sums.
+__device__ __forceinline__ void df_add_prod(float& h, float& l, float a, float xh, float xl) {
+    const float p = __fmul_rn(a, xh);
+    const float e = __fmaf_rn(a, xh, -p);
+    const float t = __fadd_rn(h, p);
+    const float bp = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(err, __fmaf_rn(a, xl, e)));
+}
+__device__ __forceinline__ void df_merge(float& h, float& l, float h2, float l2) {
+    const float t = __fadd_rn(h, h2);
+    const float bp = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(h2, bp));
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, l2), err);
+}
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        df_merge(h, l, h2, l2);  // symmetric: every lane ends with the same pair
+    }
+}
+// complex128 -> (re_hi, im_hi, re_lo, im_lo)
+__device__ __forceinline__ float4 df_split(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+}
+
+// t[vec + c] += V[:, c]^H x_leaf, double-float sums, FP64 atomics into t64.
+__global__ void __launch_bounds__(MV_THREADS) mvdf_phase1(const WorkItem* items,
+                                                         const DevChunk* hdr,
+                                                         const float2* __restrict__ arena,
+                                                         const float4* __restrict__ xdf,
+                                                         double2* t64) {
+    const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 xa[PAIRS_PER_LANE], xb[PAIRS_PER_LANE];  // rows 2 pr and 2 pr + 1
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+        const int r = 2 * (lane + 32 * q);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        xa[q] = r < it.rows ? xdf[it.dof + r] : z;
+        xb[q] = r + 1 < it.rows ? xdf[it.dof + r + 1] : z;
+    }
+    const int npair = it.ld >> 1;
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk ch = sh_hdr[ci - it.first];
+        const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const float4* col = base + (int64_t)c * (ch.ld >> 1);
+            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    const float4 v = ldg_stream(col + pr);  // (a_re, a_im, b_re, b_im)
+                    // conj(a) x: re += a_re x_re + a_im x_im, im += a_re x_im - a_im x_re
+                    df_add_prod(rh, rl, v.x, xa[q].x, xa[q].z);
+                    df_add_prod(rh, rl, v.y, xa[q].y, xa[q].w);
+                    df_add_prod(ih, il, v.x, xa[q].y, xa[q].w);
+                    df_add_prod(ih, il, -v.y, xa[q].x, xa[q].z);
+                    df_add_prod(rh, rl, v.z, xb[q].x, xb[q].z);
+                    df_add_prod(rh, rl, v.w, xb[q].y, xb[q].w);
+                    df_add_prod(ih, il, v.z, xb[q].y, xb[q].w);
+                    df_add_prod(ih, il, -v.w, xb[q].x, xb[q].z);
+                }
+            }
+            df_warp_sum(rh, rl);
+            df_warp_sum(ih, il);
+            if (lane == 0) {
+                atomicAdd(&t64[ch.vec + c].x, (double)rh + (double)rl);
+                atomicAdd(&t64[ch.vec + c].y, (double)ih + (double)il);
+            }
+        }
+    }
+}
+
+// y_leaf += sum over chunks of chunk * v (v = x or t as double-float), FP64 atomics into yp64.
+__global__ void __launch_bounds__(MV_THREADS) mvdf_phase2(const WorkItem* items,
+                                                         const DevChunk* hdr,
+                                                         const float2* __restrict__ arena,
+                                                         const float4* __restrict__ xdf,
+                                                         const float4* __restrict__ tdf,
+                                                         double2* yp64) {
+    __shared__ float4 part[MV_WARPS][MAX_LD];  // (re_hi, re_lo, im_hi, im_lo) per row
+    const WorkItem it = items[blockIdx.x];
+    __shared__ DevChunk sh_hdr[MAX_ITEM_CHUNKS];
+    for (int i = threadIdx.x; i < it.last - it.first; i += MV_THREADS) sh_hdr[i] = hdr[it.first + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int npair = it.ld >> 1;
+    float4 sa[PAIRS_PER_LANE], sb[PAIRS_PER_LANE];  // rows 2 pr, 2 pr + 1: (re_h, re_l, im_h, im_l)
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+        sa[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sb[q] = sa[q];
+    }
+    for (int ci = it.first; ci < it.last; ++ci) {
+        const DevChunk ch = sh_hdr[ci - it.first];
+        const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
+        const float4* v = (ch.kind == 0 ? xdf : tdf) + ch.vec;
+        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
+            const float4 w = __ldg(v + c);  // (re_h, im_h, re_l, im_l)
+            const float4* col = base + (int64_t)c * (ch.ld >> 1);
+#pragma unroll
+            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+                const int pr = lane + 32 * q;
+                if (pr < npair) {
+                    const float4 a = ldg_stream(col + pr);  // (a_re, a_im, b_re, b_im)
+                    // a w: re += a_re w_re - a_im w_im, im += a_re w_im + a_im w_re
+                    df_add_prod(sa[q].x, sa[q].y, a.x, w.x, w.z);
+                    df_add_prod(sa[q].x, sa[q].y, -a.y, w.y, w.w);
+                    df_add_prod(sa[q].z, sa[q].w, a.x, w.y, w.w);
+                    df_add_prod(sa[q].z, sa[q].w, a.y, w.x, w.z);
+                    df_add_prod(sb[q].x, sb[q].y, a.z, w.x, w.z);
+                    df_add_prod(sb[q].x, sb[q].y, -a.w, w.y, w.w);
+                    df_add_prod(sb[q].z, sb[q].w, a.z, w.y, w.w);
+                    df_add_prod(sb[q].z, sb[q].w, a.w, w.x, w.z);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+        const int r = 2 * (lane + 32 * q);
+        if (r < MAX_LD) {
+            part[warp][r] = sa[q];
+            part[warp][r + 1] = sb[q];
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < it.rows; r += MV_THREADS) {
+        float4 s = part[0][r];
+        for (int w = 1; w < MV_WARPS; ++w) {
+            const float4 u = part[w][r];
+            df_merge(s.x, s.y, u.x, u.y);
+            df_merge(s.z, s.w, u.z, u.w);
+        }
+        atomicAdd(&yp64[it.dof + r].x, (double)s.x + (double)s.y);
+        atomicAdd(&yp64[it.dof + r].y, (double)s.z + (double)s.w);
+    }
+}
+
+__global__ void gather_xdf_kernel(const int64_t* perm, const double2* x, float4* xdf, int64_t nc) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * nc) return;
+    const int64_t p = q / 3, a = q - 3 * p;
+    xdf[q] = df_split(x[3 * perm[p] + a]);
+}
+
+__global__ void split_df_kernel(const double2* t64, float4* tdf, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) tdf[q] = df_split(t64[q]);
 }
 
 // ---- BF16 storage ----
@@ -464,13 +622,6 @@ __global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const
         arena16[ch->data + e] = w;
     }
     if (threadIdx.x == 0) ch->scale = scale;
-}
-
-__global__ void gather_x64_kernel(const int64_t* perm, const double2* x, double2* xp, int64_t nc) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= 3 * nc) return;
-    const int64_t p = q / 3, a = q - 3 * p;
-    xp[q] = x[3 * perm[p] + a];
 }
 
 __global__ void scatter_y64_kernel(const int64_t* perm, const double2* yp, double2* y, int64_t nc) {
@@ -867,20 +1018,29 @@ void matvec_accurate(MatvecDev* m, const int64_t* d_perm, const double2* x, doub
                      double2* yp64, double2* y, int64_t nc, cudaStream_t st) {
     const int64_t n = 3 * nc;
     const unsigned nb = (unsigned)hm_cdiv(n, 256);
-    gather_x64_kernel<<<nb, 256, 0, st>>>(d_perm, x, xp64, nc);
+    // xp64 (3 nc complex128 = 16 B each) holds x in tree order as double-float pairs
+    float4* xdf = reinterpret_cast<float4*>(xp64);
+    gather_xdf_kernel<<<nb, 256, 0, st>>>(d_perm, x, xdf, nc);
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t64, 0, m->t_elems * sizeof(double2), st));
     HM_CUDA(cudaMemsetAsync(yp64, 0, n * sizeof(double2), st));
     if (m->n1) {
-        mv_phase1<true><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr1,
-                                                               m->arena, xp64, m->t64);
+        mvdf_phase1<<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr1, m->arena, xdf,
+                                                            m->t64);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    if (m->t_elems) {  // t as double-float pairs, in place (16 B either way)
+        split_df_kernel<<<(unsigned)hm_cdiv(m->t_elems, 256), 256, 0, st>>>(
+            m->t64, reinterpret_cast<float4*>(m->t64), m->t_elems);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
     if (m->n2) {
-        mv_phase2<true><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr2,
-                                                               m->arena, xp64, m->t64, yp64);
+        mvdf_phase2<<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr2, m->arena, xdf,
+                                                            reinterpret_cast<const float4*>(m->t64),
+                                                            yp64);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
