@@ -100,6 +100,10 @@ void hm_opts_default(hm_opts* opts);
  *   opts     NULL for defaults
  *   stream   cudaStream_t for all work (the call returns after the build is complete)
  *   out      receives the handle (NULL on error)
+ * An admissible block whose vector ACA had to retire a row with a non-negligible
+ * residual because all its 3x3 candidate pivots are singular (Sec. 2.3: T on
+ * coplanar points has rank-2 3x3 blocks) is stored dense instead (exact); its
+ * hm_block then reads admissible = 0, rank_aca = the steps taken.
  * Errors: HM_ERR_ARG (n_c < 1, non-finite or non-positive parameters, missing
  * normals for T, non-finite coordinates), HM_ERR_OOM, HM_ERR_CUDA. */
 hm_status hm_build(const double* points, const double* normals, int64_t n_c, double rho,
@@ -181,6 +185,17 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
  * last iterates), HM_ERR_TIMEOUT, HM_ERR_OOM, HM_ERR_CUDA. */
 hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int32_t restart,
                          double tol, int32_t maxit, int32_t* iters, double* relres, void* stream);
+
+/* The approximation error of the stored H-matrix for the a-posteriori bound
+ * of Sec. 3.3 (Eq. est_direct), ||b - A x|| <= ||b - A_H x|| + ||A - A_H||_F ||x||:
+ *   delta_f = ||A - A_H||_F, norm_f = ||A||_F, A the exact matrix (FP64 Green's
+ *   tensors, weights, diagonal blocks), A_H the stored FP32 H-matrix.
+ *   nsample <= 0: every point pair (n_c <= 2048); else nsample pairs drawn
+ *   uniformly by a counter-based generator from seed (unbiased estimates of
+ *   the squared norms).  delta_f, norm_f: HOST outputs.  Synchronises stream.
+ * Errors: HM_ERR_ARG, HM_ERR_CUDA.  (No paper counterpart for the sampling.) */
+hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double* delta_f,
+                            double* norm_f, void* stream);
 
 /* Writes a JSON object (NUL-terminated) with the build statistics: n_c, tree
  * depth, cluster and block counts, sparsity constant C_sp (Sec. 2.1), ACA
@@ -266,7 +281,10 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
  * the GPU (other streams, other host threads) race on it: serialise them.  The
  * call waits for its stream to finish.
  * Errors: HM_ERR_ARG (null or misaligned pointer, sizes beyond the limits,
- * cap too small for the block's rank: *rank = -1), HM_ERR_NUMERIC, HM_ERR_CUDA. */
+ * cap too small for the block's rank: *rank = -1), HM_ERR_NUMERIC,
+ * HM_ERR_UNSUPPORTED (a row with a non-negligible residual whose 3x3 blocks are
+ * all singular, e.g. coplanar T blocks: the vector ACA cannot pivot it and
+ * hm_build stores such blocks dense), HM_ERR_CUDA. */
 hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lambda, double mu,
                                double omega, const double* x, int64_t m, const double* y,
                                const double* ny, int64_t n, double eps, int32_t cap, void* uv,

@@ -595,10 +595,16 @@ static void src_col(const block_src* s, int64_t j, cplx* C /* 3m x 3 row-major *
 #define ACA_SINGULAR_REL 1e-12
 
 /* Runs the ACA; U (3m x k) and V (3n x k) col-major grow as needed.
- * Returns k (a multiple of 3).  pivots (optional, 2 per step) logs (i^, j^). */
+ * Returns k (a multiple of 3).  pivots (optional, 2 per step) logs (i^, j^).
+ * lost (optional): set to 1 when a row had to be retired for singular pivot
+ * blocks although its residual was not negligible (largest sigma_1 of its
+ * 3x3 blocks above eps times the largest sigma_1 seen): the vector ACA cannot
+ * pivot such a row (every 3x3 block singular, e.g. coplanar T blocks), so the
+ * approximation misses it. */
 static int64_t aca_run(const block_src* s, double eps, cplx** Uout, cplx** Vout,
-                       int64_t** pivlog)
+                       int64_t** pivlog, int* lost)
 {
+    if (lost) *lost = 0;
     const int64_t m = s->m, n = s->n, m3 = 3 * m, n3 = 3 * n;
     const int64_t kmax_steps = m < n ? m : n;
     int64_t cap = 8; /* steps of capacity */
@@ -625,7 +631,7 @@ static int64_t aca_run(const block_src* s, double eps, cplx** Uout, cplx** Vout,
             }
         /* step 2: j^ = argmax sigma_3 of the 3x3 blocks R(i^, j), j unused */
         int64_t jhat = -1;
-        double best = -1.0;
+        double best = -1.0, rowmax = 0.0;
         for (int64_t j = 0; j < n; ++j) {
             cplx B[3][3];
             double sv[3];
@@ -633,6 +639,7 @@ static int64_t aca_run(const block_src* s, double eps, cplx** Uout, cplx** Vout,
                 for (int b = 0; b < 3; ++b) B[a][b] = R[a * n3 + 3 * j + b];
             sv3(B, sv);
             if (sv[0] > sref) sref = sv[0];
+            if (sv[0] > rowmax) rowmax = sv[0];
             if (used_col[j]) continue;
             if (sv[2] > best) {
                 best = sv[2];
@@ -642,6 +649,7 @@ static int64_t aca_run(const block_src* s, double eps, cplx** Uout, cplx** Vout,
         if (jhat < 0) break; /* every column used */
         if (best <= ACA_SINGULAR_REL * sref) {
             /* singular pivot: this row is exhausted; retry on the lowest unused row */
+            if (lost && rowmax > eps * sref) *lost = 1;
             used_row[ihat] = 1;
             int64_t nxt = -1;
             for (int64_t i = 0; i < m; ++i)
@@ -752,7 +760,7 @@ int64_t or_aca_dense(const double* A, int64_t m, int64_t n, double eps, int64_t 
     s.A = A;
     cplx *Uc, *Vc;
     int64_t* pv;
-    const int64_t k = aca_run(&s, eps, &Uc, &Vc, &pv);
+    const int64_t k = aca_run(&s, eps, &Uc, &Vc, &pv, NULL);
     int64_t ret = k;
     if (k > kcap) {
         ret = -1;
@@ -936,9 +944,27 @@ or_hmat* or_hmat_build(const or_problem* pb, const double* pts, const double* nr
             src.rows = h->perm + t->begin;
             src.cols = h->perm + s->begin;
             cplx *U, *V;
-            const int64_t k = aca_run(&src, eps, &U, &V, NULL);
+            int lost = 0;
+            const int64_t k = aca_run(&src, eps, &U, &V, NULL, &lost);
             h->rank_aca[b] = k;
-            if (recompress_on) {
+            if (lost) {
+                /* rows the vector ACA cannot pivot (every 3x3 block singular):
+                 * the block is stored exactly, as a dense block */
+                free(U);
+                free(V);
+                h->blk[b].admissible = 0;
+                cplx* D = (cplx*)malloc((size_t)(9 * m * n) * sizeof(cplx));
+                for (int64_t j = 0; j < n; ++j)
+                    for (int64_t i = 0; i < m; ++i) {
+                        cplx G[3][3];
+                        entry_block(pb, pts, nrm, h->perm[t->begin + i], h->perm[s->begin + j], G);
+                        for (int a = 0; a < 3; ++a)
+                            for (int c = 0; c < 3; ++c)
+                                D[(3 * i + a) + (3 * j + c) * (3 * m)] = G[a][c];
+                    }
+                h->D[b] = D;
+                h->rank[b] = 0;
+            } else if (recompress_on) {
                 cplx *U2, *V2;
                 const int64_t r = recompress(U, V, 3 * m, 3 * n, k, eps, &U2, &V2, NULL);
                 free(U);

@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
     __shared__ double s_normB2, s_sref, s_best, s_dB2;
     __shared__ double2 s_gam[9];
     __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
+    __shared__ int s_lost;   // a row retired for singular pivots carried a non-negligible residual
     __shared__ GreenParams s_gp;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
             s_normB2 = 0.0;
             s_sref = 0.0;
             s_stop = 0;
+            s_lost = 0;
         }
         const int64_t steps_max = m < n ? m : n;
         float2* Rs = reinterpret_cast<float2*>(R + 9 * n);  // FP32 (sigma_1, sigma_3) of row candidates
@@ -398,8 +400,12 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                 break;
             }
             if (!(s_best > SING_REL * s_sref)) {
-                // singular pivot: retire row i^, restart on the lowest unused row
-                if (tid == 0) urow[ihat] = 1;
+                // singular pivot: retire row i^, restart on the lowest unused row;
+                // a row with a non-negligible residual is lost to the approximation
+                if (tid == 0) {
+                    urow[ihat] = 1;
+                    if (s1max > eps * s_sref) s_lost = 1;
+                }
                 __syncthreads();
                 double v = -1.0, dummy = 0.0;
                 int64_t li = -1;
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
         }
         if (tid == 0) {
             res[job].k = s_k;
-            res[job].status = s_stop == 1 ? 0 : (s_stop == 2 ? 1 : 2);
+            res[job].status = s_stop == 1 ? (s_lost ? 3 : 0) : (s_stop == 2 ? 1 : 2);
         }
         __syncthreads();
     }
@@ -769,6 +775,10 @@ extern "C" hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lam
         HM_CUDA(cudaStreamSynchronize(st));
         if (R.status == 1) hm_throw(HM_ERR_ARG, "ACA rank exceeds cap; call again with a larger cap");
         if (R.status == 2) hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA");
+        if (R.status == 3)
+            hm_throw(HM_ERR_UNSUPPORTED,
+                     "rows with singular 3x3 blocks only: the vector ACA cannot pivot them "
+                     "(store the block dense)");
         *rank = R.k;
     } catch (const hm_error& e) {
         hm_set_error(e.msg);

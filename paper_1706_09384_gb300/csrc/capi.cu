@@ -205,6 +205,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
     }
     double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0;
     int64_t batches = 0, reruns = 0, ws_peak = 0, ws_tot = 0;
+    std::vector<int64_t> fallback(nprob, 0);
     int* d_counter = (int*)hm_dmalloc(staging, sizeof(int), st, true);
     std::vector<int64_t> todo = adm;
     try {
@@ -274,6 +275,14 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
             for (int64_t j = 0; j < nj; ++j) {
                 if (res[j].status == 2)
                     hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA of a block");
+                if (res[j].status == 3) {  // rows the vector ACA cannot pivot: store exactly
+                    hm_block& bk = blk_of(ids[j]);
+                    bk.admissible = 0;
+                    bk.rank_aca = res[j].k;
+                    bk.rank = 0;
+                    fallback[aq[ids[j]]]++;
+                    continue;
+                }
                 if (res[j].status == 1) {
                     const int64_t a = ids[j];
                     const int64_t full = 3 * std::min(jobs[j].m, jobs[j].n);
@@ -356,6 +365,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         throw;
     }
     free_all(batchbuf);
+    for (int q = 0; q < nprob; ++q) hs[q]->aca_dense_fallback = fallback[q];
     for (hm_matrix* h : hs) {  // a batch reports the shared launches in every handle
         h->ev_aca_ms += ev_aca;
         h->t_aca_ms += t_aca;
@@ -734,6 +744,15 @@ hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int3
     HM_API_END
 }
 
+hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double* delta_f,
+                            double* norm_f, void* stream) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (!delta_f || !norm_f) hm_throw(HM_ERR_ARG, "null output");
+    estimate_error(h, nsample, seed, delta_f, norm_f, (cudaStream_t)stream);
+    HM_API_END
+}
+
 hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
@@ -782,6 +801,7 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"aca_workspace_total_bytes\": " << h->aca_workspace_total
        << ", \"rank_model\": " << h->used_rank_model
        << ", \"batch_problems\": " << h->batch_problems
+       << ", \"aca_dense_fallback\": " << h->aca_dense_fallback
        << ", \"ms\": {\"tree\": " << h->t_tree_ms << ", \"partition\": " << h->t_part_ms
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms
@@ -854,11 +874,12 @@ hm_status hm_get_block_data(hm_handle h, int64_t b, void* a, void* v) {
         const int64_t owner_begin = 3 * (c.kind == 2 ? s.begin : t.begin);
         const int64_t ld = c.kind == 2 ? n3 : m3;
         const int64_t r0 = c.leaf_dof - owner_begin;
+        const int64_t col0 = c.kind == 0 ? c.vec - 3 * s.begin : 0;  // dense: column leaf offset
         for (int col = 0; col < c.ncols; ++col)
             for (int r = 0; r < c.rows; ++r) {
                 const float2 z = tmp[(size_t)col * c.ld + r];
-                dst[2 * ((r0 + r) + col * ld)] = z.x;
-                dst[2 * ((r0 + r) + col * ld) + 1] = z.y;
+                dst[2 * ((r0 + r) + (col0 + col) * ld)] = z.x;
+                dst[2 * ((r0 + r) + (col0 + col) * ld) + 1] = z.y;
             }
     }
     HM_API_END

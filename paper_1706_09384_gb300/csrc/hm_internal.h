@@ -147,7 +147,8 @@ struct AcaJob {              // one admissible block
 };
 struct AcaResult {
     int32_t k;               // ACA rank (columns), multiple of 3
-    int32_t status;          // 0 converged, 1 capacity overflow, 2 non-finite
+    int32_t status;          // 0 converged, 1 capacity overflow, 2 non-finite,
+                             // 3 rows lost to singular pivots (block stored dense)
 };
 void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
                 const AcaJob* d_jobs, int64_t njobs, double2* d_work, double2* d_gram,
@@ -192,6 +193,10 @@ struct GmresResult {
 struct hm_matrix;
 GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int restart, double tol,
                         int maxit, cudaStream_t st);
+// ||A - A_H||_F and ||A||_F (exact tensors vs the stored FP32 H-matrix) over
+// every point pair (nsample <= 0) or nsample pairs drawn with the seed.
+void estimate_error(hm_matrix* h, int64_t nsample, uint64_t seed, double* delta_f, double* norm_f,
+                    cudaStream_t st);
 // nrhs right-hand sides in lockstep (b, x: 3 nc x nrhs column-major, device)
 void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* b, double2* x, int restart, double tol,
                        int maxit, std::vector<GmresResult>& out, cudaStream_t st);
@@ -238,5 +243,6 @@ struct hm_matrix {
     int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
     int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
     int batch_problems = 1;          // problems that shared the ACA / recompression launches
+    int64_t aca_dense_fallback = 0;  // admissible blocks stored dense (rows lost to singular pivots)
     int used_rank_model = 0;
 };

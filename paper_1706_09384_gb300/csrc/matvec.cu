@@ -738,28 +738,34 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
     for (size_t b = 0; b < blk.size(); ++b) {
         const hm_cluster& t = cl[blk[b].tau];
         const hm_cluster& s = cl[blk[b].sigma];
-        int64_t l0, l1;
+        int64_t l0, l1, c0 = 0, c1 = 1;
         leaf_range(blk[b].tau, l0, l1);
+        // dense blocks are cut along the column leaves too (chunks of at most
+        // 3 x 64 columns: blocks stored dense after the ACA can be wide)
+        if (!blk[b].admissible) leaf_range(blk[b].sigma, c0, c1);
         for (int64_t l = l0; l < l1; ++l) {
-            Chunk c;
-            c.rows = P.leaf_rows[l];
-            c.ld = (int32_t)hm_round_up(c.rows, 2);
-            c.block = (int64_t)b;
-            c.leaf_dof = P.leaf_dof_begin[l];
-            if (!blk[b].admissible) {
-                c.kind = 0;
-                c.ncols = (int32_t)(3 * (s.end - s.begin));
-                c.vec = 3 * s.begin;
-            } else {
-                c.kind = 1;
-                c.ncols = blk[b].rank;
-                c.vec = t_off[b];
+            for (int64_t lc = c0; lc < c1; ++lc) {
+                Chunk c;
+                c.rows = P.leaf_rows[l];
+                c.ld = (int32_t)hm_round_up(c.rows, 2);
+                c.block = (int64_t)b;
+                c.leaf_dof = P.leaf_dof_begin[l];
+                if (!blk[b].admissible) {
+                    c.kind = 0;
+                    c.ncols = P.leaf_rows[lc];
+                    c.vec = P.leaf_dof_begin[lc];
+                } else {
+                    c.kind = 1;
+                    c.ncols = blk[b].rank;
+                    c.vec = t_off[b];
+                }
+                c.data = -1;
+                rows_of[l].push_back((int32_t)P.chunks.size());
+                P.chunks.push_back(c);
             }
-            c.data = -1;
-            rows_of[l].push_back((int32_t)P.chunks.size());
-            P.chunks.push_back(c);
         }
         (void)t;
+        (void)s;
         if (blk[b].admissible) {
             leaf_range(blk[b].sigma, l0, l1);
             for (int64_t l = l0; l < l1; ++l) {
@@ -1089,8 +1095,9 @@ void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<
         if (!base) continue;
         const int64_t owner_begin = c.kind == 2 ? s.begin : t.begin;
         const int64_t owner_rows = 3 * (c.kind == 2 ? s.end - s.begin : t.end - t.begin);
+        const int64_t col0 = c.kind == 0 ? c.vec - 3 * s.begin : 0;  // dense: the chunk's first column
         StagedCopy J;
-        J.src = base + (c.leaf_dof - 3 * owner_begin);
+        J.src = base + (c.leaf_dof - 3 * owner_begin) + col0 * owner_rows;
         J.src_ld = owner_rows;
         J.dst = c.data;
         J.ld = c.ld;

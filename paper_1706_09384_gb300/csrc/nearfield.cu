@@ -11,7 +11,7 @@ namespace {
 struct DenseJob {
     int64_t data;       // arena offset of the chunk
     int64_t row_begin;  // tree-order point range of the leaf (rows)
-    int64_t col_begin;  // tree-order point range of sigma (columns)
+    int64_t col_begin;  // tree-order point range of the column leaf
     int32_t m, n;       // points
     int32_t ld;
     int32_t pad_;
@@ -61,14 +61,12 @@ void assemble_dense(const GreenParams& gp, const double* d_pts_p, const double* 
     std::vector<DenseJob> jobs;
     for (const Chunk& c : plan.chunks) {
         if (c.kind != 0) continue;
-        const hm_block& b = blocks[c.block];
-        const hm_cluster& s = cl[b.sigma];
-        DenseJob J;
+        DenseJob J;  // one (row leaf, column leaf) piece of a dense block
         J.data = c.data;
         J.row_begin = c.leaf_dof / 3;
-        J.col_begin = s.begin;
+        J.col_begin = c.vec / 3;
         J.m = c.rows / 3;
-        J.n = (int32_t)(s.end - s.begin);
+        J.n = c.ncols / 3;
         J.ld = c.ld;
         J.pad_ = 0;
         jobs.push_back(J);

@@ -195,7 +195,9 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
     // the rotation and broadcasts it, so the scarce FP64 pipe is not spent on
     // redundant square roots and divisions.  Only W's final columns P_j s_j are
     // needed (see T below), so the rotations are not accumulated.
-    const int G = k <= 32 ? 8 : (k <= 96 ? 16 : 32);
+    // group size: the pairs of a round (k / 2) should fit in one pass of the
+    // CTA's groups, since every round ends at a barrier (k <= 64: one pass)
+    const int G = k <= 128 ? 8 : (k <= 256 ? 16 : 32);
     const int gl = lane % G;                // lane within the group
     const int gid = tid / G;                // group index in the CTA
     const int ngroups = RT / G;

@@ -70,6 +70,7 @@ SIGNATURES = {
     "hm_matvec_host": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_gmres": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
     "hm_gmres_multi": (_I32, [_P, _I32, _P, _P, _I32, C.c_double, _I32, _P, _P, _P]),
+    "hm_estimate_error": (_I32, [_P, _I64, C.c_uint64, _P, _P, _P]),
     "hm_stats": (_I32, [_P, C.c_char_p, _SZ, _P]),
     "hm_sizes": (_I32, [_P, _P, _P, _P]),
     "hm_get_tree": (_I32, [_P, _P, _P]),
@@ -316,6 +317,14 @@ class HMatrix:
             X = torch.empty_like(B)
         X.copy_(Xc.t())
         return X, it, rr, st
+
+    def estimate_error(self, nsample=0, seed=0, stream=None):
+        """(||A - A_H||_F, ||A||_F): every point pair (nsample <= 0) or a sample."""
+        d = C.c_double(0.0)
+        a = C.c_double(0.0)
+        _check(lib().hm_estimate_error(self.h, nsample, seed, C.byref(d), C.byref(a),
+                                       _stream_ptr(stream)), "hm_estimate_error")
+        return d.value, a.value
 
     def profile_matvec(self, reps=10, stream=None):
         """Average per-kernel device times (ms) of the product and its algorithmic bytes."""

@@ -104,3 +104,34 @@ def plane_wave_rhs(points: np.ndarray, kappa_p: float, kappa_s: float, nrhs: int
             u = p[s][None, :] * np.exp(1j * kappa_s * (points @ d[s]))[:, None]
         out[:, s] = u.reshape(-1)
     return out
+
+
+SURFACE_AREA = {"sphere": 4.0 * math.pi, "cube": 6.0, "ellipsoid": 5.46}  # ellipsoid: Thomsen's estimate
+
+
+def batch_problems(count: int = 16, seed: int = 0):
+    """Independent problems of mixed size, shape, wavenumber and kernel: n_c from
+    {4096, ..., 131072}, shape sphere : cube : ellipsoid = 3 : 2 : 1, k_s ~ U[2, 24],
+    U or T by a fair coin, column weights area / n_c.  Returns a list of dicts with
+    points, normals (None for U), rho, lam, mu, omega, kernel, weights, shape, ks."""
+    rng = np.random.default_rng(seed)
+    sizes = [4096 * 2 ** k for k in range(6)]
+    shapes = ["sphere"] * 3 + ["cube"] * 2 + ["ellipsoid"]
+    out = []
+    for q in range(count):
+        nc = int(rng.choice(sizes))
+        shape = shapes[int(rng.integers(6))]
+        ks = float(rng.uniform(2.0, 24.0))
+        kern = "U" if rng.random() < 0.5 else "T"
+        if shape == "sphere":
+            pts = fibonacci_sphere(nc)
+            nrm = sphere_normals(pts)
+        elif shape == "cube":
+            pts, nrm = cube_surface(nc, seed=q)
+        else:
+            pts, nrm = ellipsoid(nc)
+        rho, lam, mu, om = material(ks)
+        out.append(dict(points=pts, normals=nrm if kern == "T" else None, rho=rho, lam=lam, mu=mu,
+                        omega=om, kernel=kern, weights=np.full(nc, SURFACE_AREA[shape] / nc),
+                        shape=shape, ks=ks))
+    return out
