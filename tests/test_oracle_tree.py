@@ -120,3 +120,19 @@ def test_storage_bound(oracle):
     bound = 2 * csp * max(rmax, leaf) * nc * (math.log2(nc) - math.log2(leaf) + 1)
     assert nst <= bound
     assert nst < nc * nc  # compression happens at all
+
+
+def test_icosphere_vertices():
+    """10 * 4^l + 2 distinct unit vectors, nearest-neighbour spacing within a
+    factor 1.5 of its mean (a quasi-uniform mesh), normals = positions."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    from paper_1706_09384_gb300 import inputs
+    for level in range(0, 5):
+        p, n = inputs.icosphere(level)
+        assert len(p) == 10 * 4 ** level + 2
+        assert np.allclose(np.linalg.norm(p, axis=1), 1.0, atol=1e-15)
+        assert np.array_equal(p, n)
+        d, _ = cKDTree(p).query(p, k=2)
+        nn = d[:, 1]
+        assert nn.min() > 0 and nn.max() < 1.5 * nn.mean() and nn.min() > nn.mean() / 1.5
