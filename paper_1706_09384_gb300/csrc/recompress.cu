@@ -14,7 +14,9 @@
 // pair ordering.  Truncation: smallest r' with
 // (sum_{i >= r'} s_i^2)^{1/2} <= eps (sum s_i^2)^{1/2} (Frobenius, matching the
 // ACA stopping test).  The tall products U T_U, V T_V are applied by a second
-// kernel that writes straight into the matvec's chunk layout.
+// kernel, in double-float arithmetic on the FP32 pipes (~44 significant bits
+// before the rounding to the FP32 storage), that writes straight into the
+// matvec's chunk layout.
 #include <algorithm>
 
 #include "hm_internal.h"
@@ -22,6 +24,13 @@
 namespace {
 
 constexpr int RT = 256;
+
+// complex128 -> double-float pair (re_hi, im_hi, re_lo, im_lo): the T factors
+// are handed to the factor application in this form (same 16 bytes)
+__device__ __forceinline__ float4 to_df(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+}
 constexpr int RW = RT / 32;
 constexpr int TILE_ROWS = 16;
 
@@ -157,8 +166,9 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
     if (!J.recompress) {
         for (int64_t e = tid; e < (int64_t)k * k; e += RT) {
             const int p = (int)(e % k), c = (int)(e / k);
-            TU[e] = make_double2(p == c ? 1.0 : 0.0, 0.0);
-            TV[e] = TU[e];
+            const float4 one = to_df(make_double2(p == c ? 1.0 : 0.0, 0.0));
+            reinterpret_cast<float4*>(TU)[e] = one;
+            reinterpret_cast<float4*>(TV)[e] = one;
         }
         if (tid == 0) rank_out[blockIdx.x] = k;
         return;
@@ -328,6 +338,12 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
         for (int t = 0; t < k; ++t) cfma(au, GVc[p + (int64_t)t * k], TV[t + (int64_t)q * k]);
         TU[p + (int64_t)q * k] = cscale(au, 1.0 / s);
     }
+    __syncthreads();
+    // T_U, T_V as double-float pairs, in place, for the factor application
+    for (int64_t e = tid; e < (int64_t)k * r; e += RT) {
+        reinterpret_cast<float4*>(TU)[e] = to_df(TU[e]);
+        reinterpret_cast<float4*>(TV)[e] = to_df(TV[e]);
+    }
 }
 
 // One item = the rows of one leaf of one factor.
@@ -339,29 +355,57 @@ struct ApplyJob {
     int32_t k, r, rows, ld;
 };
 
+// U' = U T on FP32 pipes: U (complex128) is split into a double-float pair on
+// load, T arrives as double-float pairs; each complex multiply-add is four
+// double-float multiply-adds (the high product split exactly by an FMA, the
+// cross terms and the rounding errors gathered in the low word, exact
+// two-sums), good to about 2^-44 before the final rounding to FP32.
+__device__ __forceinline__ void df_mac(float& h, float& l, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(h, p);
+    const float bp = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
 __global__ void __launch_bounds__(192) apply_factor_kernel(const ApplyJob* jobs,
                                                            const double2* __restrict__ work,
-                                                           const double2* __restrict__ scratch,
+                                                           const float4* __restrict__ scratch,
                                                            float2* out) {
     const ApplyJob J = jobs[blockIdx.x];
     const int row = threadIdx.x;
     if (row >= J.rows) return;
-    const double2* T = scratch + J.t_off;
+    const float4* T = scratch + J.t_off;
     constexpr int QB = 8;
     for (int q0 = 0; q0 < J.r; q0 += QB) {
-        double2 acc[QB];
+        float acc[QB][4];  // (re_h, re_l, im_h, im_l)
 #pragma unroll
-        for (int q = 0; q < QB; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q < QB; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
         for (int p = 0; p < J.k; ++p) {
-            const double2 u = work[J.src + row + (int64_t)p * J.src_ld];
+            const double2 ud = work[J.src + row + (int64_t)p * J.src_ld];
+            const float urh = __double2float_rn(ud.x), uih = __double2float_rn(ud.y);
+            const float url = __double2float_rn(ud.x - (double)urh);
+            const float uil = __double2float_rn(ud.y - (double)uih);
 #pragma unroll
             for (int q = 0; q < QB; ++q)
-                if (q0 + q < J.r) cfma(acc[q], u, T[p + (int64_t)(q0 + q) * J.k]);
+                if (q0 + q < J.r) {
+                    const float4 t = T[p + (int64_t)(q0 + q) * J.k];  // (re_h, im_h, re_l, im_l)
+                    // re += u_re t_re - u_im t_im ; im += u_re t_im + u_im t_re
+                    df_mac(acc[q][0], acc[q][1], urh, url, t.x, t.z);
+                    df_mac(acc[q][0], acc[q][1], -uih, -uil, t.y, t.w);
+                    df_mac(acc[q][2], acc[q][3], urh, url, t.y, t.w);
+                    df_mac(acc[q][2], acc[q][3], uih, uil, t.x, t.z);
+                }
         }
 #pragma unroll
         for (int q = 0; q < QB; ++q)
             if (q0 + q < J.r)
-                out[J.dst + row + (int64_t)(q0 + q) * J.ld] = make_float2((float)acc[q].x, (float)acc[q].y);
+                out[J.dst + row + (int64_t)(q0 + q) * J.ld] =
+                    make_float2(__fadd_rn(acc[q][0], acc[q][1]), __fadd_rn(acc[q][2], acc[q][3]));
     }
 }
 
@@ -464,7 +508,8 @@ void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
         ApplyJob* d = nullptr;
         HM_CUDA(cudaMallocAsync((void**)&d, aj.size() * sizeof(ApplyJob), st));
         HM_CUDA(cudaMemcpyAsync(d, aj.data(), aj.size() * sizeof(ApplyJob), cudaMemcpyHostToDevice, st));
-        apply_factor_kernel<<<(unsigned)aj.size(), 192, 0, st>>>(d, d_work, B->d_scratch, d_out);
+        apply_factor_kernel<<<(unsigned)aj.size(), 192, 0, st>>>(
+            d, d_work, reinterpret_cast<const float4*>(B->d_scratch), d_out);
         HM_LAUNCHED();
         HM_CUDA(cudaGetLastError());
         HM_CUDA(cudaFreeAsync(d, st));
