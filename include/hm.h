@@ -105,7 +105,8 @@ void hm_opts_default(hm_opts* opts);
  * coplanar points has rank-2 3x3 blocks) is stored dense instead (exact); its
  * hm_block then reads admissible = 0, rank_aca = the steps taken.
  * Errors: HM_ERR_ARG (n_c < 1, non-finite or non-positive parameters, missing
- * normals for T, non-finite coordinates), HM_ERR_OOM, HM_ERR_CUDA. */
+ * normals for T, non-finite coordinates, two distinct points at the same
+ * position: their Green's tensor is singular), HM_ERR_OOM, HM_ERR_CUDA. */
 hm_status hm_build(const double* points, const double* normals, int64_t n_c, double rho,
                    double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
                    int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out);

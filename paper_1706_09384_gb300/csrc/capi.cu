@@ -483,6 +483,23 @@ hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c,
         h->perm = std::move(tr.perm);
         h->depth = tr.depth;
     }
+    // coincident points share every split, hence a leaf: the Green's tensor of two
+    // distinct points at distance 0 is singular (Eq. elasto_U), so such input is refused
+    for (const hm_cluster& c : h->clusters) {
+        if (!c.is_leaf) continue;
+        for (int64_t a = c.begin; a < c.end; ++a)
+            for (int64_t b = a + 1; b < c.end; ++b) {
+                const double* pa = points + 3 * h->perm[a];
+                const double* pb = points + 3 * h->perm[b];
+                if (pa[0] == pb[0] && pa[1] == pb[1] && pa[2] == pb[2]) {
+                    char msg[160];
+                    std::snprintf(msg, sizeof(msg), "coincident points %lld and %lld",
+                                  (long long)std::min(h->perm[a], h->perm[b]),
+                                  (long long)std::max(h->perm[a], h->perm[b]));
+                    hm_throw(HM_ERR_ARG, msg);
+                }
+            }
+    }
     if (o.weights) {
         std::vector<double> wp(n_c);
         for (int64_t p = 0; p < n_c; ++p) wp[p] = o.weights[h->perm[p]];

@@ -82,6 +82,7 @@ struct MatvecDev {
     float2* xm = nullptr;
     float2* ym = nullptr;
     float2* tm = nullptr;
+    int32_t phase2_tc = 0;  // 1: phase 2 on tcgen05 (TMEM accumulators), 0: mma.sync
 };
 
 // Block of NRHS_BLOCK right-hand sides for the tensor-core product (created on

@@ -378,6 +378,258 @@ __global__ void __launch_bounds__(P2_THREADS, 2) mvm_phase2(const WorkItem* item
     }
 }
 
+// ---- phase 2 on the tcgen05 tensor cores (accumulators in TMEM) ----
+// The item's rows are the MMA's M (up to two tiles of 128), the 64 real output
+// columns its N, the complex columns (as bf16 pairs) its K.  Per stage of 16
+// complex columns (K = 32) the consumer warps load the BF16 columns from the
+// arena (16-byte loads, four columns by four rows per thread) and store them
+// transposed into K-major core matrices (8 rows x 16 bytes, no swizzle; core
+// groups 16 bytes apart beyond their 4 x 128 bytes so the 16-byte stores of
+// one warp hit distinct banks), build the weights w_j = scale_j v_j as the B
+// operand in the same layout, and signal the MMA warp; one thread issues the
+// tcgen05.mma instructions into two TMEM accumulator tiles and commits each
+// stage to an mbarrier that releases its buffers.  At the end the consumers
+// read the accumulators back with tcgen05.ld.  Shared-memory descriptors:
+// start >> 4, leading (K-direction core) byte offset 128, stride (8-row
+// group) byte offset T2_SBO, version 1, no swizzle.
+constexpr int T2_CONS = 8;
+constexpr int T2_THREADS = 32 * (T2_CONS + 1);  // + the MMA warp
+constexpr int T2_KC = 16;                        // complex columns per stage
+constexpr int T2_SBO = 4 * 128 + 16;             // bytes between 8-row core groups
+constexpr int T2_ATILE = 16 * T2_SBO;            // 128 rows
+constexpr int T2_BBYTES = 8 * T2_SBO;            // 64 rows (real output columns)
+constexpr uint32_t T2_TMEM_COLS = 128;           // two 128 x 64 FP32 accumulators
+// kind::f16: FP32 accumulate (bit 4), A and B BF16 (bits 7, 10), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t T2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(64 >> 3) << 17) |
+                              (uint32_t(128 >> 4) << 24);
+
+struct T2Smem {
+    alignas(128) unsigned char a[2][2][T2_ATILE];  // [slot][m tile]
+    alignas(128) unsigned char b[2][T2_BBYTES];    // [slot]
+    float2 cinfo[MAX_ITEM_COLS];                    // (source index | kind << 31, chunk scale)
+    DevChunk16 hdr[MAX_ITEM_CHUNKS];
+    int32_t colstart[MAX_ITEM_CHUNKS + 1];
+    int32_t ncol;
+    int32_t abort;
+    uint32_t tmem;
+    alignas(8) uint64_t ready[2];  // consumer warps -> MMA thread: slot filled
+    uint64_t done[2];              // MMA thread (tcgen05.commit) -> consumers: slot consumed
+};
+static_assert(sizeof(T2Smem) <= 56 * 1024, "four CTAs per SM");
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(T2_SBO >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(T2_THREADS, 4) mvt_phase2(const WorkItem* items,
+                                                           const DevChunk16* hdr,
+                                                           const uint32_t* __restrict__ arena,
+                                                           const float2* __restrict__ X,
+                                                           const float2* __restrict__ T,
+                                                           float2* Y, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T2Smem& S = *reinterpret_cast<T2Smem*>(smem_raw);
+    const WorkItem it = items[blockIdx.x];
+    const int nch = it.last - it.first;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < nch; i += T2_THREADS) S.hdr[i] = hdr[it.first + i];
+    if (tid == 0) {
+        S.abort = 0;
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&S.ready[q], T2_CONS);
+            mbar_init(&S.done[q], 1);
+        }
+        mbar_fence_init();
+    }
+    if (warp == T2_CONS) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem)),
+                     "r"(T2_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {  // column offsets of the chunks (exclusive scan)
+        const int a0 = 2 * lane < nch ? S.hdr[2 * lane].ncols : 0;
+        const int a1 = 2 * lane + 1 < nch ? S.hdr[2 * lane + 1].ncols : 0;
+        int inc = a0 + a1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int exc = inc - a0 - a1;
+        S.colstart[2 * lane] = exc;
+        S.colstart[2 * lane + 1] = exc + a0;
+        if (lane == 31) {
+            S.colstart[MAX_ITEM_CHUNKS] = inc;
+            S.ncol = inc;
+        }
+    }
+    __syncthreads();
+    for (int ci = warp; ci < nch; ci += T2_CONS + 1) {
+        const DevChunk16 ch = S.hdr[ci];
+        const uint32_t kind = ch.kind == 0 ? 0u : 0x80000000u;
+        for (int c = lane; c < ch.ncols; c += 32)
+            S.cinfo[S.colstart[ci] + c] =
+                make_float2(__uint_as_float((uint32_t)(ch.vec + c) | kind), ch.scale);
+    }
+    __syncthreads();
+    const int R = it.rows;
+    const int MT = R > 128 ? 2 : 1;
+    const int ncol = S.ncol;
+    const int nst = (ncol + T2_KC - 1) / T2_KC;
+    const uint32_t tmem = S.tmem;
+    if (warp == T2_CONS) {  // ---- MMA issue ----
+        if (lane == 0) {
+            int issued = -1;
+            for (int k = 0; k < nst; ++k) {
+                const int slot = k & 1;
+                if (!mbar_wait(&S.ready[slot], (k >> 1) & 1)) {
+                    atomicExch(err, MV_ERR_TIMEOUT);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sb = smem_u32(S.b[slot]);
+                for (int t = 0; t < MT; ++t) {
+                    const uint32_t sa = smem_u32(S.a[slot][t]);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t da = umma_desc(sa + kk * 256), db = umma_desc(sb + kk * 256);
+                        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                tmem + (uint32_t)(t * 64)),
+                            "l"(da), "l"(db), "r"(T2_IDESC), "r"(acc));
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&S.done[slot]))
+                    : "memory");
+                issued = k;
+            }
+            if (issued >= 0 && !mbar_wait(&S.done[issued & 1], (issued >> 1) & 1))
+                atomicExch(err, MV_ERR_TIMEOUT);  // own MMAs complete before the buffers go
+        }
+        __syncwarp();
+    } else {  // ---- consumers: operands in, accumulators out ----
+        const int RQ = (R + 3) >> 2;  // row quads (ld16 = 4 RQ)
+        const int ld16 = S.hdr[0].ld;
+        const uint32_t* src0 = arena + S.hdr[0].data;
+        const int task = tid;  // (column group cg, row quad q), q fastest
+        const int cg = task / RQ, q = task - cg * RQ;
+        const bool has_task = task < 4 * RQ;
+        uint4 u[4];
+        auto load_a = [&](int k) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = k * T2_KC + 4 * cg + c;
+                u[c] = (has_task && k < nst && j < ncol)
+                           ? __ldcs(reinterpret_cast<const uint4*>(src0 + (size_t)j * ld16) + q)
+                           : make_uint4(0, 0, 0, 0);
+            }
+        };
+        float2 wv[2];
+        float wsc[2];
+        auto load_w = [&](int k) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = k * T2_KC + warp + c * T2_CONS;
+                wv[c] = make_float2(0.f, 0.f);
+                wsc[c] = 0.f;
+                if (k < nst && j < ncol) {
+                    const float2 ci = S.cinfo[j];
+                    const uint32_t code = __float_as_uint(ci.x);
+                    const float2* src = (code & 0x80000000u) ? T : X;
+                    wv[c] = __ldg(src + (int64_t)(code & 0x7fffffffu) * NR + lane);
+                    wsc[c] = ci.y;
+                }
+            }
+        };
+        load_a(0);
+        load_w(0);
+        for (int k = 0; k < nst; ++k) {
+            const int slot = k & 1;
+            if (k >= 2 && !mbar_wait(&S.done[slot], ((k >> 1) - 1) & 1)) {
+                atomicExch(err, MV_ERR_TIMEOUT);
+                *(volatile int32_t*)&S.abort = 1;
+            }
+            if (__any_sync(0xffffffffu, *(volatile int32_t*)&S.abort)) break;  // warp-uniform
+            // A: rows 4q..4q+3 of columns 4cg..4cg+3, transposed into four 16-byte rows
+            if (has_task) {
+                const uint32_t* w = reinterpret_cast<const uint32_t*>(u);  // w[4 c + i]: column c, row i
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = 4 * q + i;
+                    const int t = r >> 7, rr = r & 127;
+                    if (t < MT) {
+                        unsigned char* dst = S.a[slot][t] + (rr >> 3) * T2_SBO + cg * 128 + (rr & 7) * 16;
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[i], w[4 + i], w[8 + i], w[12 + i]);
+                    }
+                }
+            }
+            // B: w_j as (w_r, -w_i) for real column 2s and (w_i, w_r) for 2s + 1
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = warp + c * T2_CONS;  // stage-local column
+                const float wr = wv[c].x * wsc[c], wi = wv[c].y * wsc[c];
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int n = 2 * lane + v;
+                    const uint32_t word = v == 0 ? pack_bf16(wr, -wi) : pack_bf16(wi, wr);
+                    *reinterpret_cast<uint32_t*>(S.b[slot] + (n >> 3) * T2_SBO + (j >> 2) * 128 +
+                                                 (n & 7) * 16 + (j & 3) * 4) = word;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.ready[slot]);
+            load_a(k + 1);
+            load_w(k + 1);
+        }
+        // every stage's MMAs done: accumulators to Y
+        const int last = nst - 1;
+        bool ok = last >= 0 && !*(volatile int32_t*)&S.abort;
+        if (ok && !mbar_wait(&S.done[last & 1], (last >> 1) & 1)) {
+            atomicExch(err, MV_ERR_TIMEOUT);
+            ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int t = warp >> 2, lg = warp & 3;
+        if (ok && t < MT) {
+            const int r = t * 128 + lg * 32 + lane;
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(t * 64 + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (r < R) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 2)  // real columns 2s, 2s + 1: RHS s
+                        atomicAdd(Y + (it.dof + r) * NR + (c0 + e) / 2,
+                                  make_float2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == T2_CONS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(T2_TMEM_COLS));
+}
+
 // X[(3p + a) * 32 + s] = x_s[3 perm[p] + a]  (zero for s >= nrhs)
 __global__ void gather_multi_kernel(const int64_t* perm, const double2* x, int64_t n, int nrhs,
                                     float2* X, int64_t nc) {
@@ -411,6 +663,15 @@ static_assert(sizeof(P2Smem) <= 113 * 1024, "phase 2: two CTAs per SM");
 
 }  // namespace
 
+static void launch_phase2(MatvecDev* m, cudaStream_t st) {
+    if (m->phase2_tc)
+        mvt_phase2<<<(unsigned)m->n2, T2_THREADS, sizeof(T2Smem), st>>>(
+            m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
+    else
+        mvm_phase2<<<(unsigned)m->n2, P2_THREADS, sizeof(P2Smem), st>>>(
+            m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
+}
+
 // Algorithmic bytes of one block product: the stored BF16 entries and scales,
 // plus X, T and Y for NRHS_BLOCK right-hand sides (complex64 each way).
 int64_t matvec_multi_alg_bytes(const MatvecDev* m, int64_t ndof) {
@@ -428,6 +689,11 @@ void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2
                                      (int)sizeof(P1Smem)));
         HM_CUDA(cudaFuncSetAttribute(mvm_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(P2Smem)));
+        HM_CUDA(cudaFuncSetAttribute(mvt_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(T2Smem)));
+        // phase 2 on tcgen05 unless HM_BLOCK_PHASE2=mma asks for the mma.sync kernel
+        const char* e = getenv("HM_BLOCK_PHASE2");
+        m->phase2_tc = (e && e[0] == 'm') ? 0 : 1;
         HM_CUDA(cudaMalloc((void**)&m->xm, (size_t)n * NR * sizeof(float2)));
         HM_CUDA(cudaMalloc((void**)&m->ym, (size_t)n * NR * sizeof(float2)));
         HM_CUDA(cudaMalloc((void**)&m->tm, (size_t)std::max<int64_t>(m->t_elems, 1) * NR * sizeof(float2)));
@@ -447,8 +713,7 @@ void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2
             HM_LAUNCHED();
         }
         if (m->n2) {
-            mvm_phase2<<<(unsigned)m->n2, P2_THREADS, sizeof(P2Smem), st>>>(
-                m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
+            launch_phase2(m, st);
             HM_CUDA(cudaGetLastError());
             HM_LAUNCHED();
         }
@@ -482,8 +747,7 @@ void matvec_multi_profile(MatvecDev* m, const int64_t* d_perm, const double2* x,
         }
         HM_CUDA(cudaEventRecord(ev[2], st));
         if (m->n2) {
-            mvm_phase2<<<(unsigned)m->n2, P2_THREADS, sizeof(P2Smem), st>>>(
-                m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
+            launch_phase2(m, st);
             HM_LAUNCHED();
         }
         HM_CUDA(cudaEventRecord(ev[3], st));

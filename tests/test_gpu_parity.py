@@ -415,3 +415,31 @@ def test_bf16_storage_product_and_refinement(hm, oracle):
     # the residual of the mixed solution, with the plain operator
     r = b.cpu().numpy() - H32.matvec(cuda(x16)).cpu().numpy()
     assert np.linalg.norm(r) <= 2e-6 * np.linalg.norm(b.cpu().numpy())
+
+
+def test_coincident_points_refused(hm):
+    """Two distinct points at one position have a singular Green's tensor
+    (Eq. elasto_U): the build refuses the input and names them."""
+    pts = inputs.fibonacci_sphere(500)
+    pts[321] = pts[17]
+    with pytest.raises(hm.HmError) as e:
+        hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", EPS, 3.0, 32)
+    assert e.value.status == hm.HM_ERR_ARG and "17 and 321" in str(e.value)
+
+
+def test_tiny_and_lopsided_clouds(hm, oracle):
+    """Two points; all points on a line (zero extent in two axes); a cloud
+    with a far outlier (one point alone in its half of the first split)."""
+    rho, lam, mu, om = inputs.material(3.0)
+    pb = oracle.problem(rho, lam, mu, om, "U")
+    line = np.stack([np.linspace(0, 1, 300), np.zeros(300), np.zeros(300)], axis=1)
+    outlier = np.vstack([inputs.fibonacci_sphere(400), [[40.0, 0.0, 0.0]]])
+    for pts in (np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1]]), line, outlier):
+        nc = len(pts)
+        H = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", EPS, 3.0, 16)
+        x = inputs.random_rhs(3 * nc, seed=nc)
+        y = H.matvec(cuda(x)).cpu().numpy()
+        ref = oracle.HMatrix(pb, pts, eps=EPS, eta=3.0, leaf=16)
+        yd = oracle.dense_matrix(pb, pts) @ x
+        assert np.linalg.norm(y - ref.matvec(x)) <= 1e-5 * np.linalg.norm(yd)
+        assert np.linalg.norm(y - yd) <= 3 * EPS * np.linalg.norm(yd)
