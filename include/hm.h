@@ -148,8 +148,8 @@ hm_status hm_build_batch(int32_t nprob, const hm_problem* probs, double eps, con
  *   nrhs  >= 1.  Work is enqueued on stream; the call does not synchronise.
  * With BF16 storage and nrhs > 1 the right-hand sides are taken in blocks of
  * HM_NRHS_BLOCK (the last one padded with zeros) and each block runs as one
- * dense contraction on the tensor cores: X, T = V^H X and the products in
- * BF16, sums in FP32 (relative error a few 2^-9).  Otherwise each right-hand
+ * dense contraction on the tcgen05 tensor cores: X, T = V^H X and the
+ * products in BF16, sums in FP32 (relative error a few 2^-9).  Otherwise each right-hand
  * side is one product with FP32 (or BF16 x FP32) arithmetic.
  * Errors: HM_ERR_ARG (null/overlapping pointers, nrhs < 1), HM_ERR_CUDA.  With
  * BF16 storage the product kernels wait on their own shared-memory copies with
@@ -339,8 +339,9 @@ hm_status hm_rank_model_grad(const float* params, const float* feats, const floa
 hm_status hm_profile_matvec(hm_handle h, int32_t reps, double* ms, int64_t* bytes, void* stream);
 
 /* Same report for the tensor-core product of one block of HM_NRHS_BLOCK
- * right-hand sides (BF16 storage only): ms[0] gather X, ms[1] phase 1
- * (T = V^H X), ms[2] phase 2 (Y = D X + U T), ms[3] scatter Y; bytes[0] is its
+ * right-hand sides (BF16 storage only): ms[0] gather X (and zero T, Y),
+ * ms[1] phase 1 (T = V^H X), ms[2] rounding T to BF16 and phase 2
+ * (Y = D X + U T), ms[3] scatter Y; bytes[0] is its
  * algorithmic byte count (stored BF16 entries and scales, plus X, T and Y,
  * complex64, read or written once each).
  * Errors: HM_ERR_ARG, HM_ERR_UNSUPPORTED (FP32 storage), HM_ERR_TIMEOUT,

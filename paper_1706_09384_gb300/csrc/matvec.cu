@@ -583,18 +583,20 @@ __global__ void gather_hdr16_kernel(const DevChunk16* src, const int32_t* order,
     if (q < n) dst[q] = src[order[q]];
 }
 
-// FP32 chunk -> BF16 chunk with a per-chunk scale (largest component magnitude).
+// FP32 chunk -> BF16 chunk.  Low-rank factors carry one scale per block and
+// factor (the largest component magnitude of U, resp. V, over all chunks of
+// the block); dense blocks are stored unscaled (BF16 keeps FP32's exponent
+// range).  A V chunk also records its block's U scale (fold), so that a
+// product may apply s_U s_V once to t = V^H x and use U's entries as stored.
 struct ConvJob {
-    int64_t src;   // FP32 arena offset
+    int64_t src;    // FP32 arena offset
     int32_t ld32;
     int32_t chunk;  // index into chunks16
+    int64_t slot;   // 2 block + (kind == V), -1 for dense
 };
-__global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const float2* arena32,
-                                                      uint32_t* arena16, DevChunk16* chunks16) {
-    __shared__ float red[8];
-    const ConvJob J = jobs[blockIdx.x];
-    DevChunk16* ch = chunks16 + J.chunk;
-    const int rows = ch->rows, ncols = ch->ncols, ld16 = ch->ld;
+__device__ __forceinline__ float chunk_absmax(const ConvJob& J, const DevChunk16* ch,
+                                              const float2* arena32, float* red) {
+    const int rows = ch->rows, ncols = ch->ncols;
     const int64_t n = (int64_t)rows * ncols;
     float mx = 0.f;
     for (int64_t e = threadIdx.x; e < n; e += 256) {
@@ -607,7 +609,31 @@ __global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const
     __syncthreads();
     mx = red[0];
     for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
-    const float scale = mx > 0.f ? mx : 1.f;
+    return mx;
+}
+__global__ void __launch_bounds__(256) block_absmax_kernel(const ConvJob* jobs, const float2* arena32,
+                                                           const DevChunk16* chunks16, uint32_t* bmax) {
+    __shared__ float red[8];
+    const ConvJob J = jobs[blockIdx.x];
+    if (J.slot < 0) return;
+    const float mx = chunk_absmax(J, chunks16 + J.chunk, arena32, red);
+    if (threadIdx.x == 0) atomicMax(bmax + J.slot, __float_as_uint(mx));  // non-negative floats order as integers
+}
+__global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const float2* arena32,
+                                                      uint32_t* arena16, DevChunk16* chunks16,
+                                                      const uint32_t* bmax) {
+    const ConvJob J = jobs[blockIdx.x];
+    DevChunk16* ch = chunks16 + J.chunk;
+    const int rows = ch->rows, ncols = ch->ncols, ld16 = ch->ld;
+    float scale = 1.f, fold = 1.f;
+    if (J.slot >= 0) {
+        const float m = __uint_as_float(bmax[J.slot]);
+        scale = m > 0.f ? m : 1.f;
+        if (J.slot & 1) {  // V chunk: the block's U scale
+            const float mu = __uint_as_float(bmax[J.slot - 1]);
+            fold = mu > 0.f ? mu : 1.f;
+        }
+    }
     const float inv = 1.f / scale;
     const int64_t n16 = (int64_t)ld16 * ncols;
     for (int64_t e = threadIdx.x; e < n16; e += 256) {
@@ -621,7 +647,10 @@ __global__ void __launch_bounds__(256) to_bf16_kernel(const ConvJob* jobs, const
         }
         arena16[ch->data + e] = w;
     }
-    if (threadIdx.x == 0) ch->scale = scale;
+    if (threadIdx.x == 0) {
+        ch->scale = scale;
+        ch->fold = fold;
+    }
 }
 
 __global__ void scatter_y64_kernel(const int64_t* perm, const double2* yp, double2* y, int64_t nc) {
@@ -899,22 +928,30 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
     std::vector<DevChunk16> c16(plan.chunks.size());
     std::vector<ConvJob> jobs;
     int64_t off = 0;
+    // Every work item starts on a multiple of its leading dimension, so that
+    // the tensor-core product can address it as whole rows of a 2-D view of
+    // the arena with row pitch ld16 (one TMA descriptor per ld16).
+    std::vector<char> item_start(plan.chunks.size(), 0);
+    for (const WorkItem& w : m->h_items1) item_start[m->h_order1[w.first]] = 1;
+    for (const WorkItem& w : m->h_items2) item_start[m->h_order2[w.first]] = 1;
     // same order as the FP32 arena: row streams first, then V by column leaf
     std::vector<int32_t> seq(plan.row_items);
     seq.insert(seq.end(), plan.col_items.begin(), plan.col_items.end());
     for (int32_t id : seq) {
         const Chunk& c = plan.chunks[id];
         DevChunk16& d = c16[id];
+        // >= 32 rows: a 64-element (128-byte) swizzle row never exceeds a column
+        d.ld = (int32_t)std::max<int64_t>(hm_round_up(c.rows, 4), 32);
+        if (item_start[id]) off = hm_round_up(off, d.ld);
         d.data = off;
         d.vec = c.vec;
-        d.ld = (int32_t)hm_round_up(c.rows, 4);
         d.ncols = c.ncols;
         d.kind = c.kind;
         d.rows = c.rows;
         d.scale = 1.f;
-        d.pad_ = 0;
+        d.fold = 1.f;
         off += (int64_t)d.ld * c.ncols;
-        if (c.ncols > 0) jobs.push_back({c.data, c.ld, id});
+        if (c.ncols > 0) jobs.push_back({c.data, c.ld, id, c.kind == 0 ? -1 : 2 * c.block + (c.kind == 2)});
         if (c.ncols > 0) (c.kind == 2 ? m->nchunks_v : m->nchunks_du)++;
     }
     // the streamed kernels read every item as one contiguous column-major matrix
@@ -931,6 +968,9 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
             }
             if (cols > MAX_ITEM_COLS || w.last - w.first > MAX_ITEM_CHUNKS)
                 hm_throw(HM_ERR_UNSUPPORTED, "BF16 item too large");
+            const DevChunk16& a = c16[order[w.first]];
+            if (a.data % a.ld || a.data / a.ld > INT32_MAX - MAX_ITEM_COLS)
+                hm_throw(HM_ERR_UNSUPPORTED, "BF16 item not on a row of its ld view");
         }
     };
     check_items(m->h_items1, m->h_order1);
@@ -942,6 +982,13 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
     m->arena16_elems = off;
     m->nchunks = (int64_t)c16.size();
     m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4, st, true);
+    {  // TMA descriptors of the block product: [phase][ld16 / 4]
+        std::vector<int32_t> lds;
+        for (const WorkItem& w : m->h_items1) lds.push_back(c16[m->h_order1[w.first]].ld);
+        for (const WorkItem& w : m->h_items2) lds.push_back(c16[m->h_order2[w.first]].ld);
+        m->tmaps = hm_dmalloc(owner, 2 * TMAP_PER_PHASE * 128, st, true);
+        make_block_tmaps(m->tmaps, m->arena16, off, lds, st);
+    }
     m->chunks16 = (DevChunk16*)hm_dmalloc(owner, std::max<size_t>(c16.size(), 1) * sizeof(DevChunk16),
                                           st, false);
     HM_CUDA(cudaMemcpyAsync(m->chunks16, c16.data(), c16.size() * sizeof(DevChunk16),
@@ -950,9 +997,18 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
         ConvJob* d = nullptr;
         HM_CUDA(cudaMallocAsync((void**)&d, jobs.size() * sizeof(ConvJob), st));
         HM_CUDA(cudaMemcpyAsync(d, jobs.data(), jobs.size() * sizeof(ConvJob), cudaMemcpyHostToDevice, st));
-        to_bf16_kernel<<<(unsigned)jobs.size(), 256, 0, st>>>(d, m->arena, m->arena16, m->chunks16);
+        int64_t nblk = 0;
+        for (const Chunk& c : plan.chunks) nblk = std::max<int64_t>(nblk, c.block + 1);
+        uint32_t* bmax = nullptr;
+        HM_CUDA(cudaMallocAsync((void**)&bmax, std::max<int64_t>(2 * nblk, 1) * 4, st));
+        HM_CUDA(cudaMemsetAsync(bmax, 0, std::max<int64_t>(2 * nblk, 1) * 4, st));
+        block_absmax_kernel<<<(unsigned)jobs.size(), 256, 0, st>>>(d, m->arena, m->chunks16, bmax);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
+        to_bf16_kernel<<<(unsigned)jobs.size(), 256, 0, st>>>(d, m->arena, m->arena16, m->chunks16, bmax);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+        HM_CUDA(cudaFreeAsync(bmax, st));
         HM_CUDA(cudaFreeAsync(d, st));
     }
     m->hdr16_1 = (DevChunk16*)hm_dmalloc(owner, std::max<int64_t>(m->n_o1, 1) * sizeof(DevChunk16), st, false);
@@ -974,9 +1030,11 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
 void matvec_dev_destroy(MatvecDev* m) {
     if (!m) return;
     matvec_graph_reset(m);
-    if (m->xm) cudaFree(m->xm);
+    if (m->xb) cudaFree(m->xb);
     if (m->ym) cudaFree(m->ym);
     if (m->tm) cudaFree(m->tm);
+    if (m->t16) cudaFree(m->t16);
+    if (m->tmap_xb) cudaFree(m->tmap_xb);
     delete m;
 }
 void* matvec_arena(MatvecDev* m) { return m->arena; }

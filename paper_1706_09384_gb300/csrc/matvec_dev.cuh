@@ -18,8 +18,9 @@ struct DevChunk {
     int32_t kind;
     int32_t rows;
 };
-// Chunk of the BF16 arena: complex entries as two bf16 (4 bytes), scaled by a
-// per-chunk FP32 factor; rows padded to a multiple of 4 (16-byte columns).
+// Chunk of the BF16 arena: complex entries as two bf16 (4 bytes), to be
+// multiplied by an FP32 scale (one per block and factor for U and V, 1 for
+// dense blocks); rows padded to a multiple of 4 (16-byte columns), at least 32.
 struct DevChunk16 {
     int64_t data;   // element offset in arena16
     int64_t vec;
@@ -28,7 +29,7 @@ struct DevChunk16 {
     int32_t kind;
     int32_t rows;
     float scale;
-    int32_t pad_;
+    float fold;     // V chunks: the U scale of the same block; otherwise 1
 };
 struct WorkItem {
     int64_t dof;      // first tree-order DOF of the leaf
@@ -78,12 +79,22 @@ struct MatvecDev {
     int* d_err = nullptr;             // error code written by the streamed kernels
     std::vector<WorkItem> h_items1, h_items2;
     std::vector<int32_t> h_order1, h_order2;
-    // block of NRHS_BLOCK right-hand sides (tensor-core product), allocated on first use
-    float2* xm = nullptr;
+    // block of NRHS_BLOCK right-hand sides (tensor-core product), allocated on
+    // first use: XB bf16 rows (x, -i x) per DOF, Y and T in FP32, T16 = bf16(T)
+    uint32_t* xb = nullptr;
     float2* ym = nullptr;
     float2* tm = nullptr;
-    int32_t phase2_tc = 0;  // 1: phase 2 on tcgen05 (TMEM accumulators), 0: mma.sync
+    uint32_t* t16 = nullptr;
+    // TMA descriptors (CUtensorMap, 128 bytes each): the BF16 arena viewed as
+    // rows of 2 ld16 bf16, [phase 1 | phase 2][ld16 / 4]; and XB
+    void* tmaps = nullptr;
+    void* tmap_xb = nullptr;
 };
+constexpr int TMAP_PER_PHASE = MAX_LD / 4 + 1;
+// Encodes the descriptors for the leading dimensions in lds (device copy at
+// d_maps, 2 * TMAP_PER_PHASE entries); defined with the block product.
+void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,
+                      const std::vector<int32_t>& lds, cudaStream_t st);
 
 // Block of NRHS_BLOCK right-hand sides for the tensor-core product (created on
 // first use; tree-order vectors, right-hand side fastest: v[dof * NRHS_BLOCK + s]).

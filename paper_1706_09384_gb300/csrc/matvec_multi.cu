@@ -1,35 +1,42 @@
 // matvec_multi.cu — the H-matrix product (Sec. 3.1) for a block of
-// NRHS_BLOCK = 32 right-hand sides on the tensor cores, BF16 storage only.
+// NRHS_BLOCK = 32 right-hand sides on the tcgen05 tensor cores, BF16 storage.
 //
 // With 32 right-hand sides every stored complex entry meets 32 vector
-// entries: D X and U (V^H X) become dense contractions (64 flops per stored
-// byte), so the complex products run as real BF16 MMAs (mma.sync m16n8k16,
-// FP32 accumulation).  A stored complex entry a = (a_r, a_i) is one bf16 pair,
-// i.e. two consecutive K elements of the MMA's A operand.  The B operand
-// supplies, for right-hand side s, two real columns whose K-pairs are
-//   phase 2 (Y += M W):   column 2s: (w_r, -w_i)   column 2s+1: (w_i,  w_r)
-//   phase 1 (T = V^H X):  column 2s: (x_r,  x_i)   column 2s+1: (x_i, -x_r)
-// so the FP32 accumulators of columns 2s and 2s+1 are the real and imaginary
-// parts of the complex result for right-hand side s (phase 1 conjugates V).
+// entries: D X and U (V^H X) become dense contractions, run as real BF16 MMAs
+// (kind::f16, FP32 accumulators in TMEM).  A complex entry a = (a_r, a_i) is
+// one bf16 pair; the right-hand side s occupies the real columns n = 2s
+// (real part) and n = 2s + 1 (imaginary part) of the MMA's N = 64.
 //
-// Both phases stream the items of the BF16 arena (the chunks of one leaf, one
-// contiguous column-major matrix) through a ring of shared-memory stages with
-// bulk asynchronous copies, one copy per column into a padded slot so the
-// fragment loads hit distinct banks.  Shared-memory traffic per stored byte
-// is kept low by register blocking:
-//   phase 1: K = rows of the column leaf (<= 192) is short and X is fixed per
-//            item, so each consumer warp keeps its B fragments (two n-tiles,
-//            all k-steps) in registers; the A tiles (16 columns of V) are read
-//            with ldmatrix by the four consumer warps.
-//   phase 2: M = rows of the row leaf (<= 192, 12 m-tiles), N = 64; eight
-//            consumer warps each own 3 m-tiles x 4 n-tiles of the item's
-//            accumulators; the per-column weights w_j = scale_j v_j of each
-//            stage are converted once into a shared table.
-// Vectors (tree order, right-hand side fastest): X[dof][32], T[t][32],
-// Y[dof][32], complex FP32.
+//  phase 1, t = s_U s_V V^H x per V column j (M = columns, K = 2 rows):
+//     A[j][2r + c] = component c of V[r][j] (the stored column, K-major),
+//     B[2r][n]     = (x_r, x_i) of right-hand side n / 2    (row 2r of XB),
+//     B[2r + 1][n] = (x_i, -x_r), i.e. -i x               (row 2r + 1 of XB),
+//     so D[j][2s] + i D[j][2s + 1] = sum_r conj(V[r][j]) x_s[r].
+//  phase 2, y += M w over the item's columns j (M = 2 rows, K = columns):
+//     A[2r + c][j] = component c of M[r][j] (the stored column, MN-major),
+//     B[j][n]      = the bf16 row of w_j: T16 row t_j (U columns) or XB row
+//                    2 dof_j (dense columns),
+//     so y_r(s) = D[2r][2s] - D[2r+1][2s+1] + i (D[2r][2s+1] + D[2r+1][2s]).
+//
+// The BF16 arena is viewed, per leading dimension ld16, as a 2-D tensor whose
+// rows are the stored columns (2 ld16 bf16 each, 4 ld16 bytes apart); every
+// work item (the chunks of one leaf, stored back to back) starts on a row of
+// that view.  TMA loads 128-byte-swizzled tiles of it (and of XB) straight
+// into the operand layout the MMA reads, so no thread touches the stored
+// entries.  One CTA per item: warp 0 issues the TMA loads, warp 1 the MMAs
+// (it owns the TMEM allocation), warps 2-5 copy the phase-2 weight rows and
+// move the accumulators out (FP32 atomics: several items share T rows and Y
+// rows).  Every wait is bounded; a timeout sets the error word and the CTA
+// drains its own copies and MMAs before it retires.
+//
+// Vectors (tree order, right-hand side fastest, complex): XB[2 dof + c][32]
+// bf16 pairs, T[t][32] FP32 (accumulated), T16[t][32] bf16 pairs, Y[dof][32]
+// FP32.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "matvec_dev.cuh"
 #include "pipeline.cuh"
@@ -37,44 +44,61 @@
 namespace {
 
 constexpr int NR = NRHS_BLOCK;
-static_assert(NR == 32 && NR == HM_NRHS_BLOCK, "the fragment maps below assume 32 right-hand sides (8 n-tiles)");
-
-constexpr int P1_CONS = 4;
-constexpr int P1_THREADS = 32 * (P1_CONS + 1);
-constexpr int P1_G = 16;               // V columns per stage: one m16 tile
-constexpr int P1_NSTAGE = 3;
-constexpr int P1_LDP = 196;            // largest slot stride (words): >= 192, = 4 mod 8
-constexpr int P1_KMAX = MAX_LD / 8;    // k-steps of 8 complex rows
-
-constexpr int P2_CONS = 8;
-constexpr int P2_THREADS = 32 * (P2_CONS + 1);
-constexpr int P2_G = 32;               // columns per stage: 4 k-steps
-constexpr int P2_NSTAGE = 3;
-constexpr int P2_LDP = 200;            // largest slot stride (words): >= 192, = 8 mod 16
-constexpr int P2_WLD = 72;             // weight-table row stride (words), = 8 mod 32
-
+static_assert(NR == 32 && NR == HM_NRHS_BLOCK, "N = 64 real columns: 32 right-hand sides");
 constexpr int MV_ERR_TIMEOUT = 1;
 
-struct P1Smem {
-    alignas(128) uint32_t stage[P1_NSTAGE][P1_G * P1_LDP];
-    float2 cinfo[MAX_ITEM_COLS];  // (t index bits, chunk scale)
+constexpr int TC_THREADS = 192;
+constexpr int TC_NS = 3;                              // pipeline stages
+constexpr int TC_KBMAX = 2 * MAX_LD / 64;             // 64-wide K boxes of a column (6)
+constexpr int TC1_ABYTES = 128 * 128;                 // 128 columns x 64 bf16 of K
+constexpr int TC1_BBYTES = 64 * 128;                  // 64 K rows of XB
+constexpr int TC2_ABYTES = TC_KBMAX * 4096;           // up to six 64 x 32 boxes
+constexpr int TC2_WBYTES = 32 * 128;                  // 32 weight rows
+constexpr uint32_t TC1_TMEM_COLS = 128;               // two 128 x 64 accumulators
+constexpr uint32_t TC2_TMEM_COLS = 256;               // up to three 128 x 64 accumulators
+// kind::f16 instruction descriptor: FP32 accumulate (bit 4), A and B BF16
+// (bits 7, 10), A MN-major (bit 15), B MN-major (bit 16), N >> 3 at bit 17,
+// M >> 4 at bit 24; M = 128, N = 64
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(64 >> 3) << 17) |
+                              (uint32_t(128 >> 4) << 24);
+constexpr uint32_t TC_A_MN = 1u << 15;
+constexpr uint32_t TC_B_MN = 1u << 16;
+
+struct TC1Smem {
+    unsigned char a[TC_NS][TC1_ABYTES];  // 1024-byte aligned (swizzle atoms)
+    unsigned char b[TC_KBMAX][TC1_BBYTES];
+    float2 cinfo[MAX_ITEM_COLS];         // (t index bits, s_V s_U)
     DevChunk16 hdr[MAX_ITEM_CHUNKS];
     int32_t colstart[MAX_ITEM_CHUNKS + 1];
     int32_t ncol;
-    alignas(8) uint64_t full[P1_NSTAGE];
-    uint64_t empty[P1_NSTAGE];
+    int32_t abort;
+    uint32_t tmem;
+    alignas(8) uint64_t full[TC_NS];
+    uint64_t empty[TC_NS];
+    uint64_t bfull;
+    uint64_t accf[2];
+    uint64_t acce[2];
 };
-struct P2Smem {
-    alignas(128) uint32_t stage[P2_NSTAGE][P2_G * P2_LDP];
-    alignas(16) uint32_t wt[2][P2_G * P2_WLD];  // per-stage weights, double-buffered
-    float2 cinfo[MAX_ITEM_COLS];  // (source index | kind << 31, chunk scale)
+struct TC2Smem {
+    unsigned char a[TC_NS][TC2_ABYTES];
+    unsigned char w[TC_NS][TC2_WBYTES];
+    float2 cinfo[MAX_ITEM_COLS];         // (source row | kind << 31, unused)
     DevChunk16 hdr[MAX_ITEM_CHUNKS];
     int32_t colstart[MAX_ITEM_CHUNKS + 1];
     int32_t ncol;
-    int32_t abort;  // a consumer's wait gave up: all consumers leave after the next barrier
-    alignas(8) uint64_t full[P2_NSTAGE];
-    uint64_t empty[P2_NSTAGE];
+    int32_t abort;
+    uint32_t tmem;
+    alignas(8) uint64_t full[TC_NS];
+    uint64_t wfull[TC_NS];
+    uint64_t empty[TC_NS];
+    uint64_t accf;
 };
+// two CTAs per SM: TMEM 2 x 256 columns at most, shared memory 2 x (size + 1 KB
+// alignment slack + 1 KB reserved) within 228 KB
+static_assert(sizeof(TC1Smem) + 1024 <= 112 * 1024, "phase 1: two CTAs per SM");
+static_assert(sizeof(TC2Smem) + 1024 <= 112 * 1024, "phase 2: two CTAs per SM");
+static_assert(TC1_ABYTES % 1024 == 0 && TC2_ABYTES % 1024 == 0 && TC2_WBYTES % 1024 == 0,
+              "swizzle atoms stay aligned");
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
@@ -82,377 +106,100 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return l | (h << 16);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+// Shared-memory matrix descriptor, 128-byte swizzle: start >> 4, leading byte
+// offset >> 4 (MN-major: between 64-element atoms along M/N), stride byte
+// offset >> 4 (between 8-row groups), version 1, layout 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                     uint32_t acc) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+// the 64 accumulator columns [col, col + 64) of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld64(uint32_t tmem, int lane_quarter, int col, uint32_t (&v)[64]) {
+    const uint32_t base = tmem + ((uint32_t)(lane_quarter * 32) << 16) + (uint32_t)col;
+    tmem_ld16(base, v);
+    tmem_ld16(base + 16, v + 16);
+    tmem_ld16(base + 32, v + 32);
+    tmem_ld16(base + 48, v + 48);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// y[0..3] += v without a return value (a reduction, not an atomic round trip)
+__device__ __forceinline__ void red_add_v4(float* y, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(y), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// The kernel's shared-memory struct at the first 1024-byte boundary of the
+// dynamic allocation (which carries 1024 bytes of slack).
+template <typename Smem>
+__device__ __forceinline__ Smem& tc_smem(unsigned char* raw) {
+    return *reinterpret_cast<Smem*>(raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u));
 }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1,
-                                            uint32_t& r2, uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-// Headers of the item into shared memory, barriers initialised, column
-// offsets of the chunks (exclusive scan), stages zeroed (slot padding is
-// never written by the copies and must read as zero).
-template <typename Smem, int NSTAGE, int NCONS, int THREADS>
-__device__ __forceinline__ void item_prologue(Smem& S, const WorkItem& it, const DevChunk16* hdr) {
+// Headers, TMEM allocation (warp 1), column offsets of the chunks and the
+// per-column table: phase 1 (t index, s_V s_U), phase 2 (source row | kind).
+// Barriers are initialised by the caller before; ends past a block barrier.
+template <typename Smem, bool PHASE2>
+__device__ __forceinline__ void tc_prologue(Smem& S, const WorkItem& it, const DevChunk16* hdr,
+                                            uint32_t tmem_cols) {
     const int nch = it.last - it.first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nch; i += THREADS) S.hdr[i] = hdr[it.first + i];
-    uint32_t* st = &S.stage[0][0];
-    constexpr int NW = (int)(sizeof(S.stage) / 4);
-    for (int i = tid; i < NW; i += THREADS) st[i] = 0u;
-    if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(&S.full[s], 1);
-            mbar_init(&S.empty[s], NCONS);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int a0 = 2 * lane < nch ? S.hdr[2 * lane].ncols : 0;
-        const int a1 = 2 * lane + 1 < nch ? S.hdr[2 * lane + 1].ncols : 0;
-        int inc = a0 + a1;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
-        }
-        const int exc = inc - a0 - a1;
-        S.colstart[2 * lane] = exc;
-        S.colstart[2 * lane + 1] = exc + a0;
-        if (lane == 31) {
-            S.colstart[MAX_ITEM_CHUNKS] = inc;
-            S.ncol = inc;
-        }
-    }
-    __syncthreads();
-}
-
-// Producer (one lane): the item's columns, G per stage, each into a slot of
-// ldp words; waits for a stage to be released before refilling it and for
-// its own copies before returning.
-template <typename Smem, int NSTAGE, int G>
-__device__ __forceinline__ void item_producer(Smem& S, const uint32_t* arena, int ldp, int* err) {
-    const int ncol = S.ncol;
-    const int ld16 = S.hdr[0].ld;
-    const uint32_t colb = (uint32_t)ld16 * 4u;
-    const int nst = (ncol + G - 1) / G;
-    const uint32_t* src0 = arena + S.hdr[0].data;
-    int issued = 0;
-    for (int k = 0; k < nst; ++k) {
-        const int s = k % NSTAGE;
-        if (k >= NSTAGE && !mbar_wait(&S.empty[s], ((k / NSTAGE) - 1) & 1)) {
-            atomicExch(err, MV_ERR_TIMEOUT);
-            break;
-        }
-        const int g = min(G, ncol - k * G);
-        mbar_arrive_expect_tx(&S.full[s], (uint32_t)g * colb);
-        for (int c = 0; c < g; ++c)
-            bulk_g2s(&S.stage[s][c * ldp], src0 + (size_t)(k * G + c) * ld16, colb, &S.full[s]);
-        ++issued;
-    }
-    for (int k = max(0, issued - NSTAGE); k < issued; ++k)
-        if (!mbar_wait(&S.full[k % NSTAGE], (k / NSTAGE) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
-}
-
-// ---- phase 1: T[t_j][s] += scale_j * sum_r conj(V[r][j]) X[dof + r][s] ----
-__global__ void __launch_bounds__(P1_THREADS, 3) mvm_phase1(const WorkItem* items,
-                                                           const DevChunk16* hdr,
-                                                           const uint32_t* __restrict__ arena,
-                                                           const float2* __restrict__ X,
-                                                           float2* T, int* err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    P1Smem& S = *reinterpret_cast<P1Smem*>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
-    item_prologue<P1Smem, P1_NSTAGE, P1_CONS, P1_THREADS>(S, it, hdr);
-    const int R = it.rows;
-    const int ldp = ((R + 7) & ~7) + 4;  // = 4 mod 8: ldmatrix rows on distinct banks
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == P1_CONS) {
-        if (lane == 0) item_producer<P1Smem, P1_NSTAGE, P1_G>(S, arena, ldp, err);
-        return;
-    }
-    const int nch = it.last - it.first;
-    for (int ci = warp; ci < nch; ci += P1_CONS) {
-        const DevChunk16 ch = S.hdr[ci];
-        for (int c = lane; c < ch.ncols; c += 32)
-            S.cinfo[S.colstart[ci] + c] = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale);
-    }
-    // B fragments of this warp's two n-tiles for every k-step, from X of the leaf
-    const int g = lane >> 2, t = lane & 3;
-    const int nks = (R + 7) >> 3;
-    uint32_t breg[P1_KMAX][2][2];
-#pragma unroll
-    for (int ks = 0; ks < P1_KMAX; ++ks)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int s = (2 * warp + q) * 4 + (g >> 1);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = ks * 8 + t + 4 * h;
-                float2 x = make_float2(0.f, 0.f);
-                if (ks < nks && r < R) x = __ldg(X + (it.dof + r) * NR + s);
-                breg[ks][q][h] = (g & 1) ? pack_bf16(x.y, -x.x) : pack_bf16(x.x, x.y);
-            }
-        }
-    named_sync<1, 32 * P1_CONS>();  // column table complete
-    const int ncol = S.ncol;
-    const int nst = (ncol + P1_G - 1) / P1_G;
-    // ldmatrix row addresses: lanes 0-15 rows 0-15 (k 0-7), lanes 16-31 rows 0-15 (k 8-15)
-    const uint32_t lane_off = (uint32_t)(((lane & 15) * ldp + 4 * (lane >> 4)) * 4);
-    for (int k = 0; k < nst; ++k) {
-        const int s = k % P1_NSTAGE;
-        if (!mbar_wait(&S.full[s], (k / P1_NSTAGE) & 1)) {
-            atomicExch(err, MV_ERR_TIMEOUT);
-            break;
-        }
-        const uint32_t abase = smem_u32(S.stage[s]) + lane_off;
-        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int ks = 0; ks < P1_KMAX; ++ks) {
-            if (ks < nks) {
-                uint32_t a0, a1, a2, a3;
-                ldmatrix_x4(abase + ks * 32, a0, a1, a2, a3);
-                mma_bf16(acc[0], a0, a1, a2, a3, breg[ks][0][0], breg[ks][0][1]);
-                mma_bf16(acc[1], a0, a1, a2, a3, breg[ks][1][0], breg[ks][1][1]);
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);
-        const int jb = k * P1_G;
-        const int gk = min(P1_G, ncol - jb);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int sr = (2 * warp + q) * 4 + t;
-            if (g < gk) {
-                const float2 ci = S.cinfo[jb + g];
-                atomicAdd(T + (int64_t)__float_as_int(ci.x) * NR + sr,
-                          make_float2(acc[q][0] * ci.y, acc[q][1] * ci.y));
-            }
-            if (g + 8 < gk) {
-                const float2 ci = S.cinfo[jb + g + 8];
-                atomicAdd(T + (int64_t)__float_as_int(ci.x) * NR + sr,
-                          make_float2(acc[q][2] * ci.y, acc[q][3] * ci.y));
-            }
-        }
-    }
-}
-
-// ---- phase 2: Y[dof + r][s] += sum_j M[r][j] scale_j v_j[s] ----
-__global__ void __launch_bounds__(P2_THREADS, 2) mvm_phase2(const WorkItem* items,
-                                                           const DevChunk16* hdr,
-                                                           const uint32_t* __restrict__ arena,
-                                                           const float2* __restrict__ X,
-                                                           const float2* __restrict__ T,
-                                                           float2* Y, int* err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    P2Smem& S = *reinterpret_cast<P2Smem*>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
-    if (threadIdx.x == 0) S.abort = 0;
-    item_prologue<P2Smem, P2_NSTAGE, P2_CONS, P2_THREADS>(S, it, hdr);
-    const int R = it.rows;
-    const int ldp = ((R + 15) & ~15) + 8;  // = 8 mod 16: fragment loads on distinct banks
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == P2_CONS) {
-        if (lane == 0) item_producer<P2Smem, P2_NSTAGE, P2_G>(S, arena, ldp, err);
-        return;
-    }
-    const int nch = it.last - it.first;
-    for (int ci = warp; ci < nch; ci += P2_CONS) {
-        const DevChunk16 ch = S.hdr[ci];
-        const uint32_t kind = ch.kind == 0 ? 0u : 0x80000000u;
-        for (int c = lane; c < ch.ncols; c += 32)
-            S.cinfo[S.colstart[ci] + c] =
-                make_float2(__uint_as_float((uint32_t)(ch.vec + c) | kind), ch.scale);
-    }
-    named_sync<1, 32 * P2_CONS>();
-    const int g = lane >> 2, t = lane & 3;
-    const int mt0 = warp >> 1, nt0 = 4 * (warp & 1);
-    const int MT = (R + 15) >> 4;
-    float acc[3][4][4];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][q][e] = 0.f;
-    const int ncol = S.ncol;
-    const int nst = (ncol + P2_G - 1) / P2_G;
-    // weights of stage k: loaded into registers one stage ahead (the L2
-    // latency hides behind the MMAs of the stage before), converted and stored
-    // into the double-buffered table after those MMAs
-    constexpr int WPW = P2_G / P2_CONS;  // columns per warp per stage
-    float2 wv[WPW];
-    float wsc[WPW];
-    auto load_w = [&](int k) {
-#pragma unroll
-        for (int c = 0; c < WPW; ++c) {
-            const int jj = warp + c * P2_CONS;
-            const int j = k * P2_G + jj;
-            wv[c] = make_float2(0.f, 0.f);
-            wsc[c] = 0.f;
-            if (k < nst && j < ncol) {
-                const float2 ci = S.cinfo[j];
-                const uint32_t code = __float_as_uint(ci.x);
-                const float2* src = (code & 0x80000000u) ? T : X;
-                wv[c] = __ldg(src + (int64_t)(code & 0x7fffffffu) * NR + lane);
-                wsc[c] = ci.y;
-            }
-        }
-    };
-    auto store_w = [&](int k) {
-        uint32_t* wt = S.wt[k & 1];
-#pragma unroll
-        for (int c = 0; c < WPW; ++c) {
-            const int jj = warp + c * P2_CONS;
-            const float wr = wv[c].x * wsc[c], wi = wv[c].y * wsc[c];
-            *reinterpret_cast<uint2*>(wt + jj * P2_WLD + 2 * lane) =
-                make_uint2(pack_bf16(wr, -wi), pack_bf16(wi, wr));
-        }
-    };
-    load_w(0);
-    store_w(0);
-    for (int k = 0; k < nst; ++k) {
-        const int s = k % P2_NSTAGE;
-        const int jb = k * P2_G;
-        const int gk = min(P2_G, ncol - jb);
-        if (!mbar_wait(&S.full[s], (k / P2_NSTAGE) & 1)) {
-            atomicExch(err, MV_ERR_TIMEOUT);
-            *(volatile int32_t*)&S.abort = 1;
-        }
-        named_sync<1, 32 * P2_CONS>();  // weights of stage k visible; stage k-1 done everywhere
-        if (*(volatile int32_t*)&S.abort) break;  // same decision in every consumer warp
-        load_w(k + 1);
-        const uint32_t* wt = S.wt[k & 1];
-        const uint32_t* sb = S.stage[s];
-#pragma unroll
-        for (int ks = 0; ks < P2_G / 8; ++ks) {
-            const int j0 = ks * 8;
-            if (j0 < gk) {
-                uint32_t b[4][2];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int n = (nt0 + q) * 8 + g;
-                    b[q][0] = wt[(j0 + t) * P2_WLD + n];
-                    b[q][1] = wt[(j0 + t + 4) * P2_WLD + n];
-                }
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int mt = mt0 + 4 * i;
-                    if (mt < MT) {
-                        const int r = mt * 16 + g;
-                        const uint32_t a0 = sb[(j0 + t) * ldp + r];
-                        const uint32_t a1 = sb[(j0 + t) * ldp + r + 8];
-                        const uint32_t a2 = sb[(j0 + t + 4) * ldp + r];
-                        const uint32_t a3 = sb[(j0 + t + 4) * ldp + r + 8];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) mma_bf16(acc[i][q], a0, a1, a2, a3, b[q][0], b[q][1]);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);
-        if (k + 1 < nst) store_w(k + 1);
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int mt = mt0 + 4 * i;
-        if (mt >= MT) continue;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int sr = (nt0 + q) * 4 + t;
-            const int r0 = mt * 16 + g;
-            if (r0 < R) atomicAdd(Y + (it.dof + r0) * NR + sr, make_float2(acc[i][q][0], acc[i][q][1]));
-            if (r0 + 8 < R)
-                atomicAdd(Y + (it.dof + r0 + 8) * NR + sr, make_float2(acc[i][q][2], acc[i][q][3]));
-        }
-    }
-}
-
-// ---- phase 2 on the tcgen05 tensor cores (accumulators in TMEM) ----
-// The item's rows are the MMA's M (up to two tiles of 128), the 64 real output
-// columns its N, the complex columns (as bf16 pairs) its K.  Per stage of 16
-// complex columns (K = 32) the consumer warps load the BF16 columns from the
-// arena (16-byte loads, four columns by four rows per thread) and store them
-// transposed into K-major core matrices (8 rows x 16 bytes, no swizzle; core
-// groups 16 bytes apart beyond their 4 x 128 bytes so the 16-byte stores of
-// one warp hit distinct banks), build the weights w_j = scale_j v_j as the B
-// operand in the same layout, and signal the MMA warp; one thread issues the
-// tcgen05.mma instructions into two TMEM accumulator tiles and commits each
-// stage to an mbarrier that releases its buffers.  At the end the consumers
-// read the accumulators back with tcgen05.ld.  Shared-memory descriptors:
-// start >> 4, leading (K-direction core) byte offset 128, stride (8-row
-// group) byte offset T2_SBO, version 1, no swizzle.
-constexpr int T2_CONS = 8;
-constexpr int T2_THREADS = 32 * (T2_CONS + 1);  // + the MMA warp
-constexpr int T2_KC = 16;                        // complex columns per stage
-constexpr int T2_SBO = 4 * 128 + 16;             // bytes between 8-row core groups
-constexpr int T2_ATILE = 16 * T2_SBO;            // 128 rows
-constexpr int T2_BBYTES = 8 * T2_SBO;            // 64 rows (real output columns)
-constexpr uint32_t T2_TMEM_COLS = 128;           // two 128 x 64 FP32 accumulators
-// kind::f16: FP32 accumulate (bit 4), A and B BF16 (bits 7, 10), both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t T2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(64 >> 3) << 17) |
-                              (uint32_t(128 >> 4) << 24);
-
-struct T2Smem {
-    alignas(128) unsigned char a[2][2][T2_ATILE];  // [slot][m tile]
-    alignas(128) unsigned char b[2][T2_BBYTES];    // [slot]
-    float2 cinfo[MAX_ITEM_COLS];                    // (source index | kind << 31, chunk scale)
-    DevChunk16 hdr[MAX_ITEM_CHUNKS];
-    int32_t colstart[MAX_ITEM_CHUNKS + 1];
-    int32_t ncol;
-    int32_t abort;
-    uint32_t tmem;
-    alignas(8) uint64_t ready[2];  // consumer warps -> MMA thread: slot filled
-    uint64_t done[2];              // MMA thread (tcgen05.commit) -> consumers: slot consumed
-};
-static_assert(sizeof(T2Smem) <= 56 * 1024, "four CTAs per SM");
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
-           ((uint64_t)(T2_SBO >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-__global__ void __launch_bounds__(T2_THREADS, 4) mvt_phase2(const WorkItem* items,
-                                                           const DevChunk16* hdr,
-                                                           const uint32_t* __restrict__ arena,
-                                                           const float2* __restrict__ X,
-                                                           const float2* __restrict__ T,
-                                                           float2* Y, int* err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T2Smem& S = *reinterpret_cast<T2Smem*>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
-    const int nch = it.last - it.first;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nch; i += T2_THREADS) S.hdr[i] = hdr[it.first + i];
-    if (tid == 0) {
-        S.abort = 0;
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(&S.ready[q], T2_CONS);
-            mbar_init(&S.done[q], 1);
-        }
-        mbar_fence_init();
-    }
-    if (warp == T2_CONS) {
+    for (int i = tid; i < nch; i += TC_THREADS) S.hdr[i] = hdr[it.first + i];
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&S.tmem)),
-                     "r"(T2_TMEM_COLS));
+                     "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (tid == 0) S.abort = 0;
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) {  // column offsets of the chunks (exclusive scan)
+    tc_fence_after();
+    if (warp == 0) {  // exclusive scan of the chunk widths
         const int a0 = 2 * lane < nch ? S.hdr[2 * lane].ncols : 0;
         const int a1 = 2 * lane + 1 < nch ? S.hdr[2 * lane + 1].ncols : 0;
         int inc = a0 + a1;
@@ -469,181 +216,335 @@ __global__ void __launch_bounds__(T2_THREADS, 4) mvt_phase2(const WorkItem* item
         }
     }
     __syncthreads();
-    for (int ci = warp; ci < nch; ci += T2_CONS + 1) {
+    for (int ci = warp; ci < nch; ci += TC_THREADS / 32) {
         const DevChunk16 ch = S.hdr[ci];
-        const uint32_t kind = ch.kind == 0 ? 0u : 0x80000000u;
-        for (int c = lane; c < ch.ncols; c += 32)
-            S.cinfo[S.colstart[ci] + c] =
-                make_float2(__uint_as_float((uint32_t)(ch.vec + c) | kind), ch.scale);
+        for (int c = lane; c < ch.ncols; c += 32) {
+            float2 info;
+            if (PHASE2)  // U column: T16 row t; dense column: XB row 2 dof (x itself)
+                info = make_float2(__uint_as_float(ch.kind != 0 ? ((uint32_t)(ch.vec + c) | 0x80000000u)
+                                                                : (uint32_t)(2 * (ch.vec + c))),
+                                   0.f);
+            else
+                info = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale * ch.fold);
+            S.cinfo[S.colstart[ci] + c] = info;
+        }
     }
     __syncthreads();
-    const int R = it.rows;
-    const int MT = R > 128 ? 2 : 1;
+}
+
+// A wait of one role: on a timeout the error word and the abort flag are set
+// and false is returned; once the flag is set no role starts another wait.
+template <typename Smem>
+__device__ __forceinline__ bool tc_wait(Smem& S, uint64_t* bar, uint32_t parity, int* err) {
+    if (*(volatile int32_t*)&S.abort) return false;
+    if (mbar_wait(bar, parity)) return true;
+    atomicExch(err, MV_ERR_TIMEOUT);
+    *(volatile int32_t*)&S.abort = 1;
+    return false;
+}
+
+// Phase 1 for one item (the V chunks of one column leaf): T[t_j] += s_V s_U D[j].
+// Stages: (M tile of 128 columns) x (64-wide K box); the item's XB rows (the
+// B operand, all K boxes) are loaded once.  Two TMEM accumulators let the
+// epilogue of one M tile overlap the MMAs of the next.
+__global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase1(const WorkItem* items,
+                                                           const DevChunk16* hdr,
+                                                           const CUtensorMap* maps,
+                                                           const CUtensorMap* map_xb, float2* T,
+                                                           int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TC1Smem& S = tc_smem<TC1Smem>(smem_raw);
+    const WorkItem it = items[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < TC_NS; ++q) {
+            mbar_init(&S.full[q], 1);
+            mbar_init(&S.empty[q], 1);
+        }
+        mbar_init(&S.bfull, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&S.accf[q], 1);
+            mbar_init(&S.acce[q], 4);
+        }
+        mbar_fence_init();
+    }
+    tc_prologue<TC1Smem, false>(S, it, hdr, TC1_TMEM_COLS);
+    const int ld16 = S.hdr[0].ld;
     const int ncol = S.ncol;
-    const int nst = (ncol + T2_KC - 1) / T2_KC;
+    const int nmt = (ncol + 127) >> 7;     // 128-column M tiles
+    const int nkb = (2 * ld16 + 63) >> 6;  // 64-wide K boxes
+    const int nstage = nmt * nkb;
     const uint32_t tmem = S.tmem;
-    if (warp == T2_CONS) {  // ---- MMA issue ----
+    if (warp == 0) {  // ---- TMA producer ----
         if (lane == 0) {
-            int issued = -1;
-            for (int k = 0; k < nst; ++k) {
-                const int slot = k & 1;
-                if (!mbar_wait(&S.ready[slot], (k >> 1) & 1)) {
-                    atomicExch(err, MV_ERR_TIMEOUT);
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sb = smem_u32(S.b[slot]);
-                for (int t = 0; t < MT; ++t) {
-                    const uint32_t sa = smem_u32(S.a[slot][t]);
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t da = umma_desc(sa + kk * 256), db = umma_desc(sb + kk * 256);
-                        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                tmem + (uint32_t)(t * 64)),
-                            "l"(da), "l"(db), "r"(T2_IDESC), "r"(acc));
-                    }
-                }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&S.done[slot]))
-                    : "memory");
-                issued = k;
+            const CUtensorMap* map = maps + (ld16 >> 2);
+            tmap_acquire(map);
+            tmap_acquire(map_xb);
+            const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
+            // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
+            mbar_arrive_expect_tx(&S.bfull, (uint32_t)nkb * TC1_BBYTES);
+            for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(S.b[kb], map_xb, 0, (int)(2 * it.dof) + 64 * kb, &S.bfull, pol_keep);
+            const int row0 = (int)(S.hdr[0].data / ld16);
+            int issued = 0;
+            for (int i = 0; i < nstage; ++i) {
+                const int q = i % TC_NS;
+                if (i >= TC_NS && !tc_wait(S, &S.empty[q], ((i / TC_NS) - 1) & 1, err)) break;
+                const int mt = i / nkb, kb = i - mt * nkb;
+                mbar_arrive_expect_tx(&S.full[q], TC1_ABYTES);
+                tma_load_2d(S.a[q], map, kb * 64, row0 + mt * 128, &S.full[q], pol_stream);
+                ++issued;
             }
-            if (issued >= 0 && !mbar_wait(&S.done[issued & 1], (issued >> 1) & 1))
-                atomicExch(err, MV_ERR_TIMEOUT);  // own MMAs complete before the buffers go
+            // own copies land before the block can retire
+            if (!mbar_wait(&S.bfull, 0)) atomicExch(err, MV_ERR_TIMEOUT);
+            for (int i = max(0, issued - TC_NS); i < issued; ++i)
+                if (!mbar_wait(&S.full[i % TC_NS], (i / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
         }
         __syncwarp();
-    } else {  // ---- consumers: operands in, accumulators out ----
-        const int RQ = (R + 3) >> 2;  // row quads (ld16 = 4 RQ)
-        const int ld16 = S.hdr[0].ld;
-        const uint32_t* src0 = arena + S.hdr[0].data;
-        const int task = tid;  // (column group cg, row quad q), q fastest
-        const int cg = task / RQ, q = task - cg * RQ;
-        const bool has_task = task < 4 * RQ;
-        uint4 u[4];
-        auto load_a = [&](int k) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = k * T2_KC + 4 * cg + c;
-                u[c] = (has_task && k < nst && j < ncol)
-                           ? __ldcs(reinterpret_cast<const uint4*>(src0 + (size_t)j * ld16) + q)
-                           : make_uint4(0, 0, 0, 0);
-            }
-        };
-        float2 wv[2];
-        float wsc[2];
-        auto load_w = [&](int k) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int j = k * T2_KC + warp + c * T2_CONS;
-                wv[c] = make_float2(0.f, 0.f);
-                wsc[c] = 0.f;
-                if (k < nst && j < ncol) {
-                    const float2 ci = S.cinfo[j];
-                    const uint32_t code = __float_as_uint(ci.x);
-                    const float2* src = (code & 0x80000000u) ? T : X;
-                    wv[c] = __ldg(src + (int64_t)(code & 0x7fffffffu) * NR + lane);
-                    wsc[c] = ci.y;
-                }
-            }
-        };
-        load_a(0);
-        load_w(0);
-        for (int k = 0; k < nst; ++k) {
-            const int slot = k & 1;
-            if (k >= 2 && !mbar_wait(&S.done[slot], ((k >> 1) - 1) & 1)) {
-                atomicExch(err, MV_ERR_TIMEOUT);
-                *(volatile int32_t*)&S.abort = 1;
-            }
-            if (__any_sync(0xffffffffu, *(volatile int32_t*)&S.abort)) break;  // warp-uniform
-            // A: rows 4q..4q+3 of columns 4cg..4cg+3, transposed into four 16-byte rows
-            if (has_task) {
-                const uint32_t* w = reinterpret_cast<const uint32_t*>(u);  // w[4 c + i]: column c, row i
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int r = 4 * q + i;
-                    const int t = r >> 7, rr = r & 127;
-                    if (t < MT) {
-                        unsigned char* dst = S.a[slot][t] + (rr >> 3) * T2_SBO + cg * 128 + (rr & 7) * 16;
-                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[i], w[4 + i], w[8 + i], w[12 + i]);
+    } else if (warp == 1) {  // ---- MMA issue ----
+        if (lane == 0) {
+            bool ok = tc_wait(S, &S.bfull, 0, err);
+            int committed = 0;
+            for (int mt = 0; ok && mt < nmt; ++mt) {
+                const int ab = mt & 1;
+                if (mt >= 2 && !tc_wait(S, &S.acce[ab], ((mt >> 1) - 1) & 1, err)) break;
+                tc_fence_after();
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int i = mt * nkb + kb, q = i % TC_NS;
+                    if (!tc_wait(S, &S.full[q], (i / TC_NS) & 1, err)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[kb]);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
+                        umma(tmem + (uint32_t)(ab * 64), desc_sw128(sa + kk * 32, 16, 1024),
+                             desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
+                             (kb > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&S.empty[q]);
+                    ++committed;
+                }
+                if (ok) umma_commit(&S.accf[ab]);
+            }
+            if (committed > 0) {  // the MMAs finish before shared memory and TMEM go
+                const int i = committed - 1;
+                if (!mbar_wait(&S.empty[i % TC_NS], (i / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else {  // ---- accumulators into T ----
+        const int lq = warp & 3;  // TMEM lane quarter this warp may read
+        for (int mt = 0; mt < nmt; ++mt) {
+            const int ab = mt & 1;
+            bool ok = tc_wait(S, &S.accf[ab], (mt >> 1) & 1, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            uint32_t v[64];
+            tmem_ld64(tmem, lq, ab * 64, v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acce[ab]);
+            const int j = mt * 128 + lq * 32 + lane;
+            if (j < ncol) {
+                const float2 ci = S.cinfo[j];
+                float* dst = reinterpret_cast<float*>(T + (int64_t)__float_as_int(ci.x) * NR);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    red_add_v4(dst + 4 * q, ci.y * __uint_as_float(v[4 * q]),
+                               ci.y * __uint_as_float(v[4 * q + 1]), ci.y * __uint_as_float(v[4 * q + 2]),
+                               ci.y * __uint_as_float(v[4 * q + 3]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TC1_TMEM_COLS));
+}
+
+// Phase 2 for one item (the dense and U chunks of one row leaf): Y[dof + r] +=
+// sum_j M[r][j] w_j.  Stages of 32 columns: the A boxes by TMA, the 32 weight
+// rows (128 bytes each) copied by warps 2-5 into the swizzled B layout.
+__global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase2(const WorkItem* items,
+                                                           const DevChunk16* hdr,
+                                                           const CUtensorMap* maps,
+                                                           const uint32_t* __restrict__ XB,
+                                                           const uint32_t* __restrict__ T16,
+                                                           float2* Y, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TC2Smem& S = tc_smem<TC2Smem>(smem_raw);
+    const WorkItem it = items[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < TC_NS; ++q) {
+            mbar_init(&S.full[q], 1);
+            mbar_init(&S.wfull[q], 4);
+            mbar_init(&S.empty[q], 1);
+        }
+        mbar_init(&S.accf, 1);
+        mbar_fence_init();
+    }
+    tc_prologue<TC2Smem, true>(S, it, hdr, TC2_TMEM_COLS);
+    const int ld16 = S.hdr[0].ld;
+    const int ncol = S.ncol;
+    const int nbox = (2 * ld16 + 63) >> 6;  // 64-row boxes along m = 2r + re/im
+    const int nmt = (nbox + 1) >> 1;        // 128-row M tiles
+    const int nst = (ncol + 31) >> 5;       // stages of 32 columns
+    const uint32_t tmem = S.tmem;
+    if (warp == 0) {  // ---- TMA producer ----
+        if (lane == 0) {
+            const CUtensorMap* map = maps + (ld16 >> 2);
+            tmap_acquire(map);
+            const uint64_t pol = l2_policy_evict_first();
+            const int row0 = (int)(S.hdr[0].data / ld16);
+            int issued = 0;
+            for (int k = 0; k < nst; ++k) {
+                const int q = k % TC_NS;
+                if (k >= TC_NS && !tc_wait(S, &S.empty[q], ((k / TC_NS) - 1) & 1, err)) break;
+                mbar_arrive_expect_tx(&S.full[q], (uint32_t)nbox * 4096u);
+                for (int b = 0; b < nbox; ++b)
+                    tma_load_2d(S.a[q] + b * 4096, map, b * 64, row0 + k * 32, &S.full[q], pol);
+                ++issued;
+            }
+            for (int k = max(0, issued - TC_NS); k < issued; ++k)
+                if (!mbar_wait(&S.full[k % TC_NS], (k / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp == 1) {  // ---- MMA issue ----
+        if (lane == 0) {
+            int committed = 0;
+            bool ok = true;
+            for (int k = 0; k < nst; ++k) {
+                const int q = k % TC_NS;
+                if (!tc_wait(S, &S.full[q], (k / TC_NS) & 1, err) ||
+                    !tc_wait(S, &S.wfull[q], (k / TC_NS) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(S.a[q]), sw = smem_u32(S.w[q]);
+                for (int t = 0; t < nmt; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)  // K = 16: two 8-row groups of both operands
+                        umma(tmem + (uint32_t)(t * 64), desc_sw128(sa + t * 8192 + kk * 2048, 4096, 1024),
+                             desc_sw128(sw + kk * 2048, 8192, 1024), TC_IDESC | TC_A_MN | TC_B_MN,
+                             (k > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(&S.empty[q]);
+                ++committed;
+            }
+            if (ok && nst > 0) umma_commit(&S.accf);
+            if (committed > 0) {
+                const int k = committed - 1;
+                if (!mbar_wait(&S.empty[k % TC_NS], (k / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else {  // ---- weight rows into B, then the accumulators into Y ----
+        // thread: 16-byte chunk c of rows j and j + 4 of the stage's 8-row group g
+        const int g = warp - 2, c = lane & 7, jr = lane >> 3;
+        uint4 u[2];
+        auto load = [&](int k) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = k * 32 + g * 8 + jr + 4 * h;
+                u[h] = make_uint4(0u, 0u, 0u, 0u);
+                if (k < nst && j < ncol) {
+                    const uint32_t code = __float_as_uint(S.cinfo[j].x);
+                    const uint32_t* row = (code & 0x80000000u) ? T16 + (int64_t)(code & 0x7fffffffu) * NR
+                                                               : XB + (int64_t)code * NR;
+                    u[h] = __ldg(reinterpret_cast<const uint4*>(row) + c);
                 }
             }
-            // B: w_j as (w_r, -w_i) for real column 2s and (w_i, w_r) for 2s + 1
+        };
+        load(0);
+        for (int k = 0; k < nst; ++k) {
+            const int q = k % TC_NS;
+            const bool ok = k < TC_NS || tc_wait(S, &S.empty[q], ((k / TC_NS) - 1) & 1, err);
+            if (!__all_sync(0xffffffffu, ok && !*(volatile int32_t*)&S.abort)) break;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int j = warp + c * T2_CONS;  // stage-local column
-                const float wr = wv[c].x * wsc[c], wi = wv[c].y * wsc[c];
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const int n = 2 * lane + v;
-                    const uint32_t word = v == 0 ? pack_bf16(wr, -wi) : pack_bf16(wi, wr);
-                    *reinterpret_cast<uint32_t*>(S.b[slot] + (n >> 3) * T2_SBO + (j >> 2) * 128 +
-                                                 (n & 7) * 16 + (j & 3) * 4) = word;
-                }
+            for (int h = 0; h < 2; ++h) {  // row j of the stage: 128 bytes, chunks XOR-swizzled by j mod 8
+                const int j = g * 8 + jr + 4 * h;
+                *reinterpret_cast<uint4*>(S.w[q] + j * 128 + ((c ^ (j & 7)) << 4)) = u[h];
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S.ready[slot]);
-            load_a(k + 1);
-            load_w(k + 1);
+            if (lane == 0) mbar_arrive(&S.wfull[q]);
+            load(k + 1);
         }
-        // every stage's MMAs done: accumulators to Y
-        const int last = nst - 1;
-        bool ok = last >= 0 && !*(volatile int32_t*)&S.abort;
-        if (ok && !mbar_wait(&S.done[last & 1], (last >> 1) & 1)) {
-            atomicExch(err, MV_ERR_TIMEOUT);
-            ok = false;
-        }
-        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int t = warp >> 2, lg = warp & 3;
-        if (ok && t < MT) {
-            const int r = t * 128 + lg * 32 + lane;
+        bool ok = nst > 0 && tc_wait(S, &S.accf, 0, err);
+        if (__all_sync(0xffffffffu, ok)) {
+            tc_fence_after();
+            const int lq = warp & 3;
+            const int R = it.rows;
+            const bool odd = lane & 1;
+            for (int t = 0; t < nmt; ++t) {
+                uint32_t v[64];
+                tmem_ld64(tmem, lq, t * 64, v);
+                // even lane: row m = 2r (real parts of M), odd lane: m = 2r + 1;
+                // the even lane forms y_r(s) for s < 16, the odd lane for s >= 16
+                float o[32];  // even: D_odd[cc]; odd: D_even[32 + cc]
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                uint32_t v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(t * 64 + c0)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int cc = 0; cc < 32; ++cc)
+                    o[cc] = __uint_as_float(__shfl_xor_sync(0xffffffffu, odd ? v[cc] : v[32 + cc], 1));
+                const int r = (t * 128 + lq * 32 + lane) >> 1;
                 if (r < R) {
+                    float* dst = reinterpret_cast<float*>(Y + (it.dof + r) * NR + (odd ? 16 : 0));
 #pragma unroll
-                    for (int e = 0; e < 16; e += 2)  // real columns 2s, 2s + 1: RHS s
-                        atomicAdd(Y + (it.dof + r) * NR + (c0 + e) / 2,
-                                  make_float2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])));
+                    for (int q = 0; q < 8; ++q) {
+                        float out[4];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int cc = 4 * q + 2 * h;  // 2 x (local right-hand side)
+                            if (!odd) {
+                                out[2 * h] = __uint_as_float(v[cc]) - o[cc + 1];
+                                out[2 * h + 1] = __uint_as_float(v[cc + 1]) + o[cc];
+                            } else {
+                                out[2 * h] = o[cc] - __uint_as_float(v[32 + cc + 1]);
+                                out[2 * h + 1] = o[cc + 1] + __uint_as_float(v[32 + cc]);
+                            }
+                        }
+                        red_add_v4(dst + 4 * q, out[0], out[1], out[2], out[3]);
+                    }
                 }
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == T2_CONS)
+    tc_fence_after();
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(T2_TMEM_COLS));
+                     "r"(TC2_TMEM_COLS));
 }
 
-// X[(3p + a) * 32 + s] = x_s[3 perm[p] + a]  (zero for s >= nrhs)
-__global__ void gather_multi_kernel(const int64_t* perm, const double2* x, int64_t n, int nrhs,
-                                    float2* X, int64_t nc) {
+// XB rows 2q and 2q + 1 of tree-order DOF q: (x_r, x_i) and (x_i, -x_r) of each
+// right-hand side s (zero for s >= nrhs); x is column-major n x nrhs, input order.
+__global__ void gather_xb_kernel(const int64_t* perm, const double2* x, int64_t n, int nrhs,
+                                 uint32_t* XB, int64_t nc) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= 3 * nc * NR) return;
     const int64_t q = idx / NR;
     const int s = (int)(idx - q * NR);
-    float2 v = make_float2(0.f, 0.f);
+    float xr = 0.f, xi = 0.f;
     if (s < nrhs) {
         const int64_t p = q / 3, a = q - 3 * p;
         const double2 u = x[(int64_t)s * n + 3 * perm[p] + a];
-        v = make_float2((float)u.x, (float)u.y);
+        xr = (float)u.x;
+        xi = (float)u.y;
     }
-    X[idx] = v;
+    XB[(2 * q) * NR + s] = pack_bf16(xr, xi);
+    XB[(2 * q + 1) * NR + s] = pack_bf16(xi, -xr);
+}
+
+// T16 = T rounded to bf16 pairs (the phase-2 weights of the U columns).
+__global__ void t16_kernel(const float4* T, uint2* T16, int64_t npair) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npair) return;
+    const float4 v = T[i];
+    T16[i] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
 }
 
 __global__ void scatter_multi_kernel(const int64_t* perm, const float2* Y, int64_t n, int nrhs,
@@ -658,18 +559,52 @@ __global__ void scatter_multi_kernel(const int64_t* perm, const float2* Y, int64
     y[(int64_t)s * n + 3 * perm[p] + a] = make_double2(v.x, v.y);
 }
 
-static_assert(sizeof(P1Smem) <= 113 * 1024, "phase 1: two CTAs per SM");
-static_assert(sizeof(P2Smem) <= 113 * 1024, "phase 2: two CTAs per SM");
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 2-D BF16 view (inner extent, rows, row pitch in bytes) with 128-byte swizzle.
+void encode_tmap(CUtensorMap* out, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch,
+                 uint32_t box_inner, uint32_t box_rows) {
+    static TmapEncodeFn enc = nullptr;
+    if (!enc) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            hm_throw(HM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        enc = (TmapEncodeFn)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {box_inner, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) hm_throw(HM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
 
 }  // namespace
 
-static void launch_phase2(MatvecDev* m, cudaStream_t st) {
-    if (m->phase2_tc)
-        mvt_phase2<<<(unsigned)m->n2, T2_THREADS, sizeof(T2Smem), st>>>(
-            m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
-    else
-        mvm_phase2<<<(unsigned)m->n2, P2_THREADS, sizeof(P2Smem), st>>>(
-            m->items2, m->hdr16_2, m->arena16, m->xm, m->tm, m->ym, m->d_err);
+void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,
+                      const std::vector<int32_t>& lds, cudaStream_t st) {
+    std::vector<CUtensorMap> maps(2 * TMAP_PER_PHASE);
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    std::vector<char> done(TMAP_PER_PHASE, 0);
+    for (const int32_t ld : lds) {
+        if (ld % 4 || ld < 32 || ld > MAX_LD) hm_throw(HM_ERR_UNSUPPORTED, "BF16 leading dimension");
+        if (done[ld / 4]) continue;
+        done[ld / 4] = 1;
+        // phase 1: 64 K x 128 columns; phase 2: 64 m x 32 columns
+        encode_tmap(&maps[ld / 4], arena16, 2 * ld, words / ld, 4 * ld, 64, 128);
+        encode_tmap(&maps[TMAP_PER_PHASE + ld / 4], arena16, 2 * ld, words / ld, 4 * ld, 64, 32);
+    }
+    HM_CUDA(cudaMemcpyAsync(d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                            cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaStreamSynchronize(st));
 }
 
 // Algorithmic bytes of one block product: the stored BF16 entries and scales,
@@ -680,51 +615,76 @@ int64_t matvec_multi_alg_bytes(const MatvecDev* m, int64_t ndof) {
            (int64_t)NR * 8 * (2 * ndof + 2 * m->t_elems);
 }
 
+static void multi_setup(MatvecDev* m, int64_t n, cudaStream_t st) {
+    if (m->xb) return;
+    HM_CUDA(cudaFuncSetAttribute(mvc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(TC1Smem) + 1024));
+    HM_CUDA(cudaFuncSetAttribute(mvc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(TC2Smem) + 1024));
+    const int64_t nt = std::max<int64_t>(m->t_elems, 1);
+    HM_CUDA(cudaMalloc((void**)&m->xb, (size_t)2 * n * NR * 4));
+    HM_CUDA(cudaMalloc((void**)&m->ym, (size_t)n * NR * sizeof(float2)));
+    HM_CUDA(cudaMalloc((void**)&m->tm, (size_t)nt * NR * sizeof(float2)));
+    HM_CUDA(cudaMalloc((void**)&m->t16, (size_t)nt * NR * 4));
+    HM_CUDA(cudaMalloc(&m->tmap_xb, sizeof(CUtensorMap)));
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    encode_tmap(&map, m->xb, 2 * NR, 2 * n, 4 * NR, 64, 64);  // 64 K rows of XB per box
+    HM_CUDA(cudaMemcpyAsync(m->tmap_xb, &map, sizeof(map), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+}
+
+// The kernels of one block product after the gather (zeroing, both phases,
+// the T16 rounding in between); events e1, e2 (may be null) mark the phases.
+static void multi_phases(MatvecDev* m, int64_t n, cudaStream_t st, cudaEvent_t e1, cudaEvent_t e2) {
+    if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->tm, 0, (size_t)m->t_elems * NR * sizeof(float2), st));
+    HM_CUDA(cudaMemsetAsync(m->ym, 0, (size_t)n * NR * sizeof(float2), st));
+    if (e1) HM_CUDA(cudaEventRecord(e1, st));
+    if (m->n1) {
+        mvc_phase1<<<(unsigned)m->n1, TC_THREADS, sizeof(TC1Smem) + 1024, st>>>(
+            m->items1, m->hdr16_1, (const CUtensorMap*)m->tmaps, (const CUtensorMap*)m->tmap_xb,
+            m->tm, m->d_err);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    if (e2) HM_CUDA(cudaEventRecord(e2, st));
+    if (m->t_elems) {
+        const int64_t npair = m->t_elems * NR / 2;
+        t16_kernel<<<(unsigned)hm_cdiv(npair, 256), 256, 0, st>>>((const float4*)m->tm, (uint2*)m->t16,
+                                                                   npair);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    if (m->n2) {
+        mvc_phase2<<<(unsigned)m->n2, TC_THREADS, sizeof(TC2Smem) + 1024, st>>>(
+            m->items2, m->hdr16_2, (const CUtensorMap*)m->tmaps + TMAP_PER_PHASE, m->xb, m->t16,
+            m->ym, m->d_err);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+}
+
 void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* y, int64_t nc,
                   int32_t nrhs, cudaStream_t st) {
     if (!m->arena16) hm_throw(HM_ERR_UNSUPPORTED, "tensor-core block product needs BF16 storage");
     const int64_t n = 3 * nc;
-    if (!m->xm) {
-        HM_CUDA(cudaFuncSetAttribute(mvm_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(P1Smem)));
-        HM_CUDA(cudaFuncSetAttribute(mvm_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(P2Smem)));
-        HM_CUDA(cudaFuncSetAttribute(mvt_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(T2Smem)));
-        // phase 2 on tcgen05 unless HM_BLOCK_PHASE2=mma asks for the mma.sync kernel
-        const char* e = getenv("HM_BLOCK_PHASE2");
-        m->phase2_tc = (e && e[0] == 'm') ? 0 : 1;
-        HM_CUDA(cudaMalloc((void**)&m->xm, (size_t)n * NR * sizeof(float2)));
-        HM_CUDA(cudaMalloc((void**)&m->ym, (size_t)n * NR * sizeof(float2)));
-        HM_CUDA(cudaMalloc((void**)&m->tm, (size_t)std::max<int64_t>(m->t_elems, 1) * NR * sizeof(float2)));
-    }
+    multi_setup(m, n, st);
     const unsigned nbv = (unsigned)hm_cdiv(n * NR, 256);
     for (int32_t c0 = 0; c0 < nrhs; c0 += NR) {
         const int ng = std::min<int32_t>(NR, nrhs - c0);
-        gather_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, x + (int64_t)c0 * n, n, ng, m->xm, nc);
+        gather_xb_kernel<<<nbv, 256, 0, st>>>(d_perm, x + (int64_t)c0 * n, n, ng, m->xb, nc);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
-        if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->tm, 0, (size_t)m->t_elems * NR * sizeof(float2), st));
-        HM_CUDA(cudaMemsetAsync(m->ym, 0, (size_t)n * NR * sizeof(float2), st));
-        if (m->n1) {
-            mvm_phase1<<<(unsigned)m->n1, P1_THREADS, sizeof(P1Smem), st>>>(
-                m->items1, m->hdr16_1, m->arena16, m->xm, m->tm, m->d_err);
-            HM_CUDA(cudaGetLastError());
-            HM_LAUNCHED();
-        }
-        if (m->n2) {
-            launch_phase2(m, st);
-            HM_CUDA(cudaGetLastError());
-            HM_LAUNCHED();
-        }
+        multi_phases(m, n, st, nullptr, nullptr);
         scatter_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, m->ym, n, ng, y + (int64_t)c0 * n, nc);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
 }
 
-// Per-kernel device times of one block product (ms: gather, phase 1, phase 2,
-// scatter), averaged over reps, for the roofline report.
+// Per-kernel device times of one block product (ms: gather and zeroing,
+// phase 1, T16 rounding and phase 2, scatter), averaged over reps, for the
+// roofline report.
 void matvec_multi_profile(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* y,
                           int64_t nc, int32_t reps, double ms[4], cudaStream_t st) {
     matvec_multi(m, d_perm, x, y, nc, NR, st);  // allocations and attributes
@@ -735,21 +695,9 @@ void matvec_multi_profile(MatvecDev* m, const int64_t* d_perm, const double2* x,
     for (int q = 0; q < 4; ++q) ms[q] = 0.0;
     for (int r = 0; r < reps; ++r) {
         HM_CUDA(cudaEventRecord(ev[0], st));
-        gather_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, x, n, NR, m->xm, nc);
+        gather_xb_kernel<<<nbv, 256, 0, st>>>(d_perm, x, n, NR, m->xb, nc);
         HM_LAUNCHED();
-        if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->tm, 0, (size_t)m->t_elems * NR * sizeof(float2), st));
-        HM_CUDA(cudaMemsetAsync(m->ym, 0, (size_t)n * NR * sizeof(float2), st));
-        HM_CUDA(cudaEventRecord(ev[1], st));
-        if (m->n1) {
-            mvm_phase1<<<(unsigned)m->n1, P1_THREADS, sizeof(P1Smem), st>>>(
-                m->items1, m->hdr16_1, m->arena16, m->xm, m->tm, m->d_err);
-            HM_LAUNCHED();
-        }
-        HM_CUDA(cudaEventRecord(ev[2], st));
-        if (m->n2) {
-            launch_phase2(m, st);
-            HM_LAUNCHED();
-        }
+        multi_phases(m, n, st, ev[1], ev[2]);
         HM_CUDA(cudaEventRecord(ev[3], st));
         scatter_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, m->ym, n, NR, y, nc);
         HM_LAUNCHED();

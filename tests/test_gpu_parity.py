@@ -387,9 +387,9 @@ def test_uniform_weights_keep_every_pivot(hm):
 
 
 def test_bf16_storage_product_and_refinement(hm, oracle):
-    """Mixed form: dense blocks and factors stored as BF16 with one FP32 scale
-    per chunk.  The fast product then carries the BF16 rounding (unit roundoff
-    2^-9 of each chunk's largest entry, so a few 1e-3 relative), and GMRES with
+    """Mixed form: dense blocks and factors stored as BF16 (factors with one
+    FP32 scale per block and factor).  The fast product then carries the BF16
+    rounding (unit roundoff 2^-9, so a few 1e-3 relative), and GMRES with
     BF16 inner products and accurate restart residuals (iterative refinement)
     still reaches 1e-6 and the plain form's solution."""
     nc = 4000
