@@ -307,8 +307,9 @@ def run_gpu(args, wl, world, rank, local):
         pm = H.profile_matvec_multi(reps=10)
         tb = sum(pm["ms"].values())
         tk = pm["ms"]["phase1"] + pm["ms"]["phase2"]
-        block = {"nrhs": hm.HM_NRHS_BLOCK, "kernels": "mvm_phase1 / mvm_phase2 (BF16 mma.sync "
-                 "m16n8k16, FP32 accumulation)", "ms": pm["ms"], "alg_bytes": pm["bytes"],
+        block = {"nrhs": hm.HM_NRHS_BLOCK, "kernels": "mvc_phase1 / mvc_phase2 (persistent; TMA "
+                 "128-byte-swizzled tiles, tcgen05.mma kind::f16 BF16 x BF16, FP32 accumulators in "
+                 "TMEM)", "ms": pm["ms"], "alg_bytes": pm["bytes"],
                  "achieved_GBps": pm["bytes"] / (tk * 1e-3) / 1e9,
                  "frac": pm["bytes"] / (tk * 1e-3) / 1e9 / peak, "peak": peak,
                  "per_rhs_ms": tb / hm.HM_NRHS_BLOCK,

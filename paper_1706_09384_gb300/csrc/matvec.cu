@@ -1023,6 +1023,7 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
+    make_block_items(m, c16, owner, st);
     HM_CUDA(cudaStreamSynchronize(st));
     m->storage = HM_STORE_BF16;
 }

@@ -39,6 +39,17 @@ struct WorkItem {
     int32_t last;
 };
 
+// Work item of the tensor-core block product (one leaf's chunks, contiguous
+// in the BF16 arena, starting on a row of the arena's ld16 view).
+struct TcItem {
+    int64_t dof;    // first tree-order DOF of the leaf
+    int64_t col0;   // first entry of the item in the per-column table
+    int32_t row0;   // first row of the item in the ld16 view (data / ld16)
+    int32_t ld16;
+    int32_t ncol;
+    int32_t rows;   // 3 |leaf|
+};
+
 struct MatvecDev {
     int storage = 0;
     float2* arena = nullptr;
@@ -89,8 +100,18 @@ struct MatvecDev {
     // rows of 2 ld16 bf16, [phase 1 | phase 2][ld16 / 4]; and XB
     void* tmaps = nullptr;
     void* tmap_xb = nullptr;
+    // tensor-core items and per-column tables: phase 1 (t index, s_V s_U),
+    // phase 2 (T16 row | 1 << 31 for U columns, XB row 2 dof for dense ones)
+    TcItem* titems1 = nullptr;
+    TcItem* titems2 = nullptr;
+    float2* colinfo1 = nullptr;
+    uint32_t* colcode2 = nullptr;
 };
 constexpr int TMAP_PER_PHASE = MAX_LD / 4 + 1;
+// Items and per-column tables of the tensor-core block product (after the
+// BF16 chunks, headers and scales exist on the device); c16 as uploaded.
+void make_block_items(MatvecDev* m, const std::vector<DevChunk16>& c16, std::vector<DevBuf>& owner,
+                      cudaStream_t st);
 // Encodes the descriptors for the leading dimensions in lds (device copy at
 // d_maps, 2 * TMAP_PER_PHASE entries); defined with the block product.
 void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,

@@ -47,15 +47,20 @@ constexpr int NR = NRHS_BLOCK;
 static_assert(NR == 32 && NR == HM_NRHS_BLOCK, "N = 64 real columns: 32 right-hand sides");
 constexpr int MV_ERR_TIMEOUT = 1;
 
-constexpr int TC_THREADS = 192;
-constexpr int TC_NS = 3;                              // pipeline stages
 constexpr int TC_KBMAX = 2 * MAX_LD / 64;             // 64-wide K boxes of a column (6)
-constexpr int TC1_ABYTES = 128 * 128;                 // 128 columns x 64 bf16 of K
-constexpr int TC1_BBYTES = 64 * 128;                  // 64 K rows of XB
-constexpr int TC2_ABYTES = TC_KBMAX * 4096;           // up to six 64 x 32 boxes
-constexpr int TC2_WBYTES = 32 * 128;                  // 32 weight rows
-constexpr uint32_t TC1_TMEM_COLS = 128;               // two 128 x 64 accumulators
-constexpr uint32_t TC2_TMEM_COLS = 256;               // up to three 128 x 64 accumulators
+// phase 1: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int P1_THREADS = 192;
+constexpr int P1_NS = 5;                              // A stages
+constexpr int P1_NACC = 4;                            // TMEM accumulators (128 x 64 each)
+constexpr int P1_ABYTES = 128 * 128;                  // 128 columns x 64 bf16 of K
+constexpr int P1_BBYTES = 64 * 128;                   // 64 K rows of XB
+constexpr uint32_t P1_TMEM_COLS = 256;
+// phase 2: warp 0 TMA, warp 1 MMA, warps 2-3 weight rows, warps 4-7 epilogue
+constexpr int P2_THREADS = 256;
+constexpr int P2_NS = 6;
+constexpr int P2_ABYTES = TC_KBMAX * 4096;            // up to six 64 x 32 boxes
+constexpr int P2_WBYTES = 32 * 128;                   // 32 weight rows
+constexpr uint32_t P2_TMEM_COLS = 512;                // two sets of up to three 128 x 64
 // kind::f16 instruction descriptor: FP32 accumulate (bit 4), A and B BF16
 // (bits 7, 10), A MN-major (bit 15), B MN-major (bit 16), N >> 3 at bit 17,
 // M >> 4 at bit 24; M = 128, N = 64
@@ -64,40 +69,36 @@ constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(64 
 constexpr uint32_t TC_A_MN = 1u << 15;
 constexpr uint32_t TC_B_MN = 1u << 16;
 
-struct TC1Smem {
-    unsigned char a[TC_NS][TC1_ABYTES];  // 1024-byte aligned (swizzle atoms)
-    unsigned char b[TC_KBMAX][TC1_BBYTES];
-    float2 cinfo[MAX_ITEM_COLS];         // (t index bits, s_V s_U)
-    DevChunk16 hdr[MAX_ITEM_CHUNKS];
-    int32_t colstart[MAX_ITEM_CHUNKS + 1];
-    int32_t ncol;
+struct P1Smem {
+    unsigned char a[P1_NS][P1_ABYTES];         // 1024-byte aligned (swizzle atoms)
+    unsigned char b[2][TC_KBMAX][P1_BBYTES];   // XB rows of two items
     int32_t abort;
     uint32_t tmem;
-    alignas(8) uint64_t full[TC_NS];
-    uint64_t empty[TC_NS];
-    uint64_t bfull;
+    alignas(8) uint64_t full[P1_NS];
+    uint64_t empty[P1_NS];
+    uint64_t bfull[2];
+    uint64_t bempty[2];
+    uint64_t accf[P1_NACC];
+    uint64_t acce[P1_NACC];
+};
+struct P2Smem {
+    unsigned char a[P2_NS][P2_ABYTES];
+    unsigned char w[P2_NS][P2_WBYTES];
+    uint32_t code[2][MAX_ITEM_COLS];  // column codes of two items (weight-row warps)
+    int32_t abort;
+    uint32_t tmem;
+    alignas(8) uint64_t full[P2_NS];
+    uint64_t wfull[P2_NS];
+    uint64_t empty[P2_NS];
     uint64_t accf[2];
     uint64_t acce[2];
 };
-struct TC2Smem {
-    unsigned char a[TC_NS][TC2_ABYTES];
-    unsigned char w[TC_NS][TC2_WBYTES];
-    float2 cinfo[MAX_ITEM_COLS];         // (source row | kind << 31, unused)
-    DevChunk16 hdr[MAX_ITEM_CHUNKS];
-    int32_t colstart[MAX_ITEM_CHUNKS + 1];
-    int32_t ncol;
-    int32_t abort;
-    uint32_t tmem;
-    alignas(8) uint64_t full[TC_NS];
-    uint64_t wfull[TC_NS];
-    uint64_t empty[TC_NS];
-    uint64_t accf;
-};
-// two CTAs per SM: TMEM 2 x 256 columns at most, shared memory 2 x (size + 1 KB
-// alignment slack + 1 KB reserved) within 228 KB
-static_assert(sizeof(TC1Smem) + 1024 <= 112 * 1024, "phase 1: two CTAs per SM");
-static_assert(sizeof(TC2Smem) + 1024 <= 112 * 1024, "phase 2: two CTAs per SM");
-static_assert(TC1_ABYTES % 1024 == 0 && TC2_ABYTES % 1024 == 0 && TC2_WBYTES % 1024 == 0,
+// one CTA per SM (persistent): all of TMEM is available, shared memory within
+// 227 KB including the 1 KB alignment slack
+static_assert(sizeof(P1Smem) + 1024 <= 227 * 1024, "phase 1 shared memory");
+static_assert(sizeof(P2Smem) + 1024 <= 227 * 1024, "phase 2 shared memory");
+static_assert(P1_ABYTES % 1024 == 0 && P1_BBYTES % 1024 == 0 && P2_ABYTES % 1024 == 0 &&
+                  P2_WBYTES % 1024 == 0,
               "swizzle atoms stay aligned");
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -180,58 +181,54 @@ __device__ __forceinline__ Smem& tc_smem(unsigned char* raw) {
     return *reinterpret_cast<Smem*>(raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u));
 }
 
-// Headers, TMEM allocation (warp 1), column offsets of the chunks and the
-// per-column table: phase 1 (t index, s_V s_U), phase 2 (source row | kind).
-// Barriers are initialised by the caller before; ends past a block barrier.
-template <typename Smem, bool PHASE2>
-__device__ __forceinline__ void tc_prologue(Smem& S, const WorkItem& it, const DevChunk16* hdr,
-                                            uint32_t tmem_cols) {
-    const int nch = it.last - it.first;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nch; i += TC_THREADS) S.hdr[i] = hdr[it.first + i];
-    if (warp == 1) {
+// The items of this CTA (blockIdx.x, + gridDim.x, ...), the record of the
+// next one fetched an item ahead.
+struct ItemIter {
+    const TcItem* items;
+    int nitems, item;
+    TcItem cur, nxt;
+    __device__ ItemIter(const TcItem* it, int n) : items(it), nitems(n), item(blockIdx.x) {
+        if (item < n) cur = it[item];
+        if (item + (int)gridDim.x < n) nxt = it[item + gridDim.x];
+    }
+    __device__ bool valid() const { return item < nitems; }
+    __device__ bool has_next() const { return item + (int)gridDim.x < nitems; }
+    __device__ void advance() {
+        item += gridDim.x;
+        cur = nxt;
+        if (has_next()) nxt = items[item + gridDim.x];
+    }
+};
+
+// TMEM allocation by warp 1 and the abort flag; ends past a block barrier
+// (barriers are initialised by thread 0 before).
+template <typename Smem>
+__device__ __forceinline__ void tc_setup(Smem& S, uint32_t cols) {
+    if ((threadIdx.x >> 5) == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&S.tmem)),
-                     "r"(tmem_cols));
+                     "r"(cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) S.abort = 0;
+    if (threadIdx.x == 0) S.abort = 0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) {  // exclusive scan of the chunk widths
-        const int a0 = 2 * lane < nch ? S.hdr[2 * lane].ncols : 0;
-        const int a1 = 2 * lane + 1 < nch ? S.hdr[2 * lane + 1].ncols : 0;
-        int inc = a0 + a1;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
-        }
-        const int exc = inc - a0 - a1;
-        S.colstart[2 * lane] = exc;
-        S.colstart[2 * lane + 1] = exc + a0;
-        if (lane == 31) {
-            S.colstart[MAX_ITEM_CHUNKS] = inc;
-            S.ncol = inc;
-        }
-    }
+}
+template <typename Smem>
+__device__ __forceinline__ void tc_teardown(Smem& S, uint32_t cols) {
+    tc_fence_before();
     __syncthreads();
-    for (int ci = warp; ci < nch; ci += TC_THREADS / 32) {
-        const DevChunk16 ch = S.hdr[ci];
-        for (int c = lane; c < ch.ncols; c += 32) {
-            float2 info;
-            if (PHASE2)  // U column: T16 row t; dense column: XB row 2 dof (x itself)
-                info = make_float2(__uint_as_float(ch.kind != 0 ? ((uint32_t)(ch.vec + c) | 0x80000000u)
-                                                                : (uint32_t)(2 * (ch.vec + c))),
-                                   0.f);
-            else
-                info = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale * ch.fold);
-            S.cinfo[S.colstart[ci] + c] = info;
-        }
-    }
-    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(cols));
 }
 
+// 16-byte asynchronous copy global -> shared (bytes = 16, or 0 to zero-fill)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
+                 : "memory");
+}
 // A wait of one role: on a timeout the error word and the abort flag are set
 // and false is returned; once the flag is set no role starts another wait.
 template <typename Smem>
@@ -242,247 +239,309 @@ __device__ __forceinline__ bool tc_wait(Smem& S, uint64_t* bar, uint32_t parity,
     *(volatile int32_t*)&S.abort = 1;
     return false;
 }
+template <typename Smem>
+__device__ __forceinline__ bool tc_aborted(Smem& S) {
+    return *(volatile int32_t*)&S.abort != 0;
+}
 
-// Phase 1 for one item (the V chunks of one column leaf): T[t_j] += s_V s_U D[j].
-// Stages: (M tile of 128 columns) x (64-wide K box); the item's XB rows (the
-// B operand, all K boxes) are loaded once.  Two TMEM accumulators let the
-// epilogue of one M tile overlap the MMAs of the next.
-__global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase1(const WorkItem* items,
-                                                           const DevChunk16* hdr,
+// Phase 1 (persistent, items blockIdx.x, + gridDim.x, ...): T[t_j] += s_V s_U D[j]
+// for the V columns j of each item (the V chunks of one column leaf).  Stages
+// run over (item, 128-column M tile, 64-wide K box) without breaks between
+// items; each item's XB rows (the B operand, all K boxes) go to one of two
+// buffers; four TMEM accumulators let the epilogue trail the MMAs.
+__global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items, int nitems,
+                                                           const float2* __restrict__ colinfo,
                                                            const CUtensorMap* maps,
                                                            const CUtensorMap* map_xb, float2* T,
                                                            int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TC1Smem& S = tc_smem<TC1Smem>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
+    P1Smem& S = tc_smem<P1Smem>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        for (int q = 0; q < TC_NS; ++q) {
+        for (int q = 0; q < P1_NS; ++q) {
             mbar_init(&S.full[q], 1);
             mbar_init(&S.empty[q], 1);
         }
-        mbar_init(&S.bfull, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&S.bfull[q], 1);
+            mbar_init(&S.bempty[q], 1);
+        }
+        for (int q = 0; q < P1_NACC; ++q) {
+            mbar_init(&S.accf[q], 1);
+            mbar_init(&S.acce[q], 4);
+        }
+        mbar_fence_init();
+    }
+    tc_setup(S, P1_TMEM_COLS);
+    const uint32_t tmem = S.tmem;
+    if (warp == 0) {  // ---- TMA producer ----
+        if (lane == 0) {
+            tmap_acquire(map_xb);
+            const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
+            int g = 0, ii = 0;  // stages and items issued
+            uint64_t acquired = 0;
+            for (ItemIter X(items, nitems); X.valid() && !tc_aborted(S); X.advance(), ++ii) {
+                const TcItem I = X.cur;
+                const CUtensorMap* map = maps + (I.ld16 >> 2);
+                if (!((acquired >> (I.ld16 >> 2)) & 1)) {  // each descriptor once
+                    tmap_acquire(map);
+                    acquired |= 1ull << (I.ld16 >> 2);
+                }
+                const int nmt = (I.ncol + 127) >> 7, nkb = (2 * I.ld16 + 63) >> 6;
+                const int bs = ii & 1;
+                if (ii >= 2 && !tc_wait(S, &S.bempty[bs], ((ii >> 1) - 1) & 1, err)) break;
+                // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
+                mbar_arrive_expect_tx(&S.bfull[bs], (uint32_t)nkb * P1_BBYTES);
+                for (int kb = 0; kb < nkb; ++kb)
+                    tma_load_2d(S.b[bs][kb], map_xb, 0, (int)(2 * I.dof) + 64 * kb, &S.bfull[bs], pol_keep);
+                for (int mt = 0; mt < nmt; ++mt)
+                    for (int kb = 0; kb < nkb; ++kb, ++g) {
+                        const int q = g % P1_NS;
+                        if (g >= P1_NS && !tc_wait(S, &S.empty[q], ((g / P1_NS) - 1) & 1, err)) break;
+                        mbar_arrive_expect_tx(&S.full[q], P1_ABYTES);
+                        tma_load_2d(S.a[q], map, kb * 64, I.row0 + mt * 128, &S.full[q], pol_stream);
+                    }
+            }
+            // own copies land before the block can retire (an abort may leave
+            // the count one short of a stage: waiting on it only times out)
+            for (int k = max(0, ii - 2); k < ii; ++k)
+                if (!mbar_wait(&S.bfull[k & 1], (k >> 1) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            for (int k = max(0, g - P1_NS); k < g; ++k)
+                if (!mbar_wait(&S.full[k % P1_NS], (k / P1_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+    } else if (warp == 1) {  // ---- MMA issue ----
+        if (lane == 0) {
+            int g = 0, gt = 0, ii = 0;  // stages, M tiles, items
+            bool ok = true;
+            for (ItemIter X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
+                const TcItem I = X.cur;
+                const int nmt = (I.ncol + 127) >> 7, nkb = (2 * I.ld16 + 63) >> 6;
+                const int bs = ii & 1;
+                if (!tc_wait(S, &S.bfull[bs], (ii >> 1) & 1, err)) break;
+                for (int mt = 0; ok && mt < nmt; ++mt, ++gt) {
+                    const int acc = gt % P1_NACC;
+                    if (gt >= P1_NACC && !tc_wait(S, &S.acce[acc], ((gt / P1_NACC) - 1) & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = 0; kb < nkb; ++kb, ++g) {
+                        const int q = g % P1_NS;
+                        if (!tc_wait(S, &S.full[q], (g / P1_NS) & 1, err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[bs][kb]);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
+                            umma(tmem + (uint32_t)(acc * 64), desc_sw128(sa + kk * 32, 16, 1024),
+                                 desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                        umma_commit(&S.empty[q]);
+                    }
+                    if (ok) umma_commit(&S.accf[acc]);
+                }
+                if (ok) umma_commit(&S.bempty[bs]);
+            }
+            if (g > 0) {  // the MMAs finish before shared memory and TMEM go
+                const int k = g - 1;
+                if (!mbar_wait(&S.empty[k % P1_NS], (k / P1_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else {  // ---- accumulators into T ----
+        const int lq = warp & 3;  // TMEM lane quarter this warp may read
+        int gt = 0;
+        bool ok = true;
+        for (ItemIter X(items, nitems); ok && X.valid(); X.advance()) {
+            const TcItem I = X.cur;
+            const int nmt = (I.ncol + 127) >> 7;
+            for (int mt = 0; mt < nmt; ++mt, ++gt) {
+                const int acc = gt % P1_NACC;
+                const int j = mt * 128 + lq * 32 + lane;
+                const float2 ci = j < I.ncol ? __ldg(colinfo + I.col0 + j) : make_float2(0.f, 0.f);
+                ok = __all_sync(0xffffffffu, tc_wait(S, &S.accf[acc], (gt / P1_NACC) & 1, err));
+                if (!ok) break;
+                tc_fence_after();
+                uint32_t v[64];
+                tmem_ld64(tmem, lq, acc * 64, v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.acce[acc]);
+                if (j < I.ncol) {
+                    float* dst = reinterpret_cast<float*>(T + (int64_t)__float_as_int(ci.x) * NR);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        red_add_v4(dst + 4 * q, ci.y * __uint_as_float(v[4 * q]),
+                                   ci.y * __uint_as_float(v[4 * q + 1]), ci.y * __uint_as_float(v[4 * q + 2]),
+                                   ci.y * __uint_as_float(v[4 * q + 3]));
+                }
+            }
+        }
+    }
+    tc_teardown(S, P1_TMEM_COLS);
+}
+
+// Phase 2 (persistent): Y[dof + r] += sum_j M[r][j] w_j over the columns j of
+// each item (the dense and U chunks of one row leaf).  Stages of 32 columns
+// run across items: the A boxes by TMA, the 32 weight rows (128 bytes each)
+// copied by warps 2-3 into the swizzled B layout.  Two sets of TMEM
+// accumulators (one item each) let the epilogue of an item overlap the next.
+__global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items, int nitems,
+                                                           const uint32_t* __restrict__ colcode,
+                                                           const CUtensorMap* maps,
+                                                           const uint32_t* __restrict__ XB,
+                                                           const uint32_t* __restrict__ T16,
+                                                           float2* Y, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    P2Smem& S = tc_smem<P2Smem>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < P2_NS; ++q) {
+            mbar_init(&S.full[q], 1);
+            mbar_init(&S.wfull[q], 64);  // one arrival per weight-row thread
+            mbar_init(&S.empty[q], 1);
+        }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&S.accf[q], 1);
             mbar_init(&S.acce[q], 4);
         }
         mbar_fence_init();
     }
-    tc_prologue<TC1Smem, false>(S, it, hdr, TC1_TMEM_COLS);
-    const int ld16 = S.hdr[0].ld;
-    const int ncol = S.ncol;
-    const int nmt = (ncol + 127) >> 7;     // 128-column M tiles
-    const int nkb = (2 * ld16 + 63) >> 6;  // 64-wide K boxes
-    const int nstage = nmt * nkb;
+    tc_setup(S, P2_TMEM_COLS);
     const uint32_t tmem = S.tmem;
     if (warp == 0) {  // ---- TMA producer ----
         if (lane == 0) {
-            const CUtensorMap* map = maps + (ld16 >> 2);
-            tmap_acquire(map);
-            tmap_acquire(map_xb);
-            const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
-            // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
-            mbar_arrive_expect_tx(&S.bfull, (uint32_t)nkb * TC1_BBYTES);
-            for (int kb = 0; kb < nkb; ++kb)
-                tma_load_2d(S.b[kb], map_xb, 0, (int)(2 * it.dof) + 64 * kb, &S.bfull, pol_keep);
-            const int row0 = (int)(S.hdr[0].data / ld16);
-            int issued = 0;
-            for (int i = 0; i < nstage; ++i) {
-                const int q = i % TC_NS;
-                if (i >= TC_NS && !tc_wait(S, &S.empty[q], ((i / TC_NS) - 1) & 1, err)) break;
-                const int mt = i / nkb, kb = i - mt * nkb;
-                mbar_arrive_expect_tx(&S.full[q], TC1_ABYTES);
-                tma_load_2d(S.a[q], map, kb * 64, row0 + mt * 128, &S.full[q], pol_stream);
-                ++issued;
+            const uint64_t pol = l2_policy_evict_first();
+            int g = 0;
+            uint64_t acquired = 0;
+            for (ItemIter X(items, nitems); X.valid() && !tc_aborted(S); X.advance()) {
+                const TcItem I = X.cur;
+                const CUtensorMap* map = maps + (I.ld16 >> 2);
+                if (!((acquired >> (I.ld16 >> 2)) & 1)) {  // each descriptor once
+                    tmap_acquire(map);
+                    acquired |= 1ull << (I.ld16 >> 2);
+                }
+                const int nbox = (2 * I.ld16 + 63) >> 6;  // 64-row boxes along m = 2r + re/im
+                const int nst = (I.ncol + 31) >> 5;
+                for (int k = 0; k < nst; ++k, ++g) {
+                    const int q = g % P2_NS;
+                    if (g >= P2_NS && !tc_wait(S, &S.empty[q], ((g / P2_NS) - 1) & 1, err)) break;
+                    mbar_arrive_expect_tx(&S.full[q], (uint32_t)nbox * 4096u);
+                    for (int b = 0; b < nbox; ++b)
+                        tma_load_2d(S.a[q] + b * 4096, map, b * 64, I.row0 + k * 32, &S.full[q], pol);
+                }
             }
-            // own copies land before the block can retire
-            if (!mbar_wait(&S.bfull, 0)) atomicExch(err, MV_ERR_TIMEOUT);
-            for (int i = max(0, issued - TC_NS); i < issued; ++i)
-                if (!mbar_wait(&S.full[i % TC_NS], (i / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            for (int k = max(0, g - P2_NS); k < g; ++k)
+                if (!mbar_wait(&S.full[k % P2_NS], (k / P2_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
         }
         __syncwarp();
     } else if (warp == 1) {  // ---- MMA issue ----
         if (lane == 0) {
-            bool ok = tc_wait(S, &S.bfull, 0, err);
-            int committed = 0;
-            for (int mt = 0; ok && mt < nmt; ++mt) {
-                const int ab = mt & 1;
-                if (mt >= 2 && !tc_wait(S, &S.acce[ab], ((mt >> 1) - 1) & 1, err)) break;
+            int g = 0, ii = 0;
+            bool ok = true;
+            for (ItemIter X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
+                const TcItem I = X.cur;
+                const int nmt = (((2 * I.ld16 + 63) >> 6) + 1) >> 1;  // 128-row M tiles
+                const int nst = (I.ncol + 31) >> 5;
+                const int set = ii & 1;
+                if (ii >= 2 && !tc_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
                 tc_fence_after();
-                for (int kb = 0; kb < nkb; ++kb) {
-                    const int i = mt * nkb + kb, q = i % TC_NS;
-                    if (!tc_wait(S, &S.full[q], (i / TC_NS) & 1, err)) {
+                for (int k = 0; k < nst; ++k, ++g) {
+                    const int q = g % P2_NS;
+                    if (!tc_wait(S, &S.full[q], (g / P2_NS) & 1, err) ||
+                        !tc_wait(S, &S.wfull[q], (g / P2_NS) & 1, err)) {
                         ok = false;
                         break;
                     }
+                    // the weight rows were written by cp.async (generic proxy): order
+                    // them before the tensor core's reads
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[kb]);
+                    const uint32_t sa = smem_u32(S.a[q]), sw = smem_u32(S.w[q]);
+                    for (int t = 0; t < nmt; ++t)
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
-                        umma(tmem + (uint32_t)(ab * 64), desc_sw128(sa + kk * 32, 16, 1024),
-                             desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
-                             (kb > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 2; ++kk)  // K = 16: two 8-row groups of both operands
+                            umma(tmem + (uint32_t)(set * 256 + t * 64),
+                                 desc_sw128(sa + t * 8192 + kk * 2048, 4096, 1024),
+                                 desc_sw128(sw + kk * 2048, 8192, 1024), TC_IDESC | TC_A_MN | TC_B_MN,
+                                 (k > 0 || kk > 0) ? 1u : 0u);
                     umma_commit(&S.empty[q]);
-                    ++committed;
                 }
-                if (ok) umma_commit(&S.accf[ab]);
+                if (ok) umma_commit(&S.accf[set]);  // also for an empty item: keeps the phases in step
             }
-            if (committed > 0) {  // the MMAs finish before shared memory and TMEM go
-                const int i = committed - 1;
-                if (!mbar_wait(&S.empty[i % TC_NS], (i / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            if (g > 0) {
+                const int k = g - 1;
+                if (!mbar_wait(&S.empty[k % P2_NS], (k / P2_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
             }
         }
         __syncwarp();
-    } else {  // ---- accumulators into T ----
-        const int lq = warp & 3;  // TMEM lane quarter this warp may read
-        for (int mt = 0; mt < nmt; ++mt) {
-            const int ab = mt & 1;
-            bool ok = tc_wait(S, &S.accf[ab], (mt >> 1) & 1, err);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
-            uint32_t v[64];
-            tmem_ld64(tmem, lq, ab * 64, v);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.acce[ab]);
-            const int j = mt * 128 + lq * 32 + lane;
-            if (j < ncol) {
-                const float2 ci = S.cinfo[j];
-                float* dst = reinterpret_cast<float*>(T + (int64_t)__float_as_int(ci.x) * NR);
+    } else if (warp < 4) {  // ---- weight rows into B ----
+        // thread: 16-byte chunk c of rows jr, jr + 8, jr + 16, jr + 24 of a stage
+        const int wt = tid - 64, c = wt & 7, jr = wt >> 3;  // jr 0..7
+        // both warps pass the same named barriers: after an abort they keep
+        // walking the items (every wait then returns at once) instead of leaving;
+        // each thread holds its share of the next item's column codes
+        constexpr int NPC = MAX_ITEM_COLS / 64;
+        uint32_t pc[NPC];
+        auto fetch = [&](const TcItem& J, bool valid) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    red_add_v4(dst + 4 * q, ci.y * __uint_as_float(v[4 * q]),
-                               ci.y * __uint_as_float(v[4 * q + 1]), ci.y * __uint_as_float(v[4 * q + 2]),
-                               ci.y * __uint_as_float(v[4 * q + 3]));
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TC1_TMEM_COLS));
-}
-
-// Phase 2 for one item (the dense and U chunks of one row leaf): Y[dof + r] +=
-// sum_j M[r][j] w_j.  Stages of 32 columns: the A boxes by TMA, the 32 weight
-// rows (128 bytes each) copied by warps 2-5 into the swizzled B layout.
-__global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase2(const WorkItem* items,
-                                                           const DevChunk16* hdr,
-                                                           const CUtensorMap* maps,
-                                                           const uint32_t* __restrict__ XB,
-                                                           const uint32_t* __restrict__ T16,
-                                                           float2* Y, int* err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TC2Smem& S = tc_smem<TC2Smem>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        for (int q = 0; q < TC_NS; ++q) {
-            mbar_init(&S.full[q], 1);
-            mbar_init(&S.wfull[q], 4);
-            mbar_init(&S.empty[q], 1);
-        }
-        mbar_init(&S.accf, 1);
-        mbar_fence_init();
-    }
-    tc_prologue<TC2Smem, true>(S, it, hdr, TC2_TMEM_COLS);
-    const int ld16 = S.hdr[0].ld;
-    const int ncol = S.ncol;
-    const int nbox = (2 * ld16 + 63) >> 6;  // 64-row boxes along m = 2r + re/im
-    const int nmt = (nbox + 1) >> 1;        // 128-row M tiles
-    const int nst = (ncol + 31) >> 5;       // stages of 32 columns
-    const uint32_t tmem = S.tmem;
-    if (warp == 0) {  // ---- TMA producer ----
-        if (lane == 0) {
-            const CUtensorMap* map = maps + (ld16 >> 2);
-            tmap_acquire(map);
-            const uint64_t pol = l2_policy_evict_first();
-            const int row0 = (int)(S.hdr[0].data / ld16);
-            int issued = 0;
-            for (int k = 0; k < nst; ++k) {
-                const int q = k % TC_NS;
-                if (k >= TC_NS && !tc_wait(S, &S.empty[q], ((k / TC_NS) - 1) & 1, err)) break;
-                mbar_arrive_expect_tx(&S.full[q], (uint32_t)nbox * 4096u);
-                for (int b = 0; b < nbox; ++b)
-                    tma_load_2d(S.a[q] + b * 4096, map, b * 64, row0 + k * 32, &S.full[q], pol);
-                ++issued;
-            }
-            for (int k = max(0, issued - TC_NS); k < issued; ++k)
-                if (!mbar_wait(&S.full[k % TC_NS], (k / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
-        }
-        __syncwarp();
-    } else if (warp == 1) {  // ---- MMA issue ----
-        if (lane == 0) {
-            int committed = 0;
-            bool ok = true;
-            for (int k = 0; k < nst; ++k) {
-                const int q = k % TC_NS;
-                if (!tc_wait(S, &S.full[q], (k / TC_NS) & 1, err) ||
-                    !tc_wait(S, &S.wfull[q], (k / TC_NS) & 1, err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t sa = smem_u32(S.a[q]), sw = smem_u32(S.w[q]);
-                for (int t = 0; t < nmt; ++t)
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk)  // K = 16: two 8-row groups of both operands
-                        umma(tmem + (uint32_t)(t * 64), desc_sw128(sa + t * 8192 + kk * 2048, 4096, 1024),
-                             desc_sw128(sw + kk * 2048, 8192, 1024), TC_IDESC | TC_A_MN | TC_B_MN,
-                             (k > 0 || kk > 0) ? 1u : 0u);
-                umma_commit(&S.empty[q]);
-                ++committed;
-            }
-            if (ok && nst > 0) umma_commit(&S.accf);
-            if (committed > 0) {
-                const int k = committed - 1;
-                if (!mbar_wait(&S.empty[k % TC_NS], (k / TC_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
-            }
-        }
-        __syncwarp();
-    } else {  // ---- weight rows into B, then the accumulators into Y ----
-        // thread: 16-byte chunk c of rows j and j + 4 of the stage's 8-row group g
-        const int g = warp - 2, c = lane & 7, jr = lane >> 3;
-        uint4 u[2];
-        auto load = [&](int k) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = k * 32 + g * 8 + jr + 4 * h;
-                u[h] = make_uint4(0u, 0u, 0u, 0u);
-                if (k < nst && j < ncol) {
-                    const uint32_t code = __float_as_uint(S.cinfo[j].x);
-                    const uint32_t* row = (code & 0x80000000u) ? T16 + (int64_t)(code & 0x7fffffffu) * NR
-                                                               : XB + (int64_t)code * NR;
-                    u[h] = __ldg(reinterpret_cast<const uint4*>(row) + c);
-                }
+            for (int i = 0; i < NPC; ++i) {
+                const int idx = wt + 64 * i;
+                pc[i] = (valid && idx < J.ncol) ? __ldg(colcode + J.col0 + idx) : 0u;
             }
         };
-        load(0);
-        for (int k = 0; k < nst; ++k) {
-            const int q = k % TC_NS;
-            const bool ok = k < TC_NS || tc_wait(S, &S.empty[q], ((k / TC_NS) - 1) & 1, err);
-            if (!__all_sync(0xffffffffu, ok && !*(volatile int32_t*)&S.abort)) break;
+        int g = 0, ii = 0;
+        ItemIter X(items, nitems);
+        fetch(X.cur, X.valid());
+        for (; X.valid(); X.advance(), ++ii) {
+            const TcItem I = X.cur;
+            const int nst = (I.ncol + 31) >> 5;
+            uint32_t* tab = S.code[ii & 1];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // row j of the stage: 128 bytes, chunks XOR-swizzled by j mod 8
-                const int j = g * 8 + jr + 4 * h;
-                *reinterpret_cast<uint4*>(S.w[q] + j * 128 + ((c ^ (j & 7)) << 4)) = u[h];
+            for (int i = 0; i < NPC; ++i)
+                if (wt + 64 * i < I.ncol) tab[wt + 64 * i] = pc[i];
+            named_sync<1, 64>();  // the table is complete (the other buffer may be refilled)
+            fetch(X.nxt, X.has_next());
+            for (int k = 0; k < nst; ++k, ++g) {
+                const int q = g % P2_NS;
+                bool ok = g < P2_NS || tc_wait(S, &S.empty[q], ((g / P2_NS) - 1) & 1, err);
+                ok = __all_sync(0xffffffffu, ok && !tc_aborted(S));
+                if (!ok) break;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {  // row j: 128 bytes, chunks XOR-swizzled by j mod 8
+                    const int jj = jr + 8 * h, j = k * 32 + jj;
+                    const uint32_t* row = XB;
+                    uint32_t bytes = 0;  // 0: zero fill
+                    if (j < I.ncol) {
+                        const uint32_t code = tab[j];
+                        row = (code & 0x80000000u) ? T16 + (int64_t)(code & 0x7fffffffu) * NR
+                                                   : XB + (int64_t)code * NR;
+                        bytes = 16;
+                    }
+                    cp_async16(S.w[q] + jj * 128 + ((c ^ (jj & 7)) << 4), row + 4 * c, bytes);
+                }
+                // the stage's barrier counts this thread once its copies have landed
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.wfull[q]))
+                             : "memory");
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.wfull[q]);
-            load(k + 1);
         }
-        bool ok = nst > 0 && tc_wait(S, &S.accf, 0, err);
-        if (__all_sync(0xffffffffu, ok)) {
+        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the block
+    } else {  // ---- accumulators into Y ----
+        const int lq = warp & 3;
+        const bool odd = lane & 1;
+        int ii = 0;
+        for (ItemIter X(items, nitems); X.valid(); X.advance(), ++ii) {
+            const TcItem I = X.cur;
+            const int nmt = (((2 * I.ld16 + 63) >> 6) + 1) >> 1;
+            const int set = ii & 1;
+            if (!__all_sync(0xffffffffu, tc_wait(S, &S.accf[set], (ii >> 1) & 1, err))) break;
             tc_fence_after();
-            const int lq = warp & 3;
-            const int R = it.rows;
-            const bool odd = lane & 1;
-            for (int t = 0; t < nmt; ++t) {
+            for (int t = 0; I.ncol > 0 && t < nmt; ++t) {
                 uint32_t v[64];
-                tmem_ld64(tmem, lq, t * 64, v);
+                tmem_ld64(tmem, lq, set * 256 + t * 64, v);
                 // even lane: row m = 2r (real parts of M), odd lane: m = 2r + 1;
                 // the even lane forms y_r(s) for s < 16, the odd lane for s >= 16
                 float o[32];  // even: D_odd[cc]; odd: D_even[32 + cc]
@@ -490,8 +549,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase2(const WorkItem* item
                 for (int cc = 0; cc < 32; ++cc)
                     o[cc] = __uint_as_float(__shfl_xor_sync(0xffffffffu, odd ? v[cc] : v[32 + cc], 1));
                 const int r = (t * 128 + lq * 32 + lane) >> 1;
-                if (r < R) {
-                    float* dst = reinterpret_cast<float*>(Y + (it.dof + r) * NR + (odd ? 16 : 0));
+                if (r < I.rows) {
+                    float* dst = reinterpret_cast<float*>(Y + (I.dof + r) * NR + (odd ? 16 : 0));
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float out[4];
@@ -510,14 +569,23 @@ __global__ void __launch_bounds__(TC_THREADS, 2) mvc_phase2(const WorkItem* item
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acce[set]);
         }
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TC2_TMEM_COLS));
+    tc_teardown(S, P2_TMEM_COLS);
+}
+
+// Per-column table of phase 1 from the uploaded headers (scales are final):
+// entry colpos[q] + c of chunk q = (t index, s_V s_U).
+__global__ void colinfo1_kernel(const DevChunk16* hdr, const int64_t* colpos, int64_t nchunk,
+                                float2* colinfo) {
+    const int64_t q = blockIdx.x;
+    if (q >= nchunk) return;
+    const DevChunk16 ch = hdr[q];
+    for (int c = threadIdx.x; c < ch.ncols; c += blockDim.x)
+        colinfo[colpos[q] + c] = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale * ch.fold);
 }
 
 // XB rows 2q and 2q + 1 of tree-order DOF q: (x_r, x_i) and (x_i, -x_r) of each
@@ -615,12 +683,75 @@ int64_t matvec_multi_alg_bytes(const MatvecDev* m, int64_t ndof) {
            (int64_t)NR * 8 * (2 * ndof + 2 * m->t_elems);
 }
 
+void make_block_items(MatvecDev* m, const std::vector<DevChunk16>& c16, std::vector<DevBuf>& owner,
+                      cudaStream_t st) {
+    auto build = [&](const std::vector<WorkItem>& its, const std::vector<int32_t>& order,
+                     std::vector<TcItem>& out, std::vector<int64_t>& colpos, std::vector<uint32_t>* codes) {
+        colpos.assign(order.size(), 0);
+        int64_t col = 0;
+        for (const WorkItem& w : its) {
+            const DevChunk16& a = c16[order[w.first]];
+            TcItem t;
+            t.dof = w.dof;
+            t.col0 = col;
+            t.row0 = (int32_t)(a.data / a.ld);
+            t.ld16 = a.ld;
+            t.rows = w.rows;
+            for (int32_t q = w.first; q < w.last; ++q) {
+                const DevChunk16& c = c16[order[q]];
+                colpos[q] = col;
+                if (codes)
+                    for (int32_t j = 0; j < c.ncols; ++j)
+                        codes->push_back(c.kind != 0 ? ((uint32_t)(c.vec + j) | 0x80000000u)
+                                                     : (uint32_t)(2 * (c.vec + j)));
+                col += c.ncols;
+            }
+            t.ncol = (int32_t)(col - t.col0);
+            out.push_back(t);
+        }
+        return col;
+    };
+    std::vector<TcItem> t1, t2;
+    std::vector<int64_t> pos1, pos2;
+    std::vector<uint32_t> codes;
+    const int64_t ncol1 = build(m->h_items1, m->h_order1, t1, pos1, nullptr);
+    build(m->h_items2, m->h_order2, t2, pos2, &codes);
+    m->titems1 = (TcItem*)hm_dmalloc(owner, std::max<size_t>(t1.size(), 1) * sizeof(TcItem), st, false);
+    m->titems2 = (TcItem*)hm_dmalloc(owner, std::max<size_t>(t2.size(), 1) * sizeof(TcItem), st, false);
+    m->colinfo1 = (float2*)hm_dmalloc(owner, std::max<int64_t>(ncol1, 1) * sizeof(float2), st, false);
+    m->colcode2 = (uint32_t*)hm_dmalloc(owner, std::max<size_t>(codes.size(), 1) * 4, st, false);
+    HM_CUDA(cudaMemcpyAsync(m->titems1, t1.data(), t1.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->titems2, t2.data(), t2.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->colcode2, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!pos1.empty()) {
+        int64_t* d_pos = nullptr;
+        HM_CUDA(cudaMallocAsync((void**)&d_pos, pos1.size() * 8, st));
+        HM_CUDA(cudaMemcpyAsync(d_pos, pos1.data(), pos1.size() * 8, cudaMemcpyHostToDevice, st));
+        colinfo1_kernel<<<(unsigned)pos1.size(), 128, 0, st>>>(m->hdr16_1, d_pos, (int64_t)pos1.size(),
+                                                               m->colinfo1);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+        HM_CUDA(cudaFreeAsync(d_pos, st));
+    }
+    HM_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+}
+
+static int multi_grid(int64_t nitems) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return (int)std::min<int64_t>(nitems, nsm);
+}
+
 static void multi_setup(MatvecDev* m, int64_t n, cudaStream_t st) {
     if (m->xb) return;
     HM_CUDA(cudaFuncSetAttribute(mvc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(TC1Smem) + 1024));
+                                 (int)sizeof(P1Smem) + 1024));
     HM_CUDA(cudaFuncSetAttribute(mvc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(TC2Smem) + 1024));
+                                 (int)sizeof(P2Smem) + 1024));
     const int64_t nt = std::max<int64_t>(m->t_elems, 1);
     HM_CUDA(cudaMalloc((void**)&m->xb, (size_t)2 * n * NR * 4));
     HM_CUDA(cudaMalloc((void**)&m->ym, (size_t)n * NR * sizeof(float2)));
@@ -641,9 +772,9 @@ static void multi_phases(MatvecDev* m, int64_t n, cudaStream_t st, cudaEvent_t e
     HM_CUDA(cudaMemsetAsync(m->ym, 0, (size_t)n * NR * sizeof(float2), st));
     if (e1) HM_CUDA(cudaEventRecord(e1, st));
     if (m->n1) {
-        mvc_phase1<<<(unsigned)m->n1, TC_THREADS, sizeof(TC1Smem) + 1024, st>>>(
-            m->items1, m->hdr16_1, (const CUtensorMap*)m->tmaps, (const CUtensorMap*)m->tmap_xb,
-            m->tm, m->d_err);
+        mvc_phase1<<<multi_grid(m->n1), P1_THREADS, sizeof(P1Smem) + 1024, st>>>(
+            m->titems1, (int)m->n1, m->colinfo1, (const CUtensorMap*)m->tmaps,
+            (const CUtensorMap*)m->tmap_xb, m->tm, m->d_err);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
@@ -656,9 +787,9 @@ static void multi_phases(MatvecDev* m, int64_t n, cudaStream_t st, cudaEvent_t e
         HM_LAUNCHED();
     }
     if (m->n2) {
-        mvc_phase2<<<(unsigned)m->n2, TC_THREADS, sizeof(TC2Smem) + 1024, st>>>(
-            m->items2, m->hdr16_2, (const CUtensorMap*)m->tmaps + TMAP_PER_PHASE, m->xb, m->t16,
-            m->ym, m->d_err);
+        mvc_phase2<<<multi_grid(m->n2), P2_THREADS, sizeof(P2Smem) + 1024, st>>>(
+            m->titems2, (int)m->n2, m->colcode2, (const CUtensorMap*)m->tmaps + TMAP_PER_PHASE, m->xb,
+            m->t16, m->ym, m->d_err);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
