@@ -40,8 +40,9 @@ template <> struct MvT<false> {
 };
 
 __device__ __forceinline__ float red_sum(float v) { return warp_sumf(v); }
+// *p += (re, im) as a reduction (no value returned, so no round trip to wait for)
 __device__ __forceinline__ void atomic_add_c(float2* p, float re, float im) {
-    atomicAdd(p, make_float2(re, im));
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(re), "f"(im) : "memory");
 }
 
 // Phase 1: for every V chunk of the item's column leaf, t[vec + c] += V[:, c]^H x_leaf.
@@ -360,7 +361,6 @@ __global__ void split_df_kernel(const double2* t64, float4* tdf, int64_t n) {
 __device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
     return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
 }
-constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (192 rows -> 48 quads -> 2)
 
 // ---- BF16 storage, streamed through shared memory ----
 // Every work item is one contiguous byte range of the BF16 arena: the chunks of
@@ -373,10 +373,18 @@ constexpr int QUADS_PER_LANE = (MAX_LD / 4 + 31) / 32;  // row quads per lane (1
 // registers of the consumers.  Each wait gives up after PIPE_WAIT_NS, records
 // an error code and lets the CTA finish; the producer always waits for its own
 // copies before it exits.
-constexpr int S16_CONSUMERS = 8;
+//
+// A consumer warp takes four columns of a stage at once, one per group of 8
+// lanes; a lane covers the row quads sl, sl + 8, ... of its column (about 95 %
+// of the lanes busy for the usual 150-row columns, where one column per warp
+// leaves 40 % idle), so a stored entry costs one conversion and four FMAs and
+// a column of phase 1 a three-step shuffle reduction.
+constexpr int S16_CONSUMERS = 4;
 constexpr int S16_THREADS = 32 * (S16_CONSUMERS + 1);
 constexpr int S16_NSTAGE = 3;
-constexpr int S16_STAGE_BYTES = 12288;
+constexpr int S16_COLS = 4 * S16_CONSUMERS;             // columns per stage: one per lane group
+constexpr int S16_STAGE_BYTES = S16_COLS * MAX_LD * 4;  // 12 KB
+constexpr int S16_QPL = MAX_LD / 4 / 8;                 // row quads per lane (48 quads / 8 lanes)
 constexpr int MV_ERR_TIMEOUT = 1;
 
 static_assert(S16_CONSUMERS * MAX_LD * sizeof(float2) <= S16_NSTAGE * S16_STAGE_BYTES,
@@ -397,7 +405,7 @@ __device__ __forceinline__ void consumers_sync() { named_sync<1, 32 * S16_CONSUM
 
 // PHASE 1: t[vec_j] += scale_j * V_j^H x_leaf;  PHASE 2: y_leaf += sum_j M_j scale_j v_j.
 template <int PHASE>
-__global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* items,
+__global__ void __launch_bounds__(S16_THREADS, 4) mv16s_kernel(const WorkItem* items,
                                                            const DevChunk16* hdr,
                                                            const uint32_t* __restrict__ arena,
                                                            const float2* __restrict__ xp,
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* item
     const int ncol = S.ncol;
     const int ld16 = S.hdr[0].ld;
     const int colb = ld16 * 4;
-    const int sc = S16_STAGE_BYTES / colb;  // columns per stage
+    const int sc = S16_COLS;  // columns per stage
     const int nst = (ncol + sc - 1) / sc;
     if (warp == S16_CONSUMERS) {  // ---- producer ----
         if (lane == 0) {
@@ -474,14 +482,17 @@ __global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* item
     }
     consumers_sync();
     const int nquad = (it.rows + 3) >> 2;
+    const int nq8 = (nquad + 7) >> 3;  // quad rounds of the 8-lane groups (warp-uniform)
     const int ldq = ld16 >> 2;
-    float2 xa[QUADS_PER_LANE][4];  // phase 1: x of this lane's rows; phase 2: row sums
+    const int lg = lane >> 3, sl = lane & 7;
+    // phase 1: x of this lane's rows; phase 2: the lane's partial row sums
+    float2 xa[S16_QPL][4];
 #pragma unroll
-    for (int q = 0; q < QUADS_PER_LANE; ++q)
+    for (int i = 0; i < S16_QPL; ++i)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int r = 4 * (lane + 32 * q) + e;
-            xa[q][e] = (PHASE == 1 && r < it.rows) ? xp[it.dof + r] : make_float2(0.f, 0.f);
+            const int r = 4 * (sl + 8 * i) + e;
+            xa[i][e] = (PHASE == 1 && r < it.rows) ? xp[it.dof + r] : make_float2(0.f, 0.f);
         }
     for (int k = 0; k < nst; ++k) {
         const int s = k % S16_NSTAGE;
@@ -490,81 +501,63 @@ __global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* item
             break;
         }
         const int jb = k * sc;
-        const int g = min(sc, ncol - jb);
-        const uint4* sb = reinterpret_cast<const uint4*>(S.stage[s]);
-        // two columns (c, c + S16_CONSUMERS) per pass: loads first, then arithmetic
-        for (int c = warp; c < g; c += 2 * S16_CONSUMERS) {
-            const int c1 = c + S16_CONSUMERS;
-            const bool two = c1 < g;
-            const float2 w0 = S.w[jb + c];
-            const float2 w1 = two ? S.w[jb + c1] : make_float2(0.f, 0.f);
-            uint4 u0[QUADS_PER_LANE], u1[QUADS_PER_LANE];
+        const int c = 4 * warp + lg;  // this lane group's column of the stage
+        const bool valid = c < min(sc, ncol - jb);
+        const uint4* col = reinterpret_cast<const uint4*>(S.stage[s]) + c * ldq;
+        const float2 w = valid ? S.w[jb + c] : make_float2(0.f, 0.f);
+        float re = 0.f, im = 0.f;
 #pragma unroll
-            for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                const int qq = lane + 32 * q;
-                u0[q] = qq < nquad ? sb[c * ldq + qq] : make_uint4(0, 0, 0, 0);
-                u1[q] = (two && qq < nquad) ? sb[c1 * ldq + qq] : make_uint4(0, 0, 0, 0);
-            }
-            if (PHASE == 2) {
+        for (int i = 0; i < S16_QPL; ++i) {
+            if (i < nq8) {
+                const int qd = sl + 8 * i;
+                const uint4 u = (valid && qd < nquad) ? col[qd] : make_uint4(0, 0, 0, 0);
+                const uint32_t a4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const uint32_t a4[4] = {u0[q].x, u0[q].y, u0[q].z, u0[q].w};
-                    const uint32_t b4[4] = {u1[q].x, u1[q].y, u1[q].z, u1[q].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 a = bf2_to_f2(a4[e]), b = bf2_to_f2(b4[e]);
-                        float2& s2 = xa[q][e];
-                        s2.x = fmaf(a.x, w0.x, fmaf(-a.y, w0.y, s2.x));
-                        s2.y = fmaf(a.x, w0.y, fmaf(a.y, w0.x, s2.y));
-                        s2.x = fmaf(b.x, w1.x, fmaf(-b.y, w1.y, s2.x));
-                        s2.y = fmaf(b.x, w1.y, fmaf(b.y, w1.x, s2.y));
+                for (int e = 0; e < 4; ++e) {
+                    const float2 a = bf2_to_f2(a4[e]);
+                    if (PHASE == 2) {  // rows += a w
+                        float2& s2 = xa[i][e];
+                        s2.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, s2.x));
+                        s2.y = fmaf(a.x, w.y, fmaf(a.y, w.x, s2.y));
+                    } else {           // conj(a) x
+                        const float2 xv = xa[i][e];
+                        re = fmaf(a.x, xv.x, fmaf(a.y, xv.y, re));
+                        im = fmaf(a.x, xv.y, fmaf(-a.y, xv.x, im));
                     }
                 }
-            } else {
-                float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < QUADS_PER_LANE; ++q) {
-                    const uint32_t a4[4] = {u0[q].x, u0[q].y, u0[q].z, u0[q].w};
-                    const uint32_t b4[4] = {u1[q].x, u1[q].y, u1[q].z, u1[q].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {  // conj(a) x
-                        const float2 a = bf2_to_f2(a4[e]), b = bf2_to_f2(b4[e]);
-                        const float2 xv = xa[q][e];
-                        re0 = fmaf(a.x, xv.x, fmaf(a.y, xv.y, re0));
-                        im0 = fmaf(a.x, xv.y, fmaf(-a.y, xv.x, im0));
-                        re1 = fmaf(b.x, xv.x, fmaf(b.y, xv.y, re1));
-                        im1 = fmaf(b.x, xv.y, fmaf(-b.y, xv.x, im1));
-                    }
-                }
-                // halving reduction: lanes < 16 finish column c, lanes >= 16 column c1
-                const bool up = (lane & 16) != 0;
-                float k0 = up ? re1 : re0, k1 = up ? im1 : im0;
-                k0 += __shfl_xor_sync(0xffffffffu, up ? re0 : re1, 16);
-                k1 += __shfl_xor_sync(0xffffffffu, up ? im0 : im1, 16);
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    k0 += __shfl_xor_sync(0xffffffffu, k0, o);
-                    k1 += __shfl_xor_sync(0xffffffffu, k1, o);
-                }
-                if ((lane & 15) == 0 && (!up || two)) {
-                    const float2 wj = up ? w1 : w0;
-                    atomicAdd(t + __float_as_int(wj.x), make_float2(k0 * wj.y, k1 * wj.y));
-                }
             }
+        }
+        if (PHASE == 1) {  // sum over the 8 lanes of the group
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (sl == 0 && valid) atomic_add_c(t + __float_as_int(w.x), re * w.y, im * w.y);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);
     }
     if (PHASE == 2) {
-        consumers_sync();  // every stage consumed: reuse them for the row sums
-        float2(*part)[MAX_LD] = reinterpret_cast<float2(*)[MAX_LD]>(S.stage[0]);
+        // the four lane groups of a warp hold partial sums of the same rows
 #pragma unroll
-        for (int q = 0; q < QUADS_PER_LANE; ++q)
+        for (int i = 0; i < S16_QPL; ++i)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int r = 4 * (lane + 32 * q) + e;
-                if (r < MAX_LD) part[warp][r] = xa[q][e];
+                float2& s2 = xa[i][e];
+                s2.x += __shfl_xor_sync(0xffffffffu, s2.x, 8);
+                s2.y += __shfl_xor_sync(0xffffffffu, s2.y, 8);
+                s2.x += __shfl_xor_sync(0xffffffffu, s2.x, 16);
+                s2.y += __shfl_xor_sync(0xffffffffu, s2.y, 16);
             }
+        consumers_sync();  // every stage consumed: reuse them for the row sums
+        float2(*part)[MAX_LD] = reinterpret_cast<float2(*)[MAX_LD]>(S.stage[0]);
+        if (lg == 0) {
+#pragma unroll
+            for (int i = 0; i < S16_QPL; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) part[warp][4 * (sl + 8 * i) + e] = xa[i][e];
+        }
         consumers_sync();
         for (int r = tid; r < it.rows; r += 32 * S16_CONSUMERS) {
             float2 s2 = part[0][r];
@@ -572,7 +565,7 @@ __global__ void __launch_bounds__(S16_THREADS) mv16s_kernel(const WorkItem* item
                 s2.x += part[w][r].x;
                 s2.y += part[w][r].y;
             }
-            atomicAdd(yp + it.dof + r, s2);
+            atomic_add_c(yp + it.dof + r, s2.x, s2.y);
         }
     }
 }
