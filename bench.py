@@ -349,8 +349,9 @@ def run_gpu(args, wl, world, rank, local):
         "config": {"workload": args.workload, "n_c": wl["nc"], "kappa_s": wl["ks"],
                    "kernel": wl["kernel"], "leaf": wl["leaf"], "eta": wl["eta"], "eps": wl["eps"],
                    "weights": "4 pi / n_c (W_y of Sec. 4)",
-                   "storage": ("bf16-complex + fp32 scale per chunk (products); fp32 for "
-                               "refinement residuals") if form == "mixed" else "fp32-complex",
+                   "storage": ("bf16-complex, one fp32 scale per block and factor for U and V, "
+                               "dense blocks unscaled (products); fp32 for refinement residuals")
+                   if form == "mixed" else "fp32-complex",
                    "form": form,
                    "green": "fp64", "matvecs_per_step": args.matvecs,
                    "gmres": "GMRES(100) to 1e-6, FP64 vectors",
