@@ -102,8 +102,13 @@ void hm_opts_default(hm_opts* opts);
  *   out      receives the handle (NULL on error)
  * An admissible block whose vector ACA had to retire a row with a non-negligible
  * residual because all its 3x3 candidate pivots are singular (Sec. 2.3: T on
- * coplanar points has rank-2 3x3 blocks) is stored dense instead (exact); its
- * hm_block then reads admissible = 0, rank_aca = the steps taken.
+ * coplanar points has rank-2 3x3 blocks) is compressed by the randomized SVD
+ * instead (the remark closing Sec. 2.3): an FP64 Gaussian sketch of l columns
+ * (l = 64, doubling up to min(3m, 3n, 768) until 8 probe columns certify a
+ * range error below eps/2), its orthonormal basis Q, V = A^H Q, then the
+ * recompression with eps sqrt(3)/2; its hm_block reads rank_aca = l.  The
+ * statistics count such blocks (rsvd_blocks) and those whose samples reached
+ * the cap uncertified (rsvd_uncertified).
  * Errors: HM_ERR_ARG (n_c < 1, non-finite or non-positive parameters, missing
  * normals for T, non-finite coordinates, two distinct points at the same
  * position: their Green's tensor is singular), HM_ERR_OOM, HM_ERR_CUDA. */
@@ -285,7 +290,7 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
  * cap too small for the block's rank: *rank = -1), HM_ERR_NUMERIC,
  * HM_ERR_UNSUPPORTED (a row with a non-negligible residual whose 3x3 blocks are
  * all singular, e.g. coplanar T blocks: the vector ACA cannot pivot it and
- * hm_build stores such blocks dense), HM_ERR_CUDA. */
+ * hm_build compresses such blocks by the randomized SVD), HM_ERR_CUDA. */
 hm_status hm_aca_block_noalloc(int32_t kernel, double rho, double lambda, double mu,
                                double omega, const double* x, int64_t m, const double* y,
                                const double* ny, int64_t n, double eps, int32_t cap, void* uv,

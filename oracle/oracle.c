@@ -509,7 +509,7 @@ static void qr_householder(const cplx* A, int64_t M, int64_t N, cplx* Q, cplx* R
 
 int or_qr_householder(const double* A, int64_t M, int64_t N, double* Q, double* R)
 {
-    cplx* a = (cplx*)malloc((size_t)(M * N) * sizeof(cplx));
+    cplx* a = (cplx*)calloc((size_t)(M * N) + 1, sizeof(cplx));
     cplx* q = (cplx*)malloc((size_t)(M * N) * sizeof(cplx));
     cplx* rr = (cplx*)malloc((size_t)(N * N) * sizeof(cplx));
     for (int64_t i = 0; i < M * N; ++i) a[i] = ld(A + 2 * i);
@@ -868,6 +868,154 @@ int64_t or_recompress(const double* U, const double* V, int64_t M, int64_t N, in
 }
 
 /* ======================================================================
+ * Randomized SVD (the remark closing Sec. 2.3, which prefers the randomized
+ * SVD of Liberty, Woolfe, Martinsson, Rokhlin & Tygert 2007 to the vector ACA
+ * for blocks whose 3x3 sub-blocks are all singular).  For a block A (3m x 3n):
+ *   1. draw a Gaussian test matrix Omega (3n x l) and sketch Y = A Omega;
+ *   2. Q = an orthonormal basis of range(Y) (Householder QR);
+ *   3. B = Q^H A, so that A ~ Q B;
+ * the number of samples l doubles until p further probe columns w certify
+ * the range error; the factors (U, V) = (Q, B^H) then go through the
+ * recompression of Sec. 3.2 (QR, SVD of the core, truncation).
+ * Readings (the remark names the method only):
+ *   Omega(j, c) is a complex normal number with E|w|^2 = 1, made by the
+ *     Box-Muller transform from two uniforms of the splitmix64 generator
+ *     (Steele, Lea & Flood 2014) applied to a counter (j, c) under a key made
+ *     from the block's first row and column point in tree order, so that any
+ *     implementation of the same published definitions draws the same matrix;
+ *   l starts at 64 and doubles, up to min(3m, 3n, 768);
+ *   the range is accepted when the mean over p = 8 probes of
+ *     |(I - Q Q^H) A w|^2 is at most (eps/4)^2 ||A||_F^2; since
+ *     E|(I - Q Q^H) A w|^2 = ||(I - Q Q^H) A||_F^2, the range error is then
+ *     below eps/2 ||A||_F with high probability, and the recompression
+ *     truncates with eps sqrt(3)/2: the two errors are orthogonal, so the
+ *     total stays below eps ||A||_F.
+ * ====================================================================== */
+#define RSVD_L0 64
+#define RSVD_P 8
+#define RSVD_LMAX 768
+#define RSVD_CSTRIDE 1024 /* counter of Omega(j, c) = j * RSVD_CSTRIDE + c */
+
+static uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static cplx rsvd_gauss(uint64_t key, uint64_t ctr)
+{
+    const uint64_t a = splitmix64(key ^ splitmix64(2 * ctr));
+    const uint64_t b = splitmix64(key ^ splitmix64(2 * ctr + 1));
+    const double u1 = (double)((a >> 11) + 1) * 0x1.0p-53; /* (0, 1] */
+    const double u2 = (double)(b >> 11) * 0x1.0p-53;       /* [0, 1) */
+    const double r = sqrt(-log(u1)); /* sqrt(-2 ln u1) times the 1/sqrt(2) of E|w|^2 = 1 */
+    const double th = 2.0 * M_PI * u2;
+    return r * cos(th) + I * (r * sin(th));
+}
+
+uint64_t or_splitmix64(uint64_t z) { return splitmix64(z); }
+
+uint64_t or_rsvd_key(int64_t tau_begin, int64_t sigma_begin)
+{
+    return splitmix64(((uint64_t)tau_begin << 32) ^ (uint64_t)sigma_begin);
+}
+
+void or_gauss(uint64_t key, uint64_t ctr, double* out2) { st(out2, rsvd_gauss(key, ctr)); }
+
+/* Runs steps 1-3 on the block of source s; returns l, with U = Q (3m x l) and
+ * V = B^H (3n x l) col-major in *Uout, *Vout.  *ok = 0 if l reached its cap
+ * without the probes' certificate. */
+static int64_t rsvd_run(const block_src* s, double eps, uint64_t key, cplx** Uout, cplx** Vout,
+                        int* ok)
+{
+    const int64_t M = 3 * s->m, N = 3 * s->n;
+    cplx* A = (cplx*)malloc((size_t)(M * N) * sizeof(cplx));
+    cplx* C = (cplx*)malloc((size_t)(3 * M) * sizeof(cplx));
+    for (int64_t j = 0; j < s->n; ++j) {
+        src_col(s, j, C); /* 3m x 3 row-major */
+        for (int64_t r = 0; r < M; ++r)
+            for (int b = 0; b < 3; ++b) A[r + (3 * j + b) * M] = C[3 * r + b];
+    }
+    free(C);
+    double anorm2 = 0.0;
+    for (int64_t e = 0; e < M * N; ++e) anorm2 += abs2(A[e]);
+    int64_t lmax = M < N ? M : N;
+    if (lmax > RSVD_LMAX) lmax = RSVD_LMAX;
+    int64_t l = lmax < RSVD_L0 ? lmax : RSVD_L0;
+    cplx *Y = NULL, *Q = NULL, *R = NULL;
+    *ok = 0;
+    for (;;) {
+        const int64_t L = l + RSVD_P;
+        Y = (cplx*)malloc((size_t)(M * L) * sizeof(cplx));
+        for (int64_t c = 0; c < L; ++c)
+            for (int64_t r = 0; r < M; ++r) Y[r + c * M] = 0.0;
+        for (int64_t j = 0; j < N; ++j)
+            for (int64_t c = 0; c < L; ++c) {
+                const cplx w = rsvd_gauss(key, (uint64_t)j * RSVD_CSTRIDE + (uint64_t)c);
+                for (int64_t r = 0; r < M; ++r) Y[r + c * M] += A[r + j * M] * w;
+            }
+        Q = (cplx*)malloc((size_t)(M * l) * sizeof(cplx));
+        R = (cplx*)malloc((size_t)(l * l) * sizeof(cplx));
+        qr_householder(Y, M, l, Q, R);
+        double est = 0.0;
+        for (int64_t c = l; c < L; ++c) { /* |y - Q Q^H y|^2 of the probe column */
+            const cplx* y = Y + c * M;
+            cplx* z = (cplx*)malloc((size_t)M * sizeof(cplx));
+            for (int64_t r = 0; r < M; ++r) z[r] = y[r];
+            for (int64_t t = 0; t < l; ++t) {
+                cplx d = 0.0;
+                for (int64_t r = 0; r < M; ++r) d += conj(Q[r + t * M]) * y[r];
+                for (int64_t r = 0; r < M; ++r) z[r] -= Q[r + t * M] * d;
+            }
+            for (int64_t r = 0; r < M; ++r) est += abs2(z[r]);
+            free(z);
+        }
+        est /= RSVD_P;
+        free(Y);
+        free(R);
+        if (est <= (eps / 4) * (eps / 4) * anorm2) *ok = 1;
+        if (*ok || l == lmax) break;
+        free(Q);
+        l = 2 * l < lmax ? 2 * l : lmax;
+    }
+    cplx* V = (cplx*)malloc((size_t)(N * l) * sizeof(cplx));
+    for (int64_t c = 0; c < l; ++c)
+        for (int64_t j = 0; j < N; ++j) {
+            cplx acc = 0.0;
+            for (int64_t r = 0; r < M; ++r) acc += conj(A[r + j * M]) * Q[r + c * M];
+            V[j + c * N] = acc;
+        }
+    free(A);
+    *Uout = Q;
+    *Vout = V;
+    return l;
+}
+
+int64_t or_rsvd_dense(const double* A, int64_t m, int64_t n, double eps, uint64_t key,
+                      int64_t lcap, double* U, double* V, int* ok)
+{
+    block_src src = {0};
+    src.kind = 0;
+    src.m = m;
+    src.n = n;
+    src.A = A;
+    cplx *u, *v;
+    const int64_t l = rsvd_run(&src, eps, key, &u, &v, ok);
+    if (l > lcap) {
+        free(u);
+        free(v);
+        return -1;
+    }
+    for (int64_t i = 0; i < 3 * m * l; ++i) st(U + 2 * i, u[i]);
+    for (int64_t i = 0; i < 3 * n * l; ++i) st(V + 2 * i, v[i]);
+    free(u);
+    free(v);
+    return l;
+}
+
+/* ======================================================================
  * H-matrix: tree + partition + per-block data (Sec. 2, Sec. 3.1).
  * ====================================================================== */
 struct or_hmat {
@@ -882,6 +1030,7 @@ struct or_hmat {
     int64_t* rank;
     cplx** D;  /* dense data, or U */
     cplx** V;  /* low-rank V */
+    char* method; /* admissible blocks: 0 vector ACA, 1 randomized SVD */
     char* built;
     double build_s;
 };
@@ -912,6 +1061,7 @@ or_hmat* or_hmat_build(const or_problem* pb, const double* pts, const double* nr
     h->D = (cplx**)calloc((size_t)(h->nb + 1), sizeof(cplx*));
     h->V = (cplx**)calloc((size_t)(h->nb + 1), sizeof(cplx*));
     h->built = (char*)calloc((size_t)(h->nb + 1), 1);
+    h->method = (char*)calloc((size_t)(h->nb + 1), 1);
     if (sample_stride < 1) sample_stride = 1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -949,21 +1099,26 @@ or_hmat* or_hmat_build(const or_problem* pb, const double* pts, const double* nr
             h->rank_aca[b] = k;
             if (lost) {
                 /* rows the vector ACA cannot pivot (every 3x3 block singular):
-                 * the block is stored exactly, as a dense block */
+                 * the randomized SVD (remark of Sec. 2.3) compresses the block */
                 free(U);
                 free(V);
-                h->blk[b].admissible = 0;
-                cplx* D = (cplx*)malloc((size_t)(9 * m * n) * sizeof(cplx));
-                for (int64_t j = 0; j < n; ++j)
-                    for (int64_t i = 0; i < m; ++i) {
-                        cplx G[3][3];
-                        entry_block(pb, pts, nrm, h->perm[t->begin + i], h->perm[s->begin + j], G);
-                        for (int a = 0; a < 3; ++a)
-                            for (int c = 0; c < 3; ++c)
-                                D[(3 * i + a) + (3 * j + c) * (3 * m)] = G[a][c];
-                    }
-                h->D[b] = D;
-                h->rank[b] = 0;
+                int ok = 0;
+                const int64_t l = rsvd_run(&src, eps, or_rsvd_key(t->begin, s->begin), &U, &V, &ok);
+                h->rank_aca[b] = l;
+                h->method[b] = ok ? 1 : 2;
+                if (recompress_on) {
+                    cplx *U2, *V2;
+                    const int64_t r = recompress(U, V, 3 * m, 3 * n, l, eps * sqrt(3.0) / 2, &U2, &V2, NULL);
+                    free(U);
+                    free(V);
+                    h->D[b] = U2;
+                    h->V[b] = V2;
+                    h->rank[b] = r;
+                } else {
+                    h->D[b] = U;
+                    h->V[b] = V;
+                    h->rank[b] = l;
+                }
             } else if (recompress_on) {
                 cplx *U2, *V2;
                 const int64_t r = recompress(U, V, 3 * m, 3 * n, k, eps, &U2, &V2, NULL);
@@ -994,12 +1149,18 @@ void or_hmat_free(or_hmat* h)
     free(h->D);
     free(h->V);
     free(h->built);
+    free(h->method);
     free(h->rank);
     free(h->rank_aca);
     free(h->blk);
     free(h->cl);
     free(h->perm);
     free(h);
+}
+
+void or_hmat_block_methods(const or_hmat* h, int32_t* out)
+{
+    for (int64_t b = 0; b < h->nb; ++b) out[b] = h->method[b];
 }
 
 int64_t or_hmat_nclusters(const or_hmat* h) { return h->ncl; }

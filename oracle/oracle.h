@@ -104,6 +104,20 @@ int64_t or_aca_dense(const double* A, int64_t m, int64_t n, double eps,
 int64_t or_recompress(const double* U, const double* V, int64_t M, int64_t N, int64_t k,
                       double eps, double* U2, double* V2, double* svals);
 
+/* --- randomized SVD (remark of Sec. 2.3) for blocks the vector ACA cannot
+ * pivot: Gaussian sketch, orthonormal range basis, projection; l doubles from
+ * 64 until 8 probe columns certify the range error (eps/2), capped at
+ * min(3m, 3n, 768).  A is 3m x 3n row-major; returns l with U = Q (3m x l)
+ * and V = (Q^H A)^H (3n x l) col-major, or -1 if l > lcap; *ok = 0 when the
+ * cap was reached uncertified.  or_gauss: the test matrix's entry for
+ * (key, counter): splitmix64 + Box-Muller, complex, E|w|^2 = 1; or_rsvd_key:
+ * the key of the block whose first row / column points (tree order) are given. */
+int64_t or_rsvd_dense(const double* A, int64_t m, int64_t n, double eps, uint64_t key,
+                      int64_t lcap, double* U, double* V, int* ok);
+void or_gauss(uint64_t key, uint64_t ctr, double* out2);
+uint64_t or_splitmix64(uint64_t z); /* one output of the generator from state z - gamma */
+uint64_t or_rsvd_key(int64_t tau_begin, int64_t sigma_begin);
+
 /* --- the H-matrix (build = tree + partition + dense blocks + ACA + recompress) */
 typedef struct or_hmat or_hmat;
 or_hmat* or_hmat_build(const or_problem* pb, const double* pts, const double* nrm,
@@ -115,6 +129,9 @@ void or_hmat_clusters(const or_hmat* h, or_cluster* out);
 void or_hmat_perm(const or_hmat* h, int64_t* perm);
 int64_t or_hmat_nblocks(const or_hmat* h);
 void or_hmat_blocks(const or_hmat* h, or_block* out, int64_t* rank_aca, int64_t* rank);
+/* per block: 0 dense or vector ACA, 1 randomized SVD (certified), 2 randomized
+ * SVD that reached its sample cap; rank_aca holds l for the latter two */
+void or_hmat_block_methods(const or_hmat* h, int32_t* out);
 /* dense: D (3|tau| x 3|sigma| col-major); low rank: U (3|tau| x r), V (3|sigma| x r). */
 void or_hmat_block_data(const or_hmat* h, int64_t b, double* D_or_U, double* V);
 void or_hmat_matvec(const or_hmat* h, const double* x, double* y);

@@ -62,6 +62,11 @@ def lib():
             "or_qr_householder": (_INT, [_P, _I64, _I64, _P, _P]),
             "or_aca_dense": (_I64, [_P, _I64, _I64, _D, _I64, _P, _P, _P]),
             "or_recompress": (_I64, [_P, _P, _I64, _I64, _I64, _D, _P, _P, _P]),
+            "or_rsvd_dense": (_I64, [_P, _I64, _I64, _D, C.c_uint64, _I64, _P, _P, _P]),
+            "or_gauss": (None, [C.c_uint64, C.c_uint64, _P]),
+            "or_rsvd_key": (C.c_uint64, [_I64, _I64]),
+            "or_splitmix64": (C.c_uint64, [C.c_uint64]),
+            "or_hmat_block_methods": (None, [_P, _P]),
             "or_hmat_build": (_P, [_P, _P, _P, _I64, _D, _D, _I64, _INT, _I64, _INT]),
             "or_hmat_free": (None, [_P]),
             "or_hmat_nclusters": (_I64, [_P]),
@@ -230,6 +235,38 @@ def recompress(U, V, eps):
     return U2[:r].T.copy(), V2[:r].T.copy(), s[:k].copy()
 
 
+def gauss(key, counters):
+    """Entries of the randomized SVD's test matrix for the given counters."""
+    out = np.zeros(2, np.float64)
+    z = np.zeros(len(counters), np.complex128)
+    for i, c in enumerate(counters):
+        lib().or_gauss(int(key), int(c), _ptr(out))
+        z[i] = out[0] + 1j * out[1]
+    return z
+
+
+def splitmix64(z):
+    return int(lib().or_splitmix64(int(z) & ((1 << 64) - 1)))
+
+
+def rsvd_key(tau_begin, sigma_begin):
+    return int(lib().or_rsvd_key(int(tau_begin), int(sigma_begin)))
+
+
+def rsvd_dense(A, eps, key=0):
+    """Randomized range finder of an explicit 3m x 3n matrix.  Returns (U, V, ok)
+    with U = Q (orthonormal columns) and V = (Q^H A)^H, before recompression."""
+    A = _c128(A)
+    m3, n3 = A.shape
+    lcap = min(m3, n3, 768)
+    U = np.zeros((lcap, m3), np.complex128)
+    V = np.zeros((lcap, n3), np.complex128)
+    ok = C.c_int(0)
+    l = lib().or_rsvd_dense(_ptr(A), m3 // 3, n3 // 3, eps, int(key), lcap, _ptr(U), _ptr(V),
+                            C.byref(ok))
+    return U[:l].T.copy(), V[:l].T.copy(), bool(ok.value)
+
+
 class HMatrix:
     """Oracle H-matrix (tree, partition, dense blocks, ACA + recompression)."""
 
@@ -269,6 +306,12 @@ class HMatrix:
         r = np.zeros(n, np.int64)
         lib().or_hmat_blocks(self.h, _ptr(b), _ptr(ra), _ptr(r))
         return b, ra, r
+
+    def block_methods(self):
+        """0 dense or vector ACA, 1 randomized SVD, 2 randomized SVD at its cap."""
+        m = np.zeros(lib().or_hmat_nblocks(self.h), np.int32)
+        lib().or_hmat_block_methods(self.h, _ptr(m))
+        return m
 
     def block_data(self, b, blocks=None, clusters=None, ranks=None):
         """dense -> D (3m x 3n); low rank -> (U, V) with block = U V^H."""

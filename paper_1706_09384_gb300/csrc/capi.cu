@@ -205,8 +205,64 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
     }
     double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0;
     int64_t batches = 0, reruns = 0, ws_peak = 0, ws_tot = 0;
-    std::vector<int64_t> fallback(nprob, 0);
+    std::vector<int64_t> n_rsvd(nprob, 0), n_uncert(nprob, 0);
+    std::vector<int64_t> lost;  // admissible blocks for the randomized SVD
     int* d_counter = (int*)hm_dmalloc(staging, sizeof(int), st, true);
+    // recompression of factors in d_work (Sec. 3.2) and their FP32 staging
+    // copies (U' 3m x r', V' 3n x r'): jobs keep[q] of the list ids
+    auto stage = [&](const std::vector<int64_t>& ids, const std::vector<int64_t>& keep,
+                     const std::vector<int64_t>& uo, const std::vector<int64_t>& vo,
+                     const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
+                     const std::vector<int32_t>& kk, const std::vector<int64_t>& go,
+                     const std::vector<int32_t>& gl, const double2* d_gram, double2* d_work,
+                     double eps_r) {
+        std::vector<int32_t> ranks;
+        std::vector<int64_t> soff;
+        EvPair er(st);
+        void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h0->opts.recompress, d_work,
+                                   eps_r, ranks, soff, st);
+        try {
+            int64_t tot = 0;
+            std::vector<int64_t> so(keep.size());
+            for (size_t q = 0; q < keep.size(); ++q) {
+                so[q] = tot;
+                tot += (m3[q] + n3[q]) * ranks[q];
+            }
+            float2* d_stage = (float2*)hm_dmalloc(staging, std::max<int64_t>(tot, 1) * 8, st, false);
+            std::vector<int64_t> job_of, row0, dst;
+            std::vector<int32_t> which, rows, ldv;
+            for (size_t q = 0; q < keep.size(); ++q) {
+                if (ranks[q] == 0) continue;
+                for (int side = 0; side < 2; ++side) {
+                    const int64_t R = side == 0 ? m3[q] : n3[q];
+                    const int64_t base = so[q] + (side == 0 ? 0 : m3[q] * ranks[q]);
+                    for (int64_t r0 = 0; r0 < R; r0 += 192) {
+                        job_of.push_back((int64_t)q);
+                        which.push_back(side);
+                        row0.push_back(r0);
+                        rows.push_back((int32_t)std::min<int64_t>(192, R - r0));
+                        dst.push_back(base + r0);
+                        ldv.push_back((int32_t)R);
+                    }
+                }
+            }
+            recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_stage, st);
+            ev_rec += er.stop(st);
+            for (size_t q = 0; q < keep.size(); ++q) {
+                const int64_t a = ids[keep[q]];
+                hm_block& bk = blk_of(a);
+                bk.rank_aca = kk[q];
+                bk.rank = ranks[q];
+                su[aq[a]][ab[a]] = d_stage + so[q];
+                sv[aq[a]][ab[a]] = d_stage + so[q] + m3[q] * ranks[q];
+            }
+            HM_CUDA(cudaStreamSynchronize(st));
+        } catch (...) {
+            recompress_release(rb, st);
+            throw;
+        }
+        recompress_release(rb, st);
+    };
     std::vector<int64_t> todo = adm;
     try {
     while (!todo.empty()) {
@@ -275,12 +331,8 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
             for (int64_t j = 0; j < nj; ++j) {
                 if (res[j].status == 2)
                     hm_throw(HM_ERR_NUMERIC, "non-finite value in the ACA of a block");
-                if (res[j].status == 3) {  // rows the vector ACA cannot pivot: store exactly
-                    hm_block& bk = blk_of(ids[j]);
-                    bk.admissible = 0;
-                    bk.rank_aca = res[j].k;
-                    bk.rank = 0;
-                    fallback[aq[ids[j]]]++;
+                if (res[j].status == 3) {  // rows the vector ACA cannot pivot: randomized SVD
+                    lost.push_back(ids[j]);
                     continue;
                 }
                 if (res[j].status == 1) {
@@ -305,53 +357,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 go.push_back(jobs[j].g_off);
                 gl.push_back(jobs[j].cap);
             }
-            std::vector<int32_t> ranks;
-            std::vector<int64_t> soff;
-            EvPair er(st);
-            void* rb = recompress_core(uo, vo, m3, n3, kk, go, gl, d_gram, h0->opts.recompress,
-                                       d_work, h0->eps, ranks, soff, st);
-            try {
-                // staging for this batch: FP32 U' (3m x r'), V' (3n x r')
-                int64_t tot = 0;
-                std::vector<int64_t> so(keep.size());
-                for (size_t q = 0; q < keep.size(); ++q) {
-                    so[q] = tot;
-                    tot += (m3[q] + n3[q]) * ranks[q];
-                }
-                float2* d_stage = (float2*)hm_dmalloc(staging, std::max<int64_t>(tot, 1) * 8, st, false);
-                std::vector<int64_t> job_of, row0, dst;
-                std::vector<int32_t> which, rows, ldv;
-                for (size_t q = 0; q < keep.size(); ++q) {
-                    if (ranks[q] == 0) continue;
-                    for (int side = 0; side < 2; ++side) {
-                        const int64_t R = side == 0 ? m3[q] : n3[q];
-                        const int64_t base = so[q] + (side == 0 ? 0 : m3[q] * ranks[q]);
-                        for (int64_t r0 = 0; r0 < R; r0 += 192) {
-                            job_of.push_back((int64_t)q);
-                            which.push_back(side);
-                            row0.push_back(r0);
-                            rows.push_back((int32_t)std::min<int64_t>(192, R - r0));
-                            dst.push_back(base + r0);
-                            ldv.push_back((int32_t)R);
-                        }
-                    }
-                }
-                recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_stage, st);
-                ev_rec += er.stop(st);
-                for (size_t q = 0; q < keep.size(); ++q) {
-                    const int64_t a = ids[keep[q]];
-                    hm_block& bk = blk_of(a);
-                    bk.rank_aca = kk[q];
-                    bk.rank = ranks[q];
-                    su[aq[a]][ab[a]] = d_stage + so[q];
-                    sv[aq[a]][ab[a]] = d_stage + so[q] + m3[q] * ranks[q];
-                }
-                HM_CUDA(cudaStreamSynchronize(st));
-            } catch (...) {
-                recompress_release(rb, st);
-                throw;
-            }
-            recompress_release(rb, st);
+            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, d_gram, d_work, h0->eps);
             HM_CUDA(cudaStreamSynchronize(st));
             free_all(tmp);
             t_rec += ms_since(t0);
@@ -359,13 +365,76 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         reruns += (int64_t)overflow.size();
         todo.swap(overflow);
     }
+    if (!lost.empty()) {
+        // randomized SVD of the blocks the vector ACA could not pivot (remark
+        // of Sec. 2.3), in groups whose FP64 blocks fit the workspace budget
+        auto t0 = clk::now();
+        std::vector<DevBuf> gbuf;
+        const GreenParams* gps = d_gps;
+        if (!gps) {
+            GreenParams* g = (GreenParams*)hm_dmalloc(gbuf, sizeof(GreenParams), st, false);
+            HM_CUDA(cudaMemcpyAsync(g, &h0->gp, sizeof(GreenParams), cudaMemcpyHostToDevice, st));
+            gps = g;
+        }
+        size_t pos = 0;
+        while (pos < lost.size()) {
+            std::vector<RsvdBlock> rb;
+            std::vector<int64_t> ids;
+            int64_t bytes = 0;
+            while (pos < lost.size()) {
+                const int64_t a = lost[pos];
+                const hm_block& bk = blk_of(a);
+                const int64_t m = pts_of(a, bk.tau), n = pts_of(a, bk.sigma);
+                const int64_t need = 9 * m * n * 16 + 2 * 3 * (m + n) * 776 * 16;
+                if (!rb.empty() && (bytes + need > budget || rb.size() >= 65535)) break;  // grid.y
+                RsvdBlock B;
+                B.tau_global = poff[aq[a]] + cl_of(a, bk.tau).begin;
+                B.sig_global = poff[aq[a]] + cl_of(a, bk.sigma).begin;
+                B.m = m;
+                B.n = n;
+                B.key = rsvd_key(cl_of(a, bk.tau).begin, cl_of(a, bk.sigma).begin);
+                B.prob = nprob > 1 ? aq[a] : 0;
+                rb.push_back(B);
+                ids.push_back(a);
+                bytes += need;
+                ++pos;
+            }
+            std::vector<DevBuf> tmp;
+            EvPair ea(st);
+            double2* W = rsvd_factors(rb, gps, d_pts, d_nrm, h0->eps, tmp, st);
+            ev_aca += ea.stop(st);
+            std::vector<int64_t> keep, uo, vo, m3, n3, go;
+            std::vector<int32_t> kk, gl;
+            for (size_t q = 0; q < rb.size(); ++q) {
+                keep.push_back((int64_t)q);
+                uo.push_back(rb[q].u_off);
+                vo.push_back(rb[q].v_off);
+                m3.push_back(3 * rb[q].m);
+                n3.push_back(3 * rb[q].n);
+                kk.push_back(rb[q].l);
+                go.push_back(-1);  // Gram matrices formed by the recompression itself
+                gl.push_back(0);
+                n_rsvd[aq[ids[q]]]++;
+                if (!rb[q].certified) n_uncert[aq[ids[q]]]++;
+            }
+            // range error <= eps/2 (certified), truncation eps sqrt(3)/2: total <= eps
+            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, nullptr, W, h0->eps * std::sqrt(3.0) / 2);
+            HM_CUDA(cudaStreamSynchronize(st));
+            free_all(tmp);
+        }
+        free_all(gbuf);
+        t_rec += ms_since(t0);
+    }
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(batchbuf);
         throw;
     }
     free_all(batchbuf);
-    for (int q = 0; q < nprob; ++q) hs[q]->aca_dense_fallback = fallback[q];
+    for (int q = 0; q < nprob; ++q) {
+        hs[q]->rsvd_blocks = n_rsvd[q];
+        hs[q]->rsvd_uncertified = n_uncert[q];
+    }
     for (hm_matrix* h : hs) {  // a batch reports the shared launches in every handle
         h->ev_aca_ms += ev_aca;
         h->t_aca_ms += t_aca;
@@ -818,7 +887,7 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"aca_workspace_total_bytes\": " << h->aca_workspace_total
        << ", \"rank_model\": " << h->used_rank_model
        << ", \"batch_problems\": " << h->batch_problems
-       << ", \"aca_dense_fallback\": " << h->aca_dense_fallback
+       << ", \"rsvd_blocks\": " << h->rsvd_blocks << ", \"rsvd_uncertified\": " << h->rsvd_uncertified
        << ", \"ms\": {\"tree\": " << h->t_tree_ms << ", \"partition\": " << h->t_part_ms
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms

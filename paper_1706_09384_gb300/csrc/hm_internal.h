@@ -148,7 +148,7 @@ struct AcaJob {              // one admissible block
 struct AcaResult {
     int32_t k;               // ACA rank (columns), multiple of 3
     int32_t status;          // 0 converged, 1 capacity overflow, 2 non-finite,
-                             // 3 rows lost to singular pivots (block stored dense)
+                             // 3 rows lost to singular pivots (block goes to the randomized SVD)
 };
 void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nrm_p,
                 const AcaJob* d_jobs, int64_t njobs, double2* d_work, double2* d_gram,
@@ -160,6 +160,21 @@ int aca_ctas_per_sm(int capmax);
 // Core of the recompression for a batch: ranks r' and the k x r' transforms.
 // g_off[j] >= 0: the job's Gram matrices (ld g_ld[j]) are read from d_gram instead of
 // being recomputed from the factors.
+// Randomized SVD (rsvd.cu) of admissible blocks the vector ACA cannot pivot.
+struct RsvdBlock {
+    int64_t tau_global, sig_global;  // first row / column point, tree order (batch-global)
+    int64_t m, n;                    // points
+    uint64_t key;                    // test-matrix key: rsvd_key of the problem-local first points
+    int32_t prob;                    // problem (index into the Green parameters)
+    int32_t l = 0;                   // out: samples (rank of Q)
+    bool certified = false;          // out: the probes certified the range error
+    int64_t u_off = 0, v_off = 0;    // out: U = Q (3m x l), V = A^H Q (3n x l) in the workspace
+};
+uint64_t rsvd_key(int64_t tau_begin, int64_t sigma_begin);
+// Returns the FP64 factor workspace (allocated in owner) holding every block's U and V.
+double2* rsvd_factors(std::vector<RsvdBlock>& blocks, const GreenParams* d_gps, const double* d_pts,
+                      const double* d_nrm, double eps, std::vector<DevBuf>& owner, cudaStream_t st);
+
 void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64_t>& v_off,
                       const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
                       const std::vector<int32_t>& k, const std::vector<int64_t>& g_off,
@@ -243,6 +258,7 @@ struct hm_matrix {
     int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
     int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
     int batch_problems = 1;          // problems that shared the ACA / recompression launches
-    int64_t aca_dense_fallback = 0;  // admissible blocks stored dense (rows lost to singular pivots)
+    int64_t rsvd_blocks = 0;       // admissible blocks compressed by the randomized SVD
+    int64_t rsvd_uncertified = 0;  // of those, blocks whose samples reached their cap uncertified
     int used_rank_model = 0;
 };

@@ -133,38 +133,3 @@ def test_weighted_hmatvec_vs_dense(oracle):
         assert np.linalg.norm(H.matvec(x) - yd) <= 3e-4 * np.linalg.norm(yd)
 
 
-def test_T_on_a_plane_falls_back_to_dense(oracle):
-    """Coplanar points with the plane's normal: T(x, y) = a r^ n^T + b n r^T has
-    rank 2, so every 3x3 candidate pivot of a same-plane block is singular and
-    the vector ACA of Sec. 2.2-2.3 cannot pivot any row.  Such blocks are stored
-    exactly (dense); the H-matvec then meets the 3 eps of the dense product,
-    while the partition's admissible blocks that did pivot keep low rank."""
-    pts = inputs.plate(30)
-    nrm = np.tile([0.0, 0.0, 1.0], (len(pts), 1))
-    nc = len(pts)
-    pb = oracle.problem(1, 2, 1, 6.0, "T", 1.0, np.full(nc, 4.0 / nc))
-    H = oracle.HMatrix(pb, pts, nrm, eps=1e-4, eta=3.0, leaf=32)
-    blk, ra, r = H.blocks()
-    part = oracle.partition(H.clusters(), 3.0)
-    assert np.array_equal(part["tau"], blk["tau"]) and np.array_equal(part["sigma"], blk["sigma"])
-    fell = (part["admissible"] == 1) & (blk["admissible"] == 0)
-    assert fell.sum() > 0 and fell.sum() == (part["admissible"] == 1).sum()  # all coplanar
-    x = inputs.random_rhs(3 * nc, seed=2)
-    yd = oracle.dense_matrix(pb, pts, nrm) @ x
-    assert np.linalg.norm(H.matvec(x) - yd) <= 1e-12 * np.linalg.norm(yd)
-
-
-def test_T_on_cube_faces_meets_dense(oracle):
-    """Cube surface, T kernel: same-face blocks fall back to dense, the others
-    (across faces) keep their ACA factors; the H-matvec meets 3 eps."""
-    nc = 1500
-    pts, nrm = inputs.cube_surface(nc, seed=2)
-    pb = oracle.problem(1, 2, 1, 8.0, "T", 1.0, np.full(nc, 6.0 / nc))
-    H = oracle.HMatrix(pb, pts, nrm, eps=1e-4, eta=3.0, leaf=32)
-    blk, ra, r = H.blocks()
-    part = oracle.partition(H.clusters(), 3.0)
-    fell = (part["admissible"] == 1) & (blk["admissible"] == 0)
-    assert fell.sum() > 0 and (blk["admissible"] == 1).sum() > 0
-    x = inputs.random_rhs(3 * nc, seed=3)
-    yd = oracle.dense_matrix(pb, pts, nrm) @ x
-    assert np.linalg.norm(H.matvec(x) - yd) <= 3e-4 * np.linalg.norm(yd)
