@@ -260,5 +260,6 @@ struct hm_matrix {
     int batch_problems = 1;          // problems that shared the ACA / recompression launches
     int64_t rsvd_blocks = 0;       // admissible blocks compressed by the randomized SVD
     int64_t rsvd_uncertified = 0;  // of those, blocks whose samples reached their cap uncertified
+    double t_rsvd_ms = 0;          // wall time of the randomized SVD pass (with its recompression)
     int used_rank_model = 0;
 };
