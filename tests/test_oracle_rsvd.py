@@ -150,3 +150,20 @@ def test_T_on_cube_faces_mixes_aca_and_rsvd(oracle):
     x = inputs.random_rhs(3 * nc, seed=3)
     yd = oracle.dense_matrix(pb, pts, nrm) @ x
     assert np.linalg.norm(H.matvec(x) - yd) <= 3 * EPS * np.linalg.norm(yd)
+
+
+def test_acceptance_threshold_is_a_quarter_eps(oracle):
+    """A spectrum 0.914^i: a Gaussian sketch of 128 columns leaves a range error
+    of about 5e-5 ||A||_F (numpy QR of the sketch, several draws: 4.8e-5 to
+    5.1e-5), between eps/4 and eps, so the probes must reject l = 128
+    (threshold (eps/4)^2 on the mean probe residual) and accept l = 256."""
+    rng = np.random.default_rng(21)
+    n = 330
+    rho = 0.914
+    Qa, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    Qb, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    s = rho ** np.arange(n)
+    A = (Qa * s) @ Qb.conj().T
+    U, V, ok = oracle.rsvd_dense(A, EPS, key=4)
+    assert ok and U.shape[1] == 256
+    assert np.linalg.norm(A - U @ V.conj().T) <= EPS / 2 * np.linalg.norm(A)
