@@ -324,8 +324,9 @@ def run_gpu(args, wl, world, rank, local):
                 "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (no measured FP64 peak)",
                 "unit": "TFLOP/s", "frac": aca_tf / FP64_PEAK_TFLOPS, "traffic": None,
                 "alg_flops_per_launch": statistics.mean(aca_fl), "ms_per_step": aca_t,
-                "note": "ACA device time per build (all batches), FP64 flops of the residual "
-                        "rows/columns and Gram updates"}
+                "note": "ACA device time per build (all batches); algorithmic flops of the residual "
+                        "rows/columns (run in double-float on the FP32 pipes, ~44 bits) and of the "
+                        "FP64 Gram and norm updates, against the nominal FP64 peak"}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.empty(3 * wl["nc"], dtype=torch.complex128).pin_memory()
     xh.copy_(x.cpu())

@@ -239,6 +239,43 @@ HM_D void warp_sum_many(double (&x)[N]) {
     }
 }
 
+// ---- double-float residuals (FP32 pairs, ~44 significant bits) ----
+// The residual rows and columns of steps 1 and 3 subtract sum_p U(i, p)
+// conj(V(j, p)) from the Green's tensors: k complex multiply-adds per entry,
+// the bulk of the ACA's arithmetic.  On GB300 FP64 runs at 1/64 of the FP32
+// rate, so these sums run in double-float arithmetic (Dekker's product with an
+// FMA, Knuth's two-sum; every operation an explicitly rounded intrinsic so
+// nothing is fused) over double-float copies of U and V, and the difference
+// with the FP64 tensor is taken in FP64.  The pivots, the norm updates of
+// step 6, the Gram matrices and the factors themselves stay FP64.
+__device__ __forceinline__ void dfm(float& h, float& l, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(h, p);
+    const float bp = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+// s += u conj(v) for double-float complex u, v = (re_h, im_h, re_l, im_l)
+__device__ __forceinline__ void df_cmac_conj(float (&s)[4], float4 u, float4 v) {
+    dfm(s[0], s[1], u.x, u.z, v.x, v.z);    // re += ur vr
+    dfm(s[0], s[1], u.y, u.w, v.y, v.w);    // re += ui vi
+    dfm(s[2], s[3], u.y, u.w, v.x, v.z);    // im += ui vr
+    dfm(s[2], s[3], -u.x, -u.z, v.y, v.w);  // im -= ur vi
+}
+__device__ __forceinline__ float4 df_of(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+}
+// g -= s (the double-float sum, rounded to FP64 once)
+__device__ __forceinline__ void sub_df(double2& g, const float (&s)[4]) {
+    g.x -= (double)s[0] + (double)s[1];
+    g.y -= (double)s[2] + (double)s[3];
+}
+
 template <int N>
 HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
     warp_sum_many<N>(x);
@@ -256,7 +293,8 @@ HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
     }
 }
 
-__global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
+template <bool DF>
+__global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                                                  const GreenParams* __restrict__ gps,
                                                  const double* __restrict__ pts,
                                                  const double* __restrict__ nrm,
@@ -265,10 +303,14 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                                                  unsigned char* flags, int64_t flag_stride,
                                                  double2* rowbuf, double2* colbuf,
                                                  int64_t rb_stride, int64_t cb_stride,
-                                                 int capmax, double eps, AcaResult* res) {
+                                                 int capmax, double eps, AcaResult* res,
+                                                 float4* work_df) {
     extern __shared__ double2 smem[];
     double2* Urow = smem;             // 3 x capmax: U(3 i^ + a, p)
     double2* Vrow = smem + 3 * capmax;  // 3 x capmax: V(3 j^ + c, p)
+    // DF: the same rows as double-float pairs (same 16 bytes per entry)
+    float4* Urow_df = reinterpret_cast<float4*>(smem);
+    float4* Vrow_df = reinterpret_cast<float4*>(smem + 3 * capmax);
     __shared__ BlockRed red;
     __shared__ double sums[36][AW];
     __shared__ int64_t s_job, s_ihat, s_jhat, s_inext;
@@ -297,6 +339,8 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
         const int64_t m = J.m, n = J.n, m3 = 3 * m, n3 = 3 * n;
         double2* U = work + J.u_off;
         double2* V = work + J.v_off;
+        float4* Ud = DF ? work_df + J.u_off : nullptr;  // double-float copies of U and V
+        float4* Vd = DF ? work_df + J.v_off : nullptr;
         double2* GU = (gram && J.g_off >= 0) ? gram + J.g_off : nullptr;  // U^H U, ld cap
         double2* GV = GU ? GU + (int64_t)J.cap * J.cap : nullptr;          // V^H V, ld cap
         unsigned char* urow = used;
@@ -323,7 +367,10 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
             const int64_t ihat = s_ihat;
             for (int t = tid; t < 3 * k; t += AT) {
                 const int a = t / k, p = t - a * k;
-                Urow[a * capmax + p] = U[3 * ihat + a + (int64_t)p * m3];
+                if (DF)
+                    Urow_df[a * capmax + p] = Ud[3 * ihat + a + (int64_t)p * m3];
+                else
+                    Urow[a * capmax + p] = U[3 * ihat + a + (int64_t)p * m3];
             }
             __syncthreads();
             // ---- step 1-2: row residual and sigma_3 pivot search ----
@@ -338,15 +385,32 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                     green_tensor(gp, xr + 3 * ihat, xc + 3 * j, nc ? nc + 3 * j : nullptr, G);
                     apply_weight(gp, J.sig_begin + j, G);
                 }
-                for (int p = 0; p < k; ++p) {
-                    const double2* vp = V + (int64_t)p * n3 + 3 * j;
-                    const double2 v0 = vp[0], v1 = vp[1], v2 = vp[2];
+                if (DF && k > 0) {
+                    float s9[9][4] = {};
+                    for (int p = 0; p < k; ++p) {
+                        const float4* vp = Vd + (int64_t)p * n3 + 3 * j;
+                        const float4 v0 = vp[0], v1 = vp[1], v2 = vp[2];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const double2 u = Urow[a * capmax + p];
-                        cfms_conj(G[3 * a + 0], u, v0);
-                        cfms_conj(G[3 * a + 1], u, v1);
-                        cfms_conj(G[3 * a + 2], u, v2);
+                        for (int a = 0; a < 3; ++a) {
+                            const float4 u = Urow_df[a * capmax + p];
+                            df_cmac_conj(s9[3 * a + 0], u, v0);
+                            df_cmac_conj(s9[3 * a + 1], u, v1);
+                            df_cmac_conj(s9[3 * a + 2], u, v2);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
+                } else if (!DF) {
+                    for (int p = 0; p < k; ++p) {
+                        const double2* vp = V + (int64_t)p * n3 + 3 * j;
+                        const double2 v0 = vp[0], v1 = vp[1], v2 = vp[2];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const double2 u = Urow[a * capmax + p];
+                            cfms_conj(G[3 * a + 0], u, v0);
+                            cfms_conj(G[3 * a + 1], u, v1);
+                            cfms_conj(G[3 * a + 2], u, v2);
+                        }
                     }
                 }
 #pragma unroll
@@ -443,7 +507,10 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
             }
             for (int t = tid; t < 3 * k; t += AT) {
                 const int c = t / k, p = t - c * k;
-                Vrow[c * capmax + p] = V[3 * jhat + c + (int64_t)p * n3];
+                if (DF)
+                    Vrow_df[c * capmax + p] = Vd[3 * jhat + c + (int64_t)p * n3];
+                else
+                    Vrow[c * capmax + p] = V[3 * jhat + c + (int64_t)p * n3];
             }
             __syncthreads();
             // ---- step 3-4: column residual and next row ----
@@ -458,15 +525,32 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                     green_tensor(gp, xr + 3 * i, xc + 3 * jhat, nc ? nc + 3 * jhat : nullptr, G);
                     apply_weight(gp, J.sig_begin + jhat, G);
                 }
-                for (int p = 0; p < k; ++p) {
-                    const double2* up = U + (int64_t)p * m3 + 3 * i;
-                    const double2 u0 = up[0], u1 = up[1], u2 = up[2];
+                if (DF && k > 0) {
+                    float s9[9][4] = {};
+                    for (int p = 0; p < k; ++p) {
+                        const float4* up = Ud + (int64_t)p * m3 + 3 * i;
+                        const float4 u0 = up[0], u1 = up[1], u2 = up[2];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const double2 v = Vrow[c * capmax + p];
-                        cfms_conj(G[0 + c], u0, v);
-                        cfms_conj(G[3 + c], u1, v);
-                        cfms_conj(G[6 + c], u2, v);
+                        for (int c = 0; c < 3; ++c) {
+                            const float4 v = Vrow_df[c * capmax + p];
+                            df_cmac_conj(s9[0 + c], u0, v);
+                            df_cmac_conj(s9[3 + c], u1, v);
+                            df_cmac_conj(s9[6 + c], u2, v);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
+                } else if (!DF) {
+                    for (int p = 0; p < k; ++p) {
+                        const double2* up = U + (int64_t)p * m3 + 3 * i;
+                        const double2 u0 = up[0], u1 = up[1], u2 = up[2];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const double2 v = Vrow[c * capmax + p];
+                            cfms_conj(G[0 + c], u0, v);
+                            cfms_conj(G[3 + c], u1, v);
+                            cfms_conj(G[6 + c], u2, v);
+                        }
                     }
                 }
 #pragma unroll
@@ -517,6 +601,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                         for (int a = 0; a < 3; ++a) cfma(acc, C[3 * r + a], s_gam[3 * a + q]);
                         un[q] = acc;
                         U[r + (int64_t)(k + q) * m3] = acc;
+                        if (DF) Ud[r + (int64_t)(k + q) * m3] = df_of(acc);
                     }
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
@@ -534,6 +619,7 @@ __global__ void __launch_bounds__(AT) aca_kernel(GreenParams gp0,
                     for (int a = 0; a < 3; ++a) {
                         vn[a] = cconj(R[a * n3 + c]);
                         V[c + (int64_t)(k + a) * n3] = vn[a];
+                        if (DF) Vd[c + (int64_t)(k + a) * n3] = df_of(vn[a]);
                     }
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
@@ -657,25 +743,35 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                 unsigned char* d_flags,
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
-                int* d_counter, cudaStream_t st, const GreenParams* d_gps) {
+                int* d_counter, cudaStream_t st, const GreenParams* d_gps, float4* d_work_df) {
     if (njobs == 0) return;
     const size_t smem = (size_t)6 * capmax * sizeof(double2);
-    HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
     HM_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
-    aca_kernel<<<nctas, AT, smem, st>>>(gp, d_gps, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter, d_work,
-                                        d_gram, d_flags, flag_stride, d_rowbuf, d_colbuf, rowbuf_stride,
-                                        colbuf_stride, capmax, eps, d_res);
-                                        HM_LAUNCHED();
+    if (d_work_df) {
+        HM_CUDA(cudaFuncSetAttribute(aca_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        aca_kernel<true><<<nctas, AT, smem, st>>>(gp, d_gps, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter,
+                                                  d_work, d_gram, d_flags, flag_stride, d_rowbuf, d_colbuf,
+                                                  rowbuf_stride, colbuf_stride, capmax, eps, d_res,
+                                                  d_work_df);
+    } else {
+        HM_CUDA(cudaFuncSetAttribute(aca_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        aca_kernel<false><<<nctas, AT, smem, st>>>(gp, d_gps, d_pts_p, d_nrm_p, d_jobs, njobs, d_counter,
+                                                   d_work, d_gram, d_flags, flag_stride, d_rowbuf,
+                                                   d_colbuf, rowbuf_stride, colbuf_stride, capmax, eps,
+                                                   d_res, nullptr);
+    }
+    HM_LAUNCHED();
     HM_CUDA(cudaGetLastError());
 }
 
 int aca_ctas_per_sm(int capmax) {
     int nb = 0;
     const size_t smem = (size_t)6 * capmax * sizeof(double2);
-    HM_CUDA(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HM_CUDA(cudaFuncSetAttribute(aca_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aca_kernel, AT, smem));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aca_kernel<true>, AT, smem));
     return nb > 0 ? nb : 1;
 }
 

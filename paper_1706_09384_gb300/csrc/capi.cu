@@ -279,8 +279,9 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 const int64_t a = todo[pos];
                 const hm_block& bk = blk_of(a);
                 const int64_t m = pts_of(a, bk.tau), n = pts_of(a, bk.sigma);
-                const int64_t need = (3 * (m + n) * (int64_t)cap[a] + 2 * (int64_t)cap[a] * cap[a]) * 16;
-                if (!jobs.empty() && (woff + goff) * 16 + need > budget) break;
+                // FP64 factors, their double-float copies, Gram matrices
+                const int64_t need = (6 * (m + n) * (int64_t)cap[a] + 2 * (int64_t)cap[a] * cap[a]) * 16;
+                if (!jobs.empty() && (2 * woff + goff) * 16 + need > budget) break;
                 AcaJob J;
                 J.tau_begin = poff[aq[a]] + cl_of(a, bk.tau).begin;
                 J.m = m;
@@ -301,12 +302,13 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 ++pos;
             }
             const int64_t nj = (int64_t)jobs.size();
-            ws_peak = std::max<int64_t>(ws_peak, (woff + goff) * 16);
-            ws_tot += (woff + goff) * 16;
+            ws_peak = std::max<int64_t>(ws_peak, (2 * woff + goff) * 16);
+            ws_tot += (2 * woff + goff) * 16;
             const int nctas = (int)std::min<int64_t>(nj, (int64_t)nsm * aca_ctas_per_sm(capmax));
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
             double2* d_work = (double2*)hm_dmalloc(tmp, (size_t)woff * 16, st, false);
+            float4* d_work_df = (float4*)hm_dmalloc(tmp, (size_t)woff * 16, st, false);
             double2* d_gram = (double2*)hm_dmalloc(tmp, (size_t)goff * 16, st, false);
             AcaJob* d_jobs = (AcaJob*)hm_dmalloc(tmp, nj * sizeof(AcaJob), st, false);
             AcaResult* d_res = (AcaResult*)hm_dmalloc(tmp, nj * sizeof(AcaResult), st, false);
@@ -318,7 +320,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
             HM_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nj * sizeof(AcaJob), cudaMemcpyHostToDevice, st));
             EvPair ea(st);
             launch_aca(h0->gp, d_pts, d_nrm, d_jobs, nj, d_work, d_gram, d_flags, fstride, d_rb,
-                       d_cb, rbs, cbs, h0->eps, d_res, nctas, capmax, d_counter, st, d_gps);
+                       d_cb, rbs, cbs, h0->eps, d_res, nctas, capmax, d_counter, st, d_gps, d_work_df);
             ev_aca += ea.stop(st);
             std::vector<AcaResult> res(nj);
             HM_CUDA(cudaMemcpyAsync(res.data(), d_res, nj * sizeof(AcaResult), cudaMemcpyDeviceToHost, st));
