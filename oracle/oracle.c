@@ -1373,3 +1373,442 @@ int or_gmres_dense(const double* A, int64_t n, const double* b, double* x, int r
     dense_ctx d = {(const cplx*)A, n};
     return gmres(apply_dense, &d, n, (const cplx*)b, (cplx*)x, restart, tol, maxit, iters, relres);
 }
+
+/* ======================================================================
+ * H-LU factorisation and direct solver (Sec. 3.2, "H-LU factorization and
+ * direct solver").  The H-matrix is copied into its block tree (the recursion
+ * of the partition: a node is a dense block, a low-rank block U V^H, or the
+ * 2 x 2 block matrix of its children) and factorised recursively on 2 x 2
+ * block matrices in the four steps of Sec. 3.2:
+ *   1. A11 = L11 U11 (recursion; a dense diagonal leaf is factorised in place);
+ *   2. U12 = L11^{-1} A12;
+ *   3. L21 = A21 U11^{-1};
+ *   4. A22 <- A22 - L21 U12, then A22 = L22 U22 (recursion).
+ * The update of step 4 (A''' = A + A' A'', the "27 cases") is formed in the
+ * format of the target block: into a dense target as a dense update, into a
+ * subdivided target child by child, into a low-rank target as a low-rank
+ * update [U, -U_p] [V, V_p]^H recompressed (Sec. 3.2: QR of both factors, SVD
+ * of R_U R_V^H) with eps_LU; a product with a low-rank factor stays factored
+ * (A U_b) V_b^H or U_a (B^H V_a)^H, the product of two dense or subdivided
+ * blocks is formed densely.  L (unit lower) and U share the tree in place.
+ * Readings (the paper leaves them open): no pivoting; a dense update of a
+ * low-rank target enters as [U, -P] [V, I]^H before the recompression.
+ * ====================================================================== */
+typedef struct hnode {
+    int type;              /* 0 dense, 1 low rank, 2 subdivided */
+    int64_t m, n;          /* rows, columns (DOFs) */
+    cplx* D;               /* dense: m x n col-major */
+    cplx *U, *V;           /* low rank: U (m x k), V (n x k); block = U V^H */
+    int64_t k;
+    struct hnode* ch[4];   /* (t0 s0), (t0 s1), (t1 s0), (t1 s1) */
+    int64_t m0, n0;        /* rows of t0, columns of s0 (subdivided) */
+} hnode;
+
+struct or_hlu {
+    int64_t nc;
+    int64_t* perm;
+    hnode* root;
+    double eps;
+    double seconds;
+};
+
+static hnode* hn_build(const or_hmat* h, int64_t t, int64_t s, int64_t* bi, double eta)
+{
+    const or_cluster* cl = h->cl;
+    hnode* x = (hnode*)calloc(1, sizeof(hnode));
+    x->m = 3 * (cl[t].end - cl[t].begin);
+    x->n = 3 * (cl[s].end - cl[s].begin);
+    const int adm = or_admissible_box(cl[t].lo, cl[t].hi, cl[s].lo, cl[s].hi, eta);
+    if (adm || cl[t].is_leaf || cl[s].is_leaf) { /* a leaf of the partition: the next block */
+        const int64_t b = (*bi)++;
+        if (b >= h->nb || h->blk[b].tau != t || h->blk[b].sigma != s) { /* not the partition's order */
+            x->type = 0;
+            x->D = (cplx*)calloc((size_t)(x->m * x->n + 1), sizeof(cplx));
+            *bi = h->nb + 1;
+            return x;
+        }
+        if (h->blk[b].admissible) {
+            x->type = 1;
+            x->k = h->rank[b];
+            x->U = (cplx*)malloc((size_t)(x->m * x->k + 1) * sizeof(cplx));
+            x->V = (cplx*)malloc((size_t)(x->n * x->k + 1) * sizeof(cplx));
+            memcpy(x->U, h->D[b], (size_t)(x->m * x->k) * sizeof(cplx));
+            memcpy(x->V, h->V[b], (size_t)(x->n * x->k) * sizeof(cplx));
+        } else {
+            x->type = 0;
+            x->D = (cplx*)malloc((size_t)(x->m * x->n) * sizeof(cplx));
+            memcpy(x->D, h->D[b], (size_t)(x->m * x->n) * sizeof(cplx));
+        }
+        return x;
+    }
+    x->type = 2;
+    const int64_t tc[2] = {cl[t].child0, cl[t].child1};
+    const int64_t sc[2] = {cl[s].child0, cl[s].child1};
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) x->ch[2 * u + v] = hn_build(h, tc[u], sc[v], bi, eta);
+    x->m0 = x->ch[0]->m;
+    x->n0 = x->ch[0]->n;
+    return x;
+}
+
+static void hn_free(hnode* x)
+{
+    if (!x) return;
+    for (int q = 0; q < 4; ++q) hn_free(x->ch[q]);
+    free(x->D);
+    free(x->U);
+    free(x->V);
+    free(x);
+}
+
+/* Y (m x c, ld ldy) += alpha * op(x) X (X: n x c or m x c for the adjoint), op = x or x^H */
+static void hn_apply(const hnode* x, int adj, const cplx* X, int64_t ldx, cplx* Y, int64_t ldy,
+                     int64_t c, cplx alpha)
+{
+    const int64_t rows = adj ? x->n : x->m, cols = adj ? x->m : x->n;
+    if (x->type == 0) {
+        for (int64_t j = 0; j < c; ++j)
+            for (int64_t q = 0; q < cols; ++q) {
+                const cplx xv = alpha * X[q + j * ldx];
+                if (xv == 0.0) continue;
+                for (int64_t r = 0; r < rows; ++r)
+                    Y[r + j * ldy] += (adj ? conj(x->D[q + r * x->m]) : x->D[r + q * x->m]) * xv;
+            }
+        return;
+    }
+    if (x->type == 1) { /* U V^H X, or V U^H X */
+        const cplx* A = adj ? x->U : x->V; /* contracted with X */
+        const cplx* B = adj ? x->V : x->U; /* spans the result */
+        const int64_t la = adj ? x->m : x->n, lb = adj ? x->n : x->m;
+        for (int64_t j = 0; j < c; ++j)
+            for (int64_t l = 0; l < x->k; ++l) {
+                cplx t = 0.0;
+                for (int64_t q = 0; q < la; ++q) t += conj(A[q + l * la]) * X[q + j * ldx];
+                t *= alpha;
+                for (int64_t r = 0; r < lb; ++r) Y[r + j * ldy] += B[r + l * lb] * t;
+            }
+        return;
+    }
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+            const hnode* y = x->ch[2 * u + v];
+            const int64_t ro = u ? x->m0 : 0, co = v ? x->n0 : 0;
+            if (!adj)
+                hn_apply(y, 0, X + co, ldx, Y + ro, ldy, c, alpha);
+            else
+                hn_apply(y, 1, X + ro, ldx, Y + co, ldy, c, alpha);
+        }
+}
+
+/* B (m x c) <- L^{-1} B, L the unit lower factor of the diagonal node x */
+static void hn_solve_l(const hnode* x, cplx* B, int64_t ldb, int64_t c)
+{
+    if (x->type == 0) {
+        for (int64_t j = 0; j < c; ++j)
+            for (int64_t r = 0; r < x->m; ++r) {
+                cplx acc = B[r + j * ldb];
+                for (int64_t q = 0; q < r; ++q) acc -= x->D[r + q * x->m] * B[q + j * ldb];
+                B[r + j * ldb] = acc;
+            }
+        return;
+    }
+    hn_solve_l(x->ch[0], B, ldb, c);
+    hn_apply(x->ch[2], 0, B, ldb, B + x->m0, ldb, c, -1.0);
+    hn_solve_l(x->ch[3], B + x->m0, ldb, c);
+}
+
+/* B (m x c) <- U^{-1} B, U the upper factor of the diagonal node x */
+static void hn_solve_u(const hnode* x, cplx* B, int64_t ldb, int64_t c)
+{
+    if (x->type == 0) {
+        for (int64_t j = 0; j < c; ++j)
+            for (int64_t r = x->m - 1; r >= 0; --r) {
+                cplx acc = B[r + j * ldb];
+                for (int64_t q = r + 1; q < x->m; ++q) acc -= x->D[r + q * x->m] * B[q + j * ldb];
+                B[r + j * ldb] = acc / x->D[r + r * x->m];
+            }
+        return;
+    }
+    hn_solve_u(x->ch[3], B + x->m0, ldb, c);
+    hn_apply(x->ch[1], 0, B + x->m0, ldb, B, ldb, c, -1.0);
+    hn_solve_u(x->ch[0], B, ldb, c);
+}
+
+/* B (n x c) <- U^{-H} B (solves U^H Y = B: forward substitution with U^H) */
+static void hn_solve_uh(const hnode* x, cplx* B, int64_t ldb, int64_t c)
+{
+    if (x->type == 0) {
+        for (int64_t j = 0; j < c; ++j)
+            for (int64_t r = 0; r < x->m; ++r) {
+                cplx acc = B[r + j * ldb];
+                for (int64_t q = 0; q < r; ++q) acc -= conj(x->D[q + r * x->m]) * B[q + j * ldb];
+                B[r + j * ldb] = acc / conj(x->D[r + r * x->m]);
+            }
+        return;
+    }
+    hn_solve_uh(x->ch[0], B, ldb, c);
+    hn_apply(x->ch[1], 1, B, ldb, B + x->n0, ldb, c, -1.0);
+    hn_solve_uh(x->ch[3], B + x->n0, ldb, c);
+}
+
+/* x += alpha Up Vp^H (Up: m x k, Vp: n x k, leading dimensions lu, lv) */
+static void hn_add_lr(hnode* x, const cplx* Up, int64_t lu, const cplx* Vp, int64_t lv, int64_t k,
+                      cplx alpha, double eps)
+{
+    if (k == 0) return;
+    if (x->type == 0) {
+        for (int64_t l = 0; l < k; ++l)
+            for (int64_t j = 0; j < x->n; ++j) {
+                const cplx v = alpha * conj(Vp[j + l * lv]);
+                for (int64_t i = 0; i < x->m; ++i) x->D[i + j * x->m] += Up[i + l * lu] * v;
+            }
+        return;
+    }
+    if (x->type == 2) {
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v)
+                hn_add_lr(x->ch[2 * u + v], Up + (u ? x->m0 : 0), lu, Vp + (v ? x->n0 : 0), lv, k,
+                          alpha, eps);
+        return;
+    }
+    /* low-rank target: [U, alpha Up] [V, Vp]^H, recompressed with eps_LU */
+    int64_t K = x->k + k;
+    cplx* U2 = (cplx*)malloc((size_t)(x->m * K + 1) * sizeof(cplx));
+    cplx* V2 = (cplx*)malloc((size_t)(x->n * K + 1) * sizeof(cplx));
+    memcpy(U2, x->U, (size_t)(x->m * x->k) * sizeof(cplx));
+    memcpy(V2, x->V, (size_t)(x->n * x->k) * sizeof(cplx));
+    for (int64_t l = 0; l < k; ++l) {
+        for (int64_t i = 0; i < x->m; ++i) U2[i + (x->k + l) * x->m] = alpha * Up[i + l * lu];
+        for (int64_t j = 0; j < x->n; ++j) V2[j + (x->k + l) * x->n] = Vp[j + l * lv];
+    }
+    if (K > x->m || K > x->n) {
+        /* more columns than the block's smaller side: the sum densely, then
+         * factored as D I^H (or I D^H) with min(m, n) columns */
+        cplx* Dn = (cplx*)calloc((size_t)(x->m * x->n + 1), sizeof(cplx));
+        for (int64_t l = 0; l < K; ++l)
+            for (int64_t j = 0; j < x->n; ++j) {
+                const cplx v = conj(V2[j + l * x->n]);
+                for (int64_t i = 0; i < x->m; ++i) Dn[i + j * x->m] += U2[i + l * x->m] * v;
+            }
+        free(U2);
+        free(V2);
+        if (x->m >= x->n) {
+            K = x->n;
+            U2 = Dn;
+            V2 = (cplx*)calloc((size_t)(x->n * x->n + 1), sizeof(cplx));
+            for (int64_t j = 0; j < x->n; ++j) V2[j + j * x->n] = 1.0;
+        } else {
+            K = x->m;
+            U2 = (cplx*)calloc((size_t)(x->m * x->m + 1), sizeof(cplx));
+            for (int64_t i = 0; i < x->m; ++i) U2[i + i * x->m] = 1.0;
+            V2 = (cplx*)malloc((size_t)(x->n * x->m + 1) * sizeof(cplx));
+            for (int64_t i = 0; i < x->m; ++i)
+                for (int64_t j = 0; j < x->n; ++j) V2[j + i * x->n] = conj(Dn[i + j * x->m]);
+            free(Dn);
+        }
+    }
+    free(x->U);
+    free(x->V);
+    cplx *U3, *V3;
+    x->k = recompress(U2, V2, x->m, x->n, K, eps, &U3, &V3, NULL);
+    free(U2);
+    free(V2);
+    x->U = U3 ? U3 : (cplx*)calloc(1, sizeof(cplx));
+    x->V = V3 ? V3 : (cplx*)calloc(1, sizeof(cplx));
+}
+
+/* x += alpha P (P: m x n dense, leading dimension lp) */
+static void hn_add_dense(hnode* x, const cplx* P, int64_t lp, cplx alpha, double eps)
+{
+    if (x->type == 0) {
+        for (int64_t j = 0; j < x->n; ++j)
+            for (int64_t i = 0; i < x->m; ++i) x->D[i + j * x->m] += alpha * P[i + j * lp];
+        return;
+    }
+    if (x->type == 2) {
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v)
+                hn_add_dense(x->ch[2 * u + v], P + (u ? x->m0 : 0) + (v ? x->n0 : 0) * lp, lp, alpha, eps);
+        return;
+    }
+    /* low-rank target: alpha P = (alpha P) I^H */
+    cplx* Id = (cplx*)calloc((size_t)(x->n * x->n + 1), sizeof(cplx));
+    for (int64_t j = 0; j < x->n; ++j) Id[j + j * x->n] = 1.0;
+    hn_add_lr(x, P, lp, Id, x->n, x->n, alpha, eps);
+    free(Id);
+}
+
+/* C -= A B  (A: m x l, B: l x n nodes) */
+static void hn_gemm_sub(hnode* C, const hnode* A, const hnode* B, double eps)
+{
+    if (C->type == 2 && A->type == 2 && B->type == 2) {
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v)
+                for (int w = 0; w < 2; ++w)
+                    hn_gemm_sub(C->ch[2 * u + v], A->ch[2 * u + w], B->ch[2 * w + v], eps);
+        return;
+    }
+    if (B->type == 1) { /* A (U_b V_b^H) = (A U_b) V_b^H */
+        cplx* AU = (cplx*)calloc((size_t)(A->m * B->k + 1), sizeof(cplx));
+        hn_apply(A, 0, B->U, B->m, AU, A->m, B->k, 1.0);
+        hn_add_lr(C, AU, A->m, B->V, B->n, B->k, -1.0, eps);
+        free(AU);
+        return;
+    }
+    if (A->type == 1) { /* (U_a V_a^H) B = U_a (B^H V_a)^H */
+        cplx* BV = (cplx*)calloc((size_t)(B->n * A->k + 1), sizeof(cplx));
+        hn_apply(B, 1, A->V, A->n, BV, B->n, A->k, 1.0);
+        hn_add_lr(C, A->U, A->m, BV, B->n, A->k, -1.0, eps);
+        free(BV);
+        return;
+    }
+    /* dense or subdivided operands: the product densely, P = A B */
+    cplx* Bd = (cplx*)calloc((size_t)(B->m * B->n + 1), sizeof(cplx));
+    cplx* Id = (cplx*)calloc((size_t)(B->n * B->n + 1), sizeof(cplx));
+    for (int64_t j = 0; j < B->n; ++j) Id[j + j * B->n] = 1.0;
+    hn_apply(B, 0, Id, B->n, Bd, B->m, B->n, 1.0); /* B densely */
+    free(Id);
+    cplx* P = (cplx*)calloc((size_t)(A->m * B->n + 1), sizeof(cplx));
+    hn_apply(A, 0, Bd, B->m, P, A->m, B->n, 1.0);
+    free(Bd);
+    hn_add_dense(C, P, A->m, -1.0, eps);
+    free(P);
+}
+
+/* X <- L^{-1} X for the node X (rows of the diagonal node L) */
+static void hn_trsm_l(const hnode* L, hnode* X, double eps)
+{
+    if (X->type == 0) {
+        hn_solve_l(L, X->D, X->m, X->n);
+    } else if (X->type == 1) {
+        hn_solve_l(L, X->U, X->m, X->k);
+    } else { /* X subdivided, so is L (same row cluster) */
+        for (int v = 0; v < 2; ++v) {
+            hn_trsm_l(L->ch[0], X->ch[v], eps);
+            hn_gemm_sub(X->ch[2 + v], L->ch[2], X->ch[v], eps);
+            hn_trsm_l(L->ch[3], X->ch[2 + v], eps);
+        }
+    }
+}
+
+/* X <- X U^{-1} for the node X (columns of the diagonal node U) */
+static void hn_trsm_u(const hnode* Uf, hnode* X, double eps)
+{
+    if (X->type == 0) { /* X^H <- U^{-H} X^H */
+        cplx* T = (cplx*)malloc((size_t)(X->m * X->n + 1) * sizeof(cplx));
+        for (int64_t i = 0; i < X->m; ++i)
+            for (int64_t j = 0; j < X->n; ++j) T[j + i * X->n] = conj(X->D[i + j * X->m]);
+        hn_solve_uh(Uf, T, X->n, X->m);
+        for (int64_t i = 0; i < X->m; ++i)
+            for (int64_t j = 0; j < X->n; ++j) X->D[i + j * X->m] = conj(T[j + i * X->n]);
+        free(T);
+    } else if (X->type == 1) { /* U_x (V_x^H U^{-1}) = U_x (U^{-H} V_x)^H */
+        hn_solve_uh(Uf, X->V, X->n, X->k);
+    } else {
+        for (int u = 0; u < 2; ++u) {
+            hn_trsm_u(Uf->ch[0], X->ch[2 * u], eps);
+            hn_gemm_sub(X->ch[2 * u + 1], X->ch[2 * u], Uf->ch[1], eps);
+            hn_trsm_u(Uf->ch[3], X->ch[2 * u + 1], eps);
+        }
+    }
+}
+
+static int hn_lu(hnode* x, double eps)
+{
+    if (x->type == 0) { /* dense LU without pivoting, in place */
+        for (int64_t p = 0; p < x->m; ++p) {
+            const cplx piv = x->D[p + p * x->m];
+            if (piv == 0.0) return 1;
+            for (int64_t r = p + 1; r < x->m; ++r) x->D[r + p * x->m] /= piv;
+            for (int64_t c = p + 1; c < x->n; ++c) {
+                const cplx u = x->D[p + c * x->m];
+                for (int64_t r = p + 1; r < x->m; ++r) x->D[r + c * x->m] -= x->D[r + p * x->m] * u;
+            }
+        }
+        return 0;
+    }
+    if (hn_lu(x->ch[0], eps)) return 1;            /* 1. A11 = L11 U11 */
+    hn_trsm_l(x->ch[0], x->ch[1], eps);            /* 2. U12 = L11^{-1} A12 */
+    hn_trsm_u(x->ch[0], x->ch[2], eps);            /* 3. L21 = A21 U11^{-1} */
+    hn_gemm_sub(x->ch[3], x->ch[2], x->ch[1], eps); /* 4. A22 - L21 U12 ... */
+    return hn_lu(x->ch[3], eps);                   /*    = L22 U22 */
+}
+
+static int64_t hn_stored(const hnode* x)
+{
+    if (x->type == 0) return x->m * x->n;
+    if (x->type == 1) return (x->m + x->n) * x->k;
+    int64_t s = 0;
+    for (int q = 0; q < 4; ++q) s += hn_stored(x->ch[q]);
+    return s;
+}
+
+or_hlu* or_hlu_factor(const or_hmat* h, double eta, double eps_lu, int* status)
+{
+    const double t0 = now_s();
+    or_hlu* f = (or_hlu*)calloc(1, sizeof(or_hlu));
+    f->nc = h->nc;
+    f->perm = (int64_t*)malloc((size_t)(h->nc + 1) * sizeof(int64_t));
+    memcpy(f->perm, h->perm, (size_t)h->nc * sizeof(int64_t));
+    int64_t bi = 0;
+    f->root = hn_build(h, 0, 0, &bi, eta);
+    f->eps = eps_lu;
+    *status = (bi == h->nb) ? hn_lu(f->root, eps_lu) : 2; /* 1: zero pivot, 2: partition mismatch */
+    f->seconds = now_s() - t0;
+    return f;
+}
+
+void or_hlu_free(or_hlu* f)
+{
+    if (!f) return;
+    hn_free(f->root);
+    free(f->perm);
+    free(f);
+}
+
+/* x = U^{-1} L^{-1} b, vectors in the original point order */
+void or_hlu_solve(const or_hlu* f, const double* b, double* x)
+{
+    const int64_t N = 3 * f->nc;
+    cplx* y = (cplx*)malloc((size_t)(N + 1) * sizeof(cplx));
+    for (int64_t p = 0; p < f->nc; ++p)
+        for (int a = 0; a < 3; ++a) y[3 * p + a] = ld(b + 2 * (3 * f->perm[p] + a));
+    hn_solve_l(f->root, y, N, 1);
+    hn_solve_u(f->root, y, N, 1);
+    for (int64_t p = 0; p < f->nc; ++p)
+        for (int a = 0; a < 3; ++a) st(x + 2 * (3 * f->perm[p] + a), y[3 * p + a]);
+    free(y);
+}
+
+/* L (unit lower) and U as dense N x N col-major matrices in tree order */
+void or_hlu_dense(const or_hlu* f, double* L, double* U)
+{
+    const int64_t N = 3 * f->nc;
+    cplx* Mi = (cplx*)calloc((size_t)(N * N + 1), sizeof(cplx)); /* L^{-1}, then U^{-1} */
+    cplx* F = (cplx*)calloc((size_t)(N * N + 1), sizeof(cplx));  /* L, then U */
+    for (int64_t j = 0; j < N; ++j) Mi[j + j * N] = 1.0;
+    hn_solve_l(f->root, Mi, N, N); /* Mi = L^{-1}, unit lower triangular */
+    for (int64_t j = 0; j < N; ++j) /* L = Mi^{-1}: forward substitution, column by column */
+        for (int64_t r = j; r < N; ++r) {
+            cplx acc = (r == j) ? 1.0 : 0.0;
+            for (int64_t q = j; q < r; ++q) acc -= Mi[r + q * N] * F[q + j * N];
+            F[r + j * N] = acc;
+        }
+    for (int64_t e = 0; e < N * N; ++e) st(L + 2 * e, F[e]);
+    memset(Mi, 0, (size_t)(N * N) * sizeof(cplx));
+    memset(F, 0, (size_t)(N * N) * sizeof(cplx));
+    for (int64_t j = 0; j < N; ++j) Mi[j + j * N] = 1.0;
+    hn_solve_u(f->root, Mi, N, N); /* Mi = U^{-1}, upper triangular */
+    for (int64_t j = 0; j < N; ++j) /* U = Mi^{-1}: backward substitution, column by column */
+        for (int64_t r = j; r >= 0; --r) {
+            cplx acc = (r == j) ? 1.0 : 0.0;
+            for (int64_t q = r + 1; q <= j; ++q) acc -= Mi[r + q * N] * F[q + j * N];
+            F[r + j * N] = acc / Mi[r + r * N];
+        }
+    for (int64_t e = 0; e < N * N; ++e) st(U + 2 * e, F[e]);
+    free(Mi);
+    free(F);
+}
+
+double or_hlu_seconds(const or_hlu* f) { return f->seconds; }
+int64_t or_hlu_stored(const or_hlu* f) { return hn_stored(f->root); }

@@ -137,6 +137,19 @@ void or_hmat_block_data(const or_hmat* h, int64_t b, double* D_or_U, double* V);
 void or_hmat_matvec(const or_hmat* h, const double* x, double* y);
 double or_hmat_build_seconds(const or_hmat* h);
 
+/* --- H-LU factorisation and direct solver (Sec. 3.2): recursive 2 x 2 block
+ * LU of the H-matrix (no pivoting), updates of low-rank blocks recompressed
+ * with eps_lu.  eta must be the partition's.  status: 0 ok, 1 zero pivot,
+ * 2 block tree / partition mismatch.  Vectors in the original point order;
+ * or_hlu_dense returns L (unit lower) and U, N x N col-major, tree order. */
+typedef struct or_hlu or_hlu;
+or_hlu* or_hlu_factor(const or_hmat* h, double eta, double eps_lu, int* status);
+void or_hlu_free(or_hlu* f);
+void or_hlu_solve(const or_hlu* f, const double* b, double* x);
+void or_hlu_dense(const or_hlu* f, double* L, double* U);
+double or_hlu_seconds(const or_hlu* f);
+int64_t or_hlu_stored(const or_hlu* f);
+
 /* --- restarted GMRES(m) (Sec. 3.1 drives it with the H-matvec) */
 int or_gmres_hmat(const or_hmat* h, const double* b, double* x, int restart, double tol,
                   int maxit, int* iters, double* relres);

@@ -68,6 +68,12 @@ def lib():
             "or_splitmix64": (C.c_uint64, [C.c_uint64]),
             "or_hmat_block_methods": (None, [_P, _P]),
             "or_hmat_build": (_P, [_P, _P, _P, _I64, _D, _D, _I64, _INT, _I64, _INT]),
+            "or_hlu_factor": (_P, [_P, _D, _D, _P]),
+            "or_hlu_free": (None, [_P]),
+            "or_hlu_solve": (None, [_P, _P, _P]),
+            "or_hlu_dense": (None, [_P, _P, _P]),
+            "or_hlu_seconds": (_D, [_P]),
+            "or_hlu_stored": (_I64, [_P]),
             "or_hmat_free": (None, [_P]),
             "or_hmat_nclusters": (_I64, [_P]),
             "or_hmat_clusters": (None, [_P, _P]),
@@ -356,6 +362,45 @@ def gmres_dense(A, b, restart=50, tol=1e-6, maxit=1000):
     st = lib().or_gmres_dense(_ptr(A), A.shape[0], _ptr(b), _ptr(x), restart, tol, maxit,
                               C.byref(it), C.byref(rr))
     return x, it.value, rr.value, st
+
+
+
+
+class HLU:
+    """H-LU factors of an oracle H-matrix (Sec. 3.2); solve() is the direct solver."""
+
+    def __init__(self, H, eta, eps_lu):
+        self.H = H  # keeps the H-matrix alive
+        self.nc = H.nc
+        st = C.c_int(0)
+        self.f = lib().or_hlu_factor(H.h, eta, eps_lu, C.byref(st))
+        self.status = st.value
+
+    def __del__(self):
+        if getattr(self, "f", None):
+            lib().or_hlu_free(self.f)
+            self.f = None
+
+    def solve(self, b):
+        b = _c128(b)
+        x = np.zeros_like(b)
+        lib().or_hlu_solve(self.f, _ptr(b), _ptr(x))
+        return x
+
+    def dense(self):
+        N = 3 * self.nc
+        L = np.zeros((N, N), np.complex128)
+        U = np.zeros((N, N), np.complex128)
+        lib().or_hlu_dense(self.f, _ptr(L), _ptr(U))
+        return L.T.copy(), U.T.copy()  # col-major buffers
+
+    @property
+    def seconds(self):
+        return lib().or_hlu_seconds(self.f)
+
+    @property
+    def stored(self):
+        return lib().or_hlu_stored(self.f)
 
 
 __all__ = [n for n in dir() if not n.startswith("_")]
