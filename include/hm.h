@@ -203,6 +203,26 @@ hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int3
 hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double* delta_f,
                             double* norm_f, void* stream);
 
+/* H-LU factorisation and direct solver (Sec. 3.2, "H-LU factorization and
+ * direct solver"), FP64 on the device.  hm_lu_factor copies the stored
+ * H-matrix into its block tree (FP32 -> FP64) and factorises it recursively on
+ * 2 x 2 block matrices (1. A11 = L11 U11, 2. U12 = L11^{-1} A12,
+ * 3. L21 = A21 U11^{-1}, 4. A22 - L21 U12 = L22 U22), without pivoting; the
+ * update of step 4 is formed in the target block's format and low-rank targets
+ * are recompressed (Sec. 3.2) with eps_lu.  The factors replace earlier ones
+ * in the handle.  The call synchronises stream.
+ *   eps_lu  in (0, 1): the truncation tolerance eps_LU of Sec. 3.2
+ * Errors: HM_ERR_ARG, HM_ERR_NUMERIC (zero pivot, unconverged SVD), HM_ERR_CUDA.
+ * hm_lu_solve: x = U^{-1} L^{-1} b for nrhs columns; b, x DEVICE complex128,
+ *   3 n_c x nrhs column-major, original point order, not overlapping.
+ *   Certify it with hm_estimate_error (Eq. est_direct of Sec. 3.3).
+ *   Errors: HM_ERR_ARG (no factors, bad pointers), HM_ERR_CUDA.
+ * hm_lu_info: factorisation wall time (s), complex entries stored in L and U,
+ *   kernel launches of the factorisation (any output may be NULL). */
+hm_status hm_lu_factor(hm_handle h, double eps_lu, void* stream);
+hm_status hm_lu_solve(hm_handle h, int32_t nrhs, const void* b, void* x, void* stream);
+hm_status hm_lu_info(hm_handle h, double* seconds, int64_t* entries, int64_t* launches);
+
 /* Writes a JSON object (NUL-terminated) with the build statistics: n_c, tree
  * depth, cluster and block counts, sparsity constant C_sp (Sec. 2.1), ACA
  * and recompressed ranks (as in the rank tables of Sec. 7.2), stored bytes,

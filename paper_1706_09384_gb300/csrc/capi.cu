@@ -843,6 +843,32 @@ hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double*
     HM_API_END
 }
 
+hm_status hm_lu_factor(hm_handle h, double eps_lu, void* stream) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (!(eps_lu > 0) || !(eps_lu < 1)) hm_throw(HM_ERR_ARG, "eps_lu must lie in (0, 1)");
+    hlu_factor(h, eps_lu, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_lu_solve(hm_handle h, int32_t nrhs, const void* b, void* x, void* stream) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (nrhs < 1 || !b || !x) hm_throw(HM_ERR_ARG, "null pointer or nrhs < 1");
+    const size_t bytes = (size_t)3 * h->nc * nrhs * 16;
+    const char *bb = (const char*)b, *xx = (const char*)x;
+    if (bb < xx + bytes && xx < bb + bytes) hm_throw(HM_ERR_ARG, "b and x overlap");
+    hlu_solve(h, nrhs, (const double2*)b, (double2*)x, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_lu_info(hm_handle h, double* seconds, int64_t* entries, int64_t* launches) {
+    HM_API_BEGIN
+    if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    hlu_info(h, seconds, entries, launches);
+    HM_API_END
+}
+
 hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
@@ -1165,6 +1191,10 @@ int64_t hm_kernel_launches(void) { return (int64_t)g_hm_launches.load(); }
 void hm_free(hm_handle h) {
     if (!h) return;
     cudaDeviceSynchronize();
+    try {
+        hlu_release(h, 0);
+    } catch (...) {
+    }
     free_all(h->owner);
     matvec_dev_destroy(h->mv);
     delete h;

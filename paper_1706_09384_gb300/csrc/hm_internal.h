@@ -161,6 +161,13 @@ int aca_ctas_per_sm(int capmax);
 // Core of the recompression for a batch: ranks r' and the k x r' transforms.
 // g_off[j] >= 0: the job's Gram matrices (ld g_ld[j]) are read from d_gram instead of
 // being recomputed from the factors.
+// H-LU factorisation and direct solver (hlu.cu, Sec. 3.2), FP64, kept in the handle.
+struct hm_matrix;
+void hlu_factor(hm_matrix* h, double eps_lu, cudaStream_t st);
+void hlu_solve(hm_matrix* h, int32_t nrhs, const double2* b, double2* x, cudaStream_t st);
+void hlu_info(const hm_matrix* h, double* seconds, int64_t* entries, int64_t* launches);
+void hlu_release(hm_matrix* h, cudaStream_t st);
+
 // Randomized SVD (rsvd.cu) of admissible blocks the vector ACA cannot pivot.
 struct RsvdBlock {
     int64_t tau_global, sig_global;  // first row / column point, tree order (batch-global)
@@ -262,5 +269,6 @@ struct hm_matrix {
     int64_t rsvd_blocks = 0;       // admissible blocks compressed by the randomized SVD
     int64_t rsvd_uncertified = 0;  // of those, blocks whose samples reached their cap uncertified
     double t_rsvd_ms = 0;          // wall time of the randomized SVD pass (with its recompression)
+    void* hlu = nullptr;           // H-LU factors (hlu.cu), if computed
     int used_rank_model = 0;
 };

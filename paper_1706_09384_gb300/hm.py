@@ -71,6 +71,9 @@ SIGNATURES = {
     "hm_gmres": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
     "hm_gmres_multi": (_I32, [_P, _I32, _P, _P, _I32, C.c_double, _I32, _P, _P, _P]),
     "hm_estimate_error": (_I32, [_P, _I64, C.c_uint64, _P, _P, _P]),
+    "hm_lu_factor": (_I32, [_P, _D, _P]),
+    "hm_lu_solve": (_I32, [_P, _I32, _P, _P, _P]),
+    "hm_lu_info": (_I32, [_P, _P, _P, _P]),
     "hm_stats": (_I32, [_P, C.c_char_p, _SZ, _P]),
     "hm_sizes": (_I32, [_P, _P, _P, _P]),
     "hm_get_tree": (_I32, [_P, _P, _P]),
@@ -325,6 +328,34 @@ class HMatrix:
         _check(lib().hm_estimate_error(self.h, nsample, seed, C.byref(d), C.byref(a),
                                        _stream_ptr(stream)), "hm_estimate_error")
         return d.value, a.value
+
+    def lu_factor(self, eps_lu, stream=None):
+        """H-LU factorisation (Sec. 3.2) with truncation tolerance eps_lu."""
+        _check(lib().hm_lu_factor(self.h, eps_lu, _stream_ptr(stream)), "hm_lu_factor")
+
+    def lu_solve(self, b, x=None, stream=None):
+        """x = (L U)^{-1} b with the H-LU factors; b: 3 n_c (x nrhs) complex128 on the device."""
+        import torch
+        B = b if b.dim() == 2 else b.reshape(-1, 1)
+        Bc = B.t().contiguous()  # column-major
+        Xc = torch.empty_like(Bc)
+        _check(lib().hm_lu_solve(self.h, Bc.shape[0], Bc.data_ptr(), Xc.data_ptr(),
+                                 _stream_ptr(stream)), "hm_lu_solve")
+        X = Xc.t()
+        if b.dim() == 1:
+            X = X.reshape(-1)
+        if x is not None:
+            x.copy_(X)
+            return x
+        return X.contiguous()
+
+    def lu_info(self):
+        """(seconds, stored complex entries, kernel launches) of the H-LU factorisation."""
+        sec = C.c_double(0.0)
+        ent = C.c_int64(0)
+        lau = C.c_int64(0)
+        _check(lib().hm_lu_info(self.h, C.byref(sec), C.byref(ent), C.byref(lau)), "hm_lu_info")
+        return sec.value, ent.value, lau.value
 
     def profile_matvec(self, reps=10, stream=None):
         """Average per-kernel device times (ms) of the product and its algorithmic bytes."""
