@@ -32,6 +32,8 @@
 #include <map>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "hm_internal.h"
 
 namespace {
@@ -53,31 +55,35 @@ __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-// C (M x N, ldc) += alpha opA(A) opB(B); op 0: X, op 1: X^H.
+// C (M x N, ldc) += alpha opA(A) opB(B); op 0: X, op 1: X^H.  Split-K: CTA
+// row y of the grid takes k in [y kchunk, (y + 1) kchunk) and adds into
+// C + y cstride (the caller sums the partial products).
 __global__ void __launch_bounds__(HT) hz_gemm_kernel(double2* C, const double2* A, const double2* B,
                                                      int64_t M, int64_t N, int64_t K, int64_t lda,
                                                      int64_t ldb, int64_t ldc, int opa, int opb,
-                                                     double2 alpha) {
+                                                     double2 alpha, int64_t kchunk, int64_t cstride) {
     __shared__ double2 sa[TK][TT + 1];
     __shared__ double2 sb[TK][TT + 1];
     const int64_t tm = (M + TT - 1) / TT;
     const int64_t r0 = (blockIdx.x % tm) * TT, c0 = (blockIdx.x / tm) * TT;
     const int tid = threadIdx.x, tr = tid % 16, tc = tid / 16;
+    const int64_t kb = blockIdx.y * kchunk, ke = min(K, kb + kchunk);
+    C += blockIdx.y * cstride;
     double2 acc[2][2] = {};
-    for (int64_t k0 = 0; k0 < K; k0 += TK) {
+    for (int64_t k0 = kb; k0 < ke; k0 += TK) {
         for (int e = tid; e < TK * TT; e += HT) {
             {  // opA(A)(r0 + rr, k0 + kk), the stored matrix's contiguous index fastest
                 const int kk = opa ? e % TK : e / TT, rr = opa ? e / TK : e % TT;
                 const int64_t r = r0 + rr, k = k0 + kk;
                 double2 v = make_double2(0.0, 0.0);
-                if (r < M && k < K) v = opa ? zconj(A[k + r * lda]) : A[r + k * lda];
+                if (r < M && k < ke) v = opa ? zconj(A[k + r * lda]) : A[r + k * lda];
                 sa[kk][rr] = v;
             }
             {  // opB(B)(k0 + kk, c0 + cc)
                 const int kk = opb ? e / TT : e % TK, cc = opb ? e % TT : e / TK;
                 const int64_t k = k0 + kk, c = c0 + cc;
                 double2 v = make_double2(0.0, 0.0);
-                if (k < K && c < N) v = opb ? zconj(B[c + k * ldb]) : B[k + c * ldb];
+                if (k < ke && c < N) v = opb ? zconj(B[c + k * ldb]) : B[k + c * ldb];
                 sb[kk][cc] = v;
             }
         }
@@ -124,6 +130,21 @@ __global__ void hz_copy_kernel(double2* dst, int64_t ldd, const double2* src, in
     }
 }
 
+// C (rows x cols, ldc) += sum over the splits of P (rows x cols each, in order)
+__global__ void hz_splitsum_kernel(double2* C, int64_t ldc, const double2* P, int64_t rows, int64_t cols,
+                                   int64_t splits) {
+    for (int64_t e = blockIdx.x * (int64_t)HT + threadIdx.x; e < rows * cols; e += (int64_t)gridDim.x * HT) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int64_t q = 0; q < splits; ++q) {
+            a.x += P[q * rows * cols + e].x;
+            a.y += P[q * rows * cols + e].y;
+        }
+        double2& d = C[e % rows + (e / rows) * ldc];
+        d.x += a.x;
+        d.y += a.y;
+    }
+}
+
 __global__ void hz_identity_kernel(double2* A, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)HT + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * HT)
         A[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
@@ -134,7 +155,7 @@ __global__ void __launch_bounds__(HT) hz_getrf_kernel(double2* D, int64_t m, int
     for (int64_t p = 0; p < m; ++p) {
         const double2 piv = D[p + p * m];
         if (piv.x == 0.0 && piv.y == 0.0) {
-            if (threadIdx.x == 0) atomicExch(zero_pivot, 1);
+            if (threadIdx.x == 0) atomicOr(zero_pivot, 1);
             return;  // uniform across the CTA
         }
         for (int64_t r = p + 1 + threadIdx.x; r < m; r += HT) D[r + p * m] = zdiv(D[r + p * m], piv);
@@ -291,21 +312,32 @@ __global__ void __launch_bounds__(QT) hz_qr_kernel(double2* W, int64_t M, int64_
 // orthogonal columns P_j s_j, s_j = |WJ_j|; J (the right singular vectors) is
 // not kept: the caller forms W0^H P instead.  Round-robin pairs, a warp per
 // pair; a pair is rotated when |gamma| > tol sqrt(alpha beta), tol = max(1e-15,
-// K u).  One CTA; W in shared memory up to K = JS_MAX, else in WJ.
+// K u), and neither column is negligible (squared norm above (K u)^2
+// ||W||_F^2).  One CTA; W in shared memory up to K = JS_MAX, else in WJ.
 constexpr int JT = 512;
 constexpr int64_t JS_MAX = 112;
-__global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double2* WJ, int64_t K, double* s,
-                                                       int* unconverged) {
-    extern __shared__ double2 hz_w[];
+constexpr int64_t JS_MAX_CHOL = 1024;  // Gram-form recompression: K up to here
+__device__ void hz_jacobi(const double2* W0, double2* WJ, int64_t K, double* s, int* unconverged,
+                          double2* hz_w, double tol_min) {
     __shared__ int s_conv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool in_smem = K <= JS_MAX;
     double2* W = in_smem ? hz_w : WJ;
-    for (int64_t e = threadIdx.x; e < K * K; e += JT) W[e] = W0[e];
-    __syncthreads();
+    __shared__ double red[JT / 32];
+    double f2 = 0.0;
+    for (int64_t e = threadIdx.x; e < K * K; e += JT) {
+        const double2 v = W0[e];
+        W[e] = v;
+        f2 += v.x * v.x + v.y * v.y;
+    }
+    f2 = hz_block_sum<JT>(f2, red);  // ||W||_F^2, invariant under the rotations
     const int64_t np = (K + 1) & ~1;
     // the rounding level of the computed gamma over K terms (Demmel and Veselic 1992)
-    const double tol = fmax(1e-15, (double)K * 0x1.0p-53);
+    const double tol = fmax(tol_min, (double)K * 0x1.0p-53);
+    // a column at the rounding level of W (rank-deficient W) cannot be made
+    // orthogonal to a large one to relative accuracy: it is left alone, and
+    // its singular value (<= K u ||W||_F) falls below any truncation
+    const double small = ((double)K * 0x1.0p-53) * ((double)K * 0x1.0p-53) * f2;
     int sweep = 0;
     for (; sweep < 80; ++sweep) {
         if (threadIdx.x == 0) s_conv = 1;
@@ -341,11 +373,13 @@ __global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double
                     gi += __shfl_xor_sync(0xffffffffu, gi, o);
                 }
                 const double ag = sqrt(gr * gr + gi * gi);
-                if (ag == 0.0 || ag <= tol * sqrt(al * be)) continue;  // uniform within the warp
+                if (al <= small || be <= small) continue;                      // uniform within the warp
+                if (ag == 0.0 || ag <= tol * sqrt(al) * sqrt(be)) continue;  // uniform within the warp
                 if (lane == 0) s_conv = 0;
                 const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
                 const double zeta = (be - al) / (2.0 * ag);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double az = fabs(zeta);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (az > 1e150 ? 2.0 * az : az + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
                 // [w_a, w_b] <- [w_a, w_b] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]
                 for (int64_t r = lane; r < K; r += 32) {
@@ -359,7 +393,7 @@ __global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double
         if (s_conv) break;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && sweep == 80) atomicExch(unconverged, 1);
+    if (threadIdx.x == 0 && sweep == 80) atomicOr(unconverged, 2);
     for (int64_t j = warp; j < K; j += JT / 32) {
         double a = 0.0;
         for (int64_t r = lane; r < K; r += 32) a += W[r + j * K].x * W[r + j * K].x + W[r + j * K].y * W[r + j * K].y;
@@ -368,6 +402,190 @@ __global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double
     }
     if (in_smem)
         for (int64_t e = threadIdx.x; e < K * K; e += JT) WJ[e] = W[e];
+}
+
+__global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double2* WJ, int64_t K, double* s,
+                                                       int* unconverged, double tol_min) {
+    extern __shared__ double2 hz_w[];
+    hz_jacobi(W0, WJ, K, s, unconverged, hz_w, tol_min);
+}
+
+// The same one-sided Jacobi spread over a thread-block cluster of CJ CTAs (one
+// SM each, for CJ times the FP64 rate of one SM): W lives in the shared memory
+// of CTA 0 and every warp of the cluster reaches it through distributed shared
+// memory; a warp holds its pair of columns in registers for the round (one
+// read, one write), rounds end at the cluster barrier.  K <= 128.
+constexpr int CJ = 8;
+constexpr int CJT = 256;
+constexpr int64_t CJ_MAX = 112;  // K x K complex in one CTA's shared memory
+__global__ void __cluster_dims__(CJ, 1, 1) __launch_bounds__(CJT)
+    hz_jacobi_cluster_kernel(const double2* W0, double2* WJ, int64_t K, double* s, int* unconverged,
+                             double tol_min) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double2 hz_cw[];
+    __shared__ double part[CJ];
+    __shared__ double red[CJT / 32];
+    __shared__ int conv;
+    const unsigned rank = cl.block_rank();
+    double2* W = cl.map_shared_rank(hz_cw, 0);
+    double* part0 = cl.map_shared_rank(part, 0);
+    int* conv0 = cl.map_shared_rank(&conv, 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)rank * (CJT / 32) + warp, nw = (int64_t)CJ * (CJT / 32);
+    // W0 -> CTA 0, a slice per CTA; ||W||_F^2 from the slices
+    double f2 = 0.0;
+    for (int64_t e = (int64_t)rank * CJT + threadIdx.x; e < K * K; e += (int64_t)CJ * CJT) {
+        const double2 v = W0[e];
+        W[e] = v;
+        f2 += v.x * v.x + v.y * v.y;
+    }
+    f2 = hz_block_sum<CJT>(f2, red);
+    if (threadIdx.x == 0) part0[rank] = f2;
+    cl.sync();
+    f2 = 0.0;
+    for (int q = 0; q < CJ; ++q) f2 += part0[q];
+    const int64_t np = (K + 1) & ~1;
+    const double tol = fmax(tol_min, (double)K * 0x1.0p-53);
+    const double small = ((double)K * 0x1.0p-53) * ((double)K * 0x1.0p-53) * f2;
+    int sweep = 0;
+    for (; sweep < 80; ++sweep) {
+        if (rank == 0 && threadIdx.x == 0) *conv0 = 1;
+        cl.sync();
+        for (int64_t round = 0; round < np - 1; ++round) {
+            for (int64_t pi = gw; pi < np / 2; pi += nw) {
+                int64_t a, b;
+                if (pi == 0) {
+                    a = np - 1;
+                    b = round;
+                } else {
+                    a = (round + pi) % (np - 1);
+                    b = (round - pi + np - 1) % (np - 1);
+                }
+                if (a >= K || b >= K) continue;
+                if (a > b) {
+                    const int64_t t = a;
+                    a = b;
+                    b = t;
+                }
+                double2 wa[4], wb[4];
+                double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t r = lane + 32 * i;
+                    wa[i] = r < K ? W[r + a * K] : make_double2(0.0, 0.0);
+                    wb[i] = r < K ? W[r + b * K] : make_double2(0.0, 0.0);
+                    al += wa[i].x * wa[i].x + wa[i].y * wa[i].y;
+                    be += wb[i].x * wb[i].x + wb[i].y * wb[i].y;
+                    gr += wa[i].x * wb[i].x + wa[i].y * wb[i].y;  // conj(wa) wb
+                    gi += wa[i].x * wb[i].y - wa[i].y * wb[i].x;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                }
+                const double ag = sqrt(gr * gr + gi * gi);
+                if (al <= small || be <= small) continue;                      // uniform within the warp
+                if (ag == 0.0 || ag <= tol * sqrt(al) * sqrt(be)) continue;  // uniform within the warp
+                if (lane == 0) *conv0 = 0;
+                const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
+                const double zeta = (be - al) / (2.0 * ag);
+                const double az = fabs(zeta);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (az > 1e150 ? 2.0 * az : az + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t r = lane + 32 * i;
+                    if (r < K) {
+                        const double2 pwb = zmul(phc, wb[i]);
+                        W[r + a * K] = make_double2(c * wa[i].x - sn * pwb.x, c * wa[i].y - sn * pwb.y);
+                        W[r + b * K] = make_double2(sn * wa[i].x + c * pwb.x, sn * wa[i].y + c * pwb.y);
+                    }
+                }
+            }
+            cl.sync();
+        }
+        const int done = *conv0;
+        cl.sync();  // every thread has read the flag before CTA 0 resets it
+        if (done) break;
+    }
+    if (rank == 0 && threadIdx.x == 0 && sweep == 80) atomicOr(unconverged, 2);
+    for (int64_t j = gw; j < K; j += nw) {
+        double a = 0.0;
+        for (int64_t r = lane; r < K; r += 32) {
+            const double2 v = W[r + j * K];
+            WJ[r + j * K] = v;
+            a += v.x * v.x + v.y * v.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s[j] = sqrt(a);
+    }
+    cl.sync();  // CTA 0's shared memory stays until every CTA is done with it
+}
+
+// G = R^H R for a Hermitian semi-definite G (K x K, in place -> R upper):
+// equilibrated (G' = D^-1 G D^-1, D = sqrt diag G), right-looking on the upper
+// triangle; a pivot of G' at or below 1e-13 zeroes its row of R (the
+// direction is below 3.2e-7 of its column norm).  R = R' D.
+__device__ void hz_chol_equil(double2* G, int64_t K, double* dsc) {
+    __shared__ double s_piv;
+    const int tid = threadIdx.x;
+    for (int64_t j = tid; j < K; j += JT) {
+        const double d = G[j + j * K].x;
+        dsc[j] = d > 1e-280 ? sqrt(d) : 0.0;  // a column whose squared norm underflows counts as zero
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < K * K; e += JT) {
+        const int64_t p = e % K, c = e / K;
+        const double sc = (dsc[p] > 0.0 && dsc[c] > 0.0) ? 1.0 / (dsc[p] * dsc[c]) : 0.0;
+        G[e] = make_double2(G[e].x * sc, G[e].y * sc);
+    }
+    __syncthreads();
+    for (int64_t j = 0; j < K; ++j) {
+        if (tid == 0) {
+            const double d = G[j + j * K].x;
+            s_piv = d > 1e-13 ? sqrt(d) : 0.0;
+        }
+        __syncthreads();
+        const double piv = s_piv;
+        for (int64_t c = j + 1 + tid; c < K; c += JT) {
+            const double2 g = G[j + c * K];
+            G[j + c * K] = piv > 0.0 ? make_double2(g.x / piv, g.y / piv) : make_double2(0.0, 0.0);
+        }
+        if (tid == 0) G[j + j * K] = make_double2(piv, 0.0);
+        __syncthreads();
+        const int64_t w = K - j - 1;
+        for (int64_t e = tid; e < w * w; e += JT) {
+            const int64_t a = j + 1 + e % w, b = j + 1 + e / w;
+            if (a <= b) {
+                const double2 ra = G[j + a * K], rb = G[j + b * K];
+                G[a + b * K].x -= ra.x * rb.x + ra.y * rb.y;  // conj(ra) rb
+                G[a + b * K].y -= ra.x * rb.y - ra.y * rb.x;
+            }
+        }
+        __syncthreads();
+    }
+    for (int64_t e = tid; e < K * K; e += JT) {
+        const int64_t p = e % K, c = e / K;
+        G[e] = p > c ? make_double2(0.0, 0.0) : make_double2(G[e].x * dsc[c], G[e].y * dsc[c]);
+    }
+    __syncthreads();
+}
+
+// Core of the Gram-form recompression (one CTA): R_U, R_V from G_U = U^H U and
+// G_V = V^H V (in place) and W = R_U R_V^H.
+__global__ void __launch_bounds__(JT) hz_gram_core_kernel(double2* GU, double2* GV, double2* W, int64_t K) {
+    __shared__ double dsc[JS_MAX_CHOL];
+    hz_chol_equil(GU, K, dsc);
+    hz_chol_equil(GV, K, dsc);
+    for (int64_t e = threadIdx.x; e < K * K; e += JT) {  // W_pc = sum_q RU_pq conj(RV_cq), q >= max(p, c)
+        const int64_t p = e % K, c = e / K;
+        double2 a = make_double2(0.0, 0.0);
+        for (int64_t q = p > c ? p : c; q < K; ++q) zmad(a, GU[p + q * K], zconj(GV[c + q * K]));
+        W[e] = a;
+    }
 }
 
 // dst[:, q] = src[:, idx[q]] * sc[q]  (rows x r)
@@ -487,10 +705,28 @@ void gemm(Ctx& C, double2* c, const double2* a, const double2* b, int64_t M, int
           int64_t lda, int64_t ldb, int64_t ldc, int opa, int opb, double2 alpha) {
     if (M <= 0 || N <= 0 || K <= 0) return;
     const int64_t tiles = hm_cdiv(M, TT) * hm_cdiv(N, TT);
-    hz_gemm_kernel<<<(unsigned)tiles, HT, 0, C.st>>>(c, a, b, M, N, K, lda, ldb, ldc, opa, opb, alpha);
+    // few output tiles over a long contraction: split K over up to 2 CTAs per SM
+    const int64_t splits = tiles >= 152 || K < 1024 ? 1 : std::min<int64_t>(hm_cdiv(K, 256), hm_cdiv(304, tiles));
+    if (splits <= 1) {
+        hz_gemm_kernel<<<(unsigned)tiles, HT, 0, C.st>>>(c, a, b, M, N, K, lda, ldb, ldc, opa, opb, alpha, K, 0);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+        C.launches++;
+        return;
+    }
+    const int64_t kchunk = hm_cdiv(hm_cdiv(K, splits), TK) * TK;
+    const int64_t sp = hm_cdiv(K, kchunk);
+    double2* P = zalloc(C, sp * M * N);
+    HM_CUDA(cudaMemsetAsync(P, 0, (size_t)sp * M * N * 16, C.st));
+    hz_gemm_kernel<<<dim3((unsigned)tiles, (unsigned)sp), HT, 0, C.st>>>(P, a, b, M, N, K, lda, ldb, M, opa, opb,
+                                                                          alpha, kchunk, M * N);
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
-    C.launches++;
+    hz_splitsum_kernel<<<grid_for(M * N), HT, 0, C.st>>>(c, ldc, P, M, N, sp);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    C.launches += 2;
+    zfree(C, P);
 }
 void copy2d(Ctx& C, double2* dst, int64_t ldd, const double2* src, int64_t lds, int64_t rows, int64_t cols,
             double2 alpha, int add) {
@@ -619,7 +855,32 @@ void densify(Ctx& C, const HNode* x, double2* D, int64_t ldd, double2 alpha) {
 // x->V, x->k: QR of both factors, SVD of R_U R_V^H, the smallest rank r whose
 // discarded singular values, together with an error rho2 already committed
 // (squared Frobenius norm), stay within eps_LU of the whole.
+// One-sided Jacobi of W (K x K) -> WJ = P S, s: a cluster of CJ CTAs for K up
+// to CJ_MAX, else one CTA on global memory.  Rotations stop at
+// max(K u, 1e-3 eps_LU) of orthogonality, far below what the truncation at
+// eps_LU can see.
+void jacobi(Ctx& C, const double2* W, double2* WJ, int64_t K, double* s) {
+    const double tol_min = std::max(1e-15, 1e-3 * C.eps);
+    if (K <= CJ_MAX) {
+        const size_t sm = (size_t)K * K * sizeof(double2);
+        if (sm > 40 * 1024)
+            HM_CUDA(cudaFuncSetAttribute(hz_jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(CJ_MAX * CJ_MAX * sizeof(double2))));
+        hz_jacobi_cluster_kernel<<<CJ, CJT, sm, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
+    } else {
+        hz_jacobi_kernel<<<1, JT, 0, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
+    }
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    C.launches++;
+}
+
+// eps_LU from which the Gram form below replaces the Householder QR
+constexpr double GRAM_EPS = 1e-5;
+void truncate_gram(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2);
+
 void truncate(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2 = 0.0) {
+    if (C.eps >= GRAM_EPS && K <= JS_MAX_CHOL) return truncate_gram(C, x, U2, V2, K, rho2);
     const int64_t m = x->m, n = x->n;
     double2 *QU = zalloc(C, m * K), *RU = zalloc(C, K * K), *QV = zalloc(C, n * K), *RV = zalloc(C, K * K);
     const size_t smem = (size_t)K * sizeof(double);
@@ -639,17 +900,13 @@ void truncate(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2
     double2* WJ = zalloc(C, K * K);
     double* s = nullptr;
     HM_CUDA(cudaMallocAsync((void**)&s, (size_t)K * 8, C.st));
-    const size_t wsm = K <= JS_MAX ? (size_t)K * K * sizeof(double2) : 0;
-    if (wsm > 48 * 1024)
-        HM_CUDA(cudaFuncSetAttribute(hz_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(JS_MAX * JS_MAX * sizeof(double2))));
-    hz_jacobi_kernel<<<1, JT, wsm, C.st>>>(W, WJ, K, s, C.d_flag);
-    HM_CUDA(cudaGetLastError());
-    HM_LAUNCHED();
-    C.launches++;
+    jacobi(C, W, WJ, K, s);
     std::vector<double> hs(K);
     HM_CUDA(cudaMemcpyAsync(hs.data(), s, (size_t)K * 8, cudaMemcpyDeviceToHost, C.st));
     HM_CUDA(cudaStreamSynchronize(C.st));
+    for (int64_t i = 0; i < K; ++i)
+        if (!std::isfinite(hs[i]))
+            hm_throw(HM_ERR_NUMERIC, "H-LU: non-finite singular value (Householder recompression)");
     std::vector<int32_t> ord(K);
     for (int64_t i = 0; i < K; ++i) ord[i] = (int32_t)i;
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hs[a] > hs[b]; });
@@ -716,6 +973,109 @@ void truncate(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2
     zfree(C, RU);
     zfree(C, QV);
     zfree(C, RV);
+}
+
+// The same recompression in Gram form, for eps_LU >= GRAM_EPS: R_U, R_V from
+// the Cholesky factors of U2^H U2 and V2^H V2 (split-K GEMMs over the long
+// side, many CTAs), and the orthonormal factors never formed: with
+// W = R_U R_V^H = P S L^H,
+//   Q_U P_r S_r^{1/2} = U2 T_U,  T_U = R_V^H L_r S_r^{-1/2},
+//   Q_V L_r S_r^{1/2} = V2 T_V,  T_V = R_U^H P_r S_r^{-1/2},
+// valid for singular R_U, R_V; L_r S_r = W^H P_r.  The Gram matrices square
+// the conditioning: directions below 3.2e-7 of a column are dropped, hence
+// the eps_LU floor (30 times that level).
+
+void truncate_gram(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2) {
+    const int64_t m = x->m, n = x->n;
+    double2 *GU = zalloc(C, K * K), *GV = zalloc(C, K * K);
+    HM_CUDA(cudaMemsetAsync(GU, 0, (size_t)K * K * 16, C.st));
+    HM_CUDA(cudaMemsetAsync(GV, 0, (size_t)K * K * 16, C.st));
+    gemm(C, GU, U2, U2, K, K, m, m, m, K, 1, 0, ONE);
+    gemm(C, GV, V2, V2, K, K, n, n, n, K, 1, 0, ONE);
+    double2 *W = zalloc(C, K * K), *WJ = zalloc(C, K * K);
+    double* s = nullptr;
+    HM_CUDA(cudaMallocAsync((void**)&s, (size_t)K * 8, C.st));
+    hz_gram_core_kernel<<<1, JT, 0, C.st>>>(GU, GV, W, K);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    C.launches++;
+    jacobi(C, W, WJ, K, s);
+    std::vector<double> hs(K);
+    HM_CUDA(cudaMemcpyAsync(hs.data(), s, (size_t)K * 8, cudaMemcpyDeviceToHost, C.st));
+    HM_CUDA(cudaStreamSynchronize(C.st));
+    for (int64_t i = 0; i < K; ++i)
+        if (!std::isfinite(hs[i])) hm_throw(HM_ERR_NUMERIC, "H-LU: non-finite singular value (Gram recompression)");
+    std::vector<int32_t> ord(K);
+    for (int64_t i = 0; i < K; ++i) ord[i] = (int32_t)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hs[a] > hs[b]; });
+    double tot = rho2;
+    for (int64_t i = 0; i < K; ++i) tot += hs[i] * hs[i];
+    int64_t r = K;
+    double tail = rho2;
+    for (int64_t i = K - 1; i >= 0; --i) {
+        const double sv = hs[ord[i]];
+        if (std::sqrt(tail + sv * sv) <= C.eps * std::sqrt(tot)) {
+            tail += sv * sv;
+            r = i;
+        } else {
+            break;
+        }
+    }
+    while (r > 0 && !(hs[ord[r - 1]] > 0.0)) --r;
+    zfree(C, x->U);
+    zfree(C, x->V);
+    x->U = x->V = nullptr;
+    x->k = r;
+    if (r > 0) {
+        // WJ_q = P_q s_q: Pa = P_r S_r^{-1/2}, Pb = P_r S_r^{-3/2}
+        std::vector<double> sa(r), sb(r);
+        for (int64_t q = 0; q < r; ++q) {
+            const double sq = hs[ord[q]];
+            sa[q] = 1.0 / (sq * std::sqrt(sq));
+            sb[q] = sa[q] / sq;
+        }
+        int32_t* d_ord = nullptr;
+        double* d_sc = nullptr;
+        HM_CUDA(cudaMallocAsync((void**)&d_ord, (size_t)r * 4, C.st));
+        HM_CUDA(cudaMallocAsync((void**)&d_sc, (size_t)2 * r * 8, C.st));
+        HM_CUDA(cudaMemcpyAsync(d_ord, ord.data(), (size_t)r * 4, cudaMemcpyHostToDevice, C.st));
+        HM_CUDA(cudaMemcpyAsync(d_sc, sa.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
+        HM_CUDA(cudaMemcpyAsync(d_sc + r, sb.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
+        double2 *Pa = zalloc(C, K * r), *Pb = zalloc(C, K * r);
+        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Pa, WJ, K, d_ord, d_sc, r);
+        HM_LAUNCHED();
+        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Pb, WJ, K, d_ord, d_sc + r, r);
+        HM_LAUNCHED();
+        HM_CUDA(cudaGetLastError());
+        C.launches += 2;
+        double2 *Lb = zalloc(C, K * r), *TU = zalloc(C, K * r), *TV = zalloc(C, K * r);
+        HM_CUDA(cudaMemsetAsync(Lb, 0, (size_t)K * r * 16, C.st));
+        HM_CUDA(cudaMemsetAsync(TU, 0, (size_t)K * r * 16, C.st));
+        HM_CUDA(cudaMemsetAsync(TV, 0, (size_t)K * r * 16, C.st));
+        gemm(C, Lb, W, Pb, K, r, K, K, K, K, 1, 0, ONE);   // W^H P_r S^{-3/2} = L_r S^{-1/2}
+        gemm(C, TU, GV, Lb, K, r, K, K, K, K, 1, 0, ONE);  // R_V^H L_r S^{-1/2}
+        gemm(C, TV, GU, Pa, K, r, K, K, K, K, 1, 0, ONE);  // R_U^H P_r S^{-1/2}
+        x->U = zalloc(C, m * r);
+        x->V = zalloc(C, n * r);
+        HM_CUDA(cudaMemsetAsync(x->U, 0, (size_t)m * r * 16, C.st));
+        HM_CUDA(cudaMemsetAsync(x->V, 0, (size_t)n * r * 16, C.st));
+        gemm(C, x->U, U2, TU, m, r, K, m, K, m, 0, 0, ONE);
+        gemm(C, x->V, V2, TV, n, r, K, n, K, n, 0, 0, ONE);
+        zfree(C, Pa);
+        zfree(C, Pb);
+        zfree(C, Lb);
+        zfree(C, TU);
+        zfree(C, TV);
+        HM_CUDA(cudaFreeAsync(d_ord, C.st));
+        HM_CUDA(cudaFreeAsync(d_sc, C.st));
+    }
+    HM_CUDA(cudaFreeAsync(s, C.st));
+    zfree(C, U2);
+    zfree(C, V2);
+    zfree(C, GU);
+    zfree(C, GV);
+    zfree(C, W);
+    zfree(C, WJ);
 }
 
 // Largest side up to which a dense matrix is recompressed exactly (QR of D, or
@@ -1023,7 +1383,8 @@ void hlu_factor(hm_matrix* h, double eps_lu, cudaStream_t st) {
         int flag = 0;
         HM_CUDA(cudaMemcpyAsync(&flag, C.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaStreamSynchronize(st));
-        if (flag) hm_throw(HM_ERR_NUMERIC, "H-LU: zero pivot or unconverged SVD");
+        if (flag & 1) hm_throw(HM_ERR_NUMERIC, "H-LU: zero pivot in a dense diagonal leaf");
+        if (flag & 2) hm_throw(HM_ERR_NUMERIC, "H-LU: one-sided Jacobi not converged in 80 sweeps");
     } catch (...) {
         cudaStreamSynchronize(st);
         free_tree(C, root);
