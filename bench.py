@@ -416,6 +416,41 @@ def run_gpu(args, wl, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_hlu(nc):
+    """The H-LU direct solver (Sec. 3.2) on the n_c-point sphere, U kernel at
+    omega = 4, eps = eps_LU = 1e-4, leaf 32: host wall time of the
+    factorisation (its recursion is driven from the host), of one solve, and
+    the residual of that solve with the H-matrix product."""
+    import torch
+    from paper_1706_09384_gb300 import hm, inputs
+    hm.lib()
+    pts = inputs.fibonacci_sphere(nc)
+    w = np.full(nc, 4 * np.pi / nc)
+    H = hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", 1e-4, 3.0, 32,
+                         opts=hm.hm_opts_default(weights=w))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.lu_factor(1e-4)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    b = torch.from_numpy(inputs.random_rhs(3 * nc, seed=1)).cuda()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    x = H.lu_solve(b)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    relres = (torch.linalg.vector_norm(b - H.matvec(x)) / torch.linalg.vector_norm(b)).item()
+    sec, entries, launches = H.lu_info()
+    st = H.stats()
+    print(json.dumps({
+        "metric": "H-LU factorisation time (Sec. 3.2)", "value": t1 - t0, "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "dtype": "f64c", "data": "synthetic",
+        "config": {"workload": "sphere%d_U_hlu" % nc, "n_c": nc, "kernel": "U", "omega": 4.0,
+                   "leaf": 32, "eta": 3.0, "eps": 1e-4, "eps_lu": 1e-4},
+        "solve_s": t3 - t2, "relres": relres, "gpu_launches": launches,
+        "lu_entries": entries, "N_s": st["N_s"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,7 +465,12 @@ def main():
                          "operator for the refinement residuals; plain: FP32 storage")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the untimed plain-form comparison run")
+    ap.add_argument("--hlu", type=int, default=0,
+                    help="instead of the step: time the H-LU direct solver on this many points")
     args = ap.parse_args()
+    if args.hlu:
+        run_hlu(args.hlu)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))
