@@ -588,6 +588,136 @@ __global__ void __launch_bounds__(JT) hz_gram_core_kernel(double2* GU, double2* 
     }
 }
 
+// Householder QR with column pivoting of W (K x K; Businger and Golub 1965):
+// W Pi = Q R, the column of largest remaining norm first (ties: lowest index),
+// norms recomputed at each step.  Writes R^H (K x K) and perm (Pi's column k
+// is e_perm[k]); Q is not formed; the reduction stops once the largest
+// remaining column is at the rounding level of W.  One CTA; A is a K x K
+// workspace.  R^H is
+// the preconditioned start of the one-sided Jacobi (Drmac and Veselic 2008):
+// its columns are close to orthogonal, so far fewer sweeps are needed.
+constexpr int64_t QP_MAX = 1024;
+__global__ void __launch_bounds__(JT) hz_qrcp_kernel(const double2* W0, double2* A, double2* RH, int32_t* perm,
+                                                     int64_t K) {
+    __shared__ double cn[QP_MAX];
+    __shared__ double2 alph[QP_MAX];
+    __shared__ double redv[JT / 32];
+    __shared__ int redi[JT / 32];
+    __shared__ int s_piv;
+    __shared__ double red[JT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double f2 = 0.0;
+    for (int64_t e = tid; e < K * K; e += JT) {
+        const double2 v = W0[e];
+        A[e] = v;
+        f2 += v.x * v.x + v.y * v.y;
+    }
+    for (int64_t j = tid; j < K; j += JT) perm[j] = (int32_t)j;
+    f2 = hz_block_sum<JT>(f2, red);
+    // columns at the rounding level of W are not reduced further: their
+    // reflectors would divide by underflowing norms, and their part of R
+    // (<= K u ||W||_F) lies below any truncation
+    const double negl = ((double)K * 0x1.0p-53) * ((double)K * 0x1.0p-53) * f2;
+    int64_t kstop = K;
+    for (int64_t k = 0; k < K; ++k) {
+        for (int64_t j = k + warp; j < K; j += JT / 32) {  // norms of the trailing columns, rows k..K-1
+            double a = 0.0;
+            for (int64_t r = k + lane; r < K; r += 32) a += A[r + j * K].x * A[r + j * K].x + A[r + j * K].y * A[r + j * K].y;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) cn[j] = a;
+        }
+        __syncthreads();
+        double bv = -1.0;
+        int bi = (int)k;
+        for (int64_t j = k + tid; j < K; j += JT)
+            if (cn[j] > bv) {
+                bv = cn[j];
+                bi = (int)j;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            redv[warp] = bv;
+            redi[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double v = redv[0];
+            int i = redi[0];
+            for (int w = 1; w < JT / 32; ++w)
+                if (redv[w] > v || (redv[w] == v && redi[w] < i)) {
+                    v = redv[w];
+                    i = redi[w];
+                }
+            s_piv = i;
+        }
+        __syncthreads();
+        const int64_t p = s_piv;
+        if (p != k) {
+            for (int64_t r = tid; r < K; r += JT) {
+                const double2 t = A[r + k * K];
+                A[r + k * K] = A[r + p * K];
+                A[r + p * K] = t;
+            }
+            if (tid == 0) {
+                const int32_t t = perm[k];
+                perm[k] = perm[p];
+                perm[p] = t;
+                const double c = cn[k];
+                cn[k] = cn[p];
+                cn[p] = c;
+            }
+        }
+        __syncthreads();
+        double2* x = A + k * K;
+        const double nx2 = cn[k];  // the largest remaining column (uniform)
+        if (!(nx2 > negl)) {
+            kstop = k;
+            break;
+        }
+        double tau = 0.0;
+        double2 alpha = make_double2(0.0, 0.0);
+        {
+            const double2 x0 = x[k];
+            const double a0 = sqrt(x0.x * x0.x + x0.y * x0.y), nx = sqrt(nx2);
+            const double2 ph = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
+            alpha = make_double2(-ph.x * nx, -ph.y * nx);  // H x = alpha e_1
+            const double2 v0 = make_double2(x0.x - alpha.x, x0.y - alpha.y);
+            tau = 2.0 / (nx2 - a0 * a0 + (v0.x * v0.x + v0.y * v0.y));
+            if (!(tau < 1e300)) tau = 0.0;
+            __syncthreads();
+            if (tid == 0 && tau != 0.0) x[k] = v0;
+        }
+        if (tid == 0) alph[k] = tau != 0.0 ? alpha : make_double2(0.0, 0.0);
+        __syncthreads();
+        if (tau != 0.0) hz_reflect<JT>(x, tau, k, K, A, K, k + 1, K);
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < K * K; e += JT) {  // RH(c, r) = conj(R(r, c)); rows from kstop on are zero
+        const int64_t r = e % K, c = e / K;
+        const double2 v = r >= kstop ? make_double2(0.0, 0.0)
+                                     : (r < c ? A[r + c * K] : (r == c ? alph[r] : make_double2(0.0, 0.0)));
+        RH[c + r * K] = zconj(v);
+    }
+}
+
+// dst[perm[i], q] = src[i, idx[q]] * sc[q]  (K x r; the rows go back through the pivoting)
+__global__ void hz_select_perm_kernel(double2* dst, const double2* src, int64_t rows, const int32_t* idx,
+                                      const double* sc, int64_t r, const int32_t* perm) {
+    for (int64_t e = blockIdx.x * (int64_t)HT + threadIdx.x; e < rows * r; e += (int64_t)gridDim.x * HT) {
+        const int64_t i = e % rows, q = e / rows;
+        const double2 v = src[i + (int64_t)idx[q] * rows];
+        dst[perm[i] + q * rows] = make_double2(v.x * sc[q], v.y * sc[q]);
+    }
+}
+
 // dst[:, q] = src[:, idx[q]] * sc[q]  (rows x r)
 __global__ void hz_select_kernel(double2* dst, const double2* src, int64_t rows, const int32_t* idx,
                                  const double* sc, int64_t r) {
@@ -856,11 +986,11 @@ void densify(Ctx& C, const HNode* x, double2* D, int64_t ldd, double2 alpha) {
 // discarded singular values, together with an error rho2 already committed
 // (squared Frobenius norm), stay within eps_LU of the whole.
 // One-sided Jacobi of W (K x K) -> WJ = P S, s: a cluster of CJ CTAs for K up
-// to CJ_MAX, else one CTA on global memory.  Rotations stop at
-// max(K u, 1e-3 eps_LU) of orthogonality, far below what the truncation at
-// eps_LU can see.
+// to CJ_MAX, else one CTA on global memory.  Rotations stop at max(K u, 1e-15)
+// of orthogonality: the Gram form divides by the singular values it keeps
+// (P_r = W L_r S_r^-1), so a looser stop would be amplified by up to 1/eps_LU.
 void jacobi(Ctx& C, const double2* W, double2* WJ, int64_t K, double* s) {
-    const double tol_min = std::max(1e-15, 1e-3 * C.eps);
+    const double tol_min = 1e-15;
     if (K <= CJ_MAX) {
         const size_t sm = (size_t)K * K * sizeof(double2);
         if (sm > 40 * 1024)
@@ -873,6 +1003,96 @@ void jacobi(Ctx& C, const double2* W, double2* WJ, int64_t K, double* s) {
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
     C.launches++;
+}
+
+// SVD of the recompression core W (K x K) = P S L^H: the one-sided Jacobi runs
+// on R^H of the pivoted QR W Pi = Q R, whose columns converge to X S with
+// R^H = X S Y^H, so L = Pi X (for K above QP_MAX: on W^H, L = X).  Ranks by the
+// truncation rule with rho2 already spent; ord sorts the singular values.
+struct CoreSvd {
+    double2* XS = nullptr;  // K x K, columns X_j s_j
+    int32_t* perm = nullptr;
+    std::vector<double> hs;
+    std::vector<int32_t> ord;
+    int64_t r = 0;
+};
+
+void core_svd(Ctx& C, const double2* W, int64_t K, double rho2, CoreSvd& out) {
+    double2* RH = zalloc(C, K * K);
+    HM_CUDA(cudaMallocAsync((void**)&out.perm, (size_t)K * 4, C.st));
+    if (K <= QP_MAX) {
+        double2* A = zalloc(C, K * K);
+        hz_qrcp_kernel<<<1, JT, 0, C.st>>>(W, A, RH, out.perm, K);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+        C.launches++;
+        zfree(C, A);
+    } else {
+        adjoint(C, RH, K, W, K, K, K);
+        std::vector<int32_t> id(K);
+        for (int64_t i = 0; i < K; ++i) id[i] = (int32_t)i;
+        HM_CUDA(cudaMemcpyAsync(out.perm, id.data(), (size_t)K * 4, cudaMemcpyHostToDevice, C.st));
+        HM_CUDA(cudaStreamSynchronize(C.st));
+    }
+    out.XS = zalloc(C, K * K);
+    double* s = nullptr;
+    HM_CUDA(cudaMallocAsync((void**)&s, (size_t)K * 8, C.st));
+    jacobi(C, RH, out.XS, K, s);
+    out.hs.assign(K, 0.0);
+    HM_CUDA(cudaMemcpyAsync(out.hs.data(), s, (size_t)K * 8, cudaMemcpyDeviceToHost, C.st));
+    HM_CUDA(cudaStreamSynchronize(C.st));
+    HM_CUDA(cudaFreeAsync(s, C.st));
+    zfree(C, RH);
+    const std::vector<double>& hs = out.hs;
+    for (int64_t i = 0; i < K; ++i)
+        if (!std::isfinite(hs[i])) hm_throw(HM_ERR_NUMERIC, "H-LU: non-finite singular value");
+    out.ord.resize(K);
+    for (int64_t i = 0; i < K; ++i) out.ord[i] = (int32_t)i;
+    std::stable_sort(out.ord.begin(), out.ord.end(), [&](int32_t a, int32_t b) { return hs[a] > hs[b]; });
+    double tot = rho2;
+    for (int64_t i = 0; i < K; ++i) tot += hs[i] * hs[i];
+    int64_t r = K;
+    double tail = rho2;
+    for (int64_t i = K - 1; i >= 0; --i) {
+        const double sv = hs[out.ord[i]];
+        if (std::sqrt(tail + sv * sv) <= C.eps * std::sqrt(tot)) {
+            tail += sv * sv;
+            r = i;
+        } else {
+            break;
+        }
+    }
+    while (r > 0 && !(hs[out.ord[r - 1]] > 0.0)) --r;
+    out.r = r;
+}
+
+void core_free(Ctx& C, CoreSvd& cs) {
+    zfree(C, cs.XS);
+    if (cs.perm) HM_CUDA(cudaFreeAsync(cs.perm, C.st));
+    cs.XS = nullptr;
+    cs.perm = nullptr;
+}
+
+// L_r S_r^e (K x r) from the core's X S: column q is (X S)_ord[q] s_ord[q]^(e - 1),
+// its rows put back through Pi
+double2* l_scaled(Ctx& C, const CoreSvd& cs, int64_t K, double e) {
+    const int64_t r = cs.r;
+    std::vector<double> sc(r);
+    for (int64_t q = 0; q < r; ++q) sc[q] = std::pow(cs.hs[cs.ord[q]], e - 1.0);
+    int32_t* d_ord = nullptr;
+    double* d_sc = nullptr;
+    HM_CUDA(cudaMallocAsync((void**)&d_ord, (size_t)r * 4, C.st));
+    HM_CUDA(cudaMallocAsync((void**)&d_sc, (size_t)r * 8, C.st));
+    HM_CUDA(cudaMemcpyAsync(d_ord, cs.ord.data(), (size_t)r * 4, cudaMemcpyHostToDevice, C.st));
+    HM_CUDA(cudaMemcpyAsync(d_sc, sc.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
+    double2* L = zalloc(C, K * r);
+    hz_select_perm_kernel<<<grid_for(K * r), HT, 0, C.st>>>(L, cs.XS, K, d_ord, d_sc, r, cs.perm);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+    C.launches++;
+    HM_CUDA(cudaFreeAsync(d_ord, C.st));
+    HM_CUDA(cudaFreeAsync(d_sc, C.st));
+    return L;
 }
 
 // eps_LU from which the Gram form below replaces the Householder QR
@@ -897,78 +1117,32 @@ void truncate(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double rho2
     double2* W = zalloc(C, K * K);
     HM_CUDA(cudaMemsetAsync(W, 0, (size_t)K * K * 16, C.st));
     gemm(C, W, RU, RV, K, K, K, K, K, K, 0, 1, ONE);  // R_U R_V^H
-    double2* WJ = zalloc(C, K * K);
-    double* s = nullptr;
-    HM_CUDA(cudaMallocAsync((void**)&s, (size_t)K * 8, C.st));
-    jacobi(C, W, WJ, K, s);
-    std::vector<double> hs(K);
-    HM_CUDA(cudaMemcpyAsync(hs.data(), s, (size_t)K * 8, cudaMemcpyDeviceToHost, C.st));
-    HM_CUDA(cudaStreamSynchronize(C.st));
-    for (int64_t i = 0; i < K; ++i)
-        if (!std::isfinite(hs[i]))
-            hm_throw(HM_ERR_NUMERIC, "H-LU: non-finite singular value (Householder recompression)");
-    std::vector<int32_t> ord(K);
-    for (int64_t i = 0; i < K; ++i) ord[i] = (int32_t)i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hs[a] > hs[b]; });
-    double tot = rho2;
-    for (int64_t i = 0; i < K; ++i) tot += hs[i] * hs[i];
-    int64_t r = K;
-    double tail = rho2;
-    for (int64_t i = K - 1; i >= 0; --i) {
-        const double sv = hs[ord[i]];
-        if (std::sqrt(tail + sv * sv) <= C.eps * std::sqrt(tot)) {
-            tail += sv * sv;
-            r = i;
-        } else {
-            break;
-        }
-    }
-    while (r > 0 && !(hs[ord[r - 1]] > 0.0)) --r;
+    CoreSvd cs;
+    core_svd(C, W, K, rho2, cs);
     zfree(C, x->U);
     zfree(C, x->V);
     x->U = x->V = nullptr;
+    const int64_t r = cs.r;
     x->k = r;
     if (r > 0) {
-        // W = P S L^H: U = Q_U P_r S_r^{1/2}, V = Q_V L_r S_r^{1/2} = Q_V W^H P_r S_r^{-1/2}
-        std::vector<double> su(r), sp(r);
-        for (int64_t q = 0; q < r; ++q) {
-            const double sq = hs[ord[q]];
-            su[q] = 1.0 / std::sqrt(sq);        // (P_q s_q) s_q^{-1/2}
-            sp[q] = 1.0 / (sq * std::sqrt(sq));  // (P_q s_q) s_q^{-3/2}
-        }
-        int32_t* d_ord = nullptr;
-        double* d_sc = nullptr;
-        HM_CUDA(cudaMallocAsync((void**)&d_ord, (size_t)r * 4, C.st));
-        HM_CUDA(cudaMallocAsync((void**)&d_sc, (size_t)2 * r * 8, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_ord, ord.data(), (size_t)r * 4, cudaMemcpyHostToDevice, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_sc, su.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_sc + r, sp.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
-        double2* Wp = zalloc(C, K * r);
-        double2* Pp = zalloc(C, K * r);
-        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Wp, WJ, K, d_ord, d_sc, r);
-        HM_LAUNCHED();
-        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Pp, WJ, K, d_ord, d_sc + r, r);
-        HM_LAUNCHED();
-        HM_CUDA(cudaGetLastError());
-        C.launches += 2;
-        double2* Lp = zalloc(C, K * r);
-        HM_CUDA(cudaMemsetAsync(Lp, 0, (size_t)K * r * 16, C.st));
-        gemm(C, Lp, W, Pp, K, r, K, K, K, K, 1, 0, ONE);  // W^H P_r S_r^{-1/2}
+        // U = Q_U P_r S_r^{1/2} = Q_U W L_r S_r^{-1/2},  V = Q_V L_r S_r^{1/2}
+        double2* Lh = l_scaled(C, cs, K, 0.5);
+        double2* Lm = l_scaled(C, cs, K, -0.5);
+        double2* WL = zalloc(C, K * r);
+        HM_CUDA(cudaMemsetAsync(WL, 0, (size_t)K * r * 16, C.st));
+        gemm(C, WL, W, Lm, K, r, K, K, K, K, 0, 0, ONE);
         x->U = zalloc(C, m * r);
         x->V = zalloc(C, n * r);
         HM_CUDA(cudaMemsetAsync(x->U, 0, (size_t)m * r * 16, C.st));
         HM_CUDA(cudaMemsetAsync(x->V, 0, (size_t)n * r * 16, C.st));
-        gemm(C, x->U, QU, Wp, m, r, K, m, K, m, 0, 0, ONE);
-        gemm(C, x->V, QV, Lp, n, r, K, n, K, n, 0, 0, ONE);
-        zfree(C, Wp);
-        zfree(C, Pp);
-        zfree(C, Lp);
-        HM_CUDA(cudaFreeAsync(d_ord, C.st));
-        HM_CUDA(cudaFreeAsync(d_sc, C.st));
+        gemm(C, x->U, QU, WL, m, r, K, m, K, m, 0, 0, ONE);
+        gemm(C, x->V, QV, Lh, n, r, K, n, K, n, 0, 0, ONE);
+        zfree(C, Lh);
+        zfree(C, Lm);
+        zfree(C, WL);
     }
-    HM_CUDA(cudaFreeAsync(s, C.st));
+    core_free(C, cs);
     zfree(C, W);
-    zfree(C, WJ);
     zfree(C, QU);
     zfree(C, RU);
     zfree(C, QV);
@@ -992,90 +1166,46 @@ void truncate_gram(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double
     HM_CUDA(cudaMemsetAsync(GV, 0, (size_t)K * K * 16, C.st));
     gemm(C, GU, U2, U2, K, K, m, m, m, K, 1, 0, ONE);
     gemm(C, GV, V2, V2, K, K, n, n, n, K, 1, 0, ONE);
-    double2 *W = zalloc(C, K * K), *WJ = zalloc(C, K * K);
-    double* s = nullptr;
-    HM_CUDA(cudaMallocAsync((void**)&s, (size_t)K * 8, C.st));
+    double2* W = zalloc(C, K * K);
     hz_gram_core_kernel<<<1, JT, 0, C.st>>>(GU, GV, W, K);
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
     C.launches++;
-    jacobi(C, W, WJ, K, s);
-    std::vector<double> hs(K);
-    HM_CUDA(cudaMemcpyAsync(hs.data(), s, (size_t)K * 8, cudaMemcpyDeviceToHost, C.st));
-    HM_CUDA(cudaStreamSynchronize(C.st));
-    for (int64_t i = 0; i < K; ++i)
-        if (!std::isfinite(hs[i])) hm_throw(HM_ERR_NUMERIC, "H-LU: non-finite singular value (Gram recompression)");
-    std::vector<int32_t> ord(K);
-    for (int64_t i = 0; i < K; ++i) ord[i] = (int32_t)i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return hs[a] > hs[b]; });
-    double tot = rho2;
-    for (int64_t i = 0; i < K; ++i) tot += hs[i] * hs[i];
-    int64_t r = K;
-    double tail = rho2;
-    for (int64_t i = K - 1; i >= 0; --i) {
-        const double sv = hs[ord[i]];
-        if (std::sqrt(tail + sv * sv) <= C.eps * std::sqrt(tot)) {
-            tail += sv * sv;
-            r = i;
-        } else {
-            break;
-        }
-    }
-    while (r > 0 && !(hs[ord[r - 1]] > 0.0)) --r;
+    CoreSvd cs;
+    core_svd(C, W, K, rho2, cs);
     zfree(C, x->U);
     zfree(C, x->V);
     x->U = x->V = nullptr;
+    const int64_t r = cs.r;
     x->k = r;
     if (r > 0) {
-        // WJ_q = P_q s_q: Pa = P_r S_r^{-1/2}, Pb = P_r S_r^{-3/2}
-        std::vector<double> sa(r), sb(r);
-        for (int64_t q = 0; q < r; ++q) {
-            const double sq = hs[ord[q]];
-            sa[q] = 1.0 / (sq * std::sqrt(sq));
-            sb[q] = sa[q] / sq;
-        }
-        int32_t* d_ord = nullptr;
-        double* d_sc = nullptr;
-        HM_CUDA(cudaMallocAsync((void**)&d_ord, (size_t)r * 4, C.st));
-        HM_CUDA(cudaMallocAsync((void**)&d_sc, (size_t)2 * r * 8, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_ord, ord.data(), (size_t)r * 4, cudaMemcpyHostToDevice, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_sc, sa.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
-        HM_CUDA(cudaMemcpyAsync(d_sc + r, sb.data(), (size_t)r * 8, cudaMemcpyHostToDevice, C.st));
-        double2 *Pa = zalloc(C, K * r), *Pb = zalloc(C, K * r);
-        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Pa, WJ, K, d_ord, d_sc, r);
-        HM_LAUNCHED();
-        hz_select_kernel<<<grid_for(K * r), HT, 0, C.st>>>(Pb, WJ, K, d_ord, d_sc + r, r);
-        HM_LAUNCHED();
-        HM_CUDA(cudaGetLastError());
-        C.launches += 2;
-        double2 *Lb = zalloc(C, K * r), *TU = zalloc(C, K * r), *TV = zalloc(C, K * r);
-        HM_CUDA(cudaMemsetAsync(Lb, 0, (size_t)K * r * 16, C.st));
+        double2* Lm = l_scaled(C, cs, K, -0.5);   // L_r S_r^{-1/2}
+        double2* Lm3 = l_scaled(C, cs, K, -1.5);  // L_r S_r^{-3/2}
+        double2 *WL = zalloc(C, K * r), *TU = zalloc(C, K * r), *TV = zalloc(C, K * r);
+        HM_CUDA(cudaMemsetAsync(WL, 0, (size_t)K * r * 16, C.st));
         HM_CUDA(cudaMemsetAsync(TU, 0, (size_t)K * r * 16, C.st));
         HM_CUDA(cudaMemsetAsync(TV, 0, (size_t)K * r * 16, C.st));
-        gemm(C, Lb, W, Pb, K, r, K, K, K, K, 1, 0, ONE);   // W^H P_r S^{-3/2} = L_r S^{-1/2}
-        gemm(C, TU, GV, Lb, K, r, K, K, K, K, 1, 0, ONE);  // R_V^H L_r S^{-1/2}
-        gemm(C, TV, GU, Pa, K, r, K, K, K, K, 1, 0, ONE);  // R_U^H P_r S^{-1/2}
+        gemm(C, WL, W, Lm3, K, r, K, K, K, K, 0, 0, ONE);  // W L_r S^{-3/2} = P_r S^{-1/2}
+        gemm(C, TU, GV, Lm, K, r, K, K, K, K, 1, 0, ONE);  // R_V^H L_r S^{-1/2}
+        gemm(C, TV, GU, WL, K, r, K, K, K, K, 1, 0, ONE);  // R_U^H P_r S^{-1/2}
         x->U = zalloc(C, m * r);
         x->V = zalloc(C, n * r);
         HM_CUDA(cudaMemsetAsync(x->U, 0, (size_t)m * r * 16, C.st));
         HM_CUDA(cudaMemsetAsync(x->V, 0, (size_t)n * r * 16, C.st));
         gemm(C, x->U, U2, TU, m, r, K, m, K, m, 0, 0, ONE);
         gemm(C, x->V, V2, TV, n, r, K, n, K, n, 0, 0, ONE);
-        zfree(C, Pa);
-        zfree(C, Pb);
-        zfree(C, Lb);
+        zfree(C, Lm);
+        zfree(C, Lm3);
+        zfree(C, WL);
         zfree(C, TU);
         zfree(C, TV);
-        HM_CUDA(cudaFreeAsync(d_ord, C.st));
-        HM_CUDA(cudaFreeAsync(d_sc, C.st));
     }
-    HM_CUDA(cudaFreeAsync(s, C.st));
+    core_free(C, cs);
     zfree(C, U2);
     zfree(C, V2);
     zfree(C, GU);
     zfree(C, GV);
     zfree(C, W);
-    zfree(C, WJ);
 }
 
 // Largest side up to which a dense matrix is recompressed exactly (QR of D, or
