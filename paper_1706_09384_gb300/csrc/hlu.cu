@@ -310,19 +310,18 @@ __global__ void __launch_bounds__(QT) hz_qr_kernel(double2* W, int64_t M, int64_
 
 // One-sided Jacobi (Hestenes) on W0 (K x K): WJ = W0 J with mutually
 // orthogonal columns P_j s_j, s_j = |WJ_j|; J (the right singular vectors) is
-// not kept: the caller forms W0^H P instead.  Round-robin pairs, a warp per
-// pair; a pair is rotated when |gamma| > tol sqrt(alpha beta), tol = max(1e-15,
-// K u), and neither column is negligible (squared norm above (K u)^2
-// ||W||_F^2).  One CTA; W in shared memory up to K = JS_MAX, else in WJ.
+// not kept.  Round-robin pairs, a warp per pair; a pair is rotated when
+// |gamma| > tol sqrt(alpha beta), tol = max(tol_min, K u), and neither column
+// is negligible (squared norm above (K u)^2 ||W||_F^2).  One CTA working in WJ
+// (global memory, L2-resident): the form for cores too large for the cluster
+// kernel below.
 constexpr int JT = 512;
-constexpr int64_t JS_MAX = 112;
 constexpr int64_t JS_MAX_CHOL = 1024;  // Gram-form recompression: K up to here
-__device__ void hz_jacobi(const double2* W0, double2* WJ, int64_t K, double* s, int* unconverged,
-                          double2* hz_w, double tol_min) {
+__global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double2* WJ, int64_t K, double* s,
+                                                       int* unconverged, double tol_min) {
     __shared__ int s_conv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool in_smem = K <= JS_MAX;
-    double2* W = in_smem ? hz_w : WJ;
+    double2* W = WJ;
     __shared__ double red[JT / 32];
     double f2 = 0.0;
     for (int64_t e = threadIdx.x; e < K * K; e += JT) {
@@ -400,14 +399,6 @@ __device__ void hz_jacobi(const double2* W0, double2* WJ, int64_t K, double* s, 
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (lane == 0) s[j] = sqrt(a);
     }
-    if (in_smem)
-        for (int64_t e = threadIdx.x; e < K * K; e += JT) WJ[e] = W[e];
-}
-
-__global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double2* WJ, int64_t K, double* s,
-                                                       int* unconverged, double tol_min) {
-    extern __shared__ double2 hz_w[];
-    hz_jacobi(W0, WJ, K, s, unconverged, hz_w, tol_min);
 }
 
 // The same one-sided Jacobi spread over a thread-block cluster of CJ CTAs (one
@@ -715,16 +706,6 @@ __global__ void hz_select_perm_kernel(double2* dst, const double2* src, int64_t 
         const int64_t i = e % rows, q = e / rows;
         const double2 v = src[i + (int64_t)idx[q] * rows];
         dst[perm[i] + q * rows] = make_double2(v.x * sc[q], v.y * sc[q]);
-    }
-}
-
-// dst[:, q] = src[:, idx[q]] * sc[q]  (rows x r)
-__global__ void hz_select_kernel(double2* dst, const double2* src, int64_t rows, const int32_t* idx,
-                                 const double* sc, int64_t r) {
-    for (int64_t e = blockIdx.x * (int64_t)HT + threadIdx.x; e < rows * r; e += (int64_t)gridDim.x * HT) {
-        const int64_t i = e % rows, q = e / rows;
-        const double2 v = src[i + (int64_t)idx[q] * rows];
-        dst[e] = make_double2(v.x * sc[q], v.y * sc[q]);
     }
 }
 

@@ -124,3 +124,33 @@ def test_hlu_needs_factors(hm):
         H.lu_solve(cuda(inputs.random_rhs(3 * NC, seed=1)))
     with pytest.raises(hm.HmError):
         H.lu_factor(0.0)
+
+
+def test_hlu_storage_rhs_and_refactor(hm, oracle):
+    """The factorisation reads the FP32 copy of the stored operator, which a
+    BF16-storage handle keeps as well: both handles give the same solution.
+    Several right-hand sides at once equal the one-by-one solves; a second
+    lu_factor replaces the factors (a smaller eps_LU, a smaller residual); the
+    caller's output buffer is filled in place."""
+    pts, nrm, w, pb = problem(oracle, "U")
+    b = inputs.random_rhs(3 * NC, 3, seed=11)
+    H32 = hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", 1e-6, 3.0, 16,
+                           opts=hm.hm_opts_default(weights=w))
+    H16 = hm.HMatrix.build(pts, None, 1.0, 2.0, 1.0, 4.0, "U", 1e-6, 3.0, 16,
+                           opts=hm.hm_opts_default(weights=w, storage=hm.HM_STORE_BF16))
+    H32.lu_factor(1e-4)
+    H16.lu_factor(1e-4)
+    x32 = H32.lu_solve(cuda(b)).cpu().numpy()
+    x16 = H16.lu_solve(cuda(b)).cpu().numpy()
+    assert np.linalg.norm(x16 - x32) <= 1e-12 * np.linalg.norm(x32)
+    for j in range(3):
+        xj = H32.lu_solve(cuda(b[:, j])).cpu().numpy()
+        assert np.linalg.norm(xj - x32[:, j]) <= 1e-13 * np.linalg.norm(xj)
+    res = lambda H, x, j: np.linalg.norm(b[:, j] - H.matvec(cuda(x)).cpu().numpy()) / np.linalg.norm(b[:, j])  # noqa: E731
+    r4 = res(H32, x32[:, 0], 0)
+    H32.lu_factor(1e-8)
+    out = torch.empty(3 * NC, dtype=torch.complex128, device="cuda")
+    ret = H32.lu_solve(cuda(b[:, 0]), x=out)
+    assert ret.data_ptr() == out.data_ptr()
+    r8 = res(H32, out.cpu().numpy(), 0)
+    assert r8 < r4 and r8 <= 1e-5, (r4, r8)
