@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(QT) hz_qr_kernel(double2* W, int64_t M, int64_
 // kernel below.
 constexpr int JT = 512;
 constexpr int64_t JS_MAX_CHOL = 1024;  // Gram-form recompression: K up to here
+constexpr int64_t QP_SMEM = 112;       // one-CTA cores in shared memory (K x K complex) up to here
 __global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double2* WJ, int64_t K, double* s,
                                                        int* unconverged, double tol_min) {
     __shared__ int s_conv;
@@ -520,9 +521,14 @@ __global__ void __cluster_dims__(CJ, 1, 1) __launch_bounds__(CJT)
 // equilibrated (G' = D^-1 G D^-1, D = sqrt diag G), right-looking on the upper
 // triangle; a pivot of G' at or below 1e-13 zeroes its row of R (the
 // direction is below 3.2e-7 of its column norm).  R = R' D.
-__device__ void hz_chol_equil(double2* G, int64_t K, double* dsc) {
+__device__ void hz_chol_equil(double2* Gg, int64_t K, double* dsc, double2* sbuf) {
     __shared__ double s_piv;
     const int tid = threadIdx.x;
+    double2* G = sbuf ? sbuf : Gg;  // the factorisation runs in shared memory when it fits
+    if (sbuf) {
+        for (int64_t e = tid; e < K * K; e += JT) sbuf[e] = Gg[e];
+        __syncthreads();
+    }
     for (int64_t j = tid; j < K; j += JT) {
         const double d = G[j + j * K].x;
         dsc[j] = d > 1e-280 ? sqrt(d) : 0.0;  // a column whose squared norm underflows counts as zero
@@ -560,7 +566,7 @@ __device__ void hz_chol_equil(double2* G, int64_t K, double* dsc) {
     }
     for (int64_t e = tid; e < K * K; e += JT) {
         const int64_t p = e % K, c = e / K;
-        G[e] = p > c ? make_double2(0.0, 0.0) : make_double2(G[e].x * dsc[c], G[e].y * dsc[c]);
+        Gg[e] = p > c ? make_double2(0.0, 0.0) : make_double2(G[e].x * dsc[c], G[e].y * dsc[c]);
     }
     __syncthreads();
 }
@@ -568,9 +574,11 @@ __device__ void hz_chol_equil(double2* G, int64_t K, double* dsc) {
 // Core of the Gram-form recompression (one CTA): R_U, R_V from G_U = U^H U and
 // G_V = V^H V (in place) and W = R_U R_V^H.
 __global__ void __launch_bounds__(JT) hz_gram_core_kernel(double2* GU, double2* GV, double2* W, int64_t K) {
+    extern __shared__ double2 hz_ga[];
     __shared__ double dsc[JS_MAX_CHOL];
-    hz_chol_equil(GU, K, dsc);
-    hz_chol_equil(GV, K, dsc);
+    double2* sbuf = K <= QP_SMEM ? hz_ga : nullptr;
+    hz_chol_equil(GU, K, dsc, sbuf);
+    hz_chol_equil(GV, K, dsc, sbuf);
     for (int64_t e = threadIdx.x; e < K * K; e += JT) {  // W_pc = sum_q RU_pq conj(RV_cq), q >= max(p, c)
         const int64_t p = e % K, c = e / K;
         double2 a = make_double2(0.0, 0.0);
@@ -583,13 +591,15 @@ __global__ void __launch_bounds__(JT) hz_gram_core_kernel(double2* GU, double2* 
 // W Pi = Q R, the column of largest remaining norm first (ties: lowest index),
 // norms recomputed at each step.  Writes R^H (K x K) and perm (Pi's column k
 // is e_perm[k]); Q is not formed; the reduction stops once the largest
-// remaining column is at the rounding level of W.  One CTA; A is a K x K
-// workspace.  R^H is
+// remaining column is at the rounding level of W.  One CTA working in shared
+// memory (K <= QP_SMEM; else in the K x K workspace Ag).  R^H is
 // the preconditioned start of the one-sided Jacobi (Drmac and Veselic 2008):
 // its columns are close to orthogonal, so far fewer sweeps are needed.
 constexpr int64_t QP_MAX = 1024;
-__global__ void __launch_bounds__(JT) hz_qrcp_kernel(const double2* W0, double2* A, double2* RH, int32_t* perm,
+__global__ void __launch_bounds__(JT) hz_qrcp_kernel(const double2* W0, double2* Ag, double2* RH, int32_t* perm,
                                                      int64_t K) {
+    extern __shared__ double2 hz_qa[];
+    double2* A = K <= QP_SMEM ? hz_qa : Ag;
     __shared__ double cn[QP_MAX];
     __shared__ double2 alph[QP_MAX];
     __shared__ double redv[JT / 32];
@@ -1002,8 +1012,12 @@ void core_svd(Ctx& C, const double2* W, int64_t K, double rho2, CoreSvd& out) {
     double2* RH = zalloc(C, K * K);
     HM_CUDA(cudaMallocAsync((void**)&out.perm, (size_t)K * 4, C.st));
     if (K <= QP_MAX) {
-        double2* A = zalloc(C, K * K);
-        hz_qrcp_kernel<<<1, JT, 0, C.st>>>(W, A, RH, out.perm, K);
+        const size_t sm = K <= QP_SMEM ? (size_t)K * K * sizeof(double2) : 0;
+        if (sm > 16 * 1024)
+            HM_CUDA(cudaFuncSetAttribute(hz_qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
+        double2* A = K <= QP_SMEM ? nullptr : zalloc(C, K * K);
+        hz_qrcp_kernel<<<1, JT, sm, C.st>>>(W, A, RH, out.perm, K);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
         C.launches++;
@@ -1148,7 +1162,11 @@ void truncate_gram(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double
     gemm(C, GU, U2, U2, K, K, m, m, m, K, 1, 0, ONE);
     gemm(C, GV, V2, V2, K, K, n, n, n, K, 1, 0, ONE);
     double2* W = zalloc(C, K * K);
-    hz_gram_core_kernel<<<1, JT, 0, C.st>>>(GU, GV, W, K);
+    const size_t gsm = K <= QP_SMEM ? (size_t)K * K * sizeof(double2) : 0;
+    if (gsm > 32 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(hz_gram_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
+    hz_gram_core_kernel<<<1, JT, gsm, C.st>>>(GU, GV, W, K);
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
     C.launches++;
