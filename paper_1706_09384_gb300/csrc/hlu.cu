@@ -20,7 +20,8 @@
 // computed exactly and counted in the eps_LU budget of the truncation, so the
 // result keeps the truncation bound without an SVD of the whole block.
 //
-// The recursion runs on the host and issues one FP64 kernel per dense
+// The recursion runs on the host (independent subtrees on up to 8 streams,
+// each driven by its own host thread) and issues one FP64 kernel per dense
 // operation: complex GEMM (32 x 32 tiles), LU of a dense diagonal leaf (one
 // CTA) and triangular solves with it (a warp per column), the Householder QR
 // and the one-sided Jacobi SVD of the recompression (one CTA each, the Jacobi
@@ -29,7 +30,9 @@
 #include <chrono>
 #include <cmath>
 #include <functional>
+#include <exception>
 #include <map>
+#include <thread>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -810,7 +813,60 @@ struct Ctx {
     int64_t launches = 0;
     uint64_t key = 0;  // test matrices drawn so far
     double* d_part = nullptr;  // hz_norm2_kernel partial sums
+    int spawn = 0;     // nested forks still allowed (2^spawn chains at most)
+    int device = 0;
 };
+
+// Runs f1 on C and f2 on a child context (its own stream and host thread)
+// when C may still fork, else one after the other on C.  The two must touch
+// disjoint blocks except for blocks both only read: the independent subtrees
+// of the factorisation (the two triangular solves of an LU step, the column
+// chains of a block triangular solve, the targets of a subdivided product).
+// The child stream starts after everything issued on C so far, and C waits
+// for the child before going on.
+template <class F1, class F2>
+void fork2(Ctx& C, F1&& f1, F2&& f2) {
+    if (C.spawn <= 0) {
+        f1(C);
+        f2(C);
+        return;
+    }
+    Ctx D{nullptr, C.eps, C.d_flag};
+    D.key = C.key * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull;  // a key space of its own
+    D.device = C.device;
+    const int sp = C.spawn;
+    C.spawn = D.spawn = sp - 1;
+    cudaEvent_t ev = nullptr;
+    HM_CUDA(cudaStreamCreateWithFlags(&D.st, cudaStreamNonBlocking));
+    HM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HM_CUDA(cudaEventRecord(ev, C.st));
+    HM_CUDA(cudaStreamWaitEvent(D.st, ev, 0));
+    std::exception_ptr e1, e2;
+    std::thread th([&] {
+        try {
+            HM_CUDA(cudaSetDevice(D.device));
+            f2(D);
+        } catch (...) {
+            e2 = std::current_exception();
+        }
+    });
+    try {
+        f1(C);
+    } catch (...) {
+        e1 = std::current_exception();
+    }
+    th.join();
+    C.spawn = sp;
+    C.launches += D.launches;
+    if (D.d_part) cudaFreeAsync(D.d_part, D.st);
+    cudaEventRecord(ev, D.st);
+    cudaStreamWaitEvent(C.st, ev, 0);
+    if (e1 || e2) cudaStreamSynchronize(D.st);  // nothing of the child may still run on an error
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(D.st);
+    if (e1) std::rethrow_exception(e1);
+    if (e2) std::rethrow_exception(e2);
+}
 
 double2* zalloc(Ctx& C, int64_t n) {
     double2* p = nullptr;
@@ -984,9 +1040,6 @@ void jacobi(Ctx& C, const double2* W, double2* WJ, int64_t K, double* s) {
     const double tol_min = 1e-15;
     if (K <= CJ_MAX) {
         const size_t sm = (size_t)K * K * sizeof(double2);
-        if (sm > 40 * 1024)
-            HM_CUDA(cudaFuncSetAttribute(hz_jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(CJ_MAX * CJ_MAX * sizeof(double2))));
         hz_jacobi_cluster_kernel<<<CJ, CJT, sm, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
     } else {
         hz_jacobi_kernel<<<1, JT, 0, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
@@ -1013,9 +1066,6 @@ void core_svd(Ctx& C, const double2* W, int64_t K, double rho2, CoreSvd& out) {
     HM_CUDA(cudaMallocAsync((void**)&out.perm, (size_t)K * 4, C.st));
     if (K <= QP_MAX) {
         const size_t sm = K <= QP_SMEM ? (size_t)K * K * sizeof(double2) : 0;
-        if (sm > 16 * 1024)
-            HM_CUDA(cudaFuncSetAttribute(hz_qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
         double2* A = K <= QP_SMEM ? nullptr : zalloc(C, K * K);
         hz_qrcp_kernel<<<1, JT, sm, C.st>>>(W, A, RH, out.perm, K);
         HM_CUDA(cudaGetLastError());
@@ -1163,9 +1213,6 @@ void truncate_gram(Ctx& C, HNode* x, double2* U2, double2* V2, int64_t K, double
     gemm(C, GV, V2, V2, K, K, n, n, n, K, 1, 0, ONE);
     double2* W = zalloc(C, K * K);
     const size_t gsm = K <= QP_SMEM ? (size_t)K * K * sizeof(double2) : 0;
-    if (gsm > 32 * 1024)
-        HM_CUDA(cudaFuncSetAttribute(hz_gram_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
     hz_gram_core_kernel<<<1, JT, gsm, C.st>>>(GU, GV, W, K);
     HM_CUDA(cudaGetLastError());
     HM_LAUNCHED();
@@ -1328,10 +1375,14 @@ void add_dense(Ctx& C, HNode* x, const double2* P, int64_t lp, double2 alpha) {
 
 // C -= A B
 void gemm_sub(Ctx& C, HNode* c, const HNode* a, const HNode* b) {
-    if (c->type == 2 && a->type == 2 && b->type == 2) {
-        for (int u = 0; u < 2; ++u)
-            for (int v = 0; v < 2; ++v)
-                for (int w = 0; w < 2; ++w) gemm_sub(C, c->ch[2 * u + v], a->ch[2 * u + w], b->ch[2 * w + v]);
+    if (c->type == 2 && a->type == 2 && b->type == 2) {  // four independent targets
+        auto target = [&](Ctx& X, int u, int v) {
+            for (int w = 0; w < 2; ++w) gemm_sub(X, c->ch[2 * u + v], a->ch[2 * u + w], b->ch[2 * w + v]);
+        };
+        auto row = [&](Ctx& X, int u) {
+            fork2(X, [&](Ctx& Y) { target(Y, u, 0); }, [&](Ctx& Y) { target(Y, u, 1); });
+        };
+        fork2(C, [&](Ctx& X) { row(X, 0); }, [&](Ctx& X) { row(X, 1); });
         return;
     }
     if (b->type == 1) {  // A (U_b V_b^H) = (A U_b) V_b^H
@@ -1372,11 +1423,12 @@ void gemm_sub(Ctx& C, HNode* c, const HNode* a, const HNode* b) {
 void trsm_l(Ctx& C, const HNode* L, HNode* X) {
     if (X->type == 0) return solve_l(C, L, X->D, X->m, X->n);
     if (X->type == 1) return solve_l(C, L, X->U, X->m, X->k);
-    for (int v = 0; v < 2; ++v) {
-        trsm_l(C, L->ch[0], X->ch[v]);
-        gemm_sub(C, X->ch[2 + v], L->ch[2], X->ch[v]);
-        trsm_l(C, L->ch[3], X->ch[2 + v]);
-    }
+    auto column = [&](Ctx& Y, int v) {  // the two block columns are independent
+        trsm_l(Y, L->ch[0], X->ch[v]);
+        gemm_sub(Y, X->ch[2 + v], L->ch[2], X->ch[v]);
+        trsm_l(Y, L->ch[3], X->ch[2 + v]);
+    };
+    fork2(C, [&](Ctx& Y) { column(Y, 0); }, [&](Ctx& Y) { column(Y, 1); });
 }
 
 void trsm_u(Ctx& C, const HNode* U, HNode* X) {
@@ -1389,11 +1441,12 @@ void trsm_u(Ctx& C, const HNode* U, HNode* X) {
         return;
     }
     if (X->type == 1) return solve_uh(C, U, X->V, X->n, X->k);
-    for (int u = 0; u < 2; ++u) {
-        trsm_u(C, U->ch[0], X->ch[2 * u]);
-        gemm_sub(C, X->ch[2 * u + 1], X->ch[2 * u], U->ch[1]);
-        trsm_u(C, U->ch[3], X->ch[2 * u + 1]);
-    }
+    auto row = [&](Ctx& Y, int u) {  // the two block rows are independent
+        trsm_u(Y, U->ch[0], X->ch[2 * u]);
+        gemm_sub(Y, X->ch[2 * u + 1], X->ch[2 * u], U->ch[1]);
+        trsm_u(Y, U->ch[3], X->ch[2 * u + 1]);
+    };
+    fork2(C, [&](Ctx& Y) { row(Y, 0); }, [&](Ctx& Y) { row(Y, 1); });
 }
 
 void lu(Ctx& C, HNode* x) {
@@ -1405,8 +1458,8 @@ void lu(Ctx& C, HNode* x) {
         return;
     }
     lu(C, x->ch[0]);                        // 1. A11 = L11 U11
-    trsm_l(C, x->ch[0], x->ch[1]);          // 2. U12 = L11^{-1} A12
-    trsm_u(C, x->ch[0], x->ch[2]);          // 3. L21 = A21 U11^{-1}
+    fork2(C, [&](Ctx& Y) { trsm_l(Y, x->ch[0], x->ch[1]); },   // 2. U12 = L11^{-1} A12
+          [&](Ctx& Y) { trsm_u(Y, x->ch[0], x->ch[2]); });     // 3. L21 = A21 U11^{-1}
     gemm_sub(C, x->ch[3], x->ch[2], x->ch[1]);  // 4. A22 - L21 U12 ...
     lu(C, x->ch[3]);                        //    = L22 U22
 }
@@ -1434,6 +1487,15 @@ void hlu_factor(hm_matrix* h, double eps_lu, cudaStream_t st) {
     hlu_release(h, st);
     const auto t0 = std::chrono::steady_clock::now();
     Ctx C{st, eps_lu, nullptr, 0};
+    C.spawn = 3;  // up to 8 independent chains in flight
+    HM_CUDA(cudaGetDevice(&C.device));
+    // shared-memory limits of the core kernels, set once before any chain forks
+    HM_CUDA(cudaFuncSetAttribute(hz_jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(CJ_MAX * CJ_MAX * sizeof(double2))));
+    HM_CUDA(cudaFuncSetAttribute(hz_qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
+    HM_CUDA(cudaFuncSetAttribute(hz_gram_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
     HM_CUDA(cudaMallocAsync((void**)&C.d_flag, sizeof(int), st));
     HM_CUDA(cudaMemsetAsync(C.d_flag, 0, sizeof(int), st));
     std::map<std::pair<int64_t, int64_t>, int64_t> bmap;
