@@ -1487,7 +1487,7 @@ void hlu_factor(hm_matrix* h, double eps_lu, cudaStream_t st) {
     hlu_release(h, st);
     const auto t0 = std::chrono::steady_clock::now();
     Ctx C{st, eps_lu, nullptr, 0};
-    C.spawn = 3;  // up to 8 independent chains in flight
+    C.spawn = 4;  // up to 16 independent chains in flight
     HM_CUDA(cudaGetDevice(&C.device));
     // shared-memory limits of the core kernels, set once before any chain forks
     HM_CUDA(cudaFuncSetAttribute(hz_jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
