@@ -210,9 +210,17 @@ hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double*
  * 3. L21 = A21 U11^{-1}, 4. A22 - L21 U12 = L22 U22), without pivoting; the
  * update of step 4 is formed in the target block's format and low-rank targets
  * are recompressed (Sec. 3.2) with eps_lu.  The factors replace earlier ones
- * in the handle.  The call synchronises stream.
- *   eps_lu  in (0, 1): the truncation tolerance eps_LU of Sec. 3.2
- * Errors: HM_ERR_ARG, HM_ERR_NUMERIC (zero pivot, unconverged SVD), HM_ERR_CUDA.
+ * in the handle.  Independent subtrees of the recursion run on up to 16
+ * library-owned streams, each driven by a host thread of the call; they start
+ * after the work already queued on stream and the call returns after all of
+ * them (it synchronises stream).  The handle must not be used by another
+ * thread meanwhile.  Device memory: the FP64 factors (16 bytes per stored
+ * entry, lu_entries of hm_lu_info) plus temporaries of the recompressions.
+ *   eps_lu  in (0, 1): the truncation tolerance eps_LU of Sec. 3.2; from 1e-5
+ *           up the recompression uses the Gram form of the build's
+ *           recompression, below it Householder QR of both factors
+ * Errors: HM_ERR_ARG, HM_ERR_NUMERIC (zero pivot, unconverged SVD, non-finite
+ * value), HM_ERR_OOM, HM_ERR_CUDA; on error the handle keeps no factors.
  * hm_lu_solve: x = U^{-1} L^{-1} b for nrhs columns; b, x DEVICE complex128,
  *   3 n_c x nrhs column-major, original point order, not overlapping.
  *   Certify it with hm_estimate_error (Eq. est_direct of Sec. 3.3).
