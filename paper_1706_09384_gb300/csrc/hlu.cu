@@ -405,119 +405,219 @@ __global__ void __launch_bounds__(JT) hz_jacobi_kernel(const double2* W0, double
     }
 }
 
-// The same one-sided Jacobi spread over a thread-block cluster of CJ CTAs (one
-// SM each, for CJ times the FP64 rate of one SM): W lives in the shared memory
-// of CTA 0 and every warp of the cluster reaches it through distributed shared
-// memory; a warp holds its pair of columns in registers for the round (one
-// read, one write), rounds end at the cluster barrier.  K <= 128.
+// The same one-sided Jacobi as a block Jacobi on a thread-block cluster of CJ
+// CTAs (one SM each, for CJ times the FP64 rate of one SM).  The K columns form
+// NBJ = 2 CJ blocks of bs = ceil(K / NBJ); in a block round CTA i holds the two
+// blocks of pair i of a round-robin tournament over the blocks (NBJ - 1 block
+// rounds make a sweep of all block pairs) in its own shared memory and rotates
+// all pairs across them, in bs rounds of disjoint pairs under CTA barriers
+// (the pairs inside each block in the first block round of a sweep).  Between
+// block rounds every CTA pulls its next two blocks from the CTAs that held them
+// through distributed shared memory (double-buffered); the cluster barrier
+// ends a block round.  A warp holds its pair of columns in registers (K <= 128).
 constexpr int CJ = 8;
 constexpr int CJT = 256;
-constexpr int64_t CJ_MAX = 112;  // K x K complex in one CTA's shared memory
+constexpr int NBJ = 2 * CJ;
+constexpr int64_t CJ_MAX = 128;
+
+__device__ __forceinline__ void hz_tour(int rho, int i, int& a, int& b) {
+    if (i == 0) {
+        a = NBJ - 1;
+        b = rho;
+    } else {
+        a = (rho + i) % (NBJ - 1);
+        b = (rho - i + NBJ - 1) % (NBJ - 1);
+    }
+}
+
+// One rotation of the pair (ca, cb) of K-long columns by a warp; true if rotated.
+__device__ __forceinline__ bool hz_rot_pair(double2* ca, double2* cb, int64_t K, double tol, double small,
+                                            int lane) {
+    double2 wa[4], wb[4];
+    double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = lane + 32 * i;
+        wa[i] = r < K ? ca[r] : make_double2(0.0, 0.0);
+        wb[i] = r < K ? cb[r] : make_double2(0.0, 0.0);
+        al += wa[i].x * wa[i].x + wa[i].y * wa[i].y;
+        be += wb[i].x * wb[i].x + wb[i].y * wb[i].y;
+        gr += wa[i].x * wb[i].x + wa[i].y * wb[i].y;  // conj(wa) wb
+        gi += wa[i].x * wb[i].y - wa[i].y * wb[i].x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+    const double ag = sqrt(gr * gr + gi * gi);
+    if (al <= small || be <= small) return false;                      // uniform within the warp
+    if (ag == 0.0 || ag <= tol * sqrt(al) * sqrt(be)) return false;  // uniform within the warp
+    const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
+    const double zeta = (be - al) / (2.0 * ag);
+    const double az = fabs(zeta);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (az > 1e150 ? 2.0 * az : az + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+    // [w_a, w_b] <- [w_a, w_b] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = lane + 32 * i;
+        if (r < K) {
+            const double2 pwb = zmul(phc, wb[i]);
+            ca[r] = make_double2(c * wa[i].x - sn * pwb.x, c * wa[i].y - sn * pwb.y);
+            cb[r] = make_double2(sn * wa[i].x + c * pwb.x, sn * wa[i].y + c * pwb.y);
+        }
+    }
+    return true;
+}
+
 __global__ void __cluster_dims__(CJ, 1, 1) __launch_bounds__(CJT)
     hz_jacobi_cluster_kernel(const double2* W0, double2* WJ, int64_t K, double* s, int* unconverged,
                              double tol_min) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ double2 hz_cw[];
+    extern __shared__ double2 hz_cw[];  // [parity 2][slot 2][bs][K]
     __shared__ double part[CJ];
     __shared__ double red[CJT / 32];
     __shared__ int conv;
-    const unsigned rank = cl.block_rank();
-    double2* W = cl.map_shared_rank(hz_cw, 0);
+    const int rank = (int)cl.block_rank();
     double* part0 = cl.map_shared_rank(part, 0);
     int* conv0 = cl.map_shared_rank(&conv, 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)rank * (CJT / 32) + warp, nw = (int64_t)CJ * (CJT / 32);
-    // W0 -> CTA 0, a slice per CTA; ||W||_F^2 from the slices
+    const int64_t bs = (K + NBJ - 1) / NBJ;
+    auto slot = [&](int par, int sl) { return hz_cw + (int64_t)(par * 2 + sl) * bs * K; };
+    auto ncols = [&](int beta) { return (int)max((int64_t)0, min(bs, K - beta * bs)); };
+    // ||W||_F^2 from slices of W0
     double f2 = 0.0;
     for (int64_t e = (int64_t)rank * CJT + threadIdx.x; e < K * K; e += (int64_t)CJ * CJT) {
         const double2 v = W0[e];
-        W[e] = v;
         f2 += v.x * v.x + v.y * v.y;
     }
     f2 = hz_block_sum<CJT>(f2, red);
     if (threadIdx.x == 0) part0[rank] = f2;
+    // the first placement straight from W0
+    {
+        int A, B;
+        hz_tour(0, rank, A, B);
+        const int beta[2] = {A, B};
+        for (int sl = 0; sl < 2; ++sl) {
+            double2* dst = slot(0, sl);
+            const int64_t n = (int64_t)ncols(beta[sl]) * K;
+            const double2* src = W0 + (int64_t)beta[sl] * bs * K;
+            for (int64_t e = threadIdx.x; e < n; e += CJT) dst[e] = src[e];
+        }
+    }
     cl.sync();
     f2 = 0.0;
     for (int q = 0; q < CJ; ++q) f2 += part0[q];
-    const int64_t np = (K + 1) & ~1;
     const double tol = fmax(tol_min, (double)K * 0x1.0p-53);
+    // a column at the rounding level of W (rank-deficient W) cannot be made
+    // orthogonal to a large one to relative accuracy: it is left alone
     const double small = ((double)K * 0x1.0p-53) * ((double)K * 0x1.0p-53) * f2;
+    int64_t g = 0;  // block rounds done
     int sweep = 0;
     for (; sweep < 80; ++sweep) {
         if (rank == 0 && threadIdx.x == 0) *conv0 = 1;
         cl.sync();
-        for (int64_t round = 0; round < np - 1; ++round) {
-            for (int64_t pi = gw; pi < np / 2; pi += nw) {
-                int64_t a, b;
-                if (pi == 0) {
-                    a = np - 1;
-                    b = round;
-                } else {
-                    a = (round + pi) % (np - 1);
-                    b = (round - pi + np - 1) % (np - 1);
-                }
-                if (a >= K || b >= K) continue;
-                if (a > b) {
-                    const int64_t t = a;
-                    a = b;
-                    b = t;
-                }
-                double2 wa[4], wb[4];
-                double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int64_t r = lane + 32 * i;
-                    wa[i] = r < K ? W[r + a * K] : make_double2(0.0, 0.0);
-                    wb[i] = r < K ? W[r + b * K] : make_double2(0.0, 0.0);
-                    al += wa[i].x * wa[i].x + wa[i].y * wa[i].y;
-                    be += wb[i].x * wb[i].x + wb[i].y * wb[i].y;
-                    gr += wa[i].x * wb[i].x + wa[i].y * wb[i].y;  // conj(wa) wb
-                    gi += wa[i].x * wb[i].y - wa[i].y * wb[i].x;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
-                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
-                }
-                const double ag = sqrt(gr * gr + gi * gi);
-                if (al <= small || be <= small) continue;                      // uniform within the warp
-                if (ag == 0.0 || ag <= tol * sqrt(al) * sqrt(be)) continue;  // uniform within the warp
-                if (lane == 0) *conv0 = 0;
-                const double2 phc = make_double2(gr / ag, -gi / ag);  // e^{-i phi}
-                const double zeta = (be - al) / (2.0 * ag);
-                const double az = fabs(zeta);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (az > 1e150 ? 2.0 * az : az + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int64_t r = lane + 32 * i;
-                    if (r < K) {
-                        const double2 pwb = zmul(phc, wb[i]);
-                        W[r + a * K] = make_double2(c * wa[i].x - sn * pwb.x, c * wa[i].y - sn * pwb.y);
-                        W[r + b * K] = make_double2(sn * wa[i].x + c * pwb.x, sn * wa[i].y + c * pwb.y);
+        for (int rho = 0; rho < NBJ - 1; ++rho, ++g) {
+            const int par = (int)(g & 1);
+            int A, B;
+            hz_tour(rho, rank, A, B);
+            if (g > 0) {  // pull both blocks from where they were in the previous block round
+                const int prho = (int)((g - 1) % (NBJ - 1));
+                const int beta[2] = {A, B};
+                for (int sl = 0; sl < 2; ++sl) {
+                    int src_cta = 0, src_sl = 0;
+                    for (int j = 0; j < CJ; ++j) {
+                        int a2, b2;
+                        hz_tour(prho, j, a2, b2);
+                        if (a2 == beta[sl]) {
+                            src_cta = j;
+                            src_sl = 0;
+                        }
+                        if (b2 == beta[sl]) {
+                            src_cta = j;
+                            src_sl = 1;
+                        }
                     }
+                    const double2* src = cl.map_shared_rank(slot(par ^ 1, src_sl), src_cta);
+                    double2* dst = slot(par, sl);
+                    const int64_t n = (int64_t)ncols(beta[sl]) * K;
+                    for (int64_t e = threadIdx.x; e < n; e += CJT) dst[e] = src[e];
+                }
+                __syncthreads();
+            }
+            double2* SA = slot(par, 0);
+            double2* SB = slot(par, 1);
+            const int na = ncols(A), nb = ncols(B);
+            if (rho == 0) {  // the pairs inside each block, round robin, warps 0-3 on A and 4-7 on B
+                const int sl = warp / 4, p = warp % 4;
+                const int n = sl == 0 ? na : nb;
+                const int npl = (n + 1) & ~1;
+                double2* S = sl == 0 ? SA : SB;
+                const int rounds = (int)((bs + 1) & ~1) - 1;
+                for (int r = 0; r < rounds; ++r) {
+                    if (r < npl - 1 && p < npl / 2) {
+                        int x, y;
+                        if (p == 0) {
+                            x = npl - 1;
+                            y = r;
+                        } else {
+                            x = (r + p) % (npl - 1);
+                            y = (r - p + npl - 1) % (npl - 1);
+                        }
+                        if (x < n && y < n) {
+                            if (x > y) {
+                                const int t = x;
+                                x = y;
+                                y = t;
+                            }
+                            if (hz_rot_pair(S + (int64_t)x * K, S + (int64_t)y * K, K, tol, small, lane) && lane == 0)
+                                *conv0 = 0;
+                        }
+                    }
+                    __syncthreads();
                 }
             }
-            cl.sync();
+            for (int64_t r = 0; r < bs; ++r) {  // the pairs across the two blocks: (q, q + r mod bs)
+                for (int64_t q = warp; q < bs; q += CJT / 32) {
+                    const int64_t qb = (q + r) % bs;
+                    if (q < na && qb < nb &&
+                        hz_rot_pair(SA + q * K, SB + qb * K, K, tol, small, lane) && lane == 0)
+                        *conv0 = 0;
+                }
+                __syncthreads();
+            }
+            cl.sync();  // this round's blocks are final before anyone pulls them
         }
         const int done = *conv0;
         cl.sync();  // every thread has read the flag before CTA 0 resets it
         if (done) break;
     }
     if (rank == 0 && threadIdx.x == 0 && sweep == 80) atomicOr(unconverged, 2);
-    for (int64_t j = gw; j < K; j += nw) {
-        double a = 0.0;
-        for (int64_t r = lane; r < K; r += 32) {
-            const double2 v = W[r + j * K];
-            WJ[r + j * K] = v;
-            a += v.x * v.x + v.y * v.y;
+    {  // the blocks this CTA held in the last block round, back to their columns
+        const int par = (int)((g - 1) & 1);
+        int A, B;
+        hz_tour((int)((g - 1) % (NBJ - 1)), rank, A, B);
+        const int beta[2] = {A, B};
+        for (int sl = 0; sl < 2; ++sl) {
+            const double2* S = slot(par, sl);
+            const int n = ncols(beta[sl]);
+            for (int q = warp; q < n; q += CJT / 32) {
+                const int64_t j = (int64_t)beta[sl] * bs + q;
+                double a = 0.0;
+                for (int64_t r = lane; r < K; r += 32) {
+                    const double2 v = S[q * K + r];
+                    WJ[r + j * K] = v;
+                    a += v.x * v.x + v.y * v.y;
+                }
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) s[j] = sqrt(a);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) s[j] = sqrt(a);
     }
-    cl.sync();  // CTA 0's shared memory stays until every CTA is done with it
+    cl.sync();
 }
 
 // G = R^H R for a Hermitian semi-definite G (K x K, in place -> R upper):
@@ -1039,7 +1139,7 @@ void densify(Ctx& C, const HNode* x, double2* D, int64_t ldd, double2 alpha) {
 void jacobi(Ctx& C, const double2* W, double2* WJ, int64_t K, double* s) {
     const double tol_min = 1e-15;
     if (K <= CJ_MAX) {
-        const size_t sm = (size_t)K * K * sizeof(double2);
+        const size_t sm = (size_t)4 * ((K + NBJ - 1) / NBJ) * K * sizeof(double2);
         hz_jacobi_cluster_kernel<<<CJ, CJT, sm, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
     } else {
         hz_jacobi_kernel<<<1, JT, 0, C.st>>>(W, WJ, K, s, C.d_flag, tol_min);
@@ -1491,7 +1591,7 @@ void hlu_factor(hm_matrix* h, double eps_lu, cudaStream_t st) {
     HM_CUDA(cudaGetDevice(&C.device));
     // shared-memory limits of the core kernels, set once before any chain forks
     HM_CUDA(cudaFuncSetAttribute(hz_jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(CJ_MAX * CJ_MAX * sizeof(double2))));
+                                 (int)(4 * ((CJ_MAX + NBJ - 1) / NBJ) * CJ_MAX * sizeof(double2))));
     HM_CUDA(cudaFuncSetAttribute(hz_qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(QP_SMEM * QP_SMEM * sizeof(double2))));
     HM_CUDA(cudaFuncSetAttribute(hz_gram_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
