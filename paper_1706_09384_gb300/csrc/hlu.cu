@@ -20,12 +20,16 @@
 // computed exactly and counted in the eps_LU budget of the truncation, so the
 // result keeps the truncation bound without an SVD of the whole block.
 //
-// The recursion runs on the host (independent subtrees on up to 8 streams,
+// The recursion runs on the host (independent subtrees on up to 16 streams,
 // each driven by its own host thread) and issues one FP64 kernel per dense
-// operation: complex GEMM (32 x 32 tiles), LU of a dense diagonal leaf (one
-// CTA) and triangular solves with it (a warp per column), the Householder QR
-// and the one-sided Jacobi SVD of the recompression (one CTA each, the Jacobi
-// matrix in shared memory).  Truncation ranks are read back to size the next operation.
+// operation: complex GEMM (32 x 32 tiles, split-K for long contractions), LU
+// of a dense diagonal leaf (one CTA) and triangular solves with it (a warp per
+// column).  A recompression forms the k x k core W = R_U R_V^H (Householder
+// QR of both factors, or for eps_LU >= 1e-5 the Gram form: Cholesky of the
+// Gram matrices, no orthonormal factors), reduces W by a column-pivoted QR
+// (one CTA, shared memory) and runs a one-sided block Jacobi on R^H across an
+// 8-CTA cluster; its singular values are read back to choose the rank and
+// size the next operation.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
