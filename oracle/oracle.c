@@ -137,6 +137,39 @@ static void entry_block(const or_problem* pb, const double* pts, const double* n
             for (int b = 0; b < 3; ++b) G[a][b] *= pb->weights[j];
 }
 
+/* Block (i, j) between two clouds: K(x_i, y_j) w_j for a target point x_i of
+ * X and a source point y_j of Y (normal and weight at y_j), diag_value * I3
+ * where x_i and y_j coincide, so that X = Y reproduces entry_block. */
+static void entry_block2(const or_problem* pb, const double* X, const double* Y, const double* nrmY,
+                         int64_t i, int64_t j, cplx G[3][3])
+{
+    const double* x = X + 3 * i;
+    const double* y = Y + 3 * j;
+    if (x[0] == y[0] && x[1] == y[1] && x[2] == y[2]) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[a][b] = (a == b) ? pb->diag_value : 0.0;
+        return;
+    }
+    green(pb, x, y, nrmY ? nrmY + 3 * j : NULL, G);
+    if (pb->weights)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[a][b] *= pb->weights[j];
+}
+
+/* The 3 nx x 3 ny matrix between two clouds, row-major complex. */
+void or_dense_matrix2(const or_problem* pb, const double* X, int64_t nx, const double* Y, int64_t ny,
+                      const double* nrmY, double* A)
+{
+    const int64_t N = 3 * ny;
+    for (int64_t i = 0; i < nx; ++i)
+        for (int64_t j = 0; j < ny; ++j) {
+            cplx G[3][3];
+            entry_block2(pb, X, Y, nrmY, i, j, G);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) st(A + 2 * ((3 * i + a) * N + 3 * j + b), G[a][b]);
+        }
+}
+
 void or_dense_matrix(const or_problem* pb, const double* pts, const double* nrm, int64_t nc,
                      double* A)
 {
@@ -556,7 +589,18 @@ typedef struct {
     const double* nrm;
     const int64_t* rows; /* global point index of local row point i */
     const int64_t* cols;
+    const double* pts_y; /* kind 1, two clouds: source points (columns), else NULL */
+    const double* nrm_y;
 } block_src;
+
+/* Block (i, j) of a kernel source: one cloud, or targets pts and sources pts_y. */
+static void src_entry(const block_src* s, int64_t i, int64_t j, cplx G[3][3])
+{
+    if (s->pts_y)
+        entry_block2(s->pb, s->pts, s->pts_y, s->nrm_y, s->rows[i], s->cols[j], G);
+    else
+        entry_block(s->pb, s->pts, s->nrm, s->rows[i], s->cols[j], G);
+}
 
 static void src_row(const block_src* s, int64_t i, cplx* R /* 3 x 3n row-major */)
 {
@@ -568,7 +612,7 @@ static void src_row(const block_src* s, int64_t i, cplx* R /* 3 x 3n row-major *
     }
     for (int64_t j = 0; j < s->n; ++j) {
         cplx G[3][3];
-        entry_block(s->pb, s->pts, s->nrm, s->rows[i], s->cols[j], G);
+        src_entry(s, i, j, G);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) R[a * n3 + 3 * j + b] = G[a][b];
     }
@@ -584,7 +628,7 @@ static void src_col(const block_src* s, int64_t j, cplx* C /* 3m x 3 row-major *
     }
     for (int64_t i = 0; i < s->m; ++i) {
         cplx G[3][3];
-        entry_block(s->pb, s->pts, s->nrm, s->rows[i], s->cols[j], G);
+        src_entry(s, i, j, G);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) C[3 * (3 * i + a) + b] = G[a][b];
     }
@@ -1238,6 +1282,197 @@ static void hmat_apply(const or_hmat* h, const cplx* x, cplx* y)
 void or_hmat_matvec(const or_hmat* h, const double* x, double* y)
 {
     hmat_apply(h, (const cplx*)x, (cplx*)y);
+}
+
+/* ======================================================================
+ * Two clouds: targets X (rows, the collocation points x_i) and sources Y
+ * (columns, the points y_j with their normals and weights), each with its
+ * own cluster tree (Sec. 2.1); the partition pairs a cluster of X with a
+ * cluster of Y by the same recursion and admissibility test as the square
+ * case.  Blocks are dense or compressed exactly as there (vector ACA,
+ * randomized SVD for unpivotable rows, recompression).
+ * ====================================================================== */
+static void part_rec2(const or_cluster* clX, const or_cluster* clY, double eta, int64_t t, int64_t s,
+                      or_block* out, int64_t* nb)
+{
+    const int adm = or_admissible_box(clX[t].lo, clX[t].hi, clY[s].lo, clY[s].hi, eta);
+    if (adm || clX[t].is_leaf || clY[s].is_leaf) {
+        if (out) {
+            out[*nb].tau = t;
+            out[*nb].sigma = s;
+            out[*nb].admissible = adm;
+            out[*nb].pad_ = 0;
+        }
+        (*nb)++;
+        return;
+    }
+    const int64_t tc[2] = {clX[t].child0, clX[t].child1};
+    const int64_t sc[2] = {clY[s].child0, clY[s].child1};
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) part_rec2(clX, clY, eta, tc[u], sc[v], out, nb);
+}
+
+int64_t or_partition2(const or_cluster* clX, int64_t nclX, const or_cluster* clY, int64_t nclY, double eta,
+                      or_block* out)
+{
+    if (nclX == 0 || nclY == 0) return 0;
+    int64_t nb = 0;
+    part_rec2(clX, clY, eta, 0, 0, out, &nb);
+    return nb;
+}
+
+struct or_hmat2 {
+    or_problem pb;
+    int64_t nx, ny;
+    int64_t *permX, *permY;
+    or_cluster *clX, *clY;
+    int64_t nclX, nclY;
+    or_block* blk;
+    int64_t nb;
+    int64_t *rank_aca, *rank;
+    cplx** D; /* dense data, or U */
+    cplx** V;
+};
+
+or_hmat2* or_hmat2_build(const or_problem* pb, const double* X, int64_t nx, const double* Y, int64_t ny,
+                         const double* nrmY, double eps, double eta, int64_t leaf, int nthreads)
+{
+    or_hmat2* h = (or_hmat2*)calloc(1, sizeof(or_hmat2));
+    h->pb = *pb;
+    h->nx = nx;
+    h->ny = ny;
+    h->permX = (int64_t*)malloc((size_t)(nx > 0 ? nx : 1) * sizeof(int64_t));
+    h->permY = (int64_t*)malloc((size_t)(ny > 0 ? ny : 1) * sizeof(int64_t));
+    h->clX = (or_cluster*)malloc((size_t)(2 * nx + 1) * sizeof(or_cluster));
+    h->clY = (or_cluster*)malloc((size_t)(2 * ny + 1) * sizeof(or_cluster));
+    h->nclX = or_tree_build(X, nx, leaf, h->permX, h->clX);
+    h->nclY = or_tree_build(Y, ny, leaf, h->permY, h->clY);
+    h->nb = or_partition2(h->clX, h->nclX, h->clY, h->nclY, eta, NULL);
+    h->blk = (or_block*)malloc((size_t)(h->nb + 1) * sizeof(or_block));
+    or_partition2(h->clX, h->nclX, h->clY, h->nclY, eta, h->blk);
+    h->rank_aca = (int64_t*)calloc((size_t)(h->nb + 1), sizeof(int64_t));
+    h->rank = (int64_t*)calloc((size_t)(h->nb + 1), sizeof(int64_t));
+    h->D = (cplx**)calloc((size_t)(h->nb + 1), sizeof(cplx*));
+    h->V = (cplx**)calloc((size_t)(h->nb + 1), sizeof(cplx*));
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t b = 0; b < h->nb; ++b) {
+        const or_cluster* t = &h->clX[h->blk[b].tau];
+        const or_cluster* s = &h->clY[h->blk[b].sigma];
+        const int64_t m = t->end - t->begin, n = s->end - s->begin;
+        if (!h->blk[b].admissible) {
+            cplx* D = (cplx*)malloc((size_t)(9 * m * n + 1) * sizeof(cplx));
+            for (int64_t j = 0; j < n; ++j)
+                for (int64_t i = 0; i < m; ++i) {
+                    cplx G[3][3];
+                    entry_block2(pb, X, Y, nrmY, h->permX[t->begin + i], h->permY[s->begin + j], G);
+                    for (int a = 0; a < 3; ++a)
+                        for (int c = 0; c < 3; ++c) D[(3 * i + a) + (3 * j + c) * (3 * m)] = G[a][c];
+                }
+            h->D[b] = D;
+            continue;
+        }
+        block_src src = {0};
+        src.kind = 1;
+        src.m = m;
+        src.n = n;
+        src.pb = pb;
+        src.pts = X;
+        src.pts_y = Y;
+        src.nrm_y = nrmY;
+        src.rows = h->permX + t->begin;
+        src.cols = h->permY + s->begin;
+        cplx *U, *V;
+        int lost = 0;
+        int64_t k = aca_run(&src, eps, &U, &V, NULL, &lost);
+        double eps_r = eps;
+        if (lost) { /* rows the vector ACA cannot pivot: the randomized SVD */
+            free(U);
+            free(V);
+            int ok = 0;
+            k = rsvd_run(&src, eps, or_rsvd_key(t->begin, s->begin), &U, &V, &ok);
+            eps_r = eps * sqrt(3.0) / 2;
+        }
+        h->rank_aca[b] = k;
+        cplx *U2, *V2;
+        h->rank[b] = recompress(U, V, 3 * m, 3 * n, k, eps_r, &U2, &V2, NULL);
+        free(U);
+        free(V);
+        h->D[b] = U2;
+        h->V[b] = V2;
+    }
+    return h;
+}
+
+void or_hmat2_free(or_hmat2* h)
+{
+    if (!h) return;
+    for (int64_t b = 0; b < h->nb; ++b) {
+        free(h->D[b]);
+        free(h->V[b]);
+    }
+    free(h->D);
+    free(h->V);
+    free(h->rank);
+    free(h->rank_aca);
+    free(h->blk);
+    free(h->clX);
+    free(h->clY);
+    free(h->permX);
+    free(h->permY);
+    free(h);
+}
+
+int64_t or_hmat2_nblocks(const or_hmat2* h) { return h->nb; }
+void or_hmat2_blocks(const or_hmat2* h, or_block* out, int64_t* rank)
+{
+    for (int64_t b = 0; b < h->nb; ++b) {
+        if (out) out[b] = h->blk[b];
+        if (rank) rank[b] = h->rank[b];
+    }
+}
+void or_hmat2_clusters(const or_hmat2* h, or_cluster* clX, or_cluster* clY)
+{
+    if (clX) memcpy(clX, h->clX, (size_t)h->nclX * sizeof(or_cluster));
+    if (clY) memcpy(clY, h->clY, (size_t)h->nclY * sizeof(or_cluster));
+}
+int64_t or_hmat2_nclusters(const or_hmat2* h, int side) { return side ? h->nclY : h->nclX; }
+
+/* y = A_H x: x on the sources (3 ny, original order), y on the targets (3 nx). */
+void or_hmat2_matvec(const or_hmat2* h, const double* xd, double* yd)
+{
+    const cplx* x = (const cplx*)xd;
+    cplx* y = (cplx*)yd;
+    cplx* xp = (cplx*)malloc((size_t)(3 * h->ny + 1) * sizeof(cplx));
+    cplx* yp = (cplx*)calloc((size_t)(3 * h->nx + 1), sizeof(cplx));
+    for (int64_t p = 0; p < h->ny; ++p)
+        for (int a = 0; a < 3; ++a) xp[3 * p + a] = x[3 * h->permY[p] + a];
+    for (int64_t b = 0; b < h->nb; ++b) {
+        const or_cluster* t = &h->clX[h->blk[b].tau];
+        const or_cluster* s = &h->clY[h->blk[b].sigma];
+        const int64_t m3 = 3 * (t->end - t->begin), n3 = 3 * (s->end - s->begin);
+        const cplx* xs = xp + 3 * s->begin;
+        cplx* yt = yp + 3 * t->begin;
+        if (!h->blk[b].admissible) {
+            const cplx* D = h->D[b];
+            for (int64_t c = 0; c < n3; ++c)
+                for (int64_t r = 0; r < m3; ++r) yt[r] += D[r + c * m3] * xs[c];
+        } else {
+            const cplx* U = h->D[b];
+            const cplx* V = h->V[b];
+            for (int64_t l = 0; l < h->rank[b]; ++l) {
+                cplx tl = 0.0;
+                for (int64_t c = 0; c < n3; ++c) tl += conj(V[c + l * n3]) * xs[c];
+                for (int64_t r = 0; r < m3; ++r) yt[r] += U[r + l * m3] * tl;
+            }
+        }
+    }
+    for (int64_t p = 0; p < h->nx; ++p)
+        for (int a = 0; a < 3; ++a) y[3 * h->permX[p] + a] = yp[3 * p + a];
+    free(xp);
+    free(yp);
 }
 
 /* ======================================================================

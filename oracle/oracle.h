@@ -135,6 +135,23 @@ void or_hmat_block_methods(const or_hmat* h, int32_t* out);
 /* dense: D (3|tau| x 3|sigma| col-major); low rank: U (3|tau| x r), V (3|sigma| x r). */
 void or_hmat_block_data(const or_hmat* h, int64_t b, double* D_or_U, double* V);
 void or_hmat_matvec(const or_hmat* h, const double* x, double* y);
+
+/* Two clouds: targets X (nx points, rows) and sources Y (ny points, columns;
+ * normals nrmY for T, weights from pb at y_j); a cluster tree per cloud and
+ * the partition of X x Y (Sec. 2.1); x_i = y_j gives diag_value * I3. */
+typedef struct or_hmat2 or_hmat2;
+void or_dense_matrix2(const or_problem* pb, const double* X, int64_t nx, const double* Y, int64_t ny,
+                      const double* nrmY, double* A);
+int64_t or_partition2(const or_cluster* clX, int64_t nclX, const or_cluster* clY, int64_t nclY, double eta,
+                      or_block* out);
+or_hmat2* or_hmat2_build(const or_problem* pb, const double* X, int64_t nx, const double* Y, int64_t ny,
+                         const double* nrmY, double eps, double eta, int64_t leaf, int nthreads);
+void or_hmat2_free(or_hmat2* h);
+int64_t or_hmat2_nblocks(const or_hmat2* h);
+void or_hmat2_blocks(const or_hmat2* h, or_block* out, int64_t* rank);
+int64_t or_hmat2_nclusters(const or_hmat2* h, int side);
+void or_hmat2_clusters(const or_hmat2* h, or_cluster* clX, or_cluster* clY);
+void or_hmat2_matvec(const or_hmat2* h, const double* x, double* y);
 double or_hmat_build_seconds(const or_hmat* h);
 
 /* --- H-LU factorisation and direct solver (Sec. 3.2): recursive 2 x 2 block

@@ -82,6 +82,15 @@ def lib():
             "or_hmat_blocks": (None, [_P, _P, _P, _P]),
             "or_hmat_block_data": (None, [_P, _I64, _P, _P]),
             "or_hmat_matvec": (None, [_P, _P, _P]),
+            "or_dense_matrix2": (None, [_P, _P, _I64, _P, _I64, _P, _P]),
+            "or_partition2": (_I64, [_P, _I64, _P, _I64, _D, _P]),
+            "or_hmat2_build": (_P, [_P, _P, _I64, _P, _I64, _P, _D, _D, _I64, _INT]),
+            "or_hmat2_free": (None, [_P]),
+            "or_hmat2_nblocks": (_I64, [_P]),
+            "or_hmat2_blocks": (None, [_P, _P, _P]),
+            "or_hmat2_nclusters": (_I64, [_P, _INT]),
+            "or_hmat2_clusters": (None, [_P, _P, _P]),
+            "or_hmat2_matvec": (None, [_P, _P, _P]),
             "or_hmat_build_seconds": (_D, [_P]),
             "or_gmres_hmat": (_INT, [_P, _P, _P, _INT, _D, _INT, _P, _P]),
             "or_gmres_dense": (_INT, [_P, _I64, _P, _P, _INT, _D, _INT, _P, _P]),
@@ -177,6 +186,24 @@ def admissible_box(lo1, hi1, lo2, hi2, eta):
 def admissible_exact(X, Y, eta):
     X, Y = _f64(X), _f64(Y)
     return bool(lib().or_admissible_exact(_ptr(X), X.shape[0], _ptr(Y), Y.shape[0], eta))
+
+
+def dense_matrix2(pb, X, Y, nrmY=None):
+    """The 3 nx x 3 ny matrix between targets X and sources Y (normals at Y)."""
+    X, Y = _f64(X), _f64(Y)
+    A = np.zeros((3 * X.shape[0], 3 * Y.shape[0]), np.complex128)
+    lib().or_dense_matrix2(C.byref(pb), _ptr(X), X.shape[0], _ptr(Y), Y.shape[0],
+                           _ptr(_f64(nrmY)) if nrmY is not None else None, _ptr(A))
+    return A
+
+
+def partition2(clX, clY, eta):
+    a = np.ascontiguousarray(clX, CLUSTER_DTYPE)
+    b = np.ascontiguousarray(clY, CLUSTER_DTYPE)
+    n = lib().or_partition2(_ptr(a), len(a), _ptr(b), len(b), eta, None)
+    out = np.zeros(n, BLOCK_DTYPE)
+    lib().or_partition2(_ptr(a), len(a), _ptr(b), len(b), eta, _ptr(out))
+    return out
 
 
 def partition(clusters, eta):
@@ -364,6 +391,44 @@ def gmres_dense(A, b, restart=50, tol=1e-6, maxit=1000):
     return x, it.value, rr.value, st
 
 
+
+
+class HMatrix2:
+    """Oracle H-matrix between two clouds: targets X (rows), sources Y
+    (columns, with normals and the problem's weights)."""
+
+    def __init__(self, pb, X, Y, nrmY=None, eps=1e-4, eta=3.0, leaf=32, nthreads=0):
+        self.pb = pb
+        self.X, self.Y = _f64(X), _f64(Y)
+        self.nrmY = _f64(nrmY) if nrmY is not None else None
+        self.nx, self.ny = self.X.shape[0], self.Y.shape[0]
+        self.h = lib().or_hmat2_build(C.byref(pb), _ptr(self.X), self.nx, _ptr(self.Y), self.ny,
+                                      _ptr(self.nrmY), eps, eta, leaf, nthreads)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_hmat2_free(self.h)
+            self.h = None
+
+    def blocks(self):
+        n = lib().or_hmat2_nblocks(self.h)
+        blk = np.zeros(n, BLOCK_DTYPE)
+        r = np.zeros(n, np.int64)
+        lib().or_hmat2_blocks(self.h, _ptr(blk), _ptr(r))
+        return blk, r
+
+    def clusters(self):
+        a = np.zeros(lib().or_hmat2_nclusters(self.h, 0), CLUSTER_DTYPE)
+        b = np.zeros(lib().or_hmat2_nclusters(self.h, 1), CLUSTER_DTYPE)
+        lib().or_hmat2_clusters(self.h, _ptr(a), _ptr(b))
+        return a, b
+
+    def matvec(self, x):
+        """y = A_H x for x of 3 ny complex entries (original source order)."""
+        x = _c128(x)
+        y = np.zeros(3 * self.nx, np.complex128)
+        lib().or_hmat2_matvec(self.h, _ptr(x), _ptr(y))
+        return y
 
 
 class HLU:
