@@ -3,13 +3,13 @@ of the subdivided icosahedron, N_c = 10 * 4^l + 2), for a comparison with the
 rank tables of Sec. 7.2 and the growth of the ranks with the frequency
 (Sec. 8: about flat in N_c at fixed omega, growing with omega at fixed
 points per wavelength).  Point kernel U (or T), rho = mu = 1, lambda = 2,
-eta = 3, eps = 1e-4, leaf 64 (the paper's N_leaf = 100 exceeds the leaves of
-64 points the product kernels take).  Prints one JSON line per build:
+eta = 3, eps = 1e-4, N_leaf = 100 as in Sec. 7 (--leaf to change it).  Prints
+one JSON line per build:
 min / mean / max ACA and recompressed ranks of the admissible blocks, overall
 and per level of the row cluster.
 
     python -m paper_1706_09384_gb300.rank_tables [--levels 3 4 5 6] [--omegas 3 14]
-                                                  [--ppw 10] [--kernel U]
+                                                  [--ppw 10] [--kernel U] [--leaf 100]
 """
 import argparse
 import json
@@ -40,14 +40,14 @@ def rank_stats(H):
     return out
 
 
-def run(level, omega, kernel="U", eps=1e-4, leaf=64):
+def run(level, omega, kernel="U", eps=1e-4, leaf=100):
     pts, nrm = inputs.icosphere(level)
     t0 = time.time()
     H = hm.HMatrix.build(pts, nrm if kernel == "T" else None, 1.0, 2.0, 1.0, omega, kernel, eps,
                          3.0, leaf)
     res = {"level": level, "n_c": len(pts), "omega": omega, "kappa_s": omega,
            "points_per_wavelength": 2 * math.pi / omega / math.sqrt(4 * math.pi / len(pts)),
-           "kernel": kernel, "build_s": time.time() - t0}
+           "kernel": kernel, "leaf": leaf, "build_s": time.time() - t0}
     res.update(rank_stats(H))
     H.free()
     return res
@@ -60,15 +60,17 @@ def main():
     ap.add_argument("--ppw", type=float, default=10.0,
                     help="also run every level at this many points per S-wavelength")
     ap.add_argument("--kernel", default="U", choices=["U", "T"])
+    ap.add_argument("--leaf", type=int, default=100, help="N_leaf (the paper uses 100)")
     args = ap.parse_args()
     for level in args.levels:
         for om in args.omegas:
-            print(json.dumps(run(level, om, args.kernel)), flush=True)
+            print(json.dumps(run(level, om, args.kernel, leaf=args.leaf)), flush=True)
     if args.ppw > 0:
         for level in args.levels:
             n = 10 * 4 ** level + 2
             h = math.sqrt(4 * math.pi / n)  # mean spacing on the unit sphere
-            print(json.dumps(run(level, 2 * math.pi / (args.ppw * h), args.kernel)), flush=True)
+            print(json.dumps(run(level, 2 * math.pi / (args.ppw * h), args.kernel, leaf=args.leaf)),
+                  flush=True)
 
 
 if __name__ == "__main__":
