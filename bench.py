@@ -202,7 +202,7 @@ def workload_config(args, wl, form, world):
             "storage": ("bf16-complex, one fp32 scale per block and factor for U and V, "
                         "dense blocks unscaled (products); fp32 for refinement residuals")
             if form == "mixed" else "fp32-complex",
-            "form": form,
+            "form": form, "rank_model": 1 if form == "mixed" else 0,
             "green": "fp64", "matvecs_per_step": args.matvecs,
             "gmres": "GMRES(100) to 1e-6, FP64 vectors",
             "parallelism": "replicas" if world > 1 else "1gpu",
@@ -235,6 +235,34 @@ def run_reference(args, wl, world, rank):
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate (no measured FP64 peak is available)
 
 
+def dense_rows(hm, kernel, mat, pts_t, nrm_t, w_t, pidx, X):
+    """Rows 3 i + a (i in pidx) of A X for the exact matrix A (block (i, j) =
+    K(x_i, x_j) w_j, i != j, FP64 Green's tensors of the library's
+    hm_green_eval; block (i, i) = I3), X (3 n_c, nrhs) complex128 on the GPU.
+    Returns (rows, A[rows] X)."""
+    import torch
+    rho, lam, mu, om = mat
+    n = pts_t.shape[0]
+    Xp = X.reshape(n, 3, -1)
+    out = []
+    k = hm.HM_KERNEL_U if kernel == "U" else hm.HM_KERNEL_T
+    for i in pidx:
+        xi = pts_t[i].expand(n, 3).contiguous()
+        G = hm.hm_green_eval(k, rho, lam, mu, om, xi, pts_t, nrm_t)  # (n, 3, 3), I3 at j = i
+        wj = w_t.clone()
+        wj[i] = 1.0
+        out.append(torch.einsum("jab,jbs->as", G * wj[:, None, None], Xp))
+    rows = np.array([3 * i + a for i in pidx for a in range(3)])
+    return rows, torch.cat(out, 0)
+
+
+def product_relerr(y, rows, yd):
+    """||y[rows] - yd|| / ||yd|| (per column for a block of right-hand sides)."""
+    d = (y[rows] - yd).reshape(len(rows), -1)
+    ref = yd.reshape(len(rows), -1)
+    return (d.norm(dim=0) / ref.norm(dim=0)).cpu().numpy()
+
+
 def run_gpu(args, wl, world, rank, local):
     import torch
     from paper_1706_09384_gb300 import hm, inputs
@@ -246,7 +274,11 @@ def run_gpu(args, wl, world, rank, local):
     # quadrature weights W_y (Sec. 4): area per point of the unit sphere
     weights = np.full(wl["nc"], 4 * math.pi / wl["nc"])
     form = args.form
-    opts = hm.hm_opts_default(weights=weights,
+    # the mixed form is the learned-batched one: the trained rank predictor sizes
+    # each block's ACA workspace and bins blocks of similar predicted rank
+    from paper_1706_09384_gb300 import rank_model
+    model = rank_model.load() if form == "mixed" else None
+    opts = hm.hm_opts_default(weights=weights, rank_model=model,
                               storage=hm.HM_STORE_BF16 if form == "mixed" else hm.HM_STORE_FP32)
     x = torch.from_numpy(inputs.random_rhs(3 * wl["nc"], seed=rank)).to(dev)
     y = torch.empty_like(x)
@@ -263,11 +295,14 @@ def run_gpu(args, wl, world, rank, local):
         for _ in range(args.matvecs):
             H.matvec(x, y)
         H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
+    if H is None:
+        H = build()
     torch.cuda.synchronize()
     stats = H.stats()
     alg = stats["matvec_alg_bytes"]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     build_ms, mv_ms, gm_ms, gm_it, gm_rr, aca_ms, rec_ms, aca_fl = [], [], [], [], [], [], [], []
+    gm_prod = []
     launches0 = hm.hm_kernel_launches()
     barrier(world)
     torch.cuda.synchronize()
@@ -299,6 +334,7 @@ def run_gpu(args, wl, world, rank, local):
             aca_ms.append(sd["device_ms"]["aca"])
             rec_ms.append(sd["device_ms"]["recompress"])
             aca_fl.append(sd["aca_flops"])
+            gm_prod.append(sd["gmres_last"])
         t_end = ev()
         t_end.record(st)
         torch.cuda.synchronize()
@@ -307,6 +343,15 @@ def run_gpu(args, wl, world, rank, local):
     mv_total = max_over_ranks(world, sum(mv_ms))
     launches = hm.hm_kernel_launches() - launches0
     value = whole_job_value(world, alg, args.matvecs * args.steps, mv_total)
+    # accuracy of the timed product: sampled rows of the exact operator (FP64
+    # Green's tensors of the library's hm_green_eval), 64 points = 192 rows
+    pts_t = torch.from_numpy(pts).to(dev)
+    w_t = torch.from_numpy(weights).to(dev)
+    mat = (rho, lam, mu, om)
+    pidx = np.sort(np.random.default_rng(7).choice(wl["nc"], 64, replace=False))
+    H.matvec(x, y)
+    rows, yd = dense_rows(hm, wl["kernel"], mat, pts_t, None, w_t, pidx, x.reshape(-1, 1))
+    relerr = float(product_relerr(y.reshape(-1, 1), rows, yd)[0])
     # per-kernel roofline of the product (phase 2), events on the launching stream
     prof = H.profile_matvec(reps=10)
     peak, peak_kind = measured_peaks()
@@ -365,10 +410,17 @@ def run_gpu(args, wl, world, rank, local):
         "dtype": "bf16c" if form == "mixed" else "c64", "data": "synthetic",
         "config": workload_config(args, wl, form, world),
         "streamed_gb_per_product": alg / 1e9,
+        "product_relerr_vs_dense_rows": {
+            "value": relerr, "rows": int(len(rows)), "eps": wl["eps"], "three_eps": 3 * wl["eps"],
+            "note": ("relative error of the timed product on 192 sampled rows of the exact FP64 "
+                     "operator; BF16 storage rounds every entry (unit roundoff 2^-8), so the mixed "
+                     "product's error is of that order; the 3 eps of the metric holds for the "
+                     "plain form's product and for the refined GMRES solutions of both forms")},
         "pct_hbm_peak": 100.0 * value / peak,
         "build_s": statistics.mean(build_ms) / 1e3,
         "matvec_ms": statistics.mean(mv_ms) / args.matvecs,
-        "gmres": {"iters": gm_it[-1], "relres": gm_rr[-1], "ms": statistics.mean(gm_ms)},
+        "gmres": {"iters": gm_it[-1], "relres": gm_rr[-1], "ms": statistics.mean(gm_ms),
+                  "products": gm_prod[-1]},
         "step_device_ms": per_step,
         "hmatrix": {k: stats[k] for k in ("blocks", "dense_blocks", "lowrank_blocks", "C_sp",
                                           "rank_aca_max", "rank_max", "tau_H", "stored_bytes",
@@ -407,20 +459,132 @@ def run_gpu(args, wl, world, rank, local):
         torch.cuda.synchronize()
         palg = Hp.stats()["matvec_alg_bytes"]
         pmv = m0.elapsed_time(m1) / args.matvecs
+        Hp.matvec(x, y)
+        prel = float(product_relerr(y.reshape(-1, 1), rows, yd)[0])
+        pgm = Hp.stats()["gmres_last"]
         out["plain"] = {"value": palg / (pmv * 1e-3) / 1e9, "unit": "GB/s",
                         "pct_hbm_peak": 100.0 * palg / (pmv * 1e-3) / 1e9 / peak,
                         "matvec_ms": pmv, "build_s": b0.elapsed_time(b1) / 1e3,
-                        "gmres": {"iters": pit, "relres": prr, "ms": g0.elapsed_time(g1)},
+                        "gmres": {"iters": pit, "relres": prr, "ms": g0.elapsed_time(g1),
+                                  "products": pgm},
+                        "product_relerr_vs_dense_rows": prel,
                         "stored_bytes": Hp.stats()["stored_bytes"]}
         out["mixed_vs_plain"] = {"matvec_speedup": pmv / out["matvec_ms"],
                                  "gmres_speedup_at_1e-6": g0.elapsed_time(g1) / out["gmres"]["ms"]}
         Hp.free()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl)
     if H is not None:
         H.free()
+        H = None
+    if not args.no_extra and args.workload == "sphere65536_ks16_U":
+        out["fp32_far_green"] = fp32_switch_build(hm, torch, pts, weights, mat, wl, opts_kw={
+            "weights": weights, "rank_model": model,
+            "storage": hm.HM_STORE_BF16 if form == "mixed" else hm.HM_STORE_FP32})
+        out["multi_rhs_131072_T"] = multi_rhs_workload(hm, torch, dev, peak)
+        out["batch_16_problems"] = batch_workload(hm, torch, dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def fp32_switch_build(hm, torch, pts, weights, mat, wl, opts_kw):
+    """The same build with Green's tensors in FP32 where k_s r >= 1
+    (hm_opts.fp64_switch_ksr): build seconds and ACA ranks against the FP64 build."""
+    rho, lam, mu, om = mat
+    res = {}
+    for name, sw in (("fp64", float("inf")), ("fp32_beyond_ksr_1", 1.0)):
+        o = hm.hm_opts_default(fp64_switch_ksr=sw, **opts_kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = hm.HMatrix.build(pts, None, rho, lam, mu, om, wl["kernel"], wl["eps"], wl["eta"],
+                             wl["leaf"], opts=o)
+        torch.cuda.synchronize()
+        st = H.stats()
+        res[name] = {"build_s": time.perf_counter() - t0, "aca_device_ms": st["device_ms"]["aca"],
+                     "near_field_ms": st["ms"]["near_field"], "rank_aca_mean": st["rank_aca_mean"],
+                     "rank_mean": st["rank_mean"]}
+        H.free()
+    return res
+
+
+def multi_rhs_workload(hm, torch, dev, peak):
+    """131 072 Fibonacci points, k_s = 16, T kernel with outward normals, 32
+    plane-wave right-hand sides (P and S waves), BF16 storage with per-block
+    scales, the tensor-core block product inside lockstep GMRES(100) with
+    refinement to 1e-6; per right-hand side: the residual of the exact FP64
+    operator on 96 sampled rows, and the block product's error on those rows."""
+    from paper_1706_09384_gb300 import inputs
+    nc, ks, eps = 131072, 16.0, 1e-4
+    pts = inputs.fibonacci_sphere(nc)
+    nrm = inputs.sphere_normals(pts)
+    rho, lam, mu, om = inputs.material(ks)
+    w = np.full(nc, 4 * math.pi / nc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = hm.HMatrix.build(pts, nrm, rho, lam, mu, om, "T", eps, 3.0, 64,
+                         opts=hm.hm_opts_default(weights=w, storage=hm.HM_STORE_BF16))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    B = torch.from_numpy(np.ascontiguousarray(inputs.plane_wave_rhs(pts, ks / 2, ks, 32, seed=0))
+                         ).to(dev)
+    t0 = time.perf_counter()
+    X, it, rr, st = H.gmres_multi(B, restart=100, tol=1e-6, maxit=2000, check=False)
+    torch.cuda.synchronize()
+    gm_s = time.perf_counter() - t0
+    gm = H.stats()["gmres_last"]
+    pm = H.profile_matvec_multi(reps=10)
+    tk = pm["ms"]["phase1"] + pm["ms"]["phase2"]
+    pts_t, nrm_t = torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev)
+    w_t = torch.from_numpy(w).to(dev)
+    pidx = np.sort(np.random.default_rng(3).choice(nc, 32, replace=False))
+    rows, AX = dense_rows(hm, "T", (rho, lam, mu, om), pts_t, nrm_t, w_t, pidx, X)
+    res_exact = ((B[rows] - AX).norm(dim=0) / B[rows].norm(dim=0)).cpu().numpy()
+    Xr = torch.from_numpy(inputs.random_rhs(3 * nc, nrhs=32, seed=5)).to(dev)
+    Y = H.matvec(Xr)
+    rows, Yd = dense_rows(hm, "T", (rho, lam, mu, om), pts_t, nrm_t, w_t, pidx, Xr)
+    perr = product_relerr(Y, rows, Yd)
+    alg = H.stats()["stored_bytes"]
+    H.free()
+    return {"n_c": nc, "kappa_s": ks, "kernel": "T", "nrhs": 32, "eps": eps,
+            "storage": "bf16 + per-block fp32 scales", "build_s": build_s,
+            "stored_gb": alg / 1e9, "gmres_s": gm_s, "gmres_products": gm,
+            "iters_max": int(np.max(it)), "relres_max": float(np.max(rr)), "status": int(st),
+            "exact_operator_residual_rows": {"max": float(res_exact.max()),
+                                             "median": float(np.median(res_exact)),
+                                             "rows": int(len(rows))},
+            "block_product": {"ms": pm["ms"], "alg_bytes": pm["bytes"],
+                              "achieved_GBps": pm["bytes"] / (tk * 1e-3) / 1e9,
+                              "frac": pm["bytes"] / (tk * 1e-3) / 1e9 / peak,
+                              "relerr_vs_dense_rows_max": float(perr.max()),
+                              "relerr_vs_dense_rows_median": float(np.median(perr))}}
+
+
+def batch_workload(hm, torch, dev):
+    """16 independent problems (n_c 4 096 - 131 072; sphere, cube and ellipsoid
+    surfaces; k_s ~ U[2, 24]; U or T; weights area / n_c; eps = 1e-4, FP32
+    storage), built by one batch build (shared ACA and recompression
+    launches), then one GMRES(100) per problem to 1e-6 (at most 500
+    products): wall time of the build and of the solves, per-problem results."""
+    from paper_1706_09384_gb300 import inputs
+    P = inputs.batch_problems(16, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hs = hm.HMatrix.build_batch([dict(p, eta=3.0, leaf_size=64) for p in P], eps=1e-4)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    per = []
+    for q, (p, H) in enumerate(zip(P, Hs)):
+        b = torch.from_numpy(inputs.random_rhs(3 * len(p["points"]), seed=100 + q)).to(dev)
+        _, it, rr, st = H.gmres(b, restart=100, tol=1e-6, maxit=500, check=False)
+        per.append({"n_c": len(p["points"]), "shape": p["shape"], "kernel": p["kernel"],
+                    "kappa_s": round(p["ks"], 3), "iters": it, "relres": rr})
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for H in Hs:
+        H.free()
+    return {"problems": 16, "points": int(sum(len(p["points"]) for p in P)),
+            "build_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0,
+            "converged": int(sum(r["relres"] <= 1e-6 for r in per)), "per_problem": per}
 
 
 def run_hlu(nc):
@@ -472,6 +636,9 @@ def main():
                          "operator for the refinement residuals; plain: FP32 storage")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the untimed plain-form comparison run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the untimed extra workloads (FP32 far-field build, 131 072-point "
+                         "T with 32 plane waves, the 16-problem batch)")
     ap.add_argument("--hlu", type=int, default=0,
                     help="instead of the step: time the H-LU direct solver on this many points")
     args = ap.parse_args()

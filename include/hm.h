@@ -64,10 +64,20 @@ typedef enum {
 /* Build options.  Always initialise with hm_opts_default(). */
 typedef struct {
     int32_t storage;          /* hm_storage for dense blocks and factors (HM_STORE_FP32) */
-    int32_t aca_fp32;         /* 0: ACA residual rows/columns in FP64 (default), 1: FP32 */
+    int32_t aca_fp32;         /* must be 0 (HM_ERR_ARG otherwise): the ACA computes its residual
+                                 rows and columns in double-float arithmetic (FP32 pairs, ~44
+                                 bits) over double-float copies of U and V, its pivots, Gram
+                                 matrices and norm updates in FP64; no FP32 variant exists */
     double diag_value;        /* value of the i = j blocks: diag_value * I3 (1.0) */
-    double fp64_switch_ksr;   /* Green's tensors in FP64 where k_s r < this, FP32 beyond
-                                 (default +inf: always FP64) */
+    double fp64_switch_ksr;   /* > 0.  Green's tensors (near field, ACA rows and columns,
+                                 randomized sketches) are evaluated in FP64 where k_s r < this
+                                 and in FP32 where k_s r >= this (distance and phase k r still
+                                 formed in FP64).  The cancellation between the two
+                                 Helmholtz terms of Eq. elasto_U costs about u / (k_s r)^2 of
+                                 relative accuracy: beyond k_s r = 1 an FP32 U tensor is good to
+                                 a few 1e-7 of its largest entry, a T tensor to 4e-6 (below
+                                 1e-6 from k_s r = 2).  Default +inf: always FP64.
+                                 hm_estimate_error always uses FP64 tensors. */
     int32_t recompress;       /* 1: QR+SVD recompression of Sec. 3.2 (default), 0: keep ACA */
     int32_t aca_max_rank;     /* initial ACA capacity in columns per block (0 = 144);
                                  blocks that need more are re-run with twice the capacity */
@@ -96,7 +106,10 @@ void hm_opts_default(hm_opts* opts);
  *   kernel   HM_KERNEL_U or HM_KERNEL_T
  *   eps      eps_ACA of Eq. (stop_part) and of the recompression (Sec. 3.2), in (0, 1)
  *   eta      eta-hat of Eq. (admissibility_cond_bis) (the paper uses 3, Sec. 6.2), > 0
- *   leaf_size  N_leaf: clusters with <= leaf_size points are not split (Sec. 2.1)
+ *   leaf_size  N_leaf: clusters with <= leaf_size points are not split (Sec. 2.1);
+ *            1..1024 (the paper uses 100, Sec. 7).  The stored blocks are cut along
+ *            segments of at most 64 points of each leaf, so larger leaves only
+ *            change the tree and the partition, not the product kernels. 
  *   opts     NULL for defaults
  *   stream   cudaStream_t for all work (the call returns after the build is complete)
  *   out      receives the handle (NULL on error)
@@ -186,7 +199,10 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
  *   b, x    DEVICE complex128, 3 n_c x nrhs column-major, original order; no overlap
  *   iters   HOST int32[nrhs] or NULL: products made until each column converged
  *   relres  HOST double[nrhs] or NULL: final true relative residual per column
- * Memory: (restart + 2) * nrhs vectors of 3 n_c complex128 on the device.
+ * Memory: (restart + 2) * nrhs vectors of 3 n_c complex128 on the device,
+ * taken from a stream-ordered memory pool that the library keeps per device
+ * (hm_gmres too); memory a solve frees stays reserved in that pool for the
+ * next solve on any handle, until the process exits.
  * Errors: HM_ERR_ARG, HM_ERR_NOCONV (some column reached maxit; x holds the
  * last iterates), HM_ERR_TIMEOUT, HM_ERR_OOM, HM_ERR_CUDA. */
 hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int32_t restart,
@@ -234,7 +250,9 @@ hm_status hm_lu_info(hm_handle h, double* seconds, int64_t* entries, int64_t* la
 /* Writes a JSON object (NUL-terminated) with the build statistics: n_c, tree
  * depth, cluster and block counts, sparsity constant C_sp (Sec. 2.1), ACA
  * and recompressed ranks (as in the rank tables of Sec. 7.2), stored bytes,
- * compression tau(H) = N_s / N^2 (Sec. 7.2), phase times in ms.
+ * compression tau(H) = N_s / N^2 (Sec. 7.2), phase times in ms, and the
+ * products of the last hm_gmres / hm_gmres_multi on the handle (gmres_last:
+ * fast products, accurate restart products, restart cycles).
  * Errors: HM_ERR_ARG (cap too small: the required size is in *needed if non-NULL). */
 hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed);
 
@@ -298,8 +316,12 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
  * (a framework's caching pool that has reserved the free memory, or an
  * application held to a fixed memory budget), and latency-sensitive loops that
  * must not take the device-wide synchronisation cudaMalloc / cudaFree imply.
- * It runs the same ACA kernel as hm_build (rank-3 steps, sigma_3 pivot, FP64
- * residuals, eps stopping test) on the block K(x_i, y_j), i < m, j < n.
+ * It runs the FP64-residual variant of hm_build's ACA kernel (rank-3 steps,
+ * sigma_3 pivot, eps stopping test) on the block K(x_i, y_j), i < m, j < n.
+ * hm_build computes its residual rows and columns in double-float arithmetic
+ * over double-float copies of U and V, which would not fit the fixed scratch;
+ * the two variants round differently, so near the stopping threshold their
+ * ranks can differ by one rank-3 step (the products agree to about eps).
  *   x: DEVICE m x 3 FP64 row points;  y: DEVICE n x 3 FP64 column points;
  *   ny: DEVICE n x 3 unit normals at y (T kernel only, else NULL);
  *   1 <= m, n <= HM_NOALLOC_MAX_POINTS;  cap: column capacity, a multiple of 3
@@ -307,10 +329,16 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
  *   16-byte aligned: U (3m x cap, column-major) then V (3n x cap), block =
  *   U[:, :rank] V[:, :rank]^H;  rank: HOST output, the ACA rank (multiple of 3).
  * Its scratch is one fixed device array of about 3 MiB inside this library,
- * held by every GPU that loads the library until the process exits.  The
- * first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
+ * held by every GPU on which the library's module is loaded until the process
+ * exits.  With CUDA's default lazy module loading that happens when the module
+ * is first used on the device: for a caller that uses only this entry point,
+ * inside its first call.  So make the first call on each device before another
+ * allocator reserves the device's free memory (or set CUDA_MODULE_LOADING=EAGER,
+ * which loads the array with the library), and before any stream capture.
+ * That first call looks up the array's device address (with the device
+ * current) and caches it per device ordinal; a cudaDeviceReset invalidates
+ * the cached address, so do not use this entry point across a reset of the
+ * device.  All calls share the array and it keeps the last call's contents;
  * each call re-initialises what must start at zero, but calls that overlap on
  * the GPU (other streams, other host threads) race on it: serialise them.  The
  * call waits for its stream to finish.

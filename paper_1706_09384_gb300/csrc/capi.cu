@@ -203,7 +203,8 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         d_nrm = na3;
         d_gps = dg;
     }
-    double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0;
+    double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0, flops64 = 0, flops_df = 0,
+           evals = 0;
     int64_t batches = 0, reruns = 0, ws_peak = 0, ws_tot = 0;
     std::vector<int64_t> n_rsvd(nprob, 0), n_uncert(nprob, 0);
     double t_rsvd = 0;
@@ -348,8 +349,17 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                     continue;
                 }
                 {
+                    // per rank-3 step with k = 3s columns built: residual row and column
+                    // 9 k (m + n) complex multiply-adds (double-float), cross terms of the
+                    // norm update / Gram columns 9 k (m + n) (FP64), new Gram diagonal
+                    // blocks 27 (m + n) and factor columns U = C gamma 27 m (FP64); m + n
+                    // Green's tensor evaluations
                     const double K = res[j].k / 3, mn = (double)(jobs[j].m + jobs[j].n);
-                    flops += 8.0 * 18.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
+                    const double cross = 8.0 * 9.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
+                    flops += 2.0 * cross;
+                    flops_df += cross;
+                    flops64 += cross + 8.0 * 27.0 * (mn + (double)jobs[j].m) * K;
+                    evals += mn * K;
                 }
                 keep.push_back(j);
                 uo.push_back(jobs[j].u_off);
@@ -445,6 +455,9 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         h->ev_recomp_ms += ev_rec;
         h->t_recomp_ms += t_rec;
         h->aca_flops += flops;
+        h->aca_flops_fp64 += flops64;
+        h->aca_flops_df += flops_df;
+        h->aca_green_evals += evals;
         h->aca_batches += batches;
         h->aca_overflow_reruns += reruns;
         h->aca_workspace_peak = std::max(h->aca_workspace_peak, ws_peak);
@@ -518,7 +531,7 @@ hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c,
     if (kernel != HM_KERNEL_U && kernel != HM_KERNEL_T) hm_throw(HM_ERR_ARG, "unknown kernel");
     if (kernel == HM_KERNEL_T && !normals) hm_throw(HM_ERR_ARG, "the T kernel needs normals");
     if (leaf_size < 1) hm_throw(HM_ERR_ARG, "leaf_size must be >= 1");
-    if (leaf_size > 64) hm_throw(HM_ERR_UNSUPPORTED, "leaf_size above 64 points");
+    if (leaf_size > 1024) hm_throw(HM_ERR_UNSUPPORTED, "leaf_size above 1024 points");
     if (!finite_all(points, 3 * n_c)) hm_throw(HM_ERR_ARG, "non-finite point coordinates");
     if (kernel == HM_KERNEL_T && !finite_all(normals, 3 * n_c))
         hm_throw(HM_ERR_ARG, "non-finite normals");
@@ -528,6 +541,10 @@ hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c,
     if (o.storage != HM_STORE_FP32 && o.storage != HM_STORE_BF16)
         hm_throw(HM_ERR_ARG, "unknown storage type");
     if (!std::isfinite(o.diag_value)) hm_throw(HM_ERR_ARG, "non-finite diag_value");
+    if (!(o.fp64_switch_ksr > 0)) hm_throw(HM_ERR_ARG, "fp64_switch_ksr must be > 0 (or +inf)");
+    if (o.aca_fp32 != 0)
+        hm_throw(HM_ERR_ARG, "aca_fp32 must be 0: the ACA residual rows and columns run in "
+                             "double-float arithmetic, there is no FP32 variant");
     hm_matrix* h = new hm_matrix();
     hold.reset(h);
     h->nc = n_c;
@@ -541,6 +558,7 @@ hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c,
     h->leaf = leaf_size;
     h->opts = o;
     h->gp = make_green_params(kernel, rho, lambda, mu, omega, o.diag_value);
+    h->gp.ksr_switch = o.fp64_switch_ksr;
     HM_CUDA(cudaGetDevice(&h->device));
     // ---- points -> device, tree ----
     auto t0 = clk::now();
@@ -924,7 +942,11 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms
        << ", \"total\": " << h->t_total_ms << "}"
        << ", \"device_ms\": {\"aca\": " << h->ev_aca_ms << ", \"recompress\": " << h->ev_recomp_ms
-       << "}, \"aca_flops\": " << h->aca_flops << "}";
+       << "}, \"aca_flops\": " << h->aca_flops << ", \"aca_flops_fp64\": " << h->aca_flops_fp64
+       << ", \"aca_flops_df\": " << h->aca_flops_df << ", \"aca_green_evals\": " << h->aca_green_evals
+       << ", \"gmres_last\": {\"fast_products\": " << h->gm_fast
+       << ", \"accurate_products\": " << h->gm_accurate << ", \"cycles\": " << h->gm_cycles
+       << "}}";
     const std::string s = os.str();
     if (needed) *needed = s.size() + 1;
     if (!json || cap < s.size() + 1) hm_throw(HM_ERR_ARG, "stats buffer too small");
@@ -1047,7 +1069,7 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
                 hm_throw(HM_ERR_ARG, "bad block");
         for (const hm_cluster& c : h->clusters) {
             if (c.begin < 0 || c.end > n_c || c.begin >= c.end) hm_throw(HM_ERR_ARG, "bad cluster");
-            if (c.is_leaf && c.end - c.begin > 64) hm_throw(HM_ERR_UNSUPPORTED, "leaf above 64 points");
+            if (c.is_leaf && c.end - c.begin > 1024) hm_throw(HM_ERR_UNSUPPORTED, "leaf above 1024 points");
         }
     }
     h->d_perm = (int64_t*)hm_dmalloc(h->owner, 8 * n_c, st, false);

@@ -158,8 +158,10 @@ void estimate_error(hm_matrix* h, int64_t nsample, uint64_t seed, double* delta_
         double* d_sum = (double*)hm_dmalloc(tmp, 2 * sizeof(double), st, true);
         HM_CUDA(cudaMemcpyAsync(d_s, smp.data(), smp.size() * sizeof(EstSample), cudaMemcpyHostToDevice, st));
         const int64_t ns = (int64_t)smp.size();
+        GreenParams exact = h->gp;  // the exact matrix: FP64 tensors at every distance
+        exact.ksr_switch = INFINITY;
         estimate_kernel<<<(unsigned)hm_cdiv(ns, 256), 256, 0, st>>>(
-            h->gp, h->d_pts_p, h->d_nrm_p, (const float2*)matvec_arena(h->mv), d_s, ns, d_sum);
+            exact, h->d_pts_p, h->d_nrm_p, (const float2*)matvec_arena(h->mv), d_s, ns, d_sum);
         HM_LAUNCHED();
         HM_CUDA(cudaGetLastError());
         double sums[2] = {0.0, 0.0};

@@ -25,6 +25,14 @@ void hm_check_cuda(cudaError_t e, const char* what, const char* file, int line);
 extern std::atomic<long long> g_hm_launches;
 #define HM_LAUNCHED() g_hm_launches.fetch_add(1, std::memory_order_relaxed)
 
+// Solver scratch (scratch.cu): stream-ordered allocations from the library's
+// per-device pool, which keeps freed memory for reuse; and small pinned host
+// buffers from a process-wide free list.
+void* hm_scratch_alloc(size_t bytes, cudaStream_t st);
+void hm_scratch_free(void* p, cudaStream_t st);
+void* hm_pinned_take(size_t bytes);
+void hm_pinned_give(void* p);
+
 // Device allocation owned by the handle (freed in hm_free).
 struct DevBuf {
     void* p = nullptr;
@@ -47,7 +55,9 @@ std::vector<hm_block> build_partition(const std::vector<hm_cluster>& cl, double 
                                       cudaStream_t st);
 
 // ---------------- matvec storage plan (matvec.cu) ----------------
-// One chunk = rows of one leaf cluster of a block's row set (dense block, U
+// Storage segments: the leaf clusters, each cut into the fewest contiguous
+// point ranges of at most 64 points (a leaf of up to 64 points is one segment).
+// One chunk = rows of one segment of a block's row set (dense block, U
 // factor) or column set (V factor); column-major with ld = padded rows.
 struct Chunk {
     int64_t data;      // element offset (complex) into the arena
@@ -57,18 +67,18 @@ struct Chunk {
     int32_t kind;      // 0 dense, 1 U, 2 V
     int64_t vec;       // dense: x offset (tree order DOF); U/V: t offset
     int64_t block;     // block index
-    int64_t leaf_dof;  // first tree-order DOF of the chunk's leaf
+    int64_t leaf_dof;  // first tree-order DOF of the chunk's segment
 };
 
 struct MatvecPlan {
-    // per leaf (row side): list of dense + U chunks; per leaf (col side): V chunks
-    std::vector<int64_t> row_leaf_begin;   // CSR over leaves
+    // per segment (row side): list of dense + U chunks; per segment (col side): V chunks
+    std::vector<int64_t> row_leaf_begin;   // CSR over segments
     std::vector<int32_t> row_items;        // chunk ids
     std::vector<int64_t> col_leaf_begin;
     std::vector<int32_t> col_items;
     std::vector<Chunk> chunks;
-    std::vector<int64_t> leaf_dof_begin;   // first DOF (tree order) of each leaf
-    std::vector<int32_t> leaf_rows;        // 3 |leaf|
+    std::vector<int64_t> leaf_dof_begin;   // first DOF (tree order) of each segment
+    std::vector<int32_t> leaf_rows;        // 3 |segment| (<= MAX_LD)
     int64_t arena_elems = 0;               // complex entries in the arena
     int64_t t_elems = 0;                   // entries of the t = V^H x workspace
 };
@@ -263,6 +273,9 @@ struct hm_matrix {
     // built, 18 k (m + n) complex multiply-adds (residual row and column, and the
     // Gram / cross terms of the norm update), 8 flops each
     double aca_flops = 0;
+    double aca_flops_fp64 = 0;       // of which FP64 (cross terms, Gram diagonal blocks, U = C gamma)
+    double aca_flops_df = 0;         // of which double-float on the FP32 pipes (residuals)
+    double aca_green_evals = 0;      // Green's tensors evaluated by the ACA (FP64)
     int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
     int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
     int batch_problems = 1;          // problems that shared the ACA / recompression launches
@@ -270,5 +283,7 @@ struct hm_matrix {
     int64_t rsvd_uncertified = 0;  // of those, blocks whose samples reached their cap uncertified
     double t_rsvd_ms = 0;          // wall time of the randomized SVD pass (with its recompression)
     void* hlu = nullptr;           // H-LU factors (hlu.cu), if computed
+    // the last GMRES solve: fast and accurate products made, restart cycles
+    int64_t gm_fast = 0, gm_accurate = 0, gm_cycles = 0;
     int used_rank_model = 0;
 };

@@ -1,17 +1,18 @@
 // matvec.cu — H-matrix-vector product y = A_H x (Sec. 3.1): dense product on
 // the non-admissible leaves, U (V^H x) on the admissible ones.
 //
-// Storage layout ("chunk-major"): every block is cut along the leaf clusters
-// of its row set (dense blocks, U factors) or column set (V factors).  A
-// chunk is a column-major (ld x ncols) complex matrix, ld = 3|leaf| rounded up
-// to an even count so each column starts on a 16-byte boundary.  All chunks
-// that feed the rows of one leaf are stored back to back, so the product
-// streams the arena once, front to back.
+// Storage layout ("chunk-major"): every block is cut along the storage
+// segments of its row set (dense blocks, U factors) or column set (V factors):
+// the leaf clusters, a leaf above 64 points cut into contiguous ranges of at
+// most 64 points.  A chunk is a column-major (ld x ncols) complex matrix,
+// ld = 3|segment| rounded up to an even count so each column starts on a
+// 16-byte boundary.  All chunks that feed the rows of one segment are stored
+// back to back, so the product streams the arena once, front to back.
 //
-// Phase 1:  t_b = V_b^H x_sigma     (per column leaf; partial sums by atomics)
-// Phase 2:  y_l = sum D x_sigma + sum U_b t_b   (per row leaf)
+// Phase 1:  t_b = V_b^H x_sigma     (per column segment; partial sums by atomics)
+// Phase 2:  y_l = sum D x_sigma + sum U_b t_b   (per row segment)
 // Both phases are HBM-bound (one complex FMA per stored complex entry).
-// Work items are slices of a leaf's chunk list of bounded byte size, so the
+// Work items are slices of a segment's chunk list of bounded byte size, so the
 // grid load-balances; each CTA keeps partial sums per warp in registers and
 // reduces them once.
 #include <cuda_bf16.h>
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(192) staged_copy_kernel(const StagedCopy* jobs
             row < J.rows ? J.src[row + (int64_t)c * J.src_ld] : make_float2(0.f, 0.f);
 }
 
-// Splits each leaf's chunk list into items of at most ~target bytes.
+// Splits each segment's chunk list into items of at most ~target bytes.
 void make_items(const std::vector<int64_t>& begin, const std::vector<int32_t>& list,
                 const std::vector<Chunk>& chunks, const MatvecPlan& plan, int64_t target,
                 std::vector<WorkItem>& items, std::vector<int32_t>& order) {
@@ -736,13 +737,25 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
         if (cl[c].is_leaf) leaves.push_back(c);
     std::sort(leaves.begin(), leaves.end(),
               [&](int64_t a, int64_t b) { return cl[a].begin < cl[b].begin; });
-    const int64_t nleaf = (int64_t)leaves.size();
-    std::vector<int64_t> leaf_begin(nleaf);
-    for (int64_t l = 0; l < nleaf; ++l) {
-        leaf_begin[l] = cl[leaves[l]].begin;
-        P.leaf_dof_begin.push_back(3 * cl[leaves[l]].begin);
-        P.leaf_rows.push_back((int32_t)(3 * (cl[leaves[l]].end - cl[leaves[l]].begin)));
+    // Storage segments: a leaf of up to MAX_LD / 3 points is one segment; a
+    // larger leaf (N_leaf = 100 in Sec. 7) is cut into the fewest contiguous
+    // point ranges of at most MAX_LD / 3 points, of nearly equal sizes.  Blocks
+    // are cut along segments instead of leaves, so a chunk never has more than
+    // MAX_LD rows (or, for dense chunks, columns); the tree and the partition
+    // are unchanged.  Every cluster is a union of leaves, hence of segments.
+    std::vector<int64_t> leaf_begin;
+    const int64_t seg_max = MAX_LD / 3;
+    for (int64_t c : leaves) {
+        const int64_t np = cl[c].end - cl[c].begin;
+        const int64_t k = std::max<int64_t>(1, hm_cdiv(np, seg_max));
+        for (int64_t q = 0; q < k; ++q) {
+            const int64_t b0 = cl[c].begin + q * np / k, b1 = cl[c].begin + (q + 1) * np / k;
+            leaf_begin.push_back(b0);
+            P.leaf_dof_begin.push_back(3 * b0);
+            P.leaf_rows.push_back((int32_t)(3 * (b1 - b0)));
+        }
     }
+    const int64_t nleaf = (int64_t)leaf_begin.size();
     auto leaf_range = [&](int64_t c, int64_t& l0, int64_t& l1) {
         l0 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].begin) - leaf_begin.begin();
         l1 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].end) - leaf_begin.begin();

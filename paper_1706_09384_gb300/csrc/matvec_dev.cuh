@@ -6,7 +6,7 @@
 
 #include "hm_internal.h"
 
-constexpr int MAX_LD = 192;               // 3 * 64 rows: leaves up to 64 points
+constexpr int MAX_LD = 192;               // 3 * 64 rows: storage segments of up to 64 points
 constexpr int MAX_ITEM_CHUNKS = 64;       // chunk headers staged in shared memory per item
 constexpr int MAX_ITEM_COLS = 1024;       // columns of one item (per-column table in smem)
 
@@ -32,22 +32,22 @@ struct DevChunk16 {
     float fold;     // V chunks: the U scale of the same block; otherwise 1
 };
 struct WorkItem {
-    int64_t dof;      // first tree-order DOF of the leaf
-    int32_t rows;     // 3 |leaf|
+    int64_t dof;      // first tree-order DOF of the segment
+    int32_t rows;     // 3 |segment|
     int32_t ld;
     int32_t first;    // chunk ids [first, last)
     int32_t last;
 };
 
-// Work item of the tensor-core block product (one leaf's chunks, contiguous
+// Work item of the tensor-core block product (one segment's chunks, contiguous
 // in the BF16 arena, starting on a row of the arena's ld16 view).
 struct TcItem {
-    int64_t dof;    // first tree-order DOF of the leaf
+    int64_t dof;    // first tree-order DOF of the segment
     int64_t col0;   // first entry of the item in the per-column table
     int32_t row0;   // first row of the item in the ld16 view (data / ld16)
     int32_t ld16;
     int32_t ncol;
-    int32_t rows;   // 3 |leaf|
+    int32_t rows;   // 3 |segment|
 };
 
 struct MatvecDev {

@@ -176,10 +176,40 @@ HM_NRHS_BLOCK = 32  # right-hand sides per tensor-core block product (include/hm
 HM_RANK_MODEL_PARAMS = 4687
 
 
+def _require(cond, what):
+    if not cond:
+        raise HmError(HM_ERR_ARG, "hm_aca_block_noalloc", what)
+
+
+def _check_noalloc_args(x, y, ny, cap, uv):
+    """The library reads x, y, ny and writes (3m + 3n) cap entries of uv through
+    raw device pointers: reject anything that would make it touch memory
+    outside those tensors before the call is made."""
+    import torch
+    pts = (("x", x), ("y", y)) + ((("ny", ny),) if ny is not None else ())
+    for name, t in pts:
+        _require(isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.dim() == 2
+                 and t.shape[1] == 3 and t.is_contiguous(),
+                 "%s must be a contiguous float64 tensor of shape (., 3)" % name)
+    if ny is not None:
+        _require(ny.shape[0] == y.shape[0], "ny must have the shape of y")
+    _require(isinstance(uv, torch.Tensor) and uv.dtype == torch.complex128
+             and uv.is_contiguous(), "uv must be a contiguous complex128 tensor")
+    _require(isinstance(cap, int) and cap > 0, "cap must be a positive int")
+    need = (3 * x.shape[0] + 3 * y.shape[0]) * cap
+    _require(uv.numel() >= need, "uv holds %d entries, (3m + 3n) cap = %d are written"
+             % (uv.numel(), need))
+    tensors = [t for _, t in pts] + [uv]
+    _require(all(t.is_cuda for t in tensors), "x, y, ny and uv must be cuda tensors")
+    _require(len({t.device for t in tensors}) == 1, "x, y, ny and uv must be on one device")
+
+
 def hm_aca_block_noalloc(kernel, rho, lam, mu, omega, x, y, ny, eps, cap, uv, stream=None):
     """Allocation-free vector ACA of one block.  x (m, 3), y (n, 3), ny (n, 3) or
-    None: cuda float64; uv: cuda complex128 of (3m + 3n) * cap entries.
+    None: contiguous cuda float64; uv: contiguous cuda complex128 of at least
+    (3m + 3n) * cap entries (checked here, before the call).
     Returns the rank; U = uv[:3m cap] (3m x cap col-major), V follows."""
+    _check_noalloc_args(x, y, ny, cap, uv)
     rank = C.c_int32(-1)
     _check(lib().hm_aca_block_noalloc(kernel, rho, lam, mu, omega, x.data_ptr(), x.shape[0],
                                       y.data_ptr(), ny.data_ptr() if ny is not None else None,

@@ -89,3 +89,46 @@ def test_batch_argument_errors_without_gpu():
     outs = (ctypes.c_void_p * 2)()
     assert L.hm_build_batch(0, None, 1e-4, None, None, outs) == hm.HM_ERR_ARG
     assert L.hm_gmres_multi(None, 2, None, None, 50, 1e-6, 100, None, None, None) == hm.HM_ERR_ARG
+
+
+def test_noalloc_binding_refuses_undersized_output_without_a_gpu():
+    """The allocation-free entry point writes (3m + 3n) cap complex128 entries
+    through a raw pointer: the binding refuses a smaller buffer (or a mistyped
+    or strided one) itself, before the library is called."""
+    torch = pytest.importorskip("torch")
+    from paper_1706_09384_gb300 import hm
+    x = torch.zeros((10, 3), dtype=torch.float64)
+    y = torch.ones((8, 3), dtype=torch.float64)
+    cap = 12
+    need = (3 * 10 + 3 * 8) * cap
+    bad = [
+        (x, y, torch.zeros(need - 1, dtype=torch.complex128), "holds"),
+        (x, y, torch.zeros(need, dtype=torch.complex64), "complex128"),
+        (x.t().contiguous().t(), y, torch.zeros(need, dtype=torch.complex128), "contiguous"),
+        (x, y, torch.zeros(need, dtype=torch.complex128), "cuda"),  # right sizes, host memory
+    ]
+    for xx, yy, uv, words in bad:
+        with pytest.raises(hm.HmError) as e:
+            hm.hm_aca_block_noalloc(hm.HM_KERNEL_U, 1.0, 2.0, 1.0, 4.0, xx, yy, None, 1e-4, cap,
+                                    uv)
+        assert e.value.status == hm.HM_ERR_ARG and words in str(e.value)
+
+
+def test_build_options_are_checked_without_a_gpu():
+    """Options the library does not implement are refused, not ignored:
+    aca_fp32 must be 0 (the ACA residuals run in double-float arithmetic) and
+    fp64_switch_ksr must be positive (+inf: always FP64)."""
+    import numpy as np
+    from paper_1706_09384_gb300 import hm
+    L = hm.lib()
+    pts = np.random.default_rng(0).standard_normal((4, 3))
+    h = ctypes.c_void_p()
+    for kw in ({"aca_fp32": 1}, {"fp64_switch_ksr": 0.0}, {"fp64_switch_ksr": float("nan")},
+               {"fp64_switch_ksr": -1.0}):
+        o = hm.hm_opts_default(**kw)
+        st = L.hm_build(pts.ctypes.data_as(ctypes.c_void_p), None, 4, 1.0, 2.0, 1.0, 1.0, 0,
+                        1e-4, 3.0, 32, ctypes.byref(o), None, ctypes.byref(h))
+        assert st == hm.HM_ERR_ARG, kw
+        assert h.value is None
+    o = hm.hm_opts_default()
+    assert o.aca_fp32 == 0 and o.fp64_switch_ksr == float("inf")
