@@ -52,6 +52,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_profile(kernel_file, kernel_name):
+    """The committed ncu summary of a kernel (profiles/traffic.json), only if the
+    kernel source is unchanged since the capture (sha256 of the .cu file)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1706_09384_gb300", "csrc", kernel_file)
+    if not os.path.exists(p) or not os.path.exists(src):
+        return None
+    d = json.load(open(p)).get(kernel_name)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d if d and d.get("source_sha256") == h else None
+
+
 def kernel_traffic(kernel_file, kernel_name):
     """DRAM bytes per launch from a committed ncu summary, only if the kernel
     source is unchanged since the capture (sha256 of the .cu file)."""
@@ -278,7 +290,11 @@ def run_gpu(args, wl, world, rank, local):
     # each block's ACA workspace and bins blocks of similar predicted rank
     from paper_1706_09384_gb300 import rank_model
     model = rank_model.load() if form == "mixed" else None
-    opts = hm.hm_opts_default(weights=weights, rank_model=model,
+    # the autotuner's cache (launch parameters of the product per GPU and workload
+    # class): the first build sweeps the candidates, later builds read the cache
+    tune_cache = os.path.join(ROOT, "paper_1706_09384_gb300", "_build", "tune_cache.txt")
+    os.makedirs(os.path.dirname(tune_cache), exist_ok=True)
+    opts = hm.hm_opts_default(weights=weights, rank_model=model, tune_cache=tune_cache,
                               storage=hm.HM_STORE_BF16 if form == "mixed" else hm.HM_STORE_FP32)
     x = torch.from_numpy(inputs.random_rhs(3 * wl["nc"], seed=rank)).to(dev)
     y = torch.empty_like(x)
@@ -288,10 +304,12 @@ def run_gpu(args, wl, world, rank, local):
                                 wl["leaf"], opts=opts)
 
     H = None
+    tune_first = None
     for _ in range(args.warmup):
         if H is not None:
             H.free()
         H = build()
+        tune_first = tune_first or H.stats()["tune"]
         for _ in range(args.matvecs):
             H.matvec(x, y)
         H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
@@ -302,6 +320,7 @@ def run_gpu(args, wl, world, rank, local):
     alg = stats["matvec_alg_bytes"]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     build_ms, mv_ms, gm_ms, gm_it, gm_rr, aca_ms, rec_ms, aca_fl = [], [], [], [], [], [], [], []
+    aca_fl64, aca_fldf = [], []
     gm_prod = []
     launches0 = hm.hm_kernel_launches()
     barrier(world)
@@ -334,6 +353,8 @@ def run_gpu(args, wl, world, rank, local):
             aca_ms.append(sd["device_ms"]["aca"])
             rec_ms.append(sd["device_ms"]["recompress"])
             aca_fl.append(sd["aca_flops"])
+            aca_fl64.append(sd["aca_flops_fp64"])
+            aca_fldf.append(sd["aca_flops_df"])
             gm_prod.append(sd["gmres_last"])
         t_end = ev()
         t_end.record(st)
@@ -380,14 +401,26 @@ def run_gpu(args, wl, world, rank, local):
     aca_t = statistics.mean(aca_ms)
     per_step = {"aca_kernel": aca_t, "recompression": statistics.mean(rec_ms),
                 "h_matvec": statistics.mean(mv_ms), "gmres": statistics.mean(gm_ms)}
-    aca_tf = statistics.mean(aca_fl) / (aca_t * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "aca_kernel", "achieved": aca_tf,
+    # FP64 roofline of the ACA: the algorithmic FP64 flops (norm-update cross terms / Gram
+    # columns, new Gram diagonal blocks, U = C gamma) per build over its device time,
+    # against the nominal FP64 rate; the residual rows and columns run in double-float on
+    # the FP32 pipes and are reported beside it
+    f64 = statistics.mean(aca_fl64)
+    aca_tf = f64 / (aca_t * 1e-3) / 1e12
+    prof_aca = kernel_profile("aca.cu", "aca_kernel")
+    roofline = {"bound": "fp64", "kernel": "aca_kernel", "achieved": aca_tf,
                 "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (no measured FP64 peak)",
-                "unit": "TFLOP/s", "frac": aca_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "alg_flops_per_launch": statistics.mean(aca_fl), "ms_per_step": aca_t,
-                "note": "ACA device time per build (all batches); algorithmic flops of the residual "
-                        "rows/columns (run in double-float on the FP32 pipes, ~44 bits) and of the "
-                        "FP64 Gram and norm updates, against the nominal FP64 peak"}
+                "unit": "TFLOP/s", "frac": aca_tf / FP64_PEAK_TFLOPS,
+                "traffic": (prof_aca["bytes_per_model_fp64_flop"] * f64) if prof_aca else None,
+                "alg_fp64_flops_per_launch": f64, "ms_per_step": aca_t,
+                "double_float_flops_per_launch": statistics.mean(aca_fldf),
+                "double_float_tflops": statistics.mean(aca_fldf) / (aca_t * 1e-3) / 1e12,
+                "profile": prof_aca,
+                "note": "ACA device time per build (all batches); FP64 flops of the model (norm-update "
+                        "cross terms and Gram columns 9k(m+n), Gram diagonal 27(m+n), U = C gamma "
+                        "27m complex multiply-adds per rank-3 step); traffic = the ncu DRAM bytes "
+                        "per model FP64 flop of the committed 16384-point capture times this "
+                        "launch's model flops"}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.empty(3 * wl["nc"], dtype=torch.complex128).pin_memory()
     xh.copy_(x.cpu())
@@ -426,6 +459,8 @@ def run_gpu(args, wl, world, rank, local):
                                           "rank_aca_max", "rank_max", "tau_H", "stored_bytes",
                                           "matvec_alg_bytes")},
         "build_ms_phases": stats["ms"],
+        "tune": {"first_build": tune_first, "timed_builds": stats["tune"]["source"],
+                 "nstage": stats["tune"]["nstage"], "item_bytes": stats["tune"]["item_bytes"]},
         "roofline": roofline,
         "roofline_matvec": roof_mv,
         "e2e": {"value": alg / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nb,
@@ -439,7 +474,7 @@ def run_gpu(args, wl, world, rank, local):
         # the plain form on the same workload, once, outside the timed steps
         H.free()
         H = None
-        popts = hm.hm_opts_default(weights=weights)
+        popts = hm.hm_opts_default(weights=weights, tune_cache=tune_cache)
         b0, b1 = ev(), ev()
         b0.record(st)
         Hp = hm.HMatrix.build(pts, None, rho, lam, mu, om, wl["kernel"], wl["eps"], wl["eta"],
@@ -468,6 +503,7 @@ def run_gpu(args, wl, world, rank, local):
                         "gmres": {"iters": pit, "relres": prr, "ms": g0.elapsed_time(g1),
                                   "products": pgm},
                         "product_relerr_vs_dense_rows": prel,
+                        "tune": Hp.stats()["tune"],
                         "stored_bytes": Hp.stats()["stored_bytes"]}
         out["mixed_vs_plain"] = {"matvec_speedup": pmv / out["matvec_ms"],
                                  "gmres_speedup_at_1e-6": g0.elapsed_time(g1) / out["gmres"]["ms"]}
@@ -563,8 +599,11 @@ def batch_workload(hm, torch, dev):
     """16 independent problems (n_c 4 096 - 131 072; sphere, cube and ellipsoid
     surfaces; k_s ~ U[2, 24]; U or T; weights area / n_c; eps = 1e-4, FP32
     storage), built by one batch build (shared ACA and recompression
-    launches), then one GMRES(100) per problem to 1e-6 (at most 500
-    products): wall time of the build and of the solves, per-problem results."""
+    launches), joined into one block-diagonal operator (hm_batch_join) and
+    solved by lockstep GMRES(100) to 1e-6, one per problem, one product of all
+    problems per Arnoldi step (at most 500 steps): wall time of the build, the
+    join and the solve, per-problem results; the same solves one problem at a
+    time for comparison."""
     from paper_1706_09384_gb300 import inputs
     P = inputs.batch_problems(16, seed=0)
     torch.cuda.synchronize()
@@ -572,18 +611,37 @@ def batch_workload(hm, torch, dev):
     Hs = hm.HMatrix.build_batch([dict(p, eta=3.0, leaf_size=64) for p in P], eps=1e-4)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    per = []
-    for q, (p, H) in enumerate(zip(P, Hs)):
-        b = torch.from_numpy(inputs.random_rhs(3 * len(p["points"]), seed=100 + q)).to(dev)
-        _, it, rr, st = H.gmres(b, restart=100, tol=1e-6, maxit=500, check=False)
-        per.append({"n_c": len(p["points"]), "shape": p["shape"], "kernel": p["kernel"],
-                    "kappa_s": round(p["ks"], 3), "iters": it, "relres": rr})
+    J = hm.HMatrix.join(Hs)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    b = torch.from_numpy(np.concatenate([inputs.random_rhs(3 * len(p["points"]), seed=100 + q)
+                                         for q, p in enumerate(P)])).to(dev)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    _, it, rr, st = J.gmres_batch(b, restart=100, tol=1e-6, maxit=500, check=False)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    steps = J.stats()["gmres_last"]
+    J.free()
+    per = [{"n_c": len(p["points"]), "shape": p["shape"], "kernel": p["kernel"],
+            "kappa_s": round(p["ks"], 3), "iters": int(it[q]), "relres": float(rr[q])}
+           for q, p in enumerate(P)]
+    # one problem at a time (each GMRES on its own handle)
+    off = 0
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    for p, H in zip(P, Hs):
+        n = 3 * len(p["points"])
+        H.gmres(b[off:off + n], restart=100, tol=1e-6, maxit=500, check=False)
+        off += n
+    torch.cuda.synchronize()
+    t6 = time.perf_counter()
     for H in Hs:
         H.free()
     return {"problems": 16, "points": int(sum(len(p["points"]) for p in P)),
-            "build_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0,
+            "build_s": t1 - t0, "join_s": t2 - t1, "solve_lockstep_s": t4 - t3,
+            "lockstep_products": steps, "total_s": (t2 - t0) + (t4 - t3),
+            "solve_one_by_one_s": t6 - t5,
             "converged": int(sum(r["relres"] <= 1e-6 for r in per)), "per_problem": per}
 
 

@@ -93,7 +93,17 @@ typedef struct {
                                  blocks of similar predicted rank are batched together; blocks
                                  whose rank exceeds the prediction are re-run, so the H-matrix
                                  is the same either way */
-    int32_t reserved[2];
+    const char* tune_cache;   /* HOST path of the autotuner's cache file, or NULL (default
+                                 launch parameters).  After the build, the H-matvec's launch
+                                 parameters (stages of the streamed BF16 product; work-item
+                                 size of the FP32 product) are read from this file for the
+                                 handle's workload class (GPU, storage, leading dimension,
+                                 log2 of the product's bytes), or, when the file has no such
+                                 entry, picked by timing the candidates on the handle and
+                                 written to it (a text file, one line per class; rewritten
+                                 through a temporary file).  The parameters change only the
+                                 schedule of the product.  The path is not kept after the
+                                 build. */
 } hm_opts;
 
 void hm_opts_default(hm_opts* opts);
@@ -159,6 +169,37 @@ typedef struct {
  * Errors: as hm_build, for the first problem that fails. */
 hm_status hm_build_batch(int32_t nprob, const hm_problem* probs, double eps, const hm_opts* opts,
                          void* stream, hm_handle* out);
+
+/* Joins built handles into one handle whose operator is the block-diagonal
+ * diag(A_1, ..., A_nprob) of their H-matrices (no paper counterpart: batching
+ * of independent problems).  Vectors of the joined handle are the
+ * concatenation of the problems' vectors, problem q's 3 n_c(q) entries (in its
+ * original point order) after those of problems 0..q-1.  Its stored data is a
+ * copy (the input handles stay valid and unchanged; free them if they are
+ * not needed), laid out so that one H-matvec of the joined handle applies
+ * every problem's operator in the same kernel launches.  hm_matvec,
+ * hm_matvec_host, hm_gmres (one GMRES on the whole block-diagonal system),
+ * hm_gmres_batch, hm_stats and the inspection calls work on it;
+ * hm_estimate_error, hm_lu_factor and hm_rank_samples report
+ * HM_ERR_UNSUPPORTED.  All handles must be on the current device with the
+ * same storage; a joined handle cannot be joined again.
+ *   hs   HOST array of nprob handles;  out: the joined handle (NULL on error)
+ * Errors: HM_ERR_ARG, HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_batch_join(int32_t nprob, const hm_handle* hs, void* stream, hm_handle* out);
+
+/* One restarted GMRES(restart) per problem of a joined handle, run in
+ * lockstep: each Arnoldi step makes one product of the block-diagonal
+ * operator (all problems at once), and per-problem Gram-Schmidt, Givens
+ * rotations and convergence tests (x_0 = 0, true relative residual
+ * ||b_q - A_q x_q|| / ||b_q|| <= tol at restarts, accurate restart products
+ * as in hm_gmres).  A problem that converges is frozen while the others go
+ * on.  b, x: DEVICE complex128 concatenated vectors (see hm_batch_join), not
+ * overlapping.  iters, relres: HOST arrays of nprob entries or NULL (products
+ * made until each problem converged; final true relative residual).
+ * Errors: HM_ERR_ARG (not a joined handle, bad arguments), HM_ERR_NOCONV
+ * (some problem reached maxit), HM_ERR_TIMEOUT, HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_gmres_batch(hm_handle h, const void* b, void* x, int32_t restart, double tol,
+                         int32_t maxit, int32_t* iters, double* relres, void* stream);
 
 /* y = A_H x (Sec. 3.1: dense product on P^non-ad, U (V^H x) on P^ad).
  *   x, y  DEVICE complex128, 3 n_c x nrhs column-major, original point order;

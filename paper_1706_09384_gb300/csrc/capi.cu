@@ -638,6 +638,8 @@ void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<cons
     h->d_xp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
     h->d_yp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
     HM_CUDA(cudaStreamSynchronize(st));
+    tune_product(h, o.tune_cache, st);  // times products on d_xp / d_yp
+    h->opts.tune_cache = nullptr;        // the caller's string is not kept
 }
 
 void report_build(const hm_matrix* h) {
@@ -857,6 +859,7 @@ hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double*
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!delta_f || !norm_f) hm_throw(HM_ERR_ARG, "null output");
+    if (!h->segments.empty()) hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch handle");
     estimate_error(h, nsample, seed, delta_f, norm_f, (cudaStream_t)stream);
     HM_API_END
 }
@@ -865,6 +868,7 @@ hm_status hm_lu_factor(hm_handle h, double eps_lu, void* stream) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!(eps_lu > 0) || !(eps_lu < 1)) hm_throw(HM_ERR_ARG, "eps_lu must lie in (0, 1)");
+    if (!h->segments.empty()) hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch handle");
     hlu_factor(h, eps_lu, (cudaStream_t)stream);
     HM_API_END
 }
@@ -944,6 +948,9 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"device_ms\": {\"aca\": " << h->ev_aca_ms << ", \"recompress\": " << h->ev_recomp_ms
        << "}, \"aca_flops\": " << h->aca_flops << ", \"aca_flops_fp64\": " << h->aca_flops_fp64
        << ", \"aca_flops_df\": " << h->aca_flops_df << ", \"aca_green_evals\": " << h->aca_green_evals
+       << ", \"tune\": {\"source\": \"" << h->tune_source << "\", \"key\": \"" << h->tune_key
+       << "\", \"nstage\": " << h->tune_nstage << ", \"item_bytes\": " << h->tune_item_bytes
+       << ", \"ms\": " << h->tune_ms << ", \"trials\": [" << h->tune_trials << "]}"
        << ", \"gmres_last\": {\"fast_products\": " << h->gm_fast
        << ", \"accurate_products\": " << h->gm_accurate << ", \"cycles\": " << h->gm_cycles
        << "}}";
@@ -957,6 +964,7 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
 hm_status hm_rank_samples(hm_handle h, float* feats, float* targets, int64_t* n) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
+    if (!h->segments.empty()) hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch handle");
     int64_t q = 0;
     for (const hm_block& b : h->blocks) {
         if (!b.admissible) continue;
@@ -1053,6 +1061,7 @@ hm_status hm_import(int64_t n_c, const int64_t* perm, int64_t n_clusters,
     h = new hm_matrix();
     h->nc = n_c;
     h->opts = o;
+    h->opts.tune_cache = nullptr;  // imported handles keep the default launch parameters
     HM_CUDA(cudaGetDevice(&h->device));
     h->perm.assign(perm, perm + n_c);
     h->clusters.assign(clusters, clusters + n_clusters);

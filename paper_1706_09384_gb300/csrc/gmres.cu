@@ -6,9 +6,17 @@
 // entries), so each restart cycle is one step of iterative refinement and the
 // solve reaches tolerances below the FP32 summation noise.
 //
-// One code path serves one right-hand side and nrhs of them in lockstep
-// (blockIdx.y = right-hand side; a flag per column freezes the converged
-// ones).  An Arnoldi step is the product plus four kernels:
+// One code path serves one right-hand side, nrhs of them in lockstep, and the
+// independent problems of a joined batch handle (hm_batch_join: a
+// block-diagonal operator whose diagonal blocks are the problems) in
+// lockstep.  A solve works on "segments": segment s (blockIdx.y) is the part
+// [off_s, off_s + len_s) of each vector; right-hand sides are equal-length
+// segments of one column-major block, problems are the consecutive parts of
+// the concatenated vector.  A flag per segment freezes the converged ones.
+// With several right-hand sides each Arnoldi step makes one product of all
+// of them (the tensor-core block product with BF16 storage); with a batch it
+// makes one product of the block-diagonal operator, i.e. of every problem at
+// once.  An Arnoldi step is the product plus four kernels:
 //   dot      h1 = V^H w                       (classical Gram-Schmidt, pass 1)
 //   upd_dot  w -= V h1, h2 = V^H w            (pass 2: re-orthogonalisation)
 //   norm     w -= V h2, ||w||^2, then the Givens update of the Hessenberg
@@ -38,12 +46,13 @@ constexpr int MAXM = 500;  // restart length limit of the ABI
 
 // Device pointers and sizes of a solve (passed by value to every kernel).
 struct GP {
-    int64_t n;       // vector length 3 n_c
-    int m;           // restart length
-    int nrhs;
-    int G;           // CTAs per right-hand side (row slices)
-    int64_t rpc;     // rows per CTA
-    double2* V;      // basis: vector j of rhs s at V + (j nrhs + s) n
+    int64_t N;          // length of one whole vector (all segments)
+    const int64_t* off; // [s] first entry of segment s
+    const int64_t* len; // [s] entries of segment s
+    int m;              // restart length
+    int nrhs;           // segments
+    int G;              // CTAs per segment (row slices)
+    double2* V;         // basis: vector j, segment s at V + j N + off_s
     double2* part;   // partial sums [s][cta][m + 1]
     double* partn;   // partial norms [s][cta]
     unsigned* cnt;   // tickets [s]
@@ -58,7 +67,14 @@ struct GP {
     const int* act;  // [s] 1 = column still iterating (nullptr: all)
 };
 
-HM_D double2* basis(const GP& P, int j, int s) { return P.V + ((int64_t)j * P.nrhs + s) * P.n; }
+HM_D double2* basis(const GP& P, int j, int s) { return P.V + (int64_t)j * P.N + P.off[s]; }
+
+// rows [r0, r1) of segment s handled by this CTA
+HM_D void cta_rows(const GP& P, int s, int64_t& r0, int64_t& r1) {
+    const int64_t n = P.len[s], rpc = (n + P.G - 1) / P.G;
+    r0 = min(n, (int64_t)blockIdx.x * rpc);
+    r1 = min(n, r0 + rpc);
+}
 
 // The last CTA of right-hand side s to arrive returns true (after every other
 // CTA's partial sums are visible); it also re-arms the ticket.
@@ -94,8 +110,9 @@ __global__ void __launch_bounds__(GT) dot_kernel(GP P, int ncol, const double2* 
     if (P.act && !P.act[s]) return;
     __shared__ double2 hs[MAXM + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t r0 = blockIdx.x * P.rpc, r1 = min(P.n, r0 + P.rpc);
-    double2* w = W + (int64_t)s * P.n;
+    int64_t r0, r1;
+    cta_rows(P, s, r0, r1);
+    double2* w = W + P.off[s];
     if (hsub) update_rows(P, s, ncol, hsub, w, r0, r1, hs);
     double2* part = P.part + ((int64_t)s * P.G + blockIdx.x) * (P.m + 1);
     for (int i = wid; i < ncol; i += GW) {
@@ -170,10 +187,11 @@ __global__ void __launch_bounds__(GT) norm_kernel(GP P, int mode, int j, const d
     __shared__ double2 hs[MAXM + 1];
     __shared__ double red[GW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t r0 = blockIdx.x * P.rpc, r1 = min(P.n, r0 + P.rpc);
-    double2* w = W + (int64_t)s * P.n;
+    int64_t r0, r1;
+    cta_rows(P, s, r0, r1);
+    double2* w = W + P.off[s];
     if (B) {
-        const double2* b = B + (int64_t)s * P.n;
+        const double2* b = B + P.off[s];
         for (int64_t q = r0 + threadIdx.x; q < r1; q += GT)
             w[q] = make_double2(b[q].x - w[q].x, b[q].y - w[q].y);
         __syncthreads();
@@ -214,7 +232,7 @@ __global__ void scale_kernel(GP P, int j, const double2* W) {
     if (P.act && !P.act[s]) return;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const double f = P.nrm2[s] > 0.0 ? 1.0 / sqrt(P.nrm2[s]) : 0.0;
-    if (q < P.n) basis(P, j, s)[q] = cscale(W[(int64_t)s * P.n + q], f);
+    if (q < P.len[s]) basis(P, j, s)[q] = cscale(W[P.off[s] + q], f);
 }
 
 // w_s = b_s for the active right-hand sides (first cycle: r = b for x_0 = 0)
@@ -222,7 +240,7 @@ __global__ void copy_kernel(GP P, const double2* B, double2* W) {
     const int s = blockIdx.y;
     if (P.act && !P.act[s]) return;
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < P.n) W[(int64_t)s * P.n + q] = B[(int64_t)s * P.n + q];
+    if (q < P.len[s]) W[P.off[s] + q] = B[P.off[s] + q];
 }
 
 // y_s = R^{-1} g over the first jend[s] columns (one thread per right-hand side)
@@ -249,10 +267,10 @@ __global__ void __launch_bounds__(GT) update_x_kernel(GP P, const int* jend, dou
     for (int i = threadIdx.x; i < je; i += GT) ys[i] = P.y[(int64_t)s * P.m + i];
     __syncthreads();
     const int64_t q = blockIdx.x * (int64_t)GT + threadIdx.x;
-    if (q >= P.n) return;
+    if (q >= P.len[s]) return;
     double2 acc = make_double2(0.0, 0.0);
     for (int i = 0; i < je; ++i) cfma(acc, basis(P, i, s)[q], ys[i]);
-    double2* x = X + (int64_t)s * P.n;
+    double2* x = X + P.off[s];
     x[q] = cadd(x[q], acc);
 }
 
@@ -268,6 +286,7 @@ struct GmresWork {
     double2* xp64 = nullptr;
     double2* yp64 = nullptr;
     double* host = nullptr;  // pinned: nrm2[nrhs], est[nrhs]
+    int64_t lmax = 0;        // longest segment
     std::vector<void*> bufs;
     cudaStream_t st = nullptr;
     ~GmresWork() {
@@ -276,24 +295,36 @@ struct GmresWork {
     }
 };
 
-static void gmres_work(GmresWork& g, hm_matrix* h, int m, int nrhs, cudaStream_t st) {
-    const int64_t n = 3 * h->nc;
+static void gmres_work(GmresWork& g, hm_matrix* h, int m, const std::vector<int64_t>& off,
+                       const std::vector<int64_t>& len, cudaStream_t st) {
+    const int nrhs = (int)off.size();
+    int64_t N = 0, lmax = 0;
+    for (int s = 0; s < nrhs; ++s) {
+        N = std::max(N, off[s] + len[s]);
+        lmax = std::max(lmax, len[s]);
+    }
     int nsm = 0;
     HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     g.st = st;
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(hm_cdiv(n, GT), 4 * (int64_t)nsm));
+    g.lmax = lmax;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(hm_cdiv(lmax, GT), 4 * (int64_t)nsm));
     auto dm = [&](size_t bytes) {
         void* p = hm_scratch_alloc(bytes, st);
         g.bufs.push_back(p);
         return p;
     };
     GP& P = g.P;
-    P.n = n;
+    P.N = N;
     P.m = m;
     P.nrhs = nrhs;
     P.G = G;
-    P.rpc = hm_cdiv(n, G);
-    P.V = (double2*)dm((size_t)n * (m + 1) * nrhs * sizeof(double2));
+    int64_t* d_seg = (int64_t*)dm((size_t)2 * nrhs * sizeof(int64_t));
+    std::vector<int64_t> seg(off);
+    seg.insert(seg.end(), len.begin(), len.end());
+    HM_CUDA(cudaMemcpyAsync(d_seg, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    P.off = d_seg;
+    P.len = d_seg + nrhs;
+    P.V = (double2*)dm((size_t)N * (m + 1) * sizeof(double2));
     P.part = (double2*)dm((size_t)nrhs * G * (m + 1) * sizeof(double2));
     P.partn = (double*)dm((size_t)nrhs * G * sizeof(double));
     P.cnt = (unsigned*)dm((size_t)nrhs * sizeof(unsigned));
@@ -309,36 +340,67 @@ static void gmres_work(GmresWork& g, hm_matrix* h, int m, int nrhs, cudaStream_t
     g.d_act = (int*)dm((size_t)nrhs * sizeof(int));
     P.act = g.d_act;
     g.d_jend = (int*)dm((size_t)nrhs * sizeof(int));
-    g.W = (double2*)dm((size_t)n * nrhs * sizeof(double2));
-    g.xp64 = (double2*)dm((size_t)n * sizeof(double2));
-    g.yp64 = (double2*)dm((size_t)n * sizeof(double2));
+    g.W = (double2*)dm((size_t)N * sizeof(double2));
+    g.xp64 = (double2*)dm((size_t)3 * h->nc * sizeof(double2));
+    g.yp64 = (double2*)dm((size_t)3 * h->nc * sizeof(double2));
     g.host = (double*)hm_pinned_take((size_t)2 * nrhs * sizeof(double));
 }
 
-// One restarted GMRES per column of B (3 nc x nrhs, column-major), run in
-// lockstep: each Arnoldi step makes one fast product of all active columns
-// (a block product on the tensor cores with BF16 storage and nrhs > 1, else
-// one product per column).  A column whose residual estimate reaches tol is
-// frozen for the rest of its cycle; the true residuals (accurate products) at
-// each restart decide convergence.
-void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int m, double tol,
-                       int maxit, std::vector<GmresResult>& out, cudaStream_t st) {
+// Restarted GMRES per segment of B, run in lockstep.  Columns mode: segment s
+// is right-hand side s (equal lengths 3 n_c, column-major B); each Arnoldi
+// step makes one fast product of all active columns (a block product on the
+// tensor cores with BF16 storage and several columns, else one product per
+// column).  Segments mode (a joined batch handle): segment s is problem s of
+// the block-diagonal operator and each step makes one product of the whole
+// vector.  A segment whose residual estimate reaches tol is frozen for the
+// rest of its cycle; the true residuals (accurate products) at each restart
+// decide convergence.
+static void gmres_core(hm_matrix* h, bool columns, const std::vector<int64_t>& off,
+                       const std::vector<int64_t>& len, const double2* B, double2* X, int m,
+                       double tol, int maxit, std::vector<GmresResult>& out, cudaStream_t st) {
+    const int nrhs = (int)off.size();
     const int64_t n = 3 * h->nc;
     GmresWork work;
-    gmres_work(work, h, m, nrhs, st);
+    gmres_work(work, h, m, off, len, st);
     GmresWork* gw = &work;
+    // one product covers every segment, frozen ones included: their part of the
+    // basis must hold numbers (the pool returns uninitialised memory)
+    if (!columns)
+        HM_CUDA(cudaMemsetAsync(work.P.V, 0, (size_t)work.P.N * (m + 1) * sizeof(double2), st));
     GP P = gw->P;
     double2* W = gw->W;
     h->gm_fast = h->gm_accurate = h->gm_cycles = 0;
-    const unsigned nb = (unsigned)hm_cdiv(n, GT);
+    const unsigned nb = (unsigned)hm_cdiv(gw->lmax, GT);
     const dim3 gv(nb, nrhs), gd((unsigned)P.G, nrhs);
     out.assign(nrhs, GmresResult{0, 1.0, 0});
     std::vector<int> act(nrhs, 1), jend(nrhs, 0);
     std::vector<double> bn(nrhs, 0.0);
-    double* hv = gw->host;           // nrm2 per column
-    double* hest = gw->host + nrhs;  // residual estimate per column
+    double* hv = gw->host;           // nrm2 per segment
+    double* hest = gw->host + nrhs;  // residual estimate per segment
+    // segments mode: the products skip the work items of frozen segments (the
+    // full item lists come back when the solve ends, also on an error)
+    std::vector<int64_t> bounds(off);
+    bounds.push_back(P.N);
+    struct Restore {
+        hm_matrix* h;
+        const std::vector<int64_t>* b;
+        cudaStream_t st;
+        bool on;
+        ~Restore() {
+            if (!on) return;
+            try {
+                matvec_select_segments(h->mv, *b, std::vector<int>(b->size() - 1, 1), st);
+            } catch (...) {
+            }
+        }
+    } restore{h, &bounds, st, !columns};
+    std::vector<int> sel_act;
     auto upload_act = [&]() {  // pageable source: safe to modify after the call returns
         HM_CUDA(cudaMemcpyAsync(gw->d_act, act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (!columns && act != sel_act) {
+            matvec_select_segments(h->mv, bounds, act, st);
+            sel_act = act;
+        }
     };
     auto readback = [&]() {
         HM_CUDA(cudaMemcpyAsync(gw->host, P.nrm2, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -348,7 +410,7 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
         HM_LAUNCHED();
         HM_CUDA(cudaGetLastError());
     };
-    HM_CUDA(cudaMemsetAsync(X, 0, (size_t)n * nrhs * sizeof(double2), st));
+    HM_CUDA(cudaMemsetAsync(X, 0, (size_t)P.N * sizeof(double2), st));
     upload_act();
     // ||b_s||: the norm kernel on a copy of B
     copy_kernel<<<gv, GT, 0, st>>>(P, B, W);
@@ -365,7 +427,7 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
     }
     int iters = 0;
     for (bool first = true;; first = false) {
-        // true residuals of the unconverged columns (accurate products; r = b for x_0 = 0)
+        // true residuals of the unconverged segments (accurate products; r = b for x_0 = 0)
         for (int s = 0; s < nrhs; ++s) act[s] = !out[s].converged;
         upload_act();
         if (first) {
@@ -373,12 +435,17 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
             launched();
             norm_kernel<<<gd, GT, 0, st>>>(P, 1, 0, nullptr, nullptr, 0, W);
         } else {
-            for (int s = 0; s < nrhs; ++s)
-                if (act[s]) {
-                    matvec_accurate(h->mv, h->d_perm, X + (int64_t)s * n, gw->xp64, gw->yp64,
-                                    W + (int64_t)s * n, h->nc, st);
-                    h->gm_accurate++;
-                }
+            if (columns) {
+                for (int s = 0; s < nrhs; ++s)
+                    if (act[s]) {
+                        matvec_accurate(h->mv, h->d_perm, X + off[s], gw->xp64, gw->yp64, W + off[s],
+                                        h->nc, st);
+                        h->gm_accurate++;
+                    }
+            } else {
+                matvec_accurate(h->mv, h->d_perm, X, gw->xp64, gw->yp64, W, h->nc, st);
+                h->gm_accurate++;
+            }
             norm_kernel<<<gd, GT, 0, st>>>(P, 1, 0, B, nullptr, 0, W);
         }
         launched();
@@ -403,14 +470,18 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
         h->gm_cycles++;
         std::fill(jend.begin(), jend.end(), 0);
         for (int j = 0; j < m; ++j) {
-            if (h->opts.storage == HM_STORE_BF16 && nrhs > 1) {
-                matvec_multi(h->mv, h->d_perm, P.V + (int64_t)j * nrhs * n, W, h->nc, nrhs, st);
+            double2* Vj = P.V + (int64_t)j * P.N;
+            if (!columns) {
+                matvec_graph(h->mv, h->d_perm, Vj, h->d_xp, h->d_yp, W, h->nc, st);
+                h->gm_fast++;
+            } else if (h->opts.storage == HM_STORE_BF16 && nrhs > 1) {
+                matvec_multi(h->mv, h->d_perm, Vj, W, h->nc, nrhs, st);
                 h->gm_fast += nrhs;
             } else {
                 for (int s = 0; s < nrhs; ++s)
                     if (act[s]) {
-                        matvec_graph(h->mv, h->d_perm, P.V + ((int64_t)j * nrhs + s) * n, h->d_xp,
-                                     h->d_yp, W + (int64_t)s * n, h->nc, st);
+                        matvec_graph(h->mv, h->d_perm, Vj + off[s], h->d_xp, h->d_yp, W + off[s],
+                                     h->nc, st);
                         h->gm_fast++;
                     }
             }
@@ -447,6 +518,29 @@ void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int
         update_x_kernel<<<gv, GT, 0, st>>>(P, gw->d_jend, X);
         launched();
     }
+    (void)n;
+}
+
+void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* B, double2* X, int m, double tol,
+                       int maxit, std::vector<GmresResult>& out, cudaStream_t st) {
+    const int64_t n = 3 * h->nc;
+    std::vector<int64_t> off(nrhs), len(nrhs, n);
+    for (int s = 0; s < nrhs; ++s) off[s] = s * n;
+    gmres_core(h, true, off, len, B, X, m, tol, maxit, out, st);
+}
+
+void gmres_solve_segments(hm_matrix* h, const std::vector<int64_t>& seg_points, const double2* B,
+                          double2* X, int m, double tol, int maxit, std::vector<GmresResult>& out,
+                          cudaStream_t st) {
+    std::vector<int64_t> off, len;
+    int64_t o = 0;
+    for (int64_t p : seg_points) {
+        off.push_back(3 * o);
+        len.push_back(3 * p);
+        o += p;
+    }
+    if (o != h->nc) hm_throw(HM_ERR_ARG, "segments do not cover the handle's points");
+    gmres_core(h, false, off, len, B, X, m, tol, maxit, out, st);
 }
 
 GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int m, double tol, int maxit,

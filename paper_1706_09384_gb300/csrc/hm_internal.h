@@ -89,6 +89,15 @@ struct MatvecDev;  // device side of the plan (matvec.cu)
 MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
                              cudaStream_t st);
 void matvec_dev_destroy(MatvecDev* m);
+// Products over the items of the active segments only (segment q = DOFs
+// [dof_bounds[q], dof_bounds[q + 1])); all active restores the full lists.
+void matvec_select_segments(MatvecDev* m, const std::vector<int64_t>& dof_bounds,
+                            const std::vector<int>& act, cudaStream_t st);
+// Launch parameters of the one-vector product picked by the autotuner: stages
+// of the streamed BF16 kernels (2..4) and, with FP32 storage, the byte size of
+// a work item (re-tiles the items).
+void matvec_set_params(MatvecDev* m, const MatvecPlan& plan, int s16_nstage, int64_t item_bytes,
+                       cudaStream_t st);
 // Adds the BF16 copy of the arena (per-chunk FP32 scale); the fast product then
 // reads it, the accurate product keeps reading the FP32 arena.
 void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
@@ -217,6 +226,14 @@ void rank_model_predict_dev(const float* dP, const float* dF, int64_t n, float* 
 void rank_features(const hm_cluster& t, const hm_cluster& s, double ks, double kp, double eps,
                    float f[6]);
 
+// ---------------- autotuner (tune.cu) ----------------
+struct hm_matrix;
+// Picks the product's launch parameters for the handle: from the cache file
+// at path if it holds the handle's workload key, else by timing the
+// candidates on the handle and recording the best in the file (path NULL or
+// empty: defaults).
+void tune_product(hm_matrix* h, const char* path, cudaStream_t st);
+
 // ---------------- GMRES (gmres.cu) ----------------
 struct GmresResult {
     int iters;
@@ -231,6 +248,12 @@ GmresResult gmres_solve(hm_matrix* h, const double2* b, double2* x, int restart,
 void estimate_error(hm_matrix* h, int64_t nsample, uint64_t seed, double* delta_f, double* norm_f,
                     cudaStream_t st);
 // nrhs right-hand sides in lockstep (b, x: 3 nc x nrhs column-major, device)
+// Independent problems of a joined handle (block-diagonal operator): one
+// restarted GMRES per segment of seg_points points, in lockstep, one product
+// of the whole operator per Arnoldi step (b, x: concatenated, device).
+void gmres_solve_segments(hm_matrix* h, const std::vector<int64_t>& seg_points, const double2* b,
+                          double2* x, int restart, double tol, int maxit,
+                          std::vector<GmresResult>& out, cudaStream_t st);
 void gmres_solve_multi(hm_matrix* h, int nrhs, const double2* b, double2* x, int restart, double tol,
                        int maxit, std::vector<GmresResult>& out, cudaStream_t st);
 
@@ -283,7 +306,15 @@ struct hm_matrix {
     int64_t rsvd_uncertified = 0;  // of those, blocks whose samples reached their cap uncertified
     double t_rsvd_ms = 0;          // wall time of the randomized SVD pass (with its recompression)
     void* hlu = nullptr;           // H-LU factors (hlu.cu), if computed
+    // autotuned product parameters (tune.cu): where they came from ("default",
+    // "cache" or "sweep"), the workload key, the values and the sweep's timings
+    std::string tune_source = "default", tune_key, tune_trials;
+    int tune_nstage = 3;
+    int64_t tune_item_bytes = 256 * 1024;
+    double tune_ms = 0;
     // the last GMRES solve: fast and accurate products made, restart cycles
     int64_t gm_fast = 0, gm_accurate = 0, gm_cycles = 0;
     int used_rank_model = 0;
+    // a joined batch (hm_batch_join): points of each problem, in order; empty otherwise
+    std::vector<int64_t> segments;
 };

@@ -380,45 +380,50 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
 // of the lanes busy for the usual 150-row columns, where one column per warp
 // leaves 40 % idle), so a stored entry costs one conversion and four FMAs and
 // a column of phase 1 a three-step shuffle reduction.
+// The number of stages in the ring (NS = 2, 3 or 4: 24-48 KB of the SM's
+// shared memory per CTA) is a template parameter picked per GPU and workload
+// by the autotuner (tune.cu); 3 without a tuning.
 constexpr int S16_CONSUMERS = 4;
 constexpr int S16_THREADS = 32 * (S16_CONSUMERS + 1);
-constexpr int S16_NSTAGE = 3;
 constexpr int S16_COLS = 4 * S16_CONSUMERS;             // columns per stage: one per lane group
 constexpr int S16_STAGE_BYTES = S16_COLS * MAX_LD * 4;  // 12 KB
 constexpr int S16_QPL = MAX_LD / 4 / 8;                 // row quads per lane (48 quads / 8 lanes)
 constexpr int MV_ERR_TIMEOUT = 1;
 
-static_assert(S16_CONSUMERS * MAX_LD * sizeof(float2) <= S16_NSTAGE * S16_STAGE_BYTES,
-              "row sums fit in the stages");
+template <int NS>
 struct S16Smem {
+    static_assert(S16_CONSUMERS * MAX_LD * sizeof(float2) <= NS * S16_STAGE_BYTES,
+                  "row sums fit in the stages");
     // the stages; once every stage is consumed, phase 2 reuses them for the
     // per-warp row sums (S16_CONSUMERS x MAX_LD float2)
-    alignas(128) unsigned char stage[S16_NSTAGE][S16_STAGE_BYTES];
+    alignas(128) unsigned char stage[NS][S16_STAGE_BYTES];
     float2 w[MAX_ITEM_COLS];                   // phase 2: scale * v_j; phase 1: (t index bits, scale)
     DevChunk16 hdr[MAX_ITEM_CHUNKS];
     int32_t colstart[MAX_ITEM_CHUNKS + 1];
     int32_t ncol;
-    alignas(8) uint64_t full[S16_NSTAGE];
-    uint64_t empty[S16_NSTAGE];
+    alignas(8) uint64_t full[NS];
+    uint64_t empty[NS];
 };
+// resident CTAs per SM the launch bounds ask for (48 KB stages allow three)
+template <int NS> constexpr int s16_min_blocks() { return NS >= 4 ? 3 : 4; }
 
 __device__ __forceinline__ void consumers_sync() { named_sync<1, 32 * S16_CONSUMERS>(); }
 
 // PHASE 1: t[vec_j] += scale_j * V_j^H x_leaf;  PHASE 2: y_leaf += sum_j M_j scale_j v_j.
-template <int PHASE>
-__global__ void __launch_bounds__(S16_THREADS, 4) mv16s_kernel(const WorkItem* items,
+template <int PHASE, int NS>
+__global__ void __launch_bounds__(S16_THREADS, s16_min_blocks<NS>()) mv16s_kernel(const WorkItem* items,
                                                            const DevChunk16* hdr,
                                                            const uint32_t* __restrict__ arena,
                                                            const float2* __restrict__ xp,
                                                            float2* t, float2* yp, int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    S16Smem& S = *reinterpret_cast<S16Smem*>(smem_raw);
+    S16Smem<NS>& S = *reinterpret_cast<S16Smem<NS>*>(smem_raw);
     const WorkItem it = items[blockIdx.x];
     const int nch = it.last - it.first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < nch; i += S16_THREADS) S.hdr[i] = hdr[it.first + i];
     if (tid == 0) {
-        for (int s = 0; s < S16_NSTAGE; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], S16_CONSUMERS);
         }
@@ -452,8 +457,8 @@ __global__ void __launch_bounds__(S16_THREADS, 4) mv16s_kernel(const WorkItem* i
             const unsigned char* src0 = reinterpret_cast<const unsigned char*>(arena + S.hdr[0].data);
             int issued = 0;
             for (int k = 0; k < nst; ++k) {
-                const int s = k % S16_NSTAGE;
-                if (k >= S16_NSTAGE && !mbar_wait(&S.empty[s], ((k / S16_NSTAGE) - 1) & 1)) {
+                const int s = k % NS;
+                if (k >= NS && !mbar_wait(&S.empty[s], ((k / NS) - 1) & 1)) {
                     atomicExch(err, MV_ERR_TIMEOUT);
                     break;
                 }
@@ -463,8 +468,8 @@ __global__ void __launch_bounds__(S16_THREADS, 4) mv16s_kernel(const WorkItem* i
                 bulk_g2s(S.stage[s], src0 + (size_t)k * sc * colb, bytes, &S.full[s]);
                 ++issued;
             }
-            for (int k = max(0, issued - S16_NSTAGE); k < issued; ++k)  // own copies landed
-                if (!mbar_wait(&S.full[k % S16_NSTAGE], (k / S16_NSTAGE) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
+            for (int k = max(0, issued - NS); k < issued; ++k)  // own copies landed
+                if (!mbar_wait(&S.full[k % NS], (k / NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
         }
         return;
     }
@@ -496,8 +501,8 @@ __global__ void __launch_bounds__(S16_THREADS, 4) mv16s_kernel(const WorkItem* i
             xa[i][e] = (PHASE == 1 && r < it.rows) ? xp[it.dof + r] : make_float2(0.f, 0.f);
         }
     for (int k = 0; k < nst; ++k) {
-        const int s = k % S16_NSTAGE;
-        if (!mbar_wait(&S.full[s], (k / S16_NSTAGE) & 1)) {
+        const int s = k % NS;
+        if (!mbar_wait(&S.full[s], (k / NS) & 1)) {
             atomicExch(err, MV_ERR_TIMEOUT);
             break;
         }
@@ -845,6 +850,65 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
     return P;
 }
 
+// Work items of the one-vector product (and of the accurate product): each
+// segment's chunk list cut into items of about item_bytes (FP32 bytes),
+// largest first; device copies of the items, their chunk order and the
+// chunk headers in item order.  The buffers belong to the tiling and are
+// replaced when it changes.
+static void set_tiling(MatvecDev* m, const MatvecPlan& plan, int64_t item_bytes, cudaStream_t st) {
+    std::vector<WorkItem> it1, it2;
+    std::vector<int32_t> o1, o2;
+    make_items(plan.col_leaf_begin, plan.col_items, plan.chunks, plan, item_bytes, it1, o1);
+    make_items(plan.row_leaf_begin, plan.row_items, plan.chunks, plan, item_bytes, it2, o2);
+    // largest items first
+    auto bytes_of = [&](const WorkItem& w, const std::vector<int32_t>& o) {
+        int64_t s = 0;
+        for (int32_t q = w.first; q < w.last; ++q)
+            s += (int64_t)plan.chunks[o[q]].ld * plan.chunks[o[q]].ncols;
+        return s;
+    };
+    std::stable_sort(it1.begin(), it1.end(), [&](const WorkItem& a, const WorkItem& b) {
+        return bytes_of(a, o1) > bytes_of(b, o1);
+    });
+    std::stable_sort(it2.begin(), it2.end(), [&](const WorkItem& a, const WorkItem& b) {
+        return bytes_of(a, o2) > bytes_of(b, o2);
+    });
+    HM_CUDA(cudaStreamSynchronize(st));  // the old tiling is no longer in use
+    for (DevBuf& d : m->tile_bufs) cudaFree(d.p);
+    m->tile_bufs.clear();
+    std::vector<DevBuf>& owner = m->tile_bufs;
+    m->item_bytes = item_bytes;
+    m->n1 = (int64_t)it1.size();
+    m->n2 = (int64_t)it2.size();
+    m->items1 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it1.size(), 1) * sizeof(WorkItem), st, false);
+    m->items2 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it2.size(), 1) * sizeof(WorkItem), st, false);
+    m->order1 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o1.size(), 1) * 4, st, false);
+    m->order2 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o2.size(), 1) * 4, st, false);
+    HM_CUDA(cudaMemcpyAsync(m->items1, it1.data(), it1.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->items2, it2.data(), it2.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->order1, o1.data(), o1.size() * 4, cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->order2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, st));
+    std::vector<DevChunk> h1(o1.size()), h2(o2.size());
+    for (size_t q = 0; q < o1.size(); ++q) h1[q] = m->dc[o1[q]];
+    for (size_t q = 0; q < o2.size(); ++q) h2[q] = m->dc[o2[q]];
+    m->hdr1 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h1.size(), 1) * sizeof(DevChunk), st, false);
+    m->hdr2 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h2.size(), 1) * sizeof(DevChunk), st, false);
+    HM_CUDA(cudaMemcpyAsync(m->hdr1, h1.data(), h1.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->hdr2, h2.data(), h2.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
+    m->n_o1 = (int64_t)o1.size();
+    m->n_o2 = (int64_t)o2.size();
+    m->h_items1 = it1;
+    m->h_items2 = it2;
+    m->h_order1 = o1;
+    m->h_order2 = o2;
+    m->items1_full = m->items1;
+    m->items2_full = m->items2;
+    m->n1_full = m->n1;
+    m->n2_full = m->n2;
+    m->sel1 = m->sel2 = nullptr;
+    HM_CUDA(cudaStreamSynchronize(st));  // host vectors h1, h2 leave scope
+}
+
 MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
                              cudaStream_t st) {
     MatvecDev* m = new MatvecDev();
@@ -869,49 +933,8 @@ MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<De
                                       false);
     HM_CUDA(cudaMemcpyAsync(m->chunks, dc.data(), dc.size() * sizeof(DevChunk),
                             cudaMemcpyHostToDevice, st));
-    const int64_t target = 256 * 1024;
-    std::vector<WorkItem> it1, it2;
-    std::vector<int32_t> o1, o2;
-    make_items(plan.col_leaf_begin, plan.col_items, plan.chunks, plan, target, it1, o1);
-    make_items(plan.row_leaf_begin, plan.row_items, plan.chunks, plan, target, it2, o2);
-    // largest items first
-    auto bytes_of = [&](const WorkItem& w, const std::vector<int32_t>& o) {
-        int64_t s = 0;
-        for (int32_t q = w.first; q < w.last; ++q)
-            s += (int64_t)plan.chunks[o[q]].ld * plan.chunks[o[q]].ncols;
-        return s;
-    };
-    std::stable_sort(it1.begin(), it1.end(), [&](const WorkItem& a, const WorkItem& b) {
-        return bytes_of(a, o1) > bytes_of(b, o1);
-    });
-    std::stable_sort(it2.begin(), it2.end(), [&](const WorkItem& a, const WorkItem& b) {
-        return bytes_of(a, o2) > bytes_of(b, o2);
-    });
-    m->n1 = (int64_t)it1.size();
-    m->n2 = (int64_t)it2.size();
-    m->items1 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it1.size(), 1) * sizeof(WorkItem), st, false);
-    m->items2 = (WorkItem*)hm_dmalloc(owner, std::max<size_t>(it2.size(), 1) * sizeof(WorkItem), st, false);
-    m->order1 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o1.size(), 1) * 4, st, false);
-    m->order2 = (int32_t*)hm_dmalloc(owner, std::max<size_t>(o2.size(), 1) * 4, st, false);
-    HM_CUDA(cudaMemcpyAsync(m->items1, it1.data(), it1.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
-    HM_CUDA(cudaMemcpyAsync(m->items2, it2.data(), it2.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
-    HM_CUDA(cudaMemcpyAsync(m->order1, o1.data(), o1.size() * 4, cudaMemcpyHostToDevice, st));
-    HM_CUDA(cudaMemcpyAsync(m->order2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, st));
-    {
-        std::vector<DevChunk> h1(o1.size()), h2(o2.size());
-        for (size_t q = 0; q < o1.size(); ++q) h1[q] = dc[o1[q]];
-        for (size_t q = 0; q < o2.size(); ++q) h2[q] = dc[o2[q]];
-        m->hdr1 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h1.size(), 1) * sizeof(DevChunk), st, false);
-        m->hdr2 = (DevChunk*)hm_dmalloc(owner, std::max<size_t>(h2.size(), 1) * sizeof(DevChunk), st, false);
-        HM_CUDA(cudaMemcpyAsync(m->hdr1, h1.data(), h1.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
-        HM_CUDA(cudaMemcpyAsync(m->hdr2, h2.data(), h2.size() * sizeof(DevChunk), cudaMemcpyHostToDevice, st));
-        m->n_o1 = (int64_t)o1.size();
-        m->n_o2 = (int64_t)o2.size();
-    }
-    m->h_items1 = it1;
-    m->h_items2 = it2;
-    m->h_order1 = o1;
-    m->h_order2 = o2;
+    m->dc = dc;
+    set_tiling(m, plan, m->item_bytes, st);
     m->d_err = (int*)hm_dmalloc(owner, sizeof(int), st, true);
     m->t_elems = plan.t_elems;
     m->t = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.t_elems, 1) * sizeof(float2), st, true);
@@ -926,6 +949,14 @@ static void matvec_graph_reset(MatvecDev* m) {
     m->gexec = nullptr;
     m->graph = nullptr;
     m->g_gather = m->g_scatter = nullptr;
+}
+
+template <int NS>
+static void s16_attributes() {
+    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<1, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(S16Smem<NS>)));
+    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<2, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(S16Smem<NS>)));
 }
 
 void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>& owner,
@@ -981,10 +1012,9 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
     };
     check_items(m->h_items1, m->h_order1);
     check_items(m->h_items2, m->h_order2);
-    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(S16Smem)));
-    HM_CUDA(cudaFuncSetAttribute(mv16s_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(S16Smem)));
+    s16_attributes<2>();
+    s16_attributes<3>();
+    s16_attributes<4>();
     m->arena16_elems = off;
     m->nchunks = (int64_t)c16.size();
     m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4, st, true);
@@ -1037,6 +1067,7 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
 void matvec_dev_destroy(MatvecDev* m) {
     if (!m) return;
     matvec_graph_reset(m);
+    for (DevBuf& d : m->tile_bufs) cudaFree(d.p);
     if (m->xb) cudaFree(m->xb);
     if (m->ym) cudaFree(m->ym);
     if (m->tm) cudaFree(m->tm);
@@ -1050,13 +1081,29 @@ int64_t matvec_stored_bytes(const MatvecDev* m) {
 }
 int64_t matvec_dense_bytes(const MatvecDev* m) { return m->dense_elems * 8; }
 
+template <int PHASE, int NS>
+static void launch_s16(MatvecDev* m, const float2* xp, float2* yp, cudaStream_t st) {
+    const int64_t n = PHASE == 1 ? m->n1 : m->n2;
+    mv16s_kernel<PHASE, NS><<<(unsigned)n, S16_THREADS, sizeof(S16Smem<NS>), st>>>(
+        PHASE == 1 ? m->items1 : m->items2, PHASE == 1 ? m->hdr16_1 : m->hdr16_2, m->arena16, xp,
+        m->t, yp, m->d_err);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
+}
+
+template <int PHASE>
+static void launch_s16_ns(MatvecDev* m, const float2* xp, float2* yp, cudaStream_t st) {
+    switch (m->s16_nstage) {
+        case 2: return launch_s16<PHASE, 2>(m, xp, yp, st);
+        case 4: return launch_s16<PHASE, 4>(m, xp, yp, st);
+        default: return launch_s16<PHASE, 3>(m, xp, yp, st);
+    }
+}
+
 void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->t, 0, m->t_elems * sizeof(float2), st));
     if (m->n1 && m->arena16) {
-        mv16s_kernel<1><<<(unsigned)m->n1, S16_THREADS, sizeof(S16Smem), st>>>(
-            m->items1, m->hdr16_1, m->arena16, xp, m->t, nullptr, m->d_err);
-        HM_CUDA(cudaGetLastError());
-        HM_LAUNCHED();
+        launch_s16_ns<1>(m, xp, nullptr, st);
     } else if (m->n1) {
         mv_phase1<false><<<(unsigned)m->n1, MV_THREADS, 0, st>>>(m->items1, m->hdr1,
                                                                 m->arena, xp, m->t);
@@ -1068,10 +1115,7 @@ void matvec_phase1(MatvecDev* m, const float2* xp, cudaStream_t st) {
 void matvec_phase2(MatvecDev* m, const float2* xp, float2* yp, int64_t ndof, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(yp, 0, ndof * sizeof(float2), st));
     if (m->n2 && m->arena16) {
-        mv16s_kernel<2><<<(unsigned)m->n2, S16_THREADS, sizeof(S16Smem), st>>>(
-            m->items2, m->hdr16_2, m->arena16, xp, m->t, yp, m->d_err);
-        HM_CUDA(cudaGetLastError());
-        HM_LAUNCHED();
+        launch_s16_ns<2>(m, xp, yp, st);
     } else if (m->n2) {
         mv_phase2<false><<<(unsigned)m->n2, MV_THREADS, 0, st>>>(m->items2, m->hdr2,
                                                                 m->arena, xp, m->t, yp);
@@ -1169,7 +1213,7 @@ void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<
         J.rows = c.rows;
         J.ncols = c.ncols;
         J.pad_ = 0;
-        if (J.ld > 192) hm_throw(HM_ERR_UNSUPPORTED, "leaf clusters above 64 points");
+        if (J.ld > MAX_LD) hm_throw(HM_ERR_UNSUPPORTED, "chunk above MAX_LD rows");
         jobs.push_back(J);
     }
     if (jobs.empty()) return;
@@ -1285,4 +1329,58 @@ int matvec_take_error(MatvecDev* m, cudaStream_t st) {
     HM_CUDA(cudaStreamSynchronize(st));
     if (e) HM_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
     return e;
+}
+
+// Tunable launch parameters of the one-vector product (tune.cu): the stage
+// count of the streamed BF16 kernels, and for FP32 storage the byte size of
+// the work items (the BF16 arena is laid out along the build's items, so
+// its tiling stays).  The product's CUDA graph is re-captured on next use.
+void matvec_set_params(MatvecDev* m, const MatvecPlan& plan, int s16_nstage, int64_t item_bytes,
+                       cudaStream_t st) {
+    if (s16_nstage < 2 || s16_nstage > 4) hm_throw(HM_ERR_ARG, "stage count must be 2, 3 or 4");
+    if (item_bytes < 16 * 1024 || item_bytes > 16 * 1024 * 1024)
+        hm_throw(HM_ERR_ARG, "item bytes out of range");
+    HM_CUDA(cudaStreamSynchronize(st));
+    matvec_graph_reset(m);
+    m->s16_nstage = s16_nstage;
+    if (!m->arena16 && item_bytes != m->item_bytes) set_tiling(m, plan, item_bytes, st);
+}
+
+// Restricts the one-vector and accurate products to the work items whose
+// rows (phase 2) or columns (phase 1) lie in an active segment of the vector
+// (segment q = DOFs [dof_bounds[q], dof_bounds[q + 1]); blocks never straddle
+// two segments of a joined batch).  Items of inactive segments are left out
+// of the launches, so their parts of t and y stay zero.  All segments active
+// restores the full item lists.  The product's graph is re-captured.
+void matvec_select_segments(MatvecDev* m, const std::vector<int64_t>& dof_bounds,
+                            const std::vector<int>& act, cudaStream_t st) {
+    bool all = true;
+    for (int a : act) all = all && a;
+    HM_CUDA(cudaStreamSynchronize(st));
+    matvec_graph_reset(m);
+    if (all) {
+        m->items1 = m->items1_full;
+        m->items2 = m->items2_full;
+        m->n1 = m->n1_full;
+        m->n2 = m->n2_full;
+        return;
+    }
+    if (!m->sel1) {
+        m->sel1 = (WorkItem*)hm_dmalloc(m->tile_bufs, std::max<int64_t>(m->n1_full, 1) * sizeof(WorkItem), st, false);
+        m->sel2 = (WorkItem*)hm_dmalloc(m->tile_bufs, std::max<int64_t>(m->n2_full, 1) * sizeof(WorkItem), st, false);
+    }
+    auto pick = [&](const std::vector<WorkItem>& all_items, WorkItem* dst, int64_t& n) {
+        std::vector<WorkItem> keep;
+        for (const WorkItem& w : all_items) {
+            const int64_t q = std::upper_bound(dof_bounds.begin(), dof_bounds.end(), w.dof) - dof_bounds.begin() - 1;
+            if (q >= 0 && q < (int64_t)act.size() && act[q]) keep.push_back(w);
+        }
+        n = (int64_t)keep.size();
+        if (n) HM_CUDA(cudaMemcpyAsync(dst, keep.data(), n * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+    };
+    pick(m->h_items1, m->sel1, m->n1);
+    pick(m->h_items2, m->sel2, m->n2);
+    m->items1 = m->sel1;
+    m->items2 = m->sel2;
 }

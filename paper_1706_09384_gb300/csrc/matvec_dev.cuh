@@ -52,6 +52,18 @@ struct TcItem {
 
 struct MatvecDev {
     int storage = 0;
+    int s16_nstage = 3;                 // stages of the streamed BF16 kernels (2, 3 or 4; the
+                                        // autotuner may change it)
+    int64_t item_bytes = 256 * 1024;    // target FP32 bytes of a work item
+    std::vector<DevChunk> dc;           // chunk headers in plan order (host)
+    std::vector<DevBuf> tile_bufs;      // items, orders and headers of the current tiling
+    // the full item lists of the tiling, and buffers for a subset of them (a
+    // joined batch whose converged problems are left out of the products)
+    WorkItem* items1_full = nullptr;
+    WorkItem* items2_full = nullptr;
+    int64_t n1_full = 0, n2_full = 0;
+    WorkItem* sel1 = nullptr;
+    WorkItem* sel2 = nullptr;
     float2* arena = nullptr;
     int64_t arena_elems = 0;
     DevChunk* chunks = nullptr;

@@ -32,7 +32,7 @@ class hm_opts(C.Structure):
                 ("fp64_switch_ksr", C.c_double), ("recompress", C.c_int32),
                 ("aca_max_rank", C.c_int32), ("workspace_bytes", C.c_int64),
                 ("verbose", C.c_int32), ("pad_", C.c_int32), ("weights", C.c_void_p),
-                ("rank_model", C.c_void_p), ("reserved", C.c_int32 * 2)]
+                ("rank_model", C.c_void_p), ("tune_cache", C.c_char_p)]
 
 
 class hm_problem(C.Structure):
@@ -66,6 +66,8 @@ SIGNATURES = {
     "hm_opts_default": (None, [_P]),
     "hm_build": (_I32, [_P, _P, _I64, _D, _D, _D, _D, _I32, _D, _D, _I64, _P, _P, _P]),
     "hm_build_batch": (_I32, [_I32, _P, _D, _P, _P, _P]),
+    "hm_batch_join": (_I32, [_I32, _P, _P, _P]),
+    "hm_gmres_batch": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
     "hm_matvec": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_matvec_host": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_gmres": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
@@ -149,6 +151,10 @@ def hm_opts_default(**kw):
             w = np.ascontiguousarray(v, dtype=np.float64)
             o._w = w
             o.weights = w.ctypes.data
+        elif k == "tune_cache" and v is not None:
+            b = os.fsencode(v)
+            o._tc = b
+            o.tune_cache = b
         elif k == "rank_model" and v is not None:
             m = np.ascontiguousarray(v, dtype=np.float32)
             assert m.size == HM_RANK_MODEL_PARAMS
@@ -332,6 +338,32 @@ class HMatrix:
         if check and st != HM_ERR_NOCONV:
             _check(st, "hm_gmres")
         return x, it.value, rr.value, st
+
+    @classmethod
+    def join(cls, handles, stream=None):
+        """The block-diagonal operator of several built handles (hm_batch_join)."""
+        arr = (C.c_void_p * len(handles))(*[H.h for H in handles])
+        h = C.c_void_p()
+        _check(lib().hm_batch_join(len(handles), arr, _stream_ptr(stream), C.byref(h)),
+               "hm_batch_join")
+        J = cls(h, sum(H.n_c for H in handles))
+        J.segments = [H.n_c for H in handles]
+        return J
+
+    def gmres_batch(self, b, x=None, restart=50, tol=1e-6, maxit=1000, stream=None, check=True):
+        """Lockstep GMRES, one per problem of a joined handle; b: cuda complex128
+        concatenated vector.  Returns (x, iters[nprob], relres[nprob], status)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        nprob = len(self.segments)
+        it = np.zeros(nprob, np.int32)
+        rr = np.zeros(nprob, np.float64)
+        st = lib().hm_gmres_batch(self.h, b.data_ptr(), x.data_ptr(), restart, tol, maxit,
+                                  _np_ptr(it), _np_ptr(rr), _stream_ptr(stream))
+        if check and st != HM_ERR_NOCONV:
+            _check(st, "hm_gmres_batch")
+        return x, it, rr, st
 
     def gmres_multi(self, B, X=None, restart=50, tol=1e-6, maxit=1000, stream=None, check=True):
         """Lockstep GMRES for the columns of cuda complex128 B (3 n_c, nrhs).

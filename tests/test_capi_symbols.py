@@ -81,6 +81,10 @@ def test_binding_constants_match_header():
         assert getattr(hm, name) == int(defines[name]), name
     # points, normals, n_c | rho, lambda, mu, omega | kernel, pad_ | eta, leaf_size, weights
     assert ctypes.sizeof(hm.hm_problem) == 3 * 8 + 4 * 8 + 2 * 4 + 3 * 8
+    # storage, aca_fp32 | diag_value, fp64_switch_ksr | recompress, aca_max_rank |
+    # workspace_bytes | verbose, pad_ | weights, rank_model, tune_cache
+    assert ctypes.sizeof(hm.hm_opts) == 2 * 4 + 2 * 8 + 2 * 4 + 8 + 2 * 4 + 3 * 8
+    assert "tune_cache" in text
 
 
 def test_batch_argument_errors_without_gpu():
