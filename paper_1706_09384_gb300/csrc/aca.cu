@@ -276,6 +276,31 @@ __device__ __forceinline__ void sub_df(double2& g, const float (&s)[4]) {
     g.y -= (double)s[2] + (double)s[3];
 }
 
+// This lane's share of three double-float dot products over rows lane, lane +
+// 32, ... < n of a column a and three consecutive columns b_q (ld n): out[2q],
+// out[2q + 1] = re, im of sum conj(a) b_q, or of sum a conj(b_q) (conj_b),
+// each rounded to FP64 once.  Not inlined: it keeps the ACA kernel's register
+// allocation out of the loop.
+__device__ __noinline__ void df_dots3(const float4* a, const float4* b, int64_t n, int lane,
+                                      bool conj_b, double* out) {
+    float s[3][4] = {};
+    for (int64_t r = lane; r < n; r += 32) {
+        const float4 u = a[r];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (conj_b)
+                df_cmac_conj(s[q], u, b[r + q * n]);
+            else
+                df_cmac_conj(s[q], b[r + q * n], u);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        out[2 * q] = (double)s[q][0] + (double)s[q][1];
+        out[2 * q + 1] = (double)s[q][2] + (double)s[q][3];
+    }
+}
+
 template <int N>
 HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
     warp_sum_many<N>(x);
@@ -317,6 +342,7 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
     __shared__ int s_k;
     __shared__ double s_normB2, s_sref, s_best, s_dB2;
     __shared__ double2 s_gam[9];
+    __shared__ double2 s_gdu[9], s_gdv[9];  // new diagonal Gram blocks (double-float path)
     __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
     __shared__ int s_lost;   // a row retired for singular pivots carried a non-negligible residual
     __shared__ GreenParams s_gp;
@@ -587,6 +613,95 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                 bi = i64;
             }
             if (tid == 0) s_inext = bi;
+            if constexpr (DF) {
+                // ---- step 5: new factor columns (FP64 and their double-float copies) ----
+                if (k + 3 <= J.cap) {
+                    for (int64_t r = tid; r < m3; r += AT)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) cfma(acc, C[3 * r + a], s_gam[3 * a + q]);
+                            U[r + (int64_t)(k + q) * m3] = acc;
+                            Ud[r + (int64_t)(k + q) * m3] = df_of(acc);
+                        }
+                    for (int64_t c = tid; c < n3; c += AT)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const double2 vn = cconj(R[a * n3 + c]);
+                            V[c + (int64_t)(k + a) * n3] = vn;
+                            Vd[c + (int64_t)(k + a) * n3] = df_of(vn);
+                        }
+                }
+                __syncthreads();  // publishes the new columns to the CTA
+                if (k + 3 > J.cap) {
+                    if (tid == 0) s_stop = 2;
+                    __syncthreads();
+                    break;
+                }
+                // ---- step 6: cross terms (U_p^H Un_q)(Vn_q^H V_p) of <B_k, dB> for p < k and the
+                // new diagonal Gram blocks (p = k .. k + 2), as double-float dot products over the
+                // double-float copies (FP32 pipes), each warp total rounded to FP64 once ----
+                double cre = 0.0, cim = 0.0;
+                for (int p = wid; p < k + 3; p += AW) {
+                    double xy[12];
+                    df_dots3(Ud + (int64_t)p * m3, Ud + (int64_t)k * m3, m3, lane, false, xy);
+                    df_dots3(Vd + (int64_t)p * n3, Vd + (int64_t)k * n3, n3, lane, true, xy + 6);
+                    warp_sum_many<12>(xy);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const double2 xq = make_double2(xy[2 * q], xy[2 * q + 1]);          // U_p^H Un_q
+                        const double2 yq = make_double2(xy[6 + 2 * q], xy[6 + 2 * q + 1]);  // Vn_q^H V_p
+                        if (p < k) {
+                            const double2 z = cmul(xq, yq);
+                            cre += z.x;
+                            cim += z.y;
+                            if (GU && lane == 0) {  // the new Gram columns, by Hermitian symmetry
+                                GU[p + (int64_t)(k + q) * J.cap] = xq;
+                                GU[(k + q) + (int64_t)p * J.cap] = cconj(xq);
+                                GV[(k + q) + (int64_t)p * J.cap] = yq;
+                                GV[p + (int64_t)(k + q) * J.cap] = cconj(yq);
+                            }
+                        } else if (lane == 0) {
+                            s_gdu[3 * (p - k) + q] = xq;  // Un_{p-k}^H Un_q
+                            s_gdv[3 * q + (p - k)] = yq;  // Vn_q^H Vn_{p-k}
+                        }
+                    }
+                }
+                double cr[2] = {lane == 0 ? cre : 0.0, lane == 0 ? cim : 0.0};
+                block_sum<2>(cr, sums);  // its barriers also publish s_gdu, s_gdv
+                if (tid == 0) {
+                    // ||dB||^2 = sum_{q,q2} (Un_q^H Un_q2)(Vn_q2^H Vn_q)
+                    double dB2 = 0.0;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int q2 = 0; q2 < 3; ++q2) dB2 += cmul(s_gdu[3 * q + q2], s_gdv[3 * q2 + q]).x;
+                    if (GU) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+#pragma unroll
+                            for (int q2 = 0; q2 < 3; ++q2) {
+                                const int64_t at = (k + q) + (int64_t)(k + q2) * J.cap;
+                                GU[at] = s_gdu[3 * q + q2];
+                                GV[at] = s_gdv[3 * q + q2];
+                            }
+                    }
+                    const double nb2 = s_normB2 + 2.0 * cr[0] + dB2;
+                    s_normB2 = nb2;
+                    const int k2 = k + 3;
+                    s_k = k2;
+                    if (!(nb2 == nb2) || !(dB2 == dB2))
+                        s_stop = 3;
+                    else if (sqrt(dB2) <= eps * sqrt(fmax(nb2, 0.0)))
+                        s_stop = 1;
+                    else if (s_inext < 0 || k2 / 3 >= steps_max)
+                        s_stop = 1;
+                    else
+                        s_ihat = s_inext;
+                }
+                __syncthreads();
+            } else {
             // ---- step 5: new factor columns and their Gram matrices ----
             double g[36];
 #pragma unroll
@@ -727,6 +842,7 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                     s_ihat = s_inext;
             }
             __syncthreads();
+            }  // FP64 path
         }
         if (tid == 0) {
             res[job].k = s_k;
