@@ -139,6 +139,30 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
                    double lambda, double mu, double omega, int32_t kernel, double eps, double eta,
                    int64_t leaf_size, const hm_opts* opts, void* stream, hm_handle* out);
 
+/* Builds the H-matrix between two clouds (Sec. 4: the collocation points x_i
+ * are the rows, the integration points y_j with their normals and weights the
+ * columns; Sec. 2.1: a cluster tree per cloud, the partition pairs target and
+ * source clusters from the two roots with the admissibility of Sec. 6.1): the
+ * rectangular A (3 n_x x 3 n_y), block (i, j) = K(x_i, y_j) w_j.  Compression,
+ * randomized fallback, recompression and storage are those of hm_build.
+ *   targets  host n_x x 3 FP64;  sources host n_y x 3 FP64;
+ *   normals  host n_y x 3 unit normals at the sources (T kernel), else NULL;
+ *   opts->weights: NULL or n_y source weights w_j.
+ * The handle's index space is the n_x + n_y points, targets first: vectors
+ * given to hm_matvec / hm_matvec_host have 3 (n_x + n_y) entries in the order
+ * (targets, sources), each part in its cloud's original point order; the
+ * product reads the source part of x (the target part is ignored) and writes
+ * A x_sources into the target part of y (the source part of y is zero).
+ * hm_stats reports n_targets.  hm_gmres, hm_gmres_multi (the operator is
+ * rectangular), hm_lu_factor and hm_estimate_error report HM_ERR_UNSUPPORTED;
+ * two-cloud handles cannot be joined.
+ * Errors: HM_ERR_ARG (as hm_build; also a source point that coincides with a
+ * target point: the tensor is singular there), HM_ERR_OOM, HM_ERR_CUDA. */
+hm_status hm_build2(const double* targets, int64_t n_x, const double* sources,
+                    const double* normals, int64_t n_y, double rho, double lambda, double mu,
+                    double omega, int32_t kernel, double eps, double eta, int64_t leaf_size,
+                    const hm_opts* opts, void* stream, hm_handle* out);
+
 /* Right-hand sides per block of the tensor-core product (see hm_matvec). */
 #define HM_NRHS_BLOCK 32
 

@@ -34,6 +34,7 @@ hm_status hm_batch_join(int32_t nprob, const hm_handle* hs, void* stream, hm_han
             if (hs[q]->opts.storage != hs[0]->opts.storage)
                 hm_throw(HM_ERR_ARG, "handles with different storage");
             if (!hs[q]->segments.empty()) hm_throw(HM_ERR_ARG, "a joined handle cannot be joined again");
+            if (hs[q]->n_targets) hm_throw(HM_ERR_ARG, "two-cloud handles cannot be joined");
         }
         J = new hm_matrix();
         J->device = dev;

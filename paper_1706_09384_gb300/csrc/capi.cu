@@ -11,6 +11,8 @@
 #include <numeric>
 #include <sstream>
 
+#include <unordered_set>
+
 #include "hm_internal.h"
 
 // ---------------------------------------------------------------- errors
@@ -349,16 +351,16 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                     continue;
                 }
                 {
-                    // per rank-3 step with k = 3s columns built: residual row and column
-                    // 9 k (m + n) complex multiply-adds (double-float), cross terms of the
-                    // norm update / Gram columns 9 k (m + n) (FP64), new Gram diagonal
-                    // blocks 27 (m + n) and factor columns U = C gamma 27 m (FP64); m + n
-                    // Green's tensor evaluations
+                    // per rank-3 step with k = 3s columns built (8 flops per complex
+                    // multiply-add): residual row and column 9 k (m + n), cross terms of
+                    // the norm update / Gram columns 9 k (m + n) and new Gram diagonal
+                    // blocks 27 (m + n), all in double-float; factor columns U = C gamma
+                    // 27 m in FP64; m + n Green's tensor evaluations (FP64)
                     const double K = res[j].k / 3, mn = (double)(jobs[j].m + jobs[j].n);
                     const double cross = 8.0 * 9.0 * mn * 3.0 * (K * (K - 1.0) / 2.0);
                     flops += 2.0 * cross;
-                    flops_df += cross;
-                    flops64 += cross + 8.0 * 27.0 * (mn + (double)jobs[j].m) * K;
+                    flops_df += 2.0 * cross + 8.0 * 27.0 * mn * K;
+                    flops64 += 8.0 * 27.0 * (double)jobs[j].m * K;
                     evals += mn * K;
                 }
                 keep.push_back(j);
@@ -617,6 +619,128 @@ hm_matrix* build_setup(const double* points, const double* normals, int64_t n_c,
     return h;
 }
 
+// Two clouds (Sec. 4: collocation points x_i as rows, integration points y_j
+// with their normals and weights as columns): the handle holds both clouds,
+// targets first, each with its own cluster tree (the rule of Sec. 2.1), and
+// the partition pairs a target cluster with a source cluster from the two
+// roots.  Its operator is the rectangular A (3 n_x x 3 n_y) embedded in the
+// square index space of n_x + n_y points: every block couples target rows with
+// source columns, so the product reads the source part of x and writes the
+// target part of y (the source part stays zero).
+hm_matrix* build_setup2(const double* targets, int64_t n_x, const double* sources,
+                        const double* normals, int64_t n_y, double rho, double lambda, double mu,
+                        double omega, int32_t kernel, double eps, double eta, int64_t leaf_size,
+                        const hm_opts* opts, cudaStream_t st, HandleHold& hold) {
+    if (!targets || !sources || n_x < 1 || n_y < 1) hm_throw(HM_ERR_ARG, "null pointer or empty cloud");
+    if (!(rho > 0) || !(mu > 0) || !(omega > 0) || !std::isfinite(rho) || !std::isfinite(mu) ||
+        !std::isfinite(omega) || !std::isfinite(lambda) || !(lambda + 2 * mu > 0))
+        hm_throw(HM_ERR_ARG, "material parameters must be finite with rho, mu, omega > 0");
+    if (!(eps > 0 && eps < 1)) hm_throw(HM_ERR_ARG, "eps must lie in (0, 1)");
+    if (!(eta > 0) || !std::isfinite(eta)) hm_throw(HM_ERR_ARG, "eta must be positive");
+    if (kernel != HM_KERNEL_U && kernel != HM_KERNEL_T) hm_throw(HM_ERR_ARG, "unknown kernel");
+    if (kernel == HM_KERNEL_T && !normals) hm_throw(HM_ERR_ARG, "the T kernel needs source normals");
+    if (leaf_size < 1 || leaf_size > 1024) hm_throw(HM_ERR_ARG, "leaf_size must be in 1..1024");
+    if (!finite_all(targets, 3 * n_x) || !finite_all(sources, 3 * n_y))
+        hm_throw(HM_ERR_ARG, "non-finite point coordinates");
+    if (kernel == HM_KERNEL_T && !finite_all(normals, 3 * n_y)) hm_throw(HM_ERR_ARG, "non-finite normals");
+    hm_opts o;
+    hm_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.storage != HM_STORE_FP32 && o.storage != HM_STORE_BF16)
+        hm_throw(HM_ERR_ARG, "unknown storage type");
+    if (!std::isfinite(o.diag_value)) hm_throw(HM_ERR_ARG, "non-finite diag_value");
+    if (!(o.fp64_switch_ksr > 0)) hm_throw(HM_ERR_ARG, "fp64_switch_ksr must be > 0 (or +inf)");
+    if (o.aca_fp32 != 0) hm_throw(HM_ERR_ARG, "aca_fp32 must be 0");
+    {  // a source at a target's position has a singular Green's tensor (Eq. elasto_U)
+        struct Key {
+            double x, y, z;
+            bool operator==(const Key& k) const { return x == k.x && y == k.y && z == k.z; }
+        };
+        struct Hash {
+            size_t operator()(const Key& k) const {
+                const std::hash<double> h;
+                return h(k.x) ^ (h(k.y) * 1000003u) ^ (h(k.z) * 998244353u);
+            }
+        };
+        std::unordered_set<Key, Hash> tset;
+        for (int64_t i = 0; i < n_x; ++i) tset.insert({targets[3 * i], targets[3 * i + 1], targets[3 * i + 2]});
+        for (int64_t j = 0; j < n_y; ++j)
+            if (tset.count({sources[3 * j], sources[3 * j + 1], sources[3 * j + 2]})) {
+                char msg[120];
+                std::snprintf(msg, sizeof(msg), "source point %lld coincides with a target point",
+                              (long long)j);
+                hm_throw(HM_ERR_ARG, msg);
+            }
+    }
+    hm_matrix* h = new hm_matrix();
+    hold.reset(h);
+    const int64_t n = n_x + n_y;
+    h->nc = n;
+    h->n_targets = n_x;
+    h->kernel = kernel;
+    h->rho = rho;
+    h->lam = lambda;
+    h->mu = mu;
+    h->omega = omega;
+    h->eps = eps;
+    h->eta = eta;
+    h->leaf = leaf_size;
+    h->opts = o;
+    h->gp = make_green_params(kernel, rho, lambda, mu, omega, o.diag_value);
+    h->gp.ksr_switch = o.fp64_switch_ksr;
+    HM_CUDA(cudaGetDevice(&h->device));
+    auto t0 = clk::now();
+    h->d_pts_p = (double*)hm_dmalloc(h->owner, 24 * n, st, false);
+    h->d_perm = (int64_t*)hm_dmalloc(h->owner, 8 * n, st, false);
+    {
+        std::vector<int64_t> iota(n);
+        std::iota(iota.begin(), iota.end(), 0);
+        HM_CUDA(cudaMemcpyAsync(h->d_pts_p, targets, 24 * n_x, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(h->d_pts_p + 3 * n_x, sources, 24 * n_y, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(h->d_perm, iota.data(), 8 * n, cudaMemcpyHostToDevice, st));
+        TreeResult tx = build_cluster_tree(h->d_pts_p, h->d_perm, n_x, leaf_size, st);
+        TreeResult ty = build_cluster_tree(h->d_pts_p + 3 * n_x, h->d_perm + n_x, n_y, leaf_size, st);
+        const int64_t cx = (int64_t)tx.clusters.size();
+        h->clusters = std::move(tx.clusters);
+        for (hm_cluster c : ty.clusters) {
+            c.begin += n_x;
+            c.end += n_x;
+            if (c.child0 >= 0) c.child0 += cx;
+            if (c.child1 >= 0) c.child1 += cx;
+            h->clusters.push_back(c);
+        }
+        h->perm = std::move(tx.perm);
+        h->perm.insert(h->perm.end(), ty.perm.begin(), ty.perm.end());  // already global indices
+        h->depth = std::max(tx.depth, ty.depth);
+        h->sigma_root = cx;
+    }
+    {  // source weights (W_y of Sec. 4) in tree order; targets carry 1 (never read)
+        std::vector<double> wp(n, 1.0);
+        if (o.weights) {
+            for (int64_t p = n_x; p < n; ++p) wp[p] = o.weights[h->perm[p] - n_x];
+            if (!finite_all(wp.data(), n)) hm_throw(HM_ERR_ARG, "non-finite weights");
+            double* d_w = (double*)hm_dmalloc(h->owner, 8 * n, st, false);
+            HM_CUDA(cudaMemcpyAsync(d_w, wp.data(), 8 * n, cudaMemcpyHostToDevice, st));
+            HM_CUDA(cudaStreamSynchronize(st));
+            h->gp.w = d_w;
+        }
+        h->opts.weights = nullptr;
+    }
+    if (kernel == HM_KERNEL_T) {  // source normals in tree order; targets zero (never read)
+        std::vector<double> np(3 * n, 0.0);
+        for (int64_t p = n_x; p < n; ++p)
+            for (int a = 0; a < 3; ++a) np[3 * p + a] = normals[3 * (h->perm[p] - n_x) + a];
+        h->d_nrm_p = (double*)hm_dmalloc(h->owner, 24 * n, st, false);
+        HM_CUDA(cudaMemcpyAsync(h->d_nrm_p, np.data(), 24 * n, cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+    }
+    h->t_tree_ms = ms_since(t0);
+    t0 = clk::now();
+    h->blocks = build_partition(h->clusters, eta, st, h->sigma_root);
+    h->t_part_ms = ms_since(t0);
+    return h;
+}
+
 // Storage plan, arena, near field, factor chunks (BF16 copy) and work vectors
 // once the low-rank factors of the problem are staged.
 void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<const float2*>& sv,
@@ -695,6 +819,38 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
     HandleHold hold;
     hm_matrix* h = build_setup(points, normals, n_c, rho, lambda, mu, omega, kernel, eps, eta,
                                leaf_size, opts, st, hold);
+    std::vector<hm_matrix*> hs{h};
+    std::vector<DevBuf> staging;
+    std::vector<std::vector<const float2*>> su(1), sv(1);
+    su[0].assign(h->blocks.size(), nullptr);
+    sv[0].assign(h->blocks.size(), nullptr);
+    try {
+        build_low_rank(hs, staging, su, sv, st);
+        build_finish(h, su[0], sv[0], st);
+    } catch (...) {
+        cudaStreamSynchronize(st);
+        free_all(staging);
+        throw;
+    }
+    free_all(staging);
+    h->t_total_ms = ms_since(t_all);
+    report_build(h);
+    *out = hold.release();
+    HM_API_END
+}
+
+hm_status hm_build2(const double* targets, int64_t n_x, const double* sources,
+                    const double* normals, int64_t n_y, double rho, double lambda, double mu,
+                    double omega, int32_t kernel, double eps, double eta, int64_t leaf_size,
+                    const hm_opts* opts, void* stream, hm_handle* out) {
+    if (out) *out = nullptr;
+    HM_API_BEGIN
+    if (!out) hm_throw(HM_ERR_ARG, "null output handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t_all = clk::now();
+    HandleHold hold;
+    hm_matrix* h = build_setup2(targets, n_x, sources, normals, n_y, rho, lambda, mu, omega, kernel,
+                                eps, eta, leaf_size, opts, st, hold);
     std::vector<hm_matrix*> hs{h};
     std::vector<DevBuf> staging;
     std::vector<std::vector<const float2*>> su(1), sv(1);
@@ -813,6 +969,7 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!b || !x || restart < 1 || restart > 500 || !(tol > 0) || maxit < 1)
         hm_throw(HM_ERR_ARG, "invalid GMRES arguments (restart must be in 1..500)");
+    if (h->n_targets) hm_throw(HM_ERR_UNSUPPORTED, "a two-cloud operator is rectangular: no GMRES");
     const GmresResult R = gmres_solve(h, (const double2*)b, (double2*)x, restart, tol, maxit,
                                       (cudaStream_t)stream);
     if (iters) *iters = R.iters;
@@ -832,6 +989,7 @@ hm_status hm_gmres_multi(hm_handle h, int32_t nrhs, const void* b, void* x, int3
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!b || !x || nrhs < 1 || restart < 1 || restart > 500 || !(tol > 0) || maxit < 1)
         hm_throw(HM_ERR_ARG, "invalid GMRES arguments (restart must be in 1..500)");
+    if (h->n_targets) hm_throw(HM_ERR_UNSUPPORTED, "a two-cloud operator is rectangular: no GMRES");
     const int64_t bytes = 3 * h->nc * (int64_t)nrhs * 16;
     const char* bb = (const char*)b;
     const char* xb = (const char*)x;
@@ -859,7 +1017,8 @@ hm_status hm_estimate_error(hm_handle h, int64_t nsample, uint64_t seed, double*
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!delta_f || !norm_f) hm_throw(HM_ERR_ARG, "null output");
-    if (!h->segments.empty()) hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch handle");
+    if (!h->segments.empty() || h->n_targets)
+        hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch or two-cloud handle");
     estimate_error(h, nsample, seed, delta_f, norm_f, (cudaStream_t)stream);
     HM_API_END
 }
@@ -868,7 +1027,8 @@ hm_status hm_lu_factor(hm_handle h, double eps_lu, void* stream) {
     HM_API_BEGIN
     if (validate_common(h) != HM_OK) return HM_ERR_ARG;
     if (!(eps_lu > 0) || !(eps_lu < 1)) hm_throw(HM_ERR_ARG, "eps_lu must lie in (0, 1)");
-    if (!h->segments.empty()) hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch handle");
+    if (!h->segments.empty() || h->n_targets)
+        hm_throw(HM_ERR_UNSUPPORTED, "not available on a joined batch or two-cloud handle");
     hlu_factor(h, eps_lu, (cudaStream_t)stream);
     HM_API_END
 }
@@ -921,7 +1081,8 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
     matvec_alg_bytes(h->mv, 3 * h->nc, alg);
     std::ostringstream os;
     os.precision(10);
-    os << "{\"n_c\": " << h->nc << ", \"kernel\": \"" << (h->kernel ? "T" : "U") << "\""
+    os << "{\"n_c\": " << h->nc << ", \"n_targets\": " << h->n_targets
+       << ", \"kernel\": \"" << (h->kernel ? "T" : "U") << "\""
        << ", \"depth\": " << h->depth << ", \"clusters\": " << h->clusters.size()
        << ", \"blocks\": " << h->blocks.size() << ", \"dense_blocks\": " << nd
        << ", \"lowrank_blocks\": " << nl << ", \"C_sp\": " << csp

@@ -40,6 +40,16 @@ HM_HD void cfms_conj(double2& acc, double2 a, double2 b) {
     acc.x = fma(-a.x, b.x, fma(-a.y, b.y, acc.x));
     acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
 }
+// acc += a * conj(b)
+HM_HD void cfma_conjb(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
+}
+// acc -= conj(a) * b
+HM_HD void cfms_conja(double2& acc, double2 a, double2 b) {
+    acc.x = fma(-a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(-a.x, b.y, fma(a.y, b.x, acc.y));
+}
 // acc += conj(a) * b
 HM_HD void cfma_conja(double2& acc, double2 a, double2 b) {
     acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));

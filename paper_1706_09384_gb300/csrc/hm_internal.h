@@ -50,9 +50,11 @@ struct TreeResult {
 TreeResult build_cluster_tree(double* d_pts, int64_t* d_perm, int64_t nc, int64_t leaf,
                               cudaStream_t st);
 // Level-synchronous block-cluster-tree traversal (Sec. 2.1) with the box
-// admissibility of Sec. 6.1.  Returns blocks (tau, sigma, admissible) in level order.
+// admissibility of Sec. 6.1, from the root pair (0, sigma_root): 0 for one
+// cloud; for two clouds the targets' tree comes first in cl and sigma_root is
+// the sources' root.  Returns blocks (tau, sigma, admissible) in level order.
 std::vector<hm_block> build_partition(const std::vector<hm_cluster>& cl, double eta,
-                                      cudaStream_t st);
+                                      cudaStream_t st, int64_t sigma_root = 0);
 
 // ---------------- matvec storage plan (matvec.cu) ----------------
 // Storage segments: the leaf clusters, each cut into the fewest contiguous
@@ -296,8 +298,9 @@ struct hm_matrix {
     // built, 18 k (m + n) complex multiply-adds (residual row and column, and the
     // Gram / cross terms of the norm update), 8 flops each
     double aca_flops = 0;
-    double aca_flops_fp64 = 0;       // of which FP64 (cross terms, Gram diagonal blocks, U = C gamma)
-    double aca_flops_df = 0;         // of which double-float on the FP32 pipes (residuals)
+    double aca_flops_fp64 = 0;       // FP64 flops of the model (factor columns U = C gamma)
+    double aca_flops_df = 0;         // double-float flops of the model on the FP32 pipes
+                                     // (residuals, norm-update cross terms, Gram blocks)
     double aca_green_evals = 0;      // Green's tensors evaluated by the ACA (FP64)
     int64_t aca_workspace_peak = 0;  // largest ACA workspace of one batch (bytes)
     int64_t aca_workspace_total = 0; // ACA workspace summed over batches and re-runs (bytes)
@@ -317,4 +320,8 @@ struct hm_matrix {
     int used_rank_model = 0;
     // a joined batch (hm_batch_join): points of each problem, in order; empty otherwise
     std::vector<int64_t> segments;
+    // two clouds (hm_build2): the number of target points, which come first (their
+    // clusters too); 0 for one cloud
+    int64_t n_targets = 0;
+    int64_t sigma_root = 0;  // the sources' root cluster (0 for one cloud)
 };

@@ -9,9 +9,11 @@
 // (R_U R_V^H)^H P = L S,
 //     Q_U P_r S_r^{1/2} = U (R_V^H L_r S_r^{-1/2}) =: U T_U,
 //     Q_V L_r S_r^{1/2} = V (R_U^H P_r S_r^{-1/2}) =: V T_V,
-// which holds whether or not R_U, R_V are invertible.  The SVD of the k x k
-// core is a one-sided Jacobi (Hestenes) iteration in FP64 with round-robin
-// pair ordering.  Truncation: smallest r' with
+// which holds whether or not R_U, R_V are invertible.  The Gram matrices, their
+// Cholesky factors and the core W are FP64; the SVD of the k x k core is a
+// one-sided Jacobi (Hestenes) iteration in double-float arithmetic on the FP32
+// pipes (rotation angles in FP64) with round-robin pair ordering.  Truncation:
+// smallest r' with
 // (sum_{i >= r'} s_i^2)^{1/2} <= eps (sum s_i^2)^{1/2} (Frobenius, matching the
 // ACA stopping test).  The tall products U T_U, V T_V are applied by a second
 // kernel, in double-float arithmetic on the FP32 pipes (~44 significant bits
@@ -128,7 +130,7 @@ __device__ void chol_equil(double2* G, int k, double* dsc) {
             if (a <= b) {
                 const double2 ra = G[j + (int64_t)a * k], rb = G[j + (int64_t)b * k];
                 double2 g = G[a + (int64_t)b * k];
-                g = csub(g, cconjmul(ra, rb));
+                cfms_conja(g, ra, rb);  // g -= conj(ra) rb, fused
                 G[a + (int64_t)b * k] = g;
             }
         }
@@ -142,13 +144,162 @@ __device__ void chol_equil(double2* G, int k, double* dsc) {
     __syncthreads();
 }
 
+// ---- double-float arithmetic for the core's Jacobi (pairs of FP32 numbers,
+// about 2^-46 relative; Dekker's product with an FMA, Knuth's two-sum; every
+// operation explicitly rounded so nothing is fused) ----
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfl df_norm(float h, float l) {  // |l| small against |h|
+    const float s = __fadd_rn(h, l);
+    return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    const dfl s = df_two_sum(a.h, b.h);
+    return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_of_d(double v) {
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - (double)h)};
+}
+// s += a b (accumulating; a, b double-float)
+__device__ __forceinline__ void df_acc(float& h, float& l, dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    const dfl t = df_two_sum(h, p);
+    h = t.h;
+    l = __fadd_rn(l, __fadd_rn(t.l, e));
+}
+__device__ __forceinline__ double2 from_df(float4 v) {
+    return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
+// One-sided (Hestenes) Jacobi on the columns of the k x k core W (entries as
+// double-float pairs (re_h, im_h, re_l, im_l)), round-robin pair ordering.
+// Each pair is handled by a group of G lanes (G grows with k): the lanes form
+// the pair's Gram entries as double-float dot products, the group leader turns
+// them into the rotation in FP64 and broadcasts it, and the lanes apply it in
+// double-float.  Only the final columns P_j s_j are needed (T_U, T_V below), so
+// the rotations are not accumulated.  The truncation formulas map the
+// rounding of the small columns through W^H, which amplifies it by up to
+// (s_1 / s_r)^2 ~ eps^-2: the arithmetic must keep u << eps^2 (FP32 does not;
+// double-float does for eps >= 1e-6).  A pair is rotated while
+// |<w_a, w_b>| > 1e-12 ||w_a|| ||w_b||; at most 40 sweeps.
+__device__ void jacobi_columns_df(float4* W, int k) {
+    __shared__ int s_conv;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = k <= 128 ? 8 : (k <= 256 ? 16 : 32);
+    const int gl = lane % G;                // lane within the group
+    const int gid = tid / G;                // group index in the CTA
+    const int ngroups = RT / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+    const int np = (k + 1) & ~1;  // players (a dummy when k is odd)
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_conv = 1;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pi = gid; pi < np / 2; pi += ngroups) {
+                int a, b;
+                if (pi == 0) {
+                    a = np - 1;
+                    b = round;
+                } else {
+                    a = (round + pi) % (np - 1);
+                    b = (round - pi + np - 1) % (np - 1);
+                }
+                if (a >= k || b >= k) continue;  // uniform within the group
+                float s[8] = {};  // alpha, beta, Re g, Im g as (h, l) pairs; g = <w_a, w_b>
+                for (int r = gl; r < k; r += G) {
+                    const float4 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
+                    const dfl ar = {wa.x, wa.z}, ai = {wa.y, wa.w}, br = {wb.x, wb.z}, bi = {wb.y, wb.w};
+                    df_acc(s[0], s[1], ar, ar);
+                    df_acc(s[0], s[1], ai, ai);
+                    df_acc(s[2], s[3], br, br);
+                    df_acc(s[2], s[3], bi, bi);
+                    df_acc(s[4], s[5], ar, br);          // Re conj(wa) wb
+                    df_acc(s[4], s[5], ai, bi);
+                    df_acc(s[6], s[7], ar, bi);          // Im conj(wa) wb
+                    df_acc(s[6], s[7], df_neg(ai), br);
+                }
+                for (int o = G / 2; o > 0; o >>= 1)  // group sums, double-float
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const dfl u = {__shfl_xor_sync(gmask, s[2 * q], o),
+                                       __shfl_xor_sync(gmask, s[2 * q + 1], o)};
+                        const dfl t = df_add({s[2 * q], s[2 * q + 1]}, u);
+                        s[2 * q] = t.h;
+                        s[2 * q + 1] = t.l;
+                    }
+                // rotation parameters on the group leader only (FP64)
+                double c = 1.0, sn = 0.0, pr = 0.0, pim = 0.0;
+                int rot = 0;
+                if (gl == 0) {
+                    const double al = (double)s[0] + (double)s[1], be = (double)s[2] + (double)s[3];
+                    const double gr = (double)s[4] + (double)s[5], gi = (double)s[6] + (double)s[7];
+                    const double ag = sqrt(gr * gr + gi * gi);
+                    if (ag != 0.0 && ag > 1e-12 * sqrt(al * be)) {
+                        rot = 1;
+                        pr = gr / ag;
+                        pim = -gi / ag;  // e^{-i phi}
+                        const double zeta = (be - al) / (2.0 * ag);
+                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = c * t;
+                    }
+                }
+                const int src = lane - gl;
+                rot = __shfl_sync(gmask, rot, src);
+                if (!rot) continue;
+                c = __shfl_sync(gmask, c, src);
+                sn = __shfl_sync(gmask, sn, src);
+                pr = __shfl_sync(gmask, pr, src);
+                pim = __shfl_sync(gmask, pim, src);
+                if (gl == 0) s_conv = 0;
+                const dfl dc = df_of_d(c), ds = df_of_d(sn), dpr = df_of_d(pr), dpi = df_of_d(pim);
+                // [w_a, w_b] <- [w_a, w_b] [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+                for (int r = gl; r < k; r += G) {
+                    const float4 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
+                    const dfl ar = {wa.x, wa.z}, ai = {wa.y, wa.w}, br = {wb.x, wb.z}, bi = {wb.y, wb.w};
+                    // pw = e^{-i phi} w_b
+                    const dfl pwr = df_add(df_mul(dpr, br), df_neg(df_mul(dpi, bi)));
+                    const dfl pwi = df_add(df_mul(dpr, bi), df_mul(dpi, br));
+                    const dfl nar = df_add(df_mul(dc, ar), df_neg(df_mul(ds, pwr)));
+                    const dfl nai = df_add(df_mul(dc, ai), df_neg(df_mul(ds, pwi)));
+                    const dfl nbr = df_add(df_mul(ds, ar), df_mul(dc, pwr));
+                    const dfl nbi = df_add(df_mul(ds, ai), df_mul(dc, pwi));
+                    W[r + (int64_t)a * k] = make_float4(nar.h, nai.h, nar.l, nai.l);
+                    W[r + (int64_t)b * k] = make_float4(nbr.h, nbi.h, nbr.l, nbi.l);
+                }
+            }
+            __syncthreads();
+        }
+        if (s_conv) break;
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, double2* work,
                                                          const double2* gram_in, double2* scratch,
                                                          double eps, int32_t* rank_out,
                                                          int tile_cap) {
     extern __shared__ double2 tile[];       // TILE_ROWS x k
     __shared__ double dsc[1024];
-    __shared__ int s_conv;
     __shared__ int s_r;
     const CoreJob J = jobs[blockIdx.x];
     const int k = J.k;
@@ -196,95 +347,22 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
         const int p = (int)(e % k), c = (int)(e / k);
         double2 acc = make_double2(0.0, 0.0);
         for (int t = max(p, c); t < k; ++t)  // R_U[p][t] nonzero for t >= p, R_V[c][t] for t >= c
-            acc = cadd(acc, cmulc(RU[p + (int64_t)t * k], RV[c + (int64_t)t * k]));
+            cfma_conjb(acc, RU[p + (int64_t)t * k], RV[c + (int64_t)t * k]);  // acc += a conj(b)
         W[e] = acc;
     }
     __syncthreads();
-    // One-sided Jacobi on the columns of W (round-robin ordering).  Each pair is
-    // handled by a group of G lanes (G grows with k); the group leader computes
-    // the rotation and broadcasts it, so the scarce FP64 pipe is not spent on
-    // redundant square roots and divisions.  Only W's final columns P_j s_j are
-    // needed (see T below), so the rotations are not accumulated.
-    // group size: the pairs of a round (k / 2) should fit in one pass of the
-    // CTA's groups, since every round ends at a barrier (k <= 64: one pass)
-    const int G = k <= 128 ? 8 : (k <= 256 ? 16 : 32);
-    const int gl = lane % G;                // lane within the group
-    const int gid = tid / G;                // group index in the CTA
-    const int ngroups = RT / G;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
-    const int np = (k + 1) & ~1;  // players (a dummy when k is odd)
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (tid == 0) s_conv = 1;
-        __syncthreads();
-        for (int round = 0; round < np - 1; ++round) {
-            for (int pi = gid; pi < np / 2; pi += ngroups) {
-                int a, b;
-                if (pi == 0) {
-                    a = np - 1;
-                    b = round;
-                } else {
-                    a = (round + pi) % (np - 1);
-                    b = (round - pi + np - 1) % (np - 1);
-                }
-                if (a >= k || b >= k) continue;  // uniform within the group
-                double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-                for (int r = gl; r < k; r += G) {
-                    const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
-                    al += cabs2(wa);
-                    be += cabs2(wb);
-                    const double2 z = cconjmul(wa, wb);
-                    gr += z.x;
-                    gi += z.y;
-                }
-                for (int o = G / 2; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(gmask, al, o);
-                    be += __shfl_xor_sync(gmask, be, o);
-                    gr += __shfl_xor_sync(gmask, gr, o);
-                    gi += __shfl_xor_sync(gmask, gi, o);
-                }
-                // rotation parameters on the group leader only
-                double c = 1.0, sn = 0.0, pr = 0.0, pim = 0.0;
-                int rot = 0;
-                if (gl == 0) {
-                    const double ag = sqrt(gr * gr + gi * gi);
-                    if (ag != 0.0 && ag > 1e-15 * sqrt(al * be)) {
-                        rot = 1;
-                        pr = gr / ag;
-                        pim = -gi / ag;  // e^{-i phi}
-                        const double zeta = (be - al) / (2.0 * ag);
-                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        sn = c * t;
-                    }
-                }
-                const int src = lane - gl;
-                rot = __shfl_sync(gmask, rot, src);
-                if (!rot) continue;
-                c = __shfl_sync(gmask, c, src);
-                sn = __shfl_sync(gmask, sn, src);
-                pr = __shfl_sync(gmask, pr, src);
-                pim = __shfl_sync(gmask, pim, src);
-                if (gl == 0) s_conv = 0;
-                const double2 phc = make_double2(pr, pim);
-                // [w_a, w_b] <- [w_a, w_b] [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
-                for (int r = gl; r < k; r += G) {
-                    const double2 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
-                    const double2 pw = cmul(phc, wb);
-                    W[r + (int64_t)a * k] = csub(cscale(wa, c), cscale(pw, sn));
-                    W[r + (int64_t)b * k] = cadd(cscale(wa, sn), cscale(pw, c));
-                }
-            }
-            __syncthreads();
-        }
-        if (s_conv) break;
-        __syncthreads();
-    }
+    // The k x k core's SVD: one-sided Jacobi in double-float arithmetic on W,
+    // converted in place (16 bytes per entry either way).
+    float4* Wd = reinterpret_cast<float4*>(W);
+    for (int64_t e = tid; e < (int64_t)k * k; e += RT) Wd[e] = to_df(W[e]);
+    __syncthreads();
+    jacobi_columns_df(Wd, k);
     // singular values (column norms) and descending order
     __shared__ double s_sv[1024];
     __shared__ int s_ord[1024];
     for (int j = wid; j < k; j += RW) {
         double a = 0.0;
-        for (int r = lane; r < k; r += 32) a += cabs2(W[r + (int64_t)j * k]);
+        for (int r = lane; r < k; r += 32) a += cabs2(from_df(Wd[r + (int64_t)j * k]));
         a = warp_sum(a);
         if (lane == 0) s_sv[j] = sqrt(a);
     }
@@ -327,7 +405,7 @@ __global__ void __launch_bounds__(RT) recomp_core_kernel(const CoreJob* jobs, do
         const double s = s_sv[j];
         double2 av = make_double2(0.0, 0.0);
         for (int t = 0; t <= p; ++t)  // (R_U^H)_{p t} = conj(R_U[t][p]), nonzero for t <= p
-            cfma_conja(av, RU[t + (int64_t)p * k], W[t + (int64_t)j * k]);
+            cfma_conja(av, RU[t + (int64_t)p * k], from_df(Wd[t + (int64_t)j * k]));
         TV[p + (int64_t)q * k] = cscale(av, 1.0 / (s * sqrt(s)));
     }
     __syncthreads();

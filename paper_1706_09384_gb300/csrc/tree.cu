@@ -360,7 +360,7 @@ TreeResult build_cluster_tree(double* d_pts, int64_t* d_perm, int64_t nc, int64_
 }
 
 std::vector<hm_block> build_partition(const std::vector<hm_cluster>& cl, double eta,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, int64_t sigma_root) {
     const int64_t ncl = (int64_t)cl.size();
     std::vector<double> lo(3 * ncl), hi(3 * ncl);
     std::vector<int32_t> il(ncl);
@@ -392,7 +392,7 @@ std::vector<hm_block> build_partition(const std::vector<hm_cluster>& cl, double 
     int2* blk = dalloc<int2>(bcap, st);
     int8_t* adm = dalloc<int8_t>(bcap, st);
     unsigned long long* d_counts = dalloc<unsigned long long>(2, st);
-    const int2 root = make_int2(0, 0);
+    const int2 root = make_int2(0, (int)sigma_root);
     HM_CUDA(cudaMemcpyAsync(front, &root, sizeof(int2), cudaMemcpyHostToDevice, st));
     int64_t n = 1, nb = 0;
     while (n > 0) {

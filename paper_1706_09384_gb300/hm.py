@@ -66,6 +66,7 @@ SIGNATURES = {
     "hm_opts_default": (None, [_P]),
     "hm_build": (_I32, [_P, _P, _I64, _D, _D, _D, _D, _I32, _D, _D, _I64, _P, _P, _P]),
     "hm_build_batch": (_I32, [_I32, _P, _D, _P, _P, _P]),
+    "hm_build2": (_I32, [_P, _I64, _P, _P, _I64, _D, _D, _D, _D, _I32, _D, _D, _I64, _P, _P, _P]),
     "hm_batch_join": (_I32, [_I32, _P, _P, _P]),
     "hm_gmres_batch": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, _P, _P]),
     "hm_matvec": (_I32, [_P, _I32, _P, _P, _P]),
@@ -338,6 +339,33 @@ class HMatrix:
         if check and st != HM_ERR_NOCONV:
             _check(st, "hm_gmres")
         return x, it.value, rr.value, st
+
+    @classmethod
+    def build2(cls, targets, sources, normals=None, rho=1.0, lam=2.0, mu=1.0, omega=4.0,
+               kernel="U", eps=1e-4, eta=3.0, leaf_size=32, opts=None, stream=None):
+        """H-matrix between two clouds (hm_build2): rows at the targets, columns at
+        the sources (normals and opts weights at the sources)."""
+        X = np.ascontiguousarray(targets, dtype=np.float64)
+        Y = np.ascontiguousarray(sources, dtype=np.float64)
+        N = np.ascontiguousarray(normals, dtype=np.float64) if normals is not None else None
+        k = {"U": HM_KERNEL_U, "T": HM_KERNEL_T}[kernel] if isinstance(kernel, str) else kernel
+        h = C.c_void_p()
+        _check(lib().hm_build2(_np_ptr(X), X.shape[0], _np_ptr(Y), _np_ptr(N) if N is not None else None,
+                               Y.shape[0], rho, lam, mu, omega, k, eps, eta, leaf_size,
+                               C.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                               C.byref(h)), "hm_build2")
+        H = cls(h, X.shape[0] + Y.shape[0])
+        H.n_targets = X.shape[0]
+        return H
+
+    def matvec_sources(self, x, stream=None):
+        """A x for a two-cloud handle: x, cuda complex128 (3 n_y,) at the sources;
+        returns (3 n_x,) at the targets (the handle's vectors are (targets, sources))."""
+        import torch
+        nt = 3 * self.n_targets
+        xf = torch.zeros(3 * self.n_c, dtype=torch.complex128, device=x.device)
+        xf[nt:] = x
+        return self.matvec(xf, stream=stream)[:nt]
 
     @classmethod
     def join(cls, handles, stream=None):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "hm.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(hm_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(hm_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
