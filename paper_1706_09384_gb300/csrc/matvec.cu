@@ -248,34 +248,58 @@ __global__ void __launch_bounds__(MV_THREADS) mvdf_phase1(const WorkItem* items,
         xb[q] = r + 1 < it.rows ? xdf[it.dof + r + 1] : z;
     }
     const int npair = it.ld >> 1;
+    // conj(a) x for the lane's rows of one column, a = (a_re, a_im, b_re, b_im):
+    // re += a_re x_re + a_im x_im, im += a_re x_im - a_im x_re (two rows per float4)
+    auto col_dot = [&](const float4 (&v)[PAIRS_PER_LANE], float& rh, float& rl, float& ih, float& il) {
+#pragma unroll
+        for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+            if (lane + 32 * q < npair) {
+                df_add_prod(rh, rl, v[q].x, xa[q].x, xa[q].z);
+                df_add_prod(rh, rl, v[q].y, xa[q].y, xa[q].w);
+                df_add_prod(ih, il, v[q].x, xa[q].y, xa[q].w);
+                df_add_prod(ih, il, -v[q].y, xa[q].x, xa[q].z);
+                df_add_prod(rh, rl, v[q].z, xb[q].x, xb[q].z);
+                df_add_prod(rh, rl, v[q].w, xb[q].y, xb[q].w);
+                df_add_prod(ih, il, v[q].z, xb[q].y, xb[q].w);
+                df_add_prod(ih, il, -v[q].w, xb[q].x, xb[q].z);
+            }
+        }
+    };
+    auto load_col = [&](const float4* col, float4 (&v)[PAIRS_PER_LANE]) {
+#pragma unroll
+        for (int q = 0; q < PAIRS_PER_LANE; ++q)
+            v[q] = (lane + 32 * q < npair) ? ldg_stream(col + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto finish = [&](int64_t ti, float rh, float rl, float ih, float il) {
+        df_warp_sum(rh, rl);
+        df_warp_sum(ih, il);
+        if (lane == 0) {
+            atomicAdd(&t64[ti].x, (double)rh + (double)rl);
+            atomicAdd(&t64[ti].y, (double)ih + (double)il);
+        }
+    };
     for (int ci = it.first; ci < it.last; ++ci) {
         const DevChunk ch = sh_hdr[ci - it.first];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
-        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
-            const float4* col = base + (int64_t)c * (ch.ld >> 1);
+        const int64_t cs = ch.ld >> 1;
+        int c = warp;
+        // two columns per pass: both columns' loads are in flight before the sums
+        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
+            float4 v0[PAIRS_PER_LANE], v1[PAIRS_PER_LANE];
+            load_col(base + (int64_t)c * cs, v0);
+            load_col(base + (int64_t)(c + MV_WARPS) * cs, v1);
+            float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+            col_dot(v0, r0h, r0l, i0h, i0l);
+            col_dot(v1, r1h, r1l, i1h, i1l);
+            finish(ch.vec + c, r0h, r0l, i0h, i0l);
+            finish(ch.vec + c + MV_WARPS, r1h, r1l, i1h, i1l);
+        }
+        for (; c < ch.ncols; c += MV_WARPS) {
+            float4 v0[PAIRS_PER_LANE];
+            load_col(base + (int64_t)c * cs, v0);
             float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-#pragma unroll
-            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
-                const int pr = lane + 32 * q;
-                if (pr < npair) {
-                    const float4 v = ldg_stream(col + pr);  // (a_re, a_im, b_re, b_im)
-                    // conj(a) x: re += a_re x_re + a_im x_im, im += a_re x_im - a_im x_re
-                    df_add_prod(rh, rl, v.x, xa[q].x, xa[q].z);
-                    df_add_prod(rh, rl, v.y, xa[q].y, xa[q].w);
-                    df_add_prod(ih, il, v.x, xa[q].y, xa[q].w);
-                    df_add_prod(ih, il, -v.y, xa[q].x, xa[q].z);
-                    df_add_prod(rh, rl, v.z, xb[q].x, xb[q].z);
-                    df_add_prod(rh, rl, v.w, xb[q].y, xb[q].w);
-                    df_add_prod(ih, il, v.z, xb[q].y, xb[q].w);
-                    df_add_prod(ih, il, -v.w, xb[q].x, xb[q].z);
-                }
-            }
-            df_warp_sum(rh, rl);
-            df_warp_sum(ih, il);
-            if (lane == 0) {
-                atomicAdd(&t64[ch.vec + c].x, (double)rh + (double)rl);
-                atomicAdd(&t64[ch.vec + c].y, (double)ih + (double)il);
-            }
+            col_dot(v0, rh, rl, ih, il);
+            finish(ch.vec + c, rh, rl, ih, il);
         }
     }
 }
@@ -300,29 +324,48 @@ __global__ void __launch_bounds__(MV_THREADS) mvdf_phase2(const WorkItem* items,
         sa[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         sb[q] = sa[q];
     }
+    // rows += a w for the lane's rows of one column, a = (a_re, a_im, b_re, b_im):
+    // re += a_re w_re - a_im w_im, im += a_re w_im + a_im w_re (two rows per float4)
+    auto col_fma = [&](const float4 (&a)[PAIRS_PER_LANE], const float4& w) {
+#pragma unroll
+        for (int q = 0; q < PAIRS_PER_LANE; ++q) {
+            if (lane + 32 * q < npair) {
+                df_add_prod(sa[q].x, sa[q].y, a[q].x, w.x, w.z);
+                df_add_prod(sa[q].x, sa[q].y, -a[q].y, w.y, w.w);
+                df_add_prod(sa[q].z, sa[q].w, a[q].x, w.y, w.w);
+                df_add_prod(sa[q].z, sa[q].w, a[q].y, w.x, w.z);
+                df_add_prod(sb[q].x, sb[q].y, a[q].z, w.x, w.z);
+                df_add_prod(sb[q].x, sb[q].y, -a[q].w, w.y, w.w);
+                df_add_prod(sb[q].z, sb[q].w, a[q].z, w.y, w.w);
+                df_add_prod(sb[q].z, sb[q].w, a[q].w, w.x, w.z);
+            }
+        }
+    };
+    auto load_col = [&](const float4* col, float4 (&a)[PAIRS_PER_LANE]) {
+#pragma unroll
+        for (int q = 0; q < PAIRS_PER_LANE; ++q)
+            a[q] = (lane + 32 * q < npair) ? ldg_stream(col + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
     for (int ci = it.first; ci < it.last; ++ci) {
         const DevChunk ch = sh_hdr[ci - it.first];
         const float4* base = reinterpret_cast<const float4*>(arena + ch.data);
-        const float4* v = (ch.kind == 0 ? xdf : tdf) + ch.vec;
-        for (int c = warp; c < ch.ncols; c += MV_WARPS) {
-            const float4 w = __ldg(v + c);  // (re_h, im_h, re_l, im_l)
-            const float4* col = base + (int64_t)c * (ch.ld >> 1);
-#pragma unroll
-            for (int q = 0; q < PAIRS_PER_LANE; ++q) {
-                const int pr = lane + 32 * q;
-                if (pr < npair) {
-                    const float4 a = ldg_stream(col + pr);  // (a_re, a_im, b_re, b_im)
-                    // a w: re += a_re w_re - a_im w_im, im += a_re w_im + a_im w_re
-                    df_add_prod(sa[q].x, sa[q].y, a.x, w.x, w.z);
-                    df_add_prod(sa[q].x, sa[q].y, -a.y, w.y, w.w);
-                    df_add_prod(sa[q].z, sa[q].w, a.x, w.y, w.w);
-                    df_add_prod(sa[q].z, sa[q].w, a.y, w.x, w.z);
-                    df_add_prod(sb[q].x, sb[q].y, a.z, w.x, w.z);
-                    df_add_prod(sb[q].x, sb[q].y, -a.w, w.y, w.w);
-                    df_add_prod(sb[q].z, sb[q].w, a.z, w.y, w.w);
-                    df_add_prod(sb[q].z, sb[q].w, a.w, w.x, w.z);
-                }
-            }
+        const float4* v = (ch.kind == 0 ? xdf : tdf) + ch.vec;  // (re_h, im_h, re_l, im_l)
+        const int64_t cs = ch.ld >> 1;
+        int c = warp;
+        // two columns per pass: both columns' loads are in flight before the sums
+        for (; c + MV_WARPS < ch.ncols; c += 2 * MV_WARPS) {
+            const float4 w0 = __ldg(v + c), w1 = __ldg(v + c + MV_WARPS);
+            float4 a0[PAIRS_PER_LANE], a1[PAIRS_PER_LANE];
+            load_col(base + (int64_t)c * cs, a0);
+            load_col(base + (int64_t)(c + MV_WARPS) * cs, a1);
+            col_fma(a0, w0);
+            col_fma(a1, w1);
+        }
+        for (; c < ch.ncols; c += MV_WARPS) {
+            const float4 w0 = __ldg(v + c);
+            float4 a0[PAIRS_PER_LANE];
+            load_col(base + (int64_t)c * cs, a0);
+            col_fma(a0, w0);
         }
     }
 #pragma unroll
