@@ -214,13 +214,51 @@ __device__ __forceinline__ void df_merge(float& h, float& l, float h2, float l2)
     h = t;
     l = __fadd_rn(__fadd_rn(l, l2), err);
 }
-__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+// Sums of four pairs over the warp, reduce-scatter style: after the exchange
+// across lane bit 4 the lower half carries pairs 0, 1 and the upper half
+// pairs 2, 3; after bit 3 each group of eight lanes carries one pair, and the
+// last three exchanges complete it.  Lane group g = lane >> 3 ends with the
+// total of pair g, in every lane of the group.
+__device__ __forceinline__ void df_warp_sum4(float (&h)[4], float (&l)[4], int lane, float& oh,
+                                             float& ol) {
+    const bool up = lane & 16;
+    float kh0 = up ? h[2] : h[0], kl0 = up ? l[2] : l[0];
+    float kh1 = up ? h[3] : h[1], kl1 = up ? l[3] : l[1];
+    const float sh0 = up ? h[0] : h[2], sl0 = up ? l[0] : l[2];
+    const float sh1 = up ? h[1] : h[3], sl1 = up ? l[1] : l[3];
+    df_merge(kh0, kl0, __shfl_xor_sync(0xffffffffu, sh0, 16), __shfl_xor_sync(0xffffffffu, sl0, 16));
+    df_merge(kh1, kl1, __shfl_xor_sync(0xffffffffu, sh1, 16), __shfl_xor_sync(0xffffffffu, sl1, 16));
+    const bool up8 = lane & 8;
+    oh = up8 ? kh1 : kh0;
+    ol = up8 ? kl1 : kl0;
+    const float bh = up8 ? kh0 : kh1, bl = up8 ? kl0 : kl1;
+    df_merge(oh, ol, __shfl_xor_sync(0xffffffffu, bh, 8), __shfl_xor_sync(0xffffffffu, bl, 8));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
-        df_merge(h, l, h2, l2);  // symmetric: every lane ends with the same pair
-    }
+    for (int o = 4; o > 0; o >>= 1)
+        df_merge(oh, ol, __shfl_xor_sync(0xffffffffu, oh, o), __shfl_xor_sync(0xffffffffu, ol, o));
+}
+// The same for two pairs: lane group lane >> 4 ends with the total of pair g.
+__device__ __forceinline__ void df_warp_sum2(float h0, float l0, float h1, float l1, int lane,
+                                             float& oh, float& ol) {
+    const bool up = lane & 16;
+    oh = up ? h1 : h0;
+    ol = up ? l1 : l0;
+    const float sh = up ? h0 : h1, sl = up ? l0 : l1;
+    df_merge(oh, ol, __shfl_xor_sync(0xffffffffu, sh, 16), __shfl_xor_sync(0xffffffffu, sl, 16));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+        df_merge(oh, ol, __shfl_xor_sync(0xffffffffu, oh, o), __shfl_xor_sync(0xffffffffu, ol, o));
+}
+// FP32 -> FP64 by moving the fields (exact, like the conversion instruction),
+// on the integer pipes: GB300 issues FP32/FP64 conversions on its narrow FP64
+// unit.  Zero, subnormal, infinite and NaN inputs take the conversion.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t sgn = (uint64_t)(b >> 31) << 63;
+    if (e == 0u || e == 0xffu) return (b & 0x7fffffffu) ? (double)f : __longlong_as_double((long long)sgn);
+    return __longlong_as_double(
+        (long long)(sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
 }
 // complex128 -> (re_hi, im_hi, re_lo, im_lo)
 __device__ __forceinline__ float4 df_split(double2 v) {
@@ -270,12 +308,23 @@ __global__ void __launch_bounds__(MV_THREADS) mvdf_phase1(const WorkItem* items,
         for (int q = 0; q < PAIRS_PER_LANE; ++q)
             v[q] = (lane + 32 * q < npair) ? ldg_stream(col + lane + 32 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
-    auto finish = [&](int64_t ti, float rh, float rl, float ih, float il) {
-        df_warp_sum(rh, rl);
-        df_warp_sum(ih, il);
-        if (lane == 0) {
-            atomicAdd(&t64[ti].x, (double)rh + (double)rl);
-            atomicAdd(&t64[ti].y, (double)ih + (double)il);
+    // The totals go to t64 as two FP64 atomics per component (hi, then lo),
+    // from lanes that each convert one FP32 part on the integer pipes.
+    auto finish1 = [&](int64_t ti, float rh, float rl, float ih, float il) {
+        float oh, ol;
+        df_warp_sum2(rh, rl, ih, il, lane, oh, ol);
+        if ((lane & 14) == 0) {
+            double* dst = (lane & 16) ? &t64[ti].y : &t64[ti].x;
+            atomicAdd(dst, f32_to_f64_bits((lane & 1) ? ol : oh));
+        }
+    };
+    auto finish2 = [&](int64_t t0, int64_t t1, float (&h)[4], float (&l)[4]) {
+        float oh, ol;
+        df_warp_sum4(h, l, lane, oh, ol);
+        if ((lane & 6) == 0) {
+            double2* d = &t64[(lane & 16) ? t1 : t0];
+            double* dst = (lane & 8) ? &d->y : &d->x;
+            atomicAdd(dst, f32_to_f64_bits((lane & 1) ? ol : oh));
         }
     };
     for (int ci = it.first; ci < it.last; ++ci) {
@@ -288,18 +337,17 @@ __global__ void __launch_bounds__(MV_THREADS) mvdf_phase1(const WorkItem* items,
             float4 v0[PAIRS_PER_LANE], v1[PAIRS_PER_LANE];
             load_col(base + (int64_t)c * cs, v0);
             load_col(base + (int64_t)(c + MV_WARPS) * cs, v1);
-            float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
-            col_dot(v0, r0h, r0l, i0h, i0l);
-            col_dot(v1, r1h, r1l, i1h, i1l);
-            finish(ch.vec + c, r0h, r0l, i0h, i0l);
-            finish(ch.vec + c + MV_WARPS, r1h, r1l, i1h, i1l);
+            float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};  // re0, im0, re1, im1
+            col_dot(v0, h[0], l[0], h[1], l[1]);
+            col_dot(v1, h[2], l[2], h[3], l[3]);
+            finish2(ch.vec + c, ch.vec + c + MV_WARPS, h, l);
         }
         for (; c < ch.ncols; c += MV_WARPS) {
             float4 v0[PAIRS_PER_LANE];
             load_col(base + (int64_t)c * cs, v0);
             float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
             col_dot(v0, rh, rl, ih, il);
-            finish(ch.vec + c, rh, rl, ih, il);
+            finish1(ch.vec + c, rh, rl, ih, il);
         }
     }
 }
