@@ -69,6 +69,7 @@ struct Chunk {
     int32_t kind;      // 0 dense, 1 U, 2 V
     int64_t vec;       // dense: x offset (tree order DOF); U/V: t offset
     int64_t block;     // block index
+    int64_t sigma;     // column cluster of the block
     int64_t leaf_dof;  // first tree-order DOF of the chunk's segment
 };
 

@@ -856,14 +856,19 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
         l0 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].begin) - leaf_begin.begin();
         l1 = std::lower_bound(leaf_begin.begin(), leaf_begin.end(), cl[c].end) - leaf_begin.begin();
     };
-    // t offsets
+    // t offsets, grouped by column cluster: the t entries of all blocks that
+    // share sigma are one contiguous range, in block order
     t_off.assign(blk.size(), 0);
-    int64_t toff = 0;
+    std::vector<int64_t> by_sigma;
     for (size_t b = 0; b < blk.size(); ++b)
-        if (blk[b].admissible) {
-            t_off[b] = toff;
-            toff += blk[b].rank;
-        }
+        if (blk[b].admissible) by_sigma.push_back((int64_t)b);
+    std::stable_sort(by_sigma.begin(), by_sigma.end(),
+                     [&](int64_t a, int64_t b) { return blk[a].sigma < blk[b].sigma; });
+    int64_t toff = 0;
+    for (int64_t b : by_sigma) {
+        t_off[b] = toff;
+        toff += blk[b].rank;
+    }
     P.t_elems = toff;
     std::vector<std::vector<int32_t>> rows_of(nleaf), cols_of(nleaf);
     for (size_t b = 0; b < blk.size(); ++b) {
@@ -880,6 +885,7 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
                 c.rows = P.leaf_rows[l];
                 c.ld = (int32_t)hm_round_up(c.rows, 2);
                 c.block = (int64_t)b;
+                c.sigma = blk[b].sigma;
                 c.leaf_dof = P.leaf_dof_begin[l];
                 if (!blk[b].admissible) {
                     c.kind = 0;
@@ -904,6 +910,7 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
                 c.rows = P.leaf_rows[l];
                 c.ld = (int32_t)hm_round_up(c.rows, 2);
                 c.block = (int64_t)b;
+                c.sigma = blk[b].sigma;
                 c.leaf_dof = P.leaf_dof_begin[l];
                 c.kind = 2;
                 c.ncols = blk[b].rank;
@@ -928,8 +935,14 @@ MatvecPlan build_matvec_plan(const std::vector<hm_cluster>& cl, const std::vecto
         }
         P.row_leaf_begin.push_back((int64_t)P.row_items.size());
     }
+    // V chunks of a segment grouped by column cluster (block order inside a
+    // group): the columns of the blocks that share sigma are one contiguous
+    // run of every segment of sigma, in the same order, matching their t range
     P.col_leaf_begin.push_back(0);
     for (int64_t l = 0; l < nleaf; ++l) {
+        std::stable_sort(cols_of[l].begin(), cols_of[l].end(), [&](int32_t a, int32_t b) {
+            return P.chunks[a].sigma < P.chunks[b].sigma;
+        });
         for (int32_t id : cols_of[l]) {
             P.chunks[id].data = off;
             off += (int64_t)P.chunks[id].ld * P.chunks[id].ncols;
@@ -1108,12 +1121,14 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
     s16_attributes<4>();
     m->arena16_elems = off;
     m->nchunks = (int64_t)c16.size();
-    m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4, st, true);
+    // 256 bytes of slack: the block product's phase-2 view reads whole 128-byte
+    // m-blocks, up to 126 bytes past the last stored column
+    m->arena16 = (uint32_t*)hm_dmalloc(owner, std::max<int64_t>(off, 4) * 4 + 256, st, true);
     {  // TMA descriptors of the block product: [phase][ld16 / 4]
         std::vector<int32_t> lds;
         for (const WorkItem& w : m->h_items1) lds.push_back(c16[m->h_order1[w.first]].ld);
         for (const WorkItem& w : m->h_items2) lds.push_back(c16[m->h_order2[w.first]].ld);
-        m->tmaps = hm_dmalloc(owner, 2 * TMAP_PER_PHASE * 128, st, true);
+        m->tmaps = hm_dmalloc(owner, TMAP_SETS * TMAP_PER_PHASE * 128, st, true);
         make_block_tmaps(m->tmaps, m->arena16, off, lds, st);
     }
     m->chunks16 = (DevChunk16*)hm_dmalloc(owner, std::max<size_t>(c16.size(), 1) * sizeof(DevChunk16),
@@ -1150,7 +1165,7 @@ void matvec_make_bf16(MatvecDev* m, const MatvecPlan& plan, std::vector<DevBuf>&
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
-    make_block_items(m, c16, owner, st);
+    make_block_items(m, plan, c16, owner, st);
     HM_CUDA(cudaStreamSynchronize(st));
     m->storage = HM_STORE_BF16;
 }

@@ -50,6 +50,26 @@ struct TcItem {
     int32_t rows;   // 3 |segment|
 };
 
+// Phase-1 work item of the tensor-core block product: columns [c0, c0 + ncol)
+// of one column-cluster group (the V columns of every block that shares the
+// column cluster sigma, t rows t0 - c0 ...) over the segments [seg0, seg1) of
+// sigma (all of them unless the group is cut along K; red then says that
+// other items add into the same t rows).
+struct TcGroup {
+    int64_t t0;     // t row of column c0
+    int32_t ncol;   // <= 512 (four 128-column M tiles)
+    int32_t seg0;   // entries [seg0, seg1) of the segment table
+    int32_t seg1;
+    int32_t red;    // 1: add into T (zeroed before), 0: store
+};
+// One segment of a phase-1 item: row of the item's first column in the
+// segment's ld16 view of the BF16 arena, its ld16, and its first DOF.
+struct TcSeg {
+    int64_t dof;
+    int32_t row0;
+    int32_t ld16;
+};
+
 struct MatvecDev {
     int storage = 0;
     int s16_nstage = 3;                 // stages of the streamed BF16 kernels (2, 3 or 4; the
@@ -109,23 +129,29 @@ struct MatvecDev {
     float2* tm = nullptr;
     uint32_t* t16 = nullptr;
     // TMA descriptors (CUtensorMap, 128 bytes each): the BF16 arena viewed as
-    // rows of 2 ld16 bf16, [phase 1 | phase 2][ld16 / 4]; and XB
+    // rows of 2 ld16 bf16, [set][ld16 / 4] (TMAP_SETS sets); and XB
     void* tmaps = nullptr;
     void* tmap_xb = nullptr;
-    // tensor-core items and per-column tables: phase 1 (t index, s_V s_U),
-    // phase 2 (T16 row | 1 << 31 for U columns, XB row 2 dof for dense ones)
-    TcItem* titems1 = nullptr;
+    // tensor-core items and tables: phase 1 groups, their segments and the
+    // scale s_V s_U of every t row; phase 2 items and per-column codes
+    // (T16 row | 1 << 31 for U columns, XB row 2 dof for dense ones)
+    TcGroup* tgroups1 = nullptr;
+    int64_t ngroups1 = 0;
+    TcSeg* tsegs1 = nullptr;
+    float* tscale1 = nullptr;
     TcItem* titems2 = nullptr;
-    float2* colinfo1 = nullptr;
     uint32_t* colcode2 = nullptr;
 };
 constexpr int TMAP_PER_PHASE = MAX_LD / 4 + 1;
+// descriptor sets: phase 1 with boxes of 128, 64, 32 and 16 rows, then phase 2
+constexpr int TMAP_PHASE2 = 4;
+constexpr int TMAP_SETS = 5;
 // Items and per-column tables of the tensor-core block product (after the
 // BF16 chunks, headers and scales exist on the device); c16 as uploaded.
-void make_block_items(MatvecDev* m, const std::vector<DevChunk16>& c16, std::vector<DevBuf>& owner,
-                      cudaStream_t st);
+void make_block_items(MatvecDev* m, const MatvecPlan& plan, const std::vector<DevChunk16>& c16,
+                      std::vector<DevBuf>& owner, cudaStream_t st);
 // Encodes the descriptors for the leading dimensions in lds (device copy at
-// d_maps, 2 * TMAP_PER_PHASE entries); defined with the block product.
+// d_maps, TMAP_SETS * TMAP_PER_PHASE entries); defined with the block product.
 void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,
                       const std::vector<int32_t>& lds, cudaStream_t st);
 

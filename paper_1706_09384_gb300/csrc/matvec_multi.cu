@@ -50,11 +50,14 @@ constexpr int MV_ERR_TIMEOUT = 1;
 constexpr int TC_KBMAX = 2 * MAX_LD / 64;             // 64-wide K boxes of a column (6)
 // phase 1: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int P1_THREADS = 192;
-constexpr int P1_NS = 5;                              // A stages
-constexpr int P1_NACC = 4;                            // TMEM accumulators (128 x 64 each)
+constexpr int P1_NS = 8;                              // A stages
+constexpr int P1_BOX = 16;                            // row granularity of the A boxes
+constexpr int P1_NZ = 4;                              // A box heights 128, 64, 32, 16 (map sets)
+constexpr bool P1_SPLIT_TAIL = true;                  // last tile of an item: boxes cover its rows
+constexpr int P1_MT = 4;                              // M tiles of an item (512 columns)
 constexpr int P1_ABYTES = 128 * 128;                  // 128 columns x 64 bf16 of K
 constexpr int P1_BBYTES = 64 * 128;                   // 64 K rows of XB
-constexpr uint32_t P1_TMEM_COLS = 256;
+constexpr uint32_t P1_TMEM_COLS = 512;                // two sets of four 128 x 64 accumulators
 // phase 2: warp 0 TMA, warp 1 MMA, warps 2-3 weight rows, warps 4-7 epilogue
 constexpr int P2_THREADS = 256;
 constexpr int P2_NS = 6;
@@ -71,15 +74,15 @@ constexpr uint32_t TC_B_MN = 1u << 16;
 
 struct P1Smem {
     unsigned char a[P1_NS][P1_ABYTES];         // 1024-byte aligned (swizzle atoms)
-    unsigned char b[2][TC_KBMAX][P1_BBYTES];   // XB rows of two items
+    unsigned char b[2][TC_KBMAX][P1_BBYTES];   // XB rows of two segments (all K boxes)
     int32_t abort;
     uint32_t tmem;
     alignas(8) uint64_t full[P1_NS];
     uint64_t empty[P1_NS];
     uint64_t bfull[2];
     uint64_t bempty[2];
-    uint64_t accf[P1_NACC];
-    uint64_t acce[P1_NACC];
+    uint64_t accf[2];
+    uint64_t acce[2];
 };
 struct P2Smem {
     unsigned char a[P2_NS][P2_ABYTES];
@@ -97,7 +100,9 @@ struct P2Smem {
 // 227 KB including the 1 KB alignment slack
 static_assert(sizeof(P1Smem) + 1024 <= 227 * 1024, "phase 1 shared memory");
 static_assert(sizeof(P2Smem) + 1024 <= 227 * 1024, "phase 2 shared memory");
+static_assert(P1_NZ == TMAP_PHASE2 && (128 >> (P1_NZ - 1)) == P1_BOX, "phase-1 map sets");
 static_assert(P1_ABYTES % 1024 == 0 && P1_BBYTES % 1024 == 0 && P2_ABYTES % 1024 == 0 &&
+                  (P1_BOX * 128) % 1024 == 0 && 128 % P1_BOX == 0 &&
                   P2_WBYTES % 1024 == 0,
               "swizzle atoms stay aligned");
 
@@ -133,6 +138,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
         " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
         "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {
@@ -183,11 +196,12 @@ __device__ __forceinline__ Smem& tc_smem(unsigned char* raw) {
 
 // The items of this CTA (blockIdx.x, + gridDim.x, ...), the record of the
 // next one fetched an item ahead.
+template <typename Item>
 struct ItemIter {
-    const TcItem* items;
+    const Item* items;
     int nitems, item;
-    TcItem cur, nxt;
-    __device__ ItemIter(const TcItem* it, int n) : items(it), nitems(n), item(blockIdx.x) {
+    Item cur, nxt;
+    __device__ ItemIter(const Item* it, int n) : items(it), nitems(n), item(blockIdx.x) {
         if (item < n) cur = it[item];
         if (item + (int)gridDim.x < n) nxt = it[item + gridDim.x];
     }
@@ -244,13 +258,21 @@ __device__ __forceinline__ bool tc_aborted(Smem& S) {
     return *(volatile int32_t*)&S.abort != 0;
 }
 
-// Phase 1 (persistent, items blockIdx.x, + gridDim.x, ...): T[t_j] += s_V s_U D[j]
-// for the V columns j of each item (the V chunks of one column leaf).  Stages
-// run over (item, 128-column M tile, 64-wide K box) without breaks between
-// items; each item's XB rows (the B operand, all K boxes) go to one of two
-// buffers; four TMEM accumulators let the epilogue trail the MMAs.
-__global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items, int nitems,
-                                                           const float2* __restrict__ colinfo,
+// Phase 1 (persistent, items blockIdx.x, + gridDim.x, ...): T[t0 + j] =
+// s_V s_U D[j] for the columns j of one column-cluster group: the V columns of
+// every block that shares the column cluster sigma are one run of rows of
+// each segment of sigma, in the same order, so one set of TMEM accumulators
+// (up to four 128 x 64 M tiles) sums over all segments of sigma (K) and the
+// t rows are written once.  Stages run over (item, segment, M tile, 64-wide K
+// box), so the K boxes of a stored column are read back to back; the XB rows
+// of a segment (the B operand, all its K boxes) go to one of two buffers; an
+// A tile is one 128-row TMA box, or for the last tile of an item boxes of 64,
+// 32 and 16 rows that cover its columns rounded up to 16.  Two
+// accumulator sets let the epilogue of an item trail the MMAs of the next.
+// Items of a group cut along K add into zeroed t rows.
+__global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcGroup* items, int nitems,
+                                                           const TcSeg* __restrict__ segs,
+                                                           const float* __restrict__ tscale,
                                                            const CUtensorMap* maps,
                                                            const CUtensorMap* map_xb, float2* T,
                                                            int* err) {
@@ -265,8 +287,6 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items,
         for (int q = 0; q < 2; ++q) {
             mbar_init(&S.bfull[q], 1);
             mbar_init(&S.bempty[q], 1);
-        }
-        for (int q = 0; q < P1_NACC; ++q) {
             mbar_init(&S.accf[q], 1);
             mbar_init(&S.acce[q], 4);
         }
@@ -278,33 +298,63 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items,
         if (lane == 0) {
             tmap_acquire(map_xb);
             const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
-            int g = 0, ii = 0;  // stages and items issued
-            uint64_t acquired = 0;
-            for (ItemIter X(items, nitems); X.valid() && !tc_aborted(S); X.advance(), ++ii) {
-                const TcItem I = X.cur;
-                const CUtensorMap* map = maps + (I.ld16 >> 2);
-                if (!((acquired >> (I.ld16 >> 2)) & 1)) {  // each descriptor once
-                    tmap_acquire(map);
-                    acquired |= 1ull << (I.ld16 >> 2);
-                }
-                const int nmt = (I.ncol + 127) >> 7, nkb = (2 * I.ld16 + 63) >> 6;
-                const int bs = ii & 1;
-                if (ii >= 2 && !tc_wait(S, &S.bempty[bs], ((ii >> 1) - 1) & 1, err)) break;
-                // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
-                mbar_arrive_expect_tx(&S.bfull[bs], (uint32_t)nkb * P1_BBYTES);
-                for (int kb = 0; kb < nkb; ++kb)
-                    tma_load_2d(S.b[bs][kb], map_xb, 0, (int)(2 * I.dof) + 64 * kb, &S.bfull[bs], pol_keep);
-                for (int mt = 0; mt < nmt; ++mt)
-                    for (int kb = 0; kb < nkb; ++kb, ++g) {
-                        const int q = g % P1_NS;
-                        if (g >= P1_NS && !tc_wait(S, &S.empty[q], ((g / P1_NS) - 1) & 1, err)) break;
-                        mbar_arrive_expect_tx(&S.full[q], P1_ABYTES);
-                        tma_load_2d(S.a[q], map, kb * 64, I.row0 + mt * 128, &S.full[q], pol_stream);
+            int g = 0, gs = 0;  // A stages and segments issued
+            uint64_t acquired[P1_NZ] = {0, 0, 0, 0};
+            bool ok = true;
+            for (ItemIter<TcGroup> X(items, nitems); ok && X.valid() && !tc_aborted(S); X.advance()) {
+                const TcGroup I = X.cur;
+                const int nmt = (I.ncol + 127) >> 7;
+                TcSeg nx = segs[I.seg0];
+                for (int s = I.seg0; ok && s < I.seg1; ++s) {
+                    const TcSeg sg = nx;
+                    if (s + 1 < I.seg1) nx = segs[s + 1];  // read one segment ahead
+                    const int li = sg.ld16 >> 2;
+                    const int nkb = (2 * sg.ld16 + 63) >> 6, bs = gs & 1;
+                    if (gs >= 2 && !tc_wait(S, &S.bempty[bs], ((gs >> 1) - 1) & 1, err)) break;
+                    // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
+                    mbar_arrive_expect_tx(&S.bfull[bs], (uint32_t)nkb * P1_BBYTES);
+                    for (int kb = 0; kb < nkb; ++kb)
+                        tma_load_2d(S.b[bs][kb], map_xb, 0, (int)(2 * sg.dof) + 64 * kb, &S.bfull[bs], pol_keep);
+                    ++gs;
+                    for (int mt = 0; ok && mt < nmt; ++mt) {
+                        // the tile's rows rounded up to 16: one 128-row box, or
+                        // boxes of 64, 32 and 16 rows after one another (the
+                        // bits of the count), so a tile takes at most three copies
+                        const int rr = P1_SPLIT_TAIL ? (min(128, I.ncol - 128 * mt) + P1_BOX - 1) / P1_BOX * P1_BOX
+                                                     : 128;
+                        for (int z = 0; z < P1_NZ; ++z)
+                            if ((rr == 128) == (z == 0) && (z == 0 || (rr & (128 >> z))) &&
+                                !((acquired[z] >> li) & 1)) {  // each descriptor once
+                                tmap_acquire(maps + z * TMAP_PER_PHASE + li);
+                                acquired[z] |= 1ull << li;
+                            }
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            const int q = g % P1_NS;
+                            if (g >= P1_NS && !tc_wait(S, &S.empty[q], ((g / P1_NS) - 1) & 1, err)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&S.full[q], (uint32_t)(rr * 128));
+                            const int y = sg.row0 + 128 * mt;
+                            if (rr == 128) {
+                                tma_load_2d(S.a[q], maps + li, kb * 64, y, &S.full[q], pol_stream);
+                            } else {
+                                int off = 0;
+                                for (int z = 1; z < P1_NZ; ++z)
+                                    if (rr & (128 >> z)) {
+                                        tma_load_2d(S.a[q] + off * 128, maps + z * TMAP_PER_PHASE + li, kb * 64,
+                                                    y + off, &S.full[q], pol_stream);
+                                        off += 128 >> z;
+                                    }
+                            }
+                            ++g;
+                        }
                     }
+                }
             }
             // own copies land before the block can retire (an abort may leave
             // the count one short of a stage: waiting on it only times out)
-            for (int k = max(0, ii - 2); k < ii; ++k)
+            for (int k = max(0, gs - 2); k < gs; ++k)
                 if (!mbar_wait(&S.bfull[k & 1], (k >> 1) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
             for (int k = max(0, g - P1_NS); k < g; ++k)
                 if (!mbar_wait(&S.full[k % P1_NS], (k / P1_NS) & 1)) atomicExch(err, MV_ERR_TIMEOUT);
@@ -312,38 +362,46 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items,
         __syncwarp();
     } else if (warp == 1) {  // ---- MMA issue ----
         if (lane == 0) {
-            int g = 0, gt = 0, ii = 0;  // stages, M tiles, items
+            int g = 0, gs = 0, ii = 0;  // A stages, segments, items
             bool ok = true;
-            for (ItemIter X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
-                const TcItem I = X.cur;
-                const int nmt = (I.ncol + 127) >> 7, nkb = (2 * I.ld16 + 63) >> 6;
-                const int bs = ii & 1;
-                if (!tc_wait(S, &S.bfull[bs], (ii >> 1) & 1, err)) break;
-                for (int mt = 0; ok && mt < nmt; ++mt, ++gt) {
-                    const int acc = gt % P1_NACC;
-                    if (gt >= P1_NACC && !tc_wait(S, &S.acce[acc], ((gt / P1_NACC) - 1) & 1, err)) {
+            for (ItemIter<TcGroup> X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
+                const TcGroup I = X.cur;
+                const int nmt = (I.ncol + 127) >> 7, set = ii & 1;
+                if (ii >= 2 && !tc_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
+                tc_fence_after();
+                const uint32_t dacc = tmem + (uint32_t)(set * 256);
+                int nkb_next = (2 * segs[I.seg0].ld16 + 63) >> 6;
+                for (int s = I.seg0; ok && s < I.seg1; ++s) {
+                    const int nkb = nkb_next, bs = gs & 1;
+                    if (s + 1 < I.seg1) nkb_next = (2 * segs[s + 1].ld16 + 63) >> 6;
+                    if (!tc_wait(S, &S.bfull[bs], (gs >> 1) & 1, err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    for (int kb = 0; kb < nkb; ++kb, ++g) {
-                        const int q = g % P1_NS;
-                        if (!tc_wait(S, &S.full[q], (g / P1_NS) & 1, err)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[bs][kb]);
+                    for (int mt = 0; ok && mt < nmt; ++mt) {
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            const int q = g % P1_NS;
+                            if (!tc_wait(S, &S.full[q], (g / P1_NS) & 1, err)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[bs][kb]);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
-                            umma(tmem + (uint32_t)(acc * 64), desc_sw128(sa + kk * 32, 16, 1024),
-                                 desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
-                                 (kb > 0 || kk > 0) ? 1u : 0u);
-                        umma_commit(&S.empty[q]);
+                            for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
+                                umma(dacc + (uint32_t)(mt * 64), desc_sw128(sa + kk * 32, 16, 1024),
+                                     desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
+                                     (s > I.seg0 || kb > 0 || kk > 0) ? 1u : 0u);
+                            umma_commit(&S.empty[q]);
+                            ++g;
+                        }
                     }
-                    if (ok) umma_commit(&S.accf[acc]);
+                    if (!ok) break;
+                    umma_commit(&S.bempty[bs]);
+                    ++gs;
                 }
-                if (ok) umma_commit(&S.bempty[bs]);
+                if (ok) umma_commit(&S.accf[set]);
             }
             if (g > 0) {  // the MMAs finish before shared memory and TMEM go
                 const int k = g - 1;
@@ -353,32 +411,46 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcItem* items,
         __syncwarp();
     } else {  // ---- accumulators into T ----
         const int lq = warp & 3;  // TMEM lane quarter this warp may read
-        int gt = 0;
-        bool ok = true;
-        for (ItemIter X(items, nitems); ok && X.valid(); X.advance()) {
-            const TcItem I = X.cur;
-            const int nmt = (I.ncol + 127) >> 7;
-            for (int mt = 0; mt < nmt; ++mt, ++gt) {
-                const int acc = gt % P1_NACC;
-                const int j = mt * 128 + lq * 32 + lane;
-                const float2 ci = j < I.ncol ? __ldg(colinfo + I.col0 + j) : make_float2(0.f, 0.f);
-                ok = __all_sync(0xffffffffu, tc_wait(S, &S.accf[acc], (gt / P1_NACC) & 1, err));
-                if (!ok) break;
-                tc_fence_after();
-                uint32_t v[64];
-                tmem_ld64(tmem, lq, acc * 64, v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.acce[acc]);
-                if (j < I.ncol) {
-                    float* dst = reinterpret_cast<float*>(T + (int64_t)__float_as_int(ci.x) * NR);
+        int ii = 0;
+        for (ItemIter<TcGroup> X(items, nitems); X.valid(); X.advance(), ++ii) {
+            const TcGroup I = X.cur;
+            const int nmt = (I.ncol + 127) >> 7, set = ii & 1;
+            float sc[P1_MT];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        red_add_v4(dst + 4 * q, ci.y * __uint_as_float(v[4 * q]),
-                                   ci.y * __uint_as_float(v[4 * q + 1]), ci.y * __uint_as_float(v[4 * q + 2]),
-                                   ci.y * __uint_as_float(v[4 * q + 3]));
+            for (int mt = 0; mt < P1_MT; ++mt) {
+                const int j = 128 * mt + 32 * lq + lane;
+                sc[mt] = j < I.ncol ? __ldg(tscale + I.t0 + j) : 0.f;
+            }
+            if (!__all_sync(0xffffffffu, tc_wait(S, &S.accf[set], (ii >> 1) & 1, err))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int mt = 0; mt < P1_MT; ++mt) {
+                if (mt < nmt) {
+                    uint32_t v[64];
+                    tmem_ld64(tmem, lq, set * 256 + mt * 64, v);
+                    const int j = 128 * mt + 32 * lq + lane;
+                    if (j < I.ncol) {
+                        float* dst = reinterpret_cast<float*>(T + (I.t0 + j) * NR);
+                        const float c = sc[mt];
+                        if (I.red) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                red_add_v4(dst + 4 * q, c * __uint_as_float(v[4 * q]),
+                                           c * __uint_as_float(v[4 * q + 1]), c * __uint_as_float(v[4 * q + 2]),
+                                           c * __uint_as_float(v[4 * q + 3]));
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                reinterpret_cast<float4*>(dst)[q] =
+                                    make_float4(c * __uint_as_float(v[4 * q]), c * __uint_as_float(v[4 * q + 1]),
+                                                c * __uint_as_float(v[4 * q + 2]), c * __uint_as_float(v[4 * q + 3]));
+                        }
+                    }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.acce[set]);
         }
     }
     tc_teardown(S, P1_TMEM_COLS);
@@ -417,21 +489,21 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
             const uint64_t pol = l2_policy_evict_first();
             int g = 0;
             uint64_t acquired = 0;
-            for (ItemIter X(items, nitems); X.valid() && !tc_aborted(S); X.advance()) {
+            for (ItemIter<TcItem> X(items, nitems); X.valid() && !tc_aborted(S); X.advance()) {
                 const TcItem I = X.cur;
                 const CUtensorMap* map = maps + (I.ld16 >> 2);
                 if (!((acquired >> (I.ld16 >> 2)) & 1)) {  // each descriptor once
                     tmap_acquire(map);
                     acquired |= 1ull << (I.ld16 >> 2);
                 }
-                const int nbox = (2 * I.ld16 + 63) >> 6;  // 64-row boxes along m = 2r + re/im
+                const int nbox = (2 * I.ld16 + 63) >> 6;  // 64-row m-blocks along m = 2r + re/im
                 const int nst = (I.ncol + 31) >> 5;
                 for (int k = 0; k < nst; ++k, ++g) {
                     const int q = g % P2_NS;
                     if (g >= P2_NS && !tc_wait(S, &S.empty[q], ((g / P2_NS) - 1) & 1, err)) break;
+                    // one copy: 32 stored columns x all m-blocks, m-block b at 4096 b
                     mbar_arrive_expect_tx(&S.full[q], (uint32_t)nbox * 4096u);
-                    for (int b = 0; b < nbox; ++b)
-                        tma_load_2d(S.a[q] + b * 4096, map, b * 64, I.row0 + k * 32, &S.full[q], pol);
+                    tma_load_3d(S.a[q], map, 0, I.row0 + k * 32, 0, &S.full[q], pol);
                 }
             }
             for (int k = max(0, g - P2_NS); k < g; ++k)
@@ -442,7 +514,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
         if (lane == 0) {
             int g = 0, ii = 0;
             bool ok = true;
-            for (ItemIter X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
+            for (ItemIter<TcItem> X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
                 const TcItem I = X.cur;
                 const int nmt = (((2 * I.ld16 + 63) >> 6) + 1) >> 1;  // 128-row M tiles
                 const int nst = (I.ncol + 31) >> 5;
@@ -494,7 +566,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
             }
         };
         int g = 0, ii = 0;
-        ItemIter X(items, nitems);
+        ItemIter<TcItem> X(items, nitems);
         fetch(X.cur, X.valid());
         for (; X.valid(); X.advance(), ++ii) {
             const TcItem I = X.cur;
@@ -533,7 +605,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
         const int lq = warp & 3;
         const bool odd = lane & 1;
         int ii = 0;
-        for (ItemIter X(items, nitems); X.valid(); X.advance(), ++ii) {
+        for (ItemIter<TcItem> X(items, nitems); X.valid(); X.advance(), ++ii) {
             const TcItem I = X.cur;
             const int nmt = (((2 * I.ld16 + 63) >> 6) + 1) >> 1;
             const int set = ii & 1;
@@ -577,15 +649,13 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
     tc_teardown(S, P2_TMEM_COLS);
 }
 
-// Per-column table of phase 1 from the uploaded headers (scales are final):
-// entry colpos[q] + c of chunk q = (t index, s_V s_U).
-__global__ void colinfo1_kernel(const DevChunk16* hdr, const int64_t* colpos, int64_t nchunk,
-                                float2* colinfo) {
+// Scale of every t row (s_V s_U of its block) from the uploaded V chunk
+// headers; the chunks of a block in different segments write the same value.
+__global__ void tscale_kernel(const DevChunk16* hdr, int64_t nchunk, float* tscale) {
     const int64_t q = blockIdx.x;
     if (q >= nchunk) return;
     const DevChunk16 ch = hdr[q];
-    for (int c = threadIdx.x; c < ch.ncols; c += blockDim.x)
-        colinfo[colpos[q] + c] = make_float2(__int_as_float((int)(ch.vec + c)), ch.scale * ch.fold);
+    for (int c = threadIdx.x; c < ch.ncols; c += blockDim.x) tscale[ch.vec + c] = ch.scale * ch.fold;
 }
 
 // XB rows 2q and 2q + 1 of tree-order DOF q: (x_r, x_i) and (x_i, -x_r) of each
@@ -632,9 +702,7 @@ typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 2-D BF16 view (inner extent, rows, row pitch in bytes) with 128-byte swizzle.
-void encode_tmap(CUtensorMap* out, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch,
-                 uint32_t box_inner, uint32_t box_rows) {
+TmapEncodeFn tmap_encoder() {
     static TmapEncodeFn enc = nullptr;
     if (!enc) {
         cudaDriverEntryPointQueryResult q;
@@ -645,6 +713,13 @@ void encode_tmap(CUtensorMap* out, const void* base, uint64_t inner, uint64_t ro
             hm_throw(HM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
         enc = (TmapEncodeFn)fn;
     }
+    return enc;
+}
+
+// 2-D BF16 view (inner extent, rows, row pitch in bytes) with 128-byte swizzle.
+void encode_tmap(CUtensorMap* out, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch,
+                 uint32_t box_inner, uint32_t box_rows) {
+    TmapEncodeFn enc = tmap_encoder();
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
     const cuuint32_t box[2] = {box_inner, box_rows};
@@ -655,20 +730,43 @@ void encode_tmap(CUtensorMap* out, const void* base, uint64_t inner, uint64_t ro
     if (r != CUDA_SUCCESS) hm_throw(HM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
 
+// The phase-2 view of the BF16 arena with leading dimension ld (complex
+// entries): element (i, c, b) = bf16 64 b + i of stored column c, i.e. the
+// column's 128-byte m-blocks as the outer dimension (stride 128 bytes) and the
+// columns in between (stride 4 ld bytes), so that one box of 64 x 32 x nmb
+// lands in shared memory as nmb blocks of 32 columns x 128 bytes (the
+// MN-major operand layout).  The last m-block of a column whose 2 ld is not a
+// multiple of 64 runs into the next column: those rows m >= 2 ld of A only
+// reach accumulator rows that are never read.  The arena carries 256 bytes of
+// slack so the last column's block stays inside the allocation.
+void encode_tmap_mblocks(CUtensorMap* out, const void* base, uint64_t ld, uint64_t cols) {
+    TmapEncodeFn enc = tmap_encoder();
+    const uint64_t nmb = (2 * ld + 63) / 64;
+    const cuuint64_t dims[3] = {64, (cuuint64_t)cols, (cuuint64_t)nmb};
+    const cuuint64_t strides[2] = {(cuuint64_t)(4 * ld), 128};
+    const cuuint32_t box[3] = {64, 32, (cuuint32_t)nmb};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) hm_throw(HM_ERR_CUDA, "cuTensorMapEncodeTiled failed (phase-2 view)");
+}
+
 }  // namespace
 
 void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,
                       const std::vector<int32_t>& lds, cudaStream_t st) {
-    std::vector<CUtensorMap> maps(2 * TMAP_PER_PHASE);
+    std::vector<CUtensorMap> maps(TMAP_SETS * TMAP_PER_PHASE);
     std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     std::vector<char> done(TMAP_PER_PHASE, 0);
     for (const int32_t ld : lds) {
         if (ld % 4 || ld < 32 || ld > MAX_LD) hm_throw(HM_ERR_UNSUPPORTED, "BF16 leading dimension");
         if (done[ld / 4]) continue;
         done[ld / 4] = 1;
-        // phase 1: 64 K x 128 columns; phase 2: 64 m x 32 columns
-        encode_tmap(&maps[ld / 4], arena16, 2 * ld, words / ld, 4 * ld, 64, 128);
-        encode_tmap(&maps[TMAP_PER_PHASE + ld / 4], arena16, 2 * ld, words / ld, 4 * ld, 64, 32);
+        // phase 1: 64 K x 128, 64, 32 or 16 columns; phase 2: 64 m x 32 columns x all m-blocks
+        for (int z = 0; z < P1_NZ; ++z)
+            encode_tmap(&maps[z * TMAP_PER_PHASE + ld / 4], arena16, 2 * ld, words / ld, 4 * ld, 64, 128 >> z);
+        encode_tmap_mblocks(&maps[TMAP_PHASE2 * TMAP_PER_PHASE + ld / 4], arena16, ld, words / ld);
     }
     HM_CUDA(cudaMemcpyAsync(d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                             cudaMemcpyHostToDevice, st));
@@ -683,68 +781,150 @@ int64_t matvec_multi_alg_bytes(const MatvecDev* m, int64_t ndof) {
            (int64_t)NR * 8 * (2 * ndof + 2 * m->t_elems);
 }
 
-void make_block_items(MatvecDev* m, const std::vector<DevChunk16>& c16, std::vector<DevBuf>& owner,
-                      cudaStream_t st) {
-    auto build = [&](const std::vector<WorkItem>& its, const std::vector<int32_t>& order,
-                     std::vector<TcItem>& out, std::vector<int64_t>& colpos, std::vector<uint32_t>* codes) {
-        colpos.assign(order.size(), 0);
-        int64_t col = 0;
-        for (const WorkItem& w : its) {
-            const DevChunk16& a = c16[order[w.first]];
-            TcItem t;
-            t.dof = w.dof;
-            t.col0 = col;
-            t.row0 = (int32_t)(a.data / a.ld);
-            t.ld16 = a.ld;
-            t.rows = w.rows;
-            for (int32_t q = w.first; q < w.last; ++q) {
-                const DevChunk16& c = c16[order[q]];
-                colpos[q] = col;
-                if (codes)
-                    for (int32_t j = 0; j < c.ncols; ++j)
-                        codes->push_back(c.kind != 0 ? ((uint32_t)(c.vec + j) | 0x80000000u)
-                                                     : (uint32_t)(2 * (c.vec + j)));
-                col += c.ncols;
-            }
-            t.ncol = (int32_t)(col - t.col0);
-            out.push_back(t);
-        }
-        return col;
-    };
-    std::vector<TcItem> t1, t2;
-    std::vector<int64_t> pos1, pos2;
-    std::vector<uint32_t> codes;
-    const int64_t ncol1 = build(m->h_items1, m->h_order1, t1, pos1, nullptr);
-    build(m->h_items2, m->h_order2, t2, pos2, &codes);
-    m->titems1 = (TcItem*)hm_dmalloc(owner, std::max<size_t>(t1.size(), 1) * sizeof(TcItem), st, false);
-    m->titems2 = (TcItem*)hm_dmalloc(owner, std::max<size_t>(t2.size(), 1) * sizeof(TcItem), st, false);
-    m->colinfo1 = (float2*)hm_dmalloc(owner, std::max<int64_t>(ncol1, 1) * sizeof(float2), st, false);
-    m->colcode2 = (uint32_t*)hm_dmalloc(owner, std::max<size_t>(codes.size(), 1) * 4, st, false);
-    HM_CUDA(cudaMemcpyAsync(m->titems1, t1.data(), t1.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
-    HM_CUDA(cudaMemcpyAsync(m->titems2, t2.data(), t2.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
-    HM_CUDA(cudaMemcpyAsync(m->colcode2, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st));
-    if (!pos1.empty()) {
-        int64_t* d_pos = nullptr;
-        HM_CUDA(cudaMallocAsync((void**)&d_pos, pos1.size() * 8, st));
-        HM_CUDA(cudaMemcpyAsync(d_pos, pos1.data(), pos1.size() * 8, cudaMemcpyHostToDevice, st));
-        colinfo1_kernel<<<(unsigned)pos1.size(), 128, 0, st>>>(m->hdr16_1, d_pos, (int64_t)pos1.size(),
-                                                               m->colinfo1);
-        HM_CUDA(cudaGetLastError());
-        HM_LAUNCHED();
-        HM_CUDA(cudaFreeAsync(d_pos, st));
-    }
-    HM_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
-}
-
-static int multi_grid(int64_t nitems) {
+static int device_sms() {
     static int nsm = 0;
     if (!nsm) {
         int dev = 0;
         HM_CUDA(cudaGetDevice(&dev));
         HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     }
-    return (int)std::min<int64_t>(nitems, nsm);
+    return nsm;
 }
+
+// Phase-1 groups: per segment, the runs of V chunks that share a column
+// cluster (the plan stores them contiguously, in block order); the runs of
+// one cluster must agree on width and t range in every segment.  Each group
+// is cut into items of at most P1_MT M tiles and, along its segments, into
+// pieces of about `target` stored bytes so that the persistent CTAs get
+// similar loads; items are ordered largest first.
+static void make_groups(const MatvecPlan& plan, const std::vector<DevChunk16>& c16,
+                        std::vector<TcGroup>& items, std::vector<TcSeg>& segs) {
+    struct Run {
+        int64_t sigma, seg, row, t0;
+        int32_t ld16, w;
+    };
+    std::vector<Run> runs;
+    const int64_t nseg = (int64_t)plan.col_leaf_begin.size() - 1;
+    for (int64_t l = 0; l < nseg; ++l) {
+        int64_t end_data = -1;
+        for (int64_t q = plan.col_leaf_begin[l]; q < plan.col_leaf_begin[l + 1]; ++q) {
+            const int32_t id = plan.col_items[q];
+            const DevChunk16& c = c16[id];
+            if (c.ncols == 0) continue;
+            const int64_t sig = plan.chunks[id].sigma;
+            if (!runs.empty() && runs.back().seg == l && runs.back().sigma == sig) {
+                Run& r = runs.back();
+                if (c.data != end_data || c.vec != r.t0 + r.w || c.ld != r.ld16)
+                    hm_throw(HM_ERR_UNSUPPORTED, "column group not contiguous in the BF16 arena");
+                r.w += c.ncols;
+            } else {
+                if (c.data % c.ld) hm_throw(HM_ERR_UNSUPPORTED, "column group not on a row of its ld view");
+                runs.push_back({sig, l, c.data / c.ld, c.vec, c.ld, c.ncols});
+            }
+            end_data = c.data + (int64_t)c.ld * c.ncols;
+        }
+    }
+    std::stable_sort(runs.begin(), runs.end(), [](const Run& a, const Run& b) { return a.sigma < b.sigma; });
+    int64_t total = 0;
+    for (const Run& r : runs) {
+        if (r.row > INT32_MAX - 4096) hm_throw(HM_ERR_UNSUPPORTED, "BF16 arena above 2^31 rows of its ld view");
+        total += hm_round_up(r.w, P1_BOX) * 4 * r.ld16;
+    }
+    const int64_t target = std::max<int64_t>(128 * 1024, total / (4 * device_sms()));
+    std::vector<std::pair<int64_t, int32_t>> cost;  // (bytes, item)
+    for (size_t g0 = 0; g0 < runs.size();) {
+        size_t g1 = g0;
+        while (g1 < runs.size() && runs[g1].sigma == runs[g0].sigma) ++g1;
+        const int32_t w = runs[g0].w;
+        for (size_t q = g0; q < g1; ++q)
+            if (runs[q].w != w || runs[q].t0 != runs[g0].t0)
+                hm_throw(HM_ERR_UNSUPPORTED, "column group differs between segments");
+        for (int32_t c0 = 0; c0 < w; c0 += 128 * P1_MT) {
+            const int32_t wc = std::min<int32_t>(128 * P1_MT, w - c0);
+            const int64_t wpad = hm_round_up(wc, P1_BOX);
+            std::vector<std::pair<size_t, size_t>> pieces;
+            int64_t acc = 0;
+            size_t p0 = g0;
+            for (size_t q = g0; q < g1; ++q) {
+                const int64_t b = wpad * 4 * runs[q].ld16;
+                if (q > p0 && acc + b > target) {
+                    pieces.push_back({p0, q});
+                    p0 = q;
+                    acc = 0;
+                }
+                acc += b;
+            }
+            pieces.push_back({p0, g1});
+            for (const auto& pc : pieces) {
+                TcGroup it;
+                it.t0 = runs[g0].t0 + c0;
+                it.ncol = wc;
+                it.seg0 = (int32_t)segs.size();
+                it.red = pieces.size() > 1 ? 1 : 0;
+                int64_t bytes = 0;
+                for (size_t q = pc.first; q < pc.second; ++q) {
+                    segs.push_back({plan.leaf_dof_begin[runs[q].seg], (int32_t)(runs[q].row + c0), runs[q].ld16});
+                    bytes += wpad * 4 * runs[q].ld16;
+                }
+                it.seg1 = (int32_t)segs.size();
+                cost.push_back({bytes, (int32_t)items.size()});
+                items.push_back(it);
+            }
+        }
+        g0 = g1;
+    }
+    if (segs.size() > (size_t)INT32_MAX) hm_throw(HM_ERR_UNSUPPORTED, "phase-1 segment table");
+    std::stable_sort(cost.begin(), cost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<TcGroup> sorted;
+    sorted.reserve(items.size());
+    for (const auto& c : cost) sorted.push_back(items[c.second]);
+    items.swap(sorted);
+}
+
+void make_block_items(MatvecDev* m, const MatvecPlan& plan, const std::vector<DevChunk16>& c16,
+                      std::vector<DevBuf>& owner, cudaStream_t st) {
+    std::vector<TcItem> t2;
+    std::vector<uint32_t> codes;
+    int64_t col = 0;
+    for (const WorkItem& w : m->h_items2) {
+        const DevChunk16& a = c16[m->h_order2[w.first]];
+        TcItem t;
+        t.dof = w.dof;
+        t.col0 = col;
+        t.row0 = (int32_t)(a.data / a.ld);
+        t.ld16 = a.ld;
+        t.rows = w.rows;
+        for (int32_t q = w.first; q < w.last; ++q) {
+            const DevChunk16& c = c16[m->h_order2[q]];
+            for (int32_t j = 0; j < c.ncols; ++j)
+                codes.push_back(c.kind != 0 ? ((uint32_t)(c.vec + j) | 0x80000000u) : (uint32_t)(2 * (c.vec + j)));
+            col += c.ncols;
+        }
+        t.ncol = (int32_t)(col - t.col0);
+        t2.push_back(t);
+    }
+    std::vector<TcGroup> g1;
+    std::vector<TcSeg> s1;
+    make_groups(plan, c16, g1, s1);
+    m->ngroups1 = (int64_t)g1.size();
+    m->tgroups1 = (TcGroup*)hm_dmalloc(owner, std::max<size_t>(g1.size(), 1) * sizeof(TcGroup), st, false);
+    m->tsegs1 = (TcSeg*)hm_dmalloc(owner, std::max<size_t>(s1.size(), 1) * sizeof(TcSeg), st, false);
+    m->tscale1 = (float*)hm_dmalloc(owner, std::max<int64_t>(m->t_elems, 1) * sizeof(float), st, false);
+    m->titems2 = (TcItem*)hm_dmalloc(owner, std::max<size_t>(t2.size(), 1) * sizeof(TcItem), st, false);
+    m->colcode2 = (uint32_t*)hm_dmalloc(owner, std::max<size_t>(codes.size(), 1) * 4, st, false);
+    HM_CUDA(cudaMemcpyAsync(m->tgroups1, g1.data(), g1.size() * sizeof(TcGroup), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->tsegs1, s1.data(), s1.size() * sizeof(TcSeg), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->titems2, t2.data(), t2.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->colcode2, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st));
+    if (m->n_o1) {
+        tscale_kernel<<<(unsigned)m->n_o1, 128, 0, st>>>(m->hdr16_1, m->n_o1, m->tscale1);
+        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
+    }
+    HM_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+}
+
+static int multi_grid(int64_t nitems) { return (int)std::min<int64_t>(nitems, device_sms()); }
 
 static void multi_setup(MatvecDev* m, int64_t n, cudaStream_t st) {
     if (m->xb) return;
@@ -771,9 +951,9 @@ static void multi_phases(MatvecDev* m, int64_t n, cudaStream_t st, cudaEvent_t e
     if (m->t_elems) HM_CUDA(cudaMemsetAsync(m->tm, 0, (size_t)m->t_elems * NR * sizeof(float2), st));
     HM_CUDA(cudaMemsetAsync(m->ym, 0, (size_t)n * NR * sizeof(float2), st));
     if (e1) HM_CUDA(cudaEventRecord(e1, st));
-    if (m->n1) {
-        mvc_phase1<<<multi_grid(m->n1), P1_THREADS, sizeof(P1Smem) + 1024, st>>>(
-            m->titems1, (int)m->n1, m->colinfo1, (const CUtensorMap*)m->tmaps,
+    if (m->ngroups1) {
+        mvc_phase1<<<multi_grid(m->ngroups1), P1_THREADS, sizeof(P1Smem) + 1024, st>>>(
+            m->tgroups1, (int)m->ngroups1, m->tsegs1, m->tscale1, (const CUtensorMap*)m->tmaps,
             (const CUtensorMap*)m->tmap_xb, m->tm, m->d_err);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
@@ -788,7 +968,7 @@ static void multi_phases(MatvecDev* m, int64_t n, cudaStream_t st, cudaEvent_t e
     }
     if (m->n2) {
         mvc_phase2<<<multi_grid(m->n2), P2_THREADS, sizeof(P2Smem) + 1024, st>>>(
-            m->titems2, (int)m->n2, m->colcode2, (const CUtensorMap*)m->tmaps + TMAP_PER_PHASE, m->xb,
+            m->titems2, (int)m->n2, m->colcode2, (const CUtensorMap*)m->tmaps + TMAP_PHASE2 * TMAP_PER_PHASE, m->xb,
             m->t16, m->ym, m->d_err);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();

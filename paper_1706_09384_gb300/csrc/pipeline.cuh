@@ -44,12 +44,19 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait for the completion of the phase with the given parity
+// bounded wait for the completion of the phase with the given parity; the
+// clock is read once every 64 tries (the start time after the first 64), so
+// a wait that ends soon costs no timer read
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity) {
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(b, parity))
-        if (global_ns() - t0 > PIPE_WAIT_NS) return false;
-    return true;
+    uint64_t t0 = 0;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(b, parity)) return true;
+        if ((it & 63u) == 0) {
+            const uint64_t t = global_ns();
+            if (it == 64) t0 = t;
+            else if (t - t0 > PIPE_WAIT_NS) return false;
+        }
+    }
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     return mbar_try_wait(b, parity) || mbar_wait_slow(b, parity);
