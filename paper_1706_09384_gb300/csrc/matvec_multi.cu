@@ -100,6 +100,7 @@ struct P2Smem {
 // 227 KB including the 1 KB alignment slack
 static_assert(sizeof(P1Smem) + 1024 <= 227 * 1024, "phase 1 shared memory");
 static_assert(sizeof(P2Smem) + 1024 <= 227 * 1024, "phase 2 shared memory");
+static_assert(TC_KBMAX <= 6 && P2_ABYTES == 6 * 4096, "phase-2 stages: at most three M tiles");
 static_assert(P1_NZ == TMAP_PHASE2 && (128 >> (P1_NZ - 1)) == P1_BOX, "phase-1 map sets");
 static_assert(P1_ABYTES % 1024 == 0 && P1_BBYTES % 1024 == 0 && P2_ABYTES % 1024 == 0 &&
                   (P1_BOX * 128) % 1024 == 0 && 128 % P1_BOX == 0 &&
@@ -112,6 +113,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return l | (h << 16);
 }
 
+// Slot and phase parity of a ring of n stages, advanced stage by stage (no
+// divisions in the issue loops).
+struct Ring {
+    uint32_t q = 0, ph = 0;
+    __device__ __forceinline__ void next(int n) {
+        if (++q == (uint32_t)n) {
+            q = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
+// Rows of M tile mt of an item of ncol columns as the phase-1 copies load them:
+// 128 (one box) or the tile's columns rounded up to 16.
+__device__ __forceinline__ int tile_rows(int ncol, int mt) {
+    return P1_SPLIT_TAIL ? (min(128, ncol - 128 * mt) + P1_BOX - 1) / P1_BOX * P1_BOX : 128;
+}
+
 // Shared-memory matrix descriptor, 128-byte swizzle: start >> 4, leading byte
 // offset >> 4 (MN-major: between 64-element atoms along M/N), stride byte
 // offset >> 4 (between 8-row groups), version 1, layout 2 (SWIZZLE_128B).
@@ -119,33 +138,45 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uin
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                     uint32_t acc) {
+// Issue helpers of a role that a whole warp runs with warp-uniform control
+// flow and operands: elect.sync picks the one lane that issues, so the
+// operands need not move out of the uniform datapath for every instruction.
+__device__ __forceinline__ void w_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(smem_u32(b)),
+        "r"(bytes)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            uint64_t* bar, uint64_t policy) {
+__device__ __forceinline__ void w_tma_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar,
+                                         uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;\n\t}" ::"r"(smem_u32(dst)),
         "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar, uint64_t policy) {
+__device__ __forceinline__ void w_tma_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                         uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;\n\t}" ::"r"(smem_u32(dst)),
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void w_umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void w_commit(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {
@@ -244,14 +275,32 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t 
                  : "memory");
 }
 // A wait of one role: on a timeout the error word and the abort flag are set
-// and false is returned; once the flag is set no role starts another wait.
+// and false is returned; once the flag is set no role waits for a phase that
+// has not completed.
 template <typename Smem>
 __device__ __forceinline__ bool tc_wait(Smem& S, uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
     if (*(volatile int32_t*)&S.abort) return false;
-    if (mbar_wait(bar, parity)) return true;
+    if (mbar_wait_slow(bar, parity)) return true;
     atomicExch(err, MV_ERR_TIMEOUT);
     *(volatile int32_t*)&S.abort = 1;
     return false;
+}
+// Item and segment records as warp-uniform values (lane 0's copy): the loop
+// bounds of the issuing roles then stay on the uniform datapath.
+__device__ __forceinline__ int uni(int v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ int64_t uni(int64_t v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ TcGroup uni(const TcGroup& x) {
+    return {uni(x.t0), uni(x.ncol), uni(x.seg0), uni(x.seg1), uni(x.red)};
+}
+__device__ __forceinline__ TcSeg uni(const TcSeg& x) { return {uni(x.dof), uni(x.row0), uni(x.ld16)}; }
+__device__ __forceinline__ TcItem uni(const TcItem& x) {
+    return {uni(x.dof), uni(x.col0), uni(x.row0), uni(x.ld16), uni(x.ncol), uni(x.rows)};
+}
+// The same wait taken by a whole warp, with one result for all its lanes.
+template <typename Smem>
+__device__ __forceinline__ bool w_wait(Smem& S, uint64_t* bar, uint32_t parity, int* err) {
+    return __all_sync(0xffffffffu, tc_wait(S, bar, parity, err));
 }
 template <typename Smem>
 __device__ __forceinline__ bool tc_aborted(Smem& S) {
@@ -278,7 +327,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcGroup* items
                                                            int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     P1Smem& S = tc_smem<P1Smem>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
     if (tid == 0) {
         for (int q = 0; q < P1_NS; ++q) {
             mbar_init(&S.full[q], 1);
@@ -295,59 +344,62 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcGroup* items
     tc_setup(S, P1_TMEM_COLS);
     const uint32_t tmem = S.tmem;
     if (warp == 0) {  // ---- TMA producer ----
-        if (lane == 0) {
+        {  // the whole warp: one lane issues (elect.sync)
             tmap_acquire(map_xb);
             const uint64_t pol_stream = l2_policy_evict_first(), pol_keep = l2_policy_evict_last();
             int g = 0, gs = 0;  // A stages and segments issued
+            Ring ra;            // A ring slot of stage g
             uint64_t acquired[P1_NZ] = {0, 0, 0, 0};
             bool ok = true;
             for (ItemIter<TcGroup> X(items, nitems); ok && X.valid() && !tc_aborted(S); X.advance()) {
-                const TcGroup I = X.cur;
+                const TcGroup I = uni(X.cur);
                 const int nmt = (I.ncol + 127) >> 7;
-                TcSeg nx = segs[I.seg0];
+                TcSeg nx = uni(segs[I.seg0]);
                 for (int s = I.seg0; ok && s < I.seg1; ++s) {
                     const TcSeg sg = nx;
-                    if (s + 1 < I.seg1) nx = segs[s + 1];  // read one segment ahead
+                    if (s + 1 < I.seg1) nx = uni(segs[s + 1]);  // read one segment ahead
                     const int li = sg.ld16 >> 2;
                     const int nkb = (2 * sg.ld16 + 63) >> 6, bs = gs & 1;
-                    if (gs >= 2 && !tc_wait(S, &S.bempty[bs], ((gs >> 1) - 1) & 1, err)) break;
+                    if (gs >= 2 && !w_wait(S, &S.bempty[bs], ((gs >> 1) - 1) & 1, err)) break;
                     // B: XB rows 2 dof + k, k < 64 nkb (beyond 2 R they meet zero A entries)
-                    mbar_arrive_expect_tx(&S.bfull[bs], (uint32_t)nkb * P1_BBYTES);
+                    w_expect_tx(&S.bfull[bs], (uint32_t)nkb * P1_BBYTES);
                     for (int kb = 0; kb < nkb; ++kb)
-                        tma_load_2d(S.b[bs][kb], map_xb, 0, (int)(2 * sg.dof) + 64 * kb, &S.bfull[bs], pol_keep);
+                        w_tma_2d(S.b[bs][kb], map_xb, 0, (int)(2 * sg.dof) + 64 * kb, &S.bfull[bs], pol_keep);
                     ++gs;
-                    for (int mt = 0; ok && mt < nmt; ++mt) {
-                        // the tile's rows rounded up to 16: one 128-row box, or
-                        // boxes of 64, 32 and 16 rows after one another (the
-                        // bits of the count), so a tile takes at most three copies
-                        const int rr = P1_SPLIT_TAIL ? (min(128, I.ncol - 128 * mt) + P1_BOX - 1) / P1_BOX * P1_BOX
-                                                     : 128;
+                    for (int mt = 0; mt < nmt; ++mt) {
+                        const int rr = tile_rows(I.ncol, mt);
                         for (int z = 0; z < P1_NZ; ++z)
                             if ((rr == 128) == (z == 0) && (z == 0 || (rr & (128 >> z))) &&
                                 !((acquired[z] >> li) & 1)) {  // each descriptor once
                                 tmap_acquire(maps + z * TMAP_PER_PHASE + li);
                                 acquired[z] |= 1ull << li;
                             }
+                    }
+                    const CUtensorMap* map0 = maps + li;
+                    for (int mt = 0; ok && mt < nmt; ++mt) {
+                        const int rr = tile_rows(I.ncol, mt), y = sg.row0 + 128 * mt;
                         for (int kb = 0; kb < nkb; ++kb) {
-                            const int q = g % P1_NS;
-                            if (g >= P1_NS && !tc_wait(S, &S.empty[q], ((g / P1_NS) - 1) & 1, err)) {
+                            if (g >= P1_NS && !w_wait(S, &S.empty[ra.q], ra.ph ^ 1u, err)) {
                                 ok = false;
                                 break;
                             }
-                            mbar_arrive_expect_tx(&S.full[q], (uint32_t)(rr * 128));
-                            const int y = sg.row0 + 128 * mt;
+                            unsigned char* dst = S.a[ra.q];
+                            uint64_t* bar = &S.full[ra.q];
+                            w_expect_tx(bar, (uint32_t)(rr * 128));
                             if (rr == 128) {
-                                tma_load_2d(S.a[q], maps + li, kb * 64, y, &S.full[q], pol_stream);
+                                w_tma_2d(dst, map0, kb * 64, y, bar, pol_stream);
                             } else {
                                 int off = 0;
+#pragma unroll
                                 for (int z = 1; z < P1_NZ; ++z)
                                     if (rr & (128 >> z)) {
-                                        tma_load_2d(S.a[q] + off * 128, maps + z * TMAP_PER_PHASE + li, kb * 64,
-                                                    y + off, &S.full[q], pol_stream);
+                                        w_tma_2d(dst + off * 128, map0 + z * TMAP_PER_PHASE, kb * 64, y + off,
+                                                    bar, pol_stream);
                                         off += 128 >> z;
                                     }
                             }
                             ++g;
+                            ra.next(P1_NS);
                         }
                     }
                 }
@@ -361,47 +413,55 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcGroup* items
         }
         __syncwarp();
     } else if (warp == 1) {  // ---- MMA issue ----
-        if (lane == 0) {
+        {  // the whole warp: one lane issues (elect.sync)
             int g = 0, gs = 0, ii = 0;  // A stages, segments, items
+            Ring ra;
             bool ok = true;
+            // descriptors of A stage 0 and B buffer 0; the others are offsets
+            // in the 16-byte address field (no carry: shared memory < 256 KB)
+            const uint64_t da0 = desc_sw128(smem_u32(S.a[0]), 16, 1024);
+            const uint64_t db0 = desc_sw128(smem_u32(S.b[0][0]), 8192, 1024);
             for (ItemIter<TcGroup> X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
-                const TcGroup I = X.cur;
+                const TcGroup I = uni(X.cur);
                 const int nmt = (I.ncol + 127) >> 7, set = ii & 1;
-                if (ii >= 2 && !tc_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
+                if (ii >= 2 && !w_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(set * 256);
-                int nkb_next = (2 * segs[I.seg0].ld16 + 63) >> 6;
+                int nkb_next = (2 * uni(segs[I.seg0].ld16) + 63) >> 6;
                 for (int s = I.seg0; ok && s < I.seg1; ++s) {
                     const int nkb = nkb_next, bs = gs & 1;
-                    if (s + 1 < I.seg1) nkb_next = (2 * segs[s + 1].ld16 + 63) >> 6;
-                    if (!tc_wait(S, &S.bfull[bs], (gs >> 1) & 1, err)) {
+                    if (s + 1 < I.seg1) nkb_next = (2 * uni(segs[s + 1].ld16) + 63) >> 6;
+                    if (!w_wait(S, &S.bfull[bs], (gs >> 1) & 1, err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
+                    const uint64_t dbs = db0 + (uint64_t)((bs * TC_KBMAX * P1_BBYTES) >> 4);
                     for (int mt = 0; ok && mt < nmt; ++mt) {
+                        const uint32_t d = dacc + (uint32_t)(mt * 64);
                         for (int kb = 0; kb < nkb; ++kb) {
-                            const int q = g % P1_NS;
-                            if (!tc_wait(S, &S.full[q], (g / P1_NS) & 1, err)) {
+                            if (!w_wait(S, &S.full[ra.q], ra.ph, err)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t sa = smem_u32(S.a[q]), sb = smem_u32(S.b[bs][kb]);
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)  // K = 16: 32 bytes along A's rows, two 8-row groups of B
-                                umma(dacc + (uint32_t)(mt * 64), desc_sw128(sa + kk * 32, 16, 1024),
-                                     desc_sw128(sb + kk * 2048, 8192, 1024), TC_IDESC | TC_B_MN,
-                                     (s > I.seg0 || kb > 0 || kk > 0) ? 1u : 0u);
-                            umma_commit(&S.empty[q]);
+                            const uint64_t da = da0 + (uint64_t)((ra.q * P1_ABYTES) >> 4);
+                            const uint64_t db = dbs + (uint64_t)((kb * P1_BBYTES) >> 4);
+                            // K = 16 per MMA: 32 bytes along A's rows, two 8-row groups of B
+                            w_umma(d, da, db, TC_IDESC | TC_B_MN, (s > I.seg0 || kb > 0) ? 1u : 0u);
+                            w_umma(d, da + 2, db + 128, TC_IDESC | TC_B_MN, 1u);
+                            w_umma(d, da + 4, db + 256, TC_IDESC | TC_B_MN, 1u);
+                            w_umma(d, da + 6, db + 384, TC_IDESC | TC_B_MN, 1u);
+                            w_commit(&S.empty[ra.q]);
                             ++g;
+                            ra.next(P1_NS);
                         }
                     }
                     if (!ok) break;
-                    umma_commit(&S.bempty[bs]);
+                    w_commit(&S.bempty[bs]);
                     ++gs;
                 }
-                if (ok) umma_commit(&S.accf[set]);
+                if (ok) w_commit(&S.accf[set]);
             }
             if (g > 0) {  // the MMAs finish before shared memory and TMEM go
                 const int k = g - 1;
@@ -469,7 +529,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
                                                            float2* Y, int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     P2Smem& S = tc_smem<P2Smem>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
     if (tid == 0) {
         for (int q = 0; q < P2_NS; ++q) {
             mbar_init(&S.full[q], 1);
@@ -485,12 +545,13 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
     tc_setup(S, P2_TMEM_COLS);
     const uint32_t tmem = S.tmem;
     if (warp == 0) {  // ---- TMA producer ----
-        if (lane == 0) {
+        {  // the whole warp: one lane issues (elect.sync)
             const uint64_t pol = l2_policy_evict_first();
             int g = 0;
+            Ring ra;
             uint64_t acquired = 0;
             for (ItemIter<TcItem> X(items, nitems); X.valid() && !tc_aborted(S); X.advance()) {
-                const TcItem I = X.cur;
+                const TcItem I = uni(X.cur);
                 const CUtensorMap* map = maps + (I.ld16 >> 2);
                 if (!((acquired >> (I.ld16 >> 2)) & 1)) {  // each descriptor once
                     tmap_acquire(map);
@@ -498,12 +559,11 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
                 }
                 const int nbox = (2 * I.ld16 + 63) >> 6;  // 64-row m-blocks along m = 2r + re/im
                 const int nst = (I.ncol + 31) >> 5;
-                for (int k = 0; k < nst; ++k, ++g) {
-                    const int q = g % P2_NS;
-                    if (g >= P2_NS && !tc_wait(S, &S.empty[q], ((g / P2_NS) - 1) & 1, err)) break;
+                for (int k = 0; k < nst; ++k, ++g, ra.next(P2_NS)) {
+                    if (g >= P2_NS && !w_wait(S, &S.empty[ra.q], ra.ph ^ 1u, err)) break;
                     // one copy: 32 stored columns x all m-blocks, m-block b at 4096 b
-                    mbar_arrive_expect_tx(&S.full[q], (uint32_t)nbox * 4096u);
-                    tma_load_3d(S.a[q], map, 0, I.row0 + k * 32, 0, &S.full[q], pol);
+                    w_expect_tx(&S.full[ra.q], (uint32_t)nbox * 4096u);
+                    w_tma_3d(S.a[ra.q], map, 0, I.row0 + k * 32, 0, &S.full[ra.q], pol);
                 }
             }
             for (int k = max(0, g - P2_NS); k < g; ++k)
@@ -511,20 +571,23 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
         }
         __syncwarp();
     } else if (warp == 1) {  // ---- MMA issue ----
-        if (lane == 0) {
+        {  // the whole warp: one lane issues (elect.sync)
             int g = 0, ii = 0;
+            Ring ra;
             bool ok = true;
+            // descriptors of A stage 0 and weight stage 0 (others: address-field offsets)
+            const uint64_t da0 = desc_sw128(smem_u32(S.a[0]), 4096, 1024);
+            const uint64_t dw0 = desc_sw128(smem_u32(S.w[0]), 8192, 1024);
             for (ItemIter<TcItem> X(items, nitems); ok && X.valid(); X.advance(), ++ii) {
-                const TcItem I = X.cur;
+                const TcItem I = uni(X.cur);
                 const int nmt = (((2 * I.ld16 + 63) >> 6) + 1) >> 1;  // 128-row M tiles
                 const int nst = (I.ncol + 31) >> 5;
                 const int set = ii & 1;
-                if (ii >= 2 && !tc_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
+                if (ii >= 2 && !w_wait(S, &S.acce[set], ((ii >> 1) - 1) & 1, err)) break;
                 tc_fence_after();
-                for (int k = 0; k < nst; ++k, ++g) {
-                    const int q = g % P2_NS;
-                    if (!tc_wait(S, &S.full[q], (g / P2_NS) & 1, err) ||
-                        !tc_wait(S, &S.wfull[q], (g / P2_NS) & 1, err)) {
+                const uint32_t dacc = tmem + (uint32_t)(set * 256);
+                for (int k = 0; k < nst; ++k, ++g, ra.next(P2_NS)) {
+                    if (!w_wait(S, &S.full[ra.q], ra.ph, err) || !w_wait(S, &S.wfull[ra.q], ra.ph, err)) {
                         ok = false;
                         break;
                     }
@@ -532,17 +595,20 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
                     // them before the tensor core's reads
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(S.a[q]), sw = smem_u32(S.w[q]);
-                    for (int t = 0; t < nmt; ++t)
+                    const uint64_t da = da0 + (uint64_t)((ra.q * P2_ABYTES) >> 4);
+                    const uint64_t dw = dw0 + (uint64_t)((ra.q * P2_WBYTES) >> 4);
+                    const uint32_t en = k > 0 ? 1u : 0u;
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk)  // K = 16: two 8-row groups of both operands
-                            umma(tmem + (uint32_t)(set * 256 + t * 64),
-                                 desc_sw128(sa + t * 8192 + kk * 2048, 4096, 1024),
-                                 desc_sw128(sw + kk * 2048, 8192, 1024), TC_IDESC | TC_A_MN | TC_B_MN,
-                                 (k > 0 || kk > 0) ? 1u : 0u);
-                    umma_commit(&S.empty[q]);
+                    for (int t = 0; t < 3; ++t)  // K = 16 per MMA: two 8-row groups of both operands
+                        if (t < nmt) {
+                            w_umma(dacc + (uint32_t)(t * 64), da + (uint64_t)(t * 512), dw,
+                                 TC_IDESC | TC_A_MN | TC_B_MN, en);
+                            w_umma(dacc + (uint32_t)(t * 64), da + (uint64_t)(t * 512 + 128), dw + 128,
+                                 TC_IDESC | TC_A_MN | TC_B_MN, 1u);
+                        }
+                    w_commit(&S.empty[ra.q]);
                 }
-                if (ok) umma_commit(&S.accf[set]);  // also for an empty item: keeps the phases in step
+                if (ok) w_commit(&S.accf[set]);  // also for an empty item: keeps the phases in step
             }
             if (g > 0) {
                 const int k = g - 1;
