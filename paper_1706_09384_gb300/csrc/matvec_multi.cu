@@ -58,8 +58,10 @@ constexpr int P1_MT = 4;                              // M tiles of an item (512
 constexpr int P1_ABYTES = 128 * 128;                  // 128 columns x 64 bf16 of K
 constexpr int P1_BBYTES = 64 * 128;                   // 64 K rows of XB
 constexpr uint32_t P1_TMEM_COLS = 512;                // two sets of four 128 x 64 accumulators
-// phase 2: warp 0 TMA, warp 1 MMA, warps 2-3 weight rows, warps 4-7 epilogue
-constexpr int P2_THREADS = 256;
+// phase 2: warp 0 TMA, warp 1 MMA, P2_WW weight-row warps, four epilogue warps
+constexpr int P2_WW = 4;                              // weight-row warps
+constexpr int P2_WT = 32 * P2_WW;                     // weight-row threads
+constexpr int P2_THREADS = 32 * (2 + P2_WW + 4);
 constexpr int P2_NS = 6;
 constexpr int P2_ABYTES = TC_KBMAX * 4096;            // up to six 64 x 32 boxes
 constexpr int P2_WBYTES = 32 * 128;                   // 32 weight rows
@@ -100,6 +102,7 @@ struct P2Smem {
 // 227 KB including the 1 KB alignment slack
 static_assert(sizeof(P1Smem) + 1024 <= 227 * 1024, "phase 1 shared memory");
 static_assert(sizeof(P2Smem) + 1024 <= 227 * 1024, "phase 2 shared memory");
+static_assert(P2_WT % 8 == 0 && 256 % P2_WT == 0 && MAX_ITEM_COLS % P2_WT == 0, "weight-row threads");
 static_assert(TC_KBMAX <= 6 && P2_ABYTES == 6 * 4096, "phase-2 stages: at most three M tiles");
 static_assert(P1_NZ == TMAP_PHASE2 && (128 >> (P1_NZ - 1)) == P1_BOX, "phase-1 map sets");
 static_assert(P1_ABYTES % 1024 == 0 && P1_BBYTES % 1024 == 0 && P2_ABYTES % 1024 == 0 &&
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(P1_THREADS, 1) mvc_phase1(const TcGroup* items
 // Phase 2 (persistent): Y[dof + r] += sum_j M[r][j] w_j over the columns j of
 // each item (the dense and U chunks of one row leaf).  Stages of 32 columns
 // run across items: the A boxes by TMA, the 32 weight rows (128 bytes each)
-// copied by warps 2-3 into the swizzled B layout.  Two sets of TMEM
+// copied by the weight-row warps (cp.async) into the swizzled B layout.  Two sets of TMEM
 // accumulators (one item each) let the epilogue of an item overlap the next.
 __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items, int nitems,
                                                            const uint32_t* __restrict__ colcode,
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
     if (tid == 0) {
         for (int q = 0; q < P2_NS; ++q) {
             mbar_init(&S.full[q], 1);
-            mbar_init(&S.wfull[q], 64);  // one arrival per weight-row thread
+            mbar_init(&S.wfull[q], P2_WT);  // one arrival per weight-row thread
             mbar_init(&S.empty[q], 1);
         }
         for (int q = 0; q < 2; ++q) {
@@ -616,18 +619,19 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
             }
         }
         __syncwarp();
-    } else if (warp < 4) {  // ---- weight rows into B ----
-        // thread: 16-byte chunk c of rows jr, jr + 8, jr + 16, jr + 24 of a stage
-        const int wt = tid - 64, c = wt & 7, jr = wt >> 3;  // jr 0..7
-        // both warps pass the same named barriers: after an abort they keep
+    } else if (warp < 2 + P2_WW) {  // ---- weight rows into B ----
+        // thread: 16-byte chunk c of rows jr + (P2_WT / 8) h of a stage
+        constexpr int RSTEP = P2_WT / 8, RPT = 32 / RSTEP;  // row step, rows per thread
+        const int wt = tid - 64, c = wt & 7, jr = wt >> 3;
+        // the warps pass the same named barriers: after an abort they keep
         // walking the items (every wait then returns at once) instead of leaving;
         // each thread holds its share of the next item's column codes
-        constexpr int NPC = MAX_ITEM_COLS / 64;
+        constexpr int NPC = MAX_ITEM_COLS / P2_WT;
         uint32_t pc[NPC];
         auto fetch = [&](const TcItem& J, bool valid) {
 #pragma unroll
             for (int i = 0; i < NPC; ++i) {
-                const int idx = wt + 64 * i;
+                const int idx = wt + P2_WT * i;
                 pc[i] = (valid && idx < J.ncol) ? __ldg(colcode + J.col0 + idx) : 0u;
             }
         };
@@ -640,8 +644,8 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
             uint32_t* tab = S.code[ii & 1];
 #pragma unroll
             for (int i = 0; i < NPC; ++i)
-                if (wt + 64 * i < I.ncol) tab[wt + 64 * i] = pc[i];
-            named_sync<1, 64>();  // the table is complete (the other buffer may be refilled)
+                if (wt + P2_WT * i < I.ncol) tab[wt + P2_WT * i] = pc[i];
+            named_sync<1, P2_WT>();  // the table is complete (the other buffer may be refilled)
             fetch(X.nxt, X.has_next());
             for (int k = 0; k < nst; ++k, ++g) {
                 const int q = g % P2_NS;
@@ -649,8 +653,8 @@ __global__ void __launch_bounds__(P2_THREADS, 1) mvc_phase2(const TcItem* items,
                 ok = __all_sync(0xffffffffu, ok && !tc_aborted(S));
                 if (!ok) break;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {  // row j: 128 bytes, chunks XOR-swizzled by j mod 8
-                    const int jj = jr + 8 * h, j = k * 32 + jj;
+                for (int h = 0; h < RPT; ++h) {  // row j: 128 bytes, chunks XOR-swizzled by j mod 8
+                    const int jj = jr + RSTEP * h, j = k * 32 + jj;
                     const uint32_t* row = XB;
                     uint32_t bytes = 0;  // 0: zero fill
                     if (j < I.ncol) {
