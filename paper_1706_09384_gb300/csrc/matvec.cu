@@ -1013,10 +1013,27 @@ static void set_tiling(MatvecDev* m, const MatvecPlan& plan, int64_t item_bytes,
     HM_CUDA(cudaStreamSynchronize(st));  // host vectors h1, h2 leave scope
 }
 
+// Default work-item size: the largest power of two in [256 KB, 1 MB] of FP32
+// bytes that still gives about ten waves of four resident CTAs per SM.  Each
+// CTA pays a start (headers, the segment's x rows, its first copies) before
+// its stream flows, so large operators run faster with fewer, larger items;
+// small ones keep enough items to balance the SMs.  The BF16 layout follows
+// this tiling, the FP32 products may retune it.
+static int64_t default_item_bytes(int64_t arena_bytes) {
+    int dev = 0, nsm = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t per = arena_bytes / (10LL * 4 * std::max(nsm, 1));
+    int64_t ib = 256 * 1024;
+    while (2 * ib <= per && ib < 1024 * 1024) ib *= 2;
+    return ib;
+}
+
 MatvecDev* matvec_dev_create(const MatvecPlan& plan, int storage, std::vector<DevBuf>& owner,
                              cudaStream_t st) {
     MatvecDev* m = new MatvecDev();
     m->storage = storage;
+    m->item_bytes = default_item_bytes(plan.arena_elems * (int64_t)sizeof(float2));
     m->arena_elems = plan.arena_elems;
     m->arena = (float2*)hm_dmalloc(owner, std::max<int64_t>(plan.arena_elems, 2) * sizeof(float2),
                                    st, true);

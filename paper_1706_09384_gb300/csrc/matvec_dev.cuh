@@ -74,7 +74,8 @@ struct MatvecDev {
     int storage = 0;
     int s16_nstage = 3;                 // stages of the streamed BF16 kernels (2, 3 or 4; the
                                         // autotuner may change it)
-    int64_t item_bytes = 256 * 1024;    // target FP32 bytes of a work item
+    int64_t item_bytes = 256 * 1024;    // target FP32 bytes of a work item (set from the
+                                        // operator's size at creation)
     std::vector<DevChunk> dc;           // chunk headers in plan order (host)
     std::vector<DevBuf> tile_bufs;      // items, orders and headers of the current tiling
     // the full item lists of the tiling, and buffers for a subset of them (a
