@@ -30,8 +30,10 @@
 
 namespace {
 
-constexpr int AT = 256;
+constexpr int AT = 256;             // threads of an ACA CTA
+constexpr int ACA_MIN_CTAS = 2;     // resident CTAs per SM the launch bounds ask for
 constexpr int AW = AT / 32;
+constexpr int ACA_CH = 256;         // rows of the new factor columns staged per chunk (step 6)
 constexpr double SING_REL = 1e-12;
 
 struct Cof {
@@ -276,29 +278,62 @@ __device__ __forceinline__ void sub_df(double2& g, const float (&s)[4]) {
     g.y -= (double)s[2] + (double)s[3];
 }
 
-// This lane's share of three double-float dot products over rows lane, lane +
-// 32, ... < n of a column a and three consecutive columns b_q (ld n): out[2q],
-// out[2q + 1] = re, im of sum conj(a) b_q, or of sum a conj(b_q) (conj_b),
-// each rounded to FP64 once.  Not inlined: it keeps the ACA kernel's register
-// allocation out of the loop.
-__device__ __noinline__ void df_dots3(const float4* a, const float4* b, int64_t n, int lane,
-                                      bool conj_b, double* out) {
-    float s[3][4] = {};
-    for (int64_t r = lane; r < n; r += 32) {
-        const float4 u = a[r];
+// Step 6 of the ACA, one side: out[q] = sum over the nr rows of x conj(new_q)
+// (side 1, x = column p of V) or new_q conj(x) (side 0, x = column p of U),
+// for the column p of this thread; threads tid = g P + pl (g < G), p = p0 + pl.  The
+// three new columns (k, k + 1, k + 2 of base) are staged in shared memory
+// ACA_CH rows at a time; group g sums its slice of each chunk in double-float
+// arithmetic, the slices are rounded to FP64 once and added in FP64; out is
+// set for g = 0.  Every thread of the CTA calls it (block barriers inside).
+// Not inlined: it keeps the ACA kernel's register allocation out of the loop.
+__device__ __noinline__ void df_cross_side(const float4* base, int64_t nr, int k, int p, int NP, int g, int G,
+                                           int pl, int P, int side, float4 (*s_new)[ACA_CH],
+                                           double2 (*s_red)[3], double2* out) {
+    const int tid = threadIdx.x;
+    float acc[3][4] = {};
+    for (int64_t r0 = 0; r0 < nr; r0 += ACA_CH) {
+        const int cn = (int)min((int64_t)ACA_CH, nr - r0);
+        __syncthreads();  // the previous chunk is consumed
+        for (int t = tid; t < 3 * cn; t += AT) {
+            const int q = t / cn, rr = t - q * cn;
+            s_new[q][rr] = base[(int64_t)(k + q) * nr + r0 + rr];
+        }
+        __syncthreads();
+        if (p < NP && g < G) {
+            const float4* col = base + (int64_t)p * nr + r0;
+            const int rb = g * cn / G, re = (g + 1) * cn / G;
+            auto mac = [&](const float4& x, int rr) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (conj_b)
-                df_cmac_conj(s[q], u, b[r + q * n]);
-            else
-                df_cmac_conj(s[q], b[r + q * n], u);
+                for (int q = 0; q < 3; ++q) {
+                    if (side)
+                        df_cmac_conj(acc[q], x, s_new[q][rr]);  // V_p conj(Vn_q)
+                    else
+                        df_cmac_conj(acc[q], s_new[q][rr], x);  // Un_q conj(U_p)
+                }
+            };
+            int rr = rb;
+            for (; rr + 1 < re; rr += 2) {  // two rows' loads in flight
+                const float4 x0 = col[rr], x1 = col[rr + 1];
+                mac(x0, rr);
+                mac(x1, rr + 1);
+            }
+            if (rr < re) mac(col[rr], rr);
         }
     }
+    if (g < G)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        out[2 * q] = (double)s[q][0] + (double)s[q][1];
-        out[2 * q + 1] = (double)s[q][2] + (double)s[q][3];
-    }
+        for (int q = 0; q < 3; ++q)
+            s_red[g * P + pl][q] =
+                make_double2((double)acc[q][0] + (double)acc[q][1], (double)acc[q][2] + (double)acc[q][3]);
+    __syncthreads();
+    if (g == 0 && p < NP)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double2 t2 = s_red[pl][q];
+            for (int h = 1; h < G; ++h) t2 = cadd(t2, s_red[h * P + pl][q]);
+            out[q] = t2;
+        }
+    __syncthreads();  // s_red is free again
 }
 
 template <int N>
@@ -319,7 +354,7 @@ HM_D void block_sum(double (&x)[N], double (*sh)[AW]) {
 }
 
 template <bool DF>
-__global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
+__global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                                                  const GreenParams* __restrict__ gps,
                                                  const double* __restrict__ pts,
                                                  const double* __restrict__ nrm,
@@ -343,6 +378,8 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
     __shared__ double s_normB2, s_sref, s_best, s_dB2;
     __shared__ double2 s_gam[9];
     __shared__ double2 s_gdu[9], s_gdv[9];  // new diagonal Gram blocks (double-float path)
+    __shared__ float4 s_new[3][ACA_CH];       // step 6: a chunk of the three new columns
+    __shared__ double2 s_red[AT][3];          // step 6: partial sums of the thread groups
     __shared__ int s_stop;   // 0 continue, 1 converged, 2 overflow, 3 non-finite
     __shared__ int s_lost;   // a row retired for singular pivots carried a non-negligible residual
     __shared__ GreenParams s_gp;
@@ -413,9 +450,17 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                 }
                 if (DF && k > 0) {
                     float s9[9][4] = {};
+                    // V(j, p) for p + 1 is loaded while p is summed
+                    const float4* vp = Vd + 3 * j;
+                    float4 v0 = vp[0], v1 = vp[1], v2 = vp[2];
                     for (int p = 0; p < k; ++p) {
-                        const float4* vp = Vd + (int64_t)p * n3 + 3 * j;
-                        const float4 v0 = vp[0], v1 = vp[1], v2 = vp[2];
+                        float4 w0 = v0, w1 = v1, w2 = v2;
+                        if (p + 1 < k) {
+                            const float4* vq = vp + (int64_t)(p + 1) * n3;
+                            w0 = vq[0];
+                            w1 = vq[1];
+                            w2 = vq[2];
+                        }
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             const float4 u = Urow_df[a * capmax + p];
@@ -423,6 +468,9 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                             df_cmac_conj(s9[3 * a + 1], u, v1);
                             df_cmac_conj(s9[3 * a + 2], u, v2);
                         }
+                        v0 = w0;
+                        v1 = w1;
+                        v2 = w2;
                     }
 #pragma unroll
                     for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
@@ -553,9 +601,17 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                 }
                 if (DF && k > 0) {
                     float s9[9][4] = {};
+                    // U(i, p) for p + 1 is loaded while p is summed
+                    const float4* up = Ud + 3 * i;
+                    float4 u0 = up[0], u1 = up[1], u2 = up[2];
                     for (int p = 0; p < k; ++p) {
-                        const float4* up = Ud + (int64_t)p * m3 + 3 * i;
-                        const float4 u0 = up[0], u1 = up[1], u2 = up[2];
+                        float4 w0 = u0, w1 = u1, w2 = u2;
+                        if (p + 1 < k) {
+                            const float4* uq = up + (int64_t)(p + 1) * m3;
+                            w0 = uq[0];
+                            w1 = uq[1];
+                            w2 = uq[2];
+                        }
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
                             const float4 v = Vrow_df[c * capmax + p];
@@ -563,6 +619,9 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                             df_cmac_conj(s9[3 + c], u1, v);
                             df_cmac_conj(s9[6 + c], u2, v);
                         }
+                        u0 = w0;
+                        u1 = w1;
+                        u2 = w2;
                     }
 #pragma unroll
                     for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
@@ -641,34 +700,46 @@ __global__ void __launch_bounds__(AT, 2) aca_kernel(GreenParams gp0,
                 }
                 // ---- step 6: cross terms (U_p^H Un_q)(Vn_q^H V_p) of <B_k, dB> for p < k and the
                 // new diagonal Gram blocks (p = k .. k + 2), as double-float dot products over the
-                // double-float copies (FP32 pipes), each warp total rounded to FP64 once ----
+                // double-float copies (FP32 pipes).  A small GEMM: each thread owns one column p
+                // (P of them per pass), groups of threads split the rows, the three new columns
+                // are staged in shared memory chunk by chunk, so every old column is read once;
+                // each thread's partial sum is rounded to FP64 once and the groups add in FP64 ----
                 double cre = 0.0, cim = 0.0;
-                for (int p = wid; p < k + 3; p += AW) {
-                    double xy[12];
-                    df_dots3(Ud + (int64_t)p * m3, Ud + (int64_t)k * m3, m3, lane, false, xy);
-                    df_dots3(Vd + (int64_t)p * n3, Vd + (int64_t)k * n3, n3, lane, true, xy + 6);
-                    warp_sum_many<12>(xy);
+                {
+                    // P = k + 3 columns per pass (at most AT), G = AT / P row groups;
+                    // threads g >= G only help to stage the chunks
+                    const int NP = k + 3;
+                    const int P = NP < AT ? NP : AT;
+                    const int G = AT / P, pl = tid % P, g = tid / P;
+                    for (int p0 = 0; p0 < NP; p0 += P) {
+                        const int p = p0 + pl;
+                        double2 xs[3], ys[3];
+                        df_cross_side(Ud, m3, k, p, NP, g, G, pl, P, 0, s_new, s_red, xs);
+                        df_cross_side(Vd, n3, k, p, NP, g, G, pl, P, 1, s_new, s_red, ys);
+                        if (g == 0 && p < NP) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const double2 xq = make_double2(xy[2 * q], xy[2 * q + 1]);          // U_p^H Un_q
-                        const double2 yq = make_double2(xy[6 + 2 * q], xy[6 + 2 * q + 1]);  // Vn_q^H V_p
-                        if (p < k) {
-                            const double2 z = cmul(xq, yq);
-                            cre += z.x;
-                            cim += z.y;
-                            if (GU && lane == 0) {  // the new Gram columns, by Hermitian symmetry
-                                GU[p + (int64_t)(k + q) * J.cap] = xq;
-                                GU[(k + q) + (int64_t)p * J.cap] = cconj(xq);
-                                GV[(k + q) + (int64_t)p * J.cap] = yq;
-                                GV[p + (int64_t)(k + q) * J.cap] = cconj(yq);
+                            for (int q = 0; q < 3; ++q) {
+                                const double2 xq = xs[q];  // U_p^H Un_q
+                                const double2 yq = ys[q];  // Vn_q^H V_p
+                                if (p < k) {
+                                    const double2 z = cmul(xq, yq);
+                                    cre += z.x;
+                                    cim += z.y;
+                                    if (GU) {  // the new Gram columns, by Hermitian symmetry
+                                        GU[p + (int64_t)(k + q) * J.cap] = xq;
+                                        GU[(k + q) + (int64_t)p * J.cap] = cconj(xq);
+                                        GV[(k + q) + (int64_t)p * J.cap] = yq;
+                                        GV[p + (int64_t)(k + q) * J.cap] = cconj(yq);
+                                    }
+                                } else {
+                                    s_gdu[3 * (p - k) + q] = xq;  // Un_{p-k}^H Un_q
+                                    s_gdv[3 * q + (p - k)] = yq;  // Vn_q^H Vn_{p-k}
+                                }
                             }
-                        } else if (lane == 0) {
-                            s_gdu[3 * (p - k) + q] = xq;  // Un_{p-k}^H Un_q
-                            s_gdv[3 * q + (p - k)] = yq;  // Vn_q^H Vn_{p-k}
                         }
                     }
                 }
-                double cr[2] = {lane == 0 ? cre : 0.0, lane == 0 ? cim : 0.0};
+                double cr[2] = {cre, cim};
                 block_sum<2>(cr, sums);  // its barriers also publish s_gdu, s_gdv
                 if (tid == 0) {
                     // ||dB||^2 = sum_{q,q2} (Un_q^H Un_q2)(Vn_q2^H Vn_q)
