@@ -12,7 +12,7 @@
 // which holds whether or not R_U, R_V are invertible.  The Gram matrices, their
 // Cholesky factors and the core W are FP64; the SVD of the k x k core is a
 // one-sided Jacobi (Hestenes) iteration in double-float arithmetic on the FP32
-// pipes (rotation angles in FP64) with round-robin pair ordering.  Truncation:
+// pipes (approximate angles, exactly unitary rotations) with round-robin pair ordering.  Truncation:
 // smallest r' with
 // (sum_{i >= r'} s_i^2)^{1/2} <= eps (sum s_i^2)^{1/2} (Frobenius, matching the
 // ACA stopping test).  The tall products U T_U, V T_V are applied by a second
@@ -172,10 +172,6 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     return df_norm(p, e);
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ dfl df_of_d(double v) {
-    const float h = __double2float_rn(v);
-    return {h, __double2float_rn(v - (double)h)};
-}
 // s += a b (accumulating; a, b double-float)
 __device__ __forceinline__ void df_acc(float& h, float& l, dfl a, dfl b) {
     const float p = __fmul_rn(a.h, b.h);
@@ -186,6 +182,18 @@ __device__ __forceinline__ void df_acc(float& h, float& l, dfl a, dfl b) {
     h = t.h;
     l = __fadd_rn(l, __fadd_rn(t.l, e));
 }
+// 1 / sqrt(a) for a > 0 in double-float: the FP32 estimate refined by one
+// Newton step x + x (1 - a x^2) / 2 evaluated in double-float (relative error
+// about 2^-43, from the estimate's 2^-22 squared)
+__device__ __forceinline__ dfl df_rsqrt(dfl a) {
+    const float x = rsqrtf(a.h);
+    const float x2 = __fmul_rn(x, x);
+    const dfl xx = df_norm(x2, __fmaf_rn(x, x, -x2));  // x^2 exactly
+    const dfl d = df_add({1.f, 0.f}, df_neg(df_mul(a, xx)));
+    const dfl corr = df_mul(d, {0.5f * x, 0.f});
+    return df_add({x, 0.f}, corr);
+}
+__device__ __forceinline__ dfl df_scale(dfl a, float p2) { return {a.h * p2, a.l * p2}; }  // p2 a power of 2
 __device__ __forceinline__ double2 from_df(float4 v) {
     return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
 }
@@ -194,8 +202,8 @@ __device__ __forceinline__ double2 from_df(float4 v) {
 // double-float pairs (re_h, im_h, re_l, im_l)), round-robin pair ordering.
 // Each pair is handled by a group of G lanes (G grows with k): the lanes form
 // the pair's Gram entries as double-float dot products, the group leader turns
-// them into the rotation in FP64 and broadcasts it, and the lanes apply it in
-// double-float.  Only the final columns P_j s_j are needed (T_U, T_V below), so
+// them into the rotation (tangent in FP32, the unitary factors in double-float)
+// and broadcasts it, and the lanes apply it in double-float.  Only the final columns P_j s_j are needed (T_U, T_V below), so
 // the rotations are not accumulated.  The truncation formulas map the
 // rounding of the small columns through W^H, which amplifies it by up to
 // (s_1 / s_r)^2 ~ eps^-2: the arithmetic must keep u << eps^2 (FP32 does not;
@@ -246,32 +254,48 @@ __device__ void jacobi_columns_df(float4* W, int k) {
                         s[2 * q] = t.h;
                         s[2 * q + 1] = t.l;
                     }
-                // rotation parameters on the group leader only (FP64)
-                double c = 1.0, sn = 0.0, pr = 0.0, pim = 0.0;
+                // Rotation parameters on the group leader, without FP64: the
+                // tangent t may be approximate (FP32, on values scaled by a power
+                // of two), but the applied rotation must be unitary to double-float
+                // precision, so c = 1 / sqrt(1 + t^2), s = c t and the phase
+                // e^{-i phi} = conj(g) / |g| are formed in double-float arithmetic.
+                dfl dc = {1.f, 0.f}, ds = {0.f, 0.f}, dpr = {1.f, 0.f}, dpi = {0.f, 0.f};
                 int rot = 0;
                 if (gl == 0) {
-                    const double al = (double)s[0] + (double)s[1], be = (double)s[2] + (double)s[3];
-                    const double gr = (double)s[4] + (double)s[5], gi = (double)s[6] + (double)s[7];
-                    const double ag = sqrt(gr * gr + gi * gi);
-                    if (ag != 0.0 && ag > 1e-12 * sqrt(al * be)) {
-                        rot = 1;
-                        pr = gr / ag;
-                        pim = -gi / ag;  // e^{-i phi}
-                        const double zeta = (be - al) / (2.0 * ag);
-                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        sn = c * t;
+                    const dfl al = {s[0], s[1]}, be = {s[2], s[3]}, gr = {s[4], s[5]}, gi = {s[6], s[7]};
+                    const float gmax = fmaxf(fabsf(gr.h), fabsf(gi.h));
+                    const float nmax = fmaxf(al.h, be.h);
+                    if (gmax > 0.f && nmax > 0.f) {
+                        // |g|^2 > 1e-24 al be on scaled values (norms to <= 1, g to [1, 2))
+                        const float sn = scalbnf(1.f, -ilogbf(nmax));
+                        const float sg = scalbnf(1.f, -ilogbf(gmax));
+                        const dfl grs = df_scale(gr, sg), gis = df_scale(gi, sg);
+                        const float ag = sqrtf(grs.h * grs.h + gis.h * gis.h) * (sn / sg);  // |g| sn
+                        const float als = al.h * sn, bes = be.h * sn;
+                        if (ag > 0.f && ag * ag > 1e-24f * als * bes) {
+                            rot = 1;
+                            const float zeta = (bes - als) / (2.f * ag);
+                            const float az = fabsf(zeta);
+                            const float t = (zeta >= 0.f ? 1.f : -1.f) /
+                                            (az > 1e18f ? 2.f * az : az + sqrtf(1.f + az * az));
+                            const float t2 = __fmul_rn(t, t);
+                            dc = df_rsqrt(df_add({1.f, 0.f}, df_norm(t2, __fmaf_rn(t, t, -t2))));
+                            ds = df_mul(dc, {t, 0.f});
+                            const dfl g2 = df_add(df_mul(grs, grs), df_mul(gis, gis));
+                            const dfl inv = df_rsqrt(g2);
+                            dpr = df_mul(grs, inv);
+                            dpi = df_neg(df_mul(gis, inv));
+                        }
                     }
                 }
                 const int src = lane - gl;
                 rot = __shfl_sync(gmask, rot, src);
                 if (!rot) continue;
-                c = __shfl_sync(gmask, c, src);
-                sn = __shfl_sync(gmask, sn, src);
-                pr = __shfl_sync(gmask, pr, src);
-                pim = __shfl_sync(gmask, pim, src);
+                dc = {__shfl_sync(gmask, dc.h, src), __shfl_sync(gmask, dc.l, src)};
+                ds = {__shfl_sync(gmask, ds.h, src), __shfl_sync(gmask, ds.l, src)};
+                dpr = {__shfl_sync(gmask, dpr.h, src), __shfl_sync(gmask, dpr.l, src)};
+                dpi = {__shfl_sync(gmask, dpi.h, src), __shfl_sync(gmask, dpi.l, src)};
                 if (gl == 0) s_conv = 0;
-                const dfl dc = df_of_d(c), ds = df_of_d(sn), dpr = df_of_d(pr), dpi = df_of_d(pim);
                 // [w_a, w_b] <- [w_a, w_b] [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
                 for (int r = gl; r < k; r += G) {
                     const float4 wa = W[r + (int64_t)a * k], wb = W[r + (int64_t)b * k];
