@@ -219,7 +219,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                      const std::vector<int64_t>& m3, const std::vector<int64_t>& n3,
                      const std::vector<int32_t>& kk, const std::vector<int64_t>& go,
                      const std::vector<int32_t>& gl, const double2* d_gram, double2* d_work,
-                     double eps_r) {
+                     const float4* d_work_df, double eps_r) {
         std::vector<int32_t> ranks;
         std::vector<int64_t> soff;
         EvPair er(st);
@@ -250,7 +250,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                     }
                 }
             }
-            recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_stage, st);
+            recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_work_df, d_stage, st);
             ev_rec += er.stop(st);
             for (size_t q = 0; q < keep.size(); ++q) {
                 const int64_t a = ids[keep[q]];
@@ -372,7 +372,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 go.push_back(jobs[j].g_off);
                 gl.push_back(jobs[j].cap);
             }
-            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, d_gram, d_work, h0->eps);
+            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, d_gram, d_work, d_work_df, h0->eps);
             HM_CUDA(cudaStreamSynchronize(st));
             free_all(tmp);
             t_rec += ms_since(t0);
@@ -433,7 +433,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 if (!rb[q].certified) n_uncert[aq[ids[q]]]++;
             }
             // range error <= eps/2 (certified), truncation eps sqrt(3)/2: total <= eps
-            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, nullptr, W, h0->eps * std::sqrt(3.0) / 2);
+            stage(ids, keep, uo, vo, m3, n3, kk, go, gl, nullptr, W, nullptr, h0->eps * std::sqrt(3.0) / 2);
             HM_CUDA(cudaStreamSynchronize(st));
             free_all(tmp);
         }

@@ -214,12 +214,13 @@ void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64
 // Writes U' = U T_U / V' = V T_V (FP32, column-major, ld = factor rows) for
 // row slices: job_of[i], which[i] (0 = U, 1 = V), first row row0[i], rows[i]
 // (<= 192), destination dst[i] (element offset of the slice's first row in
-// d_out), ld[i] (= factor rows).
+// d_out), ld[i] (= factor rows).  d_work_df: the double-float copy of d_work
+// the ACA keeps (same offsets), read instead of converting d_work, or null.
 void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
                       const std::vector<int32_t>& which, const std::vector<int64_t>& row0,
                       const std::vector<int32_t>& rows, const std::vector<int64_t>& dst,
                       const std::vector<int32_t>& ld, const std::vector<int32_t>& ranks,
-                      const double2* d_work, float2* d_out, cudaStream_t st);
+                      const double2* d_work, const float4* d_work_df, float2* d_out, cudaStream_t st);
 void recompress_release(void* batch, cudaStream_t st);
 
 // ---------------- rank predictor (rankmlp.cu) ----------------

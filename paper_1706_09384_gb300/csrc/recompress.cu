@@ -474,8 +474,13 @@ __device__ __forceinline__ void df_mac(float& h, float& l, float ah, float al, f
     l = __fadd_rn(l, __fadd_rn(err, e));
 }
 
+// With HAS_DF the factor is read from the ACA's double-float copy (the same
+// split as below, made once when the column was written), so no FP64
+// conversion runs per output block.
+template <bool HAS_DF>
 __global__ void __launch_bounds__(192) apply_factor_kernel(const ApplyJob* jobs,
                                                            const double2* __restrict__ work,
+                                                           const float4* __restrict__ work_df,
                                                            const float4* __restrict__ scratch,
                                                            float2* out) {
     const ApplyJob J = jobs[blockIdx.x];
@@ -488,10 +493,20 @@ __global__ void __launch_bounds__(192) apply_factor_kernel(const ApplyJob* jobs,
 #pragma unroll
         for (int q = 0; q < QB; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
         for (int p = 0; p < J.k; ++p) {
-            const double2 ud = work[J.src + row + (int64_t)p * J.src_ld];
-            const float urh = __double2float_rn(ud.x), uih = __double2float_rn(ud.y);
-            const float url = __double2float_rn(ud.x - (double)urh);
-            const float uil = __double2float_rn(ud.y - (double)uih);
+            float urh, uih, url, uil;
+            if (HAS_DF) {
+                const float4 u = work_df[J.src + row + (int64_t)p * J.src_ld];  // (re_h, im_h, re_l, im_l)
+                urh = u.x;
+                uih = u.y;
+                url = u.z;
+                uil = u.w;
+            } else {
+                const double2 ud = work[J.src + row + (int64_t)p * J.src_ld];
+                urh = __double2float_rn(ud.x);
+                uih = __double2float_rn(ud.y);
+                url = __double2float_rn(ud.x - (double)urh);
+                uil = __double2float_rn(ud.y - (double)uih);
+            }
 #pragma unroll
             for (int q = 0; q < QB; ++q)
                 if (q0 + q < J.r) {
@@ -574,12 +589,13 @@ void* recompress_core(const std::vector<int64_t>& u_off, const std::vector<int64
 
 // Applies T_U / T_V to the factors and writes the chunks.  items: for every
 // (job, leaf) pair: (job, which: 0 = U / 1 = V, first row in the factor, rows,
-// arena offset, ld).
+// arena offset, ld).  d_work_df: the double-float copy of d_work (same
+// offsets), or null.
 void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
                       const std::vector<int32_t>& which, const std::vector<int64_t>& row0,
                       const std::vector<int32_t>& rows, const std::vector<int64_t>& dst,
                       const std::vector<int32_t>& ld, const std::vector<int32_t>& ranks,
-                      const double2* d_work, float2* d_out, cudaStream_t st) {
+                      const double2* d_work, const float4* d_work_df, float2* d_out, cudaStream_t st) {
     RecompBatch* B = (RecompBatch*)batch;
     std::vector<ApplyJob> aj;
     aj.reserve(job_of.size());
@@ -610,8 +626,12 @@ void recompress_apply(void* batch, const std::vector<int64_t>& job_of,
         ApplyJob* d = nullptr;
         HM_CUDA(cudaMallocAsync((void**)&d, aj.size() * sizeof(ApplyJob), st));
         HM_CUDA(cudaMemcpyAsync(d, aj.data(), aj.size() * sizeof(ApplyJob), cudaMemcpyHostToDevice, st));
-        apply_factor_kernel<<<(unsigned)aj.size(), 192, 0, st>>>(
-            d, d_work, reinterpret_cast<const float4*>(B->d_scratch), d_out);
+        if (d_work_df)
+            apply_factor_kernel<true><<<(unsigned)aj.size(), 192, 0, st>>>(
+                d, d_work, d_work_df, reinterpret_cast<const float4*>(B->d_scratch), d_out);
+        else
+            apply_factor_kernel<false><<<(unsigned)aj.size(), 192, 0, st>>>(
+                d, d_work, nullptr, reinterpret_cast<const float4*>(B->d_scratch), d_out);
         HM_LAUNCHED();
         HM_CUDA(cudaGetLastError());
         HM_CUDA(cudaFreeAsync(d, st));
