@@ -64,18 +64,18 @@ def kernel_profile(kernel_file, kernel_name):
     return d if d and d.get("source_sha256") == h else None
 
 
-def kernel_traffic(kernel_file, kernel_name):
+def kernel_traffic(kernel_file, kernel_name, alg_bytes=None):
     """DRAM bytes per launch from a committed ncu summary, only if the kernel
-    source is unchanged since the capture (sha256 of the .cu file)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1706_09384_gb300", "csrc", kernel_file)
-    if not os.path.exists(p) or not os.path.exists(src):
-        return None
-    d = json.load(open(p)).get(kernel_name)
+    source is unchanged since the capture (sha256 of the .cu file): the
+    recorded DRAM bytes per algorithmic byte of the captured launch times this
+    launch's algorithmic bytes (the captured case is smaller than the bench's
+    where a full-size capture would hold too much device memory)."""
+    d = kernel_profile(kernel_file, kernel_name)
     if not d:
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return d.get("bytes_per_launch") if d.get("source_sha256") == h else None
+    if "dram_per_alg_byte" in d and alg_bytes:
+        return d["dram_per_alg_byte"] * alg_bytes
+    return d.get("bytes_per_launch")
 
 
 class ClockSampler:
@@ -384,7 +384,7 @@ def run_gpu(args, wl, world, rank, local):
     kname = "mv16s_kernel<2>" if form == "mixed" else "mv_phase2"
     roof_mv = {"bound": "hbm", "kernel": kname, "achieved": ph2, "peak": peak,
                "peak_kind": peak_kind, "unit": "GB/s", "frac": ph2 / peak,
-               "traffic": kernel_traffic("matvec.cu", kname),
+               "traffic": kernel_traffic("matvec.cu", kname, prof["bytes"]["phase2"]),
                "alg_bytes_per_launch": prof["bytes"]["phase2"],
                "ms_per_launch": prof["ms"]["phase2"], "kernels_ms": prof["ms"]}
     # the product for a block of 32 right-hand sides on the tensor cores (mixed form)
