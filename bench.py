@@ -521,12 +521,48 @@ def run_gpu(args, wl, world, rank, local):
         out["fp32_far_green"] = fp32_switch_build(hm, torch, pts, weights, mat, wl, opts_kw={
             "weights": weights, "rank_model": model,
             "storage": hm.HM_STORE_BF16 if form == "mixed" else hm.HM_STORE_FP32})
+        out["mixed_vs_plain_T"] = mixed_vs_plain_T(hm, torch, pts, weights, mat, wl, model, tune_cache, x)
         out["multi_rhs_131072_T"] = multi_rhs_workload(hm, torch, dev, peak)
         out["batch_16_problems"] = batch_workload(hm, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def mixed_vs_plain_T(hm, torch, pts, weights, mat, wl, model, tune_cache, x):
+    """Mixed against plain form at equal GMRES residual 1e-6 on the same sphere
+    with the traction kernel T (normals of the sphere), where GMRES needs tens of
+    iterations: the fast products dominate the solve, the refinement's accurate
+    products are diluted."""
+    from paper_1706_09384_gb300 import inputs
+    rho, lam, mu, om = mat
+    nrm = inputs.sphere_normals(pts)
+    res = {"kernel": "T", "n_c": wl["nc"], "kappa_s": wl["ks"], "eps": wl["eps"]}
+    st = torch.cuda.current_stream()
+    y = torch.empty_like(x)
+    for name, opts in (("mixed", hm.hm_opts_default(weights=weights, rank_model=model, tune_cache=tune_cache,
+                                                    storage=hm.HM_STORE_BF16)),
+                       ("plain", hm.hm_opts_default(weights=weights, tune_cache=tune_cache))):
+        H = hm.HMatrix.build(pts, nrm, rho, lam, mu, om, "T", wl["eps"], wl["eta"], wl["leaf"], opts=opts)
+        for _ in range(3):
+            H.matvec(x, y)
+        H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)  # warm-up solve
+        m0, m1, g0, g1 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        m0.record(st)
+        for _ in range(10):
+            H.matvec(x, y)
+        m1.record(st)
+        g0.record(st)
+        _, it, rr, _ = H.gmres(x, restart=100, tol=1e-6, maxit=2000, check=False)
+        g1.record(st)
+        torch.cuda.synchronize()
+        res[name] = {"matvec_ms": m0.elapsed_time(m1) / 10, "gmres": {"iters": it, "relres": rr,
+                     "ms": g0.elapsed_time(g1), "products": H.stats()["gmres_last"]}}
+        H.free()
+    res["matvec_speedup"] = res["plain"]["matvec_ms"] / res["mixed"]["matvec_ms"]
+    res["gmres_speedup_at_1e-6"] = res["plain"]["gmres"]["ms"] / res["mixed"]["gmres"]["ms"]
+    return res
 
 
 def fp32_switch_build(hm, torch, pts, weights, mat, wl, opts_kw):

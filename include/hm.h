@@ -248,8 +248,13 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
 /* Solves A_H x = b by restarted GMRES(restart) with x_0 = 0 in FP64 vectors
  * (Arnoldi by classical Gram-Schmidt with one re-orthogonalisation, complex
  * Givens rotations), stopping when the true relative residual
- * ||b - A_H x|| / ||b|| <= tol (checked at each restart) or after maxit
- * matvecs.  b, x: DEVICE complex128, length 3 n_c, original order.
+ * ||b - A_H x|| / ||b|| <= tol (checked at each restart with the accurate
+ * product) or after maxit matvecs.  With BF16 storage each restart cycle is a
+ * step of iterative refinement: its Arnoldi iteration (BF16 products) stops at
+ * max(tol ||b||, delta ||r|| / 2), r the cycle's true starting residual and
+ * delta the BF16 product's relative accuracy (1e-4 until a cycle measures a
+ * worse one), since the true residual cannot follow the BF16 operator further.
+ * b, x: DEVICE complex128, length 3 n_c, original order.
  *   iters, relres: host outputs (may be NULL).
  * Errors: HM_ERR_ARG, HM_ERR_NOCONV (maxit reached; x holds the last iterate),
  * HM_ERR_TIMEOUT (see hm_matvec), HM_ERR_CUDA. */
@@ -259,8 +264,9 @@ hm_status hm_gmres(hm_handle h, const void* b, void* x, int32_t restart, double 
 /* hm_gmres for nrhs right-hand sides at once: one restarted GMRES per column,
  * run in lockstep so that each Arnoldi step makes one product of all columns
  * (the tensor-core block product when the storage is BF16).  A column whose
- * residual estimate reaches tol stops for the rest of its cycle; restarts use
- * the accurate product per column (iterative refinement).
+ * residual estimate reaches its cycle's threshold (as hm_gmres) stops for the
+ * rest of its cycle; restarts use the accurate product per column (iterative
+ * refinement).
  *   b, x    DEVICE complex128, 3 n_c x nrhs column-major, original order; no overlap
  *   iters   HOST int32[nrhs] or NULL: products made until each column converged
  *   relres  HOST double[nrhs] or NULL: final true relative residual per column
