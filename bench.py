@@ -88,14 +88,28 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.gpu = gpu_index
         self.p = None
+        self.skip = 0
 
     def __enter__(self):
+        # the sampler is started and its first sample awaited before the timed
+        # region begins: nvidia-smi's start-up (driver and NVML initialisation)
+        # then cannot stall the timed work; that first sample is not counted
+        self.skip = 0
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        if self.p:
+            t0 = time.time()
+            while time.time() - t0 < 10.0 and self.p.poll() is None:
+                self.f.flush()
+                with open(self.f.name) as g:
+                    self.skip = sum(1 for _ in g)
+                if self.skip:
+                    break
+                time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
@@ -110,9 +124,9 @@ class ClockSampler:
         self.f.flush()
         rows = []
         try:
-            for line in open(self.f.name):
+            for q, line in enumerate(open(self.f.name)):
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
+                if q >= self.skip and len(parts) >= 9:
                     rows.append(parts)
         finally:
             os.unlink(self.f.name)
