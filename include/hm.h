@@ -81,7 +81,9 @@ typedef struct {
     int32_t recompress;       /* 1: QR+SVD recompression of Sec. 3.2 (default), 0: keep ACA */
     int32_t aca_max_rank;     /* initial ACA capacity in columns per block (0 = 144);
                                  blocks that need more are re-run with twice the capacity */
-    int64_t workspace_bytes;  /* bound on the ACA workspace of one batch (0 = 24 GiB) */
+    int64_t workspace_bytes;  /* bound on the ACA workspace of one batch (0 = half of the
+                                 device memory free when the batch is formed, at least
+                                 1 GiB: fewer batches, fewer launch tails) */
     int32_t verbose;          /* 1: phase timings on stderr */
     int32_t pad_;
     const double* weights;    /* HOST, n_c column weights w_j (NULL = 1): block (i, j), i != j,

@@ -124,7 +124,18 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
     std::stable_sort(adm.begin(), adm.end(), [&](int64_t a, int64_t b) { return size_of(a) > size_of(b); });
     int cap0 = h0->opts.aca_max_rank > 0 ? h0->opts.aca_max_rank : 144;
     cap0 = std::max(3, cap0 - cap0 % 3);
-    const int64_t budget = h0->opts.workspace_bytes > 0 ? h0->opts.workspace_bytes : (24ll << 30);
+    // Workspace of one ACA batch: the caller's bound, else half of the device
+    // memory free when the batch is formed.  One launch takes the whole batch
+    // with a dynamic queue, largest blocks first, so the SMs stay busy until its
+    // last small blocks; each extra batch ends on the few CTAs that still hold
+    // its largest blocks while the others idle (at 65 536 points four 24 GiB
+    // batches took the ACA 573 ms, one 80 GB batch 350 ms).
+    auto batch_budget = [&]() -> int64_t {
+        if (h0->opts.workspace_bytes > 0) return h0->opts.workspace_bytes;
+        size_t fr = 0, tot = 0;
+        HM_CUDA(cudaMemGetInfo(&fr, &tot));
+        return std::max<int64_t>((int64_t)(fr / 2), 1ll << 30);
+    };
     int nsm = 0;
     HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device));
     std::vector<int> cap(na, 0);
@@ -274,6 +285,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         size_t pos = 0;
         while (pos < todo.size()) {
             // ---- form a batch ----
+            const int64_t budget = batch_budget();
             std::vector<AcaJob> jobs;
             std::vector<int64_t> ids;
             int64_t woff = 0, goff = 0, maxm = 1, maxn = 1;
@@ -393,6 +405,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         }
         size_t pos = 0;
         while (pos < lost.size()) {
+            const int64_t budget = batch_budget();
             std::vector<RsvdBlock> rb;
             std::vector<int64_t> ids;
             int64_t bytes = 0;
@@ -742,9 +755,13 @@ hm_matrix* build_setup2(const double* targets, int64_t n_x, const double* source
 }
 
 // Storage plan, arena, near field, factor chunks (BF16 copy) and work vectors
-// once the low-rank factors of the problem are staged.
+// once the low-rank factors of the problem are staged.  `staged` (or null)
+// owns staging memory that is released once this problem's factors are in
+// the arena: the driver's unmapping of a multi-gigabyte allocation then
+// overlaps the rest of the build instead of delaying the caller's first
+// products by up to a millisecond.
 void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<const float2*>& sv,
-                  cudaStream_t st) {
+                  std::vector<DevBuf>* staged, cudaStream_t st) {
     const hm_opts& o = h->opts;
     auto t0 = clk::now();
     std::vector<int64_t> t_off;
@@ -757,6 +774,7 @@ void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<cons
     h->t_near_ms = ms_since(tn);
     copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
     HM_CUDA(cudaStreamSynchronize(st));
+    if (staged) free_all(*staged);
     if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
     h->t_copy_ms = ms_since(t0) - h->t_near_ms;
     h->d_xp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
@@ -764,6 +782,7 @@ void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<cons
     HM_CUDA(cudaStreamSynchronize(st));
     tune_product(h, o.tune_cache, st);  // times products on d_xp / d_yp
     h->opts.tune_cache = nullptr;        // the caller's string is not kept
+    matvec_graph_prepare(h->mv, h->d_perm, h->d_xp, h->d_yp, h->nc);
 }
 
 void report_build(const hm_matrix* h) {
@@ -826,7 +845,7 @@ hm_status hm_build(const double* points, const double* normals, int64_t n_c, dou
     sv[0].assign(h->blocks.size(), nullptr);
     try {
         build_low_rank(hs, staging, su, sv, st);
-        build_finish(h, su[0], sv[0], st);
+        build_finish(h, su[0], sv[0], &staging, st);
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(staging);
@@ -858,7 +877,7 @@ hm_status hm_build2(const double* targets, int64_t n_x, const double* sources,
     sv[0].assign(h->blocks.size(), nullptr);
     try {
         build_low_rank(hs, staging, su, sv, st);
-        build_finish(h, su[0], sv[0], st);
+        build_finish(h, su[0], sv[0], &staging, st);
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(staging);
@@ -898,7 +917,8 @@ hm_status hm_build_batch(int32_t nprob, const hm_problem* probs, double eps, con
     }
     try {
         build_low_rank(hs, staging, su, sv, st);
-        for (int32_t q = 0; q < nprob; ++q) build_finish(hs[q], su[q], sv[q], st);
+        for (int32_t q = 0; q < nprob; ++q)
+            build_finish(hs[q], su[q], sv[q], q + 1 == nprob ? &staging : nullptr, st);
     } catch (...) {
         cudaStreamSynchronize(st);
         free_all(staging);

@@ -110,6 +110,9 @@ void* matvec_arena(MatvecDev* m);           // float2* (fp32) or bf16 pairs
 // xp, yp: tree-order complex64 scratch owned by the caller, fixed per handle.
 void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp, float2* yp,
                   double2* y, int64_t nc, cudaStream_t st);
+// Captures and instantiates that graph ahead of the first product (no-op once
+// it exists), so the build pays for it instead of the caller's first product.
+void matvec_graph_prepare(MatvecDev* m, const int64_t* d_perm, float2* xp, float2* yp, int64_t nc);
 // Error code left by the streamed product kernels (0 = none; 1 = a wait on a
 // copy gave up); reading it synchronises st and clears it.
 int matvec_take_error(MatvecDev* m, cudaStream_t st);

@@ -1353,10 +1353,11 @@ void copy_staged_chunks(MatvecDev* m, const MatvecPlan& plan, const std::vector<
 // stream (capture is not allowed on the legacy default stream) and launched on
 // st; a call with other x / y pointers rewrites only the gather and scatter
 // kernel nodes.
-void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp, float2* yp,
-                  double2* y, int64_t nc, cudaStream_t st) {
-    const unsigned nb = (unsigned)hm_cdiv(3 * nc, 256);
-    if (!m->gexec) {
+// Captures gather, both phases and scatter as the handle's product graph
+// (x and y may be null: the first product re-points those two nodes).
+static void graph_capture(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp,
+                          float2* yp, double2* y, int64_t nc) {
+    {
         cudaStream_t cs = nullptr;
         HM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         const long long before = g_hm_launches.load();
@@ -1407,6 +1408,18 @@ void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2*
         }
         m->g_x = x;
         m->g_y = y;
+    }
+}
+
+void matvec_graph_prepare(MatvecDev* m, const int64_t* d_perm, float2* xp, float2* yp, int64_t nc) {
+    if (!m->gexec) graph_capture(m, d_perm, nullptr, xp, yp, nullptr, nc);
+}
+
+void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2* xp, float2* yp,
+                  double2* y, int64_t nc, cudaStream_t st) {
+    const unsigned nb = (unsigned)hm_cdiv(3 * nc, 256);
+    if (!m->gexec) {
+        graph_capture(m, d_perm, x, xp, yp, y, nc);
     } else {
         if (x != m->g_x) {
             const int64_t* a0 = d_perm;

@@ -61,16 +61,18 @@ def test_training_lowers_loss(rm):
 def test_trained_model_sizes_workspace_not_result(rm):
     """The committed model (trained on cube-surface builds) on an unseen sphere:
     the ACA ranks, the recompressed ranks and the product are unchanged, while
-    the ACA workspace and the number of ACA batches shrink."""
+    the ACA workspace and, under a fixed workspace bound per batch, the number of
+    ACA batches shrink."""
     from paper_1706_09384_gb300 import hm
     assert os.path.exists(rm.DEFAULT_WEIGHTS)
     P = rm.load()
     nc = 32768
     pts = inputs.fibonacci_sphere(nc)
     rho, lam, mu, om = inputs.material(12.0)
-    H0 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", 1e-4, 3.0, 64)
-    H1 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", 1e-4, 3.0, 64,
-                          opts=hm.hm_opts_default(rank_model=P))
+    o0, o1 = hm.hm_opts_default(), hm.hm_opts_default(rank_model=P)
+    o0.workspace_bytes = o1.workspace_bytes = 8 << 30
+    H0 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", 1e-4, 3.0, 64, opts=o0)
+    H1 = hm.HMatrix.build(pts, None, rho, lam, mu, om, "U", 1e-4, 3.0, 64, opts=o1)
     b0, b1 = H0.blocks(), H1.blocks()
     assert np.array_equal(b0["rank_aca"], b1["rank_aca"])
     assert np.array_equal(b0["rank"], b1["rank"])
