@@ -36,26 +36,9 @@ constexpr int AW = AT / 32;
 constexpr int ACA_CH = 256;         // rows of the new factor columns staged per chunk (step 6)
 constexpr double SING_REL = 1e-12;
 
-struct Cof {
-    double2 c[9];   // cofactor matrix, row-major
-    double2 det;
-};
-
-HM_D void cofactors(const double2 M[9], Cof& o) {
-    auto m = [&](int r, int c) { return M[3 * r + c]; };
-    auto minor2 = [&](int r0, int r1, int c0, int c1) {
-        return csub(cmul(m(r0, c0), m(r1, c1)), cmul(m(r0, c1), m(r1, c0)));
-    };
-    o.c[0] = minor2(1, 2, 1, 2);
-    o.c[1] = cscale(minor2(1, 2, 0, 2), -1.0);
-    o.c[2] = minor2(1, 2, 0, 1);
-    o.c[3] = cscale(minor2(0, 2, 1, 2), -1.0);
-    o.c[4] = minor2(0, 2, 0, 2);
-    o.c[5] = cscale(minor2(0, 2, 0, 1), -1.0);
-    o.c[6] = minor2(0, 1, 1, 2);
-    o.c[7] = cscale(minor2(0, 1, 0, 2), -1.0);
-    o.c[8] = minor2(0, 1, 0, 1);
-    o.det = cadd(cadd(cmul(M[0], o.c[0]), cmul(M[1], o.c[1])), cmul(M[2], o.c[2]));
+// A complex value from lane `src` of the first nine lanes of warp 0.
+HM_D double2 shfl9(double2 v, int src) {
+    return make_double2(__shfl_sync(0x1ffu, v.x, src), __shfl_sync(0x1ffu, v.y, src));
 }
 
 HM_D double2 minor2(const double2 M[9], int r0, int r1, int c0, int c1) {
@@ -106,14 +89,16 @@ HM_D void sv13(const double2 M[9], double& s1, double& s3) {
 }
 
 // FP32 estimate of (sigma_1, sigma_3) used to shortlist pivot candidates.  The
-// block is first scaled by its largest entry so that |det|^2 (~ sigma^6) stays
-// in the normal FP32 range for small residuals or weighted entries.
+// entries are truncated to FP32 on the integer pipes (a relative change below
+// 2^-23, far inside the shortlist margin); the block is then scaled by its
+// largest entry so that |det|^2 (~ sigma^6) stays in the normal FP32 range for
+// small residuals or weighted entries.
 HM_D void sv13f(const double2 Md[9], float& s1, float& s3) {
     float2 M[9];
     float amax = 0.f;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        M[q] = make_float2((float)Md[q].x, (float)Md[q].y);
+        M[q] = make_float2(f64_to_f32_rz_bits(Md[q].x), f64_to_f32_rz_bits(Md[q].y));
         amax = fmaxf(amax, fmaxf(fabsf(M[q].x), fabsf(M[q].y)));
     }
     if (!(amax > 0.f) || !(amax < 3.0e38f)) {  // zero, non-finite or NaN block
@@ -268,14 +253,19 @@ __device__ __forceinline__ void df_cmac_conj(float (&s)[4], float4 u, float4 v) 
     dfm(s[2], s[3], u.y, u.w, v.x, v.z);    // im += ui vr
     dfm(s[2], s[3], -u.x, -u.z, v.y, v.w);  // im -= ur vi
 }
+// The double-float copy of an FP64 value: hi = v truncated to FP32, lo = the
+// exact FP64 remainder truncated to FP32 (~46 significant bits in all), the
+// conversions on the integer pipes.
 __device__ __forceinline__ float4 df_of(double2 v) {
-    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+    const float rh = f64_to_f32_rz_bits(v.x), ih = f64_to_f32_rz_bits(v.y);
+    return make_float4(rh, ih, f64_to_f32_rz_bits(v.x - f32_to_f64_bits(rh)),
+                       f64_to_f32_rz_bits(v.y - f32_to_f64_bits(ih)));
 }
-// g -= s (the double-float sum, rounded to FP64 once)
+// g -= s, the double-float sum subtracted in FP64 part by part (the parts
+// converted on the integer pipes)
 __device__ __forceinline__ void sub_df(double2& g, const float (&s)[4]) {
-    g.x -= (double)s[0] + (double)s[1];
-    g.y -= (double)s[2] + (double)s[3];
+    g.x = (g.x - f32_to_f64_bits(s[0])) - f32_to_f64_bits(s[1]);
+    g.y = (g.y - f32_to_f64_bits(s[2])) - f32_to_f64_bits(s[3]);
 }
 
 // Step 6 of the ACA, one side: out[q] = sum over the nr rows of x conj(new_q)
@@ -437,7 +427,7 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
             }
             __syncthreads();
             // ---- step 1-2: row residual and sigma_3 pivot search ----
-            double best = -1.0, s1max = 0.0;
+            float bestf = -1.f, s1maxf = 0.f;  // the shortlist's bounds in FP32
             int64_t bj = -1;
             for (int64_t j = tid; j < n; j += AT) {
                 double2 G[9];
@@ -494,25 +484,26 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                 float s1f, s3f;
                 sv13f(G, s1f, s3f);
                 Rs[j] = make_float2(s1f, s3f);
-                s1max = fmax(s1max, (double)s1f);
+                s1maxf = fmaxf(s1maxf, s1f);
                 if (!ucol[j]) {
-                    const double lo = (double)s3f - SHORTLIST_REL * (double)s1f;
-                    if (lo > best || (bj < 0 && lo == lo)) {
-                        best = lo;
+                    const float lo = s3f - SHORTLIST_REL * s1f;
+                    if (lo > bestf || (bj < 0 && lo == lo)) {
+                        bestf = lo;
                         bj = j;
                     }
                 }
             }
+            double best = bestf, s1max = s1maxf;
             block_argmax(best, bj, s1max, red);  // best = largest lower bound
             {
                 // FP64 sigma_3 on the shortlist; exact argmax with ties to the lowest j
-                const double lstar = best;
+                const float lstar = (float)best;  // an FP32 value (exact)
                 double b64 = -1.0, dummy = 0.0;
                 int64_t j64 = -1;
                 for (int64_t j = tid; j < n; j += AT) {
                     if (ucol[j]) continue;
                     const float2 sf = Rs[j];
-                    if (!((double)sf.y + SHORTLIST_REL * (double)sf.x >= lstar)) continue;
+                    if (!(sf.y + SHORTLIST_REL * sf.x >= lstar)) continue;
                     double2 G[9];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -563,21 +554,22 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                 continue;
             }
             const int64_t jhat = s_jhat;
-            if (tid == 0) {
-                double2 P[9];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) P[3 * a + c] = R[a * n3 + 3 * jhat + c];
-                Cof cf;
-                cofactors(P, cf);
-                // inverse = adj / det, adj = cofactor^T
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) s_gam[3 * a + c] = cdiv(cf.c[3 * c + a], cf.det);
-                urow[ihat] = 1;
-                ucol[jhat] = 1;
+            if (tid < 9) {
+                // gamma = R(i^, j^)^-1 = adj / det (adj = cofactor^T): lane q < 9
+                // forms cofactor q, then the inverse entry q from cofactor 3 c + a
+                const int q = tid, r = q / 3, c = q % 3;
+                const int r0 = r == 0 ? 1 : 0, r1 = r == 2 ? 1 : 2;
+                const int c0 = c == 0 ? 1 : 0, c1 = c == 2 ? 1 : 2;
+                auto P = [&](int a, int b) { return R[a * n3 + 3 * jhat + b]; };
+                double2 cof = csub(cmul(P(r0, c0), P(r1, c1)), cmul(P(r0, c1), P(r1, c0)));
+                if ((r + c) & 1) cof = cscale(cof, -1.0);
+                const double2 det = cadd(cadd(cmul(P(0, 0), shfl9(cof, 0)), cmul(P(0, 1), shfl9(cof, 1))),
+                                         cmul(P(0, 2), shfl9(cof, 2)));
+                s_gam[q] = cdiv(shfl9(cof, 3 * c + r), det);
+                if (q == 0) {
+                    urow[ihat] = 1;
+                    ucol[jhat] = 1;
+                }
             }
             for (int t = tid; t < 3 * k; t += AT) {
                 const int c = t / k, p = t - c * k;
@@ -588,7 +580,8 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
             }
             __syncthreads();
             // ---- step 3-4: column residual and next row ----
-            double bestr = -1.0, unused = 0.0;
+            float bestrf = -1.f;
+            double unused = 0.0;
             int64_t bi = -1;
             for (int64_t i = tid; i < m; i += AT) {
                 double2 G[9];
@@ -644,22 +637,23 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                     float s1f, s3f;
                     sv13f(G, s1f, s3f);
                     Cs[i] = make_float2(s1f, s3f);
-                    const double lo = (double)s3f - SHORTLIST_REL * (double)s1f;
-                    if (lo > bestr || (bi < 0 && lo == lo)) {
-                        bestr = lo;
+                    const float lo = s3f - SHORTLIST_REL * s1f;
+                    if (lo > bestrf || (bi < 0 && lo == lo)) {
+                        bestrf = lo;
                         bi = i;
                     }
                 }
             }
+            double bestr = bestrf;
             block_argmax(bestr, bi, unused, red);
             {
-                const double lstar = bestr;
+                const float lstar = (float)bestr;
                 double b64 = -1.0;
                 int64_t i64 = -1;
                 for (int64_t i = tid; i < m; i += AT) {
                     if (urow[i]) continue;
                     const float2 sf = Cs[i];
-                    if (!((double)sf.y + SHORTLIST_REL * (double)sf.x >= lstar)) continue;
+                    if (!(sf.y + SHORTLIST_REL * sf.x >= lstar)) continue;
                     double2 G[9];
 #pragma unroll
                     for (int q = 0; q < 9; ++q) G[q] = C[9 * i + q];

@@ -70,6 +70,30 @@ HM_HD void cffma_conja(float2& acc, float2 a, float2 b) {
     acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
 }
 
+// ---- FP32 <-> FP64 on the integer pipes ----
+// GB300 issues FP32/FP64 conversions on its narrow FP64 unit; moving the
+// exponent and mantissa fields with integer operations leaves that unit free.
+// FP32 -> FP64, exact like the conversion instruction; zero keeps its sign,
+// subnormal, infinite and NaN inputs take the conversion.
+HM_D double f32_to_f64_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t sgn = (uint64_t)(b >> 31) << 63;
+    if (e == 0u || e == 0xffu) return (b & 0x7fffffffu) ? (double)f : __longlong_as_double((long long)sgn);
+    return __longlong_as_double(
+        (long long)(sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
+}
+// FP64 -> FP32 rounded toward zero (the mantissa truncated to 23 bits) where
+// the exponent lies in FP32's normal range; zero, values outside that range,
+// infinities and NaN take the conversion (rounded to nearest).
+HM_D float f64_to_f32_rz_bits(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+    if (e < 897u || e > 1150u) return __double2float_rn(d);
+    return __uint_as_float(((uint32_t)(b >> 63) << 31) | ((e - 896u) << 23) |
+                           ((uint32_t)(b >> 29) & 0x7fffffu));
+}
+
 // ---- reductions ----
 HM_D double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -82,7 +82,7 @@ HM_D void helmholtz_derivs_f(double k, double r, float ir, float2 g[4]) {
 HM_D float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 HM_D float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 HM_D float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-HM_D double2 f2d(float2 a) { return make_double2((double)a.x, (double)a.y); }
+HM_D double2 f2d(float2 a) { return make_double2(f32_to_f64_bits(a.x), f32_to_f64_bits(a.y)); }
 
 // The same closed forms as green_tensor below, in FP32 (r and the direction
 // from FP64 differences of the coordinates).

@@ -249,17 +249,6 @@ __device__ __forceinline__ void df_warp_sum2(float h0, float l0, float h1, float
     for (int o = 8; o > 0; o >>= 1)
         df_merge(oh, ol, __shfl_xor_sync(0xffffffffu, oh, o), __shfl_xor_sync(0xffffffffu, ol, o));
 }
-// FP32 -> FP64 by moving the fields (exact, like the conversion instruction),
-// on the integer pipes: GB300 issues FP32/FP64 conversions on its narrow FP64
-// unit.  Zero, subnormal, infinite and NaN inputs take the conversion.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xffu;
-    const uint64_t sgn = (uint64_t)(b >> 31) << 63;
-    if (e == 0u || e == 0xffu) return (b & 0x7fffffffu) ? (double)f : __longlong_as_double((long long)sgn);
-    return __longlong_as_double(
-        (long long)(sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
-}
 // complex128 -> (re_hi, im_hi, re_lo, im_lo)
 __device__ __forceinline__ float4 df_split(double2 v) {
     const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
