@@ -263,6 +263,20 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate (no measured FP64 peak 
 # 128 FP32 lanes per SM, and the FP64 rate above as 2 DFMA per SM and clock
 FP32_INST_PER_S = 152 * 128 * 2.07e9
 FP64_DFMA_PER_S = FP64_PEAK_TFLOPS * 1e12 / 2.0
+# FP64 instructions of one Green's tensor evaluation in FP64 (green.cuh, with the
+# column weights), counted from the source: every FP64 add, multiply and fused
+# multiply-add once, products and sums fused wherever the source allows, and the
+# square root, the divisions and each sine/cosine call once (they expand to more
+# instructions), so a lower bound.  U: distance and direction 13, the two
+# Helmholtz derivative sets 58, F 8, psi and chi 11, the nine entries 24, the
+# weights 18; T: the same up to psi and chi, then the derivatives of psi and chi,
+# the three coefficients and the nine entries 126, the weights 18.
+GREEN_FP64_INST = {"U": 132, "T": 234}
+# FP64 instructions of the ACA per Green's tensor evaluation besides the tensor:
+# the residual's nine double-float sums subtracted part by part (4 adds per
+# complex entry) and the double-float copies of the new factor entries of that
+# point (9 per point and rank-3 step, one subtraction per real part)
+ACA_FP64_PER_EVAL = 9 * 4 + 9 * 2
 
 
 def dense_rows(hm, kernel, mat, pts_t, nrm_t, w_t, pidx, X):
@@ -338,7 +352,7 @@ def run_gpu(args, wl, world, rank, local):
     alg = stats["matvec_alg_bytes"]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     build_ms, mv_ms, gm_ms, gm_it, gm_rr, aca_ms, rec_ms, aca_fl = [], [], [], [], [], [], [], []
-    aca_fl64, aca_fldf = [], []
+    aca_fl64, aca_fldf, aca_ev = [], [], []
     gm_prod = []
     launches0 = hm.hm_kernel_launches()
     barrier(world)
@@ -373,6 +387,7 @@ def run_gpu(args, wl, world, rank, local):
             aca_fl.append(sd["aca_flops"])
             aca_fl64.append(sd["aca_flops_fp64"])
             aca_fldf.append(sd["aca_flops_df"])
+            aca_ev.append(sd["aca_green_evals"])
             gm_prod.append(sd["gmres_last"])
         t_end = ev()
         t_end.record(st)
@@ -419,28 +434,42 @@ def run_gpu(args, wl, world, rank, local):
     aca_t = statistics.mean(aca_ms)
     per_step = {"aca_kernel": aca_t, "recompression": statistics.mean(rec_ms),
                 "h_matvec": statistics.mean(mv_ms), "gmres": statistics.mean(gm_ms)}
-    # ALU roofline of the ACA.  Its arithmetic runs on two pipes: double-float
-    # multiply-adds on the FP32 pipes (residuals, norm-update cross terms, Gram
-    # blocks) and FP64 (factor columns).  t_min = the time both shares take at
-    # their pipes' peak rates (a double-float complex multiply-add = 48 FP32
-    # instructions, an FP64 one = 4 DFMA); frac = t_min / the measured time.
+    # ALU roofline of the ACA.  Its arithmetic runs on two pipes that work side
+    # by side: the FP32 pipes take the double-float multiply-adds (residuals,
+    # norm-update cross terms, Gram blocks: 48 FP32 instructions per complex
+    # multiply-add), the FP64 pipe the Green's tensors, the residual's rounding,
+    # the double-float copies and the factor columns (4 DFMA per complex
+    # multiply-add).  Each pipe's minimum time at its nominal rate; the kernel
+    # can be no faster than the busier pipe, so t_min = max of the two and
+    # frac = t_min / the measured time (each pipe's own fraction beside it).
     f64 = statistics.mean(aca_fl64)
     fdf = statistics.mean(aca_fldf)
-    t_min = (fdf / 8.0 * 48.0) / FP32_INST_PER_S + (f64 / 8.0 * 4.0) / FP64_DFMA_PER_S
+    evals = statistics.mean(aca_ev)
+    fp64_inst = evals * (GREEN_FP64_INST[wl["kernel"]] + ACA_FP64_PER_EVAL) + f64 / 8.0 * 4.0
+    t32 = (fdf / 8.0 * 48.0) / FP32_INST_PER_S
+    t64 = fp64_inst / FP64_DFMA_PER_S
+    t_min = max(t32, t64)
     t_aca = aca_t * 1e-3
     prof_aca = kernel_profile("aca.cu", "aca_kernel")
     roofline = {"bound": "alu", "kernel": "aca_kernel", "achieved": (f64 + fdf) / t_aca / 1e12,
                 "peak": (f64 + fdf) / t_min / 1e12, "peak_kind": "derived: nominal unit counts "
-                "and clock (152 SMs x 128 FP32 lanes, 2 DFMA per SM and clock, 2.07 GHz)",
+                "and clock (152 SMs x 128 FP32 lanes, 2 DFMA per SM and clock, 2.07 GHz); "
+                "the busier pipe's minimum time",
                 "unit": "TFLOP/s", "frac": t_min / t_aca,
+                "pipes": {"fp32": {"t_min_ms": 1e3 * t32, "frac": t32 / t_aca,
+                                   "work": "double-float multiply-adds, 48 FP32 instructions each"},
+                          "fp64": {"t_min_ms": 1e3 * t64, "frac": t64 / t_aca,
+                                   "instructions": fp64_inst, "green_evals": evals,
+                                   "per_eval": GREEN_FP64_INST[wl["kernel"]] + ACA_FP64_PER_EVAL}},
                 "traffic": (prof_aca["bytes_per_model_flop"] * (f64 + fdf)) if prof_aca else None,
                 "alg_fp64_flops_per_launch": f64, "double_float_flops_per_launch": fdf,
                 "ms_per_step": aca_t, "t_min_ms": 1e3 * t_min, "profile": prof_aca,
-                "note": "ACA device time per build (all batches); model flops per rank-3 step: "
-                        "double-float 9k(m+n) residuals + 9k(m+n) cross terms + 27(m+n) Gram "
-                        "blocks, FP64 27m factor columns (complex multiply-adds, 8 flops each); "
-                        "traffic = the ncu DRAM bytes per model flop of the committed "
-                        "16384-point capture times this launch's model flops"}
+                "note": "ACA device time per build; model per rank-3 step: double-float 9k(m+n) "
+                        "residuals + 9k(m+n) cross terms + 27(m+n) Gram blocks (FP32 pipes), "
+                        "m+n FP64 Green's tensors with the residual rounding and the factor "
+                        "copies, FP64 27m factor columns (FP64 pipe); the flops count 8 per "
+                        "complex multiply-add; traffic = the ncu DRAM bytes per model flop of "
+                        "the committed 16384-point capture times this launch's model flops"}
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     xh = torch.empty(3 * wl["nc"], dtype=torch.complex128).pin_memory()
     xh.copy_(x.cpu())

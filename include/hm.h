@@ -82,8 +82,11 @@ typedef struct {
     int32_t aca_max_rank;     /* initial ACA capacity in columns per block (0 = 144);
                                  blocks that need more are re-run with twice the capacity */
     int64_t workspace_bytes;  /* bound on the ACA workspace of one batch (0 = half of the
-                                 device memory free when the batch is formed, at least
-                                 1 GiB: fewer batches, fewer launch tails) */
+                                 device memory free when the batch is formed, counting
+                                 what the library's pool holds for reuse, at least 1 GiB:
+                                 fewer batches, fewer launch tails).  The workspace comes
+                                 from that pool and stays reserved after the build (see
+                                 hm_release_cached_memory) */
     int32_t verbose;          /* 1: phase timings on stderr */
     int32_t pad_;
     const double* weights;    /* HOST, n_c column weights w_j (NULL = 1): block (i, j), i != j,
@@ -485,6 +488,18 @@ hm_status hm_profile_matvec_multi(hm_handle h, int32_t reps, double* ms, int64_t
 
 /* Number of CUDA kernels this library has launched since it was loaded. */
 int64_t hm_kernel_launches(void);
+
+/* Returns to the device the memory that the library's stream-ordered pools
+ * hold for reuse: the scratch of hm_gmres / hm_gmres_multi and the build
+ * workspaces of hm_build / hm_build2 / hm_build_batch (the ACA factors with
+ * their double-float copies, half of the free device memory at most per batch,
+ * and the staged factors), which stay reserved after a call so that the next
+ * build or solve on any handle reuses them without allocating.  A build that
+ * runs short of device memory returns them by itself first.  Call it with no
+ * library work in flight (memory still used by queued work stays reserved).
+ * Handles and their H-matrices are not affected.
+ * Errors: HM_ERR_CUDA. */
+hm_status hm_release_cached_memory(void);
 
 void hm_free(hm_handle h);
 const char* hm_status_string(hm_status s);

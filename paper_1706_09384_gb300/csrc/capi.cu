@@ -31,9 +31,22 @@ void hm_check_cuda(cudaError_t e, const char* what, const char* file, int line) 
 
 void* hm_dmalloc(std::vector<DevBuf>& owner, size_t bytes, cudaStream_t st, bool zero) {
     void* p = nullptr;
-    HM_CUDA(cudaMalloc(&p, bytes ? bytes : 16));
+    if (cudaMalloc(&p, bytes ? bytes : 16) == cudaErrorMemoryAllocation) {
+        // memory the library's pool keeps for later builds and solves goes back first
+        cudaGetLastError();
+        HM_CUDA(cudaDeviceSynchronize());
+        hm_scratch_trim();
+        HM_CUDA(cudaMalloc(&p, bytes ? bytes : 16));
+    }
+    HM_CUDA(cudaGetLastError());
     owner.push_back({p, bytes});
     if (zero && bytes) HM_CUDA(cudaMemsetAsync(p, 0, bytes, st));
+    return p;
+}
+
+void* hm_dmalloc_pooled(std::vector<DevBuf>& owner, size_t bytes, cudaStream_t st) {
+    void* p = hm_scratch_alloc(bytes, st);
+    owner.push_back({p, bytes, true, st});
     return p;
 }
 
@@ -63,7 +76,12 @@ double ms_since(clk::time_point t0) {
 
 void free_all(std::vector<DevBuf>& owner) {
     for (DevBuf& d : owner)
-        if (d.p) cudaFree(d.p);
+        if (d.p) {
+            if (d.pooled)
+                hm_scratch_free(d.p, d.st);
+            else
+                cudaFree(d.p);
+        }
     owner.clear();
 }
 
@@ -134,7 +152,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         if (h0->opts.workspace_bytes > 0) return h0->opts.workspace_bytes;
         size_t fr = 0, tot = 0;
         HM_CUDA(cudaMemGetInfo(&fr, &tot));
-        return std::max<int64_t>((int64_t)(fr / 2), 1ll << 30);
+        return std::max<int64_t>((int64_t)((fr + hm_scratch_cached()) / 2), 1ll << 30);
     };
     int nsm = 0;
     HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device));
@@ -217,7 +235,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         d_gps = dg;
     }
     double ev_aca = 0, t_aca = 0, ev_rec = 0, t_rec = 0, flops = 0, flops64 = 0, flops_df = 0,
-           evals = 0;
+           evals = 0, flops_apply = 0;
     int64_t batches = 0, reruns = 0, ws_peak = 0, ws_tot = 0;
     std::vector<int64_t> n_rsvd(nprob, 0), n_uncert(nprob, 0);
     double t_rsvd = 0;
@@ -243,7 +261,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 so[q] = tot;
                 tot += (m3[q] + n3[q]) * ranks[q];
             }
-            float2* d_stage = (float2*)hm_dmalloc(staging, std::max<int64_t>(tot, 1) * 8, st, false);
+            float2* d_stage = (float2*)hm_dmalloc_pooled(staging, std::max<int64_t>(tot, 1) * 8, st);
             std::vector<int64_t> job_of, row0, dst;
             std::vector<int32_t> which, rows, ldv;
             for (size_t q = 0; q < keep.size(); ++q) {
@@ -262,6 +280,8 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 }
             }
             recompress_apply(rb, job_of, which, row0, rows, dst, ldv, ranks, d_work, d_work_df, d_stage, st);
+            for (size_t q = 0; q < keep.size(); ++q)  // U' = U T_U, V' = V T_V in double-float
+                flops_apply += 8.0 * (double)(m3[q] + n3[q]) * kk[q] * ranks[q];
             ev_rec += er.stop(st);
             for (size_t q = 0; q < keep.size(); ++q) {
                 const int64_t a = ids[keep[q]];
@@ -322,9 +342,9 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
             const int nctas = (int)std::min<int64_t>(nj, (int64_t)nsm * aca_ctas_per_sm(capmax));
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
-            double2* d_work = (double2*)hm_dmalloc(tmp, (size_t)woff * 16, st, false);
-            float4* d_work_df = (float4*)hm_dmalloc(tmp, (size_t)woff * 16, st, false);
-            double2* d_gram = (double2*)hm_dmalloc(tmp, (size_t)goff * 16, st, false);
+            double2* d_work = (double2*)hm_dmalloc_pooled(tmp, (size_t)woff * 16, st);
+            float4* d_work_df = (float4*)hm_dmalloc_pooled(tmp, (size_t)woff * 16, st);
+            double2* d_gram = (double2*)hm_dmalloc_pooled(tmp, (size_t)goff * 16, st);
             AcaJob* d_jobs = (AcaJob*)hm_dmalloc(tmp, nj * sizeof(AcaJob), st, false);
             AcaResult* d_res = (AcaResult*)hm_dmalloc(tmp, nj * sizeof(AcaResult), st, false);
             const int64_t fstride = hm_round_up(maxm + maxn, 16);
@@ -473,6 +493,7 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
         h->aca_flops_fp64 += flops64;
         h->aca_flops_df += flops_df;
         h->aca_green_evals += evals;
+        h->apply_flops_df += flops_apply;
         h->aca_batches += batches;
         h->aca_overflow_reruns += reruns;
         h->aca_workspace_peak = std::max(h->aca_workspace_peak, ws_peak);
@@ -766,23 +787,37 @@ void build_finish(hm_matrix* h, std::vector<const float2*>& su, std::vector<cons
     auto t0 = clk::now();
     std::vector<int64_t> t_off;
     h->plan = build_matvec_plan(h->clusters, h->blocks, t_off);
+    h->t_plan_ms = ms_since(t0);
+    auto tp = clk::now();
     h->mv = matvec_dev_create(h->plan, o.storage, h->owner, st);
+    h->t_arena_ms = ms_since(tp);
     auto tn = clk::now();
     assemble_dense(h->gp, h->d_pts_p, h->d_nrm_p, h->plan, h->blocks, h->clusters, h->mv, h->owner,
                    st);
     HM_CUDA(cudaStreamSynchronize(st));
     h->t_near_ms = ms_since(tn);
+    auto tc = clk::now();
     copy_staged_chunks(h->mv, h->plan, h->blocks, h->clusters, su, sv, st);
     HM_CUDA(cudaStreamSynchronize(st));
     if (staged) free_all(*staged);
-    if (o.storage == HM_STORE_BF16) matvec_make_bf16(h->mv, h->plan, h->owner, st);
+    h->t_stage_ms = ms_since(tc);
+    tc = clk::now();
+    if (o.storage == HM_STORE_BF16) {
+        matvec_make_bf16(h->mv, h->plan, h->owner, st);
+        HM_CUDA(cudaStreamSynchronize(st));
+    }
+    h->t_bf16_ms = ms_since(tc);
     h->t_copy_ms = ms_since(t0) - h->t_near_ms;
     h->d_xp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
     h->d_yp = (float2*)hm_dmalloc(h->owner, 8 * 3 * h->nc, st, true);
     HM_CUDA(cudaStreamSynchronize(st));
+    tc = clk::now();
     tune_product(h, o.tune_cache, st);  // times products on d_xp / d_yp
     h->opts.tune_cache = nullptr;        // the caller's string is not kept
+    h->t_tune_ms = ms_since(tc);
+    tc = clk::now();
     matvec_graph_prepare(h->mv, h->d_perm, h->d_xp, h->d_yp, h->nc);
+    h->t_graph_ms = ms_since(tc);
 }
 
 void report_build(const hm_matrix* h) {
@@ -973,12 +1008,14 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
         h->d_yh = (double2*)hm_dmalloc(h->owner, (size_t)n * nrhs * 16, st, false);
         h->staging_cols = nrhs;
     }
+    PinnedInt flag;  // the product's error code, read back with y (one synchronisation)
     HM_CUDA(cudaMemcpyAsync(h->d_xh, x, (size_t)n * nrhs * 16, cudaMemcpyHostToDevice, st));
     const hm_status s = hm_matvec(h, nrhs, h->d_xh, h->d_yh, stream);
     if (s != HM_OK) return s;
     HM_CUDA(cudaMemcpyAsync(y, h->d_yh, (size_t)n * nrhs * 16, cudaMemcpyDeviceToHost, st));
+    matvec_queue_error(h->mv, flag.p, st);
     HM_CUDA(cudaStreamSynchronize(st));
-    if (matvec_take_error(h->mv, st))
+    if (matvec_read_error(h->mv, flag.p, st))
         hm_throw(HM_ERR_TIMEOUT, "a product kernel gave up waiting for its copies");
     HM_API_END
 }
@@ -1125,10 +1162,14 @@ hm_status hm_stats(hm_handle h, char* json, size_t cap, size_t* needed) {
        << ", \"aca\": " << h->t_aca_ms << ", \"recompress\": " << h->t_recomp_ms
        << ", \"rsvd\": " << h->t_rsvd_ms
        << ", \"near_field\": " << h->t_near_ms << ", \"layout\": " << h->t_copy_ms
+       << ", \"layout_plan\": " << h->t_plan_ms << ", \"layout_arena\": " << h->t_arena_ms
+       << ", \"layout_stage_copy\": " << h->t_stage_ms << ", \"layout_bf16\": " << h->t_bf16_ms
+       << ", \"tune\": " << h->t_tune_ms << ", \"graph\": " << h->t_graph_ms
        << ", \"total\": " << h->t_total_ms << "}"
        << ", \"device_ms\": {\"aca\": " << h->ev_aca_ms << ", \"recompress\": " << h->ev_recomp_ms
        << "}, \"aca_flops\": " << h->aca_flops << ", \"aca_flops_fp64\": " << h->aca_flops_fp64
        << ", \"aca_flops_df\": " << h->aca_flops_df << ", \"aca_green_evals\": " << h->aca_green_evals
+       << ", \"apply_flops_df\": " << h->apply_flops_df
        << ", \"tune\": {\"source\": \"" << h->tune_source << "\", \"key\": \"" << h->tune_key
        << "\", \"nstage\": " << h->tune_nstage << ", \"item_bytes\": " << h->tune_item_bytes
        << ", \"ms\": " << h->tune_ms << ", \"trials\": [" << h->tune_trials << "]}"
@@ -1399,6 +1440,12 @@ hm_status hm_profile_matvec_multi(hm_handle h, int32_t reps, double* ms, int64_t
 }
 
 int64_t hm_kernel_launches(void) { return (int64_t)g_hm_launches.load(); }
+
+hm_status hm_release_cached_memory(void) {
+    HM_API_BEGIN
+    hm_scratch_trim();
+    HM_API_END
+}
 
 void hm_free(hm_handle h) {
     if (!h) return;

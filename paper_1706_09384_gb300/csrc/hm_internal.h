@@ -25,20 +25,36 @@ void hm_check_cuda(cudaError_t e, const char* what, const char* file, int line);
 extern std::atomic<long long> g_hm_launches;
 #define HM_LAUNCHED() g_hm_launches.fetch_add(1, std::memory_order_relaxed)
 
-// Solver scratch (scratch.cu): stream-ordered allocations from the library's
-// per-device pool, which keeps freed memory for reuse; and small pinned host
-// buffers from a process-wide free list.
+// Solver and build scratch (scratch.cu): stream-ordered allocations from the
+// library's per-device pool, which keeps freed memory for reuse; and small
+// pinned host buffers from a process-wide free list.
 void* hm_scratch_alloc(size_t bytes, cudaStream_t st);
 void hm_scratch_free(void* p, cudaStream_t st);
+size_t hm_scratch_cached();  // bytes the current device's pool holds but does not use
+void hm_scratch_trim();      // returns every pool's unused memory to its device
 void* hm_pinned_take(size_t bytes);
 void hm_pinned_give(void* p);
+// One page-locked int from that free list, returned when it goes out of scope.
+struct PinnedInt {
+    int* p;
+    PinnedInt() : p((int*)hm_pinned_take(sizeof(int))) { *p = 0; }
+    ~PinnedInt() { hm_pinned_give(p); }
+    PinnedInt(const PinnedInt&) = delete;
+    PinnedInt& operator=(const PinnedInt&) = delete;
+};
 
 // Device allocation owned by the handle (freed in hm_free).
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool pooled = false;            // from the library's pool: freed on `st`, stays reserved
+    cudaStream_t st = nullptr;
 };
 void* hm_dmalloc(std::vector<DevBuf>& owner, size_t bytes, cudaStream_t st, bool zero);
+// The same from the library's stream-ordered pool (build workspaces: the ACA
+// factors, the staged factors): released on `st` by free_all, the memory
+// stays reserved for the next build until hm_release_cached_memory.
+void* hm_dmalloc_pooled(std::vector<DevBuf>& owner, size_t bytes, cudaStream_t st);
 
 // ---------------- tree + partition (tree.cu) ----------------
 struct TreeResult {
@@ -116,6 +132,11 @@ void matvec_graph_prepare(MatvecDev* m, const int64_t* d_perm, float2* xp, float
 // Error code left by the streamed product kernels (0 = none; 1 = a wait on a
 // copy gave up); reading it synchronises st and clears it.
 int matvec_take_error(MatvecDev* m, cudaStream_t st);
+// The same in two parts, so the readback shares the caller's synchronisation:
+// queue the copy of the code into page-locked `pinned` on st, then, once st has
+// synchronised, read it (a set code is cleared on st).
+void matvec_queue_error(MatvecDev* m, int* pinned, cudaStream_t st);
+int matvec_read_error(MatvecDev* m, const int* pinned, cudaStream_t st);
 // Y = A_H X for nrhs right-hand sides (complex128, 3 nc x nrhs column-major,
 // original order) on the tensor cores, in blocks of 32; BF16 storage only.
 void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2* y, int64_t nc,
@@ -295,6 +316,11 @@ struct hm_matrix {
     // statistics
     double t_tree_ms = 0, t_part_ms = 0, t_near_ms = 0, t_aca_ms = 0, t_recomp_ms = 0,
            t_copy_ms = 0, t_total_ms = 0;
+    // the layout phase in parts (host clock): storage plan, arena and item
+    // tables, staged-factor copy, BF16 copy, autotuner / cache, product graph
+    double t_plan_ms = 0, t_arena_ms = 0, t_stage_ms = 0, t_bf16_ms = 0, t_tune_ms = 0,
+           t_graph_ms = 0;
+    double apply_flops_df = 0;  // double-float flops of the factor application U' = U T_U
     int64_t aca_overflow_reruns = 0;
     int64_t aca_batches = 0;
     // device time of the ACA and recompression kernels (CUDA events on the build stream)

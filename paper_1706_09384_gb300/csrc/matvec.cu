@@ -1182,6 +1182,7 @@ void matvec_dev_destroy(MatvecDev* m) {
     for (DevBuf& d : m->tile_bufs) cudaFree(d.p);
     if (m->xb) cudaFree(m->xb);
     if (m->ym) cudaFree(m->ym);
+    if (m->iperm) cudaFree(m->iperm);
     if (m->tm) cudaFree(m->tm);
     if (m->t16) cudaFree(m->t16);
     if (m->tmap_xb) cudaFree(m->tmap_xb);
@@ -1449,9 +1450,18 @@ void matvec_graph(MatvecDev* m, const int64_t* d_perm, const double2* x, float2*
 
 // Error code of the streamed kernels since the last call (0 = none); resets it.
 int matvec_take_error(MatvecDev* m, cudaStream_t st) {
-    int e = 0;
-    HM_CUDA(cudaMemcpyAsync(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PinnedInt flag;
+    matvec_queue_error(m, flag.p, st);
     HM_CUDA(cudaStreamSynchronize(st));
+    return matvec_read_error(m, flag.p, st);
+}
+
+void matvec_queue_error(MatvecDev* m, int* pinned, cudaStream_t st) {
+    HM_CUDA(cudaMemcpyAsync(pinned, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+}
+
+int matvec_read_error(MatvecDev* m, const int* pinned, cudaStream_t st) {
+    const int e = *pinned;
     if (e) HM_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
     return e;
 }

@@ -127,6 +127,7 @@ struct MatvecDev {
     // first use: XB bf16 rows (x, -i x) per DOF, Y and T in FP32, T16 = bf16(T)
     uint32_t* xb = nullptr;
     float2* ym = nullptr;
+    int64_t* iperm = nullptr;  // tree position of each input-order point
     float2* tm = nullptr;
     uint32_t* t16 = nullptr;
     // TMA descriptors (CUtensorMap, 128 bytes each): the BF16 arena viewed as

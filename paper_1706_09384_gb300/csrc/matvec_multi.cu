@@ -728,23 +728,53 @@ __global__ void tscale_kernel(const DevChunk16* hdr, int64_t nchunk, float* tsca
     for (int c = threadIdx.x; c < ch.ncols; c += blockDim.x) tscale[ch.vec + c] = ch.scale * ch.fold;
 }
 
+// The gather and scatter of the block product transpose between the caller's
+// column-major vectors (input order, one column per right-hand side) and the
+// tree-order DOF rows of 32 right-hand sides, through a shared-memory tile of
+// GS_Q consecutive input-order DOFs: each warp reads (or writes) one column
+// contiguously, and each DOF's row moves whole to its tree position.
+constexpr int GS_Q = 64;        // input-order DOFs per CTA
+constexpr int GS_THREADS = 256;
+
+__global__ void invert_perm_kernel(const int64_t* perm, int64_t nc, int64_t* iperm) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < nc) iperm[perm[p]] = p;
+}
+
+// Tree-order DOF of input-order DOF i.
+__device__ __forceinline__ int64_t tree_dof(const int64_t* iperm, int64_t i) {
+    const int64_t p = i / 3;
+    return 3 * iperm[p] + (i - 3 * p);
+}
+
 // XB rows 2q and 2q + 1 of tree-order DOF q: (x_r, x_i) and (x_i, -x_r) of each
 // right-hand side s (zero for s >= nrhs); x is column-major n x nrhs, input order.
-__global__ void gather_xb_kernel(const int64_t* perm, const double2* x, int64_t n, int nrhs,
-                                 uint32_t* XB, int64_t nc) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= 3 * nc * NR) return;
-    const int64_t q = idx / NR;
-    const int s = (int)(idx - q * NR);
-    float xr = 0.f, xi = 0.f;
-    if (s < nrhs) {
-        const int64_t p = q / 3, a = q - 3 * p;
-        const double2 u = x[(int64_t)s * n + 3 * perm[p] + a];
-        xr = (float)u.x;
-        xi = (float)u.y;
+__global__ void __launch_bounds__(GS_THREADS) gather_xb_kernel(const int64_t* iperm, const double2* x,
+                                                               int64_t n, int nrhs, uint32_t* XB) {
+    __shared__ float2 tile[NR][GS_Q + 1];
+    const int64_t i0 = blockIdx.x * (int64_t)GS_Q;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // columns: warp w reads right-hand sides w, w + 8, ...; lanes the tile's DOFs
+    for (int s = wid; s < NR; s += GS_THREADS / 32)
+        for (int il = lane; il < GS_Q; il += 32) {
+            const int64_t i = i0 + il;
+            float2 v = make_float2(0.f, 0.f);
+            if (s < nrhs && i < n) {
+                const double2 u = x[(int64_t)s * n + i];
+                v = make_float2((float)u.x, (float)u.y);
+            }
+            tile[s][il] = v;
+        }
+    __syncthreads();
+    // rows: 32 consecutive threads write one 128-byte XB row
+    for (int e = tid; e < 2 * GS_Q * NR; e += GS_THREADS) {
+        const int s = e % NR, r = e / NR, il = r >> 1;
+        const int64_t i = i0 + il;
+        if (i >= n) continue;
+        const int64_t q = tree_dof(iperm, i);
+        const float2 v = tile[s][il];
+        XB[(2 * q + (r & 1)) * NR + s] = (r & 1) ? pack_bf16(v.y, -v.x) : pack_bf16(v.x, v.y);
     }
-    XB[(2 * q) * NR + s] = pack_bf16(xr, xi);
-    XB[(2 * q + 1) * NR + s] = pack_bf16(xi, -xr);
 }
 
 // T16 = T rounded to bf16 pairs (the phase-2 weights of the U columns).
@@ -755,16 +785,25 @@ __global__ void t16_kernel(const float4* T, uint2* T16, int64_t npair) {
     T16[i] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
 }
 
-__global__ void scatter_multi_kernel(const int64_t* perm, const float2* Y, int64_t n, int nrhs,
-                                     double2* y, int64_t nc) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= 3 * nc * NR) return;
-    const int64_t q = idx / NR;
-    const int s = (int)(idx - q * NR);
-    if (s >= nrhs) return;
-    const int64_t p = q / 3, a = q - 3 * p;
-    const float2 v = Y[idx];
-    y[(int64_t)s * n + 3 * perm[p] + a] = make_double2(v.x, v.y);
+// y (column-major n x nrhs, input order) from the tree-order rows Y[q][32].
+__global__ void __launch_bounds__(GS_THREADS) scatter_multi_kernel(const int64_t* iperm, const float2* Y,
+                                                                   int64_t n, int nrhs, double2* y) {
+    __shared__ float2 tile[NR][GS_Q + 1];
+    const int64_t i0 = blockIdx.x * (int64_t)GS_Q;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < GS_Q * NR; e += GS_THREADS) {  // whole 256-byte rows
+        const int s = e % NR, il = e / NR;
+        const int64_t i = i0 + il;
+        tile[s][il] = i < n ? Y[tree_dof(iperm, i) * NR + s] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int s = wid; s < nrhs; s += GS_THREADS / 32)
+        for (int il = lane; il < GS_Q; il += 32) {
+            const int64_t i = i0 + il;
+            if (i >= n) continue;
+            const float2 v = tile[s][il];
+            y[(int64_t)s * n + i] = make_double2(v.x, v.y);
+        }
 }
 
 typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -996,8 +1035,13 @@ void make_block_items(MatvecDev* m, const MatvecPlan& plan, const std::vector<De
 
 static int multi_grid(int64_t nitems) { return (int)std::min<int64_t>(nitems, device_sms()); }
 
-static void multi_setup(MatvecDev* m, int64_t n, cudaStream_t st) {
+static void multi_setup(MatvecDev* m, const int64_t* d_perm, int64_t n, cudaStream_t st) {
     if (m->xb) return;
+    const int64_t nc = n / 3;
+    HM_CUDA(cudaMalloc((void**)&m->iperm, (size_t)std::max<int64_t>(nc, 1) * 8));
+    invert_perm_kernel<<<(unsigned)hm_cdiv(nc, 256), 256, 0, st>>>(d_perm, nc, m->iperm);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
     HM_CUDA(cudaFuncSetAttribute(mvc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(P1Smem) + 1024));
     HM_CUDA(cudaFuncSetAttribute(mvc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1049,15 +1093,15 @@ void matvec_multi(MatvecDev* m, const int64_t* d_perm, const double2* x, double2
                   int32_t nrhs, cudaStream_t st) {
     if (!m->arena16) hm_throw(HM_ERR_UNSUPPORTED, "tensor-core block product needs BF16 storage");
     const int64_t n = 3 * nc;
-    multi_setup(m, n, st);
-    const unsigned nbv = (unsigned)hm_cdiv(n * NR, 256);
+    multi_setup(m, d_perm, n, st);
+    const unsigned nbv = (unsigned)hm_cdiv(n, GS_Q);
     for (int32_t c0 = 0; c0 < nrhs; c0 += NR) {
         const int ng = std::min<int32_t>(NR, nrhs - c0);
-        gather_xb_kernel<<<nbv, 256, 0, st>>>(d_perm, x + (int64_t)c0 * n, n, ng, m->xb, nc);
+        gather_xb_kernel<<<nbv, GS_THREADS, 0, st>>>(m->iperm, x + (int64_t)c0 * n, n, ng, m->xb);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
         multi_phases(m, n, st, nullptr, nullptr);
-        scatter_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, m->ym, n, ng, y + (int64_t)c0 * n, nc);
+        scatter_multi_kernel<<<nbv, GS_THREADS, 0, st>>>(m->iperm, m->ym, n, ng, y + (int64_t)c0 * n);
         HM_CUDA(cudaGetLastError());
         HM_LAUNCHED();
     }
@@ -1070,17 +1114,17 @@ void matvec_multi_profile(MatvecDev* m, const int64_t* d_perm, const double2* x,
                           int64_t nc, int32_t reps, double ms[4], cudaStream_t st) {
     matvec_multi(m, d_perm, x, y, nc, NR, st);  // allocations and attributes
     const int64_t n = 3 * nc;
-    const unsigned nbv = (unsigned)hm_cdiv(n * NR, 256);
+    const unsigned nbv = (unsigned)hm_cdiv(n, GS_Q);
     cudaEvent_t ev[5];
     for (auto& e : ev) HM_CUDA(cudaEventCreate(&e));
     for (int q = 0; q < 4; ++q) ms[q] = 0.0;
     for (int r = 0; r < reps; ++r) {
         HM_CUDA(cudaEventRecord(ev[0], st));
-        gather_xb_kernel<<<nbv, 256, 0, st>>>(d_perm, x, n, NR, m->xb, nc);
+        gather_xb_kernel<<<nbv, GS_THREADS, 0, st>>>(m->iperm, x, n, NR, m->xb);
         HM_LAUNCHED();
         multi_phases(m, n, st, ev[1], ev[2]);
         HM_CUDA(cudaEventRecord(ev[3], st));
-        scatter_multi_kernel<<<nbv, 256, 0, st>>>(d_perm, m->ym, n, NR, y, nc);
+        scatter_multi_kernel<<<nbv, GS_THREADS, 0, st>>>(m->iperm, m->ym, n, NR, y);
         HM_LAUNCHED();
         HM_CUDA(cudaEventRecord(ev[4], st));
         HM_CUDA(cudaGetLastError());

@@ -1,13 +1,16 @@
-// scratch.cu — the library's scratch memory for solver temporaries.
+// scratch.cu — the library's scratch memory for solver and build temporaries.
 //
 // Temporaries of a solve (the GMRES basis, its small Hessenberg problem,
-// partial sums) come from a stream-ordered memory pool that the library
-// creates per device (cudaMemPoolCreate) with its release threshold at the
-// maximum, so memory a solve frees stays reserved in the pool and the next
-// solve, on this or any other handle, takes it back without a cudaMalloc or
-// a device-wide synchronisation.  The pool's memory is returned to the
-// device when the process exits.  Small pinned host buffers for reading
-// scalars back are kept in a process-wide free list.
+// partial sums) and of a build (the ACA factors and their double-float
+// copies, the staged factors) come from a stream-ordered memory pool that the
+// library creates per device (cudaMemPoolCreate) with its release threshold at
+// the maximum, so memory freed stays reserved in the pool and the next solve
+// or build, on this or any other handle, takes it back without a cudaMalloc,
+// a cudaFree (tens of milliseconds for the tens of gigabytes of an ACA batch)
+// or a device-wide synchronisation.  The pool's unused memory is returned to
+// the device by hm_release_cached_memory and when the process exits.  Small
+// pinned host buffers for reading scalars back are kept in a process-wide
+// free list.
 #include <mutex>
 #include <vector>
 
@@ -50,13 +53,36 @@ cudaMemPool_t pool_of_current_device() {
 
 void* hm_scratch_alloc(size_t bytes, cudaStream_t st) {
     void* p = nullptr;
-    const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool_of_current_device(), st);
+    cudaMemPool_t pool = pool_of_current_device();
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, st);
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool's reserved pieces may not fit this request: hand them back
+        // to the device (once the stream's frees are done) and try once more
+        cudaGetLastError();
+        HM_CUDA(cudaStreamSynchronize(st));
+        HM_CUDA(cudaMemPoolTrimTo(pool, 0));
+        e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, pool, st);
+    }
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
-        hm_throw(HM_ERR_OOM, "device memory exhausted (solver scratch)");
+        hm_throw(HM_ERR_OOM, "device memory exhausted (library scratch)");
     }
     HM_CUDA(e);
     return p;
+}
+
+size_t hm_scratch_cached() {
+    cudaMemPool_t pool = pool_of_current_device();
+    uint64_t res = 0, used = 0;
+    HM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res));
+    HM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    return res > used ? (size_t)(res - used) : 0;
+}
+
+void hm_scratch_trim() {
+    std::lock_guard<std::mutex> lk(g_sc_mutex);
+    for (int d = 0; d < SC_MAX_DEVICES; ++d)
+        if (g_pool[d]) HM_CUDA(cudaMemPoolTrimTo(g_pool[d], 0));
 }
 
 void hm_scratch_free(void* p, cudaStream_t st) {

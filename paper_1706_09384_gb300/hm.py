@@ -93,6 +93,7 @@ SIGNATURES = {
     "hm_profile_matvec": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_profile_matvec_multi": (_I32, [_P, _I32, _P, _P, _P]),
     "hm_kernel_launches": (_I64, []),
+    "hm_release_cached_memory": (_I32, []),
     "hm_free": (None, [_P]),
     "hm_status_string": (C.c_char_p, [_I32]),
     "hm_last_error": (C.c_char_p, []),
@@ -141,6 +142,11 @@ def _stream_ptr(stream):
 
 def hm_kernel_launches():
     return lib().hm_kernel_launches()
+
+
+def hm_release_cached_memory():
+    """Return the memory the library's pools keep for later builds and solves."""
+    _check(lib().hm_release_cached_memory(), "hm_release_cached_memory")
 
 
 def hm_opts_default(**kw):
