@@ -430,16 +430,10 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
             float bestf = -1.f, s1maxf = 0.f;  // the shortlist's bounds in FP32
             int64_t bj = -1;
             for (int64_t j = tid; j < n; j += AT) {
-                double2 G[9];
-                if (J.tau_begin + ihat == J.sig_begin + j) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
-                } else {
-                    green_tensor(gp, xr + 3 * ihat, xc + 3 * j, nc ? nc + 3 * j : nullptr, G);
-                    apply_weight(gp, J.sig_begin + j, G);
-                }
+                // the double-float sums first, the FP64 tensor after them: G is not
+                // live across the loop (36 registers)
+                float s9[9][4] = {};
                 if (DF && k > 0) {
-                    float s9[9][4] = {};
                     // V(j, p) for p + 1 is loaded while p is summed
                     const float4* vp = Vd + 3 * j;
                     float4 v0 = vp[0], v1 = vp[1], v2 = vp[2];
@@ -462,6 +456,16 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                         v1 = w1;
                         v2 = w2;
                     }
+                }
+                double2 G[9];
+                if (J.tau_begin + ihat == J.sig_begin + j) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
+                } else {
+                    green_tensor(gp, xr + 3 * ihat, xc + 3 * j, nc ? nc + 3 * j : nullptr, G);
+                    apply_weight(gp, J.sig_begin + j, G);
+                }
+                if (DF && k > 0) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
                 } else if (!DF) {
@@ -584,16 +588,8 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
             double unused = 0.0;
             int64_t bi = -1;
             for (int64_t i = tid; i < m; i += AT) {
-                double2 G[9];
-                if (J.tau_begin + i == J.sig_begin + jhat) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
-                } else {
-                    green_tensor(gp, xr + 3 * i, xc + 3 * jhat, nc ? nc + 3 * jhat : nullptr, G);
-                    apply_weight(gp, J.sig_begin + jhat, G);
-                }
+                float s9[9][4] = {};  // double-float sums, then the FP64 tensor
                 if (DF && k > 0) {
-                    float s9[9][4] = {};
                     // U(i, p) for p + 1 is loaded while p is summed
                     const float4* up = Ud + 3 * i;
                     float4 u0 = up[0], u1 = up[1], u2 = up[2];
@@ -616,6 +612,16 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                         u1 = w1;
                         u2 = w2;
                     }
+                }
+                double2 G[9];
+                if (J.tau_begin + i == J.sig_begin + jhat) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) G[q] = make_double2((q % 4 == 0) ? gp.diag : 0.0, 0.0);
+                } else {
+                    green_tensor(gp, xr + 3 * i, xc + 3 * jhat, nc ? nc + 3 * jhat : nullptr, G);
+                    apply_weight(gp, J.sig_begin + jhat, G);
+                }
+                if (DF && k > 0) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q) sub_df(G[q], s9[q]);
                 } else if (!DF) {
