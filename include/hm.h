@@ -491,9 +491,9 @@ int64_t hm_kernel_launches(void);
 
 /* Returns to the device the memory that the library's stream-ordered pools
  * hold for reuse: the scratch of hm_gmres / hm_gmres_multi and the build
- * workspaces of hm_build / hm_build2 / hm_build_batch (the ACA factors with
- * their double-float copies, half of the free device memory at most per batch,
- * and the staged factors), which stay reserved after a call so that the next
+ * workspaces of hm_build / hm_build2 / hm_build_batch (the ACA factors as
+ * double-float pairs and their Gram matrices, half of the free device memory
+ * at most per batch, and the staged factors), which stay reserved after a call so that the next
  * build or solve on any handle reuses them without allocating.  A build that
  * runs short of device memory returns them by itself first.  Call it with no
  * library work in flight (memory still used by queued work stays reserved).

@@ -390,9 +390,12 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
         if (gps && tid == 0) s_gp = gps[J.pad_];
         const GreenParams& gp = gps ? s_gp : gp0;
         const int64_t m = J.m, n = J.n, m3 = 3 * m, n3 = 3 * n;
-        double2* U = work + J.u_off;
-        double2* V = work + J.v_off;
-        float4* Ud = DF ? work_df + J.u_off : nullptr;  // double-float copies of U and V
+        // DF: the factors are kept only as double-float pairs (every later
+        // reader, the residuals, the norm update and the factor application,
+        // takes those), the FP64 path keeps them in FP64
+        double2* U = DF ? nullptr : work + J.u_off;
+        double2* V = DF ? nullptr : work + J.v_off;
+        float4* Ud = DF ? work_df + J.u_off : nullptr;
         float4* Vd = DF ? work_df + J.v_off : nullptr;
         double2* GU = (gram && J.g_off >= 0) ? gram + J.g_off : nullptr;  // U^H U, ld cap
         double2* GV = GU ? GU + (int64_t)J.cap * J.cap : nullptr;          // V^H V, ld cap
@@ -673,7 +676,7 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
             }
             if (tid == 0) s_inext = bi;
             if constexpr (DF) {
-                // ---- step 5: new factor columns (FP64 and their double-float copies) ----
+                // ---- step 5: new factor columns, formed in FP64, stored as double-float pairs ----
                 if (k + 3 <= J.cap) {
                     for (int64_t r = tid; r < m3; r += AT)
 #pragma unroll
@@ -681,16 +684,12 @@ __global__ void __launch_bounds__(AT, ACA_MIN_CTAS) aca_kernel(GreenParams gp0,
                             double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
                             for (int a = 0; a < 3; ++a) cfma(acc, C[3 * r + a], s_gam[3 * a + q]);
-                            U[r + (int64_t)(k + q) * m3] = acc;
                             Ud[r + (int64_t)(k + q) * m3] = df_of(acc);
                         }
                     for (int64_t c = tid; c < n3; c += AT)
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const double2 vn = cconj(R[a * n3 + c]);
-                            V[c + (int64_t)(k + a) * n3] = vn;
-                            Vd[c + (int64_t)(k + a) * n3] = df_of(vn);
-                        }
+                        for (int a = 0; a < 3; ++a)
+                            Vd[c + (int64_t)(k + a) * n3] = df_of(cconj(R[a * n3 + c]));
                 }
                 __syncthreads();  // publishes the new columns to the CTA
                 if (k + 3 > J.cap) {

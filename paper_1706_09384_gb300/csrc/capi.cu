@@ -314,9 +314,9 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 const int64_t a = todo[pos];
                 const hm_block& bk = blk_of(a);
                 const int64_t m = pts_of(a, bk.tau), n = pts_of(a, bk.sigma);
-                // FP64 factors, their double-float copies, Gram matrices
-                const int64_t need = (6 * (m + n) * (int64_t)cap[a] + 2 * (int64_t)cap[a] * cap[a]) * 16;
-                if (!jobs.empty() && (2 * woff + goff) * 16 + need > budget) break;
+                // double-float factors (16 bytes an entry), Gram matrices
+                const int64_t need = (3 * (m + n) * (int64_t)cap[a] + 2 * (int64_t)cap[a] * cap[a]) * 16;
+                if (!jobs.empty() && (woff + goff) * 16 + need > budget) break;
                 AcaJob J;
                 J.tau_begin = poff[aq[a]] + cl_of(a, bk.tau).begin;
                 J.m = m;
@@ -337,12 +337,15 @@ void build_low_rank(std::vector<hm_matrix*>& hs, std::vector<DevBuf>& staging,
                 ++pos;
             }
             const int64_t nj = (int64_t)jobs.size();
-            ws_peak = std::max<int64_t>(ws_peak, (2 * woff + goff) * 16);
-            ws_tot += (2 * woff + goff) * 16;
+            ws_peak = std::max<int64_t>(ws_peak, (woff + goff) * 16);
+            ws_tot += (woff + goff) * 16;
             const int nctas = (int)std::min<int64_t>(nj, (int64_t)nsm * aca_ctas_per_sm(capmax));
             std::vector<DevBuf> tmp;
             auto t0 = clk::now();
-            double2* d_work = (double2*)hm_dmalloc_pooled(tmp, (size_t)woff * 16, st);
+            // the factors as double-float pairs only: every reader takes those
+            // (the residuals, the norm update, the factor application), the
+            // recompression takes the Gram matrices the ACA accumulates
+            double2* d_work = nullptr;
             float4* d_work_df = (float4*)hm_dmalloc_pooled(tmp, (size_t)woff * 16, st);
             double2* d_gram = (double2*)hm_dmalloc_pooled(tmp, (size_t)goff * 16, st);
             AcaJob* d_jobs = (AcaJob*)hm_dmalloc(tmp, nj * sizeof(AcaJob), st, false);
