@@ -66,8 +66,8 @@ typedef struct {
     int32_t storage;          /* hm_storage for dense blocks and factors (HM_STORE_FP32) */
     int32_t aca_fp32;         /* must be 0 (HM_ERR_ARG otherwise): the ACA computes its residual
                                  rows and columns in double-float arithmetic (FP32 pairs, ~44
-                                 bits) over double-float copies of U and V, its pivots, Gram
-                                 matrices and norm updates in FP64; no FP32 variant exists */
+                                 bits) over U and V stored as double-float pairs, its pivots
+                                 and norm updates in FP64; no FP32 variant exists */
     double diag_value;        /* value of the i = j blocks: diag_value * I3 (1.0) */
     double fp64_switch_ksr;   /* > 0.  Green's tensors (near field, ACA rows and columns,
                                  randomized sketches) are evaluated in FP64 where k_s r < this
@@ -245,9 +245,11 @@ hm_status hm_gmres_batch(hm_handle h, const void* b, void* x, int32_t restart, d
  * hm_matvec_host or hm_gmres on the handle. */
 hm_status hm_matvec(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream);
 
-/* Same product with HOST buffers: x is copied to the device, y back to the
- * host, inside the call (synchronises stream before returning).  Pinned host
- * memory gives the fastest copies.  Errors as hm_matvec. */
+/* Same product with HOST buffers: x is copied to a device buffer of the handle
+ * and y back, inside the call (synchronises stream before returning); the
+ * result and the product's error code come back with one synchronisation.
+ * Pinned host memory gives the fastest copies.  x and y must not overlap.
+ * Errors as hm_matvec. */
 hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void* stream);
 
 /* Solves A_H x = b by restarted GMRES(restart) with x_0 = 0 in FP64 vectors

@@ -13,9 +13,10 @@
 //   6. ||B_{k+1}||_F^2 = ||B_k||^2 + 2 Re <B_k, dB> + ||dB||^2, FP64
 //   stop when ||dB||_F <= eps ||B_{k+1}||_F (Eq. stop_part read for rank 3),
 //   when no row is left, or at full rank.  Ties in an argmax go to the lowest
-//   index.  The factors live in a global FP64 workspace with a fixed column
-//   capacity; a block that needs more reports an overflow and is re-run with a
-//   larger capacity by the host.
+//   index.  The factors live in a global workspace with a fixed column
+//   capacity (double-float pairs in the build, FP64 in the allocation-free
+//   entry point); a block that needs more reports an overflow and is re-run
+//   with a larger capacity by the host.
 //
 // sigma_1 and sigma_3 of a 3x3 block M are computed from the invariants of
 // M^H M: e1 = ||M||_F^2, e2 = sum of |2x2 minors|^2, e3 = |det M|^2 (the
@@ -232,9 +233,10 @@ HM_D void warp_sum_many(double (&x)[N]) {
 // the bulk of the ACA's arithmetic.  On GB300 FP64 runs at 1/64 of the FP32
 // rate, so these sums run in double-float arithmetic (Dekker's product with an
 // FMA, Knuth's two-sum; every operation an explicitly rounded intrinsic so
-// nothing is fused) over double-float copies of U and V, and the difference
-// with the FP64 tensor is taken in FP64.  The pivots, the norm updates of
-// step 6, the Gram matrices and the factors themselves stay FP64.
+// nothing is fused) over U and V stored as double-float pairs (each new
+// column formed in FP64, then split), and the difference with the FP64 tensor
+// is taken in FP64.  The pivots and the norm updates of step 6 (sums rounded
+// to FP64 once per thread) stay FP64.
 __device__ __forceinline__ void dfm(float& h, float& l, float ah, float al, float bh, float bl) {
     const float p = __fmul_rn(ah, bh);
     float e = __fmaf_rn(ah, bh, -p);

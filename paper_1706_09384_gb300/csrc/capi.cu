@@ -1012,6 +1012,9 @@ hm_status hm_matvec_host(hm_handle h, int32_t nrhs, const void* x, void* y, void
         h->staging_cols = nrhs;
     }
     PinnedInt flag;  // the product's error code, read back with y (one synchronisation)
+    const char* xb = (const char*)x;
+    const char* yb = (const char*)y;
+    if (xb < yb + n * nrhs * 16 && yb < xb + n * nrhs * 16) hm_throw(HM_ERR_ARG, "x and y overlap");
     HM_CUDA(cudaMemcpyAsync(h->d_xh, x, (size_t)n * nrhs * 16, cudaMemcpyHostToDevice, st));
     const hm_status s = hm_matvec(h, nrhs, h->d_xh, h->d_yh, stream);
     if (s != HM_OK) return s;

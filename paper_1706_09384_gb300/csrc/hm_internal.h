@@ -202,7 +202,7 @@ void launch_aca(const GreenParams& gp, const double* d_pts_p, const double* d_nr
                 int64_t flag_stride, double2* d_rowbuf, double2* d_colbuf, int64_t rowbuf_stride,
                 int64_t colbuf_stride, double eps, AcaResult* d_res, int nctas, int capmax,
                 int* d_counter, cudaStream_t st, const GreenParams* d_gps = nullptr,
-                float4* d_work_df = nullptr);  // double-float copies of U, V (same layout): DF residuals
+                float4* d_work_df = nullptr);  // U, V as double-float pairs (then d_work may be null)
 int aca_ctas_per_sm(int capmax);
 // Core of the recompression for a batch: ranks r' and the k x r' transforms.
 // g_off[j] >= 0: the job's Gram matrices (ld g_ld[j]) are read from d_gram instead of

@@ -747,6 +747,11 @@ __global__ void gather_x_kernel(const int64_t* perm, const double2* x, float2* x
     xp[q] = make_float2((float)v.x, (float)v.y);
 }
 
+__global__ void invert_perm_kernel(const int64_t* perm, int64_t nc, int64_t* iperm) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < nc) iperm[perm[p]] = p;
+}
+
 __global__ void scatter_y_kernel(const int64_t* perm, const float2* yp, double2* y, int64_t nc) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= 3 * nc) return;
@@ -1288,6 +1293,14 @@ void matvec_alg_bytes(const MatvecDev* m, int64_t ndof, int64_t out[3]) {
     out[0] = v * (m->alg_v + ndof + m->t_elems);
     out[1] = v * (m->alg_du + ndof + m->t_elems + ndof);
     out[2] = v * (m->alg_v + m->alg_du) + 2 * 16 * ndof;  // complex128 x in, y out
+}
+
+void matvec_ensure_iperm(MatvecDev* m, const int64_t* d_perm, int64_t nc, cudaStream_t st) {
+    if (m->iperm) return;
+    HM_CUDA(cudaMalloc((void**)&m->iperm, (size_t)std::max<int64_t>(nc, 1) * 8));
+    invert_perm_kernel<<<(unsigned)hm_cdiv(nc, 256), 256, 0, st>>>(d_perm, nc, m->iperm);
+    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
 }
 
 void launch_gather_x(const int64_t* d_perm, const double2* x, float2* xp, int64_t nc,

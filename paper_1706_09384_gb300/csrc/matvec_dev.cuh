@@ -160,3 +160,12 @@ void make_block_tmaps(void* d_maps, const uint32_t* arena16, int64_t words,
 // Block of NRHS_BLOCK right-hand sides for the tensor-core product (created on
 // first use; tree-order vectors, right-hand side fastest: v[dof * NRHS_BLOCK + s]).
 constexpr int NRHS_BLOCK = 32;
+
+// m->iperm (the tree position of each input-order point) from the handle's
+// permutation, computed on first use.
+void matvec_ensure_iperm(MatvecDev* m, const int64_t* d_perm, int64_t nc, cudaStream_t st);
+// Tree-order DOF of input-order DOF i.
+__device__ __forceinline__ int64_t tree_dof(const int64_t* iperm, int64_t i) {
+    const int64_t p = i / 3;
+    return 3 * iperm[p] + (i - 3 * p);
+}

@@ -736,17 +736,6 @@ __global__ void tscale_kernel(const DevChunk16* hdr, int64_t nchunk, float* tsca
 constexpr int GS_Q = 64;        // input-order DOFs per CTA
 constexpr int GS_THREADS = 256;
 
-__global__ void invert_perm_kernel(const int64_t* perm, int64_t nc, int64_t* iperm) {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < nc) iperm[perm[p]] = p;
-}
-
-// Tree-order DOF of input-order DOF i.
-__device__ __forceinline__ int64_t tree_dof(const int64_t* iperm, int64_t i) {
-    const int64_t p = i / 3;
-    return 3 * iperm[p] + (i - 3 * p);
-}
-
 // XB rows 2q and 2q + 1 of tree-order DOF q: (x_r, x_i) and (x_i, -x_r) of each
 // right-hand side s (zero for s >= nrhs); x is column-major n x nrhs, input order.
 __global__ void __launch_bounds__(GS_THREADS) gather_xb_kernel(const int64_t* iperm, const double2* x,
@@ -1037,11 +1026,7 @@ static int multi_grid(int64_t nitems) { return (int)std::min<int64_t>(nitems, de
 
 static void multi_setup(MatvecDev* m, const int64_t* d_perm, int64_t n, cudaStream_t st) {
     if (m->xb) return;
-    const int64_t nc = n / 3;
-    HM_CUDA(cudaMalloc((void**)&m->iperm, (size_t)std::max<int64_t>(nc, 1) * 8));
-    invert_perm_kernel<<<(unsigned)hm_cdiv(nc, 256), 256, 0, st>>>(d_perm, nc, m->iperm);
-    HM_CUDA(cudaGetLastError());
-    HM_LAUNCHED();
+    matvec_ensure_iperm(m, d_perm, n / 3, st);
     HM_CUDA(cudaFuncSetAttribute(mvc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(P1Smem) + 1024));
     HM_CUDA(cudaFuncSetAttribute(mvc_phase2, cudaFuncAttributeMaxDynamicSharedMemorySize,
