@@ -982,7 +982,11 @@ static void make_groups(const MatvecPlan& plan, const std::vector<DevChunk16>& c
 void make_block_items(MatvecDev* m, const MatvecPlan& plan, const std::vector<DevChunk16>& c16,
                       std::vector<DevBuf>& owner, cudaStream_t st) {
     std::vector<TcItem> t2;
-    std::vector<uint32_t> codes;
+    t2.reserve(m->h_items2.size());
+    int64_t ncodes = 0;  // one code per phase-2 column (millions): sized once
+    for (const WorkItem& w : m->h_items2)
+        for (int32_t q = w.first; q < w.last; ++q) ncodes += c16[m->h_order2[q]].ncols;
+    std::vector<uint32_t> codes((size_t)ncodes);
     int64_t col = 0;
     for (const WorkItem& w : m->h_items2) {
         const DevChunk16& a = c16[m->h_order2[w.first]];
@@ -994,8 +998,11 @@ void make_block_items(MatvecDev* m, const MatvecPlan& plan, const std::vector<De
         t.rows = w.rows;
         for (int32_t q = w.first; q < w.last; ++q) {
             const DevChunk16& c = c16[m->h_order2[q]];
-            for (int32_t j = 0; j < c.ncols; ++j)
-                codes.push_back(c.kind != 0 ? ((uint32_t)(c.vec + j) | 0x80000000u) : (uint32_t)(2 * (c.vec + j)));
+            uint32_t* dst = codes.data() + col;
+            if (c.kind != 0)
+                for (int32_t j = 0; j < c.ncols; ++j) dst[j] = (uint32_t)(c.vec + j) | 0x80000000u;
+            else
+                for (int32_t j = 0; j < c.ncols; ++j) dst[j] = (uint32_t)(2 * (c.vec + j));
             col += c.ncols;
         }
         t.ncol = (int32_t)(col - t.col0);
