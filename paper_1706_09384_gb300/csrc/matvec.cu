@@ -958,19 +958,22 @@ static void set_tiling(MatvecDev* m, const MatvecPlan& plan, int64_t item_bytes,
     std::vector<int32_t> o1, o2;
     make_items(plan.col_leaf_begin, plan.col_items, plan.chunks, plan, item_bytes, it1, o1);
     make_items(plan.row_leaf_begin, plan.row_items, plan.chunks, plan, item_bytes, it2, o2);
-    // largest items first
-    auto bytes_of = [&](const WorkItem& w, const std::vector<int32_t>& o) {
-        int64_t s = 0;
-        for (int32_t q = w.first; q < w.last; ++q)
-            s += (int64_t)plan.chunks[o[q]].ld * plan.chunks[o[q]].ncols;
-        return s;
+    // largest items first (each item's bytes summed once, not per comparison)
+    auto largest_first = [&](std::vector<WorkItem>& it, const std::vector<int32_t>& o) {
+        std::vector<std::pair<int64_t, WorkItem>> kv;
+        kv.reserve(it.size());
+        for (const WorkItem& w : it) {
+            int64_t s = 0;
+            for (int32_t q = w.first; q < w.last; ++q)
+                s += (int64_t)plan.chunks[o[q]].ld * plan.chunks[o[q]].ncols;
+            kv.push_back({s, w});
+        }
+        std::stable_sort(kv.begin(), kv.end(),
+                         [](const auto& a, const auto& b) { return a.first > b.first; });
+        for (size_t i = 0; i < it.size(); ++i) it[i] = kv[i].second;
     };
-    std::stable_sort(it1.begin(), it1.end(), [&](const WorkItem& a, const WorkItem& b) {
-        return bytes_of(a, o1) > bytes_of(b, o1);
-    });
-    std::stable_sort(it2.begin(), it2.end(), [&](const WorkItem& a, const WorkItem& b) {
-        return bytes_of(a, o2) > bytes_of(b, o2);
-    });
+    largest_first(it1, o1);
+    largest_first(it2, o2);
     HM_CUDA(cudaStreamSynchronize(st));  // the old tiling is no longer in use
     for (DevBuf& d : m->tile_bufs) cudaFree(d.p);
     m->tile_bufs.clear();
